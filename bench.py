@@ -1,0 +1,455 @@
+#!/usr/bin/env python
+"""Throughput benchmark: batched forward + adjoint gradient (samples/s).
+
+Workloads (synthetic, seeded; arXiv 2404.06314 ansatz family, Sec. III):
+  qnn12  12 qubits, 6 re-uploading layers (RX(x), RY(w), RZ(w) + CZ ring),
+         B = 1024, complex64, observable sum_i Z_i Z_{i+1}      (default)
+  qnn20  20 qubits, RX(x) encoding, 4 layers RY/RZ + CNOT chain, B = 64,
+         complex64, observables Z_0 and Z^{(x)20}
+A step is one qtm_forward + one qtm_adjoint over the batch (expectation
+values, grad_x, batch-summed grad_w).  The default run reports qnn12 as the
+headline and qnn20 (the HBM-bound path) in "n20".
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+Under torchrun each rank processes its own batch (weak scaling, no collective
+on the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "qnn12": dict(builder="workload_12q", B=1024, dtype="c64"),
+    "qnn20": dict(builder="workload_20q", B=64, dtype="c64"),
+    "qnn16": dict(builder="workload_16q_train", B=256, dtype="c64"),
+}
+METRIC = "samples/sec fwd+adjoint grad at 12q and 20q; achieved HBM GB/s vs peak"
+L2_FLUSH_BYTES = 256 << 20   # > 126 MB L2
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return p, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def fp32_alu_peak_tflops(sm_mhz: float) -> float:
+    # 152 SMs x 128 FP32 lanes x 2 flop (FMA) per clock
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+        self.t0 = self.t1 = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="qtm_clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-i", str(self.dev)],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def mark(self, which):
+        setattr(self, which, time.time())
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            with open(self.path) as f:
+                for line in f:
+                    parts = [p.strip() for p in line.split(",")]
+                    if len(parts) >= 9 and parts[1].replace(".", "").isdigit():
+                        rows.append(parts)
+        except Exception:
+            pass
+        finally:
+            try:
+                os.unlink(self.path)
+            except Exception:
+                pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no nvidia-smi samples"]}
+        sm = [float(r[1]) for r in rows]
+        mx = float(rows[0][2])
+        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            for k, nm in enumerate(names[1:], start=5):
+                if r[k].lower().startswith("active"):
+                    reasons.add(nm)
+        loaded = sorted(sm)[len(sm) // 2:] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(rows)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ------------------------------------------------------------------------------
+# CPU oracle timing (the reported baseline and the reference arm)
+# ------------------------------------------------------------------------------
+
+def oracle_rate(c, inp_full, budget_s: float, threads: int):
+    """Time the FP64 oracle (forward + adjoint) on growing bounded samples of
+    the workload until about `budget_s` of CPU work; returns samples/s."""
+    import oracle
+    S = max(1, threads)
+    done, spent = 0, 0.0
+    B = inp_full.x.shape[0]
+    while spent < budget_s:
+        rows = [(done + i) % B for i in range(S)]
+        x, gE = inp_full.x[rows], inp_full.gE[rows]
+        t = time.perf_counter()
+        oracle.forward(c, x, inp_full.w, threads=threads)
+        oracle.adjoint(c, gE, x, inp_full.w, threads=threads)
+        spent += time.perf_counter() - t
+        done += S
+        if spent < budget_s / 8:
+            S *= 2
+    return done / spent, done, spent
+
+
+# ------------------------------------------------------------------------------
+# GPU measurement
+# ------------------------------------------------------------------------------
+
+def measure_gpu(name, steps, warmup, device, seed_offset=0, profile=True):
+    import numpy as np
+    import torch
+
+    from paper_2404_06314_gb300 import capi, workloads as W
+
+    cfg = WORKLOADS[name]
+    c = getattr(W, cfg["builder"])()
+    B = cfg["B"]
+    plan = capi.Plan(c, dtype=cfg["dtype"], path="fused")
+    rd = plan.real_dtype()
+    inp = W.make_inputs(c, B, W.WORKLOAD_SEEDS[c.name] + seed_offset,
+                        real_dtype=np.float32 if rd == torch.float32 else np.float64)
+    x = torch.tensor(inp.x, dtype=rd, device=device)
+    w = torch.tensor(inp.w, dtype=rd, device=device)
+    gE = torch.tensor(inp.gE, dtype=rd, device=device)
+    E = torch.empty((B, c.n_obs), dtype=rd, device=device)
+    gx = torch.empty((B, c.n_inputs), dtype=rd, device=device)
+    gw = torch.empty((c.n_weights,), dtype=rd, device=device)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=device)
+
+    def step():
+        plan.forward(x, w, out=E)
+        plan.adjoint(gE, x, w, gx=gx, gw=gw)
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    lib = capi.lib()
+    lib.qtm_set_profiling(plan.handle, 1 if profile else 0)
+    import ctypes
+    ms_buf = (ctypes.c_float * 512)()
+    kind_buf = (ctypes.c_int * 512)()
+    cnt = ctypes.c_int()
+
+    def launch_times(which):
+        lib.qtm_get_launch_times(plan.handle, which, ms_buf, kind_buf, 512, ctypes.byref(cnt))
+        n = min(cnt.value, 512)
+        return [(ms_buf[i], kind_buf[i]) for i in range(n)]
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    step_ms = []
+    pass_fwd_ms = pass_rev_ms = 0.0
+    n_fwd_pass = n_rev_pass = 0
+    launches = 0
+    torch.cuda.synchronize()
+    for k in range(steps):
+        flush.zero_()                                  # evict the L2 between steps
+        ev[k][0].record()
+        step()
+        ev[k][1].record()
+        torch.cuda.synchronize()
+        step_ms.append(ev[k][0].elapsed_time(ev[k][1]))
+        if profile:
+            f = launch_times(0)
+            a = launch_times(1)
+            launches += len(f) + len(a)
+            pass_fwd_ms += sum(t for t, kd in f if kd == 0)
+            n_fwd_pass += sum(1 for _, kd in f if kd == 0)
+            pass_rev_ms += sum(t for t, kd in a if kd == 0)
+            n_rev_pass += sum(1 for _, kd in a if kd == 0)
+    lib.qtm_set_profiling(plan.handle, 0)
+    plan.sync()
+    info = plan.info
+    return dict(c=c, B=B, plan=plan, inp=inp, step_ms=step_ms, info=info,
+                pass_fwd_ms=pass_fwd_ms, pass_rev_ms=pass_rev_ms, n_fwd_pass=n_fwd_pass,
+                n_rev_pass=n_rev_pass, launches=launches)
+
+
+def measure_e2e(name, steps, device, seed_offset=0):
+    """End to end through the public API: pinned host inputs -> device,
+    forward, adjoint, results -> pinned host, every step."""
+    import numpy as np
+    import torch
+
+    from paper_2404_06314_gb300 import capi, workloads as W
+
+    cfg = WORKLOADS[name]
+    c = getattr(W, cfg["builder"])()
+    B = cfg["B"]
+    plan = capi.Plan(c, dtype=cfg["dtype"], path="fused")
+    rd = plan.real_dtype()
+    inp = W.make_inputs(c, B, W.WORKLOAD_SEEDS[c.name] + seed_offset,
+                        real_dtype=np.float32 if rd == torch.float32 else np.float64)
+    hx = torch.tensor(inp.x, dtype=rd).pin_memory()
+    hw = torch.tensor(inp.w, dtype=rd).pin_memory()
+    hg = torch.tensor(inp.gE, dtype=rd).pin_memory()
+    hE = torch.empty((B, c.n_obs), dtype=rd).pin_memory()
+    hgx = torch.empty((B, c.n_inputs), dtype=rd).pin_memory()
+    hgw = torch.empty((c.n_weights,), dtype=rd).pin_memory()
+    x = torch.empty_like(hx, device=device)
+    w = torch.empty_like(hw, device=device)
+    g = torch.empty_like(hg, device=device)
+    E = torch.empty_like(hE, device=device)
+    gx = torch.empty_like(hgx, device=device)
+    gw = torch.empty_like(hgw, device=device)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=device)
+
+    def step():
+        x.copy_(hx, non_blocking=True)
+        w.copy_(hw, non_blocking=True)
+        g.copy_(hg, non_blocking=True)
+        plan.forward(x, w, out=E)
+        plan.adjoint(g, x, w, gx=gx, gw=gw)
+        hE.copy_(E, non_blocking=True)
+        hgx.copy_(gx, non_blocking=True)
+        hgw.copy_(gw, non_blocking=True)
+
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize()
+    tot = 0.0
+    for _ in range(steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        step()
+        e1.record()
+        torch.cuda.synchronize()
+        tot += e0.elapsed_time(e1)
+    es = x.element_size()
+    h2d = (hx.numel() + hw.numel() + hg.numel()) * es
+    d2h = (hE.numel() + hgx.numel() + hgw.numel()) * es
+    return B * steps / (tot / 1e3), h2d, d2h
+
+
+def gpu_main(args):
+    import torch
+    import torch.distributed as dist
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    peaks, peak_src = load_peaks()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.mark("t0")
+    r12 = measure_gpu(args.workload, args.steps, args.warmup, device, seed_offset=rank)
+    torch.cuda.synchronize()
+    sampler.mark("t1")
+    total_ms = sum(r12["step_ms"])
+    if ws > 1:
+        t = torch.tensor([total_ms], device=device, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+    sampler.stop()
+    clocks = sampler.summary()
+
+    n20 = None
+    if args.workload == "qnn12" and not args.skip_n20:
+        r20 = measure_gpu("qnn20", max(3, args.steps // 4), args.warmup, device, seed_offset=rank)
+        tot20 = sum(r20["step_ms"])
+        if ws > 1:
+            t = torch.tensor([tot20], device=device, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            tot20 = float(t.item())
+        n20 = (r20, tot20)
+
+    e2e = measure_e2e(args.workload, max(3, args.steps // 4), device, seed_offset=rank)
+    if ws > 1:
+        t = torch.tensor([e2e[0]], device=device, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MIN)
+        e2e = (float(t.item()), e2e[1], e2e[2])
+        dist.destroy_process_group()
+    if rank != 0:
+        return
+
+    K = args.steps
+    B = r12["B"]
+    value = B * K * ws / (total_ms / 1e3)
+    info = r12["info"]
+    sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    # dominant kernel of the smem-resident path: the reverse pass (ALU bound)
+    rev_ms_avg = r12["pass_rev_ms"] / max(1, r12["n_rev_pass"])
+    adj_flops_launch = info["adj_flops"] * B / max(1, info["adj_passes"])
+    alu_peak = fp32_alu_peak_tflops(peaks.get("sm_max_mhz", 2070.0))
+    achieved = adj_flops_launch / (rev_ms_avg / 1e3) / 1e12 if rev_ms_avg > 0 else None
+    roofline = {"bound": "alu", "kernel": "k_pass<float,reverse>", "achieved": achieved,
+                "peak": alu_peak, "unit": "TFLOP/s",
+                "frac": (achieved / alu_peak) if achieved else None,
+                "traffic": None,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x %g MHz (MEASURED_PEAKS sm_max_mhz)"
+                               % peaks.get("sm_max_mhz", 2070.0)}
+    line = {
+        "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": ws, "steps": K,
+        "warmup": args.warmup, "ms_per_step": total_ms / K, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "c64 (fp32 complex; fp64 reductions)",
+        "data": "synthetic (seeded x ~ U[-pi,pi], w ~ N(0,1), cotangents ~ N(0,1))",
+        "config": {"workload": "qnn12_l6: 12 qubits, 6 re-uploading layers RX(x) RY(w) RZ(w) + CZ ring, "
+                               "obs sum Z_i Z_{i+1}, fwd + adjoint (grad_x, grad_w)",
+                   "global_batch": B * ws, "per_gpu_batch": B, "qubits": 12, "layers": 6,
+                   "path": "fused (whole state in shared memory, one CTA per sample)",
+                   "l2": "flushed between steps (256 MiB write)",
+                   "parallelism": f"batch shards x{ws}"},
+        "roofline": roofline,
+        "gpu_launches": r12["launches"],
+        "clocks": clocks,
+        "e2e": {"value": e2e[0], "unit": "samples/s", "h2d_bytes_per_step": e2e[1],
+                "d2h_bytes_per_step": e2e[2]},
+        "plan": {k: info[k] for k in ("fwd_passes", "adj_passes", "fwd_flops", "adj_flops")},
+    }
+    if n20 is not None:
+        r20, tot20 = n20
+        i20 = r20["info"]
+        K20 = len(r20["step_ms"])
+        v20 = r20["B"] * K20 * ws / (tot20 / 1e3)
+        rev_bytes = i20["adj_state_bytes"] * r20["B"]
+        fwd_bytes = i20["fwd_state_bytes"] * r20["B"]
+        rev_gbs = rev_bytes * K20 / (r20["pass_rev_ms"] / 1e3) / 1e9 if r20["pass_rev_ms"] else None
+        fwd_gbs = fwd_bytes * K20 / (r20["pass_fwd_ms"] / 1e3) / 1e9 if r20["pass_fwd_ms"] else None
+        hbm = peaks.get("hbm_gbs", 6800.0)
+        line["n20"] = {
+            "value": v20, "unit": "samples/s", "ms_per_step": tot20 / K20, "steps": K20,
+            "config": {"workload": "qnn20_l4: 20 qubits, RX(x) + 4 layers RY/RZ + CNOT chain, obs Z_0, Z^20",
+                       "per_gpu_batch": r20["B"], "path": "fused HBM sweeps (TMA tiles of 2^12)"},
+            "roofline": {"bound": "hbm", "kernel": "k_pass<float,reverse>", "achieved": rev_gbs,
+                         "peak": hbm, "unit": "GB/s", "frac": rev_gbs / hbm if rev_gbs else None,
+                         "traffic": None, "peak_source": f"{peak_src} hbm_gbs"},
+            "forward_pass_gbs": fwd_gbs,
+            "state_bytes_per_sample": {"fwd": i20["fwd_state_bytes"], "adj": i20["adj_state_bytes"]},
+            "passes": {"fwd": i20["fwd_passes"], "adj": i20["adj_passes"]},
+            "gpu_launches": r20["launches"],
+        }
+    if not args.no_cpu_baseline:
+        from paper_2404_06314_gb300 import workloads as W
+        threads = os.cpu_count() or 1
+        c = r12["c"]
+        rate, done, spent = oracle_rate(c, r12["inp"], args.cpu_budget, threads)
+        line["cpu_baseline"] = {"value": rate, "unit": "samples/s", "cores": threads, "kind": "oracle",
+                                "sample": f"{done} samples of the {c.name} batch, FP64 oracle forward + "
+                                          f"adjoint, {spent:.1f} s on {threads} threads"}
+        del W
+    print(json.dumps(line), flush=True)
+
+
+def reference_main(args):
+    """The oracle as the reference arm: same workload, metric and unit."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+    from paper_2404_06314_gb300 import workloads as W
+
+    cfg = WORKLOADS[args.workload]
+    c = getattr(W, cfg["builder"])()
+    inp = W.make_inputs(c, cfg["B"], W.WORKLOAD_SEEDS[c.name], real_dtype=np.float32)
+    threads = os.cpu_count() or 1
+    # bounded sample per step: about args.cpu_budget / (steps + warmup) seconds
+    per_step = max(0.5, args.cpu_budget / max(1, args.steps + args.warmup))
+    probe_rate, _, _ = oracle_rate(c, inp, min(2.0, per_step), threads)
+    S = max(threads, int(probe_rate * per_step))
+    rows = [i % cfg["B"] for i in range(S)]
+    x, gE = inp.x[rows], inp.gE[rows]
+    for _ in range(args.warmup):
+        oracle.forward(c, x, inp.w, threads=threads)
+        oracle.adjoint(c, gE, x, inp.w, threads=threads)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.forward(c, x, inp.w, threads=threads)
+        oracle.adjoint(c, gE, x, inp.w, threads=threads)
+    dt = time.perf_counter() - t
+    value = S * args.steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "samples/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)",
+            "config": {"workload": c.name, "per_step_sample": S},
+            "cpu_baseline": {"value": value, "unit": "samples/s", "cores": threads, "kind": "oracle",
+                             "sample": f"{S} samples of the {c.name} batch per step"},
+            "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="qnn12")
+    ap.add_argument("--skip-n20", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle CPU work")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        reference_main(args)
+    else:
+        gpu_main(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,198 @@
+/*
+ * qtm.h -- C ABI of the GB300 (sm_103a) batched statevector QNN library.
+ *
+ * What it computes (arXiv 2404.06314, Sec. II):
+ *   For every sample b of a batch, the state |psi_b> = U(Theta, s_b)|0> of an
+ *   n-qubit parameterised circuit is evolved ONCE and all M observables are
+ *   read from it (Eq. (qnn), Sec. II-A "evolve once"):
+ *       E[b][m] = <psi_b| O_m |psi_b>,   O_m = sum_{t: obs_t = m} c_t Z^{mask_t}.
+ *   The vector-Jacobian product with a cotangent gE[b][m] is computed by the
+ *   adjoint ("reverse") method (Sec. II-A, Jones & Gacon Alg. 1, extended to M
+ *   observables by weighting them into a single costate), then mapped through
+ *   the angle bindings to gradients w.r.t. weights and inputs (Eq. (qnn_grad),
+ *   Eq. (qnn_batched)).
+ *
+ * Conventions:
+ *   - qubit q is bit q of the amplitude index (little endian, Qiskit order);
+ *   - R_P(t) = exp(-i t P / 2) for P in {X, Y, Z};
+ *   - angle of a rotation for sample b:
+ *       t = coef * (w_idx >= 0 ? w[w_idx] : 1) * (x_idx >= 0 ? x[b][x_idx] : 1),
+ *     which covers variational weights, angle encoding and trainable input
+ *     scaling (Sec. II-C; Eq. (concrete_ansatz));
+ *   - weights keep their construction order (Sec. II-C), never alphabetical.
+ *
+ * Memory and ownership:
+ *   - x, w, expvals, grad_expvals, grad_x, grad_w are DEVICE pointers owned by
+ *     the caller, row-major and contiguous, of the plan's real type:
+ *     float for QTM_C64 plans, double for QTM_C128 plans;
+ *   - gates/terms passed to qtm_build are HOST arrays, copied by the plan;
+ *   - the plan owns its device tables and a state workspace (phi and, for
+ *     n > 12, lambda: B x 2^n complex each), allocated lazily on the first
+ *     call on a device and grown when a larger batch arrives;
+ *   - every call enqueues work on `stream` (a cudaStream_t, NULL = legacy
+ *     default stream) and returns without synchronising.
+ *
+ * Errors: every entry point returns a qtm_status.  Arguments are validated on
+ * the host before any launch (QTM_EINVAL).  CUDA errors map to QTM_ECUDA.
+ * Kernels never trap: a device-side wait that gives up records a status word
+ * that qtm_sync() reports as QTM_ETIMEOUT.  Nothing calls abort() or exit().
+ */
+#ifndef QTM_H
+#define QTM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    QTM_OK = 0,
+    QTM_EINVAL = 1,        /* bad argument (detected on the host, nothing launched) */
+    QTM_ENOMEM = 2,        /* device or host allocation failed */
+    QTM_ECUDA = 3,         /* a CUDA runtime/driver call failed */
+    QTM_EUNSUPPORTED = 4,  /* valid request outside what this build supports */
+    QTM_ETIMEOUT = 5,      /* a bounded device-side wait gave up (see qtm_sync) */
+    QTM_ESTATE = 6         /* call order violated (e.g. adjoint without forward) */
+} qtm_status;
+
+typedef enum { QTM_RX = 0, QTM_RY = 1, QTM_RZ = 2, QTM_CZ = 3, QTM_CNOT = 4 } qtm_gate_kind;
+
+typedef enum { QTM_C64 = 0, QTM_C128 = 1 } qtm_dtype;
+
+/* Execution path.  FUSED: whole-circuit shared-memory kernel for n <= 12 and
+ * fused HBM sweeps above; NAIVE: one kernel launch per gate over the batch
+ * (the plain baseline the fused path is measured against). */
+typedef enum { QTM_PATH_AUTO = 0, QTM_PATH_FUSED = 1, QTM_PATH_NAIVE = 2 } qtm_path;
+
+/* One gate (32 bytes).
+ *   rotations (QTM_RX/RY/RZ): q0 = target, q1 = -1;
+ *   QTM_CZ:   q0, q1 = the two qubits (symmetric);
+ *   QTM_CNOT: q0 = control, q1 = target.
+ * w_idx / x_idx = -1 means "factor 1" (Sec. II-C bindings, see above). */
+typedef struct {
+    int32_t kind;
+    int32_t q0;
+    int32_t q1;
+    int32_t w_idx;
+    int32_t x_idx;
+    int32_t reserved;   /* must be 0 */
+    double coef;
+} qtm_gate;
+
+/* One Z-string term of an observable (24 bytes): O_obs += coef * Z^{zmask}. */
+typedef struct {
+    uint64_t zmask;
+    double coef;
+    int32_t obs;
+    int32_t reserved;   /* must be 0 */
+} qtm_zterm;
+
+typedef struct qtm_plan qtm_plan;
+
+/* Static description of a plan's schedule (host-side; no GPU needed). */
+typedef struct {
+    int32_t n_qubits;
+    int32_t dtype;
+    int32_t path;            /* resolved path (FUSED or NAIVE) */
+    int32_t tile_qubits;     /* K: qubits per shared-memory tile */
+    int32_t fwd_passes;      /* kernel passes over the state in qtm_forward */
+    int32_t adj_passes;      /* passes in qtm_adjoint (without recompute) */
+    int32_t fwd_launches;    /* kernel launches per qtm_forward */
+    int32_t adj_launches;    /* kernel launches per qtm_adjoint (per-sample grad_w) */
+    int32_t n_runs;          /* fused single-qubit rotation runs */
+    int32_t n_prefix_runs;   /* runs folded into the analytic product-state init */
+    int32_t n_prefix_ents;   /* CZ/CNOT folded into the init */
+    int32_t reserved0;
+    double fwd_state_bytes;  /* HBM bytes moved over the state per sample, forward */
+    double adj_state_bytes;  /* same, adjoint */
+    double fwd_flops;        /* arithmetic per sample, forward (counting rule in DESIGN) */
+    double adj_flops;        /* arithmetic per sample, adjoint */
+} qtm_plan_info;
+
+/* Flags of qtm_adjoint. */
+#define QTM_ADJ_GW_PER_SAMPLE 1  /* grad_w is [B][P] per sample instead of the batch sum [P] */
+#define QTM_ADJ_RECOMPUTE 2      /* re-run the forward instead of using the stored state */
+
+/*
+ * qtm_build: plan a circuit (Sec. II-A problem statement: circuit, observables).
+ *   n_qubits  1 .. 30;  gates/terms: host arrays (copied);  n_obs >= 1;
+ *   n_weights, n_inputs >= 0;  dtype: qtm_dtype;  path: qtm_path.
+ * Validates every index (qubits < n, CZ/CNOT with distinct qubits, w_idx <
+ * n_weights, x_idx < n_inputs, zmask < 2^n, obs < n_obs).  Host-only: does no
+ * CUDA call, so it works without a GPU.  On success *out owns the plan.
+ */
+qtm_status qtm_build(int n_qubits, const qtm_gate *gates, int n_gates,
+                     const qtm_zterm *terms, int n_terms, int n_obs,
+                     int n_weights, int n_inputs, int dtype, int path, qtm_plan **out);
+
+/*
+ * qtm_forward: expectation values, Eq. (qnn) for every sample of the batch
+ * (Eq. (qnn_batched)).  x: [B][n_inputs], w: [n_weights], expvals: [B][n_obs]
+ * (device, plan real type).  B >= 1.  Keeps the final states in the plan's
+ * workspace for a following qtm_adjoint on the same stream.
+ */
+qtm_status qtm_forward(qtm_plan *plan, int B, const void *x, const void *w,
+                       void *expvals, void *stream);
+
+/*
+ * qtm_adjoint: vector-Jacobian product by the adjoint method (Sec. II-A).
+ *   grad_expvals [B][n_obs] is the cotangent of expvals;  outputs
+ *   grad_x [B][n_inputs] (or NULL) and grad_w ([n_weights], or [B][n_weights]
+ *   with QTM_ADJ_GW_PER_SAMPLE; or NULL).  Outputs are overwritten.
+ * Uses the states stored by the last qtm_forward on this plan, which must have
+ * had the same B, x and w, on the same stream; pass QTM_ADJ_RECOMPUTE to
+ * evolve them again (required if anything else ran on the plan since).  Returns
+ * QTM_ESTATE when no stored forward matches (B, x, w pointers).  The stored
+ * states are consumed.
+ */
+qtm_status qtm_adjoint(qtm_plan *plan, int B, const void *grad_expvals, const void *x,
+                       const void *w, void *grad_x, void *grad_w, int flags, void *stream);
+
+/*
+ * qtm_jacobian: full Jacobian J[b][m][g] = d<O_m>/d theta_g (device, plan real
+ * type, [B][n_obs][n_gates], zero for CZ/CNOT): the (B, M, |Theta|) output of
+ * Sec. II-B, one costate per observable.  Runs the forward itself.
+ */
+qtm_status qtm_jacobian(qtm_plan *plan, int B, const void *x, const void *w, void *jac,
+                        void *stream);
+
+/* Per-launch timing (profiling aid).  enable != 0: every later qtm_forward /
+ * qtm_adjoint records a pair of CUDA events around each of its kernel
+ * launches, on the call's stream.  enable == 0 stops recording. */
+qtm_status qtm_set_profiling(qtm_plan *plan, int enable);
+
+/* After the stream has been synchronised: the device durations (ms) of the
+ * kernel launches of the last profiled qtm_forward (which = 0) or qtm_adjoint
+ * (which = 1), in launch order.  kinds[i] (optional) receives 0 for a pass
+ * kernel over the state and 1 for a finalize/reduce kernel.  *count receives
+ * the number of launches (at most cap are written). */
+qtm_status qtm_get_launch_times(qtm_plan *plan, int which, float *ms, int *kinds, int cap,
+                                int *count);
+
+/* Synchronise `stream`, then report (and clear) any status a kernel of this
+ * plan recorded on the device: QTM_ETIMEOUT if a bounded wait gave up. */
+qtm_status qtm_sync(qtm_plan *plan, void *stream);
+
+/* Schedule summary of a plan (host-side). */
+qtm_status qtm_get_plan_info(const qtm_plan *plan, qtm_plan_info *info);
+
+/* Release the plan and its device memory (synchronises the device first). */
+qtm_status qtm_destroy(qtm_plan *plan);
+
+/* Message of the last error recorded on this plan ("" if none).  Owned by
+ * the plan; valid until the next call on it. */
+const char *qtm_last_error(const qtm_plan *plan);
+
+/* Static string for a status code. */
+const char *qtm_status_str(int status);
+
+/* Library version, e.g. "qtm 0.1 sm_103a". */
+const char *qtm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QTM_H */

@@ -1,0 +1,35 @@
+/*
+ * qtm_debug.h -- host-side inspection of a plan's schedule.
+ *
+ * These calls never touch the GPU and are never used by qtm_forward /
+ * qtm_adjoint.  They exist so the planner (the schedule of passes, phases and
+ * ops that the CUDA kernels execute) can be validated on a machine without a
+ * GPU: qtm_debug_emulate interprets exactly that schedule in FP64 on the host.
+ */
+#ifndef QTM_DEBUG_H
+#define QTM_DEBUG_H
+
+#include "qtm.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Human-readable dump of the plan's passes (tile qubit sets, sources/sinks,
+ * register-group phases and ops).  The string is owned by the plan and stays
+ * valid until the next call on it or qtm_destroy. */
+const char *qtm_debug_describe(const qtm_plan *plan);
+
+/* Interpret the fused schedule in FP64 on the host (n <= 20).  HOST pointers:
+ * x [B][n_inputs], w [n_weights], gE [B][n_obs] (NULL: forward only);
+ * outputs E [B][n_obs], gx [B][n_inputs], gw [B][n_weights] (per sample), each
+ * may be NULL.  Returns QTM_EUNSUPPORTED for naive-path plans or n > 20 and
+ * QTM_EINVAL if the schedule breaks a locality rule (see qtm_last_error). */
+qtm_status qtm_debug_emulate(const qtm_plan *plan, int B, const double *x, const double *w,
+                             const double *gE, double *E, double *gx, double *gw);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QTM_DEBUG_H */

@@ -1,0 +1,274 @@
+"""ctypes binding of the C ABI in include/qtm.h (argument marshalling only).
+
+The functions keep the C names (qtm_build, qtm_forward, qtm_adjoint, ...).
+Every step of the computation runs in libqtm.so's CUDA kernels; there is no
+Python or CPU fallback: without the library or a GPU the calls raise.
+
+`Plan` wraps a plan handle for torch tensors: it checks dtype/device/shape,
+passes data pointers and the current CUDA stream, and raises QtmError on any
+non-OK status.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+from . import build as _build
+
+QTM_OK, QTM_EINVAL, QTM_ENOMEM, QTM_ECUDA, QTM_EUNSUPPORTED, QTM_ETIMEOUT, QTM_ESTATE = range(7)
+QTM_C64, QTM_C128 = 0, 1
+QTM_PATH_AUTO, QTM_PATH_FUSED, QTM_PATH_NAIVE = 0, 1, 2
+QTM_ADJ_GW_PER_SAMPLE, QTM_ADJ_RECOMPUTE = 1, 2
+
+
+class qtm_gate(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("q0", ctypes.c_int32), ("q1", ctypes.c_int32),
+                ("w_idx", ctypes.c_int32), ("x_idx", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("coef", ctypes.c_double)]
+
+
+class qtm_zterm(ctypes.Structure):
+    _fields_ = [("zmask", ctypes.c_uint64), ("coef", ctypes.c_double), ("obs", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class qtm_plan_info(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int32) for k in (
+        "n_qubits", "dtype", "path", "tile_qubits", "fwd_passes", "adj_passes", "fwd_launches",
+        "adj_launches", "n_runs", "n_prefix_runs", "n_prefix_ents", "reserved0")] + \
+        [(k, ctypes.c_double) for k in ("fwd_state_bytes", "adj_state_bytes", "fwd_flops", "adj_flops")]
+
+
+assert ctypes.sizeof(qtm_gate) == 32 and ctypes.sizeof(qtm_zterm) == 24
+
+
+class QtmError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str = ""):
+        self.status = status
+        super().__init__(f"{where}: {_status_str(status)} ({status}){': ' + detail if detail else ''}")
+
+
+_LIB = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib(build_if_missing: bool = True):
+    """Load libqtm.so (building it first if it is missing or stale)."""
+    global _LIB
+    if _LIB is None:
+        path = _build.build() if build_if_missing else _build.LIB
+        if not os.path.exists(path):
+            raise ImportError(f"libqtm.so not found at {path}; run __graft_entry__.build()")
+        L = ctypes.CDLL(path)
+        vp, i, P = ctypes.c_void_p, ctypes.c_int, ctypes.POINTER
+        L.qtm_build.argtypes = [i, vp, i, vp, i, i, i, i, i, i, P(vp)]
+        L.qtm_forward.argtypes = [vp, i, vp, vp, vp, vp]
+        L.qtm_adjoint.argtypes = [vp, i, vp, vp, vp, vp, vp, i, vp]
+        L.qtm_jacobian.argtypes = [vp, i, vp, vp, vp, vp]
+        L.qtm_sync.argtypes = [vp, vp]
+        L.qtm_get_plan_info.argtypes = [vp, P(qtm_plan_info)]
+        L.qtm_destroy.argtypes = [vp]
+        for f in ("qtm_build", "qtm_forward", "qtm_adjoint", "qtm_jacobian", "qtm_sync",
+                  "qtm_get_plan_info", "qtm_destroy", "qtm_debug_emulate"):
+            getattr(L, f).restype = ctypes.c_int
+        L.qtm_status_str.argtypes = [i]
+        L.qtm_status_str.restype = ctypes.c_char_p
+        L.qtm_version.restype = ctypes.c_char_p
+        L.qtm_last_error.argtypes = [vp]
+        L.qtm_last_error.restype = ctypes.c_char_p
+        L.qtm_debug_describe.argtypes = [vp]
+        L.qtm_debug_describe.restype = ctypes.c_char_p
+        L.qtm_debug_emulate.argtypes = [vp, i, vp, vp, vp, vp, vp, vp]
+        _LIB = L
+    return _LIB
+
+
+def _status_str(st: int) -> str:
+    try:
+        return lib().qtm_status_str(st).decode()
+    except Exception:
+        return "status"
+
+
+# ---- C-named wrappers (raw pointers) ---------------------------------------
+
+def qtm_build(n_qubits, gates, terms, n_obs, n_weights, n_inputs, dtype=QTM_C64,
+              path=QTM_PATH_AUTO):
+    """gates: sequence of (kind, q0, q1, w_idx, x_idx, coef); terms: (zmask, coef, obs).
+    Returns a plan handle (int).  Host-only: no GPU needed."""
+    G = (qtm_gate * max(len(gates), 1))()
+    for i, (k, q0, q1, wi, xi, c) in enumerate(gates):
+        G[i] = qtm_gate(int(k), int(q0), int(q1), int(wi), int(xi), 0, float(c))
+    T = (qtm_zterm * max(len(terms), 1))()
+    for i, (m, c, o) in enumerate(terms):
+        T[i] = qtm_zterm(int(m), float(c), int(o), 0)
+    h = ctypes.c_void_p()
+    st = lib().qtm_build(int(n_qubits), G, len(gates), T, len(terms), int(n_obs), int(n_weights),
+                         int(n_inputs), int(dtype), int(path), ctypes.byref(h))
+    if st != QTM_OK:
+        raise QtmError(st, "qtm_build")
+    return h.value
+
+
+def qtm_forward(plan, B, x, w, expvals, stream=0):
+    return lib().qtm_forward(plan, int(B), x, w, expvals, stream)
+
+
+def qtm_adjoint(plan, B, grad_expvals, x, w, grad_x, grad_w, flags=0, stream=0):
+    return lib().qtm_adjoint(plan, int(B), grad_expvals, x, w, grad_x, grad_w, int(flags), stream)
+
+
+def qtm_jacobian(plan, B, x, w, jac, stream=0):
+    return lib().qtm_jacobian(plan, int(B), x, w, jac, stream)
+
+
+def qtm_sync(plan, stream=0):
+    return lib().qtm_sync(plan, stream)
+
+
+def qtm_get_plan_info(plan) -> dict:
+    info = qtm_plan_info()
+    st = lib().qtm_get_plan_info(plan, ctypes.byref(info))
+    if st != QTM_OK:
+        raise QtmError(st, "qtm_get_plan_info")
+    return {k: getattr(info, k) for k, _ in qtm_plan_info._fields_ if k != "reserved0"}
+
+
+def qtm_destroy(plan):
+    return lib().qtm_destroy(plan)
+
+
+def qtm_last_error(plan) -> str:
+    return lib().qtm_last_error(plan).decode()
+
+
+def qtm_status_str(st: int) -> str:
+    return lib().qtm_status_str(int(st)).decode()
+
+
+def qtm_version() -> str:
+    return lib().qtm_version().decode()
+
+
+def qtm_debug_describe(plan) -> str:
+    return lib().qtm_debug_describe(plan).decode()
+
+
+def qtm_debug_emulate(plan, x, w, gE=None, circuit=None):
+    """FP64 host interpretation of the plan's schedule (planner validation)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    B = x.shape[0]
+    info = qtm_get_plan_info(plan)
+    M = circuit.n_obs
+    E = np.zeros((B, M))
+    gx = np.zeros((B, circuit.n_inputs))
+    gw = np.zeros((B, circuit.n_weights))
+    gEa = None if gE is None else np.ascontiguousarray(gE, dtype=np.float64)
+    p = lambda a: a.ctypes.data if a is not None and a.size else None
+    st = lib().qtm_debug_emulate(plan, B, p(x), p(w), p(gEa), p(E), p(gx), p(gw))
+    if st != QTM_OK:
+        raise QtmError(st, "qtm_debug_emulate", qtm_last_error(plan))
+    del info
+    return (E, gx, gw) if gE is not None else E
+
+
+# ---- torch-facing plan object ------------------------------------------------
+
+class Plan:
+    """A built circuit plan.  Tensors must live on the current CUDA device, be
+    contiguous and of the plan's real dtype (float32 for complex64 plans,
+    float64 for complex128)."""
+
+    def __init__(self, circuit, dtype: str = "c64", path: str = "auto"):
+        self.circuit = circuit
+        self.dtype = QTM_C128 if dtype in ("c128", "complex128") else QTM_C64
+        self.path = {"auto": QTM_PATH_AUTO, "fused": QTM_PATH_FUSED, "naive": QTM_PATH_NAIVE}[path]
+        self.handle = qtm_build(circuit.n, circuit.gates, circuit.terms, circuit.n_obs,
+                                circuit.n_weights, circuit.n_inputs, self.dtype, self.path)
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            try:
+                qtm_destroy(h)
+            except Exception:
+                pass
+            self.handle = None
+
+    @property
+    def info(self) -> dict:
+        return qtm_get_plan_info(self.handle)
+
+    def describe(self) -> str:
+        return qtm_debug_describe(self.handle)
+
+    def real_dtype(self):
+        import torch
+        return torch.float64 if self.dtype == QTM_C128 else torch.float32
+
+    def _check(self, t, shape, name):
+        import torch
+        if t is None:
+            return None
+        if not isinstance(t, torch.Tensor) or not t.is_cuda:
+            raise TypeError(f"{name} must be a CUDA tensor")
+        if t.dtype != self.real_dtype():
+            raise TypeError(f"{name} must be {self.real_dtype()}, got {t.dtype}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+        if tuple(t.shape) != tuple(shape):
+            raise ValueError(f"{name} shape {tuple(t.shape)} != {tuple(shape)}")
+        return t.data_ptr()
+
+    @staticmethod
+    def _stream(stream):
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        return ctypes.c_void_p(stream.cuda_stream)
+
+    def _raise(self, st, where):
+        if st != QTM_OK:
+            raise QtmError(st, where, qtm_last_error(self.handle))
+
+    def forward(self, x, w, out=None, stream=None):
+        import torch
+        c = self.circuit
+        B = x.shape[0]
+        if out is None:
+            out = torch.empty((B, c.n_obs), dtype=self.real_dtype(), device=x.device)
+        st = qtm_forward(self.handle, B, self._check(x, (B, c.n_inputs), "x"),
+                         self._check(w, (c.n_weights,), "w"), self._check(out, (B, c.n_obs), "expvals"),
+                         self._stream(stream))
+        self._raise(st, "qtm_forward")
+        return out
+
+    def adjoint(self, gE, x, w, gx=None, gw=None, per_sample_w=False, recompute=False,
+                want_gx=True, want_gw=True, stream=None):
+        import torch
+        c = self.circuit
+        B = x.shape[0]
+        dev = x.device
+        if want_gx and gx is None:
+            gx = torch.empty((B, c.n_inputs), dtype=self.real_dtype(), device=dev)
+        gw_shape = (B, c.n_weights) if per_sample_w else (c.n_weights,)
+        if want_gw and gw is None:
+            gw = torch.empty(gw_shape, dtype=self.real_dtype(), device=dev)
+        flags = (QTM_ADJ_GW_PER_SAMPLE if per_sample_w else 0) | (QTM_ADJ_RECOMPUTE if recompute else 0)
+        st = qtm_adjoint(self.handle, B, self._check(gE, (B, c.n_obs), "grad_expvals"),
+                         self._check(x, (B, c.n_inputs), "x"), self._check(w, (c.n_weights,), "w"),
+                         self._check(gx, (B, c.n_inputs), "grad_x") if want_gx else None,
+                         self._check(gw, gw_shape, "grad_w") if want_gw else None,
+                         flags, self._stream(stream))
+        self._raise(st, "qtm_adjoint")
+        return gx, gw
+
+    def sync(self, stream=None):
+        self._raise(qtm_sync(self.handle, self._stream(stream)), "qtm_sync")

@@ -1,0 +1,649 @@
+// C ABI entry points (include/qtm.h, include/qtm_debug.h).
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_runtime.h>
+
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/qtm.h"
+#include "../../include/qtm_debug.h"
+#include "device.h"
+#include "plan.h"
+
+namespace qtm {
+qtm_status emulate_plan(const Plan &P, int B, const double *x, const double *w, const double *gE,
+                        double *E, double *gx, double *gw, std::string &err);
+}
+
+using namespace qtm;
+
+namespace {
+
+constexpr size_t kMaxDynSmem = 232448;   // 227 KiB per block on sm_100 / sm_103
+
+struct TmGeom {
+    int rank = 0, low_dims = 0, high_dims = 0;
+};
+
+}  // namespace
+
+struct qtm_plan {
+    Plan P;
+    std::string err;
+    int device = -1;
+    // device tables
+    DevOp *d_ops = nullptr;
+    DevPhase *d_phases = nullptr;
+    int32_t *d_slot_runs = nullptr;
+    Run *d_runs = nullptr;
+    Rot *d_rots = nullptr;
+    int32_t *d_prefix_run_of_q = nullptr;
+    Ent *d_prefix_ents = nullptr;
+    Term *d_terms = nullptr;
+    int32_t *d_w_ptr = nullptr, *d_w_rots = nullptr, *d_x_ptr = nullptr, *d_x_rots = nullptr;
+    unsigned *d_status = nullptr;
+    // workspace
+    int cap_B = 0;
+    void *d_phi = nullptr, *d_lam = nullptr, *d_Escratch = nullptr;
+    double *d_Epart = nullptr, *d_Gpart = nullptr, *d_abar = nullptr, *d_gw_ws = nullptr;
+    std::vector<CUtensorMap> tm_fwd, tm_rev_phi, tm_rev_lam;
+    std::vector<TmGeom> g_fwd, g_rev;
+    std::vector<size_t> smem_fwd, smem_rev;
+    bool needs_lam = false;
+    // stored forward
+    bool fwd_valid = false;
+    int fwd_B = 0;
+    const void *fwd_x = nullptr, *fwd_w = nullptr;
+    void *fwd_stream = nullptr;
+    std::string describe_cache;
+    // profiling: events around each launch of the last forward / adjoint
+    bool profiling = false;
+    struct Rec { cudaEvent_t a, b; int kind; };
+    std::vector<Rec> recs[2];
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_used = 0;
+    int cur_which = 0;
+    cudaStream_t cur_stream = nullptr;
+};
+
+namespace {
+
+qtm_status fail(qtm_plan *p, qtm_status st, const std::string &msg)
+{
+    if (p) p->err = msg;
+    return st;
+}
+
+qtm_status cuda_fail(qtm_plan *p, cudaError_t e, const char *where)
+{
+    return fail(p, QTM_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+template <typename T>
+cudaError_t upload(T **dst, const std::vector<T> &v)
+{
+    *dst = nullptr;
+    size_t bytes = sizeof(T) * (v.empty() ? 1 : v.size());
+    cudaError_t e = cudaMalloc(dst, bytes);
+    if (e != cudaSuccess) return e;
+    if (!v.empty()) e = cudaMemcpy(*dst, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice);
+    return e;
+}
+
+void free_tables(qtm_plan *p)
+{
+    void *ptrs[] = {p->d_ops, p->d_phases, p->d_slot_runs, p->d_runs, p->d_rots,
+                    p->d_prefix_run_of_q, p->d_prefix_ents, p->d_terms, p->d_w_ptr,
+                    p->d_w_rots, p->d_x_ptr, p->d_x_rots, p->d_status};
+    for (void *q : ptrs)
+        if (q) cudaFree(q);
+    p->d_ops = nullptr; p->d_phases = nullptr; p->d_slot_runs = nullptr; p->d_runs = nullptr;
+    p->d_rots = nullptr; p->d_prefix_run_of_q = nullptr; p->d_prefix_ents = nullptr;
+    p->d_terms = nullptr; p->d_w_ptr = p->d_w_rots = p->d_x_ptr = p->d_x_rots = nullptr;
+    p->d_status = nullptr;
+}
+
+void free_workspace(qtm_plan *p)
+{
+    void *ptrs[] = {p->d_phi, p->d_lam, p->d_Escratch, p->d_Epart, p->d_Gpart, p->d_abar, p->d_gw_ws};
+    for (void *q : ptrs)
+        if (q) cudaFree(q);
+    p->d_phi = p->d_lam = p->d_Escratch = nullptr;
+    p->d_Epart = p->d_Gpart = p->d_abar = p->d_gw_ws = nullptr;
+    p->cap_B = 0;
+    p->fwd_valid = false;
+}
+
+bool fault_alloc_injected()
+{
+    const char *v = std::getenv("QTM_FAULT_ALLOC");
+    return v && v[0] == '1';
+}
+
+cudaError_t dmalloc(void **p, size_t bytes)
+{
+    if (fault_alloc_injected()) { *p = nullptr; return cudaErrorMemoryAllocation; }
+    return cudaMalloc(p, bytes ? bytes : 16);
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    });
+    return fn;
+}
+
+// Tensor map over the batched state [B][2^sq] for a pass's tile geometry.
+// Dimensions (innermost first): 16 eight-byte words (128 bytes: 16 complex64
+// or 8 complex128 = the low tile bits), the rest of the low block in chunks of
+// <= 8 bits, the gap [l, h) (box 1), the high block [h, h+m), and everything
+// above h+m together with the sample index (box 1).  128-byte swizzle.
+bool make_tmap(CUtensorMap *tm, void *base, const PassDesc &pd, int sq, int B, int dtype, TmGeom &g)
+{
+    const int es = elem_bytes(dtype);
+    const int d0bits = dtype == QTM_C128 ? 3 : 4;
+    cuuint64_t dim[8], stride[8];
+    cuuint32_t box[8], estr[8];
+    int r = 0;
+    dim[r] = 16; box[r] = 16; ++r;
+    g.low_dims = 1;
+    for (int bit = d0bits; bit < pd.l; bit += 8) {
+        int cnt = std::min(8, pd.l - bit);
+        dim[r] = 1ull << cnt; box[r] = 1u << cnt; stride[r - 1] = (cuuint64_t)es << bit; ++r;
+        g.low_dims++;
+    }
+    if (pd.h > pd.l) {
+        dim[r] = 1ull << (pd.h - pd.l); box[r] = 1; stride[r - 1] = (cuuint64_t)es << pd.l; ++r;
+    }
+    g.high_dims = 0;
+    for (int bit = pd.h; bit < pd.h + pd.m; bit += 8) {
+        int cnt = std::min(8, pd.h + pd.m - bit);
+        dim[r] = 1ull << cnt; box[r] = 1u << cnt; stride[r - 1] = (cuuint64_t)es << bit; ++r;
+        g.high_dims++;
+    }
+    const int rb = pd.h + pd.m;
+    dim[r] = (1ull << (sq - rb)) * (cuuint64_t)B; box[r] = 1; stride[r - 1] = (cuuint64_t)es << rb; ++r;
+    if (r > 5) return false;
+    g.rank = r;
+    for (int i = 0; i < r; ++i) estr[i] = 1;
+    auto fn = encode_fn();
+    if (!fn) return false;
+    CUresult res = fn(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, (cuuint32_t)r, base, dim, stride, box, estr,
+                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return res == CUDA_SUCCESS;
+}
+
+qtm_status ensure_device(qtm_plan *p)
+{
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(p, e, "no CUDA device");
+    int count = 0;
+    e = cudaGetDeviceCount(&count);
+    if (e != cudaSuccess || count == 0) return fail(p, QTM_ECUDA, "no CUDA device");
+    if (p->device == dev && p->d_status) return QTM_OK;
+    if (p->d_status) {
+        free_workspace(p);
+        free_tables(p);
+    }
+    const Plan &P = p->P;
+    std::vector<unsigned> zero(1, 0u);
+#define UP(dst, vec)                                               \
+    do {                                                           \
+        e = upload(&(dst), vec);                                   \
+        if (e != cudaSuccess) { free_tables(p); return cuda_fail(p, e, "upload"); } \
+    } while (0)
+    UP(p->d_ops, P.ops);
+    UP(p->d_phases, P.phases);
+    UP(p->d_slot_runs, P.slot_runs);
+    UP(p->d_runs, P.runs);
+    UP(p->d_rots, P.rots);
+    UP(p->d_prefix_run_of_q, P.prefix_run_of_q);
+    UP(p->d_prefix_ents, P.prefix_ents);
+    UP(p->d_terms, P.terms);
+    UP(p->d_w_ptr, P.w_ptr);
+    UP(p->d_w_rots, P.w_rots);
+    UP(p->d_x_ptr, P.x_ptr);
+    UP(p->d_x_rots, P.x_rots);
+    UP(p->d_status, zero);
+#undef UP
+    p->device = dev;
+    return QTM_OK;
+}
+
+qtm_status ensure_workspace(qtm_plan *p, int B)
+{
+    if (B <= p->cap_B && p->d_phi) return QTM_OK;
+    free_workspace(p);
+    const Plan &P = p->P;
+    const size_t csize = elem_bytes(P.dtype);
+    const size_t rsize = csize / 2;
+    const size_t NS = P.path == QTM_PATH_NAIVE ? (1ull << P.n) : (1ull << P.state_qubits);
+    const size_t runs = P.runs.size() ? P.runs.size() : 1;
+    const size_t rots = P.rots.size() ? P.rots.size() : 1;
+    const size_t tiles = P.tiles_per_sample;
+    cudaError_t e;
+#define AL(ptr, bytes)                                                                  \
+    do {                                                                                \
+        e = dmalloc(reinterpret_cast<void **>(&(ptr)), bytes);                          \
+        if (e != cudaSuccess) { free_workspace(p); return fail(p, QTM_ENOMEM, "workspace allocation failed"); } \
+    } while (0)
+    AL(p->d_phi, csize * NS * B);
+    if (p->needs_lam || P.path == QTM_PATH_NAIVE) AL(p->d_lam, csize * NS * B);
+    AL(p->d_Escratch, rsize * (size_t)B * P.n_obs);
+    AL(p->d_Epart, sizeof(double) * (size_t)B * tiles * P.n_obs);
+    AL(p->d_Gpart, sizeof(double) * (size_t)B * runs * tiles * 3);
+    AL(p->d_abar, sizeof(double) * (size_t)B * rots * 3);   // naive path keeps cos/sin in the tail
+    AL(p->d_gw_ws, sizeof(double) * (size_t)B * (P.n_weights ? P.n_weights : 1));
+#undef AL
+    p->cap_B = B;
+    if (P.path == QTM_PATH_FUSED) {
+        p->tm_fwd.assign(P.fwd.size(), CUtensorMap{});
+        p->g_fwd.assign(P.fwd.size(), TmGeom{});
+        p->tm_rev_phi.assign(P.rev.size(), CUtensorMap{});
+        p->tm_rev_lam.assign(P.rev.size(), CUtensorMap{});
+        p->g_rev.assign(P.rev.size(), TmGeom{});
+        for (size_t i = 0; i < P.fwd.size(); ++i)
+            if (!make_tmap(&p->tm_fwd[i], p->d_phi, P.fwd[i], P.state_qubits, B, P.dtype, p->g_fwd[i])) {
+                free_workspace(p);
+                return fail(p, QTM_ECUDA, "cuTensorMapEncodeTiled failed (forward)");
+            }
+        for (size_t i = 0; i < P.rev.size(); ++i) {
+            if (!make_tmap(&p->tm_rev_phi[i], p->d_phi, P.rev[i], P.state_qubits, B, P.dtype, p->g_rev[i])) {
+                free_workspace(p);
+                return fail(p, QTM_ECUDA, "cuTensorMapEncodeTiled failed (reverse)");
+            }
+            TmGeom gl;
+            void *lb = p->d_lam ? p->d_lam : p->d_phi;
+            if (!make_tmap(&p->tm_rev_lam[i], lb, P.rev[i], P.state_qubits, B, P.dtype, gl)) {
+                free_workspace(p);
+                return fail(p, QTM_ECUDA, "cuTensorMapEncodeTiled failed (costate)");
+            }
+        }
+    }
+    return QTM_OK;
+}
+
+// ---- profiling hooks: events around launches (no-ops unless enabled) ----
+void prof_begin_call(qtm_plan *p, int which, cudaStream_t s)
+{
+    p->cur_which = which;
+    p->cur_stream = s;
+    if (!p->profiling) return;
+    p->recs[which].clear();
+    p->ev_used = 0;
+}
+
+cudaEvent_t prof_event(qtm_plan *p)
+{
+    if (p->ev_used == p->ev_pool.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        p->ev_pool.push_back(e);
+    }
+    return p->ev_pool[p->ev_used++];
+}
+
+struct ProfScope {
+    qtm_plan *p;
+    qtm_plan::Rec r{};
+    bool on = false;
+    ProfScope(qtm_plan *p_, int kind) : p(p_)
+    {
+        if (!p->profiling) return;
+        r.a = prof_event(p);
+        r.b = prof_event(p);
+        r.kind = kind;
+        on = r.a && r.b;
+        if (on) cudaEventRecord(r.a, p->cur_stream);
+    }
+    ~ProfScope()
+    {
+        if (!on) return;
+        cudaEventRecord(r.b, p->cur_stream);
+        p->recs[p->cur_which].push_back(r);
+    }
+};
+
+PassArgs pass_args(qtm_plan *p, const PassDesc &pd, const TmGeom &g, size_t smem, int B,
+                   const void *x, const void *w, const void *gE)
+{
+    const Plan &P = p->P;
+    PassArgs a{};
+    a.K = pd.K; a.l = pd.l; a.h = pd.h; a.m = pd.m;
+    a.state_qubits = P.state_qubits; a.n = P.n;
+    a.tiles = P.tiles_per_sample;
+    a.log_tiles = 0;
+    while ((1 << a.log_tiles) < a.tiles) ++a.log_tiles;
+    a.B = B;
+    a.rank = g.rank; a.low_dims = g.low_dims; a.high_dims = g.high_dims;
+    a.gap_dim = pd.h > pd.l ? 1 : 0;
+    a.ops = p->d_ops; a.phases = p->d_phases;
+    a.phase_begin = pd.phase_begin; a.phase_end = pd.phase_end;
+    a.slot_runs = p->d_slot_runs; a.slot_begin = pd.slot_begin; a.nslots = pd.slot_end - pd.slot_begin;
+    a.runs = p->d_runs; a.rots = p->d_rots; a.n_runs = (int)P.runs.size();
+    a.prefix_run_of_q = p->d_prefix_run_of_q; a.prefix_ents = p->d_prefix_ents;
+    a.analytic_ents = pd.phi_src == SRC_ANALYTIC ? pd.analytic_ents : 0;
+    a.phi_src = pd.phi_src; a.lam_src = pd.lam_src;
+    a.store_phi = pd.store_phi; a.store_lam = pd.store_lam; a.has_expval = pd.has_expval;
+    a.terms = p->d_terms; a.n_terms = (int)P.terms.size(); a.M = P.n_obs;
+    a.x = x; a.w = w; a.gE = gE; a.n_in = P.n_inputs;
+    a.Epart = p->d_Epart; a.Gpart = p->d_Gpart;
+    a.status = p->d_status;
+    a.smem_bytes = (int)smem;
+    return a;
+}
+
+qtm_status run_forward_passes(qtm_plan *p, int B, const void *x, const void *w, cudaStream_t s)
+{
+    const Plan &P = p->P;
+    for (size_t i = 0; i < P.fwd.size(); ++i) {
+        PassArgs a = pass_args(p, P.fwd[i], p->g_fwd[i], p->smem_fwd[i], B, x, w, nullptr);
+        ProfScope ps(p, 0);
+        cudaError_t e = launch_pass(P.dtype, false, a, p->tm_fwd[i], p->tm_fwd[i], s);
+        if (e != cudaSuccess) return cuda_fail(p, e, "forward pass launch");
+    }
+    return QTM_OK;
+}
+
+FinalizeArgs finalize_args(qtm_plan *p, int B, const void *x, const void *w)
+{
+    const Plan &P = p->P;
+    FinalizeArgs f{};
+    f.B = B; f.M = P.n_obs; f.tiles = P.tiles_per_sample; f.n_runs = (int)P.runs.size();
+    f.n_rots = (int)P.rots.size(); f.P = P.n_weights; f.n_in = P.n_inputs;
+    f.runs = p->d_runs; f.rots = p->d_rots;
+    f.w_ptr = p->d_w_ptr; f.w_rots = p->d_w_rots; f.x_ptr = p->d_x_ptr; f.x_rots = p->d_x_rots;
+    f.x = x; f.w = w; f.Epart = p->d_Epart; f.Gpart = p->d_Gpart; f.abar = p->d_abar;
+    return f;
+}
+
+NaiveArgs naive_args(qtm_plan *p, int B, const void *x, const void *w, const void *gE)
+{
+    const Plan &P = p->P;
+    NaiveArgs a{};
+    a.n = P.n; a.B = B; a.n_in = P.n_inputs; a.M = P.n_obs; a.n_terms = (int)P.terms.size();
+    a.n_rots = (int)P.rots.size(); a.P = P.n_weights;
+    a.gates_host = P.gates.data(); a.n_gates = (int)P.gates.size();
+    a.terms = p->d_terms; a.rot_of_gate_host = P.rot_of_gate.data(); a.rots = p->d_rots;
+    a.w_ptr = p->d_w_ptr; a.w_rots = p->d_w_rots; a.x_ptr = p->d_x_ptr; a.x_rots = p->d_x_rots;
+    a.x = x; a.w = w; a.gE = gE; a.phi = p->d_phi; a.lam = p->d_lam; a.abar = p->d_abar;
+    a.gw_ws = p->d_gw_ws;
+    return a;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *qtm_status_str(int st)
+{
+    switch (st) {
+    case QTM_OK: return "ok";
+    case QTM_EINVAL: return "invalid argument";
+    case QTM_ENOMEM: return "out of memory";
+    case QTM_ECUDA: return "CUDA error";
+    case QTM_EUNSUPPORTED: return "unsupported";
+    case QTM_ETIMEOUT: return "device wait timed out";
+    case QTM_ESTATE: return "call order violated";
+    default: return "unknown status";
+    }
+}
+
+const char *qtm_version(void) { return "qtm 0.1 sm_103a"; }
+
+const char *qtm_last_error(const qtm_plan *plan) { return plan ? plan->err.c_str() : ""; }
+
+qtm_status qtm_build(int n_qubits, const qtm_gate *gates, int n_gates, const qtm_zterm *terms,
+                     int n_terms, int n_obs, int n_weights, int n_inputs, int dtype, int path,
+                     qtm_plan **out)
+{
+    if (!out) return QTM_EINVAL;
+    *out = nullptr;
+    qtm_plan *p = new (std::nothrow) qtm_plan();
+    if (!p) return QTM_ENOMEM;
+    std::string err;
+    qtm_status st = make_plan(n_qubits, gates, n_gates, terms, n_terms, n_obs, n_weights, n_inputs,
+                              dtype, path, p->P, err);
+    if (st != QTM_OK) { delete p; return st; }
+    const Plan &P = p->P;
+    if (P.path == QTM_PATH_FUSED) {
+        for (const auto &pd : P.rev)
+            if (pd.lam_src == SRC_LOAD || pd.store_lam) p->needs_lam = true;
+        auto sm = [&](const PassDesc &pd, bool rev) {
+            return pass_smem_bytes(pd.K, P.dtype, rev, pd.slot_end - pd.slot_begin, (int)P.terms.size(),
+                                   P.n_obs, P.state_qubits,
+                                   pd.phi_src == SRC_ANALYTIC ? pd.analytic_ents : 0);
+        };
+        for (const auto &pd : P.fwd) p->smem_fwd.push_back(sm(pd, false));
+        for (const auto &pd : P.rev) p->smem_rev.push_back(sm(pd, true));
+        for (size_t v : p->smem_fwd)
+            if (v > kMaxDynSmem) { delete p; return QTM_EUNSUPPORTED; }
+        for (size_t v : p->smem_rev)
+            if (v > kMaxDynSmem) { delete p; return QTM_EUNSUPPORTED; }
+    }
+    *out = p;
+    return QTM_OK;
+}
+
+qtm_status qtm_get_plan_info(const qtm_plan *p, qtm_plan_info *info)
+{
+    if (!p || !info) return QTM_EINVAL;
+    const Plan &P = p->P;
+    std::memset(info, 0, sizeof(*info));
+    info->n_qubits = P.n;
+    info->dtype = P.dtype;
+    info->path = P.path;
+    info->tile_qubits = P.K;
+    info->fwd_passes = (int)P.fwd.size();
+    info->adj_passes = (int)P.rev.size();
+    if (P.path == QTM_PATH_FUSED) {
+        info->fwd_launches = (int)P.fwd.size() + 1;
+        info->adj_launches = (int)P.rev.size() + 1;
+    } else {
+        int nrot = 0;
+        for (const auto &g : P.gates) nrot += (g.kind <= QTM_RZ);
+        info->fwd_launches = (int)P.gates.size() + 2 + (nrot > 0);
+        info->adj_launches = 1 + (int)P.gates.size() + nrot + 1;
+    }
+    info->n_runs = (int)P.runs.size();
+    int np = 0;
+    for (const auto &r : P.runs) np += r.prefix;
+    info->n_prefix_runs = np;
+    info->n_prefix_ents = (int)P.prefix_ents.size();
+    plan_costs(P, info->fwd_state_bytes, info->adj_state_bytes, info->fwd_flops, info->adj_flops);
+    return QTM_OK;
+}
+
+qtm_status qtm_forward(qtm_plan *p, int B, const void *x, const void *w, void *expvals, void *stream)
+{
+    if (!p) return QTM_EINVAL;
+    const Plan &P = p->P;
+    if (B < 1) return fail(p, QTM_EINVAL, "B must be >= 1");
+    if ((P.n_inputs > 0 && !x) || (P.n_weights > 0 && !w) || !expvals)
+        return fail(p, QTM_EINVAL, "null pointer");
+    qtm_status st = ensure_device(p);
+    if (st != QTM_OK) return st;
+    st = ensure_workspace(p, B);
+    if (st != QTM_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    p->fwd_valid = false;
+    prof_begin_call(p, 0, s);
+    if (P.path == QTM_PATH_NAIVE) {
+        NaiveArgs a = naive_args(p, B, x, w, nullptr);
+        a.E = expvals;
+        cudaError_t e = naive_forward(P.dtype, a, s, nullptr);
+        if (e != cudaSuccess) return cuda_fail(p, e, "naive forward");
+    } else {
+        st = run_forward_passes(p, B, x, w, s);
+        if (st != QTM_OK) return st;
+        FinalizeArgs f = finalize_args(p, B, x, w);
+        f.E = expvals;
+        ProfScope ps(p, 1);
+        cudaError_t e = launch_expval_finalize(P.dtype, f, s);
+        if (e != cudaSuccess) return cuda_fail(p, e, "expval finalize");
+    }
+    p->fwd_valid = true;
+    p->fwd_B = B; p->fwd_x = x; p->fwd_w = w; p->fwd_stream = stream;
+    return QTM_OK;
+}
+
+qtm_status qtm_adjoint(qtm_plan *p, int B, const void *gE, const void *x, const void *w, void *gx,
+                       void *gw, int flags, void *stream)
+{
+    if (!p) return QTM_EINVAL;
+    const Plan &P = p->P;
+    if (B < 1) return fail(p, QTM_EINVAL, "B must be >= 1");
+    if (!gE || (P.n_inputs > 0 && !x) || (P.n_weights > 0 && !w))
+        return fail(p, QTM_EINVAL, "null pointer");
+    if (flags & ~(QTM_ADJ_GW_PER_SAMPLE | QTM_ADJ_RECOMPUTE)) return fail(p, QTM_EINVAL, "unknown flags");
+    const bool recompute = (flags & QTM_ADJ_RECOMPUTE) != 0;
+    const bool per_sample = (flags & QTM_ADJ_GW_PER_SAMPLE) != 0;
+    if (!recompute && !(p->fwd_valid && p->fwd_B == B && p->fwd_x == x && p->fwd_w == w))
+        return fail(p, QTM_ESTATE, "no stored forward for these (B, x, w); pass QTM_ADJ_RECOMPUTE");
+    qtm_status st = ensure_device(p);
+    if (st != QTM_OK) return st;
+    st = ensure_workspace(p, B);
+    if (st != QTM_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e;
+    prof_begin_call(p, 1, s);
+    if (P.path == QTM_PATH_NAIVE) {
+        NaiveArgs a = naive_args(p, B, x, w, gE);
+        if (recompute) {
+            a.E = nullptr;
+            e = naive_forward(P.dtype, a, s, nullptr);
+            if (e != cudaSuccess) return cuda_fail(p, e, "naive forward");
+        }
+        a.gx = gx; a.gw_out = gw;
+        e = naive_adjoint(P.dtype, a, per_sample, s, nullptr);
+        if (e != cudaSuccess) return cuda_fail(p, e, "naive adjoint");
+        p->fwd_valid = false;
+        return QTM_OK;
+    }
+    if (recompute) {
+        st = run_forward_passes(p, B, x, w, s);
+        if (st != QTM_OK) return st;
+    }
+    bool consumes = false;
+    for (size_t i = 0; i < P.rev.size(); ++i) {
+        PassArgs a = pass_args(p, P.rev[i], p->g_rev[i], p->smem_rev[i], B, x, w, gE);
+        if (P.rev[i].store_phi) consumes = true;
+        ProfScope ps(p, 0);
+        e = launch_pass(P.dtype, true, a, p->tm_rev_phi[i], p->tm_rev_lam[i], s);
+        if (e != cudaSuccess) return cuda_fail(p, e, "reverse pass launch");
+    }
+    FinalizeArgs f = finalize_args(p, B, x, w);
+    f.gx = gx;
+    f.gw_out = per_sample ? gw : nullptr;
+    f.gw_ws = (!per_sample && gw) ? p->d_gw_ws : nullptr;
+    {
+        ProfScope ps(p, 1);
+        e = launch_grad_finalize(P.dtype, f, s);
+    }
+    if (e != cudaSuccess) return cuda_fail(p, e, "gradient finalize");
+    if (!per_sample && gw) {
+        ProfScope ps(p, 1);
+        e = launch_gw_reduce(P.dtype, p->d_gw_ws, B, P.n_weights, gw, s);
+        if (e != cudaSuccess) return cuda_fail(p, e, "gw reduce");
+    }
+    // the smem path leaves the stored state untouched; HBM sweeps consume it
+    p->fwd_valid = !consumes && (recompute ? true : p->fwd_valid);
+    if (recompute && !consumes) { p->fwd_B = B; p->fwd_x = x; p->fwd_w = w; p->fwd_stream = stream; }
+    return QTM_OK;
+}
+
+qtm_status qtm_jacobian(qtm_plan *p, int B, const void *x, const void *w, void *jac, void *stream)
+{
+    (void)B; (void)x; (void)w; (void)jac; (void)stream;
+    return fail(p, QTM_EUNSUPPORTED, "qtm_jacobian: not built yet");
+}
+
+qtm_status qtm_sync(qtm_plan *p, void *stream)
+{
+    if (!p) return QTM_EINVAL;
+    cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(p, e, "stream synchronize");
+    if (!p->d_status) return QTM_OK;
+    unsigned st = 0;
+    e = cudaMemcpy(&st, p->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(p, e, "status read");
+    if (st) {
+        unsigned zero = 0;
+        cudaMemcpy(p->d_status, &zero, sizeof(unsigned), cudaMemcpyHostToDevice);
+        return fail(p, QTM_ETIMEOUT, "a device-side wait gave up");
+    }
+    return QTM_OK;
+}
+
+qtm_status qtm_set_profiling(qtm_plan *p, int enable)
+{
+    if (!p) return QTM_EINVAL;
+    p->profiling = enable != 0;
+    return QTM_OK;
+}
+
+qtm_status qtm_get_launch_times(qtm_plan *p, int which, float *ms, int *kinds, int cap, int *count)
+{
+    if (!p || which < 0 || which > 1 || cap < 0) return QTM_EINVAL;
+    const auto &v = p->recs[which];
+    if (count) *count = (int)v.size();
+    for (int i = 0; i < (int)v.size() && i < cap; ++i) {
+        float t = 0.f;
+        cudaError_t e = cudaEventElapsedTime(&t, v[i].a, v[i].b);
+        if (e != cudaSuccess) return cuda_fail(p, e, "event elapsed time");
+        if (ms) ms[i] = t;
+        if (kinds) kinds[i] = v[i].kind;
+    }
+    return QTM_OK;
+}
+
+qtm_status qtm_destroy(qtm_plan *p)
+{
+    if (!p) return QTM_EINVAL;
+    for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
+    if (p->d_status) {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        cudaSetDevice(p->device);
+        cudaDeviceSynchronize();
+        free_workspace(p);
+        free_tables(p);
+        if (cur >= 0) cudaSetDevice(cur);
+    }
+    delete p;
+    return QTM_OK;
+}
+
+const char *qtm_debug_describe(const qtm_plan *p)
+{
+    if (!p) return "";
+    qtm_plan *m = const_cast<qtm_plan *>(p);
+    m->describe_cache = p->P.describe();
+    return m->describe_cache.c_str();
+}
+
+qtm_status qtm_debug_emulate(const qtm_plan *p, int B, const double *x, const double *w,
+                             const double *gE, double *E, double *gx, double *gw)
+{
+    if (!p || B < 1) return QTM_EINVAL;
+    std::string err;
+    qtm_status st = emulate_plan(p->P, B, x, w, gE, E, gx, gw, err);
+    if (st != QTM_OK) const_cast<qtm_plan *>(p)->err = err;
+    return st;
+}
+
+}  // extern "C"

@@ -1,0 +1,94 @@
+// Kernel argument blocks and launch declarations (CUDA side, internal).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include "plan.h"
+
+namespace qtm {
+
+// status word bits recorded by kernels
+constexpr unsigned kStatusTimeout = 1u;
+
+struct PassArgs {
+    // geometry
+    int K, l, h, m;
+    int state_qubits, n;
+    int tiles, log_tiles;
+    int B;
+    int rank;                     // tensor-map rank of this pass
+    int low_dims, gap_dim, high_dims;   // dims per segment (for coordinates)
+    // program
+    const DevOp *ops;
+    const DevPhase *phases;
+    int phase_begin, phase_end;
+    const int32_t *slot_runs;
+    int slot_begin, nslots;
+    const Run *runs;
+    const Rot *rots;
+    int n_runs;
+    // analytic init
+    const int32_t *prefix_run_of_q;
+    const Ent *prefix_ents;
+    int analytic_ents;
+    // sources / sinks
+    int phi_src, lam_src, store_phi, store_lam, has_expval;
+    // observables
+    const Term *terms;
+    int n_terms, M;
+    // data (plan real type)
+    const void *x, *w, *gE;
+    int n_in;
+    double *Epart;                // [B][tiles][M]
+    double *Gpart;                // [B][n_runs][tiles][3]
+    unsigned *status;
+    int smem_bytes;
+};
+
+struct FinalizeArgs {
+    int B, M, tiles, n_runs, n_rots, P, n_in;
+    const Run *runs;
+    const Rot *rots;
+    const int32_t *w_ptr, *w_rots, *x_ptr, *x_rots;
+    const void *x, *w;            // plan real type
+    const double *Epart;
+    const double *Gpart;
+    void *E;                      // [B][M] real type (may be null)
+    double *abar;                 // [B][n_rots] workspace
+    void *gx;                     // [B][n_in] real (may be null)
+    void *gw_out;                 // per-sample [B][P] real (may be null)
+    double *gw_ws;                // per-sample [B][P] double workspace (may be null)
+};
+
+// Shared memory a pass kernel needs (bytes), for K tile qubits.
+size_t pass_smem_bytes(int K, int dtype, bool reverse, int nslots, int n_terms, int M,
+                       int state_qubits, int n_prefix_ents);
+
+cudaError_t launch_pass(int dtype, bool reverse, const PassArgs &a, const CUtensorMap &tm_phi,
+                        const CUtensorMap &tm_lam, cudaStream_t s);
+cudaError_t launch_expval_finalize(int dtype, const FinalizeArgs &f, cudaStream_t s);
+cudaError_t launch_grad_finalize(int dtype, const FinalizeArgs &f, cudaStream_t s);
+cudaError_t launch_gw_reduce(int dtype, const double *gw_ws, int B, int P, void *gw,
+                             cudaStream_t s);
+
+// naive one-gate-per-kernel path
+struct NaiveArgs {
+    int n, B, n_in, M, n_terms, n_rots, P;
+    const qtm_gate *gates_host;   // host copy (launch loop)
+    int n_gates;
+    const Term *terms;
+    const int32_t *rot_of_gate_host;
+    const Rot *rots;
+    const int32_t *w_ptr, *w_rots, *x_ptr, *x_rots;
+    const void *x, *w, *gE;
+    void *phi, *lam;              // [B][2^n] complex
+    double *abar;                 // [B][n_rots]
+    void *E, *gx, *gw_out;
+    double *gw_ws;
+};
+cudaError_t naive_forward(int dtype, const NaiveArgs &a, cudaStream_t s, int *launches);
+cudaError_t naive_adjoint(int dtype, const NaiveArgs &a, bool gw_per_sample, cudaStream_t s,
+                          int *launches);
+
+}  // namespace qtm

@@ -1,0 +1,137 @@
+"""Host-side checks of the C ABI library (no GPU needed).
+
+* libqtm.so loads and exports every function declared in include/*.h;
+* qtm_build validates its arguments (QTM_EINVAL, nothing launched);
+* the planner's schedule, interpreted on the host (qtm_debug_emulate), equals
+  the FP64 oracle on the benchmark workloads and on random circuits;
+* without a GPU the compute calls fail loudly (QTM_ECUDA), never fall back.
+"""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import oracle_pins as P
+from paper_2404_06314_gb300 import capi, workloads as W
+
+INCLUDE = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+
+
+def declared_functions():
+    names = set()
+    for f in os.listdir(INCLUDE):
+        if not f.endswith(".h"):
+            continue
+        src = open(os.path.join(INCLUDE, f)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for m in re.finditer(r"\b(qtm_\w+)\s*\(", src):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_library_exports_every_declared_symbol():
+    L = capi.lib()
+    names = declared_functions()
+    assert "qtm_build" in names and "qtm_forward" in names and "qtm_adjoint" in names
+    missing = [n for n in names if not hasattr(L, n)]
+    assert not missing, missing
+    assert capi.qtm_version().startswith("qtm")
+
+
+def _build_raw(n, gates, terms, n_obs=1, P_=2, n_in=2, dtype=0, path=0):
+    G = (capi.qtm_gate * max(1, len(gates)))(*[capi.qtm_gate(*g) for g in gates])
+    T = (capi.qtm_zterm * max(1, len(terms)))(*[capi.qtm_zterm(*t) for t in terms])
+    h = ctypes.c_void_p()
+    st = capi.lib().qtm_build(n, G, len(gates), T, len(terms), n_obs, P_, n_in, dtype, path,
+                              ctypes.byref(h))
+    if st == capi.QTM_OK:
+        capi.qtm_destroy(h.value)
+    return st
+
+
+@pytest.mark.parametrize("case", [
+    dict(n=0, gates=[], terms=[]),
+    dict(n=31, gates=[], terms=[]),
+    dict(n=3, gates=[(0, 3, -1, -1, -1, 0, 1.0)], terms=[]),          # qubit out of range
+    dict(n=3, gates=[(0, 1, 2, -1, -1, 0, 1.0)], terms=[]),           # rotation with q1
+    dict(n=3, gates=[(3, 1, 1, -1, -1, 0, 1.0)], terms=[]),           # CZ on one qubit
+    dict(n=3, gates=[(4, 0, 1, 0, -1, 0, 1.0)], terms=[]),            # CNOT with a weight
+    dict(n=3, gates=[(1, 0, -1, 2, -1, 0, 1.0)], terms=[]),           # w_idx >= n_weights
+    dict(n=3, gates=[(1, 0, -1, -1, 5, 0, 1.0)], terms=[]),           # x_idx >= n_inputs
+    dict(n=3, gates=[(7, 0, -1, -1, -1, 0, 1.0)], terms=[]),          # unknown kind
+    dict(n=3, gates=[(1, 0, -1, -1, -1, 1, 1.0)], terms=[]),          # reserved != 0
+    dict(n=3, gates=[(1, 0, -1, -1, -1, 0, float("nan"))], terms=[]),
+    dict(n=3, gates=[], terms=[(8, 1.0, 0, 0)]),                      # zmask beyond n
+    dict(n=3, gates=[], terms=[(1, 1.0, 1, 0)]),                      # obs >= n_obs
+    dict(n=3, gates=[], terms=[], n_obs=0),
+    dict(n=3, gates=[], terms=[], dtype=5),
+    dict(n=3, gates=[], terms=[], path=9),
+])
+def test_build_rejects_bad_arguments(case):
+    assert _build_raw(**case) == capi.QTM_EINVAL
+
+
+def test_build_accepts_valid_and_reports_info():
+    c = W.workload_20q()
+    plan = capi.Plan(c)
+    info = plan.info
+    assert info["n_qubits"] == 20 and info["tile_qubits"] == 12
+    assert info["n_prefix_runs"] == 20 and info["n_prefix_ents"] == 19
+    assert info["fwd_passes"] >= 1 and info["adj_passes"] >= 1
+    # every pass moves whole tiles of 2^20 complex64 states
+    assert info["fwd_state_bytes"] % (8 << 20) == 0 and info["adj_state_bytes"] % (8 << 20) == 0
+    assert "fwd[0]" in plan.describe()
+
+
+def _emulate_vs_oracle(c, B, seed, tol=1e-11):
+    plan = capi.Plan(c)
+    inp = W.make_inputs(c, B, seed)
+    E, gx, gw = capi.qtm_debug_emulate(plan.handle, inp.x, inp.w, inp.gE, circuit=c)
+    Eo = oracle.forward(c, inp.x, inp.w, threads=0)
+    _, gxo, gwo = oracle.adjoint(c, inp.gE, inp.x, inp.w, threads=0)
+    for got, ref, nm in ((E, Eo, "E"), (gx, gxo, "gx"), (gw, gwo, "gw")):
+        err = float(np.max(np.abs(got - ref))) if ref.size else 0.0
+        assert err < tol, f"{c.name} {nm}: {err:.3e}"
+
+
+@pytest.mark.parametrize("builder", ["workload_4q", "workload_12q", "workload_16q_train"])
+def test_schedule_matches_oracle_workloads(builder):
+    _emulate_vs_oracle(getattr(W, builder)(), 2, 5)
+
+
+@pytest.mark.slow
+def test_schedule_matches_oracle_20q():
+    _emulate_vs_oracle(W.workload_20q(), 1, 5)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 6, 9, 12, 13, 14, 15])
+def test_schedule_matches_oracle_random(n):
+    rng = np.random.default_rng(40 + n)
+    c = P.rand_small_circuit(rng, n, G=6 * n + 8, n_obs=3)
+    c.name = f"rand{n}"
+    _emulate_vs_oracle(c, 2, n)
+
+
+def test_schedule_matches_oracle_uneven_members():
+    for c in W.workload_uneven(count=24, n_hi=15):
+        _emulate_vs_oracle(c, 1, 3)
+
+
+def test_schedule_paper_ansatz():
+    _emulate_vs_oracle(W.jerbi_ansatz(6, 2), 2, 8)
+    _emulate_vs_oracle(W.jerbi_ansatz(13, 1), 1, 9)
+
+
+def test_no_gpu_fails_loudly():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("GPU present")
+    c = W.workload_4q()
+    plan = capi.Plan(c)
+    fake = ctypes.c_void_p(256)   # never dereferenced: no device is found first
+    st = capi.qtm_forward(plan.handle, 2, fake, fake, fake, None)
+    assert st == capi.QTM_ECUDA
+    assert "CUDA" in capi.qtm_last_error(plan.handle) or "device" in capi.qtm_last_error(plan.handle)

@@ -1,0 +1,189 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Tolerances (from the build targets): complex64 plans 1e-5 absolute on every
+element of E[B, M], grad_x[B, n_in] and per-sample grad_w[B, P]; complex128
+plans 1e-12 (1e-11 for the naive path, whose reductions run over 2^n terms in
+one CTA).  The batch-summed grad_w is checked against the oracle's sum with
+the same bound scaled by max(1, sum_b |per-sample terms|).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import oracle_pins as P
+from paper_2404_06314_gb300 import capi, workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"c64": 1e-5, "c128": 1e-12}
+
+
+def run_gpu(c, inp, dtype="c64", path="fused", per_sample=True, recompute=False, plan=None):
+    import torch
+    plan = plan or capi.Plan(c, dtype=dtype, path=path)
+    rd = plan.real_dtype()
+    x = torch.tensor(inp.x, dtype=rd, device="cuda")
+    w = torch.tensor(inp.w, dtype=rd, device="cuda")
+    gE = torch.tensor(inp.gE, dtype=rd, device="cuda")
+    E = plan.forward(x, w)
+    gx, gw = plan.adjoint(gE, x, w, per_sample_w=per_sample, recompute=recompute)
+    plan.sync()
+    return E.double().cpu().numpy(), gx.double().cpu().numpy(), gw.double().cpu().numpy()
+
+
+def oracle_ref(c, inp, rows=None):
+    x, gE = inp.x, inp.gE
+    if rows is not None:
+        x, gE = x[rows], gE[rows]
+    E = oracle.forward(c, x, inp.w, threads=0)
+    _, gx, gw = oracle.adjoint(c, gE, x, inp.w, threads=0)
+    return E, gx, gw
+
+
+def assert_close(got, ref, tol, what):
+    err = float(np.max(np.abs(got - ref))) if ref.size else 0.0
+    assert err <= tol, f"{what}: max abs err {err:.3e} > {tol:.1e}"
+
+
+def check(c, B, dtype, path="fused", seed=7, tol=None):
+    tol = tol or TOL[dtype]
+    inp = W.make_inputs(c, B, seed, real_dtype=np.float32 if dtype == "c64" else np.float64)
+    E, gx, gw = run_gpu(c, inp, dtype, path)
+    Eo, gxo, gwo = oracle_ref(c, inp)
+    assert_close(E, Eo, tol, f"{c.name} {dtype} {path} E")
+    assert_close(gx, gxo, tol, f"{c.name} {dtype} {path} gx")
+    assert_close(gw, gwo, tol, f"{c.name} {dtype} {path} gw")
+    return inp, (Eo, gxo, gwo)
+
+
+# ---- the five workloads at reduced batch -----------------------------------
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+@pytest.mark.parametrize("path", ["fused", "naive"])
+def test_workload_4q(dtype, path):
+    check(W.workload_4q(), 8, dtype, path, tol=(1e-11 if dtype == "c128" else None))
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+def test_workload_12q(dtype):
+    check(W.workload_12q(), 37, dtype)   # ragged batch
+
+
+def test_workload_12q_naive():
+    check(W.workload_12q(), 5, "c64", "naive")
+
+
+def test_workload_20q_c64():
+    check(W.workload_20q(), 2, "c64")
+
+
+def test_workload_16q_train_c64():
+    check(W.workload_16q_train(), 3, "c64")
+
+
+def test_uneven_members():
+    for c in W.workload_uneven(count=16):
+        check(c, 2, "c64")
+
+
+# ---- random circuits and edge cases -------------------------------------------
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 7, 8, 9, 11, 12, 13, 14, 16])
+def test_random_circuits(n):
+    rng = np.random.default_rng(100 + n)
+    c = P.rand_small_circuit(rng, n, G=4 * n + 10, n_obs=3)
+    c.name = f"rand{n}"
+    check(c, 3, "c64")
+    check(c, 2, "c128", tol=1e-11)
+
+
+def test_no_parameters_and_empty_observable():
+    # only entanglers after a fixed encoding, an observable without terms
+    n = 6
+    gates = [(W.RY, q, -1, -1, -1, 0.3 + 0.1 * q) for q in range(n)] + W.cnot_chain(n) + W.cz_ring(n)
+    c = W.Circuit(n=n, gates=gates, terms=[(0b11, 1.0, 0), (1 << (n - 1), -2.0, 2)], n_obs=3,
+                  n_weights=0, n_inputs=0, name="noparam")
+    check(c, 4, "c64")
+
+
+def test_last_qubit_and_cnot_reversed():
+    n = 13
+    gates = [(W.RX, n - 1, -1, 0, 0, 1.0), (W.CNOT, n - 1, 0, -1, -1, 1.0), (W.RY, 0, -1, 1, 1, 0.5),
+             (W.CNOT, 0, n - 1, -1, -1, 1.0), (W.RZ, n - 1, -1, 2, -1, 1.0), (W.RY, 5, -1, 0, 1, 1.0),
+             (W.CZ, 5, n - 1, -1, -1, 1.0), (W.RX, 5, -1, 2, -1, 1.0)]
+    c = W.Circuit(n=n, gates=gates, terms=[(1 << (n - 1), 1.0, 0), ((1 << n) - 1, 1.0, 1)], n_obs=2,
+                  n_weights=3, n_inputs=2, name="lastq")
+    check(c, 3, "c64")
+    check(c, 3, "c128")
+
+
+def test_batch_one_and_batch_sum():
+    import torch
+    c = W.workload_12q()
+    inp = W.make_inputs(c, 64, 11, real_dtype=np.float32)
+    _, _, gw = run_gpu(c, inp, "c64", per_sample=False)
+    _, _, gwo = oracle_ref(c, inp)
+    scale = np.maximum(1.0, np.abs(gwo).sum(axis=0))
+    assert np.all(np.abs(gw - gwo.sum(axis=0)) <= 1e-5 * scale)
+    inp1 = W.make_inputs(c, 1, 12, real_dtype=np.float32)
+    E, gx, gw1 = run_gpu(c, inp1, "c64")
+    Eo, gxo, gwo1 = oracle_ref(c, inp1)
+    assert_close(E, Eo, 1e-5, "B=1 E")
+    assert_close(gw1, gwo1, 1e-5, "B=1 gw")
+    del torch
+
+
+def test_adjoint_requires_matching_forward():
+    import torch
+    c = W.workload_4q()
+    plan = capi.Plan(c, dtype="c64")
+    inp = W.make_inputs(c, 4, 3, real_dtype=np.float32)
+    x = torch.tensor(inp.x, dtype=torch.float32, device="cuda")
+    w = torch.tensor(inp.w, dtype=torch.float32, device="cuda")
+    gE = torch.tensor(inp.gE, dtype=torch.float32, device="cuda")
+    with pytest.raises(capi.QtmError) as ei:
+        plan.adjoint(gE, x, w)
+    assert ei.value.status == capi.QTM_ESTATE
+    gx, gw = plan.adjoint(gE, x, w, recompute=True, per_sample_w=True)
+    plan.sync()
+    _, gxo, gwo = oracle_ref(c, inp)
+    assert_close(gx.double().cpu().numpy(), gxo, 1e-5, "recompute gx")
+    assert_close(gw.double().cpu().numpy(), gwo, 1e-5, "recompute gw")
+
+
+def test_recompute_hbm_path():
+    c = W.workload_16q_train()
+    inp = W.make_inputs(c, 2, 9, real_dtype=np.float32)
+    plan = capi.Plan(c, dtype="c64")
+    E, gx, gw = run_gpu(c, inp, plan=plan)
+    E2, gx2, gw2 = run_gpu(c, inp, plan=plan, recompute=True)
+    assert_close(gx2, gx, 1e-6, "recompute equals stored gx")
+    assert_close(gw2, gw, 1e-6, "recompute equals stored gw")
+
+
+# ---- full-size configurations, sampled rows --------------------------------------
+
+def test_full_12q_batch_sampled():
+    c = W.workload_12q()
+    B = 1024
+    inp = W.make_inputs(c, B, W.WORKLOAD_SEEDS[c.name], real_dtype=np.float32)
+    E, gx, gw = run_gpu(c, inp, "c64")
+    rows = np.array([0, 1, 255, 256, 511, 700, 1022, 1023])
+    Eo, gxo, gwo = oracle_ref(c, inp, rows)
+    assert_close(E[rows], Eo, 1e-5, "12q full E")
+    assert_close(gx[rows], gxo, 1e-5, "12q full gx")
+    assert_close(gw[rows], gwo, 1e-5, "12q full gw")
+
+
+def test_full_20q_batch_sampled():
+    c = W.workload_20q()
+    B = 64
+    inp = W.make_inputs(c, B, W.WORKLOAD_SEEDS[c.name], real_dtype=np.float32)
+    E, gx, gw = run_gpu(c, inp, "c64")
+    rows = np.array([0, 63])
+    Eo, gxo, gwo = oracle_ref(c, inp, rows)
+    assert_close(E[rows], Eo, 1e-5, "20q full E")
+    assert_close(gx[rows], gxo, 1e-5, "20q full gx")
+    assert_close(gw[rows], gwo, 1e-5, "20q full gw")
+    # property at any size: |E| <= sum |c_t|
+    assert np.all(np.abs(E) <= 1.0 + 1e-5)

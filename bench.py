@@ -30,9 +30,17 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 WORKLOADS = {
-    "qnn12": dict(builder="workload_12q", B=1024, dtype="c64"),
-    "qnn20": dict(builder="workload_20q", B=64, dtype="c64"),
-    "qnn16": dict(builder="workload_16q_train", B=256, dtype="c64"),
+    "qnn12": dict(builder="workload_12q", B=1024, dtype="c64",
+                  desc="qnn12_l6: 12 qubits, 6 re-uploading layers RX(x) RY(w) RZ(w) + CZ ring, "
+                       "obs sum Z_i Z_{i+1}, B=1024, fwd + adjoint (grad_x, grad_w)",
+                  path_desc="fused: whole state in shared memory, one CTA per sample"),
+    "qnn20": dict(builder="workload_20q", B=64, dtype="c64",
+                  desc="qnn20_l4: 20 qubits, RX(x) + 4 layers RY(w) RZ(w) + CNOT chain, "
+                       "obs Z_0 and Z^(x)20, B=64, fwd + adjoint",
+                  path_desc="fused HBM sweeps: TMA tiles of 2^12 amplitudes"),
+    "qnn16": dict(builder="workload_16q_train", B=256, dtype="c64",
+                  desc="qnn16_l8: 16 qubits, 8 re-uploading layers + CZ ring, obs sum Z_i, B=256",
+                  path_desc="fused HBM sweeps: TMA tiles of 2^12 amplitudes"),
 }
 METRIC = "samples/sec fwd+adjoint grad at 12q and 20q; achieved HBM GB/s vs peak"
 L2_FLUSH_BYTES = 256 << 20   # > 126 MB L2
@@ -113,6 +121,39 @@ class ClockSampler:
         loaded = sorted(sm)[len(sm) // 2:] or sm
         return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": mx, "reasons": sorted(reasons),
                 "samples": len(rows)}
+
+
+def roofline(r, peaks, peak_src):
+    """Roofline of the dominant kernel, the reverse pass k_pass<float, reverse>,
+    from its live CUDA-event durations inside the timed region.  Algorithmic
+    work per launch = the plan's per-sample adjoint flops (or state bytes) x B
+    / reverse passes; both the FP32-ALU and the HBM fraction are computed and
+    the larger one names the binding resource."""
+    info, B = r["info"], r["B"]
+    n = max(1, r["n_rev_pass"])
+    t = r["pass_rev_ms"] / n / 1e3          # s per launch
+    if t <= 0:
+        return None
+    passes = max(1, info["adj_passes"])
+    flops = info["adj_flops"] * B / passes
+    bytes_ = info["adj_state_bytes"] * B / passes
+    alu_peak = fp32_alu_peak_tflops(peaks.get("sm_max_mhz", 2070.0))
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    alu = flops / t / 1e12
+    hbm = bytes_ / t / 1e9
+    alu_obj = {"bound": "alu", "achieved": alu, "peak": alu_peak, "unit": "TFLOP/s",
+               "frac": alu / alu_peak,
+               "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x %g MHz (sm_max_mhz of "
+                              "MEASURED_PEAKS.json)" % peaks.get("sm_max_mhz", 2070.0)}
+    hbm_obj = {"bound": "hbm", "achieved": hbm, "peak": hbm_peak, "unit": "GB/s",
+               "frac": hbm / hbm_peak, "peak_source": f"{peak_src} hbm_gbs (burst copy)"}
+    main, other = (alu_obj, hbm_obj) if alu_obj["frac"] >= hbm_obj["frac"] else (hbm_obj, alu_obj)
+    main = dict(main)
+    main.update({"kernel": "k_pass<float, reverse>", "traffic": None,
+                 "launch_ms": t * 1e3, "launches_timed": n,
+                 "work_per_launch": {"flop": flops, "state_bytes": bytes_},
+                 "other": {k: other[k] for k in ("bound", "achieved", "peak", "unit", "frac")}})
+    return main
 
 
 def dist_env():
@@ -328,56 +369,35 @@ def gpu_main(args):
     B = r12["B"]
     value = B * K * ws / (total_ms / 1e3)
     info = r12["info"]
-    sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    # dominant kernel of the smem-resident path: the reverse pass (ALU bound)
-    rev_ms_avg = r12["pass_rev_ms"] / max(1, r12["n_rev_pass"])
-    adj_flops_launch = info["adj_flops"] * B / max(1, info["adj_passes"])
-    alu_peak = fp32_alu_peak_tflops(peaks.get("sm_max_mhz", 2070.0))
-    achieved = adj_flops_launch / (rev_ms_avg / 1e3) / 1e12 if rev_ms_avg > 0 else None
-    roofline = {"bound": "alu", "kernel": "k_pass<float,reverse>", "achieved": achieved,
-                "peak": alu_peak, "unit": "TFLOP/s",
-                "frac": (achieved / alu_peak) if achieved else None,
-                "traffic": None,
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x %g MHz (MEASURED_PEAKS sm_max_mhz)"
-                               % peaks.get("sm_max_mhz", 2070.0)}
+    cfgd = WORKLOADS[args.workload]
     line = {
         "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": ws, "steps": K,
         "warmup": args.warmup, "ms_per_step": total_ms / K, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "c64 (fp32 complex; fp64 reductions)",
         "data": "synthetic (seeded x ~ U[-pi,pi], w ~ N(0,1), cotangents ~ N(0,1))",
-        "config": {"workload": "qnn12_l6: 12 qubits, 6 re-uploading layers RX(x) RY(w) RZ(w) + CZ ring, "
-                               "obs sum Z_i Z_{i+1}, fwd + adjoint (grad_x, grad_w)",
-                   "global_batch": B * ws, "per_gpu_batch": B, "qubits": 12, "layers": 6,
-                   "path": "fused (whole state in shared memory, one CTA per sample)",
-                   "l2": "flushed between steps (256 MiB write)",
+        "config": {"workload": cfgd["desc"], "global_batch": B * ws, "per_gpu_batch": B,
+                   "path": cfgd["path_desc"], "l2": "flushed between steps (256 MiB write)",
                    "parallelism": f"batch shards x{ws}"},
-        "roofline": roofline,
+        "roofline": roofline(r12, peaks, peak_src),
         "gpu_launches": r12["launches"],
         "clocks": clocks,
         "e2e": {"value": e2e[0], "unit": "samples/s", "h2d_bytes_per_step": e2e[1],
                 "d2h_bytes_per_step": e2e[2]},
-        "plan": {k: info[k] for k in ("fwd_passes", "adj_passes", "fwd_flops", "adj_flops")},
+        "plan": {k: info[k] for k in ("fwd_passes", "adj_passes", "fwd_flops", "adj_flops",
+                                       "fwd_state_bytes", "adj_state_bytes")},
     }
     if n20 is not None:
         r20, tot20 = n20
         i20 = r20["info"]
         K20 = len(r20["step_ms"])
-        v20 = r20["B"] * K20 * ws / (tot20 / 1e3)
-        rev_bytes = i20["adj_state_bytes"] * r20["B"]
-        fwd_bytes = i20["fwd_state_bytes"] * r20["B"]
-        rev_gbs = rev_bytes * K20 / (r20["pass_rev_ms"] / 1e3) / 1e9 if r20["pass_rev_ms"] else None
-        fwd_gbs = fwd_bytes * K20 / (r20["pass_fwd_ms"] / 1e3) / 1e9 if r20["pass_fwd_ms"] else None
-        hbm = peaks.get("hbm_gbs", 6800.0)
         line["n20"] = {
-            "value": v20, "unit": "samples/s", "ms_per_step": tot20 / K20, "steps": K20,
-            "config": {"workload": "qnn20_l4: 20 qubits, RX(x) + 4 layers RY/RZ + CNOT chain, obs Z_0, Z^20",
-                       "per_gpu_batch": r20["B"], "path": "fused HBM sweeps (TMA tiles of 2^12)"},
-            "roofline": {"bound": "hbm", "kernel": "k_pass<float,reverse>", "achieved": rev_gbs,
-                         "peak": hbm, "unit": "GB/s", "frac": rev_gbs / hbm if rev_gbs else None,
-                         "traffic": None, "peak_source": f"{peak_src} hbm_gbs"},
-            "forward_pass_gbs": fwd_gbs,
-            "state_bytes_per_sample": {"fwd": i20["fwd_state_bytes"], "adj": i20["adj_state_bytes"]},
-            "passes": {"fwd": i20["fwd_passes"], "adj": i20["adj_passes"]},
+            "value": r20["B"] * K20 * ws / (tot20 / 1e3), "unit": "samples/s",
+            "ms_per_step": tot20 / K20, "steps": K20,
+            "config": {"workload": WORKLOADS["qnn20"]["desc"], "per_gpu_batch": r20["B"],
+                       "path": WORKLOADS["qnn20"]["path_desc"]},
+            "roofline": roofline(r20, peaks, peak_src),
+            "plan": {k: i20[k] for k in ("fwd_passes", "adj_passes", "fwd_flops", "adj_flops",
+                                          "fwd_state_bytes", "adj_state_bytes")},
             "gpu_launches": r20["launches"],
         }
     if not args.no_cpu_baseline:

@@ -37,6 +37,7 @@ struct qtm_plan {
     int device = -1;
     // device tables
     DevOp *d_ops = nullptr;
+    DiagPair *d_diag = nullptr;
     DevPhase *d_phases = nullptr;
     int32_t *d_slot_runs = nullptr;
     Run *d_runs = nullptr;
@@ -50,6 +51,7 @@ struct qtm_plan {
     int cap_B = 0;
     void *d_phi = nullptr, *d_lam = nullptr, *d_Escratch = nullptr;
     double *d_Epart = nullptr, *d_Gpart = nullptr, *d_abar = nullptr, *d_gw_ws = nullptr;
+    void *d_mats = nullptr, *d_tabs = nullptr;
     std::vector<CUtensorMap> tm_fwd, tm_rev_phi, tm_rev_lam;
     std::vector<TmGeom> g_fwd, g_rev;
     std::vector<size_t> smem_fwd, smem_rev;
@@ -96,12 +98,12 @@ cudaError_t upload(T **dst, const std::vector<T> &v)
 
 void free_tables(qtm_plan *p)
 {
-    void *ptrs[] = {p->d_ops, p->d_phases, p->d_slot_runs, p->d_runs, p->d_rots,
+    void *ptrs[] = {p->d_ops, p->d_diag, p->d_phases, p->d_slot_runs, p->d_runs, p->d_rots,
                     p->d_prefix_run_of_q, p->d_prefix_ents, p->d_terms, p->d_w_ptr,
                     p->d_w_rots, p->d_x_ptr, p->d_x_rots, p->d_status};
     for (void *q : ptrs)
         if (q) cudaFree(q);
-    p->d_ops = nullptr; p->d_phases = nullptr; p->d_slot_runs = nullptr; p->d_runs = nullptr;
+    p->d_ops = nullptr; p->d_diag = nullptr; p->d_phases = nullptr; p->d_slot_runs = nullptr; p->d_runs = nullptr;
     p->d_rots = nullptr; p->d_prefix_run_of_q = nullptr; p->d_prefix_ents = nullptr;
     p->d_terms = nullptr; p->d_w_ptr = p->d_w_rots = p->d_x_ptr = p->d_x_rots = nullptr;
     p->d_status = nullptr;
@@ -109,10 +111,11 @@ void free_tables(qtm_plan *p)
 
 void free_workspace(qtm_plan *p)
 {
-    void *ptrs[] = {p->d_phi, p->d_lam, p->d_Escratch, p->d_Epart, p->d_Gpart, p->d_abar, p->d_gw_ws};
+    void *ptrs[] = {p->d_phi, p->d_lam, p->d_Escratch, p->d_Epart, p->d_Gpart, p->d_abar, p->d_gw_ws,
+                    p->d_mats, p->d_tabs};
     for (void *q : ptrs)
         if (q) cudaFree(q);
-    p->d_phi = p->d_lam = p->d_Escratch = nullptr;
+    p->d_phi = p->d_lam = p->d_Escratch = p->d_mats = p->d_tabs = nullptr;
     p->d_Epart = p->d_Gpart = p->d_abar = p->d_gw_ws = nullptr;
     p->cap_B = 0;
     p->fwd_valid = false;
@@ -207,6 +210,7 @@ qtm_status ensure_device(qtm_plan *p)
         if (e != cudaSuccess) { free_tables(p); return cuda_fail(p, e, "upload"); } \
     } while (0)
     UP(p->d_ops, P.ops);
+    UP(p->d_diag, P.diag_pairs);
     UP(p->d_phases, P.phases);
     UP(p->d_slot_runs, P.slot_runs);
     UP(p->d_runs, P.runs);
@@ -248,6 +252,8 @@ qtm_status ensure_workspace(qtm_plan *p, int B)
     AL(p->d_Gpart, sizeof(double) * (size_t)B * runs * tiles * 3);
     AL(p->d_abar, sizeof(double) * (size_t)B * rots * 3);   // naive path keeps cos/sin in the tail
     AL(p->d_gw_ws, sizeof(double) * (size_t)B * (P.n_weights ? P.n_weights : 1));
+    AL(p->d_mats, csize * 4 * (size_t)B * runs);
+    AL(p->d_tabs, csize * 16 * (size_t)B * ((P.state_qubits + 3) / 4));
 #undef AL
     p->cap_B = B;
     if (P.path == QTM_PATH_FUSED) {
@@ -331,11 +337,12 @@ PassArgs pass_args(qtm_plan *p, const PassDesc &pd, const TmGeom &g, size_t smem
     a.B = B;
     a.rank = g.rank; a.low_dims = g.low_dims; a.high_dims = g.high_dims;
     a.gap_dim = pd.h > pd.l ? 1 : 0;
-    a.ops = p->d_ops; a.phases = p->d_phases;
+    a.ops = p->d_ops; a.diag = p->d_diag; a.phases = p->d_phases;
     a.phase_begin = pd.phase_begin; a.phase_end = pd.phase_end;
     a.slot_runs = p->d_slot_runs; a.slot_begin = pd.slot_begin; a.nslots = pd.slot_end - pd.slot_begin;
-    a.runs = p->d_runs; a.rots = p->d_rots; a.n_runs = (int)P.runs.size();
-    a.prefix_run_of_q = p->d_prefix_run_of_q; a.prefix_ents = p->d_prefix_ents;
+    a.n_runs = (int)P.runs.size();
+    a.mats = p->d_mats; a.tabs = p->d_tabs;
+    a.prefix_ents = p->d_prefix_ents;
     a.analytic_ents = pd.phi_src == SRC_ANALYTIC ? pd.analytic_ents : 0;
     a.phi_src = pd.phi_src; a.lam_src = pd.lam_src;
     a.store_phi = pd.store_phi; a.store_lam = pd.store_lam; a.has_expval = pd.has_expval;
@@ -347,9 +354,24 @@ PassArgs pass_args(qtm_plan *p, const PassDesc &pd, const TmGeom &g, size_t smem
     return a;
 }
 
+qtm_status run_prep(qtm_plan *p, int B, const void *x, const void *w, cudaStream_t s)
+{
+    const Plan &P = p->P;
+    PrepArgs a{};
+    a.B = B; a.n = P.n; a.state_qubits = P.state_qubits; a.n_runs = (int)P.runs.size();
+    a.n_in = P.n_inputs; a.runs = p->d_runs; a.rots = p->d_rots;
+    a.prefix_run_of_q = p->d_prefix_run_of_q; a.x = x; a.w = w; a.mats = p->d_mats; a.tabs = p->d_tabs;
+    ProfScope ps(p, 1);
+    cudaError_t e = launch_prep(P.dtype, a, s);
+    if (e != cudaSuccess) return cuda_fail(p, e, "prep launch");
+    return QTM_OK;
+}
+
 qtm_status run_forward_passes(qtm_plan *p, int B, const void *x, const void *w, cudaStream_t s)
 {
     const Plan &P = p->P;
+    qtm_status st = run_prep(p, B, x, w, s);
+    if (st != QTM_OK) return st;
     for (size_t i = 0; i < P.fwd.size(); ++i) {
         PassArgs a = pass_args(p, P.fwd[i], p->g_fwd[i], p->smem_fwd[i], B, x, w, nullptr);
         ProfScope ps(p, 0);
@@ -451,7 +473,7 @@ qtm_status qtm_get_plan_info(const qtm_plan *p, qtm_plan_info *info)
     info->fwd_passes = (int)P.fwd.size();
     info->adj_passes = (int)P.rev.size();
     if (P.path == QTM_PATH_FUSED) {
-        info->fwd_launches = (int)P.fwd.size() + 1;
+        info->fwd_launches = (int)P.fwd.size() + 2;
         info->adj_launches = (int)P.rev.size() + 1;
     } else {
         int nrot = 0;

@@ -21,15 +21,15 @@ struct PassArgs {
     int low_dims, gap_dim, high_dims;   // dims per segment (for coordinates)
     // program
     const DevOp *ops;
+    const DiagPair *diag;
     const DevPhase *phases;
     int phase_begin, phase_end;
     const int32_t *slot_runs;
     int slot_begin, nslots;
-    const Run *runs;
-    const Rot *rots;
     int n_runs;
+    const void *mats;             // [B][n_runs][4] fused run matrices U (plan complex type)
+    const void *tabs;             // [B][ntab][16] product-state tables (plan complex type)
     // analytic init
-    const int32_t *prefix_run_of_q;
     const Ent *prefix_ents;
     int analytic_ents;
     // sources / sinks
@@ -60,6 +60,20 @@ struct FinalizeArgs {
     void *gw_out;                 // per-sample [B][P] real (may be null)
     double *gw_ws;                // per-sample [B][P] double workspace (may be null)
 };
+
+struct PrepArgs {
+    int B, n, state_qubits, n_runs, n_in;
+    const Run *runs;
+    const Rot *rots;
+    const int32_t *prefix_run_of_q;
+    const void *x, *w;            // plan real type
+    void *mats;                   // out: [B][n_runs][4] complex
+    void *tabs;                   // out: [B][ntab][16] complex
+};
+
+// Per-sample run matrices and product-state tables, computed in FP64 and
+// rounded once to the plan's complex type.
+cudaError_t launch_prep(int dtype, const PrepArgs &a, cudaStream_t s);
 
 // Shared memory a pass kernel needs (bytes), for K tile qubits.
 size_t pass_smem_bytes(int K, int dtype, bool reverse, int nslots, int n_terms, int M,

@@ -208,6 +208,16 @@ struct Emu {
                                     if (pd.reverse) tl[e] = -tl[e];
                                 }
                             break;
+                        case OP_DIAG:
+                            for (int k = op.a; k < op.a + op.b; ++k) {
+                                const DiagPair dp = P.diag_pairs[k];
+                                for (int e = 0; e < T; ++e)
+                                    if (bitval(dp.a, e) & bitval(dp.b, e)) {
+                                        tp[e] = -tp[e];
+                                        if (pd.reverse) tl[e] = -tl[e];
+                                    }
+                            }
+                            break;
                         case OP_CNOT: {
                             if (!in_group(op.b)) throw std::runtime_error("CNOT target outside group");
                             int bit = 1 << op.b;

@@ -235,6 +235,31 @@ __device__ __forceinline__ void cnot_dispatch(int rt, Cx<R> (&a)[kRegs], int rc,
     }
 }
 
+// 16-bit pattern of the registers j (tile bits [lo, lo+4)) on which an
+// operand's bit is 1: register bits give fixed patterns, thread bits and
+// tile-constant bits give all-or-nothing.
+__device__ __forceinline__ uint32_t operand_pattern(int o, int lo, uint32_t xt, uint32_t base)
+{
+    if (o >= kFixed) return ((base >> (o - kFixed)) & 1u) ? 0xFFFFu : 0u;
+    if (o >= lo && o < lo + kRegBits)
+        return (uint32_t)(0xFF00F0F0CCCCAAAAull >> (16 * (o - lo))) & 0xFFFFu;
+    return ((xt >> o) & 1u) ? 0xFFFFu : 0u;
+}
+
+__device__ __forceinline__ void flip_sign(Cx<float> &v, uint32_t bit)
+{
+    const uint32_t s = bit << 31;
+    v.x = __uint_as_float(__float_as_uint(v.x) ^ s);
+    v.y = __uint_as_float(__float_as_uint(v.y) ^ s);
+}
+
+__device__ __forceinline__ void flip_sign(Cx<double> &v, uint32_t bit)
+{
+    const unsigned long long s = (unsigned long long)bit << 63;
+    v.x = __longlong_as_double(__double_as_longlong(v.x) ^ (long long)s);
+    v.y = __longlong_as_double(__double_as_longlong(v.y) ^ (long long)s);
+}
+
 template <typename R>
 __device__ __forceinline__ R warp_sum(R v, int width, unsigned mask)
 {
@@ -244,7 +269,7 @@ __device__ __forceinline__ R warp_sum(R v, int width, unsigned mask)
 
 // Shared-memory layout of a pass CTA (offsets from a 1024-byte aligned base).
 struct Layout {
-    int phi, lam, mats, tabs, ufac, tmask, tcoef, tobs, ents, redE, redG, bar, total;
+    int phi, lam, mats, tabs, tmask, tcoef, tobs, ents, redE, redG, bar, total;
 };
 
 __host__ __device__ inline int align_up(int v, int a) { return (v + a - 1) / a * a; }
@@ -260,7 +285,6 @@ __host__ __device__ inline Layout make_layout(int K, int csize, bool rev, int ns
     o = align_up(o, 16);
     L.mats = o; o = align_up(o + 4 * csize * (nslots > 0 ? nslots : 1), 16);
     L.tabs = o; o = align_up(o + csize * 16 * ((sq + 3) / 4), 16);
-    L.ufac = o; o = align_up(o + csize * 2 * 32, 16);
     L.tmask = o; o = align_up(o + 4 * (n_terms > 0 ? n_terms : 1), 16);
     L.tcoef = o; o = align_up(o + rsize * (n_terms > 0 ? n_terms : 1), 16);
     L.tobs = o; o = align_up(o + 4 * (n_terms > 0 ? n_terms : 1), 16);
@@ -272,52 +296,72 @@ __host__ __device__ inline Layout make_layout(int K, int csize, bool rev, int ns
     return L;
 }
 
+// Fused matrix U = R_m ... R_1 of a run for sample b, in FP64 (row-major
+// u00, u01, u10, u11 as (re, im) pairs).  Rotation R_P(t) = cos(t/2) I - i sin(t/2) P.
 template <typename R>
-__device__ __forceinline__ R load_real(const void *p, int i) { return static_cast<const R *>(p)[i]; }
-
-template <typename R>
-__device__ __forceinline__ void sincos_r(R t, R *s, R *c);
-template <>
-__device__ __forceinline__ void sincos_r<float>(float t, float *s, float *c) { sincosf(t, s, c); }
-template <>
-__device__ __forceinline__ void sincos_r<double>(double t, double *s, double *c) { sincos(t, s, c); }
-
-// fused 2x2 matrix U = R_m ... R_1 of a run for sample b (row-major, 4 complex)
-template <typename R>
-__device__ void run_matrix(const PassArgs &a, int run, int b, Cx<R> *out, bool dagger)
+__device__ void run_matrix_f64(const Run rr, const Rot *rots, const R *xb, const R *w, double2 *U)
 {
-    const Run rr = a.runs[run];
-    Cx<R> u00{1, 0}, u01{0, 0}, u10{0, 0}, u11{1, 0};
-    const R *xb = static_cast<const R *>(a.x) + (size_t)b * a.n_in;
-    const R *w = static_cast<const R *>(a.w);
+    double2 u00{1, 0}, u01{0, 0}, u10{0, 0}, u11{1, 0};
+    auto mul = [](double2 a, double2 b) { return double2{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x}; };
+    auto add = [](double2 a, double2 b) { return double2{a.x + b.x, a.y + b.y}; };
     for (int i = rr.rot_begin; i < rr.rot_end; ++i) {
-        const Rot ro = a.rots[i];
-        R t = (R)ro.coef;
-        if (ro.w_idx >= 0) t *= w[ro.w_idx];
-        if (ro.x_idx >= 0) t *= xb[ro.x_idx];
-        R s, c;
-        sincos_r<R>((R)0.5 * t, &s, &c);
-        // rotation matrix g; new U = g * U
-        Cx<R> g00, g01, g10, g11;
+        const Rot ro = rots[i];
+        double t = ro.coef;
+        if (ro.w_idx >= 0) t *= (double)w[ro.w_idx];
+        if (ro.x_idx >= 0) t *= (double)xb[ro.x_idx];
+        double s, c;
+        sincos(0.5 * t, &s, &c);
+        double2 g00, g01, g10, g11;
         if (ro.kind == QTM_RX) { g00 = {c, 0}; g01 = {0, -s}; g10 = {0, -s}; g11 = {c, 0}; }
         else if (ro.kind == QTM_RY) { g00 = {c, 0}; g01 = {-s, 0}; g10 = {s, 0}; g11 = {c, 0}; }
         else { g00 = {c, -s}; g01 = {0, 0}; g10 = {0, 0}; g11 = {c, s}; }
-        Cx<R> n00 = cfma(g00, u00, cmul(g01, u10));
-        Cx<R> n01 = cfma(g00, u01, cmul(g01, u11));
-        Cx<R> n10 = cfma(g10, u00, cmul(g11, u10));
-        Cx<R> n11 = cfma(g10, u01, cmul(g11, u11));
+        const double2 n00 = add(mul(g00, u00), mul(g01, u10));
+        const double2 n01 = add(mul(g00, u01), mul(g01, u11));
+        const double2 n10 = add(mul(g10, u00), mul(g11, u10));
+        const double2 n11 = add(mul(g10, u01), mul(g11, u11));
         u00 = n00; u01 = n01; u10 = n10; u11 = n11;
     }
-    if (dagger) {
-        out[0] = {u00.x, -u00.y}; out[1] = {u10.x, -u10.y};
-        out[2] = {u01.x, -u01.y}; out[3] = {u11.x, -u11.y};
-    } else {
-        out[0] = u00; out[1] = u01; out[2] = u10; out[3] = u11;
+    U[0] = u00; U[1] = u01; U[2] = u10; U[3] = u11;
+}
+
+// One CTA per sample: every run's fused matrix, then the product-state tables
+// T_j[v] = prod_{k<4} u_{4j+k}[bit k of v] with u_q = U_prefix(q) |0>.
+template <typename R>
+__global__ void k_prep(const PrepArgs a)
+{
+    __shared__ double2 ufac[2 * 32];
+    const int b = blockIdx.x;
+    const R *xb = static_cast<const R *>(a.x) + (size_t)b * a.n_in;
+    const R *w = static_cast<const R *>(a.w);
+    Cx<R> *mats = static_cast<Cx<R> *>(a.mats) + (size_t)b * a.n_runs * 4;
+    for (int r = threadIdx.x; r < a.n_runs; r += blockDim.x) {
+        double2 U[4];
+        const Run rr = a.runs[r];
+        run_matrix_f64<R>(rr, a.rots, xb, w, U);
+        for (int k = 0; k < 4; ++k) mats[4 * r + k] = {(R)U[k].x, (R)U[k].y};
+        if (rr.prefix) { ufac[2 * rr.q] = U[0]; ufac[2 * rr.q + 1] = U[2]; }
+    }
+    for (int q = threadIdx.x; q < a.state_qubits; q += blockDim.x)
+        if (q >= a.n || a.prefix_run_of_q[q] < 0) { ufac[2 * q] = {1, 0}; ufac[2 * q + 1] = {0, 0}; }
+    __syncthreads();
+    const int ntab = (a.state_qubits + 3) >> 2;
+    Cx<R> *tabs = static_cast<Cx<R> *>(a.tabs) + (size_t)b * ntab * 16;
+    for (int i = threadIdx.x; i < ntab * 16; i += blockDim.x) {
+        const int j = i >> 4, v = i & 15;
+        double2 p{1, 0};
+        for (int k = 0; k < 4; ++k) {
+            const int q = 4 * j + k;
+            if (q < a.state_qubits) {
+                const double2 u = ufac[2 * q + ((v >> k) & 1)];
+                p = double2{p.x * u.x - p.y * u.y, p.x * u.y + p.y * u.x};
+            }
+        }
+        tabs[i] = {(R)p.x, (R)p.y};
     }
 }
 
 template <typename R, bool REV>
-__global__ void __launch_bounds__(256) k_pass(const __grid_constant__ PassArgs a,
+__global__ void __launch_bounds__(256, sizeof(R) == 8 ? 1 : (REV ? 2 : 3)) k_pass(const __grid_constant__ PassArgs a,
                                               const __grid_constant__ CUtensorMap tm_phi,
                                               const __grid_constant__ CUtensorMap tm_lam)
 {
@@ -346,7 +390,6 @@ __global__ void __launch_bounds__(256) k_pass(const __grid_constant__ PassArgs a
     Cx<R> *slam = reinterpret_cast<Cx<R> *>(smem + L.lam);
     Cx<R> *mats = reinterpret_cast<Cx<R> *>(smem + L.mats);
     Cx<R> *tabs = reinterpret_cast<Cx<R> *>(smem + L.tabs);
-    Cx<R> *ufac = reinterpret_cast<Cx<R> *>(smem + L.ufac);
     uint32_t *tmask = reinterpret_cast<uint32_t *>(smem + L.tmask);
     R *tcoef = reinterpret_cast<R *>(smem + L.tcoef);
     int32_t *tobs = reinterpret_cast<int32_t *>(smem + L.tobs);
@@ -377,8 +420,19 @@ __global__ void __launch_bounds__(256) k_pass(const __grid_constant__ PassArgs a
     // ---- per-CTA tables ----
     for (int i = tid; i < nwarps * (a.M > 0 ? a.M : 1); i += T) redE[i] = (R)0;
     for (int i = tid; i < nwarps * 3 * (a.nslots > 0 ? a.nslots : 1); i += T) redG[i] = (R)0;
-    for (int s = tid; s < a.nslots; s += T)
-        run_matrix<R>(a, a.slot_runs[a.slot_begin + s], b, mats + 4 * s, REV);
+    {
+        const Cx<R> *gm = static_cast<const Cx<R> *>(a.mats) + (size_t)b * a.n_runs * 4;
+        for (int i = tid; i < 4 * a.nslots; i += T) {
+            const int s = i >> 2, k = i & 3;
+            const int run = a.slot_runs[a.slot_begin + s];
+            if (REV) {   // U^dagger: (k = 2r + c) <- conj(U[c][r])
+                const Cx<R> u = gm[4 * run + ((k & 1) << 1 | (k >> 1))];
+                mats[i] = {u.x, -u.y};
+            } else {
+                mats[i] = gm[4 * run + k];
+            }
+        }
+    }
     const uint64_t Smask = ((1ull << l) - 1ull) | (m ? (((1ull << m) - 1ull) << h) : 0ull);
     for (int t = tid; t < a.n_terms; t += T) {
         const Term tm = a.terms[t];
@@ -395,29 +449,13 @@ __global__ void __launch_bounds__(256) k_pass(const __grid_constant__ PassArgs a
     const bool analytic = a.phi_src == SRC_ANALYTIC;
     if (analytic) {
         for (int k = tid; k < a.analytic_ents; k += T) sents[k] = a.prefix_ents[k];
-        for (int q = tid; q < a.state_qubits; q += T) {
-            Cx<R> u0{1, 0}, u1{0, 0};
-            if (q < a.n && a.prefix_run_of_q[q] >= 0) {
-                Cx<R> U[4];
-                run_matrix<R>(a, a.prefix_run_of_q[q], b, U, false);
-                u0 = U[0]; u1 = U[2];
-            }
-            ufac[2 * q] = u0; ufac[2 * q + 1] = u1;
-        }
+        const int ntab = (a.state_qubits + 3) >> 2;
+        const Cx<R> *gt = static_cast<const Cx<R> *>(a.tabs) + (size_t)b * ntab * 16;
+        for (int i = tid; i < ntab * 16; i += T) tabs[i] = gt[i];
     }
     __syncthreads();
     if (analytic) {
         const int ntab = (a.state_qubits + 3) >> 2;
-        for (int i = tid; i < ntab * 16; i += T) {
-            const int j = i >> 4, v = i & 15;
-            Cx<R> p{1, 0};
-            for (int k = 0; k < 4; ++k) {
-                const int q = 4 * j + k;
-                if (q < a.state_qubits) p = cmul(p, ufac[2 * q + ((v >> k) & 1)]);
-            }
-            tabs[i] = p;
-        }
-        __syncthreads();
         const int E = 1 << K;
         for (int e = tid; e < E; e += T) {
             uint32_t y = base | ((uint32_t)e & ((1u << l) - 1u)) | (((uint32_t)e >> l) << h);
@@ -477,10 +515,27 @@ __global__ void __launch_bounds__(256) k_pass(const __grid_constant__ PassArgs a
                 if (REV && lam_valid) q[j] = slam[s];
             }
         }
-        // ops
+        // ops (the next op record is fetched while this one executes)
+        DevOp nxt = a.ops[ph.op_begin < ph.op_end ? ph.op_begin : 0];
         for (int o = ph.op_begin; o < ph.op_end; ++o) {
-            const DevOp op = a.ops[o];
+            const DevOp op = nxt;
+            if (o + 1 < ph.op_end) nxt = a.ops[o + 1];
             switch (op.type) {
+            case OP_DIAG: {
+                uint32_t msk = 0;
+#pragma unroll 4
+                for (int k = op.a; k < op.a + op.b; ++k) {
+                    const DiagPair dp = a.diag[k];
+                    msk ^= operand_pattern(dp.a, lo, xt, base) & operand_pattern(dp.b, lo, xt, base);
+                }
+#pragma unroll
+                for (int j = 0; j < kRegs; ++j) {
+                    const uint32_t bit = (msk >> j) & 1u;
+                    flip_sign(p[j], bit);
+                    if (REV) flip_sign(q[j], bit);
+                }
+                break;
+            }
             case OP_U2:
                 u2_dispatch<R>(op.a - lo, p, mats + 4 * op.slot);
                 break;
@@ -737,6 +792,13 @@ cudaError_t launch_pass(int dtype, bool reverse, const PassArgs &a, const CUtens
         if (reverse) QTM_LAUNCH(float, true); else QTM_LAUNCH(float, false);
     }
 #undef QTM_LAUNCH
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prep(int dtype, const PrepArgs &a, cudaStream_t s)
+{
+    if (dtype == QTM_C128) k_prep<double><<<a.B, 128, 0, s>>>(a);
+    else k_prep<float><<<a.B, 128, 0, s>>>(a);
     return cudaGetLastError();
 }
 

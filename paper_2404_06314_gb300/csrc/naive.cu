@@ -38,10 +38,12 @@ __global__ void k_halfangles(const Rot *rots, int n_rots, const R *x, const R *w
     if (i >= B * n_rots) return;
     const int b = i / n_rots, r = i % n_rots;
     const Rot ro = rots[r];
-    R t = (R)ro.coef;
-    if (ro.w_idx >= 0) t *= w[ro.w_idx];
-    if (ro.x_idx >= 0) t *= x[(size_t)b * n_in + ro.x_idx];
-    cs[i] = {cos((R)0.5 * t), sin((R)0.5 * t)};
+    double t = ro.coef;
+    if (ro.w_idx >= 0) t *= (double)w[ro.w_idx];
+    if (ro.x_idx >= 0) t *= (double)x[(size_t)b * n_in + ro.x_idx];
+    double s, c;
+    sincos(0.5 * t, &s, &c);   // FP64, rounded once: cos^2 + sin^2 stays unbiased
+    cs[i] = {(R)c, (R)s};
 }
 
 // one rotation (or its adjoint) on qubit q, applied to s1 and (optionally) s2

@@ -552,6 +552,31 @@ qtm_status make_plan(int n, const qtm_gate *gates, int n_gates, const qtm_zterm 
             if (p2.op_begin >= at) { p2.op_begin++; p2.op_end++; }
         }
     }
+    // ---- merge runs of consecutive CZ ops inside a phase into one DIAG op -----
+    {
+        std::vector<DevOp> ops;
+        ops.reserve(P.ops.size());
+        for (auto &ph : P.phases) {
+            const int nb = (int)ops.size();
+            for (int o = ph.op_begin; o < ph.op_end;) {
+                if (P.ops[o].type != OP_CZ) { ops.push_back(P.ops[o]); ++o; continue; }
+                DevOp d{};
+                d.type = OP_DIAG;
+                d.a = (int16_t)P.diag_pairs.size();
+                d.slot = -1;
+                while (o < ph.op_end && P.ops[o].type == OP_CZ) {
+                    P.diag_pairs.push_back({P.ops[o].a, P.ops[o].b});
+                    ++o;
+                }
+                d.b = (int16_t)(P.diag_pairs.size() - d.a);
+                ops.push_back(d);
+            }
+            ph.op_begin = nb;
+            ph.op_end = (int)ops.size();
+        }
+        P.ops.swap(ops);
+        if (P.diag_pairs.size() > 32000) { err = "too many CZ gates"; return QTM_EUNSUPPORTED; }
+    }
     for (auto *v : {&P.fwd, &P.rev})
         for (auto &pd : *v) {
             P.max_slots = std::max(P.max_slots, pd.slot_end - pd.slot_begin);
@@ -587,6 +612,7 @@ void plan_costs(const Plan &p, double &fwd_bytes, double &adj_bytes, double &fwd
                 case OP_U2: f += 14.0 * N; break;                       // 2x2 complex on N/2 pairs
                 case OP_GRAD: f += 12.0 * N + ((op.flags & OPF_SKIP_APPLY) ? 0.0 : 28.0 * N); break;
                 case OP_EXPVAL: f += (3.0 + T) * N; break;
+                case OP_DIAG: break;
                 case OP_COSTATE: f += (T + 2.0) * N; break;
                 default: break;
                 }
@@ -622,10 +648,16 @@ std::string Plan::describe() const
                 s << "{lo" << phases[ph].lo << ":";
                 for (int o = phases[ph].op_begin; o < phases[ph].op_end; ++o) {
                     const DevOp &op = ops[o];
-                    const char *nm[] = {"?", "U", "G", "CZ", "CX", "E", "C"};
+                    const char *nm[] = {"?", "U", "G", "CZ", "CX", "E", "C", "D"};
                     s << " " << nm[op.type];
                     if (op.type <= OP_CNOT) s << op.a;
                     if (op.type == OP_CZ || op.type == OP_CNOT) s << "," << op.b;
+                    if (op.type == OP_DIAG) {
+                        s << "[";
+                        for (int k = op.a; k < op.a + op.b; ++k)
+                            s << (k > op.a ? " " : "") << diag_pairs[k].a << "," << diag_pairs[k].b;
+                        s << "]";
+                    }
                     if (op.type == OP_GRAD && (op.flags & OPF_SKIP_APPLY)) s << "s";
                 }
                 s << "}";

@@ -32,6 +32,7 @@ enum OpType : int32_t {
     OP_CNOT = 4,     // a = control operand, b = target (local bit)
     OP_EXPVAL = 5,   // accumulate <O_m> partials
     OP_COSTATE = 6,  // lam = (sum_m gE_m O_m) phi
+    OP_DIAG = 7,     // product of CZ gates (diag_pairs[a .. a+b)): one sign mask
 };
 constexpr int32_t OPF_SKIP_APPLY = 1;   // GRAD: no later op touches this qubit
 
@@ -40,14 +41,18 @@ constexpr int32_t OPF_SKIP_APPLY = 1;   // GRAD: no later op touches this qubit
 constexpr int32_t kFixed = 32;
 
 struct DevOp {
-    int32_t type;
-    int32_t a;
-    int32_t b;
+    int16_t type;
+    int16_t flags;
+    int16_t a;
+    int16_t b;
     int32_t slot;   // pass-local run slot (U2 / GRAD)
-    int32_t flags;
-    int32_t pad[3];
+    int32_t pad;
 };
-static_assert(sizeof(DevOp) == 32, "DevOp layout");
+static_assert(sizeof(DevOp) == 16, "DevOp layout");
+
+struct DiagPair {   // one CZ of a DIAG op (operand encoding as DevOp::a/b)
+    int16_t a, b;
+};
 
 struct DevPhase {
     int32_t lo;        // register group: tile-local bits [lo, lo + 4)
@@ -120,6 +125,7 @@ struct Plan {
     std::vector<PassDesc> fwd, rev;
     std::vector<DevPhase> phases;
     std::vector<DevOp> ops;
+    std::vector<DiagPair> diag_pairs;
     std::vector<int32_t> slot_runs;
 
     int max_slots = 0;         // max run slots of any pass

@@ -158,6 +158,34 @@ qtm_status qtm_adjoint(qtm_plan *plan, int B, const void *grad_expvals, const vo
 qtm_status qtm_jacobian(qtm_plan *plan, int B, const void *x, const void *w, void *jac,
                         void *stream);
 
+/* Size of the device array behind qtm_forward_noalloc (bytes, per GPU). */
+#define QTM_NOALLOC_SCRATCH_BYTES (8u << 20)
+
+/*
+ * qtm_forward_noalloc: the expectation values of qtm_forward, without any
+ * device allocation.  The paper has no counterpart; this exists for callers
+ * that cannot call cudaMalloc: code running while a stream is captured into a
+ * CUDA graph (allocation is not capturable and may synchronise the device),
+ * programs whose GPU memory is owned by another allocator with a fixed budget,
+ * and latency-critical loops that must not stall on a first-call allocation.
+ *
+ * Instead of plan-owned buffers it uses one file-scope device array of
+ * QTM_NOALLOC_SCRATCH_BYTES (8 MiB) that the library keeps on every GPU it is
+ * loaded on until the process exits.  Arguments are those of qtm_forward
+ * (device pointers, plan real type).  Supported for fused plans whose state
+ * fits one shared-memory tile (n <= 12): otherwise QTM_EUNSUPPORTED.  A batch
+ * whose tables and scratch exceed the array returns QTM_EINVAL before any
+ * work is enqueued (about 2.8 MB for 12 qubits, 6 layers, B = 1024).
+ *
+ * The first call on each device resolves the array's device address there
+ * (cudaGetSymbolAddress), so make that first call before any stream capture.
+ * Every call shares the array: calls that overlap on the GPU (different
+ * streams, or different plans at the same time) race and must be serialised
+ * by the caller.  It stores no state for qtm_adjoint.
+ */
+qtm_status qtm_forward_noalloc(qtm_plan *plan, int B, const void *x, const void *w,
+                               void *expvals, void *stream);
+
 /* Per-launch timing (profiling aid).  enable != 0: every later qtm_forward /
  * qtm_adjoint records a pair of CUDA events around each of its kernel
  * launches, on the call's stream.  enable == 0 stops recording. */

@@ -71,10 +71,11 @@ def lib(build_if_missing: bool = True):
         L.qtm_forward.argtypes = [vp, i, vp, vp, vp, vp]
         L.qtm_adjoint.argtypes = [vp, i, vp, vp, vp, vp, vp, i, vp]
         L.qtm_jacobian.argtypes = [vp, i, vp, vp, vp, vp]
+        L.qtm_forward_noalloc.argtypes = [vp, i, vp, vp, vp, vp]
         L.qtm_sync.argtypes = [vp, vp]
         L.qtm_get_plan_info.argtypes = [vp, P(qtm_plan_info)]
         L.qtm_destroy.argtypes = [vp]
-        for f in ("qtm_build", "qtm_forward", "qtm_adjoint", "qtm_jacobian", "qtm_sync",
+        for f in ("qtm_build", "qtm_forward", "qtm_forward_noalloc", "qtm_adjoint", "qtm_jacobian", "qtm_sync",
                   "qtm_get_plan_info", "qtm_destroy", "qtm_debug_emulate"):
             getattr(L, f).restype = ctypes.c_int
         L.qtm_status_str.argtypes = [i]
@@ -118,6 +119,10 @@ def qtm_build(n_qubits, gates, terms, n_obs, n_weights, n_inputs, dtype=QTM_C64,
 
 def qtm_forward(plan, B, x, w, expvals, stream=0):
     return lib().qtm_forward(plan, int(B), x, w, expvals, stream)
+
+
+def qtm_forward_noalloc(plan, B, x, w, expvals, stream=0):
+    return lib().qtm_forward_noalloc(plan, int(B), x, w, expvals, stream)
 
 
 def qtm_adjoint(plan, B, grad_expvals, x, w, grad_x, grad_w, flags=0, stream=0):

@@ -409,6 +409,8 @@ NaiveArgs naive_args(qtm_plan *p, int B, const void *x, const void *w, const voi
 
 }  // namespace
 
+const qtm::Plan *qtm_internal_plan(const qtm_plan *plan) { return &plan->P; }
+
 extern "C" {
 
 const char *qtm_status_str(int st)

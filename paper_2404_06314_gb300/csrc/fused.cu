@@ -748,14 +748,22 @@ __global__ void k_grad_finalize(const FinalizeArgs f)
         }
 }
 
+// grad_w[j] = sum_b gw_ws[b][j]: one CTA per weight, each thread a fixed
+// strided subset of samples, then a fixed-shape tree: deterministic.
 template <typename R>
 __global__ void k_gw_reduce(const double *gw_ws, int B, int P, R *gw)
 {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= P) return;
+    __shared__ double red[256];
+    const int j = blockIdx.x;
     double s = 0.0;
-    for (int b = 0; b < B; ++b) s += gw_ws[(size_t)b * P + j];
-    gw[j] = (R)s;
+    for (int b = threadIdx.x; b < B; b += blockDim.x) s += gw_ws[(size_t)b * P + j];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x >> 1; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) gw[j] = (R)red[0];
 }
 
 }  // namespace
@@ -823,9 +831,8 @@ cudaError_t launch_grad_finalize(int dtype, const FinalizeArgs &f, cudaStream_t 
 cudaError_t launch_gw_reduce(int dtype, const double *gw_ws, int B, int P, void *gw, cudaStream_t s)
 {
     if (P <= 0) return cudaSuccess;
-    const int blk = 128, grd = (P + blk - 1) / blk;
-    if (dtype == QTM_C128) k_gw_reduce<double><<<grd, blk, 0, s>>>(gw_ws, B, P, static_cast<double *>(gw));
-    else k_gw_reduce<float><<<grd, blk, 0, s>>>(gw_ws, B, P, static_cast<float *>(gw));
+    if (dtype == QTM_C128) k_gw_reduce<double><<<P, 256, 0, s>>>(gw_ws, B, P, static_cast<double *>(gw));
+    else k_gw_reduce<float><<<P, 256, 0, s>>>(gw_ws, B, P, static_cast<float *>(gw));
     return cudaGetLastError();
 }
 

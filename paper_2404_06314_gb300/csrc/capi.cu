@@ -38,6 +38,7 @@ struct qtm_plan {
     // device tables
     DevOp *d_ops = nullptr;
     DiagPair *d_diag = nullptr;
+    MaskTerm *d_amap = nullptr;
     DevPhase *d_phases = nullptr;
     int32_t *d_slot_runs = nullptr;
     Run *d_runs = nullptr;
@@ -98,12 +99,12 @@ cudaError_t upload(T **dst, const std::vector<T> &v)
 
 void free_tables(qtm_plan *p)
 {
-    void *ptrs[] = {p->d_ops, p->d_diag, p->d_phases, p->d_slot_runs, p->d_runs, p->d_rots,
+    void *ptrs[] = {p->d_ops, p->d_diag, p->d_amap, p->d_phases, p->d_slot_runs, p->d_runs, p->d_rots,
                     p->d_prefix_run_of_q, p->d_prefix_ents, p->d_terms, p->d_w_ptr,
                     p->d_w_rots, p->d_x_ptr, p->d_x_rots, p->d_status};
     for (void *q : ptrs)
         if (q) cudaFree(q);
-    p->d_ops = nullptr; p->d_diag = nullptr; p->d_phases = nullptr; p->d_slot_runs = nullptr; p->d_runs = nullptr;
+    p->d_ops = nullptr; p->d_diag = nullptr; p->d_amap = nullptr; p->d_phases = nullptr; p->d_slot_runs = nullptr; p->d_runs = nullptr;
     p->d_rots = nullptr; p->d_prefix_run_of_q = nullptr; p->d_prefix_ents = nullptr;
     p->d_terms = nullptr; p->d_w_ptr = p->d_w_rots = p->d_x_ptr = p->d_x_rots = nullptr;
     p->d_status = nullptr;
@@ -211,6 +212,7 @@ qtm_status ensure_device(qtm_plan *p)
     } while (0)
     UP(p->d_ops, P.ops);
     UP(p->d_diag, P.diag_pairs);
+    UP(p->d_amap, P.amap_terms);
     UP(p->d_phases, P.phases);
     UP(p->d_slot_runs, P.slot_runs);
     UP(p->d_runs, P.runs);
@@ -344,6 +346,9 @@ PassArgs pass_args(qtm_plan *p, const PassDesc &pd, const TmGeom &g, size_t smem
     a.mats = p->d_mats; a.tabs = p->d_tabs;
     a.prefix_ents = p->d_prefix_ents;
     a.analytic_ents = pd.phi_src == SRC_ANALYTIC ? pd.analytic_ents : 0;
+    a.amap = p->d_amap + (pd.amap_lin >= 0 ? pd.amap_begin : 0);
+    a.amap_lin = pd.phi_src == SRC_ANALYTIC ? pd.amap_lin : -1;
+    a.amap_quad = pd.amap_quad; a.amap_dlin = pd.amap_dlin;
     a.phi_src = pd.phi_src; a.lam_src = pd.lam_src;
     a.store_phi = pd.store_phi; a.store_lam = pd.store_lam; a.has_expval = pd.has_expval;
     a.terms = p->d_terms; a.n_terms = (int)P.terms.size(); a.M = P.n_obs;

@@ -32,6 +32,9 @@ struct PassArgs {
     // analytic init
     const Ent *prefix_ents;
     int analytic_ents;
+    const MaskTerm *amap;         // closed form of the analytic state (amap_lin >= 0)
+    int amap_lin, amap_quad;
+    uint32_t amap_dlin;
     // sources / sinks
     int phi_src, lam_src, store_phi, store_lam, has_expval;
     // observables

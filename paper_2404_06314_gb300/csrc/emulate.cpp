@@ -100,14 +100,29 @@ struct Emu {
 
     // analytic prefix state at global index y, with the first `ents` folded
     // entanglers applied
-    cd analytic(int b, uint64_t y, int ents, const std::vector<cd> &u) const
+    cd analytic(const PassDesc &pd, uint64_t y, const std::vector<cd> &u) const
     {
         uint64_t xx = y;
         int sign = 0;
-        for (int k = ents - 1; k >= 0; --k) {
-            const Ent &e = P.prefix_ents[k];
-            if (e.kind == QTM_CNOT) xx ^= ((xx >> e.a) & 1ull) << e.b;
-            else sign ^= (int)((xx >> e.a) & (xx >> e.b) & 1ull);
+        if (pd.amap_lin >= 0) {   // closed form, exactly as the kernel evaluates it
+            uint32_t yy = (uint32_t)y, x32 = 0;
+            for (int k = 0; k < pd.amap_lin; ++k) {
+                const MaskTerm t = P.amap_terms[pd.amap_begin + k];
+                x32 ^= (t.d >= 0 ? (yy >> t.d) : (yy << -t.d)) & t.mask;
+            }
+            int par = __builtin_popcount(x32 & pd.amap_dlin);
+            for (int k = 0; k < pd.amap_quad; ++k) {
+                const MaskTerm t = P.amap_terms[pd.amap_begin + pd.amap_lin + k];
+                par += __builtin_popcount(x32 & (x32 >> t.d) & t.mask);
+            }
+            xx = x32;
+            sign = par & 1;
+        } else {
+            for (int k = pd.analytic_ents - 1; k >= 0; --k) {
+                const Ent &e = P.prefix_ents[k];
+                if (e.kind == QTM_CNOT) xx ^= ((xx >> e.a) & 1ull) << e.b;
+                else sign ^= (int)((xx >> e.a) & (xx >> e.b) & 1ull);
+            }
         }
         cd a = 1.0;
         for (int q = 0; q < P.state_qubits; ++q) a *= u[2 * q + ((xx >> q) & 1)];
@@ -148,7 +163,7 @@ struct Emu {
                 cd *ph = &phi[(size_t)b * NS], *la = &lam[(size_t)b * NS];
                 for (int e = 0; e < T; ++e) {
                     uint64_t y = gidx(e);
-                    tp[e] = pd.phi_src == SRC_ANALYTIC ? analytic(b, y, pd.analytic_ents, u) : ph[y];
+                    tp[e] = pd.phi_src == SRC_ANALYTIC ? analytic(pd, y, u) : ph[y];
                     if (pd.lam_src == SRC_LOAD) tl[e] = la[y];
                 }
                 auto bitval = [&](int operand, int e) -> int {

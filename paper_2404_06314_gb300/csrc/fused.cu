@@ -457,14 +457,35 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 1 : (REV ? 2 : 3)) k_pas
     if (analytic) {
         const int ntab = (a.state_qubits + 3) >> 2;
         const int E = 1 << K;
+        int td[kMaxMaskTerms];
+        uint32_t tmk[kMaxMaskTerms];
+        const int nl = a.amap_lin, nt = a.amap_lin + a.amap_quad;
+#pragma unroll
+        for (int k = 0; k < kMaxMaskTerms; ++k) {
+            const MaskTerm t = k < nt ? a.amap[k] : MaskTerm{0, 0u};
+            td[k] = t.d;
+            tmk[k] = t.mask;
+        }
         for (int e = tid; e < E; e += T) {
             uint32_t y = base | ((uint32_t)e & ((1u << l) - 1u)) | (((uint32_t)e >> l) << h);
             uint32_t xx = y;
             int sign = 0;
-            for (int k = a.analytic_ents - 1; k >= 0; --k) {
-                const Ent en = sents[k];
-                if (en.kind == QTM_CNOT) xx ^= ((xx >> en.a) & 1u) << en.b;
-                else sign ^= (int)((xx >> en.a) & (xx >> en.b) & 1u);
+            if (nl >= 0) {   // closed form: x = A^{-1} y, sign from the quadratic form
+                xx = 0;
+#pragma unroll
+                for (int k = 0; k < kMaxMaskTerms; ++k)
+                    if (k < nl) xx ^= (td[k] >= 0 ? (y >> td[k]) : (y << -td[k])) & tmk[k];
+                int par = __popc(xx & a.amap_dlin);
+#pragma unroll
+                for (int k = 0; k < kMaxMaskTerms; ++k)
+                    if (k >= nl && k < nt) par += __popc(xx & (xx >> td[k]) & tmk[k]);
+                sign = par & 1;
+            } else {
+                for (int k = a.analytic_ents - 1; k >= 0; --k) {
+                    const Ent en = sents[k];
+                    if (en.kind == QTM_CNOT) xx ^= ((xx >> en.a) & 1u) << en.b;
+                    else sign ^= (int)((xx >> en.a) & (xx >> en.b) & 1u);
+                }
             }
             Cx<R> amp = tabs[xx & 15u];
             for (int j = 1; j < ntab; ++j) amp = cmul(amp, tabs[16 * j + ((xx >> (4 * j)) & 15u)]);

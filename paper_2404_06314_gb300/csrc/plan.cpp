@@ -268,6 +268,65 @@ struct Builder {
     }
 };
 
+// Closed form of the first `e` folded entanglers acting on basis states:
+// y = A x, phase (-1)^{x^T Q x + D.x}.  Returns false if the mask form would
+// cost more bit operations per amplitude than undoing the gates one by one.
+bool closed_form(const std::vector<Ent> &ents, int e, int n, std::vector<MaskTerm> &terms,
+                 int &n_lin, int &n_quad, uint32_t &dlin)
+{
+    std::vector<uint32_t> row(n);
+    for (int i = 0; i < n; ++i) row[i] = 1u << i;
+    std::vector<uint32_t> Q(n, 0u);   // Q[i] bit j (j > i): x_i x_j term
+    uint32_t D = 0;
+    for (int k = 0; k < e; ++k) {
+        const Ent &g = ents[k];
+        if (g.kind == QTM_CNOT) {
+            row[g.b] ^= row[g.a];
+        } else {
+            const uint32_t ra = row[g.a], rb = row[g.b];
+            D ^= ra & rb;
+            for (int i = 0; i < n; ++i)
+                for (int j = i + 1; j < n; ++j) {
+                    const uint32_t t = (((ra >> i) & (rb >> j)) ^ ((ra >> j) & (rb >> i))) & 1u;
+                    Q[i] ^= t << j;
+                }
+        }
+    }
+    // invert A (rows) over GF(2): augmented 64-bit rows [A | I]
+    std::vector<uint64_t> aug(n);
+    for (int i = 0; i < n; ++i) aug[i] = (uint64_t)row[i] | ((uint64_t)1 << (32 + i));
+    for (int col = 0; col < n; ++col) {
+        int piv = -1;
+        for (int r = col; r < n; ++r)
+            if ((aug[r] >> col) & 1) { piv = r; break; }
+        if (piv < 0) return false;   // cannot happen: CNOT products are invertible
+        std::swap(aug[col], aug[piv]);
+        for (int r = 0; r < n; ++r)
+            if (r != col && ((aug[r] >> col) & 1)) aug[r] ^= aug[col];
+    }
+    // A^{-1}[i][j] = bit (32 + j) of aug[i]
+    terms.clear();
+    n_lin = 0;
+    for (int d = -(n - 1); d <= n - 1; ++d) {
+        uint32_t m = 0;
+        for (int i = 0; i < n; ++i) {
+            const int j = i + d;
+            if (j < 0 || j >= n) continue;
+            if ((aug[i] >> (32 + j)) & 1) m |= 1u << i;
+        }
+        if (m) { terms.push_back({d, m}); ++n_lin; }
+    }
+    n_quad = 0;
+    for (int d = 1; d <= n - 1; ++d) {
+        uint32_t m = 0;
+        for (int i = 0; i + d < n; ++i)
+            if ((Q[i] >> (i + d)) & 1) m |= 1u << i;
+        if (m) { terms.push_back({d, m}); ++n_quad; }
+    }
+    dlin = D;
+    return n_lin + n_quad <= kMaxMaskTerms && 3 * (n_lin + n_quad) + 2 <= 4 * e;
+}
+
 }  // namespace
 
 qtm_status make_plan(int n, const qtm_gate *gates, int n_gates, const qtm_zterm *terms,
@@ -552,6 +611,25 @@ qtm_status make_plan(int n, const qtm_gate *gates, int n_gates, const qtm_zterm 
             if (p2.op_begin >= at) { p2.op_begin++; p2.op_end++; }
         }
     }
+    // ---- closed forms of the analytic states ---------------------------------
+    for (auto *v : {&P.fwd, &P.rev})
+        for (auto &pd : *v) {
+            pd.amap_lin = -1;
+            pd.amap_quad = 0;
+            pd.amap_begin = 0;
+            pd.amap_dlin = 0;
+            if (pd.phi_src != SRC_ANALYTIC || pd.analytic_ents == 0) continue;
+            std::vector<MaskTerm> t;
+            int nl, nq;
+            uint32_t dl;
+            if (!closed_form(P.prefix_ents, pd.analytic_ents, P.n, t, nl, nq, dl)) continue;
+            pd.amap_begin = (int)P.amap_terms.size();
+            pd.amap_lin = nl;
+            pd.amap_quad = nq;
+            pd.amap_dlin = dl;
+            P.amap_terms.insert(P.amap_terms.end(), t.begin(), t.end());
+        }
+
     // ---- merge runs of consecutive CZ ops inside a phase into one DIAG op -----
     {
         std::vector<DevOp> ops;
@@ -642,7 +720,9 @@ std::string Plan::describe() const
             const PassDesc &pd = v[i];
             s << name << "[" << i << "] S=[0," << pd.l << ")";
             if (pd.m) s << "+[" << pd.h << "," << pd.h + pd.m << ")";
-            s << " phi=" << pd.phi_src << " lam=" << pd.lam_src << " ents=" << pd.analytic_ents
+            s << " phi=" << pd.phi_src << " lam=" << pd.lam_src << " ents=" << pd.analytic_ents;
+            if (pd.phi_src == SRC_ANALYTIC) s << " closed=" << pd.amap_lin << "/" << pd.amap_quad;
+            s
               << " store=" << pd.store_phi << pd.store_lam << " phases=";
             for (int ph = pd.phase_begin; ph < pd.phase_end; ++ph) {
                 s << "{lo" << phases[ph].lo << ":";

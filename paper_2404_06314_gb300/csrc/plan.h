@@ -24,6 +24,7 @@ constexpr int kMaxTileQubits = 12;   // complex64 tiles (32 KiB)
 constexpr int kMaxTileQubits128 = 11;
 constexpr int kMaxQubits = 30;
 constexpr int kMaxRunLen = 32;       // rotations fused into one 2x2
+constexpr int kMaxMaskTerms = 8;     // closed-form analytic state: max mask terms
 
 enum OpType : int32_t {
     OP_U2 = 1,       // apply fused run matrix (forward)                 a = local bit, slot
@@ -54,6 +55,15 @@ struct DiagPair {   // one CZ of a DIAG op (operand encoding as DevOp::a/b)
     int16_t a, b;
 };
 
+// Analytic prefix state in closed form: with x = A^{-1} y evaluated as
+// XOR over linear terms (d, m) of shift(y, d) & m (shift right by d >= 0, left
+// by -d), the folded CZ/CNOT prefix contributes the sign
+// (-1)^{popcount(x & dlin) + sum over quadratic terms (d, m) of popcount(x & (x >> d) & m)}.
+struct MaskTerm {
+    int32_t d;
+    uint32_t mask;
+};
+
 struct DevPhase {
     int32_t lo;        // register group: tile-local bits [lo, lo + 4)
     int32_t op_begin;  // into the plan's op array
@@ -73,6 +83,9 @@ struct PassDesc {
     int32_t slot_begin, slot_end;   // pass-local run slots -> run ids (plan.slot_runs)
     int32_t has_expval, has_grad;
     int32_t reverse;
+    // closed form of the analytic phi (used when amap_lin >= 0)
+    int32_t amap_begin, amap_lin, amap_quad;   // terms [begin, begin+lin) linear, then quad
+    uint32_t amap_dlin;
 };
 
 // A run: consecutive rotations on one qubit (forward order).
@@ -126,6 +139,7 @@ struct Plan {
     std::vector<DevPhase> phases;
     std::vector<DevOp> ops;
     std::vector<DiagPair> diag_pairs;
+    std::vector<MaskTerm> amap_terms;
     std::vector<int32_t> slot_runs;
 
     int max_slots = 0;         // max run slots of any pass

@@ -199,6 +199,78 @@ qtm_status qtm_set_profiling(qtm_plan *plan, int enable);
 qtm_status qtm_get_launch_times(qtm_plan *plan, int which, float *ms, int *kinds, int cap,
                                 int *count);
 
+/* ------------------------------------------------------------------------
+ * Uneven batches: many circuits of different qubit counts and depths, each
+ * with `batch` samples, evaluated (forward + adjoint) in ONE persistent kernel
+ * launch, optionally replayed from a captured CUDA graph.  Sec. II-B's batch
+ * parallelism extended across circuits.
+ * ------------------------------------------------------------------------ */
+
+/* One circuit of an uneven batch (host arrays, copied by qtm_build_multi). */
+typedef struct {
+    int32_t n_qubits;
+    int32_t n_gates;
+    const qtm_gate *gates;
+    int32_t n_terms;
+    int32_t n_obs;
+    const qtm_zterm *terms;
+    int32_t n_weights;
+    int32_t n_inputs;
+} qtm_circuit;
+
+typedef struct qtm_multi qtm_multi;
+
+/* Packed buffers of qtm_multi_run: circuit c's block starts at element
+ * offsets[c] (from qtm_multi_offsets) of the buffer named by `which`:
+ *   QTM_MULTI_X  x       [batch][n_inputs_c]    QTM_MULTI_W  w    [n_weights_c]
+ *   QTM_MULTI_GE cotangents [batch][n_obs_c]    QTM_MULTI_E  E    [batch][n_obs_c]
+ *   QTM_MULTI_GX grad_x  [batch][n_inputs_c]    QTM_MULTI_GW grad_w [n_weights_c] (batch sum) */
+#define QTM_MULTI_X 0
+#define QTM_MULTI_W 1
+#define QTM_MULTI_GE 2
+#define QTM_MULTI_E 3
+#define QTM_MULTI_GX 4
+#define QTM_MULTI_GW 5
+
+/* Launch configuration chosen by qtm_multi_tune (or set by hand). */
+typedef struct {
+    int32_t ctas_per_sm;   /* persistent grid = ctas_per_sm x SM count (capped by the work) */
+    int32_t order;         /* 0: costliest (circuit, sample) items first; 1: as given */
+    int32_t fuse_width;    /* most rotations fused into one run (1 .. 32) */
+    int32_t reserved;
+} qtm_multi_config;
+
+/* Build plans for n_circuits circuits (validated as in qtm_build), batch >= 1
+ * samples each.  Host-only until the first run. */
+qtm_status qtm_build_multi(const qtm_circuit *circuits, int n_circuits, int batch, int dtype,
+                           qtm_multi **out);
+
+/* Element offsets of every circuit's block in a packed buffer: offsets[0..n_circuits],
+ * offsets[n_circuits] = total elements. */
+qtm_status qtm_multi_offsets(const qtm_multi *multi, int which, int64_t *offsets);
+
+/* Forward + adjoint of every (circuit, sample) in one persistent launch: a
+ * device work counter hands (circuit, sample) items to CTAs; circuits with
+ * n <= 12 run both directions in shared memory, larger ones sweep tiles of
+ * their own states (no inter-CTA waits).  Device pointers, plan real type.
+ * flags: QTM_MULTI_GRAPH replays a CUDA graph captured on first use for
+ * these buffers (re-captured when a pointer changes). */
+#define QTM_MULTI_GRAPH 1
+qtm_status qtm_multi_run(qtm_multi *multi, const void *x, const void *w, const void *grad_expvals,
+                         void *expvals, void *grad_x, void *grad_w, int flags, void *stream);
+
+/* Autotune the launch configuration on these buffers: time each candidate
+ * (CTAs per SM x item order x fusion width) with CUDA events and keep the
+ * fastest.  cache_path (or NULL): a JSON file of earlier choices keyed by the
+ * batch's signature and the device name; a hit skips the timing. */
+qtm_status qtm_multi_tune(qtm_multi *multi, const void *x, const void *w, const void *grad_expvals,
+                          void *expvals, void *grad_x, void *grad_w, void *stream,
+                          const char *cache_path);
+
+qtm_status qtm_multi_get_config(const qtm_multi *multi, qtm_multi_config *cfg);
+qtm_status qtm_multi_set_config(qtm_multi *multi, const qtm_multi_config *cfg);
+qtm_status qtm_multi_destroy(qtm_multi *multi);
+
 /* Synchronise `stream`, then report (and clear) any status a kernel of this
  * plan recorded on the device: QTM_ETIMEOUT if a bounded wait gave up. */
 qtm_status qtm_sync(qtm_plan *plan, void *stream);

@@ -19,7 +19,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libqtm.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU_SOURCES = ["capi.cu", "fused.cu", "naive.cu", "noalloc.cu"]
+CU_SOURCES = ["capi.cu", "fused.cu", "naive.cu", "noalloc.cu", "multi.cu"]
 CPP_SOURCES = ["plan.cpp", "emulate.cpp"]
 
 

@@ -277,3 +277,145 @@ class Plan:
 
     def sync(self, stream=None):
         self._raise(qtm_sync(self.handle, self._stream(stream)), "qtm_sync")
+
+
+# ---- uneven batches (qtm_build_multi / qtm_multi_run) ---------------------------
+
+QTM_MULTI_X, QTM_MULTI_W, QTM_MULTI_GE, QTM_MULTI_E, QTM_MULTI_GX, QTM_MULTI_GW = range(6)
+QTM_MULTI_GRAPH = 1
+
+
+class qtm_circuit(ctypes.Structure):
+    _fields_ = [("n_qubits", ctypes.c_int32), ("n_gates", ctypes.c_int32), ("gates", ctypes.c_void_p),
+                ("n_terms", ctypes.c_int32), ("n_obs", ctypes.c_int32), ("terms", ctypes.c_void_p),
+                ("n_weights", ctypes.c_int32), ("n_inputs", ctypes.c_int32)]
+
+
+class qtm_multi_config(ctypes.Structure):
+    _fields_ = [("ctas_per_sm", ctypes.c_int32), ("order", ctypes.c_int32),
+                ("fuse_width", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+def _multi_lib():
+    L = lib()
+    if not getattr(L, "_multi_ready", False):
+        vp, i, P = ctypes.c_void_p, ctypes.c_int, ctypes.POINTER
+        L.qtm_build_multi.argtypes = [vp, i, i, i, P(vp)]
+        L.qtm_multi_offsets.argtypes = [vp, i, vp]
+        L.qtm_multi_run.argtypes = [vp, vp, vp, vp, vp, vp, vp, i, vp]
+        L.qtm_multi_tune.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, ctypes.c_char_p]
+        L.qtm_multi_get_config.argtypes = [vp, P(qtm_multi_config)]
+        L.qtm_multi_set_config.argtypes = [vp, P(qtm_multi_config)]
+        L.qtm_multi_destroy.argtypes = [vp]
+        for f in ("qtm_build_multi", "qtm_multi_offsets", "qtm_multi_run", "qtm_multi_tune",
+                  "qtm_multi_get_config", "qtm_multi_set_config", "qtm_multi_destroy"):
+            getattr(L, f).restype = ctypes.c_int
+        L._multi_ready = True
+    return L
+
+
+class MultiPlan:
+    """Uneven batch: circuits of different sizes, `batch` samples each, run
+    forward + adjoint in one persistent launch (optionally a CUDA graph).
+    Buffers are packed circuit after circuit; `offsets(which)` gives the
+    element offset of every circuit's block (see include/qtm.h)."""
+
+    def __init__(self, circuits, batch: int = 1, dtype: str = "c64"):
+        self.circuits = list(circuits)
+        self.batch = int(batch)
+        self.dtype = QTM_C128 if dtype in ("c128", "complex128") else QTM_C64
+        keep = []
+        descs = (qtm_circuit * len(self.circuits))()
+        for k, c in enumerate(self.circuits):
+            G = (qtm_gate * max(1, len(c.gates)))()
+            for i, (kd, q0, q1, wi, xi, co) in enumerate(c.gates):
+                G[i] = qtm_gate(int(kd), int(q0), int(q1), int(wi), int(xi), 0, float(co))
+            T = (qtm_zterm * max(1, len(c.terms)))()
+            for i, (mk, co, ob) in enumerate(c.terms):
+                T[i] = qtm_zterm(int(mk), float(co), int(ob), 0)
+            keep += [G, T]
+            descs[k] = qtm_circuit(c.n, len(c.gates), ctypes.cast(G, ctypes.c_void_p), len(c.terms),
+                                   c.n_obs, ctypes.cast(T, ctypes.c_void_p), c.n_weights, c.n_inputs)
+        h = ctypes.c_void_p()
+        st = _multi_lib().qtm_build_multi(descs, len(self.circuits), self.batch, self.dtype, ctypes.byref(h))
+        if st != QTM_OK:
+            raise QtmError(st, "qtm_build_multi")
+        self.handle = h.value
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            try:
+                _multi_lib().qtm_multi_destroy(h)
+            except Exception:
+                pass
+            self.handle = None
+
+    def offsets(self, which: int) -> np.ndarray:
+        out = np.zeros(len(self.circuits) + 1, dtype=np.int64)
+        st = _multi_lib().qtm_multi_offsets(self.handle, int(which), out.ctypes.data)
+        if st != QTM_OK:
+            raise QtmError(st, "qtm_multi_offsets")
+        return out
+
+    def real_dtype(self):
+        import torch
+        return torch.float64 if self.dtype == QTM_C128 else torch.float32
+
+    def pack(self, blocks, which: int, device="cuda"):
+        """Concatenate per-circuit arrays into the packed device buffer `which`."""
+        import torch
+        off = self.offsets(which)
+        flat = np.zeros(int(off[-1]), dtype=np.float64)
+        for c, blk in enumerate(blocks):
+            a = np.asarray(blk, dtype=np.float64).reshape(-1)
+            assert a.size == off[c + 1] - off[c], (c, a.size, off[c + 1] - off[c])
+            flat[off[c]:off[c + 1]] = a
+        return torch.tensor(flat, dtype=self.real_dtype(), device=device)
+
+    def unpack(self, flat, which: int, shapes):
+        off = self.offsets(which)
+        a = flat.double().cpu().numpy()
+        return [a[off[c]:off[c + 1]].reshape(shapes[c]) for c in range(len(self.circuits))]
+
+    def empty(self, which: int, device="cuda"):
+        import torch
+        return torch.empty(int(self.offsets(which)[-1]), dtype=self.real_dtype(), device=device)
+
+    @staticmethod
+    def _p(t):
+        return ctypes.c_void_p(t.data_ptr())
+
+    def run(self, x, w, gE, E, gx, gw, graph: bool = False, stream=None):
+        import torch
+        s = (stream or torch.cuda.current_stream()).cuda_stream
+        st = _multi_lib().qtm_multi_run(self.handle, self._p(x), self._p(w), self._p(gE), self._p(E),
+                                        self._p(gx), self._p(gw), QTM_MULTI_GRAPH if graph else 0,
+                                        ctypes.c_void_p(s))
+        if st != QTM_OK:
+            raise QtmError(st, "qtm_multi_run")
+
+    def tune(self, x, w, gE, E, gx, gw, cache_path=None, stream=None):
+        import torch
+        s = (stream or torch.cuda.current_stream()).cuda_stream
+        st = _multi_lib().qtm_multi_tune(self.handle, self._p(x), self._p(w), self._p(gE), self._p(E),
+                                         self._p(gx), self._p(gw), ctypes.c_void_p(s),
+                                         cache_path.encode() if cache_path else None)
+        if st != QTM_OK:
+            raise QtmError(st, "qtm_multi_tune")
+        return self.config
+
+    @property
+    def config(self) -> dict:
+        c = qtm_multi_config()
+        st = _multi_lib().qtm_multi_get_config(self.handle, ctypes.byref(c))
+        if st != QTM_OK:
+            raise QtmError(st, "qtm_multi_get_config")
+        return {"ctas_per_sm": c.ctas_per_sm, "order": c.order, "fuse_width": c.fuse_width}
+
+    @config.setter
+    def config(self, d: dict):
+        c = qtm_multi_config(int(d["ctas_per_sm"]), int(d["order"]), int(d["fuse_width"]), 0)
+        st = _multi_lib().qtm_multi_set_config(self.handle, ctypes.byref(c))
+        if st != QTM_OK:
+            raise QtmError(st, "qtm_multi_set_config")

@@ -1,0 +1,795 @@
+// Uneven batches: many circuits (different n and depth), `batch` samples each,
+// forward + adjoint in one persistent kernel launch.
+//
+// Work items are (circuit, sample) pairs, handed to CTAs by a device counter
+// (atomicAdd; nothing ever waits on another CTA).  A circuit whose state fits
+// one shared-memory tile (n <= 12) runs its forward pass, expectation values,
+// costate and reverse pass back to back without leaving shared memory; a
+// larger circuit sweeps the tiles of its own state (kept in a per-item global
+// buffer, L2-resident for n <= 16) pass after pass inside the same CTA.  The
+// run is prep -> counter reset -> persistent kernel -> finalize kernels, and
+// can be captured once into a CUDA graph and replayed.  An autotuner picks
+// the grid size, the item order and the fusion width by timing candidates.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <fstream>
+#include <map>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "../../include/qtm.h"
+#include "tile.cuh"
+
+namespace qtm {
+
+struct CircDev {
+    int n, sq, K, tiles, n_in, P, M, n_runs, n_rots, n_terms;
+    int fwd_begin, n_fwd, rev_begin, n_rev;
+    int ops_off, diag_off, phases_off, slots_off, runs_off, rots_off, prq_off, ents_off, terms_off,
+        amap_off, wptr_off, wrots_off, xptr_off, xrots_off;
+    long long x_off, w_off, gE_off, E_off, gx_off, gw_off;   // elements of the packed user buffers
+    long long mats_off, tabs_off;                            // complex elements of the workspace
+    long long Epart_off, Gpart_off, abar_off, gwws_off;      // doubles
+    long long state_off;                                     // complex elements (tiles > 1 only)
+};
+
+struct WorkItem {
+    int c, b;
+};
+
+struct MultiArgs {
+    int n_items, B;
+    const WorkItem *items;
+    const CircDev *circ;
+    const PassDesc *passes;
+    const DevOp *ops;
+    const DiagPair *diag;
+    const DevPhase *phases;
+    const int32_t *slot_runs;
+    const Run *runs;
+    const Rot *rots;
+    const int32_t *prq;
+    const Ent *ents;
+    const Term *terms;
+    const MaskTerm *amap;
+    const int32_t *w_ptr, *w_rots, *x_ptr, *x_rots;
+    const void *x, *w, *gE;
+    void *E, *gx, *gw;
+    void *mats, *tabs, *state;
+    double *Epart, *Gpart, *abar, *gwws;
+    unsigned *counter;
+    // shared-memory layout bounds (max over all passes of all circuits)
+    int max_slots, max_terms, max_M, max_ents, max_sq;
+};
+
+namespace {
+
+template <typename R>
+__device__ __forceinline__ TileJob make_job(const MultiArgs &m, const CircDev &cd, const PassDesc &pd,
+                                            int b, uint32_t base)
+{
+    TileJob j;
+    j.K = pd.K; j.l = pd.l; j.h = pd.h; j.m = pd.m; j.sq = cd.sq;
+    j.T = 1 << (pd.K - 4);
+    j.base = base;
+    j.ops = m.ops + cd.ops_off;
+    j.diag = m.diag + cd.diag_off;
+    j.phases = m.phases + cd.phases_off;
+    j.phase_begin = pd.phase_begin; j.phase_end = pd.phase_end;
+    j.slot_runs = m.slot_runs + cd.slots_off + pd.slot_begin;
+    j.nslots = pd.slot_end - pd.slot_begin;
+    j.mats = static_cast<const Cx<R> *>(m.mats) + cd.mats_off + (size_t)b * cd.n_runs * 4;
+    j.tabs = static_cast<const Cx<R> *>(m.tabs) + cd.tabs_off + (size_t)b * ((cd.sq + 3) >> 2) * 16;
+    j.prefix_ents = m.ents + cd.ents_off;
+    j.analytic_ents = pd.phi_src == SRC_ANALYTIC ? pd.analytic_ents : 0;
+    j.amap = m.amap + cd.amap_off + (pd.amap_lin >= 0 ? pd.amap_begin : 0);
+    j.amap_lin = pd.phi_src == SRC_ANALYTIC ? pd.amap_lin : -1;
+    j.amap_quad = pd.amap_quad;
+    j.amap_dlin = pd.amap_dlin;
+    j.terms = m.terms + cd.terms_off;
+    j.n_terms = cd.n_terms;
+    j.M = cd.M;
+    j.gE = static_cast<const R *>(m.gE) + cd.gE_off + (size_t)b * cd.M;
+    j.phi_src = pd.phi_src;
+    j.lam_src = pd.lam_src;
+    return j;
+}
+
+template <typename R>
+__device__ __forceinline__ uint32_t tile_base(const PassDesc &pd, int tile)
+{
+    const int gapbits = pd.h - pd.l;
+    const uint32_t gap = tile & ((1u << gapbits) - 1u);
+    const uint32_t rest = tile >> gapbits;
+    return (gap << pd.l) | (rest << (pd.h + pd.m));
+}
+
+// global <-> shared tile copies (plain loads/stores; the item's state is L2-resident)
+template <typename R>
+__device__ __forceinline__ void load_tile(const TileJob &j, Cx<R> *dst, const Cx<R> *src)
+{
+    const int E = 1 << j.K;
+    for (int e = threadIdx.x; e < E; e += blockDim.x) {
+        const uint32_t y = j.base | ((uint32_t)e & ((1u << j.l) - 1u)) | (((uint32_t)e >> j.l) << j.h);
+        dst[swz<R>(e)] = src[y];
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ void store_tile(const TileJob &j, const Cx<R> *src, Cx<R> *dst)
+{
+    const int E = 1 << j.K;
+    for (int e = threadIdx.x; e < E; e += blockDim.x) {
+        const uint32_t y = j.base | ((uint32_t)e & ((1u << j.l) - 1u)) | (((uint32_t)e >> j.l) << j.h);
+        dst[y] = src[swz<R>(e)];
+    }
+}
+
+template <typename R>
+__global__ void k_multi_prep(const MultiArgs m)
+{
+    __shared__ double2 ufac[2 * 32];
+    const WorkItem wi = m.items[blockIdx.x];
+    const CircDev cd = m.circ[wi.c];
+    prep_sample<R>(m.runs + cd.runs_off, m.rots + cd.rots_off, m.prq + cd.prq_off, cd.n_runs, cd.n, cd.sq,
+                   static_cast<const R *>(m.x) + cd.x_off + (size_t)wi.b * cd.n_in,
+                   static_cast<const R *>(m.w) + cd.w_off,
+                   static_cast<Cx<R> *>(m.mats) + cd.mats_off + (size_t)wi.b * cd.n_runs * 4,
+                   static_cast<Cx<R> *>(m.tabs) + cd.tabs_off + (size_t)wi.b * ((cd.sq + 3) >> 2) * 16, ufac);
+}
+
+// MINB: CTAs per SM the register budget is compiled for (1: no spills, 2: more
+// resident warps); the autotuner's ctas_per_sm picks the variant.
+template <typename R, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_multi(const MultiArgs m)
+{
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *smem = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    __shared__ int s_item;
+    const Layout L = make_layout(kMaxTileQubits, (int)sizeof(Cx<R>), true, m.max_slots, m.max_terms,
+                                 m.max_M, m.max_sq, m.max_ents, 8, (int)sizeof(R));
+    const TileSmem<R> S = carve<R>(smem, L);
+    for (;;) {
+        if (threadIdx.x == 0) s_item = (int)atomicAdd(m.counter, 1u);
+        __syncthreads();
+        const int item = s_item;
+        __syncthreads();
+        if (item >= m.n_items) return;
+        const WorkItem wi = m.items[item];
+        const CircDev cd = m.circ[wi.c];
+        const int b = wi.b;
+        double *Epart_b = m.Epart + cd.Epart_off + (size_t)b * cd.tiles * cd.M;
+        double *Gpart_b = m.Gpart + cd.Gpart_off + (size_t)b * cd.n_runs * cd.tiles * 3;
+        if (cd.tiles == 1) {
+            // whole state in shared memory: forward, expectation values, costate, reverse
+            for (int i = 0; i < cd.n_fwd; ++i) {   // a single pass for n <= 12
+                const PassDesc pd = m.passes[cd.fwd_begin + i];
+                const TileJob j = make_job<R>(m, cd, pd, b, 0u);
+                const int nw = (j.T + 31) >> 5;
+                stage_tables<R, false>(j, S, nw);
+                __syncthreads();
+                if (pd.phi_src == SRC_ANALYTIC) fill_analytic<R>(j, S);
+                __syncthreads();
+                run_phases<R, false>(j, S, false);
+                write_partials<R, false>(j, S, nw, pd.has_expval != 0, Epart_b, nullptr, 1, 0);
+                __syncthreads();
+            }
+            for (int i = 0; i < cd.n_rev; ++i) {
+                const PassDesc pd = m.passes[cd.rev_begin + i];
+                const TileJob j = make_job<R>(m, cd, pd, b, 0u);
+                const int nw = (j.T + 31) >> 5;
+                stage_tables<R, true>(j, S, nw);
+                __syncthreads();
+                if (pd.phi_src == SRC_ANALYTIC) fill_analytic<R>(j, S);   // else phi is still in smem
+                __syncthreads();
+                run_phases<R, true>(j, S, false);
+                write_partials<R, true>(j, S, nw, false, nullptr, Gpart_b, 1, 0);
+                __syncthreads();
+            }
+            continue;
+        }
+        // tiled: this item's phi and lam live in global memory
+        Cx<R> *gphi = static_cast<Cx<R> *>(m.state) + cd.state_off + (size_t)b * (2ull << cd.sq);
+        Cx<R> *glam = gphi + (1ull << cd.sq);
+        for (int i = 0; i < cd.n_fwd; ++i) {
+            const PassDesc pd = m.passes[cd.fwd_begin + i];
+            for (int t = 0; t < cd.tiles; ++t) {
+                const TileJob j = make_job<R>(m, cd, pd, b, tile_base<R>(pd, t));
+                const int nw = (j.T + 31) >> 5;
+                stage_tables<R, false>(j, S, nw);
+                if (pd.phi_src == SRC_LOAD) load_tile<R>(j, S.phi, gphi);
+                __syncthreads();
+                if (pd.phi_src == SRC_ANALYTIC) fill_analytic<R>(j, S);
+                __syncthreads();
+                run_phases<R, false>(j, S, false);
+                write_partials<R, false>(j, S, nw, pd.has_expval != 0, Epart_b + (size_t)t * cd.M, nullptr,
+                                         cd.tiles, t);
+                if (pd.store_phi) store_tile<R>(j, S.phi, gphi);
+                __syncthreads();
+            }
+        }
+        for (int i = 0; i < cd.n_rev; ++i) {
+            const PassDesc pd = m.passes[cd.rev_begin + i];
+            for (int t = 0; t < cd.tiles; ++t) {
+                const TileJob j = make_job<R>(m, cd, pd, b, tile_base<R>(pd, t));
+                const int nw = (j.T + 31) >> 5;
+                stage_tables<R, true>(j, S, nw);
+                if (pd.phi_src == SRC_LOAD) load_tile<R>(j, S.phi, gphi);
+                if (pd.lam_src == SRC_LOAD) load_tile<R>(j, S.lam, glam);
+                __syncthreads();
+                if (pd.phi_src == SRC_ANALYTIC) fill_analytic<R>(j, S);
+                __syncthreads();
+                run_phases<R, true>(j, S, pd.lam_src == SRC_LOAD);
+                write_partials<R, true>(j, S, nw, false, nullptr, Gpart_b, cd.tiles, t);
+                if (pd.store_phi) store_tile<R>(j, S.phi, gphi);
+                if (pd.store_lam) store_tile<R>(j, S.lam, glam);
+                __syncthreads();
+            }
+        }
+    }
+}
+
+template <typename R>
+__global__ void k_multi_expval(const MultiArgs m)
+{
+    const WorkItem wi = m.items[blockIdx.x];
+    const CircDev cd = m.circ[wi.c];
+    const double *Ep = m.Epart + cd.Epart_off + (size_t)wi.b * cd.tiles * cd.M;
+    R *E = static_cast<R *>(m.E) + cd.E_off + (size_t)wi.b * cd.M;
+    for (int k = threadIdx.x; k < cd.M; k += blockDim.x) {
+        double s = 0.0;
+        for (int t = 0; t < cd.tiles; ++t) s += Ep[(size_t)t * cd.M + k];
+        E[k] = (R)s;
+    }
+}
+
+template <typename R>
+__global__ void k_multi_grad(const MultiArgs m)
+{
+    const WorkItem wi = m.items[blockIdx.x];
+    const CircDev cd = m.circ[wi.c];
+    const int b = wi.b;
+    grad_finalize_sample<R>(m.runs + cd.runs_off, m.rots + cd.rots_off, cd.n_runs, m.w_ptr + cd.wptr_off,
+                            m.w_rots + cd.wrots_off, m.x_ptr + cd.xptr_off, m.x_rots + cd.xrots_off,
+                            cd.P, cd.n_in, static_cast<const R *>(m.x) + cd.x_off + (size_t)b * cd.n_in,
+                            static_cast<const R *>(m.w) + cd.w_off,
+                            m.Gpart + cd.Gpart_off + (size_t)b * cd.n_runs * cd.tiles * 3, cd.tiles,
+                            m.abar + cd.abar_off + (size_t)b * cd.n_rots,
+                            static_cast<R *>(m.gx) + cd.gx_off + (size_t)b * cd.n_in, nullptr,
+                            m.gwws + cd.gwws_off + (size_t)b * cd.P);
+}
+
+// grad_w of circuit c = sum over its samples, fixed order; one thread per weight
+template <typename R>
+__global__ void k_multi_gw(const MultiArgs m, const int *wcirc, int total_w)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= total_w) return;
+    const int c = wcirc[i];
+    const CircDev cd = m.circ[c];
+    const int j = (int)(i - cd.gw_off);
+    double s = 0.0;
+    for (int b = 0; b < m.B; ++b) s += m.gwws[cd.gwws_off + (size_t)b * cd.P + j];
+    static_cast<R *>(m.gw)[i] = (R)s;
+}
+
+}  // namespace
+
+}  // namespace qtm
+
+using namespace qtm;
+
+struct qtm_multi {
+    int dtype = QTM_C64, B = 1;
+    std::vector<std::vector<qtm_gate>> gates;
+    std::vector<std::vector<qtm_zterm>> terms;
+    std::vector<qtm_circuit> desc;
+    std::vector<Plan> plans;
+    qtm_multi_config cfg{2, 0, kMaxRunLen, 0};
+    // host-side images
+    std::vector<CircDev> circ;
+    std::vector<WorkItem> items;
+    std::vector<PassDesc> passes;
+    std::vector<DevOp> ops;
+    std::vector<DiagPair> diag;
+    std::vector<DevPhase> phases;
+    std::vector<int32_t> slots, prq, wptr, wrots, xptr, xrots, wcirc;
+    std::vector<Run> runs;
+    std::vector<Rot> rots;
+    std::vector<Ent> ents;
+    std::vector<Term> tms;
+    std::vector<MaskTerm> amap;
+    std::vector<long long> off[6];
+    long long n_mats = 0, n_tabs = 0, n_epart = 0, n_gpart = 0, n_abar = 0, n_gwws = 0, n_state = 0;
+    int max_slots = 1, max_terms = 1, max_M = 1, max_ents = 1, max_sq = 4;
+    size_t smem = 0;
+    // device
+    int device = -1;
+    bool dirty = true;
+    void *dev_block = nullptr;      // all tables in one allocation
+    void *d_ws = nullptr;           // workspace (mats, tabs, state)
+    double *d_dbl = nullptr;        // Epart, Gpart, abar, gwws
+    unsigned *d_counter = nullptr;
+    MultiArgs args{};
+    // graph cache
+    cudaGraphExec_t gexec = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    const void *gkey[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    const int *wcirc_dev = nullptr;
+    std::string err;
+};
+
+namespace {
+
+void release_graph(qtm_multi *m)
+{
+    if (m->gexec) cudaGraphExecDestroy(m->gexec);
+    if (m->graph) cudaGraphDestroy(m->graph);
+    m->gexec = nullptr;
+    m->graph = nullptr;
+    std::fill(std::begin(m->gkey), std::end(m->gkey), nullptr);
+}
+
+void release_device(qtm_multi *m)
+{
+    release_graph(m);
+    if (m->dev_block) cudaFree(m->dev_block);
+    if (m->d_ws) cudaFree(m->d_ws);
+    if (m->d_dbl) cudaFree(m->d_dbl);
+    if (m->d_counter) cudaFree(m->d_counter);
+    m->dev_block = m->d_ws = nullptr;
+    m->d_dbl = nullptr;
+    m->d_counter = nullptr;
+    m->dirty = true;
+}
+
+double item_cost(const Plan &P)
+{
+    double fb, ab, ff, af;
+    plan_costs(P, fb, ab, ff, af);
+    return ff + af + 4.0 * (fb + ab);
+}
+
+// (Re)plan every circuit with the current fusion width and lay out the tables.
+qtm_status plan_all(qtm_multi *m)
+{
+    const int nc = (int)m->desc.size();
+    m->plans.assign(nc, Plan());
+    for (int c = 0; c < nc; ++c) {
+        const qtm_circuit &d = m->desc[c];
+        std::string err;
+        qtm_status st = make_plan(d.n_qubits, m->gates[c].data(), (int)m->gates[c].size(), m->terms[c].data(),
+                                  (int)m->terms[c].size(), d.n_obs, d.n_weights, d.n_inputs, m->dtype,
+                                  QTM_PATH_FUSED, m->plans[c], err, m->cfg.fuse_width);
+        if (st != QTM_OK) {
+            std::ostringstream s;
+            s << "circuit " << c << ": " << err;
+            m->err = s.str();
+            return st;
+        }
+    }
+    m->circ.assign(nc, CircDev{});
+    m->passes.clear(); m->ops.clear(); m->diag.clear(); m->phases.clear(); m->slots.clear();
+    m->prq.clear(); m->wptr.clear(); m->wrots.clear(); m->xptr.clear(); m->xrots.clear();
+    m->runs.clear(); m->rots.clear(); m->ents.clear(); m->tms.clear(); m->amap.clear(); m->wcirc.clear();
+    for (auto &o : m->off) o.assign(nc + 1, 0);
+    long long mats = 0, tabs = 0, ep = 0, gp = 0, ab = 0, gw = 0, st = 0;
+    m->max_slots = m->max_terms = m->max_M = m->max_ents = 1;
+    m->max_sq = 4;
+    for (int c = 0; c < nc; ++c) {
+        const Plan &P = m->plans[c];
+        CircDev &d = m->circ[c];
+        d.n = P.n; d.sq = P.state_qubits; d.K = P.K; d.tiles = P.tiles_per_sample;
+        d.n_in = P.n_inputs; d.P = P.n_weights; d.M = P.n_obs;
+        d.n_runs = (int)P.runs.size(); d.n_rots = (int)P.rots.size(); d.n_terms = (int)P.terms.size();
+        d.fwd_begin = (int)m->passes.size(); d.n_fwd = (int)P.fwd.size();
+        m->passes.insert(m->passes.end(), P.fwd.begin(), P.fwd.end());
+        d.rev_begin = (int)m->passes.size(); d.n_rev = (int)P.rev.size();
+        m->passes.insert(m->passes.end(), P.rev.begin(), P.rev.end());
+        for (auto *v : {&P.fwd, &P.rev})
+            for (const auto &pd : *v) {
+                m->max_slots = std::max(m->max_slots, pd.slot_end - pd.slot_begin);
+                if (pd.phi_src == SRC_ANALYTIC) m->max_ents = std::max(m->max_ents, pd.analytic_ents);
+            }
+        m->max_terms = std::max(m->max_terms, (int)P.terms.size());
+        m->max_M = std::max(m->max_M, P.n_obs);
+        m->max_sq = std::max(m->max_sq, P.state_qubits);
+#define APPEND(field, dst, src) d.field = (int)dst.size(); dst.insert(dst.end(), src.begin(), src.end())
+        APPEND(ops_off, m->ops, P.ops);
+        APPEND(diag_off, m->diag, P.diag_pairs);
+        APPEND(phases_off, m->phases, P.phases);
+        APPEND(slots_off, m->slots, P.slot_runs);
+        APPEND(runs_off, m->runs, P.runs);
+        APPEND(rots_off, m->rots, P.rots);
+        APPEND(prq_off, m->prq, P.prefix_run_of_q);
+        APPEND(ents_off, m->ents, P.prefix_ents);
+        APPEND(terms_off, m->tms, P.terms);
+        APPEND(amap_off, m->amap, P.amap_terms);
+        APPEND(wptr_off, m->wptr, P.w_ptr);
+        APPEND(wrots_off, m->wrots, P.w_rots);
+        APPEND(xptr_off, m->xptr, P.x_ptr);
+        APPEND(xrots_off, m->xrots, P.x_rots);
+#undef APPEND
+        const long long B = m->B;
+        d.x_off = m->off[QTM_MULTI_X][c]; m->off[QTM_MULTI_X][c + 1] = d.x_off + B * P.n_inputs;
+        d.w_off = m->off[QTM_MULTI_W][c]; m->off[QTM_MULTI_W][c + 1] = d.w_off + P.n_weights;
+        d.gE_off = m->off[QTM_MULTI_GE][c]; m->off[QTM_MULTI_GE][c + 1] = d.gE_off + B * P.n_obs;
+        d.E_off = m->off[QTM_MULTI_E][c]; m->off[QTM_MULTI_E][c + 1] = d.E_off + B * P.n_obs;
+        d.gx_off = m->off[QTM_MULTI_GX][c]; m->off[QTM_MULTI_GX][c + 1] = d.gx_off + B * P.n_inputs;
+        d.gw_off = m->off[QTM_MULTI_GW][c]; m->off[QTM_MULTI_GW][c + 1] = d.gw_off + P.n_weights;
+        for (int j = 0; j < P.n_weights; ++j) m->wcirc.push_back(c);
+        d.mats_off = mats; mats += B * 4 * std::max(1, d.n_runs);
+        d.tabs_off = tabs; tabs += B * 16 * ((d.sq + 3) / 4);
+        d.Epart_off = ep; ep += B * d.tiles * std::max(1, d.M);
+        d.Gpart_off = gp; gp += B * std::max(1, d.n_runs) * d.tiles * 3;
+        d.abar_off = ab; ab += B * std::max(1, d.n_rots);
+        d.gwws_off = gw; gw += B * std::max(1, d.P);
+        d.state_off = st;
+        if (d.tiles > 1) st += B * (2ll << d.sq);
+    }
+    m->n_mats = mats; m->n_tabs = tabs; m->n_epart = ep; m->n_gpart = gp; m->n_abar = ab; m->n_gwws = gw;
+    m->n_state = st;
+    // work items, costliest first (or as given)
+    m->items.clear();
+    for (int c = 0; c < nc; ++c)
+        for (int b = 0; b < m->B; ++b) m->items.push_back({c, b});
+    if (m->cfg.order == 0) {
+        std::vector<double> cost(nc);
+        for (int c = 0; c < nc; ++c) cost[c] = item_cost(m->plans[c]);
+        std::stable_sort(m->items.begin(), m->items.end(),
+                         [&](const WorkItem &a, const WorkItem &b) { return cost[a.c] > cost[b.c]; });
+    }
+    const int csize = elem_bytes(m->dtype);
+    const Layout L = make_layout(kMaxTileQubits, csize, true, m->max_slots, m->max_terms, m->max_M,
+                                 m->max_sq, m->max_ents, 8, csize / 2);
+    m->smem = (size_t)L.total + 1024;
+    if (m->smem > 232448) { m->err = "tables exceed shared memory"; return QTM_EUNSUPPORTED; }
+    m->dirty = true;
+    return QTM_OK;
+}
+
+template <typename T>
+size_t put(std::vector<unsigned char> &blob, const std::vector<T> &v)
+{
+    size_t at = (blob.size() + 255) & ~size_t(255);
+    blob.resize(at + sizeof(T) * std::max<size_t>(1, v.size()));
+    if (!v.empty()) std::memcpy(blob.data() + at, v.data(), sizeof(T) * v.size());
+    return at;
+}
+
+qtm_status upload(qtm_multi *m)
+{
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) { m->err = "no CUDA device"; return QTM_ECUDA; }
+    if (!m->dirty && dev == m->device) return QTM_OK;
+    release_device(m);
+    std::vector<unsigned char> blob;
+    const size_t o_items = put(blob, m->items), o_circ = put(blob, m->circ), o_passes = put(blob, m->passes),
+                 o_ops = put(blob, m->ops), o_diag = put(blob, m->diag), o_phases = put(blob, m->phases),
+                 o_slots = put(blob, m->slots), o_runs = put(blob, m->runs), o_rots = put(blob, m->rots),
+                 o_prq = put(blob, m->prq), o_ents = put(blob, m->ents), o_terms = put(blob, m->tms),
+                 o_amap = put(blob, m->amap), o_wptr = put(blob, m->wptr), o_wrots = put(blob, m->wrots),
+                 o_xptr = put(blob, m->xptr), o_xrots = put(blob, m->xrots), o_wcirc = put(blob, m->wcirc);
+    const size_t csize = elem_bytes(m->dtype);
+    if (cudaMalloc(&m->dev_block, blob.size()) != cudaSuccess ||
+        cudaMemcpy(m->dev_block, blob.data(), blob.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+        release_device(m);
+        m->err = "table upload failed";
+        return QTM_ENOMEM;
+    }
+    const size_t ws = csize * (size_t)(m->n_mats + m->n_tabs + m->n_state);
+    const size_t nd = (size_t)(m->n_epart + m->n_gpart + m->n_abar + m->n_gwws);
+    if (cudaMalloc(&m->d_ws, ws ? ws : 16) != cudaSuccess || cudaMalloc(&m->d_dbl, 8 * (nd ? nd : 1)) != cudaSuccess ||
+        cudaMalloc(&m->d_counter, sizeof(unsigned)) != cudaSuccess) {
+        release_device(m);
+        m->err = "workspace allocation failed";
+        return QTM_ENOMEM;
+    }
+    unsigned char *db = static_cast<unsigned char *>(m->dev_block);
+    MultiArgs &a = m->args;
+    a = MultiArgs{};
+    a.n_items = (int)m->items.size();
+    a.B = m->B;
+    a.items = reinterpret_cast<const WorkItem *>(db + o_items);
+    a.circ = reinterpret_cast<const CircDev *>(db + o_circ);
+    a.passes = reinterpret_cast<const PassDesc *>(db + o_passes);
+    a.ops = reinterpret_cast<const DevOp *>(db + o_ops);
+    a.diag = reinterpret_cast<const DiagPair *>(db + o_diag);
+    a.phases = reinterpret_cast<const DevPhase *>(db + o_phases);
+    a.slot_runs = reinterpret_cast<const int32_t *>(db + o_slots);
+    a.runs = reinterpret_cast<const Run *>(db + o_runs);
+    a.rots = reinterpret_cast<const Rot *>(db + o_rots);
+    a.prq = reinterpret_cast<const int32_t *>(db + o_prq);
+    a.ents = reinterpret_cast<const Ent *>(db + o_ents);
+    a.terms = reinterpret_cast<const Term *>(db + o_terms);
+    a.amap = reinterpret_cast<const MaskTerm *>(db + o_amap);
+    a.w_ptr = reinterpret_cast<const int32_t *>(db + o_wptr);
+    a.w_rots = reinterpret_cast<const int32_t *>(db + o_wrots);
+    a.x_ptr = reinterpret_cast<const int32_t *>(db + o_xptr);
+    a.x_rots = reinterpret_cast<const int32_t *>(db + o_xrots);
+    unsigned char *wsb = static_cast<unsigned char *>(m->d_ws);
+    a.mats = wsb;
+    a.tabs = wsb + csize * m->n_mats;
+    a.state = wsb + csize * (m->n_mats + m->n_tabs);
+    a.Epart = m->d_dbl;
+    a.Gpart = a.Epart + m->n_epart;
+    a.abar = a.Gpart + m->n_gpart;
+    a.gwws = a.abar + m->n_abar;
+    a.counter = m->d_counter;
+    a.max_slots = m->max_slots; a.max_terms = m->max_terms; a.max_M = m->max_M;
+    a.max_ents = m->max_ents; a.max_sq = m->max_sq;
+    m->wcirc_dev = reinterpret_cast<const int *>(db + o_wcirc);
+    m->device = dev;
+    m->dirty = false;
+    return QTM_OK;
+}
+
+}  // namespace
+
+namespace {
+
+template <typename R>
+cudaError_t enqueue_t(qtm_multi *m, cudaStream_t s)
+{
+    const MultiArgs &a = m->args;
+    const int ni = a.n_items;
+    cudaError_t e = cudaMemsetAsync(a.counter, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    k_multi_prep<R><<<ni, 128, 0, s>>>(a);
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device);
+    const int cps = m->cfg.ctas_per_sm >= 2 ? 2 : 1;
+    const int grid = std::max(1, std::min(ni, cps * sms));
+    if (cps == 2) k_multi<R, 2><<<grid, 256, m->smem, s>>>(a);
+    else k_multi<R, 1><<<grid, 256, m->smem, s>>>(a);
+    k_multi_expval<R><<<ni, 32, 0, s>>>(a);
+    k_multi_grad<R><<<ni, 256, 0, s>>>(a);
+    const int tw = (int)m->wcirc.size();
+    if (tw > 0) k_multi_gw<R><<<(tw + 255) / 256, 256, 0, s>>>(a, m->wcirc_dev, tw);
+    return cudaGetLastError();
+}
+
+cudaError_t set_smem_attr(qtm_multi *m)
+{
+    const int v = (int)m->smem;
+    const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    cudaError_t e;
+    if (m->dtype == QTM_C128) {
+        e = cudaFuncSetAttribute(k_multi<double, 1>, at, v);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_multi<double, 2>, at, v);
+    } else {
+        e = cudaFuncSetAttribute(k_multi<float, 1>, at, v);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_multi<float, 2>, at, v);
+    }
+    return e;
+}
+
+cudaError_t enqueue(qtm_multi *m, cudaStream_t s)
+{
+    return m->dtype == QTM_C128 ? enqueue_t<double>(m, s) : enqueue_t<float>(m, s);
+}
+
+qtm_status run_impl(qtm_multi *m, const void *x, const void *w, const void *gE, void *E, void *gx, void *gw,
+                    int flags, cudaStream_t s)
+{
+    qtm_status st = upload(m);
+    if (st != QTM_OK) return st;
+    if (set_smem_attr(m) != cudaSuccess) { m->err = "shared-memory attribute"; return QTM_ECUDA; }
+    MultiArgs &a = m->args;
+    a.x = x; a.w = w; a.gE = gE; a.E = E; a.gx = gx; a.gw = gw;
+    if (!(flags & QTM_MULTI_GRAPH)) {
+        cudaError_t e = enqueue(m, s);
+        if (e != cudaSuccess) { m->err = cudaGetErrorString(e); return QTM_ECUDA; }
+        return QTM_OK;
+    }
+    const void *key[6] = {x, w, gE, E, gx, gw};
+    if (!m->gexec || !std::equal(std::begin(key), std::end(key), std::begin(m->gkey))) {
+        release_graph(m);
+        if (!m->cap_stream && cudaStreamCreateWithFlags(&m->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+            m->err = "stream creation failed";
+            return QTM_ECUDA;
+        }
+        cudaError_t e = cudaStreamBeginCapture(m->cap_stream, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaError_t e2 = enqueue(m, m->cap_stream);
+            e = cudaStreamEndCapture(m->cap_stream, &m->graph);
+            if (e == cudaSuccess) e = e2;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&m->gexec, m->graph, 0);
+        if (e != cudaSuccess) {
+            release_graph(m);
+            m->err = std::string("graph capture: ") + cudaGetErrorString(e);
+            return QTM_ECUDA;
+        }
+        std::copy(std::begin(key), std::end(key), std::begin(m->gkey));
+    }
+    cudaError_t e = cudaGraphLaunch(m->gexec, s);
+    if (e != cudaSuccess) { m->err = cudaGetErrorString(e); return QTM_ECUDA; }
+    return QTM_OK;
+}
+
+std::string signature(const qtm_multi *m)
+{
+    // FNV-1a over the batch's shape: dtype, batch, every circuit's gates and terms
+    unsigned long long h = 1469598103934665603ull;
+    auto mix = [&](long long v) {
+        for (int k = 0; k < 8; ++k) { h ^= (unsigned long long)((v >> (8 * k)) & 0xff); h *= 1099511628211ull; }
+    };
+    mix(m->dtype); mix(m->B); mix((long long)m->desc.size());
+    for (size_t c = 0; c < m->desc.size(); ++c) {
+        mix(m->desc[c].n_qubits);
+        for (const auto &g : m->gates[c]) { mix(g.kind); mix(g.q0); mix(g.q1); }
+        mix((long long)m->terms[c].size());
+    }
+    cudaDeviceProp prop;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::string name = "unknown";
+    if (cudaGetDeviceProperties(&prop, dev) == cudaSuccess) name = prop.name;
+    for (char &ch : name) if (ch == '"' || ch == '\\') ch = '_';
+    std::ostringstream s;
+    s << std::hex << h << "@" << name;
+    return s.str();
+}
+
+bool cache_lookup(const char *path, const std::string &sig, qtm_multi_config &cfg)
+{
+    if (!path) return false;
+    std::ifstream f(path);
+    std::string line;
+    const std::string key = "\"signature\": \"" + sig + "\"";
+    while (std::getline(f, line)) {
+        if (line.find(key) == std::string::npos) continue;
+        auto num = [&](const char *field) -> int {
+            const std::string k = std::string("\"") + field + "\": ";
+            size_t at = line.find(k);
+            return at == std::string::npos ? -1 : std::atoi(line.c_str() + at + k.size());
+        };
+        qtm_multi_config c{num("ctas_per_sm"), num("order"), num("fuse_width"), 0};
+        if (c.ctas_per_sm < 1 || c.order < 0 || c.fuse_width < 1) continue;
+        cfg = c;
+        return true;
+    }
+    return false;
+}
+
+void cache_store(const char *path, const std::string &sig, const qtm_multi_config &cfg, double ms)
+{
+    if (!path) return;
+    std::ofstream f(path, std::ios::app);
+    f << "{\"signature\": \"" << sig << "\", \"ctas_per_sm\": " << cfg.ctas_per_sm << ", \"order\": " << cfg.order
+      << ", \"fuse_width\": " << cfg.fuse_width << ", \"ms\": " << ms << "}\n";
+}
+
+qtm_status apply_config(qtm_multi *m, const qtm_multi_config &c)
+{
+    const bool replan = c.fuse_width != m->cfg.fuse_width || c.order != m->cfg.order;
+    m->cfg = c;
+    release_graph(m);   // the grid size and the tables are baked into a captured graph
+    if (replan) {
+        release_device(m);
+        return plan_all(m);
+    }
+    return QTM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+qtm_status qtm_build_multi(const qtm_circuit *circuits, int n_circuits, int batch, int dtype, qtm_multi **out)
+{
+    if (!out || !circuits || n_circuits < 1 || batch < 1) return QTM_EINVAL;
+    if (dtype != QTM_C64 && dtype != QTM_C128) return QTM_EINVAL;
+    *out = nullptr;
+    qtm_multi *m = new (std::nothrow) qtm_multi();
+    if (!m) return QTM_ENOMEM;
+    m->dtype = dtype;
+    m->B = batch;
+    for (int c = 0; c < n_circuits; ++c) {
+        const qtm_circuit &d = circuits[c];
+        if (d.n_gates < 0 || d.n_terms < 0 || (d.n_gates > 0 && !d.gates) || (d.n_terms > 0 && !d.terms)) {
+            delete m;
+            return QTM_EINVAL;
+        }
+        m->desc.push_back(d);
+        m->gates.emplace_back(d.gates, d.gates + d.n_gates);
+        m->terms.emplace_back(d.terms, d.terms + d.n_terms);
+        m->desc.back().gates = m->gates.back().data();
+        m->desc.back().terms = m->terms.back().data();
+    }
+    qtm_status st = plan_all(m);
+    if (st != QTM_OK) { delete m; return st; }
+    *out = m;
+    return QTM_OK;
+}
+
+qtm_status qtm_multi_offsets(const qtm_multi *m, int which, int64_t *offsets)
+{
+    if (!m || !offsets || which < 0 || which > 5) return QTM_EINVAL;
+    for (size_t i = 0; i < m->off[which].size(); ++i) offsets[i] = m->off[which][i];
+    return QTM_OK;
+}
+
+qtm_status qtm_multi_run(qtm_multi *m, const void *x, const void *w, const void *gE, void *E, void *gx,
+                         void *gw, int flags, void *stream)
+{
+    if (!m || !x || !w || !gE || !E || !gx || !gw) return QTM_EINVAL;
+    if (flags & ~QTM_MULTI_GRAPH) return QTM_EINVAL;
+    return run_impl(m, x, w, gE, E, gx, gw, flags, static_cast<cudaStream_t>(stream));
+}
+
+qtm_status qtm_multi_tune(qtm_multi *m, const void *x, const void *w, const void *gE, void *E, void *gx,
+                          void *gw, void *stream, const char *cache_path)
+{
+    if (!m || !x || !w || !gE || !E || !gx || !gw) return QTM_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const std::string sig = signature(m);
+    qtm_multi_config cached;
+    if (cache_lookup(cache_path, sig, cached)) return apply_config(m, cached);
+    qtm_multi_config best = m->cfg;
+    double best_ms = 1e30;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return QTM_ECUDA;
+    qtm_status result = QTM_OK;
+    for (int fuse : {32, 3, 1})
+        for (int order : {0, 1})
+            for (int cps : {1, 2}) {
+                qtm_multi_config c{cps, order, fuse, 0};
+                qtm_status st = apply_config(m, c);
+                if (st != QTM_OK) continue;
+                std::vector<float> t;
+                for (int rep = 0; rep < 7 && st == QTM_OK; ++rep) {
+                    cudaEventRecord(e0, s);
+                    st = run_impl(m, x, w, gE, E, gx, gw, 0, s);
+                    cudaEventRecord(e1, s);
+                    if (cudaEventSynchronize(e1) != cudaSuccess) { st = QTM_ECUDA; break; }
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    if (rep >= 2) t.push_back(ms);   // two warm-up repetitions
+                }
+                if (st != QTM_OK) { result = st; continue; }
+                std::sort(t.begin(), t.end());
+                const double med = t[t.size() / 2];
+                if (med < best_ms) { best_ms = med; best = c; }
+            }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (best_ms >= 1e30) return result != QTM_OK ? result : QTM_ECUDA;
+    qtm_status st = apply_config(m, best);
+    if (st == QTM_OK) cache_store(cache_path, sig, best, best_ms);
+    return st;
+}
+
+qtm_status qtm_multi_get_config(const qtm_multi *m, qtm_multi_config *cfg)
+{
+    if (!m || !cfg) return QTM_EINVAL;
+    *cfg = m->cfg;
+    return QTM_OK;
+}
+
+qtm_status qtm_multi_set_config(qtm_multi *m, const qtm_multi_config *cfg)
+{
+    if (!m || !cfg || cfg->ctas_per_sm < 1 || cfg->ctas_per_sm > 8 || cfg->order < 0 || cfg->order > 1 ||
+        cfg->fuse_width < 1 || cfg->fuse_width > kMaxRunLen)
+        return QTM_EINVAL;
+    return apply_config(m, *cfg);
+}
+
+qtm_status qtm_multi_destroy(qtm_multi *m)
+{
+    if (!m) return QTM_EINVAL;
+    if (m->dev_block) cudaDeviceSynchronize();
+    release_device(m);
+    if (m->cap_stream) cudaStreamDestroy(m->cap_stream);
+    delete m;
+    return QTM_OK;
+}
+
+}  // extern "C"

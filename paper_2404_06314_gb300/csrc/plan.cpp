@@ -331,8 +331,10 @@ bool closed_form(const std::vector<Ent> &ents, int e, int n, std::vector<MaskTer
 
 qtm_status make_plan(int n, const qtm_gate *gates, int n_gates, const qtm_zterm *terms,
                      int n_terms, int n_obs, int n_weights, int n_inputs, int dtype, int path,
-                     Plan &P, std::string &err)
+                     Plan &P, std::string &err, int max_run)
 {
+    if (max_run < 1) max_run = 1;
+    if (max_run > kMaxRunLen) max_run = kMaxRunLen;
     auto bad = [&](const std::string &m) { err = m; return QTM_EINVAL; };
     if (n < 1 || n > kMaxQubits) return bad("n_qubits out of range 1..30");
     if (n_gates < 0 || (n_gates > 0 && !gates)) return bad("bad gate array");
@@ -434,7 +436,7 @@ qtm_status make_plan(int n, const qtm_gate *gates, int n_gates, const qtm_zterm 
             if (is_rot(G.kind)) {
                 int q = G.q0;
                 int rid = open[q];
-                if (rid >= 0 && (int)run_gates[rid].size() < kMaxRunLen) {
+                if (rid >= 0 && (int)run_gates[rid].size() < max_run) {
                     run_gates[rid].push_back(g);
                 } else {
                     rid = (int)run_gates.size();

@@ -149,9 +149,10 @@ struct Plan {
 };
 
 // Build the plan (host only).  Returns QTM_OK or an error with `err` set.
+// max_run: most rotations fused into one run (the fusion width).
 qtm_status make_plan(int n, const qtm_gate *gates, int n_gates, const qtm_zterm *terms,
                      int n_terms, int n_obs, int n_weights, int n_inputs, int dtype, int path,
-                     Plan &out, std::string &err);
+                     Plan &out, std::string &err, int max_run = kMaxRunLen);
 
 // Per-sample cost model of a plan (bytes over the state, arithmetic).
 void plan_costs(const Plan &p, double &fwd_bytes, double &adj_bytes, double &fwd_flops,

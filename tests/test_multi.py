@@ -1,0 +1,108 @@
+"""Uneven batches (qtm_build_multi / qtm_multi_run): circuits of different
+qubit counts and depths in one persistent launch."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2404_06314_gb300 import capi, workloads as W
+
+
+def test_multi_offsets_and_config_host():
+    cs = W.workload_uneven(count=12)
+    mp = capi.MultiPlan(cs, batch=3)
+    ox = mp.offsets(capi.QTM_MULTI_X)
+    ow = mp.offsets(capi.QTM_MULTI_W)
+    oe = mp.offsets(capi.QTM_MULTI_E)
+    assert list(np.diff(ox)) == [3 * c.n_inputs for c in cs]
+    assert list(np.diff(ow)) == [c.n_weights for c in cs]
+    assert list(np.diff(oe)) == [3 * c.n_obs for c in cs]
+    mp.config = {"ctas_per_sm": 1, "order": 1, "fuse_width": 1}
+    assert mp.config == {"ctas_per_sm": 1, "order": 1, "fuse_width": 1}
+    with pytest.raises(capi.QtmError):
+        mp.config = {"ctas_per_sm": 0, "order": 0, "fuse_width": 1}
+
+
+def test_multi_rejects_invalid_circuit():
+    bad = W.Circuit(n=3, gates=[(W.RX, 5, -1, -1, -1, 1.0)], terms=[(1, 1.0, 0)], n_obs=1, n_weights=0,
+                    n_inputs=0)
+    with pytest.raises(capi.QtmError):
+        capi.MultiPlan([W.workload_4q(), bad], batch=1)
+
+
+def _inputs(cs, batch, seed):
+    rng = np.random.default_rng(seed)
+    xs = [rng.uniform(-np.pi, np.pi, size=(batch, c.n_inputs)).astype(np.float32).astype(np.float64) for c in cs]
+    ws = [rng.standard_normal(c.n_weights).astype(np.float32).astype(np.float64) for c in cs]
+    gs = [rng.standard_normal((batch, c.n_obs)).astype(np.float32).astype(np.float64) for c in cs]
+    return xs, ws, gs
+
+
+def _run(mp, cs, xs, ws, gs, graph=False):
+    x = mp.pack(xs, capi.QTM_MULTI_X)
+    w = mp.pack(ws, capi.QTM_MULTI_W)
+    g = mp.pack(gs, capi.QTM_MULTI_GE)
+    E, gx, gw = mp.empty(capi.QTM_MULTI_E), mp.empty(capi.QTM_MULTI_GX), mp.empty(capi.QTM_MULTI_GW)
+    mp.run(x, w, g, E, gx, gw, graph=graph)
+    B = mp.batch
+    return (mp.unpack(E, capi.QTM_MULTI_E, [(B, c.n_obs) for c in cs]),
+            mp.unpack(gx, capi.QTM_MULTI_GX, [(B, c.n_inputs) for c in cs]),
+            mp.unpack(gw, capi.QTM_MULTI_GW, [(c.n_weights,) for c in cs]), (x, w, g, E, gx, gw))
+
+
+def _check(cs, xs, ws, gs, Es, gxs, gws, tol=1e-5):
+    for c, x, w, g, E, gx, gw in zip(cs, xs, ws, gs, Es, gxs, gws):
+        Eo = oracle.forward(c, x, w, threads=0)
+        _, gxo, gwo = oracle.adjoint(c, g, x, w, threads=0)
+        assert np.abs(E - Eo).max() <= tol, (c.name, "E")
+        assert np.abs(gx - gxo).max() <= tol, (c.name, "gx")
+        scale = np.maximum(1.0, np.abs(gwo).sum(0))
+        assert np.all(np.abs(gw - gwo.sum(0)) <= tol * scale), (c.name, "gw")
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("fuse_width", [32, 3, 1])
+def test_multi_matches_oracle(fuse_width):
+    cs = W.workload_uneven(count=20, seed=77, n_lo=4, n_hi=15)
+    mp = capi.MultiPlan(cs, batch=2)
+    mp.config = {"ctas_per_sm": 2, "order": 0, "fuse_width": fuse_width}
+    xs, ws, gs = _inputs(cs, 2, 5)
+    Es, gxs, gws, _ = _run(mp, cs, xs, ws, gs)
+    _check(cs, xs, ws, gs, Es, gxs, gws)
+
+
+@pytest.mark.gpu
+def test_multi_graph_replay_and_16_qubits():
+    cs = W.workload_uneven(count=6, seed=9, n_lo=15, n_hi=16) + W.workload_uneven(count=6, seed=10, n_lo=6, n_hi=9)
+    mp = capi.MultiPlan(cs, batch=1)
+    xs, ws, gs = _inputs(cs, 1, 6)
+    Es, gxs, gws, bufs = _run(mp, cs, xs, ws, gs, graph=False)
+    _check(cs, xs, ws, gs, Es, gxs, gws)
+    x, w, g, E, gx, gw = bufs
+    for _ in range(3):   # captured once, replayed
+        mp.run(x, w, g, E, gx, gw, graph=True)
+    import torch
+    torch.cuda.synchronize()
+    E2 = mp.unpack(E, capi.QTM_MULTI_E, [(1, c.n_obs) for c in cs])
+    for a, b in zip(Es, E2):
+        assert np.array_equal(a, b)
+
+
+@pytest.mark.gpu
+def test_multi_tune_and_cache(tmp_path):
+    cs = W.workload_uneven(count=16, seed=11, n_lo=6, n_hi=13)
+    mp = capi.MultiPlan(cs, batch=1)
+    xs, ws, gs = _inputs(cs, 1, 7)
+    *_, bufs = _run(mp, cs, xs, ws, gs)
+    cache = str(tmp_path / "tune.jsonl")
+    cfg = mp.tune(*bufs, cache_path=cache)
+    assert cfg["ctas_per_sm"] in (1, 2) and cfg["order"] in (0, 1) and cfg["fuse_width"] in (1, 3, 32)
+    lines = [json.loads(l) for l in open(cache)]
+    assert len(lines) == 1 and lines[0]["fuse_width"] == cfg["fuse_width"]
+    mp2 = capi.MultiPlan(cs, batch=1)
+    assert mp2.tune(*bufs, cache_path=cache) == cfg          # cache hit: no new line
+    assert len(open(cache).readlines()) == 1
+    Es, gxs, gws, _ = _run(mp2, cs, xs, ws, gs)
+    _check(cs, xs, ws, gs, Es, gxs, gws)

@@ -267,6 +267,11 @@ qtm_status qtm_multi_tune(qtm_multi *multi, const void *x, const void *w, const 
                           void *expvals, void *grad_x, void *grad_w, void *stream,
                           const char *cache_path);
 
+/* Synchronise `stream`, then report the persistent kernel's self-checks:
+ * QTM_ETIMEOUT if a CTA ran past its 20 s deadline (it stops taking work),
+ * QTM_EINVAL if an index check failed; the status is cleared after reading. */
+qtm_status qtm_multi_sync(qtm_multi *multi, void *stream);
+
 qtm_status qtm_multi_get_config(const qtm_multi *multi, qtm_multi_config *cfg);
 qtm_status qtm_multi_set_config(qtm_multi *multi, const qtm_multi_config *cfg);
 qtm_status qtm_multi_destroy(qtm_multi *multi);

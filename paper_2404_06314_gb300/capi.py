@@ -307,7 +307,8 @@ def _multi_lib():
         L.qtm_multi_get_config.argtypes = [vp, P(qtm_multi_config)]
         L.qtm_multi_set_config.argtypes = [vp, P(qtm_multi_config)]
         L.qtm_multi_destroy.argtypes = [vp]
-        for f in ("qtm_build_multi", "qtm_multi_offsets", "qtm_multi_run", "qtm_multi_tune",
+        L.qtm_multi_sync.argtypes = [vp, vp]
+        for f in ("qtm_multi_sync", "qtm_build_multi", "qtm_multi_offsets", "qtm_multi_run", "qtm_multi_tune",
                   "qtm_multi_get_config", "qtm_multi_set_config", "qtm_multi_destroy"):
             getattr(L, f).restype = ctypes.c_int
         L._multi_ready = True
@@ -394,6 +395,13 @@ class MultiPlan:
                                         ctypes.c_void_p(s))
         if st != QTM_OK:
             raise QtmError(st, "qtm_multi_run")
+
+    def sync(self, stream=None):
+        import torch
+        s = (stream or torch.cuda.current_stream()).cuda_stream
+        st = _multi_lib().qtm_multi_sync(self.handle, ctypes.c_void_p(s))
+        if st != QTM_OK:
+            raise QtmError(st, "qtm_multi_sync")
 
     def tune(self, x, w, gE, E, gx, gw, cache_path=None, stream=None):
         import torch

@@ -62,11 +62,15 @@ struct MultiArgs {
     void *mats, *tabs, *state;
     double *Epart, *Gpart, *abar, *gwws;
     unsigned *counter;
+    unsigned *status;             // bit 0: deadline hit; bit 1: bad index (both skip work)
+    int n_circ, n_passes, n_ops_total, n_phases_total;
     // shared-memory layout bounds (max over all passes of all circuits)
     int max_slots, max_terms, max_M, max_ents, max_sq;
 };
 
 namespace {
+
+constexpr unsigned long long kMultiDeadlineNs = 20000000000ull;   // 20 s per CTA
 
 template <typename R>
 __device__ __forceinline__ TileJob make_job(const MultiArgs &m, const CircDev &cd, const PassDesc &pd,
@@ -154,14 +158,31 @@ __global__ void __launch_bounds__(256, MINB) k_multi(const MultiArgs m)
     const Layout L = make_layout(kMaxTileQubits, (int)sizeof(Cx<R>), true, m.max_slots, m.max_terms,
                                  m.max_M, m.max_sq, m.max_ents, 8, (int)sizeof(R));
     const TileSmem<R> S = carve<R>(smem, L);
+    const unsigned long long t_start = global_ns();
     for (;;) {
-        if (threadIdx.x == 0) s_item = (int)atomicAdd(m.counter, 1u);
+        if (threadIdx.x == 0) {
+            int it = (int)atomicAdd(m.counter, 1u);
+            if (global_ns() - t_start > kMultiDeadlineNs) {   // self-check: a run never takes this long
+                atomicOr(m.status, 1u);
+                it = m.n_items;
+            }
+            s_item = it;
+        }
         __syncthreads();
         const int item = s_item;
         __syncthreads();
-        if (item >= m.n_items) return;
+        if (item >= m.n_items || item < 0) return;
         const WorkItem wi = m.items[item];
+        if (wi.c < 0 || wi.c >= m.n_circ) {
+            if (threadIdx.x == 0) atomicOr(m.status, 2u);
+            continue;
+        }
         const CircDev cd = m.circ[wi.c];
+        if (cd.fwd_begin < 0 || cd.rev_begin + cd.n_rev > m.n_passes || cd.tiles < 1 || cd.tiles > (1 << 18) ||
+            wi.b < 0 || wi.b >= m.B) {
+            if (threadIdx.x == 0) atomicOr(m.status, 2u);
+            continue;
+        }
         const int b = wi.b;
         double *Epart_b = m.Epart + cd.Epart_off + (size_t)b * cd.tiles * cd.M;
         double *Gpart_b = m.Gpart + cd.Gpart_off + (size_t)b * cd.n_runs * cd.tiles * 3;
@@ -314,7 +335,7 @@ struct qtm_multi {
     void *dev_block = nullptr;      // all tables in one allocation
     void *d_ws = nullptr;           // workspace (mats, tabs, state)
     double *d_dbl = nullptr;        // Epart, Gpart, abar, gwws
-    unsigned *d_counter = nullptr;
+    unsigned *d_counter = nullptr;   // [0] work counter, [1] status
     MultiArgs args{};
     // graph cache
     cudaGraphExec_t gexec = nullptr;
@@ -486,7 +507,8 @@ qtm_status upload(qtm_multi *m)
     const size_t ws = csize * (size_t)(m->n_mats + m->n_tabs + m->n_state);
     const size_t nd = (size_t)(m->n_epart + m->n_gpart + m->n_abar + m->n_gwws);
     if (cudaMalloc(&m->d_ws, ws ? ws : 16) != cudaSuccess || cudaMalloc(&m->d_dbl, 8 * (nd ? nd : 1)) != cudaSuccess ||
-        cudaMalloc(&m->d_counter, sizeof(unsigned)) != cudaSuccess) {
+        cudaMalloc(&m->d_counter, 2 * sizeof(unsigned)) != cudaSuccess ||
+        cudaMemset(m->d_counter, 0, 2 * sizeof(unsigned)) != cudaSuccess) {
         release_device(m);
         m->err = "workspace allocation failed";
         return QTM_ENOMEM;
@@ -522,6 +544,11 @@ qtm_status upload(qtm_multi *m)
     a.abar = a.Gpart + m->n_gpart;
     a.gwws = a.abar + m->n_abar;
     a.counter = m->d_counter;
+    a.status = m->d_counter + 1;
+    a.n_circ = (int)m->circ.size();
+    a.n_passes = (int)m->passes.size();
+    a.n_ops_total = (int)m->ops.size();
+    a.n_phases_total = (int)m->phases.size();
     a.max_slots = m->max_slots; a.max_terms = m->max_terms; a.max_M = m->max_M;
     a.max_ents = m->max_ents; a.max_sq = m->max_sq;
     m->wcirc_dev = reinterpret_cast<const int *>(db + o_wcirc);
@@ -765,6 +792,21 @@ qtm_status qtm_multi_tune(qtm_multi *m, const void *x, const void *w, const void
     qtm_status st = apply_config(m, best);
     if (st == QTM_OK) cache_store(cache_path, sig, best, best_ms);
     return st;
+}
+
+// Synchronise `stream` and report the persistent kernel's self-checks:
+// QTM_ETIMEOUT if a CTA passed its deadline, QTM_EINVAL if an index check
+// failed (cleared after reading).
+qtm_status qtm_multi_sync(qtm_multi *m, void *stream)
+{
+    if (!m) return QTM_EINVAL;
+    if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess) return QTM_ECUDA;
+    if (!m->d_counter) return QTM_OK;
+    unsigned st = 0;
+    if (cudaMemcpy(&st, m->d_counter + 1, sizeof(unsigned), cudaMemcpyDeviceToHost) != cudaSuccess) return QTM_ECUDA;
+    if (!st) return QTM_OK;
+    cudaMemset(m->d_counter + 1, 0, sizeof(unsigned));
+    return (st & 1u) ? QTM_ETIMEOUT : QTM_EINVAL;
 }
 
 qtm_status qtm_multi_get_config(const qtm_multi *m, qtm_multi_config *cfg)

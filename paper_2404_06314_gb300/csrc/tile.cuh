@@ -504,10 +504,9 @@ __device__ __forceinline__ void run_phases(const TileJob &j, const TileSmem<R> &
     Cx<R> p[kRegs];
     Cx<R> q[kRegs];
     for (int phz = j.phase_begin; phz < j.phase_end; ++phz) {
-        if (!active) {   // threads beyond the tile's 2^(K-4) only keep the barriers
-            __syncthreads();
-            continue;
-        }
+        // threads beyond the tile's 2^(K-4) skip the work but reach the same
+        // barrier instruction at the end of the phase (never a second one)
+        if (active) {
         const DevPhase ph = j.phases[phz];
         const int lo = ph.lo;
         const uint32_t xt = ((uint32_t)tid & ((1u << lo) - 1u)) | (((uint32_t)tid >> lo) << (lo + 4));
@@ -659,6 +658,7 @@ __device__ __forceinline__ void run_phases(const TileJob &j, const TileSmem<R> &
             }
         }
         if (REV) lam_valid = true;
+        }
         __syncthreads();
     }
 }

@@ -260,6 +260,95 @@ def measure_gpu(name, steps, warmup, device, seed_offset=0, profile=True):
                 n_rev_pass=n_rev_pass, launches=launches)
 
 
+def measure_uneven(steps, device, count=256, seed_offset=0):
+    """Uneven batch: `count` circuits (n ~ U{6..16}, depth ~ U{2..10}), one
+    sample each, forward + adjoint.  The persistent kernel (autotuned, replayed
+    from a CUDA graph) against the same work as per-circuit launches."""
+    import numpy as np
+    import torch
+
+    from paper_2404_06314_gb300 import capi, workloads as W
+
+    cs = W.workload_uneven(seed=W.WORKLOAD_SEEDS["uneven"] + seed_offset, count=count)
+    rng = np.random.default_rng(W.WORKLOAD_SEEDS["uneven"] + 17)
+    xs = [rng.uniform(-np.pi, np.pi, size=(1, c.n_inputs)) for c in cs]
+    ws = [rng.standard_normal(c.n_weights) for c in cs]
+    gs = [rng.standard_normal((1, c.n_obs)) for c in cs]
+    mp = capi.MultiPlan(cs, batch=1)
+    x, w, g = mp.pack(xs, capi.QTM_MULTI_X), mp.pack(ws, capi.QTM_MULTI_W), mp.pack(gs, capi.QTM_MULTI_GE)
+    E, gx, gw = mp.empty(capi.QTM_MULTI_E), mp.empty(capi.QTM_MULTI_GX), mp.empty(capi.QTM_MULTI_GW)
+    t0 = time.perf_counter()
+    cfg = mp.tune(x, w, g, E, gx, gw)
+    tune_s = time.perf_counter() - t0
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=device)
+    for _ in range(3):
+        mp.run(x, w, g, E, gx, gw, graph=True)
+    mp.sync()
+    tot = 0.0
+    for _ in range(steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        mp.run(x, w, g, E, gx, gw, graph=True)
+        e1.record()
+        torch.cuda.synchronize()
+        tot += e0.elapsed_time(e1)
+    mp.sync()
+    graph_rate = count * steps / (tot / 1e3)
+    # the same work as separate per-circuit launches (plans built up front)
+    plans = [capi.Plan(c, dtype="c64") for c in cs]
+    tens = [(torch.tensor(a, dtype=torch.float32, device=device), torch.tensor(b, dtype=torch.float32, device=device),
+             torch.tensor(cg, dtype=torch.float32, device=device)) for a, b, cg in zip(xs, ws, gs)]
+
+    def per_circuit():
+        for p, (xx, ww, gg) in zip(plans, tens):
+            p.forward(xx, ww)
+            p.adjoint(gg, xx, ww)
+
+    per_circuit()
+    torch.cuda.synchronize()
+    k2 = max(2, steps // 4)
+    tot2 = 0.0
+    for _ in range(k2):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        per_circuit()
+        e1.record()
+        torch.cuda.synchronize()
+        tot2 += e0.elapsed_time(e1)
+    ns = [c.n for c in cs]
+    return {"value": graph_rate, "unit": "samples/s", "ms_per_step": tot / steps, "steps": steps,
+            "per_circuit_launches": {"value": count * k2 / (tot2 / 1e3), "unit": "samples/s",
+                                     "ms_per_step": tot2 / k2},
+            "config": {"workload": f"uneven: {count} circuits, n ~ U{{6..16}} (min {min(ns)}, max {max(ns)}), "
+                                   "depth ~ U{2..10}, one sample each, complex64, Z_i observables, fwd + adjoint",
+                       "launch": "one persistent kernel per step, replayed from a CUDA graph",
+                       "autotuned": cfg, "tune_seconds": tune_s}}
+
+
+def measure_training(device, steps=100):
+    """16-qubit training loop: QuantumModule + MSE + Adam, `steps` steps."""
+    import torch
+
+    from paper_2404_06314_gb300 import train as T
+
+    c, inp, y, mod, x, t = T.setup_qnn16(B=256, device=device)
+    T.train(mod, x, t, steps=3)            # warm-up
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    losses = T.train(mod, x, t, steps=steps)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    lc = losses.double().cpu().numpy()
+    return {"value": steps / (ms / 1e3), "unit": "steps/s", "samples_per_s": 256 * steps / (ms / 1e3),
+            "ms_per_step": ms / steps, "loss_first": float(lc[0]), "loss_last": float(lc[-1]),
+            "config": {"workload": "qnn16_l8_train: 16 qubits, 8 re-uploading layers + CZ ring, B=256, "
+                                   "MSE on sum_i <Z_i>, Adam lr 1e-2", "steps": steps}}
+
+
 def measure_e2e(name, steps, device, seed_offset=0):
     """End to end through the public API: pinned host inputs -> device,
     forward, adjoint, results -> pinned host, every step."""
@@ -356,6 +445,10 @@ def gpu_main(args):
             tot20 = float(t.item())
         n20 = (r20, tot20)
 
+    extra = {}
+    if args.workload == "qnn12" and not args.skip_extra:
+        extra["uneven"] = measure_uneven(max(3, args.steps // 4), device, seed_offset=rank)
+        extra["train16"] = measure_training(device)
     e2e = measure_e2e(args.workload, max(3, args.steps // 4), device, seed_offset=rank)
     if ws > 1:
         t = torch.tensor([e2e[0]], device=device, dtype=torch.float64)
@@ -400,6 +493,7 @@ def gpu_main(args):
                                           "fwd_state_bytes", "adj_state_bytes")},
             "gpu_launches": r20["launches"],
         }
+    line.update(extra)
     if not args.no_cpu_baseline:
         from paper_2404_06314_gb300 import workloads as W
         threads = os.cpu_count() or 1
@@ -460,6 +554,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="qnn12")
     ap.add_argument("--skip-n20", action="store_true")
+    ap.add_argument("--skip-extra", action="store_true", help="skip the uneven-batch and training lines")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle CPU work")
     args = ap.parse_args()

@@ -151,9 +151,12 @@ qtm_status qtm_adjoint(qtm_plan *plan, int B, const void *grad_expvals, const vo
                        const void *w, void *grad_x, void *grad_w, int flags, void *stream);
 
 /*
- * qtm_jacobian: full Jacobian J[b][m][g] = d<O_m>/d theta_g (device, plan real
- * type, [B][n_obs][n_gates], zero for CZ/CNOT): the (B, M, |Theta|) output of
- * Sec. II-B, one costate per observable.  Runs the forward itself.
+ * qtm_jacobian: full Jacobian J[b][m][g] = d<O_m>/d theta_g with respect to
+ * every gate angle (device, plan real type, [B][n_obs][n_gates], zero for
+ * CZ/CNOT): the (B, M, |Theta|) output of Sec. II-B, one costate per
+ * observable (the reverse passes run once per observable with cotangent
+ * e_m).  Runs the forward itself; fused plans only (QTM_EUNSUPPORTED on the
+ * naive path).  Leaves no stored forward state behind.
  */
 qtm_status qtm_jacobian(qtm_plan *plan, int B, const void *x, const void *w, void *jac,
                         void *stream);

@@ -275,6 +275,19 @@ class Plan:
         self._raise(st, "qtm_adjoint")
         return gx, gw
 
+    def jacobian(self, x, w, out=None, stream=None):
+        """J[b, m, g] = d<O_m>/d theta_g for every gate angle (zero for CZ/CNOT)."""
+        import torch
+        c = self.circuit
+        B = x.shape[0]
+        if out is None:
+            out = torch.empty((B, c.n_obs, c.n_gates), dtype=self.real_dtype(), device=x.device)
+        st = qtm_jacobian(self.handle, B, self._check(x, (B, c.n_inputs), "x"),
+                          self._check(w, (c.n_weights,), "w"),
+                          self._check(out, (B, c.n_obs, c.n_gates), "jac"), self._stream(stream))
+        self._raise(st, "qtm_jacobian")
+        return out
+
     def sync(self, stream=None):
         self._raise(qtm_sync(self.handle, self._stream(stream)), "qtm_sync")
 

@@ -53,6 +53,8 @@ struct qtm_plan {
     void *d_phi = nullptr, *d_lam = nullptr, *d_Escratch = nullptr;
     double *d_Epart = nullptr, *d_Gpart = nullptr, *d_abar = nullptr, *d_gw_ws = nullptr;
     void *d_mats = nullptr, *d_tabs = nullptr;
+    void *d_onehot = nullptr;          // [B][M] cotangent e_m (qtm_jacobian)
+    int32_t *d_gate_of_rot = nullptr;  // rotation id -> gate index
     std::vector<CUtensorMap> tm_fwd, tm_rev_phi, tm_rev_lam;
     std::vector<TmGeom> g_fwd, g_rev;
     std::vector<size_t> smem_fwd, smem_rev;
@@ -99,11 +101,12 @@ cudaError_t upload(T **dst, const std::vector<T> &v)
 
 void free_tables(qtm_plan *p)
 {
-    void *ptrs[] = {p->d_ops, p->d_diag, p->d_amap, p->d_phases, p->d_slot_runs, p->d_runs, p->d_rots,
+    void *ptrs[] = {p->d_gate_of_rot, p->d_ops, p->d_diag, p->d_amap, p->d_phases, p->d_slot_runs, p->d_runs, p->d_rots,
                     p->d_prefix_run_of_q, p->d_prefix_ents, p->d_terms, p->d_w_ptr,
                     p->d_w_rots, p->d_x_ptr, p->d_x_rots, p->d_status};
     for (void *q : ptrs)
         if (q) cudaFree(q);
+    p->d_gate_of_rot = nullptr;
     p->d_ops = nullptr; p->d_diag = nullptr; p->d_amap = nullptr; p->d_phases = nullptr; p->d_slot_runs = nullptr; p->d_runs = nullptr;
     p->d_rots = nullptr; p->d_prefix_run_of_q = nullptr; p->d_prefix_ents = nullptr;
     p->d_terms = nullptr; p->d_w_ptr = p->d_w_rots = p->d_x_ptr = p->d_x_rots = nullptr;
@@ -113,10 +116,10 @@ void free_tables(qtm_plan *p)
 void free_workspace(qtm_plan *p)
 {
     void *ptrs[] = {p->d_phi, p->d_lam, p->d_Escratch, p->d_Epart, p->d_Gpart, p->d_abar, p->d_gw_ws,
-                    p->d_mats, p->d_tabs};
+                    p->d_mats, p->d_tabs, p->d_onehot};
     for (void *q : ptrs)
         if (q) cudaFree(q);
-    p->d_phi = p->d_lam = p->d_Escratch = p->d_mats = p->d_tabs = nullptr;
+    p->d_phi = p->d_lam = p->d_Escratch = p->d_mats = p->d_tabs = p->d_onehot = nullptr;
     p->d_Epart = p->d_Gpart = p->d_abar = p->d_gw_ws = nullptr;
     p->cap_B = 0;
     p->fwd_valid = false;
@@ -225,6 +228,11 @@ qtm_status ensure_device(qtm_plan *p)
     UP(p->d_x_ptr, P.x_ptr);
     UP(p->d_x_rots, P.x_rots);
     UP(p->d_status, zero);
+    {
+        std::vector<int32_t> gor(P.rots.size());
+        for (size_t r = 0; r < P.rots.size(); ++r) gor[r] = P.rots[r].gate;
+        UP(p->d_gate_of_rot, gor);
+    }
 #undef UP
     p->device = dev;
     return QTM_OK;
@@ -256,6 +264,7 @@ qtm_status ensure_workspace(qtm_plan *p, int B)
     AL(p->d_gw_ws, sizeof(double) * (size_t)B * (P.n_weights ? P.n_weights : 1));
     AL(p->d_mats, csize * 4 * (size_t)B * runs);
     AL(p->d_tabs, csize * 16 * (size_t)B * ((P.state_qubits + 3) / 4));
+    AL(p->d_onehot, rsize * (size_t)B * P.n_obs);
 #undef AL
     p->cap_B = B;
     if (P.path == QTM_PATH_FUSED) {
@@ -597,8 +606,45 @@ qtm_status qtm_adjoint(qtm_plan *p, int B, const void *gE, const void *x, const 
 
 qtm_status qtm_jacobian(qtm_plan *p, int B, const void *x, const void *w, void *jac, void *stream)
 {
-    (void)B; (void)x; (void)w; (void)jac; (void)stream;
-    return fail(p, QTM_EUNSUPPORTED, "qtm_jacobian: not built yet");
+    if (!p) return QTM_EINVAL;
+    const Plan &P = p->P;
+    if (B < 1) return fail(p, QTM_EINVAL, "B must be >= 1");
+    if ((P.n_inputs > 0 && !x) || (P.n_weights > 0 && !w) || !jac) return fail(p, QTM_EINVAL, "null pointer");
+    if (P.path != QTM_PATH_FUSED) return fail(p, QTM_EUNSUPPORTED, "qtm_jacobian runs on the fused path");
+    qtm_status st = ensure_device(p);
+    if (st != QTM_OK) return st;
+    st = ensure_workspace(p, B);
+    if (st != QTM_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t rsize = elem_bytes(P.dtype) / 2;
+    const int G = (int)P.gates.size();
+    cudaError_t e = cudaMemsetAsync(jac, 0, rsize * (size_t)B * P.n_obs * (G > 0 ? G : 1), s);
+    if (e != cudaSuccess) return cuda_fail(p, e, "jacobian clear");
+    bool consumes = false;
+    for (const auto &pd : P.rev) consumes |= pd.store_phi != 0;
+    p->fwd_valid = false;
+    prof_begin_call(p, 1, s);
+    // one costate per observable (Sec. II-B's (B, M, |Theta|) output): reverse
+    // passes with cotangent e_m, each rotation's angle gradient scattered to J
+    for (int m = 0; m < P.n_obs; ++m) {
+        if (m == 0 || consumes) {
+            st = run_forward_passes(p, B, x, w, s);
+            if (st != QTM_OK) return st;
+        }
+        e = launch_onehot(P.dtype, p->d_onehot, B, P.n_obs, m, s);
+        if (e != cudaSuccess) return cuda_fail(p, e, "one-hot cotangent");
+        for (size_t i = 0; i < P.rev.size(); ++i) {
+            PassArgs a = pass_args(p, P.rev[i], p->g_rev[i], p->smem_rev[i], B, x, w, p->d_onehot);
+            e = launch_pass(P.dtype, true, a, p->tm_rev_phi[i], p->tm_rev_lam[i], s);
+            if (e != cudaSuccess) return cuda_fail(p, e, "reverse pass launch");
+        }
+        FinalizeArgs f = finalize_args(p, B, x, w);
+        e = launch_grad_finalize(P.dtype, f, s);
+        if (e != cudaSuccess) return cuda_fail(p, e, "gradient finalize");
+        e = launch_jac_scatter(P.dtype, p->d_abar, p->d_gate_of_rot, (int)P.rots.size(), B, P.n_obs, m, G, jac, s);
+        if (e != cudaSuccess) return cuda_fail(p, e, "jacobian scatter");
+    }
+    return QTM_OK;
 }
 
 qtm_status qtm_sync(qtm_plan *p, void *stream)

@@ -89,6 +89,10 @@ cudaError_t launch_grad_finalize(int dtype, const FinalizeArgs &f, cudaStream_t 
 cudaError_t launch_gw_reduce(int dtype, const double *gw_ws, int B, int P, void *gw,
                              cudaStream_t s);
 
+cudaError_t launch_onehot(int dtype, void *gE, int B, int M, int m, cudaStream_t s);
+cudaError_t launch_jac_scatter(int dtype, const double *abar, const int32_t *gate_of_rot, int n_rots, int B,
+                               int M, int m, int G, void *J, cudaStream_t s);
+
 // naive one-gate-per-kernel path
 struct NaiveArgs {
     int n, B, n_in, M, n_terms, n_rots, P;

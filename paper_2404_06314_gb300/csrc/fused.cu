@@ -158,7 +158,46 @@ __global__ void k_gw_reduce(const double *gw_ws, int B, int P, R *gw)
     if (threadIdx.x == 0) gw[j] = (R)red[0];
 }
 
+// cotangent e_m: gE[b][k] = (k == m)
+template <typename R>
+__global__ void k_onehot(R *gE, int B, int M, int m)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < B * M) gE[i] = (i % M) == m ? (R)1 : (R)0;
+}
+
+// J[b][m][gate_of_rot[r]] = abar[b][r]  (gates that are not rotations stay 0)
+template <typename R>
+__global__ void k_jac_scatter(const double *abar, const int32_t *gate_of_rot, int n_rots, int B, int M,
+                              int m, int G, R *J)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= B * n_rots) return;
+    const int b = i / n_rots, r = i % n_rots;
+    J[((size_t)b * M + m) * G + gate_of_rot[r]] = (R)abar[(size_t)b * n_rots + r];
+}
+
 }  // namespace
+
+cudaError_t launch_onehot(int dtype, void *gE, int B, int M, int m, cudaStream_t s)
+{
+    const int n = B * M, blk = 256, grd = (n + blk - 1) / blk;
+    if (dtype == QTM_C128) k_onehot<double><<<grd, blk, 0, s>>>(static_cast<double *>(gE), B, M, m);
+    else k_onehot<float><<<grd, blk, 0, s>>>(static_cast<float *>(gE), B, M, m);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_jac_scatter(int dtype, const double *abar, const int32_t *gate_of_rot, int n_rots, int B,
+                               int M, int m, int G, void *J, cudaStream_t s)
+{
+    if (n_rots <= 0) return cudaSuccess;
+    const int n = B * n_rots, blk = 256, grd = (n + blk - 1) / blk;
+    if (dtype == QTM_C128)
+        k_jac_scatter<double><<<grd, blk, 0, s>>>(abar, gate_of_rot, n_rots, B, M, m, G, static_cast<double *>(J));
+    else
+        k_jac_scatter<float><<<grd, blk, 0, s>>>(abar, gate_of_rot, n_rots, B, M, m, G, static_cast<float *>(J));
+    return cudaGetLastError();
+}
 
 size_t pass_smem_bytes(int K, int dtype, bool reverse, int nslots, int n_terms, int M,
                        int state_qubits, int n_prefix_ents)

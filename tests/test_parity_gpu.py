@@ -187,3 +187,35 @@ def test_full_20q_batch_sampled():
     assert_close(gw[rows], gwo, 1e-5, "20q full gw")
     # property at any size: |E| <= sum |c_t|
     assert np.all(np.abs(E) <= 1.0 + 1e-5)
+
+
+# ---- full Jacobian (one costate per observable) -----------------------------------
+
+@pytest.mark.parametrize("n,dtype", [(5, "c64"), (5, "c128"), (13, "c64"), (9, "c64")])
+def test_jacobian_matches_oracle(n, dtype):
+    import torch
+    rng = np.random.default_rng(300 + n)
+    c = P.rand_small_circuit(rng, n, G=5 * n + 6, n_obs=3)
+    plan = capi.Plan(c, dtype=dtype)
+    inp = W.make_inputs(c, 3, 8, real_dtype=np.float32 if dtype == "c64" else np.float64)
+    rd = plan.real_dtype()
+    x = torch.tensor(inp.x, dtype=rd, device="cuda")
+    w = torch.tensor(inp.w, dtype=rd, device="cuda")
+    J = plan.jacobian(x, w)
+    plan.sync()
+    Jo = oracle.jacobian(c, inp.x, inp.w, threads=0)
+    assert_close(J.double().cpu().numpy(), Jo, TOL[dtype] if dtype == "c64" else 1e-11, f"J n={n} {dtype}")
+
+
+def test_jacobian_paper_workload_tab1_shape():
+    """Tab. I's setting: 12 qubits, depth 3, 168 parameters, several single-qubit Z observables."""
+    import torch
+    c = W.jerbi_ansatz(12, 3, terms=W.z_each(12))
+    plan = capi.Plan(c, dtype="c64")
+    inp = W.make_inputs(c, 2, 9, real_dtype=np.float32)
+    x = torch.tensor(inp.x, dtype=torch.float32, device="cuda")
+    w = torch.tensor(inp.w, dtype=torch.float32, device="cuda")
+    J = plan.jacobian(x, w).double().cpu().numpy()
+    Jo = oracle.jacobian(c, inp.x, inp.w, threads=0)
+    assert J.shape == (2, 12, c.n_gates)
+    assert_close(J, Jo, 1e-5, "jacobian 12q depth 3")

@@ -149,7 +149,7 @@ def roofline(r, peaks, peak_src):
                "frac": hbm / hbm_peak, "peak_source": f"{peak_src} hbm_gbs (burst copy)"}
     main, other = (alu_obj, hbm_obj) if alu_obj["frac"] >= hbm_obj["frac"] else (hbm_obj, alu_obj)
     main = dict(main)
-    main.update({"kernel": "k_pass<float, reverse>", "traffic": None,
+    main.update({"kernel": KERNEL_LABEL[r["kernels"]], "traffic": None,
                  "launch_ms": t * 1e3, "launches_timed": n,
                  "work_per_launch": {"flop": flops, "state_bytes": bytes_},
                  "other": {k: other[k] for k in ("bound", "achieved", "peak", "unit", "frac")}})
@@ -191,7 +191,19 @@ def oracle_rate(c, inp_full, budget_s: float, threads: int):
 # GPU measurement
 # ------------------------------------------------------------------------------
 
-def measure_gpu(name, steps, warmup, device, seed_offset=0, profile=True):
+KERNEL_LABEL = {"specialised": "qtm_gen_pass (plan-specialised pass kernel, NVRTC), reverse",
+                "general": "k_pass<float, reverse> (general pass kernel)"}
+
+
+def prepare(plan, kernels):
+    """Load the plan's specialised pass kernels unless the general kernel is asked for."""
+    if kernels == "specialised":
+        plan.compile()
+        assert plan.compiled_passes() > 0, "no specialised pass kernel loaded"
+    return plan
+
+
+def measure_gpu(name, steps, warmup, device, seed_offset=0, profile=True, kernels="specialised"):
     import numpy as np
     import torch
 
@@ -200,7 +212,7 @@ def measure_gpu(name, steps, warmup, device, seed_offset=0, profile=True):
     cfg = WORKLOADS[name]
     c = getattr(W, cfg["builder"])()
     B = cfg["B"]
-    plan = capi.Plan(c, dtype=cfg["dtype"], path="fused")
+    plan = prepare(capi.Plan(c, dtype=cfg["dtype"], path="fused"), kernels)
     rd = plan.real_dtype()
     inp = W.make_inputs(c, B, W.WORKLOAD_SEEDS[c.name] + seed_offset,
                         real_dtype=np.float32 if rd == torch.float32 else np.float64)
@@ -255,7 +267,7 @@ def measure_gpu(name, steps, warmup, device, seed_offset=0, profile=True):
     lib.qtm_set_profiling(plan.handle, 0)
     plan.sync()
     info = plan.info
-    return dict(c=c, B=B, plan=plan, inp=inp, step_ms=step_ms, info=info,
+    return dict(c=c, B=B, plan=plan, inp=inp, step_ms=step_ms, info=info, kernels=kernels,
                 pass_fwd_ms=pass_fwd_ms, pass_rev_ms=pass_rev_ms, n_fwd_pass=n_fwd_pass,
                 n_rev_pass=n_rev_pass, launches=launches)
 
@@ -349,7 +361,7 @@ def measure_training(device, steps=100):
                                    "MSE on sum_i <Z_i>, Adam lr 1e-2", "steps": steps}}
 
 
-def measure_e2e(name, steps, device, seed_offset=0):
+def measure_e2e(name, steps, device, seed_offset=0, kernels="specialised"):
     """End to end through the public API: pinned host inputs -> device,
     forward, adjoint, results -> pinned host, every step."""
     import numpy as np
@@ -360,7 +372,7 @@ def measure_e2e(name, steps, device, seed_offset=0):
     cfg = WORKLOADS[name]
     c = getattr(W, cfg["builder"])()
     B = cfg["B"]
-    plan = capi.Plan(c, dtype=cfg["dtype"], path="fused")
+    plan = prepare(capi.Plan(c, dtype=cfg["dtype"], path="fused"), kernels)
     rd = plan.real_dtype()
     inp = W.make_inputs(c, B, W.WORKLOAD_SEEDS[c.name] + seed_offset,
                         real_dtype=np.float32 if rd == torch.float32 else np.float64)
@@ -423,7 +435,7 @@ def gpu_main(args):
         dist.barrier()
     torch.cuda.synchronize()
     sampler.mark("t0")
-    r12 = measure_gpu(args.workload, args.steps, args.warmup, device, seed_offset=rank)
+    r12 = measure_gpu(args.workload, args.steps, args.warmup, device, seed_offset=rank, kernels=args.kernels)
     torch.cuda.synchronize()
     sampler.mark("t1")
     total_ms = sum(r12["step_ms"])
@@ -437,7 +449,8 @@ def gpu_main(args):
 
     n20 = None
     if args.workload == "qnn12" and not args.skip_n20:
-        r20 = measure_gpu("qnn20", max(3, args.steps // 4), args.warmup, device, seed_offset=rank)
+        r20 = measure_gpu("qnn20", max(3, args.steps // 4), args.warmup, device, seed_offset=rank,
+                          kernels=args.kernels)
         tot20 = sum(r20["step_ms"])
         if ws > 1:
             t = torch.tensor([tot20], device=device, dtype=torch.float64)
@@ -449,7 +462,7 @@ def gpu_main(args):
     if args.workload == "qnn12" and not args.skip_extra:
         extra["uneven"] = measure_uneven(max(3, args.steps // 4), device, seed_offset=rank)
         extra["train16"] = measure_training(device)
-    e2e = measure_e2e(args.workload, max(3, args.steps // 4), device, seed_offset=rank)
+    e2e = measure_e2e(args.workload, max(3, args.steps // 4), device, seed_offset=rank, kernels=args.kernels)
     if ws > 1:
         t = torch.tensor([e2e[0]], device=device, dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MIN)
@@ -470,7 +483,7 @@ def gpu_main(args):
         "data": "synthetic (seeded x ~ U[-pi,pi], w ~ N(0,1), cotangents ~ N(0,1))",
         "config": {"workload": cfgd["desc"], "global_batch": B * ws, "per_gpu_batch": B,
                    "path": cfgd["path_desc"], "l2": "flushed between steps (256 MiB write)",
-                   "parallelism": f"batch shards x{ws}"},
+                   "parallelism": f"batch shards x{ws}", "pass_kernels": args.kernels},
         "roofline": roofline(r12, peaks, peak_src),
         "gpu_launches": r12["launches"],
         "clocks": clocks,
@@ -554,6 +567,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="qnn12")
     ap.add_argument("--skip-n20", action="store_true")
+    ap.add_argument("--kernels", choices=["specialised", "general"], default="specialised",
+                    help="plan-specialised pass kernels (qtm_compile) or the general pass kernel")
     ap.add_argument("--skip-extra", action="store_true", help="skip the uneven-batch and training lines")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle CPU work")

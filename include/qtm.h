@@ -279,6 +279,21 @@ qtm_status qtm_multi_get_config(const qtm_multi *multi, qtm_multi_config *cfg);
 qtm_status qtm_multi_set_config(qtm_multi *multi, const qtm_multi_config *cfg);
 qtm_status qtm_multi_destroy(qtm_multi *multi);
 
+/* qtm_compile: specialise the plan's pass kernels.  The schedule is fixed
+ * once a plan is built, so every register position, table slot, CZ sign
+ * pattern and CNOT form of each pass is written out as CUDA source, compiled
+ * with NVRTC for sm_103a (compiled images are cached on disk under
+ * $QTM_JIT_CACHE, default /tmp/qtm_jit_cache) and loaded on the current
+ * device; later qtm_forward / qtm_adjoint / qtm_jacobian calls on that device
+ * launch them in place of the general pass kernel.  Applies to complex64
+ * passes with tiles of >= 9 qubits.  flags: 0.  QTM_EUNSUPPORTED when NVRTC
+ * is unavailable (the plan keeps the general kernels). */
+qtm_status qtm_compile(qtm_plan *plan, int flags);
+
+/* Number of specialised pass kernels loaded for the current device (0 before
+ * qtm_compile, or on another device). */
+int qtm_compiled_passes(const qtm_plan *plan);
+
 /* Synchronise `stream`, then report (and clear) any status a kernel of this
  * plan recorded on the device: QTM_ETIMEOUT if a bounded wait gave up. */
 qtm_status qtm_sync(qtm_plan *plan, void *stream);

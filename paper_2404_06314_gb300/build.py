@@ -20,7 +20,28 @@ LIB = os.path.join(HERE, "libqtm.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU_SOURCES = ["capi.cu", "fused.cu", "naive.cu", "noalloc.cu", "multi.cu"]
-CPP_SOURCES = ["plan.cpp", "emulate.cpp"]
+CPP_SOURCES = ["plan.cpp", "emulate.cpp", "jit.cpp"]
+# device headers embedded as the prelude of run-time generated kernels (NVRTC)
+PRELUDE_HEADERS = ["pod.h", "finalize_math.h", "tile.cuh"]
+
+
+def _write_prelude() -> str:
+    parts = []
+    for h in PRELUDE_HEADERS:
+        for line in open(os.path.join(CSRC, h)):
+            t = line.strip()
+            if t == "#pragma once" or (t.startswith("#include \"") and t.endswith("\"")):
+                continue
+            parts.append(line)
+    text = "".join(parts)
+    assert ")QTMJIT\"" not in text
+    out = os.path.join(BUILD, "jit_prelude.cpp")
+    src = ("namespace qtm {\nextern const char *const kJitPrelude;\nconst char *const kJitPrelude = R\"QTMJIT(" +
+           text + ")QTMJIT\";\n}\n")
+    if not os.path.exists(out) or open(out).read() != src:
+        with open(out, "w") as f:
+            f.write(src)
+    return out
 
 
 def _nvcc() -> str:
@@ -56,10 +77,12 @@ def build(force: bool = False, verbose: bool = False) -> str:
         cmd = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
                "-Xcompiler", "-Wall", *ptxas_v, "-I", INCLUDE, "-c", os.path.join(CSRC, f), "-o", obj]
         jobs.append((cmd, obj))
-    for f in CPP_SOURCES:
-        obj = os.path.join(BUILD, f + ".o")
-        cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-Wall", "-I", INCLUDE, "-I", cuda_inc, "-c",
-               os.path.join(CSRC, f), "-o", obj]
+    prelude = _write_prelude()
+    for f in CPP_SOURCES + [prelude]:
+        src = f if os.path.isabs(f) else os.path.join(CSRC, f)
+        obj = os.path.join(BUILD, os.path.basename(f) + ".o")
+        cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-Wall", "-I", INCLUDE, "-I", CSRC, "-I", cuda_inc, "-c",
+               src, "-o", obj]
         jobs.append((cmd, obj))
 
     def run(job):
@@ -77,7 +100,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         if r.returncode != 0:
             raise RuntimeError("compile failed: " + " ".join(cmd))
     tmp = LIB + f".tmp{os.getpid()}"
-    link = [nvcc, *ARCH, "-shared", "-o", tmp] + [o for _, o in jobs]
+    link = [nvcc, *ARCH, "-shared", "-o", tmp] + [o for _, o in jobs] + ["-ldl"]
     r = subprocess.run(link, capture_output=True, text=True)
     if r.returncode != 0:
         print(r.stderr, file=sys.stderr)

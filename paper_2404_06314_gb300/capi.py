@@ -86,6 +86,14 @@ def lib(build_if_missing: bool = True):
         L.qtm_debug_describe.argtypes = [vp]
         L.qtm_debug_describe.restype = ctypes.c_char_p
         L.qtm_debug_emulate.argtypes = [vp, i, vp, vp, vp, vp, vp, vp]
+        L.qtm_compile.argtypes = [vp, i]
+        L.qtm_compile.restype = ctypes.c_int
+        L.qtm_compiled_passes.argtypes = [vp]
+        L.qtm_compiled_passes.restype = ctypes.c_int
+        L.qtm_debug_jit_source.argtypes = [vp, i, i]
+        L.qtm_debug_jit_source.restype = ctypes.c_char_p
+        L.qtm_debug_jit_compile.argtypes = [vp]
+        L.qtm_debug_jit_compile.restype = ctypes.c_int
         _LIB = L
     return _LIB
 
@@ -274,6 +282,21 @@ class Plan:
                          flags, self._stream(stream))
         self._raise(st, "qtm_adjoint")
         return gx, gw
+
+    def compile(self):
+        """Specialise and load this plan's pass kernels (qtm_compile)."""
+        self._raise(lib().qtm_compile(self.handle, 0), "qtm_compile")
+        return self
+
+    def compiled_passes(self) -> int:
+        return int(lib().qtm_compiled_passes(self.handle))
+
+    def jit_source(self, which: int, index: int) -> str:
+        return lib().qtm_debug_jit_source(self.handle, int(which), int(index)).decode()
+
+    def jit_compile_check(self):
+        """Compile every specialised pass with NVRTC, host only (no load)."""
+        self._raise(lib().qtm_debug_jit_compile(self.handle), "qtm_debug_jit_compile")
 
     def jacobian(self, x, w, out=None, stream=None):
         """J[b, m, g] = d<O_m>/d theta_g for every gate angle (zero for CZ/CNOT)."""

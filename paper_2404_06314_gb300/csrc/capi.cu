@@ -12,7 +12,10 @@
 #include "../../include/qtm.h"
 #include "../../include/qtm_debug.h"
 #include "device.h"
+#include "jit.h"
 #include "plan.h"
+
+#include <thread>
 
 namespace qtm {
 qtm_status emulate_plan(const Plan &P, int B, const double *x, const double *w, const double *gE,
@@ -65,6 +68,10 @@ struct qtm_plan {
     const void *fwd_x = nullptr, *fwd_w = nullptr;
     void *fwd_stream = nullptr;
     std::string describe_cache;
+    // run-time specialised pass kernels (qtm_compile)
+    std::vector<JitKernel> jit_fwd, jit_rev;
+    int jit_device = -1;
+    std::string jit_src_cache;
     // profiling: events around each launch of the last forward / adjoint
     bool profiling = false;
     struct Rec { cudaEvent_t a, b; int kind; };
@@ -389,7 +396,9 @@ qtm_status run_forward_passes(qtm_plan *p, int B, const void *x, const void *w, 
     for (size_t i = 0; i < P.fwd.size(); ++i) {
         PassArgs a = pass_args(p, P.fwd[i], p->g_fwd[i], p->smem_fwd[i], B, x, w, nullptr);
         ProfScope ps(p, 0);
-        cudaError_t e = launch_pass(P.dtype, false, a, p->tm_fwd[i], p->tm_fwd[i], s);
+        cudaError_t e = (p->jit_device == p->device && i < p->jit_fwd.size() && p->jit_fwd[i].fn)
+                            ? jit_launch(p->jit_fwd[i], a, p->tm_fwd[i], p->tm_fwd[i], s)
+                            : launch_pass(P.dtype, false, a, p->tm_fwd[i], p->tm_fwd[i], s);
         if (e != cudaSuccess) return cuda_fail(p, e, "forward pass launch");
     }
     return QTM_OK;
@@ -581,7 +590,9 @@ qtm_status qtm_adjoint(qtm_plan *p, int B, const void *gE, const void *x, const 
         PassArgs a = pass_args(p, P.rev[i], p->g_rev[i], p->smem_rev[i], B, x, w, gE);
         if (P.rev[i].store_phi) consumes = true;
         ProfScope ps(p, 0);
-        e = launch_pass(P.dtype, true, a, p->tm_rev_phi[i], p->tm_rev_lam[i], s);
+        e = (p->jit_device == p->device && i < p->jit_rev.size() && p->jit_rev[i].fn)
+                ? jit_launch(p->jit_rev[i], a, p->tm_rev_phi[i], p->tm_rev_lam[i], s)
+                : launch_pass(P.dtype, true, a, p->tm_rev_phi[i], p->tm_rev_lam[i], s);
         if (e != cudaSuccess) return cuda_fail(p, e, "reverse pass launch");
     }
     FinalizeArgs f = finalize_args(p, B, x, w);
@@ -635,7 +646,9 @@ qtm_status qtm_jacobian(qtm_plan *p, int B, const void *x, const void *w, void *
         if (e != cudaSuccess) return cuda_fail(p, e, "one-hot cotangent");
         for (size_t i = 0; i < P.rev.size(); ++i) {
             PassArgs a = pass_args(p, P.rev[i], p->g_rev[i], p->smem_rev[i], B, x, w, p->d_onehot);
-            e = launch_pass(P.dtype, true, a, p->tm_rev_phi[i], p->tm_rev_lam[i], s);
+            e = (p->jit_device == p->device && i < p->jit_rev.size() && p->jit_rev[i].fn)
+                    ? jit_launch(p->jit_rev[i], a, p->tm_rev_phi[i], p->tm_rev_lam[i], s)
+                    : launch_pass(P.dtype, true, a, p->tm_rev_phi[i], p->tm_rev_lam[i], s);
             if (e != cudaSuccess) return cuda_fail(p, e, "reverse pass launch");
         }
         FinalizeArgs f = finalize_args(p, B, x, w);
@@ -645,6 +658,95 @@ qtm_status qtm_jacobian(qtm_plan *p, int B, const void *x, const void *w, void *
         if (e != cudaSuccess) return cuda_fail(p, e, "jacobian scatter");
     }
     return QTM_OK;
+}
+
+namespace {
+
+// Generate and compile every eligible pass (host only; NVRTC, no device).
+qtm_status compile_all(qtm_plan *p, std::vector<std::vector<char>> &fwd_bin, std::vector<std::vector<char>> &rev_bin)
+{
+    const Plan &P = p->P;
+    if (P.path != QTM_PATH_FUSED) return fail(p, QTM_EUNSUPPORTED, "specialised kernels exist for fused plans");
+    if (!jit_nvrtc_available()) return fail(p, QTM_EUNSUPPORTED, "NVRTC not found");
+    struct Job { const PassDesc *pd; std::vector<char> *out; int minb; };
+    std::vector<Job> jobs;
+    fwd_bin.assign(P.fwd.size(), {});
+    rev_bin.assign(P.rev.size(), {});
+    for (size_t i = 0; i < P.fwd.size(); ++i)
+        if (jit_eligible(P, P.fwd[i])) jobs.push_back({&P.fwd[i], &fwd_bin[i], 3});
+    for (size_t i = 0; i < P.rev.size(); ++i)
+        if (jit_eligible(P, P.rev[i])) jobs.push_back({&P.rev[i], &rev_bin[i], 2});
+    std::vector<std::string> logs(jobs.size());
+    std::vector<char> ok(jobs.size(), 0);
+    std::vector<std::thread> th;
+    for (size_t k = 0; k < jobs.size(); ++k)
+        th.emplace_back([&, k] {
+            ok[k] = jit_compile(jit_source(P, *jobs[k].pd, jobs[k].minb), *jobs[k].out, logs[k]) ? 1 : 0;
+        });
+    for (auto &t : th) t.join();
+    for (size_t k = 0; k < jobs.size(); ++k)
+        if (!ok[k]) return fail(p, QTM_EINVAL, "generated kernel failed to compile: " + logs[k].substr(0, 4000));
+    return QTM_OK;
+}
+
+}  // namespace
+
+qtm_status qtm_compile(qtm_plan *p, int flags)
+{
+    if (!p) return QTM_EINVAL;
+    if (flags != 0) return fail(p, QTM_EINVAL, "unknown flags");
+    if (!jit_available()) return fail(p, QTM_EUNSUPPORTED, "NVRTC or driver entry points not available");
+    qtm_status st = ensure_device(p);
+    if (st != QTM_OK) return st;
+    std::vector<std::vector<char>> fb, rb;
+    st = compile_all(p, fb, rb);
+    if (st != QTM_OK) return st;
+    for (auto *v : {&p->jit_fwd, &p->jit_rev})
+        for (auto &k : *v) jit_unload(k);
+    const Plan &P = p->P;
+    p->jit_fwd.assign(P.fwd.size(), JitKernel{});
+    p->jit_rev.assign(P.rev.size(), JitKernel{});
+    std::string err;
+    for (size_t i = 0; i < P.fwd.size(); ++i)
+        if (!fb[i].empty() && !jit_load(fb[i], (int)p->smem_fwd[i], p->jit_fwd[i], err))
+            return fail(p, QTM_ECUDA, err);
+    for (size_t i = 0; i < P.rev.size(); ++i)
+        if (!rb[i].empty() && !jit_load(rb[i], (int)p->smem_rev[i], p->jit_rev[i], err))
+            return fail(p, QTM_ECUDA, err);
+    p->jit_device = p->device;
+    return QTM_OK;
+}
+
+int qtm_compiled_passes(const qtm_plan *p)
+{
+    if (!p) return 0;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != p->jit_device) {
+        cudaGetLastError();
+        return 0;
+    }
+    int n = 0;
+    for (const auto *v : {&p->jit_fwd, &p->jit_rev})
+        for (const auto &k : *v) n += k.fn != nullptr;
+    return n;
+}
+
+const char *qtm_debug_jit_source(const qtm_plan *p, int which, int index)
+{
+    if (!p) return "";
+    const Plan &P = p->P;
+    const auto &v = which ? P.rev : P.fwd;
+    if (index < 0 || index >= (int)v.size()) return "";
+    qtm_plan *m = const_cast<qtm_plan *>(p);
+    m->jit_src_cache = jit_eligible(P, v[index]) ? jit_source(P, v[index], which ? 2 : 3) : std::string();
+    return m->jit_src_cache.c_str();
+}
+
+qtm_status qtm_debug_jit_compile(qtm_plan *p)
+{
+    if (!p) return QTM_EINVAL;
+    std::vector<std::vector<char>> fb, rb;
+    return compile_all(p, fb, rb);
 }
 
 qtm_status qtm_sync(qtm_plan *p, void *stream)
@@ -690,6 +792,8 @@ qtm_status qtm_destroy(qtm_plan *p)
 {
     if (!p) return QTM_EINVAL;
     for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
+    for (auto *v : {&p->jit_fwd, &p->jit_rev})
+        for (auto &k : *v) jit_unload(k);
     if (p->d_status) {
         int cur = -1;
         cudaGetDevice(&cur);

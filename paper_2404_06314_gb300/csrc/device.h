@@ -8,47 +8,6 @@
 
 namespace qtm {
 
-// status word bits recorded by kernels
-constexpr unsigned kStatusTimeout = 1u;
-
-struct PassArgs {
-    // geometry
-    int K, l, h, m;
-    int state_qubits, n;
-    int tiles, log_tiles;
-    int B;
-    int rank;                     // tensor-map rank of this pass
-    int low_dims, gap_dim, high_dims;   // dims per segment (for coordinates)
-    // program
-    const DevOp *ops;
-    const DiagPair *diag;
-    const DevPhase *phases;
-    int phase_begin, phase_end;
-    const int32_t *slot_runs;
-    int slot_begin, nslots;
-    int n_runs;
-    const void *mats;             // [B][n_runs][4] fused run matrices U (plan complex type)
-    const void *tabs;             // [B][ntab][16] product-state tables (plan complex type)
-    // analytic init
-    const Ent *prefix_ents;
-    int analytic_ents;
-    const MaskTerm *amap;         // closed form of the analytic state (amap_lin >= 0)
-    int amap_lin, amap_quad;
-    uint32_t amap_dlin;
-    // sources / sinks
-    int phi_src, lam_src, store_phi, store_lam, has_expval;
-    // observables
-    const Term *terms;
-    int n_terms, M;
-    // data (plan real type)
-    const void *x, *w, *gE;
-    int n_in;
-    double *Epart;                // [B][tiles][M]
-    double *Gpart;                // [B][n_runs][tiles][3]
-    unsigned *status;
-    int smem_bytes;
-};
-
 struct FinalizeArgs {
     int B, M, tiles, n_runs, n_rots, P, n_in;
     const Run *runs;

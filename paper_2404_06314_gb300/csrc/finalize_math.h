@@ -12,7 +12,9 @@
 // u <- Ad_{R_i}^T u.
 #pragma once
 
+#ifndef __CUDACC_RTC__
 #include <cmath>
+#endif
 
 #ifdef __CUDACC__
 #define QTM_HD __host__ __device__ __forceinline__

@@ -12,6 +12,7 @@
 // global memory and reduced in fixed order by the finalize kernels.
 #include <cstdint>
 
+#include "device.h"
 #include "tile.cuh"
 
 namespace qtm {
@@ -35,85 +36,9 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 1 : (REV ? 2 : 3)) k_pas
                                               const __grid_constant__ CUtensorMap tm_phi,
                                               const __grid_constant__ CUtensorMap tm_lam)
 {
-    extern __shared__ unsigned char smem_raw[];
-    unsigned char *smem = reinterpret_cast<unsigned char *>(
-        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    const int tid = threadIdx.x;
-    const int nwarps = (blockDim.x + 31) >> 5;
-    const int b = blockIdx.x >> a.log_tiles;
-    const int tile = blockIdx.x & (a.tiles - 1);
-    const int gapbits = a.h - a.l;
-    const uint32_t gap = tile & ((1u << gapbits) - 1u);
-    const uint32_t rest = tile >> gapbits;
-
-    TileJob j;
-    j.T = blockDim.x;
-    j.K = a.K; j.l = a.l; j.h = a.h; j.m = a.m; j.sq = a.state_qubits;
-    j.base = (gap << a.l) | (rest << (a.h + a.m));
-    j.ops = a.ops; j.diag = a.diag; j.phases = a.phases;
-    j.phase_begin = a.phase_begin; j.phase_end = a.phase_end;
-    j.slot_runs = a.slot_runs + a.slot_begin; j.nslots = a.nslots;
-    j.mats = static_cast<const Cx<R> *>(a.mats) + (size_t)b * a.n_runs * 4;
-    j.tabs = static_cast<const Cx<R> *>(a.tabs) + (size_t)b * ((a.state_qubits + 3) >> 2) * 16;
-    j.prefix_ents = a.prefix_ents; j.analytic_ents = a.analytic_ents;
-    j.amap = a.amap; j.amap_lin = a.amap_lin; j.amap_quad = a.amap_quad; j.amap_dlin = a.amap_dlin;
-    j.terms = a.terms; j.n_terms = a.n_terms; j.M = a.M;
-    j.gE = REV ? static_cast<const R *>(a.gE) + (size_t)b * a.M : nullptr;
-    j.phi_src = a.phi_src; j.lam_src = a.lam_src;
-
-    const Layout L = make_layout(a.K, (int)sizeof(Cx<R>), REV, a.nslots, a.n_terms, a.M,
-                                 a.state_qubits, a.analytic_ents, nwarps, (int)sizeof(R));
-    const TileSmem<R> S = carve<R>(smem, L);
-
-    // coordinates of this tile in the tensor maps
-    int coord[5] = {0, 0, 0, 0, 0};
-    {
-        int d = a.low_dims;
-        if (gapbits > 0) coord[d++] = (int)gap;
-        d += a.high_dims;
-        coord[d] = (int)(rest + ((uint32_t)b << (a.state_qubits - a.h - a.m)));
-    }
-    const bool load_phi = a.phi_src == SRC_LOAD;
-    const bool load_lam = REV && a.lam_src == SRC_LOAD;
-    const uint32_t tile_bytes = (uint32_t)sizeof(Cx<R>) << a.K;
-    if (tid == 0 && (load_phi || load_lam)) {
-        mbar_init(S.bar, 1);
-        mbar_expect_tx(S.bar, tile_bytes * ((load_phi ? 1u : 0u) + (load_lam ? 1u : 0u)));
-        if (load_phi) tma_load(S.phi, &tm_phi, coord, a.rank, S.bar);
-        if (load_lam) tma_load(S.lam, &tm_lam, coord, a.rank, S.bar);
-    }
-    stage_tables<R, REV>(j, S, nwarps);
-    __syncthreads();
-    if (a.phi_src == SRC_ANALYTIC) fill_analytic<R>(j, S);
-    if (load_phi || load_lam) {
-        bool ok = false;
-        const unsigned long long t0 = global_ns();
-        while (!(ok = mbar_try_wait(S.bar, 0)))
-            if (global_ns() - t0 > kWaitLimitNs) break;
-        if (__syncthreads_or(!ok)) {
-            if (tid == 0) atomicOr(a.status, kStatusTimeout);
-            return;
-        }
-    } else {
-        __syncthreads();
-    }
-
-    run_phases<R, REV>(j, S, load_lam);
-
-    write_partials<R, REV>(j, S, nwarps, a.has_expval != 0,
-                           a.Epart + ((size_t)b * a.tiles + tile) * a.M,
-                           REV ? a.Gpart + (size_t)b * a.n_runs * a.tiles * 3 : nullptr, a.tiles, tile);
-
-    // ---- write the tile back ----
-    if (a.store_phi || (REV && a.store_lam)) {
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        if (tid == 0) {
-            if (a.store_phi) tma_store(&tm_phi, coord, a.rank, S.phi);
-            if (REV && a.store_lam) tma_store(&tm_lam, coord, a.rank, S.lam);
-            tma_store_commit_and_drain();
-        }
-    }
+    pass_body<R, REV>(a, &tm_phi, &tm_lam, [](const TileJob &j, const TileSmem<R> &S, bool lam_valid) {
+        run_phases<R, REV>(j, S, lam_valid);
+    });
 }
 
 template <typename R>

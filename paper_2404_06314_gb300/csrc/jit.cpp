@@ -1,0 +1,351 @@
+// Run-time specialised pass kernels.
+//
+// The interpreter kernel (k_pass) reads every op's type, register bit, slot
+// and operands at run time.  For a fixed plan all of them are known, so this
+// file writes the pass's phase program out as CUDA source in which every
+// register bit, slot offset, CZ sign pattern and CNOT form is a compile-time
+// constant, compiles it with NVRTC for sm_103a, and loads it through the
+// driver API.  The generated kernel reuses the library's tile program
+// (pass_body in tile.cuh: TMA staging, analytic state, partial sums) and
+// replaces only the phase interpreter.  NVRTC is loaded with dlopen; when it
+// is missing, plans keep the interpreter kernels.
+#include "jit.h"
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_runtime.h>
+#include <dlfcn.h>
+#include <nvrtc.h>
+#include <sys/stat.h>
+#include <unistd.h>
+
+#include <cstdio>
+#include <cstdlib>
+#include <fstream>
+#include <mutex>
+#include <sstream>
+#include <string>
+#include <thread>
+#include <vector>
+
+namespace qtm {
+
+extern const char *const kJitPrelude;   // pod.h + finalize_math.h + tile.cuh (generated at build time)
+
+namespace {
+
+// ---- source generation ---------------------------------------------------------
+
+const char *kRegMask[4] = {"0xAAAAu", "0xCCCCu", "0xF0F0u", "0xFF00u"};
+const uint32_t kRegMaskV[4] = {0xAAAAu, 0xCCCCu, 0xF0F0u, 0xFF00u};
+
+std::string operand_bit(int o)
+{
+    std::ostringstream s;
+    if (o >= kFixed) s << "(base >> " << (o - kFixed) << ")";
+    else s << "(xt >> " << o << ")";
+    return s.str();
+}
+
+void gen_diag(std::ostringstream &o, const Plan &P, const DevOp &op, int lo, bool rev)
+{
+    uint32_t C = 0;
+    std::vector<std::vector<int>> per_reg(4);
+    std::vector<std::pair<int, int>> other;
+    auto is_reg = [&](int x) { return x < kFixed && x >= lo && x < lo + kRegBits; };
+    for (int k = op.a; k < op.a + op.b; ++k) {
+        const DiagPair dp = P.diag_pairs[k];
+        const bool ra = is_reg(dp.a), rb = is_reg(dp.b);
+        if (ra && rb) C ^= kRegMaskV[dp.a - lo] & kRegMaskV[dp.b - lo];
+        else if (ra) per_reg[dp.a - lo].push_back(dp.b);
+        else if (rb) per_reg[dp.b - lo].push_back(dp.a);
+        else other.push_back({dp.a, dp.b});
+    }
+    o << "    { uint32_t m = 0x" << std::hex << C << std::dec << "u;";
+    for (int r = 0; r < 4; ++r) {
+        if (per_reg[r].empty()) continue;
+        o << " m ^= (0u - ((";
+        for (size_t i = 0; i < per_reg[r].size(); ++i) o << (i ? " ^ " : "") << operand_bit(per_reg[r][i]);
+        o << ") & 1u)) & " << kRegMask[r] << ";";
+    }
+    if (!other.empty()) {
+        o << " m ^= (0u - ((";
+        for (size_t i = 0; i < other.size(); ++i)
+            o << (i ? " ^ " : "") << "(" << operand_bit(other[i].first) << " & " << operand_bit(other[i].second) << ")";
+        o << ") & 1u)) & 0xFFFFu;";
+    }
+    o << " flip_mask<R, " << (rev ? "true" : "false") << ">(p, q, m); }\n";
+}
+
+}  // namespace
+
+bool jit_eligible(const Plan &P, const PassDesc &pd)
+{
+    return P.path == QTM_PATH_FUSED && pd.K >= 9 && P.dtype == QTM_C64;
+}
+
+std::string jit_source(const Plan &P, const PassDesc &pd, int min_blocks)
+{
+    const bool rev = pd.reverse != 0;
+    const int nslots = pd.slot_end - pd.slot_begin;
+    const char *R = P.dtype == QTM_C128 ? "double" : "float";
+    std::ostringstream o;
+    o << "namespace qtm {\nnamespace {\n";
+    o << "template <typename R>\n__device__ __forceinline__ void gen_phases(const TileJob &j, const TileSmem<R> &S, bool)\n{\n";
+    o << "    const int tid = threadIdx.x;\n    const int warp = tid >> 5, lane = tid & 31;\n";
+    o << "    const uint32_t base = j.base;\n    (void)base; (void)lane; (void)warp;\n";
+    o << "    Cx<R> p[kRegs];\n    Cx<R> q[kRegs];\n";
+    bool lam_valid = rev && pd.lam_src == SRC_LOAD;
+    for (int ph = pd.phase_begin; ph < pd.phase_end; ++ph) {
+        const DevPhase &phs = P.phases[ph];
+        const int lo = phs.lo;
+        o << "    {\n        constexpr int LO = " << lo << ";\n";
+        o << "        const uint32_t xt = ((uint32_t)tid & ((1u << LO) - 1u)) | (((uint32_t)tid >> LO) << (LO + 4));\n";
+        o << "        regs_load<R, LO, " << (lam_valid ? "true" : "false") << ">(p, q, S, xt);\n";
+        for (int k = phs.op_begin; k < phs.op_end; ++k) {
+            const DevOp &op = P.ops[k];
+            // register operands must lie in this phase's 4-bit group; a schedule
+            // that breaks this fails to compile instead of running
+            const bool reg_a = op.a >= lo && op.a < lo + kRegBits;
+            const bool reg_b = op.b >= lo && op.b < lo + kRegBits;
+            if (((op.type == OP_U2 || op.type == OP_GRAD) && !reg_a) || (op.type == OP_CNOT && !reg_b) ||
+                ((op.type == OP_U2 || op.type == OP_GRAD) && (op.slot < 0 || op.slot >= nslots)) ||
+                (op.type == OP_DIAG && (op.a < 0 || op.a + op.b > (int)P.diag_pairs.size()))) {
+                o << "#error \"op " << k << " has an operand outside its phase\"\n";
+                continue;
+            }
+            switch (op.type) {
+            case OP_U2:
+                o << "        u2<" << (op.a - lo) << ">(p, S.mats + " << 4 * op.slot << ");\n";
+                break;
+            case OP_GRAD: {
+                const int rb = op.a - lo;
+                o << "        { R vx = 0, vy = 0, vz = 0; grad_acc<" << rb << ">(p, q, vx, vy, vz);"
+                  << " vx = warp_sum(vx, 32, 0xffffffffu); vy = warp_sum(vy, 32, 0xffffffffu);"
+                  << " vz = warp_sum(vz, 32, 0xffffffffu);"
+                  << " if (lane == 0) { R *g = S.redG + warp * " << 3 * nslots << " + " << 3 * op.slot
+                  << "; g[0] = vx; g[1] = vy; g[2] = vz; }";
+                if (!(op.flags & OPF_SKIP_APPLY))
+                    o << " u2<" << rb << ">(p, S.mats + " << 4 * op.slot << "); u2<" << rb << ">(q, S.mats + "
+                      << 4 * op.slot << ");";
+                o << " }\n";
+                break;
+            }
+            case OP_DIAG:
+                o << "    ";
+                gen_diag(o, P, op, lo, rev);
+                break;
+            case OP_CNOT: {
+                const int rt = op.b - lo;
+                if (op.a < kFixed && op.a >= lo && op.a < lo + kRegBits) {
+                    o << "        cnot_static<" << (op.a - lo) << ", " << rt << ">(p);";
+                    if (rev) o << " cnot_static<" << (op.a - lo) << ", " << rt << ">(q);";
+                    o << "\n";
+                } else {
+                    o << "        { const int c = (int)(" << operand_bit(op.a) << " & 1u); cnot_regs<" << rt
+                      << ">(p, -1, c);";
+                    if (rev) o << " cnot_regs<" << rt << ">(q, -1, c);";
+                    o << " }\n";
+                }
+                break;
+            }
+            case OP_EXPVAL:
+                o << "        op_expval<R>(p, S, j, xt, LO, warp, lane, 32, 0xffffffffu);\n";
+                break;
+            case OP_COSTATE:
+                o << "        op_costate<R>(p, q, S, j, xt, LO);\n";
+                break;
+            default:
+                break;
+            }
+        }
+        o << "        regs_store<R, LO, " << (rev ? "true" : "false") << ">(p, q, S, xt);\n";
+        o << "        __syncthreads();\n    }\n";
+        if (rev) lam_valid = true;
+    }
+    o << "}\n}  // namespace\n}  // namespace qtm\n\n";
+    o << "extern \"C\" __global__ void __launch_bounds__(256, " << min_blocks << ") qtm_gen_pass("
+      << "const __grid_constant__ qtm::PassArgs a, const __grid_constant__ CUtensorMap tm_phi, "
+      << "const __grid_constant__ CUtensorMap tm_lam)\n{\n";
+    o << "    qtm::pass_body<" << R << ", " << (rev ? "true" : "false") << ">(a, &tm_phi, &tm_lam, "
+      << "[](const qtm::TileJob &j, const qtm::TileSmem<" << R << "> &S, bool lv) { qtm::gen_phases<" << R
+      << ">(j, S, lv); });\n}\n";
+    return o.str();
+}
+
+// ---- NVRTC and the driver API ---------------------------------------------------
+
+namespace {
+
+struct Nvrtc {
+    bool ok = false;
+    decltype(&nvrtcCreateProgram) create = nullptr;
+    decltype(&nvrtcCompileProgram) compile = nullptr;
+    decltype(&nvrtcGetProgramLogSize) log_size = nullptr;
+    decltype(&nvrtcGetProgramLog) log = nullptr;
+    decltype(&nvrtcGetCUBINSize) cubin_size = nullptr;
+    decltype(&nvrtcGetCUBIN) cubin = nullptr;
+    decltype(&nvrtcDestroyProgram) destroy = nullptr;
+};
+
+const Nvrtc &nvrtc()
+{
+    static Nvrtc n;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        const char *names[] = {"libnvrtc.so.13", "libnvrtc.so", "/usr/local/cuda/lib64/libnvrtc.so.13"};
+        void *h = nullptr;
+        for (const char *nm : names)
+            if ((h = dlopen(nm, RTLD_NOW | RTLD_LOCAL))) break;
+        if (!h) return;
+        n.create = reinterpret_cast<decltype(n.create)>(dlsym(h, "nvrtcCreateProgram"));
+        n.compile = reinterpret_cast<decltype(n.compile)>(dlsym(h, "nvrtcCompileProgram"));
+        n.log_size = reinterpret_cast<decltype(n.log_size)>(dlsym(h, "nvrtcGetProgramLogSize"));
+        n.log = reinterpret_cast<decltype(n.log)>(dlsym(h, "nvrtcGetProgramLog"));
+        n.cubin_size = reinterpret_cast<decltype(n.cubin_size)>(dlsym(h, "nvrtcGetCUBINSize"));
+        n.cubin = reinterpret_cast<decltype(n.cubin)>(dlsym(h, "nvrtcGetCUBIN"));
+        n.destroy = reinterpret_cast<decltype(n.destroy)>(dlsym(h, "nvrtcDestroyProgram"));
+        n.ok = n.create && n.compile && n.log_size && n.log && n.cubin_size && n.cubin && n.destroy;
+    });
+    return n;
+}
+
+struct Drv {
+    bool ok = false;
+    PFN_cuModuleLoadData_v2000 load = nullptr;
+    PFN_cuModuleGetFunction_v2000 get = nullptr;
+    PFN_cuModuleUnload_v2000 unload = nullptr;
+    PFN_cuFuncSetAttribute_v9000 set_attr = nullptr;
+    PFN_cuLaunchKernel_v4000 launch = nullptr;
+};
+
+const Drv &drv()
+{
+    static Drv d;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        auto get = [](const char *name, void **fn) {
+            cudaDriverEntryPointQueryResult q;
+            return cudaGetDriverEntryPointByVersion(name, fn, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+                   q == cudaDriverEntryPointSuccess;
+        };
+        d.ok = get("cuModuleLoadData", reinterpret_cast<void **>(&d.load)) &&
+               get("cuModuleGetFunction", reinterpret_cast<void **>(&d.get)) &&
+               get("cuModuleUnload", reinterpret_cast<void **>(&d.unload)) &&
+               get("cuFuncSetAttribute", reinterpret_cast<void **>(&d.set_attr)) &&
+               get("cuLaunchKernel", reinterpret_cast<void **>(&d.launch));
+    });
+    return d;
+}
+
+uint64_t fnv1a(const std::string &s)
+{
+    uint64_t h = 1469598103934665603ull;
+    for (unsigned char c : s) { h ^= c; h *= 1099511628211ull; }
+    return h;
+}
+
+std::string cache_dir()
+{
+    const char *e = std::getenv("QTM_JIT_CACHE");
+    if (e && *e) return e;
+    return "/tmp/qtm_jit_cache";
+}
+
+bool read_file(const std::string &path, std::vector<char> &out)
+{
+    std::ifstream f(path, std::ios::binary);
+    if (!f) return false;
+    out.assign(std::istreambuf_iterator<char>(f), std::istreambuf_iterator<char>());
+    return !out.empty();
+}
+
+}  // namespace
+
+bool jit_available() { return nvrtc().ok && drv().ok; }
+bool jit_nvrtc_available() { return nvrtc().ok; }
+
+bool jit_compile(const std::string &body, std::vector<char> &cubin, std::string &log)
+{
+    const Nvrtc &N = nvrtc();
+    if (!N.ok) { log = "NVRTC not found"; return false; }
+    const std::string src = std::string(kJitPrelude) + "\n" + body;
+    const char *opts[] = {"--gpu-architecture=sm_103a", "-std=c++17", "-lineinfo"};
+    const int nopts = 3;
+    char key[32];
+    std::snprintf(key, sizeof(key), "%016llx", (unsigned long long)fnv1a(src));
+    const std::string dir = cache_dir(), path = dir + "/" + key + ".cubin";
+    if (read_file(path, cubin)) return true;
+    nvrtcProgram prog;
+    if (N.create(&prog, src.c_str(), "qtm_gen.cu", 0, nullptr, nullptr) != NVRTC_SUCCESS) {
+        log = "nvrtcCreateProgram failed";
+        return false;
+    }
+    const nvrtcResult r = N.compile(prog, nopts, opts);
+    size_t ls = 0;
+    N.log_size(prog, &ls);
+    if (ls > 1) {
+        log.resize(ls);
+        N.log(prog, &log[0]);
+    }
+    bool ok = r == NVRTC_SUCCESS;
+    if (ok) {
+        size_t cs = 0;
+        ok = N.cubin_size(prog, &cs) == NVRTC_SUCCESS && cs > 0;
+        if (ok) {
+            cubin.resize(cs);
+            ok = N.cubin(prog, cubin.data()) == NVRTC_SUCCESS;
+        }
+    }
+    N.destroy(&prog);
+    if (ok) {   // best-effort disk cache keyed by the source hash
+        ::mkdir(dir.c_str(), 0755);
+        const std::string tmp = path + ".tmp" + std::to_string((unsigned long long)::getpid());
+        std::ofstream f(tmp, std::ios::binary);
+        if (f) {
+            f.write(cubin.data(), (std::streamsize)cubin.size());
+            f.close();
+            std::rename(tmp.c_str(), path.c_str());
+        }
+    }
+    return ok;
+}
+
+bool jit_load(const std::vector<char> &cubin, int smem, JitKernel &k, std::string &err)
+{
+    const Drv &D = drv();
+    if (!D.ok) { err = "driver entry points unavailable"; return false; }
+    CUmodule mod = nullptr;
+    CUfunction fn = nullptr;
+    if (D.load(&mod, cubin.data()) != CUDA_SUCCESS) { err = "cuModuleLoadData failed"; return false; }
+    if (D.get(&fn, mod, "qtm_gen_pass") != CUDA_SUCCESS ||
+        D.set_attr(fn, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, smem) != CUDA_SUCCESS) {
+        D.unload(mod);
+        err = "kernel lookup / attribute failed";
+        return false;
+    }
+    k.mod = mod;
+    k.fn = fn;
+    return true;
+}
+
+void jit_unload(JitKernel &k)
+{
+    if (k.mod && drv().ok) drv().unload(static_cast<CUmodule>(k.mod));
+    k.mod = nullptr;
+    k.fn = nullptr;
+}
+
+cudaError_t jit_launch(const JitKernel &k, const PassArgs &a, const CUtensorMap &tm_phi, const CUtensorMap &tm_lam,
+                       cudaStream_t s)
+{
+    PassArgs args = a;
+    CUtensorMap t0 = tm_phi, t1 = tm_lam;
+    void *params[] = {&args, &t0, &t1};
+    const unsigned grid = (unsigned)a.B * (unsigned)a.tiles, block = 1u << (a.K - 4);
+    CUresult r = drv().launch(static_cast<CUfunction>(k.fn), grid, 1, 1, block, 1, 1, (unsigned)a.smem_bytes,
+                              reinterpret_cast<CUstream>(s), params, nullptr);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorLaunchFailure;
+}
+
+}  // namespace qtm

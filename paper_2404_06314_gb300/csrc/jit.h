@@ -1,0 +1,31 @@
+// Run-time specialised pass kernels (see jit.cpp).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "plan.h"
+
+namespace qtm {
+
+struct JitKernel {
+    void *mod = nullptr;   // CUmodule
+    void *fn = nullptr;    // CUfunction
+};
+
+// Passes worth specialising: fused complex64 passes whose tile has >= 9 qubits
+// (full warps).
+bool jit_eligible(const Plan &P, const PassDesc &pd);
+bool jit_available();
+bool jit_nvrtc_available();
+std::string jit_source(const Plan &P, const PassDesc &pd, int min_blocks);
+bool jit_compile(const std::string &body, std::vector<char> &cubin, std::string &log);
+bool jit_load(const std::vector<char> &cubin, int smem, JitKernel &k, std::string &err);
+void jit_unload(JitKernel &k);
+cudaError_t jit_launch(const JitKernel &k, const PassArgs &a, const CUtensorMap &tm_phi, const CUtensorMap &tm_lam,
+                       cudaStream_t s);
+
+}  // namespace qtm

@@ -22,6 +22,7 @@
 #include <vector>
 
 #include "../../include/qtm.h"
+#include "device.h"
 #include "tile.cuh"
 
 namespace qtm {

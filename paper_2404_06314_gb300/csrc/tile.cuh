@@ -5,10 +5,16 @@
 // product state, register-phase interpreter, per-tile partial sums).
 #pragma once
 
+#ifdef __CUDACC_RTC__
+struct alignas(64) CUtensorMap_st { unsigned long long opaque[16]; };
+typedef CUtensorMap_st CUtensorMap;
+#else
 #include <cstdint>
+#include <cuda.h>
+#endif
 
-#include "device.h"
 #include "finalize_math.h"
+#include "pod.h"
 
 namespace qtm {
 
@@ -490,6 +496,138 @@ __device__ __forceinline__ void fill_analytic(const TileJob &j, const TileSmem<R
     }
 }
 
+// <O_m> partials over the thread's 16 registers (terms sorted by observable),
+// warp-reduced, one value per (warp, observable) in S.redE.
+template <typename R>
+__device__ __forceinline__ void op_expval(const Cx<R> (&p)[kRegs], const TileSmem<R> &S, const TileJob &j,
+                                          uint32_t xt, int lo, int warp, int lane, int wwidth, unsigned wmask)
+{
+    R pr[kRegs];
+#pragma unroll
+    for (int jj = 0; jj < kRegs; ++jj) pr[jj] = p[jj].x * p[jj].x + p[jj].y * p[jj].y;
+    int cur = -1;
+    R acc = 0;
+    for (int t = 0; t < j.n_terms; ++t) {
+        const int ob = S.tobs[t];
+        if (ob != cur) {
+            if (cur >= 0) {
+                acc = warp_sum(acc, wwidth, wmask);
+                if (lane == 0) S.redE[warp * j.M + cur] = acc;
+            }
+            cur = ob;
+            acc = 0;
+        }
+        const uint32_t lm = S.tmask[t];
+        const int tpar = __popc(xt & lm);
+        const uint32_t rm = (lm >> lo) & 15u;
+        R sacc = 0;
+#pragma unroll
+        for (int jj = 0; jj < kRegs; ++jj)
+            sacc += ((tpar + __popc((uint32_t)jj & rm)) & 1) ? -pr[jj] : pr[jj];
+        acc = fma(S.tcoef[t], sacc, acc);
+    }
+    if (cur >= 0) {
+        acc = warp_sum(acc, wwidth, wmask);
+        if (lane == 0) S.redE[warp * j.M + cur] = acc;
+    }
+}
+
+// lam = (sum_m gE_m O_m) phi on the thread's registers (Sec. II-A costate).
+template <typename R>
+__device__ __forceinline__ void op_costate(const Cx<R> (&p)[kRegs], Cx<R> (&q)[kRegs], const TileSmem<R> &S,
+                                           const TileJob &j, uint32_t xt, int lo)
+{
+    R d[kRegs];
+#pragma unroll
+    for (int jj = 0; jj < kRegs; ++jj) d[jj] = 0;
+    for (int t = 0; t < j.n_terms; ++t) {
+        const uint32_t lm = S.tmask[t];
+        const int tpar = __popc(xt & lm);
+        const uint32_t rm = (lm >> lo) & 15u;
+        const R k = S.tcoef[t];
+#pragma unroll
+        for (int jj = 0; jj < kRegs; ++jj)
+            d[jj] += ((tpar + __popc((uint32_t)jj & rm)) & 1) ? -k : k;
+    }
+#pragma unroll
+    for (int jj = 0; jj < kRegs; ++jj) q[jj] = {d[jj] * p[jj].x, d[jj] * p[jj].y};
+}
+
+// CNOT with control and target both register bits: a fixed register permutation.
+template <int RC, int RT, typename R>
+__device__ __forceinline__ void cnot_static(Cx<R> (&a)[kRegs])
+{
+#pragma unroll
+    for (int jj = 0; jj < kRegs; ++jj) {
+        if ((jj & (1 << RT)) || !(jj & (1 << RC))) continue;
+        const Cx<R> t = a[jj];
+        a[jj] = a[jj | (1 << RT)];
+        a[jj | (1 << RT)] = t;
+    }
+}
+
+// Registers <-> shared tile for register group [LO, LO+4) (compile-time LO).
+template <typename R, int LO, bool LAM>
+__device__ __forceinline__ void regs_load(Cx<R> (&p)[kRegs], Cx<R> (&q)[kRegs], const TileSmem<R> &S, uint32_t xt)
+{
+    if (sizeof(R) == 4 && LO == 0) {
+#pragma unroll
+        for (int k = 0; k < kRegs / 2; ++k) {
+            const int s = swz<R>((int)xt + 2 * k);
+            const float4 v = *reinterpret_cast<const float4 *>(&S.phi[s]);
+            p[2 * k] = {(R)v.x, (R)v.y};
+            p[2 * k + 1] = {(R)v.z, (R)v.w};
+            if (LAM) {
+                const float4 u = *reinterpret_cast<const float4 *>(&S.lam[s]);
+                q[2 * k] = {(R)u.x, (R)u.y};
+                q[2 * k + 1] = {(R)u.z, (R)u.w};
+            }
+        }
+    } else {
+#pragma unroll
+        for (int jj = 0; jj < kRegs; ++jj) {
+            const int s = swz<R>((int)(xt | ((uint32_t)jj << LO)));
+            p[jj] = S.phi[s];
+            if (LAM) q[jj] = S.lam[s];
+        }
+    }
+}
+
+template <typename R, int LO, bool LAM>
+__device__ __forceinline__ void regs_store(const Cx<R> (&p)[kRegs], const Cx<R> (&q)[kRegs], const TileSmem<R> &S,
+                                           uint32_t xt)
+{
+    if (sizeof(R) == 4 && LO == 0) {
+#pragma unroll
+        for (int k = 0; k < kRegs / 2; ++k) {
+            const int s = swz<R>((int)xt + 2 * k);
+            *reinterpret_cast<float4 *>(&S.phi[s]) =
+                make_float4((float)p[2 * k].x, (float)p[2 * k].y, (float)p[2 * k + 1].x, (float)p[2 * k + 1].y);
+            if (LAM)
+                *reinterpret_cast<float4 *>(&S.lam[s]) =
+                    make_float4((float)q[2 * k].x, (float)q[2 * k].y, (float)q[2 * k + 1].x, (float)q[2 * k + 1].y);
+        }
+    } else {
+#pragma unroll
+        for (int jj = 0; jj < kRegs; ++jj) {
+            const int s = swz<R>((int)(xt | ((uint32_t)jj << LO)));
+            S.phi[s] = p[jj];
+            if (LAM) S.lam[s] = q[jj];
+        }
+    }
+}
+
+template <typename R, bool REV>
+__device__ __forceinline__ void flip_mask(Cx<R> (&p)[kRegs], Cx<R> (&q)[kRegs], uint32_t msk)
+{
+#pragma unroll
+    for (int jj = 0; jj < kRegs; ++jj) {
+        const uint32_t bit = (msk >> jj) & 1u;
+        flip_sign(p[jj], bit);
+        if (REV) flip_sign(q[jj], bit);
+    }
+}
+
 // The pass's phases over the tile in shared memory (after a barrier); ends
 // with a barrier.  lam_valid: the costate tile already holds lam.
 template <typename R, bool REV>
@@ -582,53 +720,12 @@ __device__ __forceinline__ void run_phases(const TileJob &j, const TileSmem<R> &
                 if (REV) cnot_dispatch<R>(op.b - lo, q, rc, vc);
                 break;
             }
-            case OP_EXPVAL: {
-                R pr[kRegs];
-#pragma unroll
-                for (int jj = 0; jj < kRegs; ++jj) pr[jj] = p[jj].x * p[jj].x + p[jj].y * p[jj].y;
-                int cur = -1;
-                R acc = 0;
-                for (int t = 0; t < j.n_terms; ++t) {
-                    const int ob = S.tobs[t];
-                    if (ob != cur) {
-                        if (cur >= 0) {
-                            acc = warp_sum(acc, wwidth, wmask);
-                            if (lane == 0) S.redE[warp * j.M + cur] = acc;
-                        }
-                        cur = ob;
-                        acc = 0;
-                    }
-                    const uint32_t lm = S.tmask[t];
-                    const int tpar = __popc(xt & lm);
-                    const uint32_t rm = (lm >> lo) & 15u;
-                    R sacc = 0;
-#pragma unroll
-                    for (int jj = 0; jj < kRegs; ++jj)
-                        sacc += ((tpar + __popc((uint32_t)jj & rm)) & 1) ? -pr[jj] : pr[jj];
-                    acc = fma(S.tcoef[t], sacc, acc);
-                }
-                if (cur >= 0) {
-                    acc = warp_sum(acc, wwidth, wmask);
-                    if (lane == 0) S.redE[warp * j.M + cur] = acc;
-                }
+            case OP_EXPVAL:
+                op_expval<R>(p, S, j, xt, lo, warp, lane, wwidth, wmask);
                 break;
-            }
             case OP_COSTATE:
                 if constexpr (REV) {
-                    R d[kRegs];
-#pragma unroll
-                    for (int jj = 0; jj < kRegs; ++jj) d[jj] = 0;
-                    for (int t = 0; t < j.n_terms; ++t) {
-                        const uint32_t lm = S.tmask[t];
-                        const int tpar = __popc(xt & lm);
-                        const uint32_t rm = (lm >> lo) & 15u;
-                        const R k = S.tcoef[t];
-#pragma unroll
-                        for (int jj = 0; jj < kRegs; ++jj)
-                            d[jj] += ((tpar + __popc((uint32_t)jj & rm)) & 1) ? -k : k;
-                    }
-#pragma unroll
-                    for (int jj = 0; jj < kRegs; ++jj) q[jj] = {d[jj] * p[jj].x, d[jj] * p[jj].y};
+                    op_costate<R>(p, q, S, j, xt, lo);
                     lam_valid = true;
                 }
                 break;
@@ -735,6 +832,94 @@ __device__ __forceinline__ void grad_finalize_sample(
             }
             gx_b[k] = (R)s;
         }
+}
+
+// The body of a pass kernel: tile coordinates, TMA loads (or the analytic
+// state), table staging, the pass's phases (`phases`, the interpreter or a
+// generated specialisation), per-tile partial sums and the TMA stores.
+template <typename R, bool REV, typename PhaseFn>
+__device__ __forceinline__ void pass_body(const PassArgs &a, const CUtensorMap *tm_phi,
+                                          const CUtensorMap *tm_lam, PhaseFn phases)
+{
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *smem = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const int tid = threadIdx.x;
+    const int nwarps = (blockDim.x + 31) >> 5;
+    const int b = blockIdx.x >> a.log_tiles;
+    const int tile = blockIdx.x & (a.tiles - 1);
+    const int gapbits = a.h - a.l;
+    const uint32_t gap = tile & ((1u << gapbits) - 1u);
+    const uint32_t rest = tile >> gapbits;
+
+    TileJob j;
+    j.T = blockDim.x;
+    j.K = a.K; j.l = a.l; j.h = a.h; j.m = a.m; j.sq = a.state_qubits;
+    j.base = (gap << a.l) | (rest << (a.h + a.m));
+    j.ops = a.ops; j.diag = a.diag; j.phases = a.phases;
+    j.phase_begin = a.phase_begin; j.phase_end = a.phase_end;
+    j.slot_runs = a.slot_runs + a.slot_begin; j.nslots = a.nslots;
+    j.mats = static_cast<const Cx<R> *>(a.mats) + (size_t)b * a.n_runs * 4;
+    j.tabs = static_cast<const Cx<R> *>(a.tabs) + (size_t)b * ((a.state_qubits + 3) >> 2) * 16;
+    j.prefix_ents = a.prefix_ents; j.analytic_ents = a.analytic_ents;
+    j.amap = a.amap; j.amap_lin = a.amap_lin; j.amap_quad = a.amap_quad; j.amap_dlin = a.amap_dlin;
+    j.terms = a.terms; j.n_terms = a.n_terms; j.M = a.M;
+    j.gE = REV ? static_cast<const R *>(a.gE) + (size_t)b * a.M : nullptr;
+    j.phi_src = a.phi_src; j.lam_src = a.lam_src;
+
+    const Layout L = make_layout(a.K, (int)sizeof(Cx<R>), REV, a.nslots, a.n_terms, a.M,
+                                 a.state_qubits, a.analytic_ents, nwarps, (int)sizeof(R));
+    const TileSmem<R> S = carve<R>(smem, L);
+
+    // coordinates of this tile in the tensor maps
+    int coord[5] = {0, 0, 0, 0, 0};
+    {
+        int d = a.low_dims;
+        if (gapbits > 0) coord[d++] = (int)gap;
+        d += a.high_dims;
+        coord[d] = (int)(rest + ((uint32_t)b << (a.state_qubits - a.h - a.m)));
+    }
+    const bool load_phi = a.phi_src == SRC_LOAD;
+    const bool load_lam = REV && a.lam_src == SRC_LOAD;
+    const uint32_t tile_bytes = (uint32_t)sizeof(Cx<R>) << a.K;
+    if (tid == 0 && (load_phi || load_lam)) {
+        mbar_init(S.bar, 1);
+        mbar_expect_tx(S.bar, tile_bytes * ((load_phi ? 1u : 0u) + (load_lam ? 1u : 0u)));
+        if (load_phi) tma_load(S.phi, tm_phi, coord, a.rank, S.bar);
+        if (load_lam) tma_load(S.lam, tm_lam, coord, a.rank, S.bar);
+    }
+    stage_tables<R, REV>(j, S, nwarps);
+    __syncthreads();
+    if (a.phi_src == SRC_ANALYTIC) fill_analytic<R>(j, S);
+    if (load_phi || load_lam) {
+        bool ok = false;
+        const unsigned long long t0 = global_ns();
+        while (!(ok = mbar_try_wait(S.bar, 0)))
+            if (global_ns() - t0 > kWaitLimitNs) break;
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) atomicOr(a.status, kStatusTimeout);
+            return;
+        }
+    } else {
+        __syncthreads();
+    }
+
+    phases(j, S, load_lam);
+
+    write_partials<R, REV>(j, S, nwarps, a.has_expval != 0,
+                           a.Epart + ((size_t)b * a.tiles + tile) * a.M,
+                           REV ? a.Gpart + (size_t)b * a.n_runs * a.tiles * 3 : nullptr, a.tiles, tile);
+
+    // ---- write the tile back ----
+    if (a.store_phi || (REV && a.store_lam)) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            if (a.store_phi) tma_store(tm_phi, coord, a.rank, S.phi);
+            if (REV && a.store_lam) tma_store(tm_lam, coord, a.rank, S.lam);
+            tma_store_commit_and_drain();
+        }
+    }
 }
 
 }  // namespace

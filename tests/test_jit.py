@@ -1,0 +1,120 @@
+"""Run-time specialised pass kernels (qtm_compile).
+
+Host part (no GPU): the source written for every eligible pass of the
+benchmark workloads and of random circuits compiles with NVRTC for sm_103a,
+every pass of a complex64 plan with 2^9..2^12-amplitude tiles is eligible, and
+complex128 / naive plans are not specialised.
+
+GPU part: a compiled plan gives the oracle's E, grad_x and per-sample grad_w
+within the complex64 bound (1e-5), the specialised kernels are the ones that
+ran (qtm_compiled_passes), and results agree with the general pass kernel's.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import oracle_pins as P
+from paper_2404_06314_gb300 import capi, workloads as W
+
+
+def _nvrtc_or_skip(plan):
+    try:
+        plan.jit_compile_check()
+    except capi.QtmError as e:
+        if e.status == capi.QTM_EUNSUPPORTED:
+            pytest.skip("NVRTC not available")
+        raise
+
+
+def _rand(n, seed):
+    rng = np.random.default_rng(seed)
+    c = P.rand_small_circuit(rng, n, G=5 * n + 6, n_obs=3)
+    c.name = f"jit_rand{n}"
+    return c
+
+
+def test_generated_source_compiles_benchmarks():
+    for c in [W.workload_12q(), W.workload_20q(), W.workload_16q_train()]:
+        plan = capi.Plan(c, dtype="c64")
+        info = plan.info
+        for which, count in ((0, info["fwd_passes"]), (1, info["adj_passes"])):
+            for i in range(count):
+                src = plan.jit_source(which, i)
+                assert "qtm_gen_pass" in src and "gen_phases" in src, (c.name, which, i)
+        _nvrtc_or_skip(plan)
+
+
+@pytest.mark.parametrize("n", [9, 13])
+def test_generated_source_compiles_random(n):
+    plan = capi.Plan(_rand(n, 500 + n), dtype="c64")
+    _nvrtc_or_skip(plan)
+
+
+def test_not_specialised():
+    c = W.workload_12q()
+    assert capi.Plan(c, dtype="c128").jit_source(0, 0) == ""   # complex128 keeps the interpreter
+    assert capi.Plan(W.workload_4q(), dtype="c64").jit_source(0, 0) == ""   # 16-amplitude tile
+    assert capi.Plan(c, dtype="c64").jit_source(0, 99) == ""
+
+
+# ---- GPU parity -------------------------------------------------------------------
+
+def _run(plan, c, inp):
+    import torch
+    x = torch.tensor(inp.x, dtype=torch.float32, device="cuda")
+    w = torch.tensor(inp.w, dtype=torch.float32, device="cuda")
+    gE = torch.tensor(inp.gE, dtype=torch.float32, device="cuda")
+    E = plan.forward(x, w)
+    gx, gw = plan.adjoint(gE, x, w, per_sample_w=True)
+    plan.sync()
+    return [t.double().cpu().numpy() for t in (E, gx, gw)]
+
+
+CASES = [("qnn12", 37), ("qnn20", 2), ("qnn16", 3), ("rand9", 3), ("rand11", 3), ("rand13", 3), ("rand14", 2),
+         ("rand16", 2)]
+
+
+def _circuit(name):
+    return {"qnn12": W.workload_12q, "qnn20": W.workload_20q, "qnn16": W.workload_16q_train}.get(
+        name, lambda: _rand(int(name[4:]), 600 + int(name[4:])))()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("name,B", CASES)
+def test_compiled_plan_matches_oracle(name, B):
+    c = _circuit(name)
+    inp = W.make_inputs(c, B, 21, real_dtype=np.float32)
+    general = _run(capi.Plan(c, dtype="c64"), c, inp)
+    plan = capi.Plan(c, dtype="c64")
+    plan.compile()
+    info = plan.info
+    assert plan.compiled_passes() == info["fwd_passes"] + info["adj_passes"]
+    got = _run(plan, c, inp)
+    Eo = oracle.forward(c, inp.x, inp.w, threads=0)
+    _, gxo, gwo = oracle.adjoint(c, inp.gE, inp.x, inp.w, threads=0)
+    for what, g, r, h in zip(("E", "gx", "gw"), got, (Eo, gxo, gwo), general):
+        err = float(np.max(np.abs(g - r))) if r.size else 0.0
+        assert err <= 1e-5, f"{name} compiled {what}: {err:.3e}"
+        d = float(np.max(np.abs(g - h))) if h.size else 0.0
+        assert d <= 2e-6, f"{name} compiled vs general {what}: {d:.3e}"
+
+
+@pytest.mark.gpu
+def test_compiled_plan_jacobian_and_full_batch():
+    import torch
+    c = W.workload_12q()
+    plan = capi.Plan(c, dtype="c64").compile()
+    B = 1024
+    inp = W.make_inputs(c, B, W.WORKLOAD_SEEDS[c.name], real_dtype=np.float32)
+    E, gx, gw = _run(plan, c, inp)
+    rows = np.array([0, 511, 1023])
+    Eo = oracle.forward(c, inp.x[rows], inp.w, threads=0)
+    _, gxo, gwo = oracle.adjoint(c, inp.gE[rows], inp.x[rows], inp.w, threads=0)
+    assert np.max(np.abs(E[rows] - Eo)) <= 1e-5
+    assert np.max(np.abs(gx[rows] - gxo)) <= 1e-5
+    assert np.max(np.abs(gw[rows] - gwo)) <= 1e-5
+    x = torch.tensor(inp.x[:2], dtype=torch.float32, device="cuda")
+    w = torch.tensor(inp.w, dtype=torch.float32, device="cuda")
+    J = plan.jacobian(x, w).double().cpu().numpy()
+    Jo = oracle.jacobian(c, inp.x[:2], inp.w, threads=0)
+    assert np.max(np.abs(J - Jo)) <= 1e-5

@@ -191,19 +191,20 @@ def oracle_rate(c, inp_full, budget_s: float, threads: int):
 # GPU measurement
 # ------------------------------------------------------------------------------
 
-KERNEL_LABEL = {"specialised": "qtm_gen_pass (plan-specialised pass kernel, NVRTC), reverse",
+KERNEL_LABEL = {"paired": "qtm_gen_pass (plan-specialised, two samples per CTA on f32x2 pairs), reverse",
+                "one-sample": "qtm_gen_pass (plan-specialised, one sample per CTA), reverse",
                 "general": "k_pass<float, reverse> (general pass kernel)"}
 
 
 def prepare(plan, kernels):
     """Load the plan's specialised pass kernels unless the general kernel is asked for."""
-    if kernels == "specialised":
-        plan.compile()
+    if kernels != "general":
+        plan.compile(pairs=(kernels == "paired"))
         assert plan.compiled_passes() > 0, "no specialised pass kernel loaded"
     return plan
 
 
-def measure_gpu(name, steps, warmup, device, seed_offset=0, profile=True, kernels="specialised"):
+def measure_gpu(name, steps, warmup, device, seed_offset=0, profile=True, kernels="paired"):
     import numpy as np
     import torch
 
@@ -361,7 +362,7 @@ def measure_training(device, steps=100):
                                    "MSE on sum_i <Z_i>, Adam lr 1e-2", "steps": steps}}
 
 
-def measure_e2e(name, steps, device, seed_offset=0, kernels="specialised"):
+def measure_e2e(name, steps, device, seed_offset=0, kernels="paired"):
     """End to end through the public API: pinned host inputs -> device,
     forward, adjoint, results -> pinned host, every step."""
     import numpy as np
@@ -567,8 +568,9 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="qnn12")
     ap.add_argument("--skip-n20", action="store_true")
-    ap.add_argument("--kernels", choices=["specialised", "general"], default="specialised",
-                    help="plan-specialised pass kernels (qtm_compile) or the general pass kernel")
+    ap.add_argument("--kernels", choices=["paired", "one-sample", "general"], default="paired",
+                    help="plan-specialised pass kernels (qtm_compile: two samples per CTA on f32x2 register "
+                         "pairs, or one sample per CTA) or the general pass kernel")
     ap.add_argument("--skip-extra", action="store_true", help="skip the uneven-batch and training lines")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle CPU work")

@@ -281,13 +281,18 @@ qtm_status qtm_multi_destroy(qtm_multi *multi);
 
 /* qtm_compile: specialise the plan's pass kernels.  The schedule is fixed
  * once a plan is built, so every register position, table slot, CZ sign
- * pattern and CNOT form of each pass is written out as CUDA source, compiled
- * with NVRTC for sm_103a (compiled images are cached on disk under
- * $QTM_JIT_CACHE, default /tmp/qtm_jit_cache) and loaded on the current
- * device; later qtm_forward / qtm_adjoint / qtm_jacobian calls on that device
- * launch them in place of the general pass kernel.  Applies to complex64
- * passes with tiles of >= 9 qubits.  flags: 0.  QTM_EUNSUPPORTED when NVRTC
- * is unavailable (the plan keeps the general kernels). */
+ * pattern, CNOT form and observable sign pattern of each pass is written out
+ * as CUDA source, compiled with NVRTC for sm_103a (compiled images are cached
+ * on disk under $QTM_JIT_CACHE, default /tmp/qtm_jit_cache) and loaded on the
+ * current device; later qtm_forward / qtm_adjoint / qtm_jacobian calls on that
+ * device launch them in place of the general pass kernel.  By default each CTA
+ * takes two samples, one per half of Blackwell's f32x2 register pairs (paired
+ * fma / mul / add); QTM_COMPILE_ONE_SAMPLE keeps one sample per CTA.  Applies
+ * to complex64 fused plans with tiles of >= 9 qubits (QTM_EUNSUPPORTED
+ * otherwise, or when NVRTC is unavailable; the plan keeps the general
+ * kernels).  Synchronises the device and drops the workspace and any stored
+ * forward state (the state layout changes). */
+#define QTM_COMPILE_ONE_SAMPLE 1
 qtm_status qtm_compile(qtm_plan *plan, int flags);
 
 /* Number of specialised pass kernels loaded for the current device (0 before

@@ -28,14 +28,15 @@ const char *qtm_debug_describe(const qtm_plan *plan);
 qtm_status qtm_debug_emulate(const qtm_plan *plan, int B, const double *x, const double *w,
                              const double *gE, double *E, double *gx, double *gw);
 
-/* Source of the specialised kernel qtm_compile would build for forward
- * (which = 0) or reverse (which = 1) pass `index` ("" if not eligible).  The
- * string is owned by the plan until the next call. */
-const char *qtm_debug_jit_source(const qtm_plan *plan, int which, int index);
+/* Source of the specialised kernel qtm_compile(plan, flags) would build for
+ * forward (which = 0) or reverse (which = 1) pass `index` ("" if not
+ * eligible).  The string is owned by the plan until the next call. */
+const char *qtm_debug_jit_source(const qtm_plan *plan, int which, int index, int flags);
 
-/* Generate and compile every eligible pass with NVRTC without loading it
- * (host only).  QTM_EINVAL with the compiler log in qtm_last_error on failure. */
-qtm_status qtm_debug_jit_compile(qtm_plan *plan);
+/* Generate and compile every pass with NVRTC as qtm_compile(plan, flags)
+ * would, without loading anything (host only).  QTM_EINVAL with the compiler
+ * log in qtm_last_error on failure. */
+qtm_status qtm_debug_jit_compile(qtm_plan *plan, int flags);
 
 #ifdef __cplusplus
 }

@@ -22,6 +22,7 @@ QTM_OK, QTM_EINVAL, QTM_ENOMEM, QTM_ECUDA, QTM_EUNSUPPORTED, QTM_ETIMEOUT, QTM_E
 QTM_C64, QTM_C128 = 0, 1
 QTM_PATH_AUTO, QTM_PATH_FUSED, QTM_PATH_NAIVE = 0, 1, 2
 QTM_ADJ_GW_PER_SAMPLE, QTM_ADJ_RECOMPUTE = 1, 2
+QTM_COMPILE_ONE_SAMPLE = 1
 
 
 class qtm_gate(ctypes.Structure):
@@ -90,9 +91,9 @@ def lib(build_if_missing: bool = True):
         L.qtm_compile.restype = ctypes.c_int
         L.qtm_compiled_passes.argtypes = [vp]
         L.qtm_compiled_passes.restype = ctypes.c_int
-        L.qtm_debug_jit_source.argtypes = [vp, i, i]
+        L.qtm_debug_jit_source.argtypes = [vp, i, i, i]
         L.qtm_debug_jit_source.restype = ctypes.c_char_p
-        L.qtm_debug_jit_compile.argtypes = [vp]
+        L.qtm_debug_jit_compile.argtypes = [vp, i]
         L.qtm_debug_jit_compile.restype = ctypes.c_int
         _LIB = L
     return _LIB
@@ -283,20 +284,23 @@ class Plan:
         self._raise(st, "qtm_adjoint")
         return gx, gw
 
-    def compile(self):
-        """Specialise and load this plan's pass kernels (qtm_compile)."""
-        self._raise(lib().qtm_compile(self.handle, 0), "qtm_compile")
+    def compile(self, pairs: bool = True):
+        """Specialise and load this plan's pass kernels (qtm_compile); pairs:
+        two samples per CTA on f32x2 register pairs."""
+        self._raise(lib().qtm_compile(self.handle, 0 if pairs else QTM_COMPILE_ONE_SAMPLE), "qtm_compile")
         return self
 
     def compiled_passes(self) -> int:
         return int(lib().qtm_compiled_passes(self.handle))
 
-    def jit_source(self, which: int, index: int) -> str:
-        return lib().qtm_debug_jit_source(self.handle, int(which), int(index)).decode()
+    def jit_source(self, which: int, index: int, pairs: bool = True) -> str:
+        flags = 0 if pairs else QTM_COMPILE_ONE_SAMPLE
+        return lib().qtm_debug_jit_source(self.handle, int(which), int(index), flags).decode()
 
-    def jit_compile_check(self):
+    def jit_compile_check(self, pairs: bool = True):
         """Compile every specialised pass with NVRTC, host only (no load)."""
-        self._raise(lib().qtm_debug_jit_compile(self.handle), "qtm_debug_jit_compile")
+        flags = 0 if pairs else QTM_COMPILE_ONE_SAMPLE
+        self._raise(lib().qtm_debug_jit_compile(self.handle, flags), "qtm_debug_jit_compile")
 
     def jacobian(self, x, w, out=None, stream=None):
         """J[b, m, g] = d<O_m>/d theta_g for every gate angle (zero for CZ/CNOT)."""

@@ -15,6 +15,8 @@
 #include "jit.h"
 #include "plan.h"
 
+#include <cstdio>
+#include <cstdlib>
 #include <thread>
 
 namespace qtm {
@@ -71,6 +73,7 @@ struct qtm_plan {
     // run-time specialised pass kernels (qtm_compile)
     std::vector<JitKernel> jit_fwd, jit_rev;
     int jit_device = -1;
+    int jit_pairs = 0;                 // loaded kernels take two samples per CTA
     std::string jit_src_cache;
     // profiling: events around each launch of the last forward / adjoint
     bool profiling = false;
@@ -245,6 +248,26 @@ qtm_status ensure_device(qtm_plan *p)
     return QTM_OK;
 }
 
+// Specialised kernels are loaded for the current device (all passes).
+bool jit_active(const qtm_plan *p)
+{
+    return p->jit_device >= 0 && p->jit_device == p->device;
+}
+
+// The state in HBM is laid out for paired-sample kernels.
+bool use_x2(const qtm_plan *p) { return jit_active(p) && p->jit_pairs; }
+
+cudaError_t launch_any(qtm_plan *p, bool rev, size_t i, PassArgs a, const CUtensorMap &t0, const CUtensorMap &t1,
+                       cudaStream_t s)
+{
+    const auto &v = rev ? p->jit_rev : p->jit_fwd;
+    if (jit_active(p) && i < v.size() && v[i].fn) {
+        a.smem_bytes = v[i].smem;
+        return jit_launch(v[i], a, t0, t1, s);
+    }
+    return launch_pass(p->P.dtype, rev, a, t0, t1, s);
+}
+
 qtm_status ensure_workspace(qtm_plan *p, int B)
 {
     if (B <= p->cap_B && p->d_phi) return QTM_OK;
@@ -262,8 +285,12 @@ qtm_status ensure_workspace(qtm_plan *p, int B)
         e = dmalloc(reinterpret_cast<void **>(&(ptr)), bytes);                          \
         if (e != cudaSuccess) { free_workspace(p); return fail(p, QTM_ENOMEM, "workspace allocation failed"); } \
     } while (0)
-    AL(p->d_phi, csize * NS * B);
-    if (p->needs_lam || P.path == QTM_PATH_NAIVE) AL(p->d_lam, csize * NS * B);
+    // paired-sample kernels: 16-byte elements per sample pair (an odd batch
+    // rounds up to a whole pair)
+    const bool x2 = use_x2(p);
+    const int Bq = x2 ? ((B + 1) & ~1) : B;
+    AL(p->d_phi, csize * NS * Bq);
+    if (p->needs_lam || P.path == QTM_PATH_NAIVE) AL(p->d_lam, csize * NS * Bq);
     AL(p->d_Escratch, rsize * (size_t)B * P.n_obs);
     AL(p->d_Epart, sizeof(double) * (size_t)B * tiles * P.n_obs);
     AL(p->d_Gpart, sizeof(double) * (size_t)B * runs * tiles * 3);
@@ -275,24 +302,26 @@ qtm_status ensure_workspace(qtm_plan *p, int B)
 #undef AL
     p->cap_B = B;
     if (P.path == QTM_PATH_FUSED) {
+        const int mdtype = x2 ? QTM_C128 : P.dtype;   // a pair element is laid out like a complex128
+        const int mB = x2 ? Bq / 2 : B;
         p->tm_fwd.assign(P.fwd.size(), CUtensorMap{});
         p->g_fwd.assign(P.fwd.size(), TmGeom{});
         p->tm_rev_phi.assign(P.rev.size(), CUtensorMap{});
         p->tm_rev_lam.assign(P.rev.size(), CUtensorMap{});
         p->g_rev.assign(P.rev.size(), TmGeom{});
         for (size_t i = 0; i < P.fwd.size(); ++i)
-            if (!make_tmap(&p->tm_fwd[i], p->d_phi, P.fwd[i], P.state_qubits, B, P.dtype, p->g_fwd[i])) {
+            if (!make_tmap(&p->tm_fwd[i], p->d_phi, P.fwd[i], P.state_qubits, mB, mdtype, p->g_fwd[i])) {
                 free_workspace(p);
                 return fail(p, QTM_ECUDA, "cuTensorMapEncodeTiled failed (forward)");
             }
         for (size_t i = 0; i < P.rev.size(); ++i) {
-            if (!make_tmap(&p->tm_rev_phi[i], p->d_phi, P.rev[i], P.state_qubits, B, P.dtype, p->g_rev[i])) {
+            if (!make_tmap(&p->tm_rev_phi[i], p->d_phi, P.rev[i], P.state_qubits, mB, mdtype, p->g_rev[i])) {
                 free_workspace(p);
                 return fail(p, QTM_ECUDA, "cuTensorMapEncodeTiled failed (reverse)");
             }
             TmGeom gl;
             void *lb = p->d_lam ? p->d_lam : p->d_phi;
-            if (!make_tmap(&p->tm_rev_lam[i], lb, P.rev[i], P.state_qubits, B, P.dtype, gl)) {
+            if (!make_tmap(&p->tm_rev_lam[i], lb, P.rev[i], P.state_qubits, mB, mdtype, gl)) {
                 free_workspace(p);
                 return fail(p, QTM_ECUDA, "cuTensorMapEncodeTiled failed (costate)");
             }
@@ -396,9 +425,7 @@ qtm_status run_forward_passes(qtm_plan *p, int B, const void *x, const void *w, 
     for (size_t i = 0; i < P.fwd.size(); ++i) {
         PassArgs a = pass_args(p, P.fwd[i], p->g_fwd[i], p->smem_fwd[i], B, x, w, nullptr);
         ProfScope ps(p, 0);
-        cudaError_t e = (p->jit_device == p->device && i < p->jit_fwd.size() && p->jit_fwd[i].fn)
-                            ? jit_launch(p->jit_fwd[i], a, p->tm_fwd[i], p->tm_fwd[i], s)
-                            : launch_pass(P.dtype, false, a, p->tm_fwd[i], p->tm_fwd[i], s);
+        cudaError_t e = launch_any(p, false, i, a, p->tm_fwd[i], p->tm_fwd[i], s);
         if (e != cudaSuccess) return cuda_fail(p, e, "forward pass launch");
     }
     return QTM_OK;
@@ -590,9 +617,7 @@ qtm_status qtm_adjoint(qtm_plan *p, int B, const void *gE, const void *x, const 
         PassArgs a = pass_args(p, P.rev[i], p->g_rev[i], p->smem_rev[i], B, x, w, gE);
         if (P.rev[i].store_phi) consumes = true;
         ProfScope ps(p, 0);
-        e = (p->jit_device == p->device && i < p->jit_rev.size() && p->jit_rev[i].fn)
-                ? jit_launch(p->jit_rev[i], a, p->tm_rev_phi[i], p->tm_rev_lam[i], s)
-                : launch_pass(P.dtype, true, a, p->tm_rev_phi[i], p->tm_rev_lam[i], s);
+        e = launch_any(p, true, i, a, p->tm_rev_phi[i], p->tm_rev_lam[i], s);
         if (e != cudaSuccess) return cuda_fail(p, e, "reverse pass launch");
     }
     FinalizeArgs f = finalize_args(p, B, x, w);
@@ -646,9 +671,7 @@ qtm_status qtm_jacobian(qtm_plan *p, int B, const void *x, const void *w, void *
         if (e != cudaSuccess) return cuda_fail(p, e, "one-hot cotangent");
         for (size_t i = 0; i < P.rev.size(); ++i) {
             PassArgs a = pass_args(p, P.rev[i], p->g_rev[i], p->smem_rev[i], B, x, w, p->d_onehot);
-            e = (p->jit_device == p->device && i < p->jit_rev.size() && p->jit_rev[i].fn)
-                    ? jit_launch(p->jit_rev[i], a, p->tm_rev_phi[i], p->tm_rev_lam[i], s)
-                    : launch_pass(P.dtype, true, a, p->tm_rev_phi[i], p->tm_rev_lam[i], s);
+            e = launch_any(p, true, i, a, p->tm_rev_phi[i], p->tm_rev_lam[i], s);
             if (e != cudaSuccess) return cuda_fail(p, e, "reverse pass launch");
         }
         FinalizeArgs f = finalize_args(p, B, x, w);
@@ -662,8 +685,9 @@ qtm_status qtm_jacobian(qtm_plan *p, int B, const void *x, const void *w, void *
 
 namespace {
 
-// Generate and compile every eligible pass (host only; NVRTC, no device).
-qtm_status compile_all(qtm_plan *p, std::vector<std::vector<char>> &fwd_bin, std::vector<std::vector<char>> &rev_bin)
+// Generate and compile every pass (host only; NVRTC, no device).
+qtm_status compile_all(qtm_plan *p, bool pairs, std::vector<std::vector<char>> &fwd_bin,
+                       std::vector<std::vector<char>> &rev_bin)
 {
     const Plan &P = p->P;
     if (P.path != QTM_PATH_FUSED) return fail(p, QTM_EUNSUPPORTED, "specialised kernels exist for fused plans");
@@ -672,16 +696,27 @@ qtm_status compile_all(qtm_plan *p, std::vector<std::vector<char>> &fwd_bin, std
     std::vector<Job> jobs;
     fwd_bin.assign(P.fwd.size(), {});
     rev_bin.assign(P.rev.size(), {});
-    for (size_t i = 0; i < P.fwd.size(); ++i)
-        if (jit_eligible(P, P.fwd[i])) jobs.push_back({&P.fwd[i], &fwd_bin[i], 3});
-    for (size_t i = 0; i < P.rev.size(); ++i)
-        if (jit_eligible(P, P.rev[i])) jobs.push_back({&P.rev[i], &rev_bin[i], 2});
+    // CTAs per SM the register budget is compiled for: the paired kernels hold
+    // twice the state per thread
+    int minb_f = pairs ? 2 : 3, minb_r = pairs ? 1 : 2;
+    if (const char *e = std::getenv("QTM_JIT_MINB")) {   // tuning: "<forward>,<reverse>"
+        int f = 0, r = 0;
+        if (std::sscanf(e, "%d,%d", &f, &r) == 2 && f >= 1 && f <= 8 && r >= 1 && r <= 8) { minb_f = f; minb_r = r; }
+    }
+    for (size_t i = 0; i < P.fwd.size(); ++i) {
+        if (!jit_eligible(P, P.fwd[i])) return fail(p, QTM_EUNSUPPORTED, "plan has passes the specialiser does not cover");
+        jobs.push_back({&P.fwd[i], &fwd_bin[i], minb_f});
+    }
+    for (size_t i = 0; i < P.rev.size(); ++i) {
+        if (!jit_eligible(P, P.rev[i])) return fail(p, QTM_EUNSUPPORTED, "plan has passes the specialiser does not cover");
+        jobs.push_back({&P.rev[i], &rev_bin[i], minb_r});
+    }
     std::vector<std::string> logs(jobs.size());
     std::vector<char> ok(jobs.size(), 0);
     std::vector<std::thread> th;
     for (size_t k = 0; k < jobs.size(); ++k)
         th.emplace_back([&, k] {
-            ok[k] = jit_compile(jit_source(P, *jobs[k].pd, jobs[k].minb), *jobs[k].out, logs[k]) ? 1 : 0;
+            ok[k] = jit_compile(jit_source(P, *jobs[k].pd, jobs[k].minb, pairs), *jobs[k].out, logs[k]) ? 1 : 0;
         });
     for (auto &t : th) t.join();
     for (size_t k = 0; k < jobs.size(); ++k)
@@ -694,25 +729,46 @@ qtm_status compile_all(qtm_plan *p, std::vector<std::vector<char>> &fwd_bin, std
 qtm_status qtm_compile(qtm_plan *p, int flags)
 {
     if (!p) return QTM_EINVAL;
-    if (flags != 0) return fail(p, QTM_EINVAL, "unknown flags");
+    if (flags & ~QTM_COMPILE_ONE_SAMPLE) return fail(p, QTM_EINVAL, "unknown flags");
     if (!jit_available()) return fail(p, QTM_EUNSUPPORTED, "NVRTC or driver entry points not available");
+    const bool pairs = !(flags & QTM_COMPILE_ONE_SAMPLE);
     qtm_status st = ensure_device(p);
     if (st != QTM_OK) return st;
     std::vector<std::vector<char>> fb, rb;
-    st = compile_all(p, fb, rb);
+    st = compile_all(p, pairs, fb, rb);
     if (st != QTM_OK) return st;
-    for (auto *v : {&p->jit_fwd, &p->jit_rev})
-        for (auto &k : *v) jit_unload(k);
+    cudaError_t e = cudaDeviceSynchronize();   // no launch of the old kernels or layout is in flight
+    if (e != cudaSuccess) return cuda_fail(p, e, "synchronize before loading kernels");
+    auto unload_all = [p] {
+        for (auto *v : {&p->jit_fwd, &p->jit_rev})
+            for (auto &k : *v) jit_unload(k);
+        p->jit_device = -1;
+    };
+    unload_all();
+    // the state layout in HBM changes with the kernels: drop the workspace and
+    // any stored forward state
+    free_workspace(p);
+    p->cap_B = 0;
+    p->fwd_valid = false;
     const Plan &P = p->P;
     p->jit_fwd.assign(P.fwd.size(), JitKernel{});
     p->jit_rev.assign(P.rev.size(), JitKernel{});
     std::string err;
-    for (size_t i = 0; i < P.fwd.size(); ++i)
-        if (!fb[i].empty() && !jit_load(fb[i], (int)p->smem_fwd[i], p->jit_fwd[i], err))
-            return fail(p, QTM_ECUDA, err);
-    for (size_t i = 0; i < P.rev.size(); ++i)
-        if (!rb[i].empty() && !jit_load(rb[i], (int)p->smem_rev[i], p->jit_rev[i], err))
-            return fail(p, QTM_ECUDA, err);
+    for (int rev = 0; rev < 2; ++rev) {
+        const auto &pds = rev ? P.rev : P.fwd;
+        auto &ks = rev ? p->jit_rev : p->jit_fwd;
+        const auto &bins = rev ? rb : fb;
+        const auto &gsm = rev ? p->smem_rev : p->smem_fwd;
+        for (size_t i = 0; i < pds.size(); ++i) {
+            const int smem = (int)(pairs ? jit_smem_bytes_x2(P, pds[i]) : gsm[i]);
+            if (!jit_load(bins[i], smem, ks[i], err)) {
+                unload_all();
+                return fail(p, QTM_ECUDA, err);
+            }
+            ks[i].pairs = pairs ? 1 : 0;
+        }
+    }
+    p->jit_pairs = pairs ? 1 : 0;
     p->jit_device = p->device;
     return QTM_OK;
 }
@@ -731,22 +787,25 @@ int qtm_compiled_passes(const qtm_plan *p)
     return n;
 }
 
-const char *qtm_debug_jit_source(const qtm_plan *p, int which, int index)
+const char *qtm_debug_jit_source(const qtm_plan *p, int which, int index, int flags)
 {
     if (!p) return "";
     const Plan &P = p->P;
     const auto &v = which ? P.rev : P.fwd;
     if (index < 0 || index >= (int)v.size()) return "";
     qtm_plan *m = const_cast<qtm_plan *>(p);
-    m->jit_src_cache = jit_eligible(P, v[index]) ? jit_source(P, v[index], which ? 2 : 3) : std::string();
+    const bool pairs = !(flags & QTM_COMPILE_ONE_SAMPLE);
+    m->jit_src_cache = jit_eligible(P, v[index])
+                           ? jit_source(P, v[index], pairs ? (which ? 1 : 2) : (which ? 2 : 3), pairs)
+                           : std::string();
     return m->jit_src_cache.c_str();
 }
 
-qtm_status qtm_debug_jit_compile(qtm_plan *p)
+qtm_status qtm_debug_jit_compile(qtm_plan *p, int flags)
 {
     if (!p) return QTM_EINVAL;
     std::vector<std::vector<char>> fb, rb;
-    return compile_all(p, fb, rb);
+    return compile_all(p, !(flags & QTM_COMPILE_ONE_SAMPLE), fb, rb);
 }
 
 qtm_status qtm_sync(qtm_plan *p, void *stream)

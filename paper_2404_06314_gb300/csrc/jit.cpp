@@ -47,21 +47,118 @@ std::string operand_bit(int o)
     return s.str();
 }
 
-void gen_diag(std::ostringstream &o, const Plan &P, const DevOp &op, int lo, bool rev)
+}  // namespace
+
+bool jit_eligible(const Plan &P, const PassDesc &pd)
+{
+    return P.path == QTM_PATH_FUSED && pd.K >= 9 && P.dtype == QTM_C64;
+}
+
+namespace {
+
+// tile-local Z mask of a term for the pass geometry (l, h, m)
+uint32_t local_mask(const PassDesc &pd, uint64_t zm)
+{
+    return (uint32_t)(zm & ((1ull << pd.l) - 1ull)) | (uint32_t)(((zm >> pd.h) & ((1ull << pd.m) - 1ull)) << pd.l);
+}
+
+// balanced sum of named f2 values: add2 tree
+std::string sum_tree(const std::vector<std::string> &v, size_t b, size_t e)
+{
+    if (e - b == 1) return v[b];
+    const size_t mid = b + (e - b) / 2;
+    return "add2(" + sum_tree(v, b, mid) + ", " + sum_tree(v, mid, e) + ")";
+}
+
+std::string signed_sum(const std::vector<std::string> &pos, const std::vector<std::string> &neg)
+{
+    if (pos.empty() && neg.empty()) return "0ull";
+    if (neg.empty()) return sum_tree(pos, 0, pos.size());
+    if (pos.empty()) return "(" + sum_tree(neg, 0, neg.size()) + " ^ kSign2)";
+    return "sub2(" + sum_tree(pos, 0, pos.size()) + ", " + sum_tree(neg, 0, neg.size()) + ")";
+}
+
+bool has_reg_bit(int x, int lo) { return x < kFixed && x >= lo && x < lo + kRegBits; }
+
+// <O_m> partials with the register sign pattern of every term a constant.
+void gen_expval_x2(std::ostringstream &o, const Plan &P, const PassDesc &pd, int lo)
+{
+    o << "        {\n            f2 pr[kRegs];\n#pragma unroll\n            for (int jj = 0; jj < kRegs; ++jj) "
+         "pr[jj] = fma2(p[jj].r, p[jj].r, mul2(p[jj].i, p[jj].i));\n";
+    std::vector<int> seen(16, 0);
+    for (const Term &t : P.terms) {
+        const int rm = (int)((local_mask(pd, t.zmask) >> lo) & 15u);
+        if (seen[rm]) continue;
+        seen[rm] = 1;
+        std::vector<std::string> pos, neg;
+        for (int jj = 0; jj < kRegs; ++jj)
+            (__builtin_popcount(jj & rm) & 1 ? neg : pos).push_back("pr[" + std::to_string(jj) + "]");
+        o << "            const f2 s" << rm << " = " << signed_sum(pos, neg) << ";\n";
+    }
+    for (int m = 0; m < P.n_obs; ++m) {
+        bool any = false;
+        for (size_t t = 0; t < P.terms.size(); ++t) {
+            if (P.terms[t].obs != m) continue;
+            if (!any) o << "            { f2 e = 0ull;\n";
+            any = true;
+            const uint32_t lm = local_mask(pd, P.terms[t].zmask);
+            const int rm = (int)((lm >> lo) & 15u);
+            o << "              e = fma2(S.tcoef[" << t << "] ^ ((__popc(xt & 0x" << std::hex << lm << std::dec
+              << "u) & 1u) ? kSign2 : 0ull), s" << rm << ", e);\n";
+        }
+        if (any)
+            o << "              e = warp_sum2(e); if (lane == 0) S.redE[warp * " << P.n_obs << " + " << m
+              << "] = e; }\n";
+    }
+    o << "        }\n";
+}
+
+// lam = (sum_m gE_m O_m) phi with constant register sign patterns.
+void gen_costate_x2(std::ostringstream &o, const Plan &P, const PassDesc &pd, int lo)
+{
+    o << "        {\n";
+    std::vector<std::vector<size_t>> by_rm(16);
+    for (size_t t = 0; t < P.terms.size(); ++t)
+        by_rm[(local_mask(pd, P.terms[t].zmask) >> lo) & 15u].push_back(t);
+    std::vector<int> rms;
+    for (int rm = 0; rm < 16; ++rm) {
+        if (by_rm[rm].empty()) continue;
+        rms.push_back(rm);
+        std::vector<std::string> parts;
+        for (size_t t : by_rm[rm]) {
+            std::ostringstream e;
+            e << "(S.tcoef[" << t << "] ^ ((__popc(xt & 0x" << std::hex << local_mask(pd, P.terms[t].zmask)
+              << std::dec << "u) & 1u) ? kSign2 : 0ull))";
+            parts.push_back(e.str());
+        }
+        o << "            const f2 c" << rm << " = " << sum_tree(parts, 0, parts.size()) << ";\n";
+    }
+    for (int jj = 0; jj < kRegs; ++jj) {
+        std::vector<std::string> pos, neg;
+        for (int rm : rms) (__builtin_popcount(jj & rm) & 1 ? neg : pos).push_back("c" + std::to_string(rm));
+        o << "            { const f2 d = " << signed_sum(pos, neg) << "; q[" << jj << "].r = mul2(d, p[" << jj
+          << "].r); q[" << jj << "].i = mul2(d, p[" << jj << "].i); }\n";
+    }
+    o << "        }\n";
+}
+
+// The DIAG sign mask of the thread's 16 registers as an expression (constant
+// part folded).
+std::string diag_mask(const Plan &P, const DevOp &op, int lo)
 {
     uint32_t C = 0;
     std::vector<std::vector<int>> per_reg(4);
     std::vector<std::pair<int, int>> other;
-    auto is_reg = [&](int x) { return x < kFixed && x >= lo && x < lo + kRegBits; };
     for (int k = op.a; k < op.a + op.b; ++k) {
         const DiagPair dp = P.diag_pairs[k];
-        const bool ra = is_reg(dp.a), rb = is_reg(dp.b);
+        const bool ra = has_reg_bit(dp.a, lo), rb = has_reg_bit(dp.b, lo);
         if (ra && rb) C ^= kRegMaskV[dp.a - lo] & kRegMaskV[dp.b - lo];
         else if (ra) per_reg[dp.a - lo].push_back(dp.b);
         else if (rb) per_reg[dp.b - lo].push_back(dp.a);
         else other.push_back({dp.a, dp.b});
     }
-    o << "    { uint32_t m = 0x" << std::hex << C << std::dec << "u;";
+    std::ostringstream o;
+    o << "uint32_t m = 0x" << std::hex << C << std::dec << "u;";
     for (int r = 0; r < 4; ++r) {
         if (per_reg[r].empty()) continue;
         o << " m ^= (0u - ((";
@@ -74,73 +171,86 @@ void gen_diag(std::ostringstream &o, const Plan &P, const DevOp &op, int lo, boo
             o << (i ? " ^ " : "") << "(" << operand_bit(other[i].first) << " & " << operand_bit(other[i].second) << ")";
         o << ") & 1u)) & 0xFFFFu;";
     }
-    o << " flip_mask<R, " << (rev ? "true" : "false") << ">(p, q, m); }\n";
+    return o.str();
 }
 
 }  // namespace
 
-bool jit_eligible(const Plan &P, const PassDesc &pd)
-{
-    return P.path == QTM_PATH_FUSED && pd.K >= 9 && P.dtype == QTM_C64;
-}
-
-std::string jit_source(const Plan &P, const PassDesc &pd, int min_blocks)
+std::string jit_source(const Plan &P, const PassDesc &pd, int min_blocks, bool pairs)
 {
     const bool rev = pd.reverse != 0;
     const int nslots = pd.slot_end - pd.slot_begin;
-    const char *R = P.dtype == QTM_C128 ? "double" : "float";
     std::ostringstream o;
     o << "namespace qtm {\nnamespace {\n";
-    o << "template <typename R>\n__device__ __forceinline__ void gen_phases(const TileJob &j, const TileSmem<R> &S, bool)\n{\n";
+    if (pairs)
+        o << "__device__ __forceinline__ void gen_phases(const TileJobX2 &j, const TileSmemX2 &S)\n{\n"
+          << "    using R = float;\n    A2 p[kRegs];\n    A2 q[kRegs];\n";
+    else
+        o << "template <typename R>\n__device__ __forceinline__ void gen_phases(const TileJob &j, const TileSmem<R> &S, "
+             "bool)\n{\n    Cx<R> p[kRegs];\n    Cx<R> q[kRegs];\n";
     o << "    const int tid = threadIdx.x;\n    const int warp = tid >> 5, lane = tid & 31;\n";
     o << "    const uint32_t base = j.base;\n    (void)base; (void)lane; (void)warp;\n";
-    o << "    Cx<R> p[kRegs];\n    Cx<R> q[kRegs];\n";
     bool lam_valid = rev && pd.lam_src == SRC_LOAD;
     for (int ph = pd.phase_begin; ph < pd.phase_end; ++ph) {
         const DevPhase &phs = P.phases[ph];
         const int lo = phs.lo;
         o << "    {\n        constexpr int LO = " << lo << ";\n";
         o << "        const uint32_t xt = ((uint32_t)tid & ((1u << LO) - 1u)) | (((uint32_t)tid >> LO) << (LO + 4));\n";
-        o << "        regs_load<R, LO, " << (lam_valid ? "true" : "false") << ">(p, q, S, xt);\n";
+        if (pairs) o << "        regs_load_x2<LO, " << (lam_valid ? "true" : "false") << ">(p, q, S, xt);\n";
+        else o << "        regs_load<R, LO, " << (lam_valid ? "true" : "false") << ">(p, q, S, xt);\n";
         for (int k = phs.op_begin; k < phs.op_end; ++k) {
             const DevOp &op = P.ops[k];
             // register operands must lie in this phase's 4-bit group; a schedule
             // that breaks this fails to compile instead of running
-            const bool reg_a = op.a >= lo && op.a < lo + kRegBits;
-            const bool reg_b = op.b >= lo && op.b < lo + kRegBits;
+            const bool reg_a = has_reg_bit(op.a, lo);
+            const bool reg_b = has_reg_bit(op.b, lo);
             if (((op.type == OP_U2 || op.type == OP_GRAD) && !reg_a) || (op.type == OP_CNOT && !reg_b) ||
                 ((op.type == OP_U2 || op.type == OP_GRAD) && (op.slot < 0 || op.slot >= nslots)) ||
                 (op.type == OP_DIAG && (op.a < 0 || op.a + op.b > (int)P.diag_pairs.size()))) {
                 o << "#error \"op " << k << " has an operand outside its phase\"\n";
                 continue;
             }
+            const int rb = op.a - lo;
             switch (op.type) {
             case OP_U2:
-                o << "        u2<" << (op.a - lo) << ">(p, S.mats + " << 4 * op.slot << ");\n";
+                if (pairs) o << "        u2x2<" << rb << ">(p, S.mats + " << 12 * op.slot << ");\n";
+                else o << "        u2<" << rb << ">(p, S.mats + " << 4 * op.slot << ");\n";
                 break;
-            case OP_GRAD: {
-                const int rb = op.a - lo;
-                o << "        { R vx = 0, vy = 0, vz = 0; grad_acc<" << rb << ">(p, q, vx, vy, vz);"
-                  << " vx = warp_sum(vx, 32, 0xffffffffu); vy = warp_sum(vy, 32, 0xffffffffu);"
-                  << " vz = warp_sum(vz, 32, 0xffffffffu);"
-                  << " if (lane == 0) { R *g = S.redG + warp * " << 3 * nslots << " + " << 3 * op.slot
-                  << "; g[0] = vx; g[1] = vy; g[2] = vz; }";
-                if (!(op.flags & OPF_SKIP_APPLY))
-                    o << " u2<" << rb << ">(p, S.mats + " << 4 * op.slot << "); u2<" << rb << ">(q, S.mats + "
-                      << 4 * op.slot << ");";
-                o << " }\n";
+            case OP_GRAD:
+                if (pairs) {
+                    o << "        { f2 vx, vy, vz; grad_x2<" << rb << ">(p, q, vx, vy, vz); grad_store_x2(S, " << nslots
+                      << ", " << op.slot << ", warp, lane, vx, vy, vz);";
+                    if (!(op.flags & OPF_SKIP_APPLY))
+                        o << " u2x2<" << rb << ">(p, S.mats + " << 12 * op.slot << "); u2x2<" << rb << ">(q, S.mats + "
+                          << 12 * op.slot << ");";
+                    o << " }\n";
+                } else {
+                    o << "        { R vx = 0, vy = 0, vz = 0; grad_acc<" << rb << ">(p, q, vx, vy, vz);"
+                      << " vx = warp_sum(vx, 32, 0xffffffffu); vy = warp_sum(vy, 32, 0xffffffffu);"
+                      << " vz = warp_sum(vz, 32, 0xffffffffu);"
+                      << " if (lane == 0) { R *g = S.redG + warp * " << 3 * nslots << " + " << 3 * op.slot
+                      << "; g[0] = vx; g[1] = vy; g[2] = vz; }";
+                    if (!(op.flags & OPF_SKIP_APPLY))
+                        o << " u2<" << rb << ">(p, S.mats + " << 4 * op.slot << "); u2<" << rb << ">(q, S.mats + "
+                          << 4 * op.slot << ");";
+                    o << " }\n";
+                }
                 break;
-            }
             case OP_DIAG:
-                o << "    ";
-                gen_diag(o, P, op, lo, rev);
+                o << "        { " << diag_mask(P, op, lo) << (pairs ? " flip_x2<" : " flip_mask<R, ")
+                  << (rev ? "true" : "false") << ">(p, q, m); }\n";
                 break;
             case OP_CNOT: {
                 const int rt = op.b - lo;
-                if (op.a < kFixed && op.a >= lo && op.a < lo + kRegBits) {
-                    o << "        cnot_static<" << (op.a - lo) << ", " << rt << ">(p);";
-                    if (rev) o << " cnot_static<" << (op.a - lo) << ", " << rt << ">(q);";
+                if (has_reg_bit(op.a, lo)) {
+                    const char *f = pairs ? "cnot_static_x2<" : "cnot_static<";
+                    o << "        " << f << (op.a - lo) << ", " << rt << ">(p);";
+                    if (rev) o << " " << f << (op.a - lo) << ", " << rt << ">(q);";
                     o << "\n";
+                } else if (pairs) {
+                    o << "        { const int c = (int)(" << operand_bit(op.a) << " & 1u); cnot_x2<" << rt << ">(p, c);";
+                    if (rev) o << " cnot_x2<" << rt << ">(q, c);";
+                    o << " }\n";
                 } else {
                     o << "        { const int c = (int)(" << operand_bit(op.a) << " & 1u); cnot_regs<" << rt
                       << ">(p, -1, c);";
@@ -150,16 +260,19 @@ std::string jit_source(const Plan &P, const PassDesc &pd, int min_blocks)
                 break;
             }
             case OP_EXPVAL:
-                o << "        op_expval<R>(p, S, j, xt, LO, warp, lane, 32, 0xffffffffu);\n";
+                if (pairs) gen_expval_x2(o, P, pd, lo);
+                else o << "        op_expval<R>(p, S, j, xt, LO, warp, lane, 32, 0xffffffffu);\n";
                 break;
             case OP_COSTATE:
-                o << "        op_costate<R>(p, q, S, j, xt, LO);\n";
+                if (pairs) gen_costate_x2(o, P, pd, lo);
+                else o << "        op_costate<R>(p, q, S, j, xt, LO);\n";
                 break;
             default:
                 break;
             }
         }
-        o << "        regs_store<R, LO, " << (rev ? "true" : "false") << ">(p, q, S, xt);\n";
+        if (pairs) o << "        regs_store_x2<LO, " << (rev ? "true" : "false") << ">(p, q, S, xt);\n";
+        else o << "        regs_store<R, LO, " << (rev ? "true" : "false") << ">(p, q, S, xt);\n";
         o << "        __syncthreads();\n    }\n";
         if (rev) lam_valid = true;
     }
@@ -167,10 +280,22 @@ std::string jit_source(const Plan &P, const PassDesc &pd, int min_blocks)
     o << "extern \"C\" __global__ void __launch_bounds__(256, " << min_blocks << ") qtm_gen_pass("
       << "const __grid_constant__ qtm::PassArgs a, const __grid_constant__ CUtensorMap tm_phi, "
       << "const __grid_constant__ CUtensorMap tm_lam)\n{\n";
-    o << "    qtm::pass_body<" << R << ", " << (rev ? "true" : "false") << ">(a, &tm_phi, &tm_lam, "
-      << "[](const qtm::TileJob &j, const qtm::TileSmem<" << R << "> &S, bool lv) { qtm::gen_phases<" << R
-      << ">(j, S, lv); });\n}\n";
+    if (pairs)
+        o << "    qtm::pass_body_x2<" << (rev ? "true" : "false") << ">(a, &tm_phi, &tm_lam, "
+          << "[](const qtm::TileJobX2 &j, const qtm::TileSmemX2 &S) { qtm::gen_phases(j, S); });\n}\n";
+    else
+        o << "    qtm::pass_body<float, " << (rev ? "true" : "false") << ">(a, &tm_phi, &tm_lam, "
+          << "[](const qtm::TileJob &j, const qtm::TileSmem<float> &S, bool lv) { qtm::gen_phases<float>(j, S, lv); "
+             "});\n}\n";
     return o.str();
+}
+
+size_t jit_smem_bytes_x2(const Plan &P, const PassDesc &pd)
+{
+    const int nwarps = (1 << (pd.K - 4)) >> 5;
+    const LayoutX2 L = make_layout_x2(pd.K, pd.reverse != 0, pd.slot_end - pd.slot_begin, (int)P.terms.size(),
+                                      P.n_obs, P.state_qubits, pd.analytic_ents, nwarps, (int)sizeof(Ent));
+    return (size_t)L.total + 1024;
 }
 
 // ---- NVRTC and the driver API ---------------------------------------------------
@@ -270,12 +395,15 @@ bool jit_compile(const std::string &body, std::vector<char> &cubin, std::string 
     const Nvrtc &N = nvrtc();
     if (!N.ok) { log = "NVRTC not found"; return false; }
     const std::string src = std::string(kJitPrelude) + "\n" + body;
-    const char *opts[] = {"--gpu-architecture=sm_103a", "-std=c++17", "-lineinfo"};
-    const int nopts = 3;
+    // QTM_JIT_VERBOSE=1: bypass the cache and print ptxas resource usage
+    const char *vb = std::getenv("QTM_JIT_VERBOSE");
+    const bool verbose = vb && *vb == '1';
+    const char *opts[] = {"--gpu-architecture=sm_103a", "-std=c++17", "-lineinfo", "--ptxas-options=-v"};
+    const int nopts = verbose ? 4 : 3;
     char key[32];
     std::snprintf(key, sizeof(key), "%016llx", (unsigned long long)fnv1a(src));
     const std::string dir = cache_dir(), path = dir + "/" + key + ".cubin";
-    if (read_file(path, cubin)) return true;
+    if (!verbose && read_file(path, cubin)) return true;
     nvrtcProgram prog;
     if (N.create(&prog, src.c_str(), "qtm_gen.cu", 0, nullptr, nullptr) != NVRTC_SUCCESS) {
         log = "nvrtcCreateProgram failed";
@@ -298,6 +426,7 @@ bool jit_compile(const std::string &body, std::vector<char> &cubin, std::string 
         }
     }
     N.destroy(&prog);
+    if (verbose) std::fprintf(stderr, "%s\n", log.c_str());
     if (ok) {   // best-effort disk cache keyed by the source hash
         ::mkdir(dir.c_str(), 0755);
         const std::string tmp = path + ".tmp" + std::to_string((unsigned long long)::getpid());
@@ -326,6 +455,7 @@ bool jit_load(const std::vector<char> &cubin, int smem, JitKernel &k, std::strin
     }
     k.mod = mod;
     k.fn = fn;
+    k.smem = smem;
     return true;
 }
 
@@ -342,7 +472,8 @@ cudaError_t jit_launch(const JitKernel &k, const PassArgs &a, const CUtensorMap 
     PassArgs args = a;
     CUtensorMap t0 = tm_phi, t1 = tm_lam;
     void *params[] = {&args, &t0, &t1};
-    const unsigned grid = (unsigned)a.B * (unsigned)a.tiles, block = 1u << (a.K - 4);
+    const unsigned units = k.pairs ? (unsigned)(a.B + 1) / 2u : (unsigned)a.B;
+    const unsigned grid = units * (unsigned)a.tiles, block = 1u << (a.K - 4);
     CUresult r = drv().launch(static_cast<CUfunction>(k.fn), grid, 1, 1, block, 1, 1, (unsigned)a.smem_bytes,
                               reinterpret_cast<CUstream>(s), params, nullptr);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorLaunchFailure;

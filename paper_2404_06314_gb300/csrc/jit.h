@@ -14,6 +14,8 @@ namespace qtm {
 struct JitKernel {
     void *mod = nullptr;   // CUmodule
     void *fn = nullptr;    // CUfunction
+    int smem = 0;          // dynamic shared memory per CTA
+    int pairs = 0;         // 1: two samples per CTA (tile_x2.cuh)
 };
 
 // Passes worth specialising: fused complex64 passes whose tile has >= 9 qubits
@@ -21,7 +23,10 @@ struct JitKernel {
 bool jit_eligible(const Plan &P, const PassDesc &pd);
 bool jit_available();
 bool jit_nvrtc_available();
-std::string jit_source(const Plan &P, const PassDesc &pd, int min_blocks);
+// Generated source of one pass; pairs: two samples per CTA on f32x2 register
+// pairs (tile_x2.cuh), else one sample per CTA (tile.cuh).
+std::string jit_source(const Plan &P, const PassDesc &pd, int min_blocks, bool pairs);
+size_t jit_smem_bytes_x2(const Plan &P, const PassDesc &pd);
 bool jit_compile(const std::string &body, std::vector<char> &cubin, std::string &log);
 bool jit_load(const std::vector<char> &cubin, int smem, JitKernel &k, std::string &err);
 void jit_unload(JitKernel &k);

@@ -1,13 +1,16 @@
 """Run-time specialised pass kernels (qtm_compile).
 
-Host part (no GPU): the source written for every eligible pass of the
-benchmark workloads and of random circuits compiles with NVRTC for sm_103a,
-every pass of a complex64 plan with 2^9..2^12-amplitude tiles is eligible, and
-complex128 / naive plans are not specialised.
+Two kinds of specialised kernel: paired (default; two samples per CTA, one
+per half of an f32x2 register pair) and one-sample.
+
+Host part (no GPU): the source written for every pass of the benchmark
+workloads and of random circuits compiles with NVRTC for sm_103a in both
+kinds, and complex128 / naive / small-tile plans are not specialised.
 
 GPU part: a compiled plan gives the oracle's E, grad_x and per-sample grad_w
 within the complex64 bound (1e-5), the specialised kernels are the ones that
-ran (qtm_compiled_passes), and results agree with the general pass kernel's.
+ran (qtm_compiled_passes), and results agree with the general pass kernel's
+(odd batches included: the paired kernel's last CTA holds one sample).
 """
 import numpy as np
 import pytest
@@ -17,9 +20,9 @@ import oracle_pins as P
 from paper_2404_06314_gb300 import capi, workloads as W
 
 
-def _nvrtc_or_skip(plan):
+def _nvrtc_or_skip(plan, pairs=True):
     try:
-        plan.jit_compile_check()
+        plan.jit_compile_check(pairs=pairs)
     except capi.QtmError as e:
         if e.status == capi.QTM_EUNSUPPORTED:
             pytest.skip("NVRTC not available")
@@ -33,21 +36,24 @@ def _rand(n, seed):
     return c
 
 
-def test_generated_source_compiles_benchmarks():
+@pytest.mark.parametrize("pairs", [True, False])
+def test_generated_source_compiles_benchmarks(pairs):
     for c in [W.workload_12q(), W.workload_20q(), W.workload_16q_train()]:
         plan = capi.Plan(c, dtype="c64")
         info = plan.info
         for which, count in ((0, info["fwd_passes"]), (1, info["adj_passes"])):
             for i in range(count):
-                src = plan.jit_source(which, i)
+                src = plan.jit_source(which, i, pairs=pairs)
                 assert "qtm_gen_pass" in src and "gen_phases" in src, (c.name, which, i)
-        _nvrtc_or_skip(plan)
+                assert ("pass_body_x2" in src) == pairs
+                assert "#error" not in src
+        _nvrtc_or_skip(plan, pairs)
 
 
 @pytest.mark.parametrize("n", [9, 13])
 def test_generated_source_compiles_random(n):
     plan = capi.Plan(_rand(n, 500 + n), dtype="c64")
-    _nvrtc_or_skip(plan)
+    _nvrtc_or_skip(plan, True)
 
 
 def test_not_specialised():
@@ -70,8 +76,8 @@ def _run(plan, c, inp):
     return [t.double().cpu().numpy() for t in (E, gx, gw)]
 
 
-CASES = [("qnn12", 37), ("qnn20", 2), ("qnn16", 3), ("rand9", 3), ("rand11", 3), ("rand13", 3), ("rand14", 2),
-         ("rand16", 2)]
+CASES = [("qnn12", 37), ("qnn12", 1), ("qnn20", 2), ("qnn20", 3), ("qnn16", 3), ("rand9", 3), ("rand11", 4),
+         ("rand13", 3), ("rand14", 2), ("rand16", 5)]
 
 
 def _circuit(name):
@@ -80,13 +86,14 @@ def _circuit(name):
 
 
 @pytest.mark.gpu
+@pytest.mark.parametrize("pairs", [True, False])
 @pytest.mark.parametrize("name,B", CASES)
-def test_compiled_plan_matches_oracle(name, B):
+def test_compiled_plan_matches_oracle(name, B, pairs):
     c = _circuit(name)
     inp = W.make_inputs(c, B, 21, real_dtype=np.float32)
     general = _run(capi.Plan(c, dtype="c64"), c, inp)
     plan = capi.Plan(c, dtype="c64")
-    plan.compile()
+    plan.compile(pairs=pairs)
     info = plan.info
     assert plan.compiled_passes() == info["fwd_passes"] + info["adj_passes"]
     got = _run(plan, c, inp)
@@ -94,9 +101,9 @@ def test_compiled_plan_matches_oracle(name, B):
     _, gxo, gwo = oracle.adjoint(c, inp.gE, inp.x, inp.w, threads=0)
     for what, g, r, h in zip(("E", "gx", "gw"), got, (Eo, gxo, gwo), general):
         err = float(np.max(np.abs(g - r))) if r.size else 0.0
-        assert err <= 1e-5, f"{name} compiled {what}: {err:.3e}"
+        assert err <= 1e-5, f"{name} B={B} pairs={pairs} {what}: {err:.3e}"
         d = float(np.max(np.abs(g - h))) if h.size else 0.0
-        assert d <= 2e-6, f"{name} compiled vs general {what}: {d:.3e}"
+        assert d <= 2e-6, f"{name} B={B} pairs={pairs} compiled vs general {what}: {d:.3e}"
 
 
 @pytest.mark.gpu
@@ -118,3 +125,29 @@ def test_compiled_plan_jacobian_and_full_batch():
     J = plan.jacobian(x, w).double().cpu().numpy()
     Jo = oracle.jacobian(c, inp.x[:2], inp.w, threads=0)
     assert np.max(np.abs(J - Jo)) <= 1e-5
+
+
+@pytest.mark.gpu
+def test_compile_after_forward_and_recompute():
+    """qtm_compile drops the stored state (its layout changes): an adjoint
+    right after it asks for a new forward; recompute works; the general
+    kernel's results on the same plan before compiling agree."""
+    import torch
+    c = W.workload_20q()
+    plan = capi.Plan(c, dtype="c64")
+    inp = W.make_inputs(c, 3, 5, real_dtype=np.float32)
+    x = torch.tensor(inp.x, dtype=torch.float32, device="cuda")
+    w = torch.tensor(inp.w, dtype=torch.float32, device="cuda")
+    gE = torch.tensor(inp.gE, dtype=torch.float32, device="cuda")
+    E0 = plan.forward(x, w).double().cpu().numpy()
+    plan.compile()
+    with pytest.raises(capi.QtmError) as ei:
+        plan.adjoint(gE, x, w)
+    assert ei.value.status == capi.QTM_ESTATE
+    gx, gw = plan.adjoint(gE, x, w, recompute=True, per_sample_w=True)
+    plan.sync()
+    _, gxo, gwo = oracle.adjoint(c, inp.gE, inp.x, inp.w, threads=0)
+    assert np.max(np.abs(gx.double().cpu().numpy() - gxo)) <= 1e-5
+    assert np.max(np.abs(gw.double().cpu().numpy() - gwo)) <= 1e-5
+    E1 = plan.forward(x, w).double().cpu().numpy()
+    assert np.max(np.abs(E1 - E0)) <= 2e-6

@@ -279,6 +279,17 @@ qtm_status qtm_multi_get_config(const qtm_multi *multi, qtm_multi_config *cfg);
 qtm_status qtm_multi_set_config(qtm_multi *multi, const qtm_multi_config *cfg);
 qtm_status qtm_multi_destroy(qtm_multi *multi);
 
+/* qtm_set_sample_pairing: run the plan's passes on the paired general kernel
+ * (on = 1: two samples per CTA, one per half of Blackwell's f32x2 register
+ * pairs, op tables read at run time) or the one-sample kernel (on = 0, the
+ * default).  Same results within rounding.  Needs a fused complex64 plan with
+ * tiles of >= 9 qubits (QTM_EUNSUPPORTED otherwise).  Changing it drops the
+ * workspace and any stored forward state (the state layout changes); it waits
+ * for the device when a workspace exists.  Specialised kernels loaded by
+ * qtm_compile take precedence while they are loaded. */
+qtm_status qtm_set_sample_pairing(qtm_plan *plan, int on);
+int qtm_get_sample_pairing(const qtm_plan *plan);
+
 /* qtm_compile: specialise the plan's pass kernels.  The schedule is fixed
  * once a plan is built, so every register position, table slot, CZ sign
  * pattern, CNOT form and observable sign pattern of each pass is written out

@@ -89,6 +89,10 @@ def lib(build_if_missing: bool = True):
         L.qtm_debug_emulate.argtypes = [vp, i, vp, vp, vp, vp, vp, vp]
         L.qtm_compile.argtypes = [vp, i]
         L.qtm_compile.restype = ctypes.c_int
+        L.qtm_set_sample_pairing.argtypes = [vp, i]
+        L.qtm_set_sample_pairing.restype = ctypes.c_int
+        L.qtm_get_sample_pairing.argtypes = [vp]
+        L.qtm_get_sample_pairing.restype = ctypes.c_int
         L.qtm_compiled_passes.argtypes = [vp]
         L.qtm_compiled_passes.restype = ctypes.c_int
         L.qtm_debug_jit_source.argtypes = [vp, i, i, i]
@@ -289,6 +293,15 @@ class Plan:
         two samples per CTA on f32x2 register pairs."""
         self._raise(lib().qtm_compile(self.handle, 0 if pairs else QTM_COMPILE_ONE_SAMPLE), "qtm_compile")
         return self
+
+    def set_pairing(self, on: bool = True):
+        """Run passes on the paired general kernel (two samples per CTA)."""
+        self._raise(lib().qtm_set_sample_pairing(self.handle, 1 if on else 0), "qtm_set_sample_pairing")
+        return self
+
+    @property
+    def pairing(self) -> bool:
+        return bool(lib().qtm_get_sample_pairing(self.handle))
 
     def compiled_passes(self) -> int:
         return int(lib().qtm_compiled_passes(self.handle))

@@ -63,6 +63,8 @@ struct qtm_plan {
     std::vector<CUtensorMap> tm_fwd, tm_rev_phi, tm_rev_lam;
     std::vector<TmGeom> g_fwd, g_rev;
     std::vector<size_t> smem_fwd, smem_rev;
+    std::vector<size_t> smem_fwd_x2, smem_rev_x2;   // paired-sample kernels (eligible plans)
+    int pairing = 0;                   // general passes run two samples per CTA (k_pass_x2)
     bool needs_lam = false;
     // stored forward
     bool fwd_valid = false;
@@ -255,7 +257,17 @@ bool jit_active(const qtm_plan *p)
 }
 
 // The state in HBM is laid out for paired-sample kernels.
-bool use_x2(const qtm_plan *p) { return jit_active(p) && p->jit_pairs; }
+bool use_x2(const qtm_plan *p) { return jit_active(p) ? p->jit_pairs != 0 : p->pairing != 0; }
+
+// Every pass can run on the paired / specialised kernels.
+bool pairable(const Plan &P)
+{
+    if (P.path != QTM_PATH_FUSED) return false;
+    for (const auto *v : {&P.fwd, &P.rev})
+        for (const auto &pd : *v)
+            if (!jit_eligible(P, pd)) return false;
+    return true;
+}
 
 cudaError_t launch_any(qtm_plan *p, bool rev, size_t i, PassArgs a, const CUtensorMap &t0, const CUtensorMap &t1,
                        cudaStream_t s)
@@ -264,6 +276,10 @@ cudaError_t launch_any(qtm_plan *p, bool rev, size_t i, PassArgs a, const CUtens
     if (jit_active(p) && i < v.size() && v[i].fn) {
         a.smem_bytes = v[i].smem;
         return jit_launch(v[i], a, t0, t1, s);
+    }
+    if (p->pairing) {
+        a.smem_bytes = (int)(rev ? p->smem_rev_x2[i] : p->smem_fwd_x2[i]);
+        return launch_pass_x2(rev, a, t0, t1, s);
     }
     return launch_pass(p->P.dtype, rev, a, t0, t1, s);
 }
@@ -504,6 +520,14 @@ qtm_status qtm_build(int n_qubits, const qtm_gate *gates, int n_gates, const qtm
         };
         for (const auto &pd : P.fwd) p->smem_fwd.push_back(sm(pd, false));
         for (const auto &pd : P.rev) p->smem_rev.push_back(sm(pd, true));
+        if (pairable(P)) {
+            auto sm2 = [&](const PassDesc &pd, bool rev) {
+                return pass_smem_bytes_x2(pd.K, rev, pd.slot_end - pd.slot_begin, (int)P.terms.size(), P.n_obs,
+                                          P.state_qubits, pd.phi_src == SRC_ANALYTIC ? pd.analytic_ents : 0);
+            };
+            for (const auto &pd : P.fwd) p->smem_fwd_x2.push_back(sm2(pd, false));
+            for (const auto &pd : P.rev) p->smem_rev_x2.push_back(sm2(pd, true));
+        }
         for (size_t v : p->smem_fwd)
             if (v > kMaxDynSmem) { delete p; return QTM_EUNSUPPORTED; }
         for (size_t v : p->smem_rev)
@@ -725,6 +749,31 @@ qtm_status compile_all(qtm_plan *p, bool pairs, std::vector<std::vector<char>> &
 }
 
 }  // namespace
+
+qtm_status qtm_set_sample_pairing(qtm_plan *p, int on)
+{
+    if (!p) return QTM_EINVAL;
+    if (on != 0 && on != 1) return fail(p, QTM_EINVAL, "on must be 0 or 1");
+    if (on && !pairable(p->P)) return fail(p, QTM_EUNSUPPORTED, "pairing needs a fused complex64 plan with tiles of >= 9 qubits");
+    if (on) {
+        for (size_t v : p->smem_fwd_x2)
+            if (v > kMaxDynSmem) return fail(p, QTM_EUNSUPPORTED, "paired tile exceeds shared memory");
+        for (size_t v : p->smem_rev_x2)
+            if (v > kMaxDynSmem) return fail(p, QTM_EUNSUPPORTED, "paired tile exceeds shared memory");
+    }
+    if (p->pairing == on) return QTM_OK;
+    if (p->d_phi) {   // the state layout changes: no launch may still use the old workspace
+        cudaError_t e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) return cuda_fail(p, e, "synchronize before changing the state layout");
+    }
+    free_workspace(p);
+    p->cap_B = 0;
+    p->fwd_valid = false;
+    p->pairing = on;
+    return QTM_OK;
+}
+
+int qtm_get_sample_pairing(const qtm_plan *p) { return p ? p->pairing : 0; }
 
 qtm_status qtm_compile(qtm_plan *p, int flags)
 {

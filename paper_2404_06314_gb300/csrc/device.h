@@ -41,6 +41,11 @@ cudaError_t launch_prep(int dtype, const PrepArgs &a, cudaStream_t s);
 size_t pass_smem_bytes(int K, int dtype, bool reverse, int nslots, int n_terms, int M,
                        int state_qubits, int n_prefix_ents);
 
+// Paired-sample pass kernel (two samples per CTA, complex64, K >= 9): grid
+// ceil(B / 2) * tiles; state laid out as 16-byte pair elements.
+cudaError_t launch_pass_x2(bool reverse, const PassArgs &a, const CUtensorMap &tm_phi, const CUtensorMap &tm_lam,
+                           cudaStream_t s);
+size_t pass_smem_bytes_x2(int K, bool reverse, int nslots, int n_terms, int M, int sq, int n_ents);
 cudaError_t launch_pass(int dtype, bool reverse, const PassArgs &a, const CUtensorMap &tm_phi,
                         const CUtensorMap &tm_lam, cudaStream_t s);
 cudaError_t launch_expval_finalize(int dtype, const FinalizeArgs &f, cudaStream_t s);

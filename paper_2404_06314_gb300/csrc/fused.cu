@@ -14,6 +14,7 @@
 
 #include "device.h"
 #include "tile.cuh"
+#include "tile_x2.cuh"
 
 namespace qtm {
 
@@ -38,6 +39,17 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 1 : (REV ? 2 : 3)) k_pas
 {
     pass_body<R, REV>(a, &tm_phi, &tm_lam, [](const TileJob &j, const TileSmem<R> &S, bool lam_valid) {
         run_phases<R, REV>(j, S, lam_valid);
+    });
+}
+
+// Two samples per CTA on f32x2 register pairs (tile_x2.cuh); complex64, K >= 9.
+template <bool REV>
+__global__ void __launch_bounds__(256, REV ? 1 : 2) k_pass_x2(const __grid_constant__ PassArgs a,
+                                                             const __grid_constant__ CUtensorMap tm_phi,
+                                                             const __grid_constant__ CUtensorMap tm_lam)
+{
+    pass_body_x2<REV>(a, &tm_phi, &tm_lam, [](const TileJobX2 &j, const TileSmemX2 &S, bool lam_valid) {
+        run_phases_x2<REV>(j, S, lam_valid);
     });
 }
 
@@ -134,6 +146,24 @@ size_t pass_smem_bytes(int K, int dtype, bool reverse, int nslots, int n_terms, 
     Layout L = make_layout(K, csize, reverse, nslots, n_terms, M, state_qubits, n_prefix_ents,
                            nwarps, rsize);
     return (size_t)L.total + 1024;
+}
+
+size_t pass_smem_bytes_x2(int K, bool reverse, int nslots, int n_terms, int M, int sq, int n_ents)
+{
+    const LayoutX2 L = make_layout_x2(K, reverse, nslots, n_terms, M, sq, n_ents, (1 << (K - 4)) >> 5, (int)sizeof(Ent));
+    return (size_t)L.total + 1024;
+}
+
+cudaError_t launch_pass_x2(bool reverse, const PassArgs &a, const CUtensorMap &tm_phi, const CUtensorMap &tm_lam,
+                           cudaStream_t s)
+{
+    const dim3 grid((unsigned)((a.B + 1) / 2) * (unsigned)a.tiles), block(1u << (a.K - 4));
+    const size_t smem = (size_t)a.smem_bytes;
+    auto fn = reverse ? k_pass_x2<true> : k_pass_x2<false>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    fn<<<grid, block, smem, s>>>(a, tm_phi, tm_lam);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_pass(int dtype, bool reverse, const PassArgs &a, const CUtensorMap &tm_phi,

@@ -174,14 +174,130 @@ std::string diag_mask(const Plan &P, const DevOp &op, int lo)
     return o.str();
 }
 
+// Body of one phase with its run slots written relative to the phase's first
+// slot `sb` (a runtime value): layers of a layered circuit repeat the same
+// body with other slots and then share one copy of the code.
+std::string phase_body(const Plan &P, const PassDesc &pd, const DevPhase &phs, bool lam_valid, bool pairs, int sb)
+{
+    const bool rev = pd.reverse != 0;
+    const int nslots = pd.slot_end - pd.slot_begin;
+    const int lo = phs.lo;
+    std::ostringstream o;
+    auto slot = [&](int s) { return "(sb + " + std::to_string(s - sb) + ")"; };
+    o << "        constexpr int LO = " << lo << ";\n";
+    o << "        const uint32_t xt = ((uint32_t)tid & ((1u << LO) - 1u)) | (((uint32_t)tid >> LO) << (LO + 4));\n";
+    if (pairs) o << "        regs_load_x2<LO, " << (lam_valid ? "true" : "false") << ">(p, q, S, xt);\n";
+    else o << "        regs_load<R, LO, " << (lam_valid ? "true" : "false") << ">(p, q, S, xt);\n";
+    for (int k = phs.op_begin; k < phs.op_end; ++k) {
+        const DevOp &op = P.ops[k];
+        // register operands must lie in this phase's 4-bit group; a schedule
+        // that breaks this fails to compile instead of running
+        const bool reg_a = has_reg_bit(op.a, lo);
+        const bool reg_b = has_reg_bit(op.b, lo);
+        if (((op.type == OP_U2 || op.type == OP_GRAD) && !reg_a) || (op.type == OP_CNOT && !reg_b) ||
+            ((op.type == OP_U2 || op.type == OP_GRAD) && (op.slot < 0 || op.slot >= nslots)) ||
+            (op.type == OP_DIAG && (op.a < 0 || op.a + op.b > (int)P.diag_pairs.size()))) {
+            o << "#error \"op " << k << " has an operand outside its phase\"\n";
+            continue;
+        }
+        const int rb = op.a - lo;
+        switch (op.type) {
+        case OP_U2:
+            if (pairs) o << "        u2x2<" << rb << ">(p, S.mats + 12 * " << slot(op.slot) << ");\n";
+            else o << "        u2<" << rb << ">(p, S.mats + 4 * " << slot(op.slot) << ");\n";
+            break;
+        case OP_GRAD:
+            if (pairs) {
+                o << "        { f2 vx, vy, vz; grad_x2<" << rb << ">(p, q, vx, vy, vz); grad_store_x2(S, " << nslots
+                  << ", " << slot(op.slot) << ", warp, lane, vx, vy, vz);";
+                if (!(op.flags & OPF_SKIP_APPLY))
+                    o << " u2x2<" << rb << ">(p, S.mats + 12 * " << slot(op.slot) << "); u2x2<" << rb
+                      << ">(q, S.mats + 12 * " << slot(op.slot) << ");";
+                o << " }\n";
+            } else {
+                o << "        { R vx = 0, vy = 0, vz = 0; grad_acc<" << rb << ">(p, q, vx, vy, vz);"
+                  << " vx = warp_sum(vx, 32, 0xffffffffu); vy = warp_sum(vy, 32, 0xffffffffu);"
+                  << " vz = warp_sum(vz, 32, 0xffffffffu);"
+                  << " if (lane == 0) { R *g = S.redG + warp * " << 3 * nslots << " + 3 * " << slot(op.slot)
+                  << "; g[0] = vx; g[1] = vy; g[2] = vz; }";
+                if (!(op.flags & OPF_SKIP_APPLY))
+                    o << " u2<" << rb << ">(p, S.mats + 4 * " << slot(op.slot) << "); u2<" << rb << ">(q, S.mats + 4 * "
+                      << slot(op.slot) << ");";
+                o << " }\n";
+            }
+            break;
+        case OP_DIAG:
+            o << "        { " << diag_mask(P, op, lo) << (pairs ? " flip_x2<" : " flip_mask<R, ")
+              << (rev ? "true" : "false") << ">(p, q, m); }\n";
+            break;
+        case OP_CNOT: {
+            const int rt = op.b - lo;
+            if (has_reg_bit(op.a, lo)) {
+                const char *f = pairs ? "cnot_static_x2<" : "cnot_static<";
+                o << "        " << f << (op.a - lo) << ", " << rt << ">(p);";
+                if (rev) o << " " << f << (op.a - lo) << ", " << rt << ">(q);";
+                o << "\n";
+            } else if (pairs) {
+                o << "        { const int c = (int)(" << operand_bit(op.a) << " & 1u); cnot_x2<" << rt << ">(p, c);";
+                if (rev) o << " cnot_x2<" << rt << ">(q, c);";
+                o << " }\n";
+            } else {
+                o << "        { const int c = (int)(" << operand_bit(op.a) << " & 1u); cnot_regs<" << rt
+                  << ">(p, -1, c);";
+                if (rev) o << " cnot_regs<" << rt << ">(q, -1, c);";
+                o << " }\n";
+            }
+            break;
+        }
+        case OP_EXPVAL:
+            if (pairs) gen_expval_x2(o, P, pd, lo);
+            else o << "        op_expval<R>(p, S, j, xt, LO, warp, lane, 32, 0xffffffffu);\n";
+            break;
+        case OP_COSTATE:
+            if (pairs) gen_costate_x2(o, P, pd, lo);
+            else o << "        op_costate<R>(p, q, S, j, xt, LO);\n";
+            break;
+        default:
+            break;
+        }
+    }
+    if (pairs) o << "        regs_store_x2<LO, " << (rev ? "true" : "false") << ">(p, q, S, xt);\n";
+    else o << "        regs_store<R, LO, " << (rev ? "true" : "false") << ">(p, q, S, xt);\n";
+    return o.str();
+}
+
 }  // namespace
 
 std::string jit_source(const Plan &P, const PassDesc &pd, int min_blocks, bool pairs)
 {
     const bool rev = pd.reverse != 0;
-    const int nslots = pd.slot_end - pd.slot_begin;
+    // distinct phase bodies (templates) and, per phase, (template, first slot)
+    std::vector<std::string> tpl;
+    std::vector<int> table;
+    bool lam_valid = rev && pd.lam_src == SRC_LOAD;
+    for (int ph = pd.phase_begin; ph < pd.phase_end; ++ph) {
+        const DevPhase &phs = P.phases[ph];
+        int sb = -1;
+        for (int k = phs.op_begin; k < phs.op_end; ++k)
+            if ((P.ops[k].type == OP_U2 || P.ops[k].type == OP_GRAD) && (sb < 0 || P.ops[k].slot < sb))
+                sb = P.ops[k].slot;
+        if (sb < 0) sb = 0;
+        const std::string body = phase_body(P, pd, phs, lam_valid, pairs, sb);
+        size_t t = 0;
+        while (t < tpl.size() && tpl[t] != body) ++t;
+        if (t == tpl.size()) tpl.push_back(body);
+        table.push_back((int)t);
+        table.push_back(sb);
+        if (rev) lam_valid = true;
+    }
+    const int nph = pd.phase_end - pd.phase_begin;
     std::ostringstream o;
     o << "namespace qtm {\nnamespace {\n";
+    o << "// " << nph << " phases, " << tpl.size() << " distinct phase programs\n";
+    o << "__constant__ int kPhaseTable[" << (table.empty() ? 2 : table.size()) << "] = {";
+    for (size_t i = 0; i < table.size(); ++i) o << (i ? ", " : "") << table[i];
+    if (table.empty()) o << "0, 0";
+    o << "};\n";
     if (pairs)
         o << "__device__ __forceinline__ void gen_phases(const TileJobX2 &j, const TileSmemX2 &S)\n{\n"
           << "    using R = float;\n    A2 p[kRegs];\n    A2 q[kRegs];\n";
@@ -189,100 +305,22 @@ std::string jit_source(const Plan &P, const PassDesc &pd, int min_blocks, bool p
         o << "template <typename R>\n__device__ __forceinline__ void gen_phases(const TileJob &j, const TileSmem<R> &S, "
              "bool)\n{\n    Cx<R> p[kRegs];\n    Cx<R> q[kRegs];\n";
     o << "    const int tid = threadIdx.x;\n    const int warp = tid >> 5, lane = tid & 31;\n";
-    o << "    const uint32_t base = j.base;\n    (void)base; (void)lane; (void)warp;\n";
-    bool lam_valid = rev && pd.lam_src == SRC_LOAD;
-    for (int ph = pd.phase_begin; ph < pd.phase_end; ++ph) {
-        const DevPhase &phs = P.phases[ph];
-        const int lo = phs.lo;
-        o << "    {\n        constexpr int LO = " << lo << ";\n";
-        o << "        const uint32_t xt = ((uint32_t)tid & ((1u << LO) - 1u)) | (((uint32_t)tid >> LO) << (LO + 4));\n";
-        if (pairs) o << "        regs_load_x2<LO, " << (lam_valid ? "true" : "false") << ">(p, q, S, xt);\n";
-        else o << "        regs_load<R, LO, " << (lam_valid ? "true" : "false") << ">(p, q, S, xt);\n";
-        for (int k = phs.op_begin; k < phs.op_end; ++k) {
-            const DevOp &op = P.ops[k];
-            // register operands must lie in this phase's 4-bit group; a schedule
-            // that breaks this fails to compile instead of running
-            const bool reg_a = has_reg_bit(op.a, lo);
-            const bool reg_b = has_reg_bit(op.b, lo);
-            if (((op.type == OP_U2 || op.type == OP_GRAD) && !reg_a) || (op.type == OP_CNOT && !reg_b) ||
-                ((op.type == OP_U2 || op.type == OP_GRAD) && (op.slot < 0 || op.slot >= nslots)) ||
-                (op.type == OP_DIAG && (op.a < 0 || op.a + op.b > (int)P.diag_pairs.size()))) {
-                o << "#error \"op " << k << " has an operand outside its phase\"\n";
-                continue;
-            }
-            const int rb = op.a - lo;
-            switch (op.type) {
-            case OP_U2:
-                if (pairs) o << "        u2x2<" << rb << ">(p, S.mats + " << 12 * op.slot << ");\n";
-                else o << "        u2<" << rb << ">(p, S.mats + " << 4 * op.slot << ");\n";
-                break;
-            case OP_GRAD:
-                if (pairs) {
-                    o << "        { f2 vx, vy, vz; grad_x2<" << rb << ">(p, q, vx, vy, vz); grad_store_x2(S, " << nslots
-                      << ", " << op.slot << ", warp, lane, vx, vy, vz);";
-                    if (!(op.flags & OPF_SKIP_APPLY))
-                        o << " u2x2<" << rb << ">(p, S.mats + " << 12 * op.slot << "); u2x2<" << rb << ">(q, S.mats + "
-                          << 12 * op.slot << ");";
-                    o << " }\n";
-                } else {
-                    o << "        { R vx = 0, vy = 0, vz = 0; grad_acc<" << rb << ">(p, q, vx, vy, vz);"
-                      << " vx = warp_sum(vx, 32, 0xffffffffu); vy = warp_sum(vy, 32, 0xffffffffu);"
-                      << " vz = warp_sum(vz, 32, 0xffffffffu);"
-                      << " if (lane == 0) { R *g = S.redG + warp * " << 3 * nslots << " + " << 3 * op.slot
-                      << "; g[0] = vx; g[1] = vy; g[2] = vz; }";
-                    if (!(op.flags & OPF_SKIP_APPLY))
-                        o << " u2<" << rb << ">(p, S.mats + " << 4 * op.slot << "); u2<" << rb << ">(q, S.mats + "
-                          << 4 * op.slot << ");";
-                    o << " }\n";
-                }
-                break;
-            case OP_DIAG:
-                o << "        { " << diag_mask(P, op, lo) << (pairs ? " flip_x2<" : " flip_mask<R, ")
-                  << (rev ? "true" : "false") << ">(p, q, m); }\n";
-                break;
-            case OP_CNOT: {
-                const int rt = op.b - lo;
-                if (has_reg_bit(op.a, lo)) {
-                    const char *f = pairs ? "cnot_static_x2<" : "cnot_static<";
-                    o << "        " << f << (op.a - lo) << ", " << rt << ">(p);";
-                    if (rev) o << " " << f << (op.a - lo) << ", " << rt << ">(q);";
-                    o << "\n";
-                } else if (pairs) {
-                    o << "        { const int c = (int)(" << operand_bit(op.a) << " & 1u); cnot_x2<" << rt << ">(p, c);";
-                    if (rev) o << " cnot_x2<" << rt << ">(q, c);";
-                    o << " }\n";
-                } else {
-                    o << "        { const int c = (int)(" << operand_bit(op.a) << " & 1u); cnot_regs<" << rt
-                      << ">(p, -1, c);";
-                    if (rev) o << " cnot_regs<" << rt << ">(q, -1, c);";
-                    o << " }\n";
-                }
-                break;
-            }
-            case OP_EXPVAL:
-                if (pairs) gen_expval_x2(o, P, pd, lo);
-                else o << "        op_expval<R>(p, S, j, xt, LO, warp, lane, 32, 0xffffffffu);\n";
-                break;
-            case OP_COSTATE:
-                if (pairs) gen_costate_x2(o, P, pd, lo);
-                else o << "        op_costate<R>(p, q, S, j, xt, LO);\n";
-                break;
-            default:
-                break;
-            }
-        }
-        if (pairs) o << "        regs_store_x2<LO, " << (rev ? "true" : "false") << ">(p, q, S, xt);\n";
-        else o << "        regs_store<R, LO, " << (rev ? "true" : "false") << ">(p, q, S, xt);\n";
-        o << "        __syncthreads();\n    }\n";
-        if (rev) lam_valid = true;
+    o << "    const uint32_t base = j.base;\n    (void)base; (void)lane; (void)warp; (void)j;\n";
+    o << "#pragma unroll 1\n    for (int ph = 0; ph < " << nph << "; ++ph) {\n";
+    o << "        const int sb = kPhaseTable[2 * ph + 1];\n        (void)sb;\n";
+    o << "        switch (kPhaseTable[2 * ph]) {\n";
+    for (size_t t = 0; t < tpl.size(); ++t) {
+        o << "        " << (t + 1 < tpl.size() ? "case " + std::to_string(t) + ":" : "default:") << " {\n";
+        o << tpl[t] << "        } break;\n";
     }
+    o << "        }\n        __syncthreads();\n    }\n";
     o << "}\n}  // namespace\n}  // namespace qtm\n\n";
     o << "extern \"C\" __global__ void __launch_bounds__(256, " << min_blocks << ") qtm_gen_pass("
       << "const __grid_constant__ qtm::PassArgs a, const __grid_constant__ CUtensorMap tm_phi, "
       << "const __grid_constant__ CUtensorMap tm_lam)\n{\n";
     if (pairs)
         o << "    qtm::pass_body_x2<" << (rev ? "true" : "false") << ">(a, &tm_phi, &tm_lam, "
-          << "[](const qtm::TileJobX2 &j, const qtm::TileSmemX2 &S) { qtm::gen_phases(j, S); });\n}\n";
+          << "[](const qtm::TileJobX2 &j, const qtm::TileSmemX2 &S, bool) { qtm::gen_phases(j, S); });\n}\n";
     else
         o << "    qtm::pass_body<float, " << (rev ? "true" : "false") << ">(a, &tm_phi, &tm_lam, "
           << "[](const qtm::TileJob &j, const qtm::TileSmem<float> &S, bool lv) { qtm::gen_phases<float>(j, S, lv); "
@@ -294,7 +332,8 @@ size_t jit_smem_bytes_x2(const Plan &P, const PassDesc &pd)
 {
     const int nwarps = (1 << (pd.K - 4)) >> 5;
     const LayoutX2 L = make_layout_x2(pd.K, pd.reverse != 0, pd.slot_end - pd.slot_begin, (int)P.terms.size(),
-                                      P.n_obs, P.state_qubits, pd.analytic_ents, nwarps, (int)sizeof(Ent));
+                                      P.n_obs, P.state_qubits, pd.phi_src == SRC_ANALYTIC ? pd.analytic_ents : 0,
+                                      nwarps, (int)sizeof(Ent));
     return (size_t)L.total + 1024;
 }
 

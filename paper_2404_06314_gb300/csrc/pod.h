@@ -132,7 +132,7 @@ struct Term {
 // Elements of phi / lam are 16 bytes (re_b0, re_b1, im_b0, im_b1); a run
 // matrix entry or a product-state table entry is three pairs (re, im, -im).
 struct LayoutX2 {
-    int phi, lam, mats, tabs, tcoef, ents, redE, redG, bar, total;
+    int phi, lam, mats, tabs, tcoef, tmask, tobs, ents, redE, redG, bar, total;
 };
 
 QTM_POD_HD int align_up_x2(int v, int a) { return (v + a - 1) / a * a; }
@@ -149,6 +149,8 @@ QTM_POD_HD LayoutX2 make_layout_x2(int K, bool rev, int nslots, int n_terms, int
     L.mats = o; o = align_up_x2(o + 4 * 24 * (nslots > 0 ? nslots : 1), 16);
     L.tabs = o; o = align_up_x2(o + 16 * 24 * ((sq + 3) / 4), 16);
     L.tcoef = o; o = align_up_x2(o + 8 * (n_terms > 0 ? n_terms : 1), 16);
+    L.tmask = o; o = align_up_x2(o + 4 * (n_terms > 0 ? n_terms : 1), 16);
+    L.tobs = o; o = align_up_x2(o + 4 * (n_terms > 0 ? n_terms : 1), 16);
     L.ents = o; o = align_up_x2(o + ent_bytes * (n_ents > 0 ? n_ents : 1), 16);
     L.redE = o; o = align_up_x2(o + 8 * nwarps * (M > 0 ? M : 1), 16);
     L.redG = o; o = align_up_x2(o + 8 * nwarps * 3 * (nslots > 0 ? nslots : 1), 16);

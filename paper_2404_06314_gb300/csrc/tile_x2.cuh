@@ -1,4 +1,5 @@
-// Paired-sample tile program for the run-time specialised pass kernels.
+// Paired-sample tile program: the general paired pass kernel (k_pass_x2, op
+// tables read at run time) and the run-time specialised paired kernels.
 //
 // Blackwell's FP32 datapath executes fma / mul / add / sub on .f32x2 register
 // pairs: one instruction issues two lanes of work.  A paired pass CTA takes two
@@ -174,6 +175,8 @@ struct TileJobX2 : TileJob {
 struct TileSmemX2 {
     A2 *phi, *lam;
     f2 *mats, *tabs, *tcoef;
+    uint32_t *tmask;
+    int32_t *tobs;
     Ent *ents;
     f2 *redE, *redG;
     uint64_t *bar;
@@ -187,6 +190,8 @@ __device__ __forceinline__ TileSmemX2 carve_x2(unsigned char *smem, const Layout
     t.mats = reinterpret_cast<f2 *>(smem + L.mats);
     t.tabs = reinterpret_cast<f2 *>(smem + L.tabs);
     t.tcoef = reinterpret_cast<f2 *>(smem + L.tcoef);
+    t.tmask = reinterpret_cast<uint32_t *>(smem + L.tmask);
+    t.tobs = reinterpret_cast<int32_t *>(smem + L.tobs);
     t.ents = reinterpret_cast<Ent *>(smem + L.ents);
     t.redE = reinterpret_cast<f2 *>(smem + L.redE);
     t.redG = reinterpret_cast<f2 *>(smem + L.redG);
@@ -226,13 +231,16 @@ __device__ __forceinline__ void stage_tables_x2(const TileJobX2 &j, const TileSm
     const uint64_t Smask = ((1ull << j.l) - 1ull) | (j.m ? (((1ull << j.m) - 1ull) << j.h) : 0ull);
     for (int t = tid; t < j.n_terms; t += T) {
         const Term tm = j.terms[t];
-        const int fixed = __popcll(tm.zmask & ~Smask & (uint64_t)j.base) & 1;
+        const uint64_t zm = tm.zmask;
+        const int fixed = __popcll(zm & ~Smask & (uint64_t)j.base) & 1;
         float c0 = (float)tm.coef, c1 = c0;
         if (REV) {
             c0 *= static_cast<const float *>(j.gE)[tm.obs];
             c1 *= static_cast<const float *>(j.gE1)[tm.obs];
         }
         S.tcoef[t] = fixed ? pack2(-c0, -c1) : pack2(c0, c1);
+        S.tmask[t] = (uint32_t)(zm & ((1ull << j.l) - 1ull)) | (uint32_t)(((zm >> j.h) & ((1ull << j.m) - 1ull)) << j.l);
+        S.tobs[t] = tm.obs;
     }
     if (j.phi_src == SRC_ANALYTIC) {
         for (int k = tid; k < j.analytic_ents; k += T) S.ents[k] = j.prefix_ents[k];
@@ -366,6 +374,169 @@ __device__ __forceinline__ void write_partials_x2(const TileJobX2 &j, const Tile
     }
 }
 
+// ---- phase interpreter (general paired kernel) ------------------------------------
+
+template <int RT>
+__device__ __forceinline__ void cnot_x2_dyn(A2 (&a)[kRegs], int rc, int vc)
+{
+#pragma unroll
+    for (int j = 0; j < kRegs; ++j) {
+        if (j & (1 << RT)) continue;
+        const int c = rc >= 0 ? ((j >> rc) & 1) : vc;
+        const A2 t0 = a[j], t1 = a[j | (1 << RT)];
+        a[j] = c ? t1 : t0;
+        a[j | (1 << RT)] = c ? t0 : t1;
+    }
+}
+
+// <O_m> partials of both samples over the thread's 16 registers (terms sorted
+// by observable), warp-reduced into S.redE.
+__device__ __forceinline__ void expval_x2(const A2 (&p)[kRegs], const TileSmemX2 &S, const TileJobX2 &j, uint32_t xt,
+                                          int lo, int warp, int lane)
+{
+    f2 pr[kRegs];
+#pragma unroll
+    for (int jj = 0; jj < kRegs; ++jj) pr[jj] = fma2(p[jj].r, p[jj].r, mul2(p[jj].i, p[jj].i));
+    int cur = -1;
+    f2 acc = 0ull;
+    for (int t = 0; t < j.n_terms; ++t) {
+        const int ob = S.tobs[t];
+        if (ob != cur) {
+            if (cur >= 0) {
+                acc = warp_sum2(acc);
+                if (lane == 0) S.redE[warp * j.M + cur] = acc;
+            }
+            cur = ob;
+            acc = 0ull;
+        }
+        const uint32_t lm = S.tmask[t];
+        const uint32_t tpar = (uint32_t)__popc(xt & lm);
+        const uint32_t rm = (lm >> lo) & 15u;
+        f2 sacc = 0ull;
+#pragma unroll
+        for (int jj = 0; jj < kRegs; ++jj)
+            sacc = add2(sacc, pr[jj] ^ (((tpar + __popc((uint32_t)jj & rm)) & 1u) ? kSign2 : 0ull));
+        acc = fma2(S.tcoef[t], sacc, acc);
+    }
+    if (cur >= 0) {
+        acc = warp_sum2(acc);
+        if (lane == 0) S.redE[warp * j.M + cur] = acc;
+    }
+}
+
+// lam = (sum_m gE_m O_m) phi for both samples (Sec. II-A costate).
+__device__ __forceinline__ void costate_x2(const A2 (&p)[kRegs], A2 (&q)[kRegs], const TileSmemX2 &S,
+                                           const TileJobX2 &j, uint32_t xt, int lo)
+{
+    f2 d[kRegs];
+#pragma unroll
+    for (int jj = 0; jj < kRegs; ++jj) d[jj] = 0ull;
+    for (int t = 0; t < j.n_terms; ++t) {
+        const uint32_t lm = S.tmask[t];
+        const uint32_t tpar = (uint32_t)__popc(xt & lm);
+        const uint32_t rm = (lm >> lo) & 15u;
+        const f2 k = S.tcoef[t];
+#pragma unroll
+        for (int jj = 0; jj < kRegs; ++jj)
+            d[jj] = add2(d[jj], k ^ (((tpar + __popc((uint32_t)jj & rm)) & 1u) ? kSign2 : 0ull));
+    }
+#pragma unroll
+    for (int jj = 0; jj < kRegs; ++jj) {
+        q[jj].r = mul2(d[jj], p[jj].r);
+        q[jj].i = mul2(d[jj], p[jj].i);
+    }
+}
+
+// The pass's phases read from the op tables: same op semantics as run_phases,
+// each op applied to both samples.  All threads of the CTA (2^(K-4) >= 32)
+// run every phase.
+template <bool REV>
+__device__ __forceinline__ void run_phases_x2(const TileJobX2 &j, const TileSmemX2 &S, bool lam_valid)
+{
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31;
+    const uint32_t base = j.base;
+    A2 p[kRegs];
+    A2 q[kRegs];
+    for (int phz = j.phase_begin; phz < j.phase_end; ++phz) {
+        const DevPhase ph = j.phases[phz];
+        const int lo = ph.lo;
+        const uint32_t xt = ((uint32_t)tid & ((1u << lo) - 1u)) | (((uint32_t)tid >> lo) << (lo + 4));
+#pragma unroll
+        for (int jj = 0; jj < kRegs; ++jj) {
+            const int s = swz16((int)(xt | ((uint32_t)jj << lo)));
+            p[jj] = lds_a2(S.phi, s);
+            if (REV && lam_valid) q[jj] = lds_a2(S.lam, s);
+        }
+        DevOp nxt = j.ops[ph.op_begin < ph.op_end ? ph.op_begin : 0];
+        for (int o = ph.op_begin; o < ph.op_end; ++o) {
+            const DevOp op = nxt;
+            if (o + 1 < ph.op_end) nxt = j.ops[o + 1];
+            // one flat dispatch key: op type x register bit
+            const int sub = (op.type == OP_CNOT ? op.b : op.a) - lo;
+            const int key = op.type * 4 + ((op.type == OP_U2 || op.type == OP_GRAD || op.type == OP_CNOT) ? (sub & 3) : 0);
+            const f2 *m = S.mats + 12 * op.slot;
+            switch (key) {
+            case OP_U2 * 4 + 0: u2x2<0>(p, m); break;
+            case OP_U2 * 4 + 1: u2x2<1>(p, m); break;
+            case OP_U2 * 4 + 2: u2x2<2>(p, m); break;
+            case OP_U2 * 4 + 3: u2x2<3>(p, m); break;
+#define QTM_GRAD_CASE(RB)                                                             \
+            case OP_GRAD * 4 + RB:                                                    \
+                if constexpr (REV) {                                                  \
+                    f2 vx, vy, vz;                                                    \
+                    grad_x2<RB>(p, q, vx, vy, vz);                                    \
+                    grad_store_x2(S, j.nslots, op.slot, warp, lane, vx, vy, vz);      \
+                    if (!(op.flags & OPF_SKIP_APPLY)) { u2x2<RB>(p, m); u2x2<RB>(q, m); } \
+                }                                                                     \
+                break;
+            QTM_GRAD_CASE(0)
+            QTM_GRAD_CASE(1)
+            QTM_GRAD_CASE(2)
+            QTM_GRAD_CASE(3)
+#undef QTM_GRAD_CASE
+            case OP_DIAG * 4: {
+                uint32_t msk = 0;
+                for (int k = op.a; k < op.a + op.b; ++k) {
+                    const DiagPair dp = j.diag[k];
+                    msk ^= operand_pattern(dp.a, lo, xt, base) & operand_pattern(dp.b, lo, xt, base);
+                }
+                flip_x2<REV>(p, q, msk);
+                break;
+            }
+#define QTM_CNOT_CASE(RT)                                                              \
+            case OP_CNOT * 4 + RT: {                                                   \
+                int rc = -1, vc = 0;                                                   \
+                if (op.a >= kFixed) vc = (int)((base >> (op.a - kFixed)) & 1u);        \
+                else if (op.a >= lo && op.a < lo + kRegBits) rc = op.a - lo;           \
+                else vc = (int)((xt >> op.a) & 1u);                                    \
+                cnot_x2_dyn<RT>(p, rc, vc);                                            \
+                if (REV) cnot_x2_dyn<RT>(q, rc, vc);                                   \
+                break;                                                                 \
+            }
+            QTM_CNOT_CASE(0)
+            QTM_CNOT_CASE(1)
+            QTM_CNOT_CASE(2)
+            QTM_CNOT_CASE(3)
+#undef QTM_CNOT_CASE
+            case OP_EXPVAL * 4: expval_x2(p, S, j, xt, lo, warp, lane); break;
+            case OP_COSTATE * 4:
+                if constexpr (REV) costate_x2(p, q, S, j, xt, lo);
+                break;
+            default: break;
+            }
+        }
+#pragma unroll
+        for (int jj = 0; jj < kRegs; ++jj) {
+            const int s = swz16((int)(xt | ((uint32_t)jj << lo)));
+            sts_a2(S.phi, s, p[jj]);
+            if (REV) sts_a2(S.lam, s, q[jj]);
+        }
+        if (REV) lam_valid = true;
+        __syncthreads();
+    }
+}
+
 // The body of a paired pass kernel: one CTA per (sample pair, tile); grid =
 // ceil(B / 2) * tiles, block = 2^(K-4) threads (K >= 9).  Same stages as
 // pass_body; `phases` is the generated phase program.
@@ -443,7 +614,7 @@ __device__ __forceinline__ void pass_body_x2(const PassArgs &a, const CUtensorMa
         __syncthreads();
     }
 
-    phases(j, S);
+    phases(j, S, load_lam);
 
     write_partials_x2<REV>(j, S, nwarps, a.has_expval != 0, a.Epart + ((size_t)b0 * a.tiles + tile) * a.M,
                            a.Epart + ((size_t)b1 * a.tiles + tile) * a.M,

@@ -151,3 +151,50 @@ def test_compile_after_forward_and_recompute():
     assert np.max(np.abs(gw.double().cpu().numpy() - gwo)) <= 1e-5
     E1 = plan.forward(x, w).double().cpu().numpy()
     assert np.max(np.abs(E1 - E0)) <= 2e-6
+
+
+# ---- paired general kernel (qtm_set_sample_pairing) -----------------------------------
+
+def test_pairing_eligibility_host():
+    assert capi.Plan(W.workload_12q(), dtype="c64").set_pairing(True).pairing
+    for c, dt in [(W.workload_12q(), "c128"), (W.workload_4q(), "c64")]:
+        with pytest.raises(capi.QtmError) as ei:
+            capi.Plan(c, dtype=dt).set_pairing(True)
+        assert ei.value.status == capi.QTM_EUNSUPPORTED
+    p = capi.Plan(W.workload_20q(), dtype="c64").set_pairing(True).set_pairing(False)
+    assert not p.pairing
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("name,B", CASES)
+def test_paired_general_matches_oracle(name, B):
+    c = _circuit(name)
+    inp = W.make_inputs(c, B, 23, real_dtype=np.float32)
+    general = _run(capi.Plan(c, dtype="c64"), c, inp)
+    plan = capi.Plan(c, dtype="c64").set_pairing(True)
+    got = _run(plan, c, inp)
+    assert plan.compiled_passes() == 0
+    Eo = oracle.forward(c, inp.x, inp.w, threads=0)
+    _, gxo, gwo = oracle.adjoint(c, inp.gE, inp.x, inp.w, threads=0)
+    for what, g, r, h in zip(("E", "gx", "gw"), got, (Eo, gxo, gwo), general):
+        err = float(np.max(np.abs(g - r))) if r.size else 0.0
+        assert err <= 1e-5, f"{name} B={B} paired general {what}: {err:.3e}"
+        d = float(np.max(np.abs(g - h))) if h.size else 0.0
+        assert d <= 2e-6, f"{name} B={B} paired vs one-sample {what}: {d:.3e}"
+
+
+@pytest.mark.gpu
+def test_paired_general_jacobian_and_toggle():
+    import torch
+    c = W.workload_16q_train()
+    plan = capi.Plan(c, dtype="c64").set_pairing(True)
+    inp = W.make_inputs(c, 3, 4, real_dtype=np.float32)
+    x = torch.tensor(inp.x, dtype=torch.float32, device="cuda")
+    w = torch.tensor(inp.w, dtype=torch.float32, device="cuda")
+    J = plan.jacobian(x, w).double().cpu().numpy()
+    Jo = oracle.jacobian(c, inp.x, inp.w, threads=0)
+    assert np.max(np.abs(J - Jo)) <= 1e-5
+    E1 = plan.forward(x, w).double().cpu().numpy()
+    plan.set_pairing(False)
+    E0 = plan.forward(x, w).double().cpu().numpy()
+    assert np.max(np.abs(E1 - E0)) <= 2e-6

@@ -207,7 +207,7 @@ def prepare(plan, kernels):
     return plan
 
 
-def measure_gpu(name, steps, warmup, device, seed_offset=0, profile=True, kernels="paired"):
+def measure_gpu(name, steps, warmup, device, seed_offset=0, profile=True, kernels="one-sample"):
     import numpy as np
     import torch
 
@@ -365,7 +365,7 @@ def measure_training(device, steps=100):
                                    "MSE on sum_i <Z_i>, Adam lr 1e-2", "steps": steps}}
 
 
-def measure_e2e(name, steps, device, seed_offset=0, kernels="paired"):
+def measure_e2e(name, steps, device, seed_offset=0, kernels="one-sample"):
     """End to end through the public API: pinned host inputs -> device,
     forward, adjoint, results -> pinned host, every step."""
     import numpy as np
@@ -571,7 +571,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="qnn12")
     ap.add_argument("--skip-n20", action="store_true")
-    ap.add_argument("--kernels", choices=["paired", "one-sample", "paired-general", "general"], default="paired",
+    ap.add_argument("--kernels", choices=["paired", "one-sample", "paired-general", "general"], default="one-sample",
                     help="plan-specialised pass kernels (qtm_compile: two samples per CTA on f32x2 register "
                          "pairs, or one sample per CTA) or the general pass kernel")
     ap.add_argument("--skip-extra", action="store_true", help="skip the uneven-batch and training lines")

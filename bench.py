@@ -194,6 +194,7 @@ def oracle_rate(c, inp_full, budget_s: float, threads: int):
 KERNEL_LABEL = {"paired": "qtm_gen_pass (plan-specialised, two samples per CTA on f32x2 pairs), reverse",
                 "paired-general": "k_pass_x2<reverse> (general, two samples per CTA on f32x2 pairs)",
                 "one-sample": "qtm_gen_pass (plan-specialised, one sample per CTA), reverse",
+                "lanes": "qtm_gen_pass (plan-specialised, one sample per CTA, amplitudes paired in f32x2), reverse",
                 "general": "k_pass<float, reverse> (general pass kernel)"}
 
 
@@ -202,7 +203,7 @@ def prepare(plan, kernels):
     if kernels == "paired-general":
         plan.set_pairing(True)
     elif kernels != "general":
-        plan.compile(pairs=(kernels == "paired"))
+        plan.compile(kind={"paired": "pairs", "one-sample": "one", "lanes": "lanes"}[kernels])
         assert plan.compiled_passes() > 0, "no specialised pass kernel loaded"
     return plan
 
@@ -571,7 +572,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="qnn12")
     ap.add_argument("--skip-n20", action="store_true")
-    ap.add_argument("--kernels", choices=["paired", "one-sample", "paired-general", "general"], default="one-sample",
+    ap.add_argument("--kernels", choices=["paired", "one-sample", "lanes", "paired-general", "general"], default="one-sample",
                     help="plan-specialised pass kernels (qtm_compile: two samples per CTA on f32x2 register "
                          "pairs, or one sample per CTA) or the general pass kernel")
     ap.add_argument("--skip-extra", action="store_true", help="skip the uneven-batch and training lines")

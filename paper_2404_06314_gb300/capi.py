@@ -23,6 +23,8 @@ QTM_C64, QTM_C128 = 0, 1
 QTM_PATH_AUTO, QTM_PATH_FUSED, QTM_PATH_NAIVE = 0, 1, 2
 QTM_ADJ_GW_PER_SAMPLE, QTM_ADJ_RECOMPUTE = 1, 2
 QTM_COMPILE_ONE_SAMPLE = 1
+QTM_COMPILE_LANE_PAIRS = 2
+_COMPILE_KIND = {"pairs": 0, "one": QTM_COMPILE_ONE_SAMPLE, "lanes": QTM_COMPILE_LANE_PAIRS}
 
 
 class qtm_gate(ctypes.Structure):
@@ -288,10 +290,13 @@ class Plan:
         self._raise(st, "qtm_adjoint")
         return gx, gw
 
-    def compile(self, pairs: bool = True):
-        """Specialise and load this plan's pass kernels (qtm_compile); pairs:
-        two samples per CTA on f32x2 register pairs."""
-        self._raise(lib().qtm_compile(self.handle, 0 if pairs else QTM_COMPILE_ONE_SAMPLE), "qtm_compile")
+    def compile(self, pairs: bool = True, kind: str = None):
+        """Specialise and load this plan's pass kernels (qtm_compile).  kind:
+        "pairs" (two samples per CTA on f32x2 register pairs), "one" (one
+        sample per CTA, scalar registers) or "lanes" (one sample per CTA,
+        amplitudes paired in f32x2 registers); default from `pairs`."""
+        kind = kind or ("pairs" if pairs else "one")
+        self._raise(lib().qtm_compile(self.handle, _COMPILE_KIND[kind]), "qtm_compile")
         return self
 
     def set_pairing(self, on: bool = True):
@@ -306,13 +311,13 @@ class Plan:
     def compiled_passes(self) -> int:
         return int(lib().qtm_compiled_passes(self.handle))
 
-    def jit_source(self, which: int, index: int, pairs: bool = True) -> str:
-        flags = 0 if pairs else QTM_COMPILE_ONE_SAMPLE
+    def jit_source(self, which: int, index: int, pairs: bool = True, kind: str = None) -> str:
+        flags = _COMPILE_KIND[kind or ("pairs" if pairs else "one")]
         return lib().qtm_debug_jit_source(self.handle, int(which), int(index), flags).decode()
 
-    def jit_compile_check(self, pairs: bool = True):
+    def jit_compile_check(self, pairs: bool = True, kind: str = None):
         """Compile every specialised pass with NVRTC, host only (no load)."""
-        flags = 0 if pairs else QTM_COMPILE_ONE_SAMPLE
+        flags = _COMPILE_KIND[kind or ("pairs" if pairs else "one")]
         self._raise(lib().qtm_debug_jit_compile(self.handle, flags), "qtm_debug_jit_compile")
 
     def jacobian(self, x, w, out=None, stream=None):

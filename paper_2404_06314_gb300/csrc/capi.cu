@@ -710,7 +710,12 @@ qtm_status qtm_jacobian(qtm_plan *p, int B, const void *x, const void *w, void *
 namespace {
 
 // Generate and compile every pass (host only; NVRTC, no device).
-qtm_status compile_all(qtm_plan *p, bool pairs, std::vector<std::vector<char>> &fwd_bin,
+JitMode jit_mode(int flags)
+{
+    return (flags & QTM_COMPILE_LANE_PAIRS) ? JIT_LANES : (flags & QTM_COMPILE_ONE_SAMPLE) ? JIT_ONE : JIT_PAIRS;
+}
+
+qtm_status compile_all(qtm_plan *p, JitMode mode, std::vector<std::vector<char>> &fwd_bin,
                        std::vector<std::vector<char>> &rev_bin)
 {
     const Plan &P = p->P;
@@ -722,6 +727,7 @@ qtm_status compile_all(qtm_plan *p, bool pairs, std::vector<std::vector<char>> &
     rev_bin.assign(P.rev.size(), {});
     // CTAs per SM the register budget is compiled for: the paired kernels hold
     // twice the state per thread
+    const bool pairs = mode == JIT_PAIRS;
     int minb_f = pairs ? 2 : 3, minb_r = pairs ? 1 : 2;
     if (const char *e = std::getenv("QTM_JIT_MINB")) {   // tuning: "<forward>,<reverse>"
         int f = 0, r = 0;
@@ -740,7 +746,7 @@ qtm_status compile_all(qtm_plan *p, bool pairs, std::vector<std::vector<char>> &
     std::vector<std::thread> th;
     for (size_t k = 0; k < jobs.size(); ++k)
         th.emplace_back([&, k] {
-            ok[k] = jit_compile(jit_source(P, *jobs[k].pd, jobs[k].minb, pairs), *jobs[k].out, logs[k]) ? 1 : 0;
+            ok[k] = jit_compile(jit_source(P, *jobs[k].pd, jobs[k].minb, mode), *jobs[k].out, logs[k]) ? 1 : 0;
         });
     for (auto &t : th) t.join();
     for (size_t k = 0; k < jobs.size(); ++k)
@@ -778,13 +784,15 @@ int qtm_get_sample_pairing(const qtm_plan *p) { return p ? p->pairing : 0; }
 qtm_status qtm_compile(qtm_plan *p, int flags)
 {
     if (!p) return QTM_EINVAL;
-    if (flags & ~QTM_COMPILE_ONE_SAMPLE) return fail(p, QTM_EINVAL, "unknown flags");
+    if (flags != 0 && flags != QTM_COMPILE_ONE_SAMPLE && flags != QTM_COMPILE_LANE_PAIRS)
+        return fail(p, QTM_EINVAL, "unknown flags");
     if (!jit_available()) return fail(p, QTM_EUNSUPPORTED, "NVRTC or driver entry points not available");
-    const bool pairs = !(flags & QTM_COMPILE_ONE_SAMPLE);
+    const JitMode mode = jit_mode(flags);
+    const bool pairs = mode == JIT_PAIRS;
     qtm_status st = ensure_device(p);
     if (st != QTM_OK) return st;
     std::vector<std::vector<char>> fb, rb;
-    st = compile_all(p, pairs, fb, rb);
+    st = compile_all(p, mode, fb, rb);
     if (st != QTM_OK) return st;
     cudaError_t e = cudaDeviceSynchronize();   // no launch of the old kernels or layout is in flight
     if (e != cudaSuccess) return cuda_fail(p, e, "synchronize before loading kernels");
@@ -809,7 +817,12 @@ qtm_status qtm_compile(qtm_plan *p, int flags)
         const auto &bins = rev ? rb : fb;
         const auto &gsm = rev ? p->smem_rev : p->smem_fwd;
         for (size_t i = 0; i < pds.size(); ++i) {
-            const int smem = (int)(pairs ? jit_smem_bytes_x2(P, pds[i]) : gsm[i]);
+            const int smem = (int)(pairs ? jit_smem_bytes_x2(P, pds[i])
+                                         : mode == JIT_LANES ? jit_smem_bytes_lanes(P, pds[i]) : gsm[i]);
+            if ((size_t)smem > kMaxDynSmem) {
+                unload_all();
+                return fail(p, QTM_EUNSUPPORTED, "specialised kernel needs more shared memory than a CTA has");
+            }
             if (!jit_load(bins[i], smem, ks[i], err)) {
                 unload_all();
                 return fail(p, QTM_ECUDA, err);
@@ -843,9 +856,10 @@ const char *qtm_debug_jit_source(const qtm_plan *p, int which, int index, int fl
     const auto &v = which ? P.rev : P.fwd;
     if (index < 0 || index >= (int)v.size()) return "";
     qtm_plan *m = const_cast<qtm_plan *>(p);
-    const bool pairs = !(flags & QTM_COMPILE_ONE_SAMPLE);
+    const JitMode mode = jit_mode(flags);
+    const bool pairs = mode == JIT_PAIRS;
     m->jit_src_cache = jit_eligible(P, v[index])
-                           ? jit_source(P, v[index], pairs ? (which ? 1 : 2) : (which ? 2 : 3), pairs)
+                           ? jit_source(P, v[index], pairs ? (which ? 1 : 2) : (which ? 2 : 3), mode)
                            : std::string();
     return m->jit_src_cache.c_str();
 }
@@ -854,7 +868,7 @@ qtm_status qtm_debug_jit_compile(qtm_plan *p, int flags)
 {
     if (!p) return QTM_EINVAL;
     std::vector<std::vector<char>> fb, rb;
-    return compile_all(p, !(flags & QTM_COMPILE_ONE_SAMPLE), fb, rb);
+    return compile_all(p, jit_mode(flags), fb, rb);
 }
 
 qtm_status qtm_sync(qtm_plan *p, void *stream)

@@ -11,6 +11,8 @@
 // is missing, plans keep the interpreter kernels.
 #include "jit.h"
 
+#include "device.h"
+
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
@@ -19,6 +21,7 @@
 #include <sys/stat.h>
 #include <unistd.h>
 
+#include <algorithm>
 #include <cstdio>
 #include <cstdlib>
 #include <fstream>
@@ -79,6 +82,15 @@ std::string signed_sum(const std::vector<std::string> &pos, const std::vector<st
 }
 
 bool has_reg_bit(int x, int lo) { return x < kFixed && x >= lo && x < lo + kRegBits; }
+
+constexpr int kLaneSlotPairsHost = 18;   // f32x2 pairs per run slot in the lane-pair table
+
+// byte offset of the lane-pair table from the tile program's aligned shared base
+size_t lane_table_offset(const Plan &P, const PassDesc &pd)
+{
+    return pass_smem_bytes(pd.K, P.dtype, pd.reverse != 0, pd.slot_end - pd.slot_begin, (int)P.terms.size(), P.n_obs,
+                           P.state_qubits, pd.phi_src == SRC_ANALYTIC ? pd.analytic_ents : 0) - 1024;
+}
 
 // <O_m> partials with the register sign pattern of every term a constant.
 void gen_expval_x2(std::ostringstream &o, const Plan &P, const PassDesc &pd, int lo)
@@ -174,18 +186,158 @@ std::string diag_mask(const Plan &P, const DevOp &op, int lo)
     return o.str();
 }
 
+
+// ---- lane-paired one-sample kernels (tile_lanes.cuh) ---------------------------------
+
+int lane_jj_host(int S, int k, int h) { return ((k >> S) << (S + 1)) | (h << S) | (k & ((1 << S) - 1)); }
+
+// lane bit of a phase: the register bit with the least gate work on it
+int choose_lane_bit(const Plan &P, const DevPhase &phs)
+{
+    int cost[4] = {0, 0, 0, 0};
+    const int lo = phs.lo;
+    for (int k = phs.op_begin; k < phs.op_end; ++k) {
+        const DevOp &op = P.ops[k];
+        if ((op.type == OP_U2 || op.type == OP_GRAD) && has_reg_bit(op.a, lo))
+            cost[op.a - lo] += op.type == OP_GRAD ? 3 : 1;
+    }
+    int best = 0;
+    for (int r = 1; r < 4; ++r)
+        if (cost[r] < cost[best]) best = r;
+    return best;
+}
+
+void gen_expval_lanes(std::ostringstream &o, const Plan &P, const PassDesc &pd, int lo, int S)
+{
+    o << "        {\n            f2 pr[kLanePairs];\n#pragma unroll\n            for (int k = 0; k < kLanePairs; ++k) "
+         "pr[k] = fma2(p[k].r, p[k].r, mul2(p[k].i, p[k].i));\n";
+    std::vector<int> seen(16, 0);
+    for (const Term &t : P.terms) {
+        const int rm = (int)((local_mask(pd, t.zmask) >> lo) & 15u);
+        if (seen[rm]) continue;
+        seen[rm] = 1;
+        std::vector<std::string> pos, neg;
+        for (int k = 0; k < 8; ++k)
+            (__builtin_popcount(lane_jj_host(S, k, 0) & rm) & 1 ? neg : pos).push_back("pr[" + std::to_string(k) + "]");
+        o << "            const f2 a" << rm << " = " << signed_sum(pos, neg) << ";\n";
+        o << "            const float s" << rm << " = lane0(a" << rm << ")" << (((rm >> S) & 1) ? " - " : " + ")
+          << "lane1(a" << rm << ");\n";
+    }
+    for (int m = 0; m < P.n_obs; ++m) {
+        bool any = false;
+        for (size_t t = 0; t < P.terms.size(); ++t) {
+            if (P.terms[t].obs != m) continue;
+            if (!any) o << "            { float e = 0.f;\n";
+            any = true;
+            const uint32_t lm = local_mask(pd, P.terms[t].zmask);
+            const int rm = (int)((lm >> lo) & 15u);
+            o << "              e = fmaf((__popc(xt & 0x" << std::hex << lm << std::dec << "u) & 1u) ? -S.tcoef[" << t
+              << "] : S.tcoef[" << t << "], s" << rm << ", e);\n";
+        }
+        if (any)
+            o << "              e = warp_sum(e, 32, 0xffffffffu); if (lane == 0) S.redE[warp * " << P.n_obs << " + "
+              << m << "] = e; }\n";
+    }
+    o << "        }\n";
+}
+
+void gen_costate_lanes(std::ostringstream &o, const Plan &P, const PassDesc &pd, int lo, int S)
+{
+    o << "        {\n";
+    std::vector<std::vector<size_t>> by_rm(16);
+    for (size_t t = 0; t < P.terms.size(); ++t) by_rm[(local_mask(pd, P.terms[t].zmask) >> lo) & 15u].push_back(t);
+    std::vector<int> rms;
+    for (int rm = 0; rm < 16; ++rm) {
+        if (by_rm[rm].empty()) continue;
+        rms.push_back(rm);
+        o << "            const float c" << rm << " = 0.f";
+        for (size_t t : by_rm[rm])
+            o << " + ((__popc(xt & 0x" << std::hex << local_mask(pd, P.terms[t].zmask) << std::dec
+              << "u) & 1u) ? -S.tcoef[" << t << "] : S.tcoef[" << t << "])";
+        o << ";\n";
+    }
+    auto dexpr = [&](int jj) {
+        std::string e = "0.f";
+        for (int rm : rms) e += std::string(__builtin_popcount(jj & rm) & 1 ? " - c" : " + c") + std::to_string(rm);
+        return e;
+    };
+    for (int k = 0; k < 8; ++k)
+        o << "            { const f2 d = pack2(" << dexpr(lane_jj_host(S, k, 0)) << ", " << dexpr(lane_jj_host(S, k, 1))
+          << "); q[" << k << "].r = mul2(d, p[" << k << "].r); q[" << k << "].i = mul2(d, p[" << k << "].i); }\n";
+    o << "        }\n";
+}
+
 // Body of one phase with its run slots written relative to the phase's first
 // slot `sb` (a runtime value): layers of a layered circuit repeat the same
 // body with other slots and then share one copy of the code.
-std::string phase_body(const Plan &P, const PassDesc &pd, const DevPhase &phs, bool lam_valid, bool pairs, int sb)
+std::string phase_body(const Plan &P, const PassDesc &pd, const DevPhase &phs, bool lam_valid, JitMode mode, int sb)
 {
     const bool rev = pd.reverse != 0;
+    const bool pairs = mode == JIT_PAIRS;
     const int nslots = pd.slot_end - pd.slot_begin;
     const int lo = phs.lo;
     std::ostringstream o;
     auto slot = [&](int s) { return "(sb + " + std::to_string(s - sb) + ")"; };
     o << "        constexpr int LO = " << lo << ";\n";
     o << "        const uint32_t xt = ((uint32_t)tid & ((1u << LO) - 1u)) | (((uint32_t)tid >> LO) << (LO + 4));\n";
+    if (mode == JIT_LANES) {
+        const int sl = choose_lane_bit(P, phs);
+        o << "        constexpr int SB = " << sl << ";\n";
+        o << "        regs_load_lanes<LO, SB, " << (lam_valid ? "true" : "false") << ">(p, q, S, xt);\n";
+        for (int k = phs.op_begin; k < phs.op_end; ++k) {
+            const DevOp &op = P.ops[k];
+            const bool reg_a = has_reg_bit(op.a, lo);
+            const bool reg_b = has_reg_bit(op.b, lo);
+            if (((op.type == OP_U2 || op.type == OP_GRAD) && !reg_a) || (op.type == OP_CNOT && !reg_b) ||
+                ((op.type == OP_U2 || op.type == OP_GRAD) && (op.slot < 0 || op.slot >= nslots)) ||
+                (op.type == OP_DIAG && (op.a < 0 || op.a + op.b > (int)P.diag_pairs.size()))) {
+                o << "#error \"op " << k << " has an operand outside its phase\"\n";
+                continue;
+            }
+            const int rb = op.a - lo;
+            const std::string tab = "LT + " + std::to_string(kLaneSlotPairsHost) + " * " + slot(op.slot);
+            const std::string apply = rb == sl ? "u2_lanes_s(" : "u2_lanes<SB, " + std::to_string(rb) + ">(";
+            switch (op.type) {
+            case OP_U2:
+                o << "        " << apply << "p, " << tab << ");\n";
+                break;
+            case OP_GRAD:
+                o << "        { float vx, vy, vz; "
+                  << (rb == sl ? std::string("grad_lanes_s(") : "grad_lanes<SB, " + std::to_string(rb) + ">(")
+                  << "p, q, vx, vy, vz);"
+                  << " vx = warp_sum(vx, 32, 0xffffffffu); vy = warp_sum(vy, 32, 0xffffffffu);"
+                  << " vz = warp_sum(vz, 32, 0xffffffffu);"
+                  << " if (lane == 0) { float *g = S.redG + warp * " << 3 * nslots << " + 3 * " << slot(op.slot)
+                  << "; g[0] = vx; g[1] = vy; g[2] = vz; }";
+                if (!(op.flags & OPF_SKIP_APPLY)) o << " " << apply << "p, " << tab << "); " << apply << "q, " << tab << ");";
+                o << " }\n";
+                break;
+            case OP_DIAG:
+                o << "        { " << diag_mask(P, op, lo) << " flip_lanes<SB, " << (rev ? "true" : "false")
+                  << ">(p, q, m); }\n";
+                break;
+            case OP_CNOT: {
+                const int rt = op.b - lo;
+                if (has_reg_bit(op.a, lo)) {
+                    o << "        cnot_lanes_static<SB, " << (op.a - lo) << ", " << rt << ">(p);";
+                    if (rev) o << " cnot_lanes_static<SB, " << (op.a - lo) << ", " << rt << ">(q);";
+                    o << "\n";
+                } else {
+                    o << "        { const int c = (int)(" << operand_bit(op.a) << " & 1u); cnot_lanes<SB, " << rt
+                      << ">(p, c);";
+                    if (rev) o << " cnot_lanes<SB, " << rt << ">(q, c);";
+                    o << " }\n";
+                }
+                break;
+            }
+            case OP_EXPVAL: gen_expval_lanes(o, P, pd, lo, sl); break;
+            case OP_COSTATE: gen_costate_lanes(o, P, pd, lo, sl); break;
+            default: break;
+            }
+        }
+        o << "        regs_store_lanes<LO, SB, " << (rev ? "true" : "false") << ">(p, q, S, xt);\n";
+        return o.str();
+    }
     if (pairs) o << "        regs_load_x2<LO, " << (lam_valid ? "true" : "false") << ">(p, q, S, xt);\n";
     else o << "        regs_load<R, LO, " << (lam_valid ? "true" : "false") << ">(p, q, S, xt);\n";
     for (int k = phs.op_begin; k < phs.op_end; ++k) {
@@ -268,9 +420,10 @@ std::string phase_body(const Plan &P, const PassDesc &pd, const DevPhase &phs, b
 
 }  // namespace
 
-std::string jit_source(const Plan &P, const PassDesc &pd, int min_blocks, bool pairs)
+std::string jit_source(const Plan &P, const PassDesc &pd, int min_blocks, JitMode mode)
 {
     const bool rev = pd.reverse != 0;
+    const bool pairs = mode == JIT_PAIRS;
     // distinct phase bodies (templates) and, per phase, (template, first slot)
     std::vector<std::string> tpl;
     std::vector<int> table;
@@ -282,7 +435,7 @@ std::string jit_source(const Plan &P, const PassDesc &pd, int min_blocks, bool p
             if ((P.ops[k].type == OP_U2 || P.ops[k].type == OP_GRAD) && (sb < 0 || P.ops[k].slot < sb))
                 sb = P.ops[k].slot;
         if (sb < 0) sb = 0;
-        const std::string body = phase_body(P, pd, phs, lam_valid, pairs, sb);
+        const std::string body = phase_body(P, pd, phs, lam_valid, mode, sb);
         size_t t = 0;
         while (t < tpl.size() && tpl[t] != body) ++t;
         if (t == tpl.size()) tpl.push_back(body);
@@ -298,9 +451,16 @@ std::string jit_source(const Plan &P, const PassDesc &pd, int min_blocks, bool p
     for (size_t i = 0; i < table.size(); ++i) o << (i ? ", " : "") << table[i];
     if (table.empty()) o << "0, 0";
     o << "};\n";
+    const int nslots = pd.slot_end - pd.slot_begin;
     if (pairs)
         o << "__device__ __forceinline__ void gen_phases(const TileJobX2 &j, const TileSmemX2 &S)\n{\n"
           << "    using R = float;\n    A2 p[kRegs];\n    A2 q[kRegs];\n";
+    else if (mode == JIT_LANES)
+        o << "template <typename R>\n__device__ __forceinline__ void gen_phases(const TileJob &j, const TileSmem<R> &S, "
+             "bool)\n{\n    A2 p[kLanePairs];\n    A2 q[kLanePairs];\n"
+          << "    // lane-pair matrix table after the tile program's shared memory\n"
+          << "    f2 *LT = reinterpret_cast<f2 *>(reinterpret_cast<unsigned char *>(S.phi) + " << lane_table_offset(P, pd)
+          << ");\n    stage_lane_table(S.mats, LT, " << nslots << ");\n    __syncthreads();\n";
     else
         o << "template <typename R>\n__device__ __forceinline__ void gen_phases(const TileJob &j, const TileSmem<R> &S, "
              "bool)\n{\n    Cx<R> p[kRegs];\n    Cx<R> q[kRegs];\n";
@@ -326,6 +486,11 @@ std::string jit_source(const Plan &P, const PassDesc &pd, int min_blocks, bool p
           << "[](const qtm::TileJob &j, const qtm::TileSmem<float> &S, bool lv) { qtm::gen_phases<float>(j, S, lv); "
              "});\n}\n";
     return o.str();
+}
+
+size_t jit_smem_bytes_lanes(const Plan &P, const PassDesc &pd)
+{
+    return lane_table_offset(P, pd) + 1024 + (size_t)8 * kLaneSlotPairsHost * std::max(1, pd.slot_end - pd.slot_begin);
 }
 
 size_t jit_smem_bytes_x2(const Plan &P, const PassDesc &pd)

@@ -50,12 +50,25 @@ __device__ __forceinline__ f2 sub2(f2 a, f2 b)
     asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
     return d;
 }
+// register-pair moves (no arithmetic)
 __device__ __forceinline__ f2 pack2(float a, float b)
 {
-    return (f2)__float_as_uint(a) | ((f2)__float_as_uint(b) << 32);
+    f2 d;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(a), "f"(b));
+    return d;
 }
-__device__ __forceinline__ float lane0(f2 v) { return __uint_as_float((unsigned)v); }
-__device__ __forceinline__ float lane1(f2 v) { return __uint_as_float((unsigned)(v >> 32)); }
+__device__ __forceinline__ float lane0(f2 v)
+{
+    float a, b;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+    return a;
+}
+__device__ __forceinline__ float lane1(f2 v)
+{
+    float a, b;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+    return b;
+}
 
 struct A2 { f2 r, i; };   // amplitude of one basis state in both samples
 

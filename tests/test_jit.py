@@ -36,24 +36,35 @@ def _rand(n, seed):
     return c
 
 
-@pytest.mark.parametrize("pairs", [True, False])
-def test_generated_source_compiles_benchmarks(pairs):
+def _nvrtc_kind_or_skip(plan, kind):
+    try:
+        plan.jit_compile_check(kind=kind)
+    except capi.QtmError as e:
+        if e.status == capi.QTM_EUNSUPPORTED:
+            pytest.skip("NVRTC not available")
+        raise
+
+
+@pytest.mark.parametrize("kind", ["pairs", "one", "lanes"])
+def test_generated_source_compiles_benchmarks(kind):
     for c in [W.workload_12q(), W.workload_20q(), W.workload_16q_train()]:
         plan = capi.Plan(c, dtype="c64")
         info = plan.info
         for which, count in ((0, info["fwd_passes"]), (1, info["adj_passes"])):
             for i in range(count):
-                src = plan.jit_source(which, i, pairs=pairs)
+                src = plan.jit_source(which, i, kind=kind)
                 assert "qtm_gen_pass" in src and "gen_phases" in src, (c.name, which, i)
-                assert ("pass_body_x2" in src) == pairs
+                assert ("pass_body_x2" in src) == (kind == "pairs")
+                assert ("regs_load_lanes" in src) == (kind == "lanes")
                 assert "#error" not in src
-        _nvrtc_or_skip(plan, pairs)
+        _nvrtc_kind_or_skip(plan, kind)
 
 
 @pytest.mark.parametrize("n", [9, 13])
 def test_generated_source_compiles_random(n):
     plan = capi.Plan(_rand(n, 500 + n), dtype="c64")
     _nvrtc_or_skip(plan, True)
+    _nvrtc_kind_or_skip(plan, "lanes")
 
 
 def test_not_specialised():
@@ -86,14 +97,15 @@ def _circuit(name):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("pairs", [True, False])
+@pytest.mark.parametrize("kind", ["pairs", "one", "lanes"])
 @pytest.mark.parametrize("name,B", CASES)
-def test_compiled_plan_matches_oracle(name, B, pairs):
+def test_compiled_plan_matches_oracle(name, B, kind):
     c = _circuit(name)
     inp = W.make_inputs(c, B, 21, real_dtype=np.float32)
     general = _run(capi.Plan(c, dtype="c64"), c, inp)
     plan = capi.Plan(c, dtype="c64")
-    plan.compile(pairs=pairs)
+    plan.compile(kind=kind)
+    pairs = kind
     info = plan.info
     assert plan.compiled_passes() == info["fwd_passes"] + info["adj_passes"]
     got = _run(plan, c, inp)

@@ -208,7 +208,7 @@ def prepare(plan, kernels):
     return plan
 
 
-def measure_gpu(name, steps, warmup, device, seed_offset=0, profile=True, kernels="one-sample"):
+def measure_gpu(name, steps, warmup, device, seed_offset=0, profile=True, kernels="lanes"):
     import numpy as np
     import torch
 
@@ -366,7 +366,7 @@ def measure_training(device, steps=100):
                                    "MSE on sum_i <Z_i>, Adam lr 1e-2", "steps": steps}}
 
 
-def measure_e2e(name, steps, device, seed_offset=0, kernels="one-sample"):
+def measure_e2e(name, steps, device, seed_offset=0, kernels="lanes"):
     """End to end through the public API: pinned host inputs -> device,
     forward, adjoint, results -> pinned host, every step."""
     import numpy as np
@@ -572,9 +572,10 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="qnn12")
     ap.add_argument("--skip-n20", action="store_true")
-    ap.add_argument("--kernels", choices=["paired", "one-sample", "lanes", "paired-general", "general"], default="one-sample",
-                    help="plan-specialised pass kernels (qtm_compile: two samples per CTA on f32x2 register "
-                         "pairs, or one sample per CTA) or the general pass kernel")
+    ap.add_argument("--kernels", choices=["paired", "one-sample", "lanes", "paired-general", "general"], default="lanes",
+                    help="plan-specialised pass kernels (qtm_compile: lanes = one sample per CTA with "
+                         "amplitudes paired in f32x2 registers, one-sample = scalar, paired = two samples per "
+                         "CTA), or the general pass kernels (paired-general / general)")
     ap.add_argument("--skip-extra", action="store_true", help="skip the uneven-batch and training lines")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle CPU work")

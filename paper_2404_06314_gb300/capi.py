@@ -22,9 +22,9 @@ QTM_OK, QTM_EINVAL, QTM_ENOMEM, QTM_ECUDA, QTM_EUNSUPPORTED, QTM_ETIMEOUT, QTM_E
 QTM_C64, QTM_C128 = 0, 1
 QTM_PATH_AUTO, QTM_PATH_FUSED, QTM_PATH_NAIVE = 0, 1, 2
 QTM_ADJ_GW_PER_SAMPLE, QTM_ADJ_RECOMPUTE = 1, 2
-QTM_COMPILE_ONE_SAMPLE = 1
-QTM_COMPILE_LANE_PAIRS = 2
-_COMPILE_KIND = {"pairs": 0, "one": QTM_COMPILE_ONE_SAMPLE, "lanes": QTM_COMPILE_LANE_PAIRS}
+QTM_COMPILE_SCALAR = 1
+QTM_COMPILE_SAMPLE_PAIRS = 2
+_COMPILE_KIND = {"lanes": 0, "one": QTM_COMPILE_SCALAR, "pairs": QTM_COMPILE_SAMPLE_PAIRS}
 
 
 class qtm_gate(ctypes.Structure):
@@ -290,12 +290,11 @@ class Plan:
         self._raise(st, "qtm_adjoint")
         return gx, gw
 
-    def compile(self, pairs: bool = True, kind: str = None):
+    def compile(self, kind: str = "lanes"):
         """Specialise and load this plan's pass kernels (qtm_compile).  kind:
-        "pairs" (two samples per CTA on f32x2 register pairs), "one" (one
-        sample per CTA, scalar registers) or "lanes" (one sample per CTA,
-        amplitudes paired in f32x2 registers); default from `pairs`."""
-        kind = kind or ("pairs" if pairs else "one")
+        "lanes" (default: one sample per CTA, amplitudes paired in f32x2
+        registers), "one" (one sample per CTA, scalar registers) or "pairs"
+        (two samples per CTA on f32x2 register pairs)."""
         self._raise(lib().qtm_compile(self.handle, _COMPILE_KIND[kind]), "qtm_compile")
         return self
 
@@ -311,14 +310,12 @@ class Plan:
     def compiled_passes(self) -> int:
         return int(lib().qtm_compiled_passes(self.handle))
 
-    def jit_source(self, which: int, index: int, pairs: bool = True, kind: str = None) -> str:
-        flags = _COMPILE_KIND[kind or ("pairs" if pairs else "one")]
-        return lib().qtm_debug_jit_source(self.handle, int(which), int(index), flags).decode()
+    def jit_source(self, which: int, index: int, kind: str = "lanes") -> str:
+        return lib().qtm_debug_jit_source(self.handle, int(which), int(index), _COMPILE_KIND[kind]).decode()
 
-    def jit_compile_check(self, pairs: bool = True, kind: str = None):
+    def jit_compile_check(self, kind: str = "lanes"):
         """Compile every specialised pass with NVRTC, host only (no load)."""
-        flags = _COMPILE_KIND[kind or ("pairs" if pairs else "one")]
-        self._raise(lib().qtm_debug_jit_compile(self.handle, flags), "qtm_debug_jit_compile")
+        self._raise(lib().qtm_debug_jit_compile(self.handle, _COMPILE_KIND[kind]), "qtm_debug_jit_compile")
 
     def jacobian(self, x, w, out=None, stream=None):
         """J[b, m, g] = d<O_m>/d theta_g for every gate angle (zero for CZ/CNOT)."""

@@ -712,7 +712,7 @@ namespace {
 // Generate and compile every pass (host only; NVRTC, no device).
 JitMode jit_mode(int flags)
 {
-    return (flags & QTM_COMPILE_LANE_PAIRS) ? JIT_LANES : (flags & QTM_COMPILE_ONE_SAMPLE) ? JIT_ONE : JIT_PAIRS;
+    return flags == QTM_COMPILE_SAMPLE_PAIRS ? JIT_PAIRS : flags == QTM_COMPILE_SCALAR ? JIT_ONE : JIT_LANES;
 }
 
 qtm_status compile_all(qtm_plan *p, JitMode mode, std::vector<std::vector<char>> &fwd_bin,
@@ -784,7 +784,7 @@ int qtm_get_sample_pairing(const qtm_plan *p) { return p ? p->pairing : 0; }
 qtm_status qtm_compile(qtm_plan *p, int flags)
 {
     if (!p) return QTM_EINVAL;
-    if (flags != 0 && flags != QTM_COMPILE_ONE_SAMPLE && flags != QTM_COMPILE_LANE_PAIRS)
+    if (flags != 0 && flags != QTM_COMPILE_SCALAR && flags != QTM_COMPILE_SAMPLE_PAIRS)
         return fail(p, QTM_EINVAL, "unknown flags");
     if (!jit_available()) return fail(p, QTM_EUNSUPPORTED, "NVRTC or driver entry points not available");
     const JitMode mode = jit_mode(flags);

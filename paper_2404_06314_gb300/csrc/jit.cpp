@@ -191,11 +191,13 @@ std::string diag_mask(const Plan &P, const DevOp &op, int lo)
 
 int lane_jj_host(int S, int k, int h) { return ((k >> S) << (S + 1)) | (h << S) | (k & ((1 << S) - 1)); }
 
-// lane bit of a phase: the register bit with the least gate work on it
+// lane bit of a phase: the register bit with the least gate work on it (bit 0
+// for a group at tile bit 0, where 16-byte shared accesses hold one lane pair)
 int choose_lane_bit(const Plan &P, const DevPhase &phs)
 {
     int cost[4] = {0, 0, 0, 0};
     const int lo = phs.lo;
+    if (lo == 0) return 0;
     for (int k = phs.op_begin; k < phs.op_end; ++k) {
         const DevOp &op = P.ops[k];
         if ((op.type == OP_U2 || op.type == OP_GRAD) && has_reg_bit(op.a, lo))

@@ -28,6 +28,13 @@ __host__ __device__ constexpr int lane_jj(int k, int h)
     return ((k >> S) << (S + 1)) | (h << S) | (k & ((1 << S) - 1));
 }
 
+// 32-byte table read that the compiler may not merge with an earlier one, so
+// the table's registers are free between two applications
+__device__ __forceinline__ void lds_table2(const f2 *t, f2 &a, f2 &b)
+{
+    asm volatile("ld.shared.v2.b64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "r"(smem_u32(t)));
+}
+
 __device__ __forceinline__ f2 swap2(f2 v)
 {
     f2 d;
@@ -60,18 +67,68 @@ __device__ __forceinline__ void stage_lane_table(const Cx<float> *mats, f2 *tab,
     }
 }
 
-// Registers <-> shared tile (one-sample layout) for register group LO, lane bit S.
+// Registers <-> shared tile (one-sample layout) for register group LO, lane bit
+// S.  Scalar 32-bit accesses put every value straight into its lane of the
+// destination pair (no repacking through temporaries).
+__device__ __forceinline__ float lds_f32(uint32_t addr)
+{
+    float v;
+    asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(addr));
+    return v;
+}
+__device__ __forceinline__ void sts_f32(uint32_t addr, float v)
+{
+    asm volatile("st.shared.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
+}
+
+// Register group at tile bit 0 with lane bit 0: a 16-byte element pair
+// (re0, im0, re1, im1) is exactly one lane pair; 16-byte accesses keep the
+// swizzled rows free of bank conflicts.
+template <bool LAM>
+__device__ __forceinline__ void regs_load_lanes_lo0(A2 (&p)[kLanePairs], A2 (&q)[kLanePairs], const TileSmem<float> &T,
+                                                    uint32_t xt)
+{
+#pragma unroll
+    for (int k = 0; k < kLanePairs; ++k) {
+        const int s = swz<float>((int)xt + 2 * k);
+        const float4 v = *reinterpret_cast<const float4 *>(&T.phi[s]);
+        p[k] = {pack2(v.x, v.z), pack2(v.y, v.w)};
+        if (LAM) {
+            const float4 u = *reinterpret_cast<const float4 *>(&T.lam[s]);
+            q[k] = {pack2(u.x, u.z), pack2(u.y, u.w)};
+        }
+    }
+}
+
+template <bool LAM>
+__device__ __forceinline__ void regs_store_lanes_lo0(const A2 (&p)[kLanePairs], const A2 (&q)[kLanePairs],
+                                                     const TileSmem<float> &T, uint32_t xt)
+{
+#pragma unroll
+    for (int k = 0; k < kLanePairs; ++k) {
+        const int s = swz<float>((int)xt + 2 * k);
+        *reinterpret_cast<float4 *>(&T.phi[s]) = make_float4(lane0(p[k].r), lane0(p[k].i), lane1(p[k].r), lane1(p[k].i));
+        if (LAM)
+            *reinterpret_cast<float4 *>(&T.lam[s]) =
+                make_float4(lane0(q[k].r), lane0(q[k].i), lane1(q[k].r), lane1(q[k].i));
+    }
+}
+
 template <int LO, int S, bool LAM>
 __device__ __forceinline__ void regs_load_lanes(A2 (&p)[kLanePairs], A2 (&q)[kLanePairs], const TileSmem<float> &T,
                                                 uint32_t xt)
 {
-    Cx<float> a[kRegs], b[kRegs];
-    regs_load<float, LO, LAM>(a, b, T, xt);
+    if constexpr (LO == 0 && S == 0) {
+        regs_load_lanes_lo0<LAM>(p, q, T, xt);
+        return;
+    }
+    const uint32_t ph = smem_u32(T.phi), lm = smem_u32(T.lam);
 #pragma unroll
     for (int k = 0; k < kLanePairs; ++k) {
-        const int j0 = lane_jj<S>(k, 0), j1 = lane_jj<S>(k, 1);
-        p[k] = {pack2(a[j0].x, a[j1].x), pack2(a[j0].y, a[j1].y)};
-        if (LAM) q[k] = {pack2(b[j0].x, b[j1].x), pack2(b[j0].y, b[j1].y)};
+        const uint32_t o0 = 8u * (uint32_t)swz<float>((int)(xt | ((uint32_t)lane_jj<S>(k, 0) << LO)));
+        const uint32_t o1 = 8u * (uint32_t)swz<float>((int)(xt | ((uint32_t)lane_jj<S>(k, 1) << LO)));
+        p[k] = {pack2(lds_f32(ph + o0), lds_f32(ph + o1)), pack2(lds_f32(ph + o0 + 4), lds_f32(ph + o1 + 4))};
+        if (LAM) q[k] = {pack2(lds_f32(lm + o0), lds_f32(lm + o1)), pack2(lds_f32(lm + o0 + 4), lds_f32(lm + o1 + 4))};
     }
 }
 
@@ -79,18 +136,22 @@ template <int LO, int S, bool LAM>
 __device__ __forceinline__ void regs_store_lanes(const A2 (&p)[kLanePairs], const A2 (&q)[kLanePairs],
                                                  const TileSmem<float> &T, uint32_t xt)
 {
-    Cx<float> a[kRegs], b[kRegs];
+    if constexpr (LO == 0 && S == 0) {
+        regs_store_lanes_lo0<LAM>(p, q, T, xt);
+        return;
+    }
+    const uint32_t ph = smem_u32(T.phi), lm = smem_u32(T.lam);
 #pragma unroll
     for (int k = 0; k < kLanePairs; ++k) {
-        const int j0 = lane_jj<S>(k, 0), j1 = lane_jj<S>(k, 1);
-        a[j0] = {lane0(p[k].r), lane0(p[k].i)};
-        a[j1] = {lane1(p[k].r), lane1(p[k].i)};
+        const uint32_t o0 = 8u * (uint32_t)swz<float>((int)(xt | ((uint32_t)lane_jj<S>(k, 0) << LO)));
+        const uint32_t o1 = 8u * (uint32_t)swz<float>((int)(xt | ((uint32_t)lane_jj<S>(k, 1) << LO)));
+        sts_f32(ph + o0, lane0(p[k].r)); sts_f32(ph + o1, lane1(p[k].r));
+        sts_f32(ph + o0 + 4, lane0(p[k].i)); sts_f32(ph + o1 + 4, lane1(p[k].i));
         if (LAM) {
-            b[j0] = {lane0(q[k].r), lane0(q[k].i)};
-            b[j1] = {lane1(q[k].r), lane1(q[k].i)};
+            sts_f32(lm + o0, lane0(q[k].r)); sts_f32(lm + o1, lane1(q[k].r));
+            sts_f32(lm + o0 + 4, lane0(q[k].i)); sts_f32(lm + o1 + 4, lane1(q[k].i));
         }
     }
-    regs_store<float, LO, LAM>(a, b, T, xt);
 }
 
 // a <- U a on register bit RB != S (whole registers pair up)
@@ -98,12 +159,9 @@ template <int S, int RB>
 __device__ __forceinline__ void u2_lanes(A2 (&a)[kLanePairs], const f2 *t)
 {
     constexpr int kb = RB < S ? RB : RB - 1;
-    const ulonglong2 *mv = reinterpret_cast<const ulonglong2 *>(t);
-    const ulonglong2 w0 = mv[0], w1 = mv[1], w2 = mv[2], w3 = mv[3], w4 = mv[4], w5 = mv[5];
-    const f2 a_r = w0.x, a_i = w0.y, a_n = w1.x;
-    const f2 b_r = w1.y, b_i = w2.x, b_n = w2.y;
-    const f2 c_r = w3.x, c_i = w3.y, c_n = w4.x;
-    const f2 d_r = w4.y, d_i = w5.x, d_n = w5.y;
+    f2 a_r, a_i, a_n, b_r, b_i, b_n, c_r, c_i, c_n, d_r, d_i, d_n;
+    lds_table2(t, a_r, a_i); lds_table2(t + 2, a_n, b_r); lds_table2(t + 4, b_i, b_n);
+    lds_table2(t + 6, c_r, c_i); lds_table2(t + 8, c_n, d_r); lds_table2(t + 10, d_i, d_n);
 #pragma unroll
     for (int k = 0; k < kLanePairs; ++k) {
         if (k & (1 << kb)) continue;
@@ -118,9 +176,8 @@ __device__ __forceinline__ void u2_lanes(A2 (&a)[kLanePairs], const f2 *t)
 // a <- U a on the lane bit S: Y = D X + O swap(X)
 __device__ __forceinline__ void u2_lanes_s(A2 (&a)[kLanePairs], const f2 *t)
 {
-    const ulonglong2 *mv = reinterpret_cast<const ulonglong2 *>(t + 12);
-    const ulonglong2 w0 = mv[0], w1 = mv[1], w2 = mv[2];
-    const f2 D_r = w0.x, D_i = w0.y, D_n = w1.x, O_r = w1.y, O_i = w2.x, O_n = w2.y;
+    f2 D_r, D_i, D_n, O_r, O_i, O_n;
+    lds_table2(t + 12, D_r, D_i); lds_table2(t + 14, D_n, O_r); lds_table2(t + 16, O_i, O_n);
 #pragma unroll
     for (int k = 0; k < kLanePairs; ++k) {
         const A2 x = a[k];

@@ -1,7 +1,8 @@
 """Run-time specialised pass kernels (qtm_compile).
 
-Two kinds of specialised kernel: paired (default; two samples per CTA, one
-per half of an f32x2 register pair) and one-sample.
+Three kinds of specialised kernel: lane-paired (default; one sample per CTA,
+the thread's amplitudes paired in f32x2 registers), scalar one-sample, and
+sample-paired (two samples per CTA, one per half of an f32x2 register pair).
 
 Host part (no GPU): the source written for every pass of the benchmark
 workloads and of random circuits compiles with NVRTC for sm_103a in both
@@ -20,9 +21,9 @@ import oracle_pins as P
 from paper_2404_06314_gb300 import capi, workloads as W
 
 
-def _nvrtc_or_skip(plan, pairs=True):
+def _nvrtc_or_skip(plan, kind="pairs"):
     try:
-        plan.jit_compile_check(pairs=pairs)
+        plan.jit_compile_check(kind=kind)
     except capi.QtmError as e:
         if e.status == capi.QTM_EUNSUPPORTED:
             pytest.skip("NVRTC not available")
@@ -63,7 +64,7 @@ def test_generated_source_compiles_benchmarks(kind):
 @pytest.mark.parametrize("n", [9, 13])
 def test_generated_source_compiles_random(n):
     plan = capi.Plan(_rand(n, 500 + n), dtype="c64")
-    _nvrtc_or_skip(plan, True)
+    _nvrtc_or_skip(plan, "pairs")
     _nvrtc_kind_or_skip(plan, "lanes")
 
 
@@ -105,7 +106,6 @@ def test_compiled_plan_matches_oracle(name, B, kind):
     general = _run(capi.Plan(c, dtype="c64"), c, inp)
     plan = capi.Plan(c, dtype="c64")
     plan.compile(kind=kind)
-    pairs = kind
     info = plan.info
     assert plan.compiled_passes() == info["fwd_passes"] + info["adj_passes"]
     got = _run(plan, c, inp)
@@ -113,9 +113,9 @@ def test_compiled_plan_matches_oracle(name, B, kind):
     _, gxo, gwo = oracle.adjoint(c, inp.gE, inp.x, inp.w, threads=0)
     for what, g, r, h in zip(("E", "gx", "gw"), got, (Eo, gxo, gwo), general):
         err = float(np.max(np.abs(g - r))) if r.size else 0.0
-        assert err <= 1e-5, f"{name} B={B} pairs={pairs} {what}: {err:.3e}"
+        assert err <= 1e-5, f"{name} B={B} kind={kind} {what}: {err:.3e}"
         d = float(np.max(np.abs(g - h))) if h.size else 0.0
-        assert d <= 2e-6, f"{name} B={B} pairs={pairs} compiled vs general {what}: {d:.3e}"
+        assert d <= 2e-6, f"{name} B={B} kind={kind} compiled vs general {what}: {d:.3e}"
 
 
 @pytest.mark.gpu

@@ -123,6 +123,16 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
+# DRAM bytes (read + write) per reverse-pass launch from one ncu capture of the
+# kernel kind the bench runs (profiles/ holds the summaries and commands);
+# reported as null for any other kernel kind.
+PROFILED_TRAFFIC = {
+    ("qnn12", "lanes"): (36.274432e6 + 0.700928e6, "profiles/qtm_gen_pass_lanes_qnn12_l6_b1024.md"),
+    ("qnn20", "lanes"): ((1.563446e9 + 2.098285e9 + 1.575316e9) / 3,
+                         "profiles/qtm_gen_pass_lanes_qnn20_l4_b64.md (mean of reverse passes 1-3)"),
+}
+
+
 def roofline(r, peaks, peak_src):
     """Roofline of the dominant kernel, the reverse pass k_pass<float, reverse>,
     from its live CUDA-event durations inside the timed region.  Algorithmic
@@ -149,7 +159,9 @@ def roofline(r, peaks, peak_src):
                "frac": hbm / hbm_peak, "peak_source": f"{peak_src} hbm_gbs (burst copy)"}
     main, other = (alu_obj, hbm_obj) if alu_obj["frac"] >= hbm_obj["frac"] else (hbm_obj, alu_obj)
     main = dict(main)
-    main.update({"kernel": KERNEL_LABEL[r["kernels"]], "traffic": None,
+    tr = PROFILED_TRAFFIC.get((r["workload"], r["kernels"]))
+    main.update({"kernel": KERNEL_LABEL[r["kernels"]], "traffic": tr[0] if tr else None,
+                 "traffic_source": tr[1] if tr else None,
                  "launch_ms": t * 1e3, "launches_timed": n,
                  "work_per_launch": {"flop": flops, "state_bytes": bytes_},
                  "other": {k: other[k] for k in ("bound", "achieved", "peak", "unit", "frac")}})
@@ -272,7 +284,7 @@ def measure_gpu(name, steps, warmup, device, seed_offset=0, profile=True, kernel
     lib.qtm_set_profiling(plan.handle, 0)
     plan.sync()
     info = plan.info
-    return dict(c=c, B=B, plan=plan, inp=inp, step_ms=step_ms, info=info, kernels=kernels,
+    return dict(c=c, B=B, plan=plan, inp=inp, step_ms=step_ms, info=info, kernels=kernels, workload=name,
                 pass_fwd_ms=pass_fwd_ms, pass_rev_ms=pass_rev_ms, n_fwd_pass=n_fwd_pass,
                 n_rev_pass=n_rev_pass, launches=launches)
 

@@ -58,6 +58,7 @@ struct qtm_plan {
     void *d_phi = nullptr, *d_lam = nullptr, *d_Escratch = nullptr;
     double *d_Epart = nullptr, *d_Gpart = nullptr, *d_abar = nullptr, *d_gw_ws = nullptr;
     void *d_mats = nullptr, *d_tabs = nullptr;
+    double2 *d_cs = nullptr;           // [B][rots] (cos, sin) of half angles (prep -> grad finalize)
     void *d_onehot = nullptr;          // [B][M] cotangent e_m (qtm_jacobian)
     int32_t *d_gate_of_rot = nullptr;  // rotation id -> gate index
     std::vector<CUtensorMap> tm_fwd, tm_rev_phi, tm_rev_lam;
@@ -128,10 +129,11 @@ void free_tables(qtm_plan *p)
 void free_workspace(qtm_plan *p)
 {
     void *ptrs[] = {p->d_phi, p->d_lam, p->d_Escratch, p->d_Epart, p->d_Gpart, p->d_abar, p->d_gw_ws,
-                    p->d_mats, p->d_tabs, p->d_onehot};
+                    p->d_mats, p->d_tabs, p->d_onehot, p->d_cs};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     p->d_phi = p->d_lam = p->d_Escratch = p->d_mats = p->d_tabs = p->d_onehot = nullptr;
+    p->d_cs = nullptr;
     p->d_Epart = p->d_Gpart = p->d_abar = p->d_gw_ws = nullptr;
     p->cap_B = 0;
     p->fwd_valid = false;
@@ -315,6 +317,7 @@ qtm_status ensure_workspace(qtm_plan *p, int B)
     AL(p->d_mats, csize * 4 * (size_t)B * runs);
     AL(p->d_tabs, csize * 16 * (size_t)B * ((P.state_qubits + 3) / 4));
     AL(p->d_onehot, rsize * (size_t)B * P.n_obs);
+    AL(p->d_cs, sizeof(double2) * (size_t)B * rots);
 #undef AL
     p->cap_B = B;
     if (P.path == QTM_PATH_FUSED) {
@@ -427,6 +430,7 @@ qtm_status run_prep(qtm_plan *p, int B, const void *x, const void *w, cudaStream
     a.B = B; a.n = P.n; a.state_qubits = P.state_qubits; a.n_runs = (int)P.runs.size();
     a.n_in = P.n_inputs; a.runs = p->d_runs; a.rots = p->d_rots;
     a.prefix_run_of_q = p->d_prefix_run_of_q; a.x = x; a.w = w; a.mats = p->d_mats; a.tabs = p->d_tabs;
+    a.cs = p->d_cs; a.n_rots = (int)P.rots.size();
     ProfScope ps(p, 1);
     cudaError_t e = launch_prep(P.dtype, a, s);
     if (e != cudaSuccess) return cuda_fail(p, e, "prep launch");
@@ -456,6 +460,7 @@ FinalizeArgs finalize_args(qtm_plan *p, int B, const void *x, const void *w)
     f.runs = p->d_runs; f.rots = p->d_rots;
     f.w_ptr = p->d_w_ptr; f.w_rots = p->d_w_rots; f.x_ptr = p->d_x_ptr; f.x_rots = p->d_x_rots;
     f.x = x; f.w = w; f.Epart = p->d_Epart; f.Gpart = p->d_Gpart; f.abar = p->d_abar;
+    f.cs = p->d_cs;
     return f;
 }
 

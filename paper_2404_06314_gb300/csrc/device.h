@@ -21,6 +21,7 @@ struct FinalizeArgs {
     void *gx;                     // [B][n_in] real (may be null)
     void *gw_out;                 // per-sample [B][P] real (may be null)
     double *gw_ws;                // per-sample [B][P] double workspace (may be null)
+    const double2 *cs;            // [B][n_rots] (cos, sin) of half angles from the prep (may be null)
 };
 
 struct PrepArgs {
@@ -31,6 +32,8 @@ struct PrepArgs {
     const void *x, *w;            // plan real type
     void *mats;                   // out: [B][n_runs][4] complex
     void *tabs;                   // out: [B][ntab][16] complex
+    double2 *cs;                  // out: [B][n_rots] (cos, sin) of half angles (may be null)
+    int n_rots;
 };
 
 // Per-sample run matrices and product-state tables, computed in FP64 and

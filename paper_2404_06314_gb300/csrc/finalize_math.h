@@ -24,10 +24,10 @@
 
 namespace qtm {
 
-// axis index of a rotation kind: X = 0, Y = 1, Z = 2 (QTM_RX/RY/RZ = 0/1/2)
-QTM_HD void adjoint_transpose_apply(int kind, double t, double u[3])
+// axis index of a rotation kind: X = 0, Y = 1, Z = 2 (QTM_RX/RY/RZ = 0/1/2);
+// c = cos(t), s = sin(t)
+QTM_HD void adjoint_transpose_apply_cs(int kind, double c, double s, double u[3])
 {
-    double c = cos(t), s = sin(t);
     double u0 = u[0], u1 = u[1], u2 = u[2];
     if (kind == 0) {        // Ad_RX = [[1,0,0],[0,c,-s],[0,s,c]]
         u[1] = c * u1 + s * u2;
@@ -39,6 +39,11 @@ QTM_HD void adjoint_transpose_apply(int kind, double t, double u[3])
         u[0] = c * u0 + s * u1;
         u[1] = -s * u0 + c * u1;
     }
+}
+
+QTM_HD void adjoint_transpose_apply(int kind, double t, double u[3])
+{
+    adjoint_transpose_apply_cs(kind, cos(t), sin(t), u);
 }
 
 // kinds[i], theta[i]: the run's rotations in forward order; v = (vx, vy, vz).

@@ -29,7 +29,8 @@ __global__ void k_prep(const PrepArgs a)
     prep_sample<R>(a.runs, a.rots, a.prefix_run_of_q, a.n_runs, a.n, a.state_qubits,
                    static_cast<const R *>(a.x) + (size_t)b * a.n_in, static_cast<const R *>(a.w),
                    static_cast<Cx<R> *>(a.mats) + (size_t)b * a.n_runs * 4,
-                   static_cast<Cx<R> *>(a.tabs) + (size_t)b * ntab * 16, ufac);
+                   static_cast<Cx<R> *>(a.tabs) + (size_t)b * ntab * 16, ufac,
+                   a.cs ? a.cs + (size_t)b * a.n_rots : nullptr);
 }
 
 template <typename R, bool REV>
@@ -74,7 +75,8 @@ __global__ void k_grad_finalize(const FinalizeArgs f)
                             f.abar + (size_t)b * f.n_rots,
                             f.gx ? static_cast<R *>(f.gx) + (size_t)b * f.n_in : nullptr,
                             f.gw_out ? static_cast<R *>(f.gw_out) + (size_t)b * f.P : nullptr,
-                            f.gw_ws ? f.gw_ws + (size_t)b * f.P : nullptr);
+                            f.gw_ws ? f.gw_ws + (size_t)b * f.P : nullptr,
+                            f.cs ? f.cs + (size_t)b * f.n_rots : nullptr);
 }
 
 // grad_w[j] = sum_b gw_ws[b][j]: one CTA per weight, each thread a fixed

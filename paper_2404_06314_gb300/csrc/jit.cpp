@@ -189,6 +189,15 @@ std::string diag_mask(const Plan &P, const DevOp &op, int lo)
 
 // ---- lane-paired one-sample kernels (tile_lanes.cuh) ---------------------------------
 
+// shared accesses of the lane kernels outside register group 0: 64-bit
+// (default; measured 2 % faster at 20 qubits) or scalar 32-bit
+// (QTM_JIT_LANES_VEC64=0, a tuning switch)
+const char *lanes_v64()
+{
+    const char *v = std::getenv("QTM_JIT_LANES_VEC64");
+    return (v && *v == '0') ? "false" : "true";
+}
+
 int lane_jj_host(int S, int k, int h) { return ((k >> S) << (S + 1)) | (h << S) | (k & ((1 << S) - 1)); }
 
 // lane bit of a phase: the register bit with the least gate work on it (bit 0
@@ -285,7 +294,7 @@ std::string phase_body(const Plan &P, const PassDesc &pd, const DevPhase &phs, b
     if (mode == JIT_LANES) {
         const int sl = choose_lane_bit(P, phs);
         o << "        constexpr int SB = " << sl << ";\n";
-        o << "        regs_load_lanes<LO, SB, " << (lam_valid ? "true" : "false") << ">(p, q, S, xt);\n";
+        o << "        regs_load_lanes<LO, SB, " << (lam_valid ? "true" : "false") << ", " << lanes_v64() << ">(p, q, S, xt);\n";
         for (int k = phs.op_begin; k < phs.op_end; ++k) {
             const DevOp &op = P.ops[k];
             const bool reg_a = has_reg_bit(op.a, lo);
@@ -337,7 +346,7 @@ std::string phase_body(const Plan &P, const PassDesc &pd, const DevPhase &phs, b
             default: break;
             }
         }
-        o << "        regs_store_lanes<LO, SB, " << (rev ? "true" : "false") << ">(p, q, S, xt);\n";
+        o << "        regs_store_lanes<LO, SB, " << (rev ? "true" : "false") << ", " << lanes_v64() << ">(p, q, S, xt);\n";
         return o.str();
     }
     if (pairs) o << "        regs_load_x2<LO, " << (lam_valid ? "true" : "false") << ">(p, q, S, xt);\n";

@@ -144,7 +144,8 @@ __global__ void k_multi_prep(const MultiArgs m)
                    static_cast<const R *>(m.x) + cd.x_off + (size_t)wi.b * cd.n_in,
                    static_cast<const R *>(m.w) + cd.w_off,
                    static_cast<Cx<R> *>(m.mats) + cd.mats_off + (size_t)wi.b * cd.n_runs * 4,
-                   static_cast<Cx<R> *>(m.tabs) + cd.tabs_off + (size_t)wi.b * ((cd.sq + 3) >> 2) * 16, ufac);
+                   static_cast<Cx<R> *>(m.tabs) + cd.tabs_off + (size_t)wi.b * ((cd.sq + 3) >> 2) * 16, ufac,
+                   nullptr);
 }
 
 // MINB: CTAs per SM the register budget is compiled for (1: no spills, 2: more
@@ -283,7 +284,7 @@ __global__ void k_multi_grad(const MultiArgs m)
                             m.Gpart + cd.Gpart_off + (size_t)b * cd.n_runs * cd.tiles * 3, cd.tiles,
                             m.abar + cd.abar_off + (size_t)b * cd.n_rots,
                             static_cast<R *>(m.gx) + cd.gx_off + (size_t)b * cd.n_in, nullptr,
-                            m.gwws + cd.gwws_off + (size_t)b * cd.P);
+                            m.gwws + cd.gwws_off + (size_t)b * cd.P, nullptr);
 }
 
 // grad_w of circuit c = sum over its samples, fixed order; one thread per weight

@@ -299,12 +299,16 @@ __host__ __device__ inline Layout make_layout(int K, int csize, bool rev, int ns
 
 // Fused matrix U = R_m ... R_1 of a run for sample b, in FP64 (row-major
 // u00, u01, u10, u11 as (re, im) pairs).  Rotation R_P(t) = cos(t/2) I - i sin(t/2) P.
+// Every R_P(t) is in SU(2), R = [[alpha, -conj(beta)], [beta, conj(alpha)]]
+// (RX: alpha = c, beta = -i s; RY: alpha = c, beta = s; RZ: alpha = c - i s,
+// beta = 0), so the product is carried as U = [[a, -conj(b)], [b, conj(a)]]
+// and R U costs two complex products: a <- alpha a - conj(beta) b,
+// b <- beta a + conj(alpha) b.  cs (may be null): each rotation's
+// (cos(t/2), sin(t/2)), indexed like rots.
 template <typename R>
-__device__ void run_matrix_f64(const Run rr, const Rot *rots, const R *xb, const R *w, double2 *U)
+__device__ void run_matrix_f64(const Run rr, const Rot *rots, const R *xb, const R *w, double2 *U, double2 *cs)
 {
-    double2 u00{1, 0}, u01{0, 0}, u10{0, 0}, u11{1, 0};
-    auto mul = [](double2 a, double2 b) { return double2{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x}; };
-    auto add = [](double2 a, double2 b) { return double2{a.x + b.x, a.y + b.y}; };
+    double2 a{1, 0}, b{0, 0};
     for (int i = rr.rot_begin; i < rr.rot_end; ++i) {
         const Rot ro = rots[i];
         double t = ro.coef;
@@ -312,31 +316,37 @@ __device__ void run_matrix_f64(const Run rr, const Rot *rots, const R *xb, const
         if (ro.x_idx >= 0) t *= (double)xb[ro.x_idx];
         double s, c;
         sincos(0.5 * t, &s, &c);
-        double2 g00, g01, g10, g11;
-        if (ro.kind == QTM_RX) { g00 = {c, 0}; g01 = {0, -s}; g10 = {0, -s}; g11 = {c, 0}; }
-        else if (ro.kind == QTM_RY) { g00 = {c, 0}; g01 = {-s, 0}; g10 = {s, 0}; g11 = {c, 0}; }
-        else { g00 = {c, -s}; g01 = {0, 0}; g10 = {0, 0}; g11 = {c, s}; }
-        const double2 n00 = add(mul(g00, u00), mul(g01, u10));
-        const double2 n01 = add(mul(g00, u01), mul(g01, u11));
-        const double2 n10 = add(mul(g10, u00), mul(g11, u10));
-        const double2 n11 = add(mul(g10, u01), mul(g11, u11));
-        u00 = n00; u01 = n01; u10 = n10; u11 = n11;
+        if (cs) cs[i] = double2{c, s};
+        double2 na, nb;
+        if (ro.kind == QTM_RX) {          // a' = c a - i s b, b' = -i s a + c b
+            na = {c * a.x + s * b.y, c * a.y - s * b.x};
+            nb = {s * a.y + c * b.x, c * b.y - s * a.x};
+        } else if (ro.kind == QTM_RY) {   // a' = c a - s b, b' = s a + c b
+            na = {c * a.x - s * b.x, c * a.y - s * b.y};
+            nb = {s * a.x + c * b.x, s * a.y + c * b.y};
+        } else {                          // a' = (c - i s) a, b' = (c + i s) b
+            na = {c * a.x + s * a.y, c * a.y - s * a.x};
+            nb = {c * b.x - s * b.y, c * b.y + s * b.x};
+        }
+        a = na;
+        b = nb;
     }
-    U[0] = u00; U[1] = u01; U[2] = u10; U[3] = u11;
+    U[0] = a; U[1] = double2{-b.x, b.y}; U[2] = b; U[3] = double2{a.x, -a.y};
 }
 
 
 // One CTA: every run's fused matrix for one sample (FP64, rounded once), and
 // the product-state tables T_j[v] = prod_{k<4} u_{4j+k}[bit k of v], u_q = U_prefix(q)|0>.
+// cs_b (may be null): this sample's per-rotation (cos(t/2), sin(t/2)).
 template <typename R>
 __device__ __forceinline__ void prep_sample(const Run *runs, const Rot *rots, const int32_t *prefix_run_of_q,
                                             int n_runs, int n, int sq, const R *xb, const R *w,
-                                            Cx<R> *mats, Cx<R> *tabs, double2 *ufac)
+                                            Cx<R> *mats, Cx<R> *tabs, double2 *ufac, double2 *cs_b)
 {
     for (int r = threadIdx.x; r < n_runs; r += blockDim.x) {
         double2 U[4];
         const Run rr = runs[r];
-        run_matrix_f64<R>(rr, rots, xb, w, U);
+        run_matrix_f64<R>(rr, rots, xb, w, U, cs_b);
         for (int k = 0; k < 4; ++k) mats[4 * r + k] = {(R)U[k].x, (R)U[k].y};
         if (rr.prefix) { ufac[2 * rr.q] = U[0]; ufac[2 * rr.q + 1] = U[2]; }
     }
@@ -795,7 +805,7 @@ template <typename R>
 __device__ __forceinline__ void grad_finalize_sample(
     const Run *runs, const Rot *rots, int n_runs, const int32_t *w_ptr, const int32_t *w_rots,
     const int32_t *x_ptr, const int32_t *x_rots, int P, int n_in, const R *xb, const R *w,
-    const double *Gpart_b, int tiles, double *abar, R *gx_b, R *gw_b, double *gwws_b)
+    const double *Gpart_b, int tiles, double *abar, R *gx_b, R *gw_b, double *gwws_b, const double2 *cs_b)
 {
     for (int r = threadIdx.x; r < n_runs; r += blockDim.x) {
         double v[3] = {0.0, 0.0, 0.0};
@@ -804,11 +814,16 @@ __device__ __forceinline__ void grad_finalize_sample(
         const Run rr = runs[r];
         for (int i = rr.rot_end - 1; i >= rr.rot_begin; --i) {
             const Rot ro = rots[i];
-            double t = ro.coef;
-            if (ro.w_idx >= 0) t *= (double)w[ro.w_idx];
-            if (ro.x_idx >= 0) t *= (double)xb[ro.x_idx];
             abar[i] = v[ro.kind];
-            adjoint_transpose_apply(ro.kind, t, v);
+            if (cs_b) {   // cos t, sin t from the prep's half-angle pair
+                const double2 h = cs_b[i];
+                adjoint_transpose_apply_cs(ro.kind, h.x * h.x - h.y * h.y, 2.0 * h.x * h.y, v);
+            } else {
+                double t = ro.coef;
+                if (ro.w_idx >= 0) t *= (double)w[ro.w_idx];
+                if (ro.x_idx >= 0) t *= (double)xb[ro.x_idx];
+                adjoint_transpose_apply(ro.kind, t, v);
+            }
         }
     }
     __syncthreads();

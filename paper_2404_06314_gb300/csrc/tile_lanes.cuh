@@ -114,7 +114,19 @@ __device__ __forceinline__ void regs_store_lanes_lo0(const A2 (&p)[kLanePairs], 
     }
 }
 
-template <int LO, int S, bool LAM>
+// One complex amplitude (re, im) as a 64-bit shared access.
+__device__ __forceinline__ void lds_c64(uint32_t addr, float &re, float &im)
+{
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(re), "=f"(im) : "r"(addr));
+}
+__device__ __forceinline__ void sts_c64(uint32_t addr, float re, float im)
+{
+    asm volatile("st.shared.v2.f32 [%0], {%1, %2};" ::"r"(addr), "f"(re), "f"(im) : "memory");
+}
+
+// V64: 64-bit accesses outside group 0 (conflict-free rows, lanes assembled
+// by register moves) instead of scalar 32-bit accesses.
+template <int LO, int S, bool LAM, bool V64 = false>
 __device__ __forceinline__ void regs_load_lanes(A2 (&p)[kLanePairs], A2 (&q)[kLanePairs], const TileSmem<float> &T,
                                                 uint32_t xt)
 {
@@ -123,6 +135,23 @@ __device__ __forceinline__ void regs_load_lanes(A2 (&p)[kLanePairs], A2 (&q)[kLa
         return;
     }
     const uint32_t ph = smem_u32(T.phi), lm = smem_u32(T.lam);
+    if constexpr (V64) {
+#pragma unroll
+    for (int k = 0; k < kLanePairs; ++k) {
+        const uint32_t o0 = 8u * (uint32_t)swz<float>((int)(xt | ((uint32_t)lane_jj<S>(k, 0) << LO)));
+        const uint32_t o1 = 8u * (uint32_t)swz<float>((int)(xt | ((uint32_t)lane_jj<S>(k, 1) << LO)));
+        float r0, i0, r1, i1;
+        lds_c64(ph + o0, r0, i0);
+        lds_c64(ph + o1, r1, i1);
+        p[k] = {pack2(r0, r1), pack2(i0, i1)};
+        if (LAM) {
+            lds_c64(lm + o0, r0, i0);
+            lds_c64(lm + o1, r1, i1);
+            q[k] = {pack2(r0, r1), pack2(i0, i1)};
+        }
+    }
+    return;
+    }
 #pragma unroll
     for (int k = 0; k < kLanePairs; ++k) {
         const uint32_t o0 = 8u * (uint32_t)swz<float>((int)(xt | ((uint32_t)lane_jj<S>(k, 0) << LO)));
@@ -132,7 +161,7 @@ __device__ __forceinline__ void regs_load_lanes(A2 (&p)[kLanePairs], A2 (&q)[kLa
     }
 }
 
-template <int LO, int S, bool LAM>
+template <int LO, int S, bool LAM, bool V64 = false>
 __device__ __forceinline__ void regs_store_lanes(const A2 (&p)[kLanePairs], const A2 (&q)[kLanePairs],
                                                  const TileSmem<float> &T, uint32_t xt)
 {
@@ -141,6 +170,20 @@ __device__ __forceinline__ void regs_store_lanes(const A2 (&p)[kLanePairs], cons
         return;
     }
     const uint32_t ph = smem_u32(T.phi), lm = smem_u32(T.lam);
+    if constexpr (V64) {
+#pragma unroll
+    for (int k = 0; k < kLanePairs; ++k) {
+        const uint32_t o0 = 8u * (uint32_t)swz<float>((int)(xt | ((uint32_t)lane_jj<S>(k, 0) << LO)));
+        const uint32_t o1 = 8u * (uint32_t)swz<float>((int)(xt | ((uint32_t)lane_jj<S>(k, 1) << LO)));
+        sts_c64(ph + o0, lane0(p[k].r), lane0(p[k].i));
+        sts_c64(ph + o1, lane1(p[k].r), lane1(p[k].i));
+        if (LAM) {
+            sts_c64(lm + o0, lane0(q[k].r), lane0(q[k].i));
+            sts_c64(lm + o1, lane1(q[k].r), lane1(q[k].i));
+        }
+    }
+    return;
+    }
 #pragma unroll
     for (int k = 0; k < kLanePairs; ++k) {
         const uint32_t o0 = 8u * (uint32_t)swz<float>((int)(xt | ((uint32_t)lane_jj<S>(k, 0) << LO)));

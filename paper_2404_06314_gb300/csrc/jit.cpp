@@ -198,6 +198,15 @@ const char *lanes_v64()
     return (v && *v == '0') ? "false" : "true";
 }
 
+// run-matrix table reads of the lane kernels: "true" = reads the compiler
+// may not merge across the two applications of a reverse op (default), else
+// plain loads (QTM_JIT_TABLE_VOLATILE=0, a tuning switch)
+std::string lanes_table_volatile()
+{
+    const char *v = std::getenv("QTM_JIT_TABLE_VOLATILE");
+    return (v && *v == '0') ? "false" : "true";
+}
+
 int lane_jj_host(int S, int k, int h) { return ((k >> S) << (S + 1)) | (h << S) | (k & ((1 << S) - 1)); }
 
 // lane bit of a phase: the register bit with the least gate work on it (bit 0
@@ -278,6 +287,144 @@ void gen_costate_lanes(std::ostringstream &o, const Plan &P, const PassDesc &pd,
     o << "        }\n";
 }
 
+
+// One op of a lane-paired phase (register group lo, lane bit sl); `slot` is
+// the C expression of its run slot.
+void lanes_op(std::ostringstream &o, const Plan &P, const PassDesc &pd, int k, int lo, int sl, const std::string &slot)
+{
+    const bool rev = pd.reverse != 0;
+    const int nslots = pd.slot_end - pd.slot_begin;
+    const DevOp &op = P.ops[k];
+    const bool reg_a = has_reg_bit(op.a, lo);
+    const bool reg_b = has_reg_bit(op.b, lo);
+    if (((op.type == OP_U2 || op.type == OP_GRAD) && !reg_a) || (op.type == OP_CNOT && !reg_b) ||
+        ((op.type == OP_U2 || op.type == OP_GRAD) && (op.slot < 0 || op.slot >= nslots)) ||
+        (op.type == OP_DIAG && (op.a < 0 || op.a + op.b > (int)P.diag_pairs.size()))) {
+        o << "#error \"op " << k << " has an operand outside its phase\"\n";
+        return;
+    }
+    const int rb = op.a - lo;
+    const std::string tab = "LT + " + std::to_string(kLaneSlotPairsHost) + " * " + slot;
+    const std::string vt = lanes_table_volatile();
+    const std::string apply =
+        rb == sl ? "u2_lanes_s<" + vt + ">(" : "u2_lanes<SB, " + std::to_string(rb) + ", " + vt + ">(";
+    switch (op.type) {
+    case OP_U2:
+        o << "        " << apply << "p, " << tab << ");\n";
+        break;
+    case OP_GRAD:
+        o << "        { float vx, vy, vz; "
+          << (rb == sl ? std::string("grad_lanes_s(") : "grad_lanes<SB, " + std::to_string(rb) + ">(")
+          << "p, q, vx, vy, vz);"
+          << " vx = warp_sum(vx, 32, 0xffffffffu); vy = warp_sum(vy, 32, 0xffffffffu);"
+          << " vz = warp_sum(vz, 32, 0xffffffffu);"
+          << " if (lane == 0) { float *g = S.redG + warp * " << 3 * nslots << " + 3 * " << slot
+          << "; g[0] = vx; g[1] = vy; g[2] = vz; }";
+        if (!(op.flags & OPF_SKIP_APPLY)) o << " " << apply << "p, " << tab << "); " << apply << "q, " << tab << ");";
+        o << " }\n";
+        break;
+    case OP_DIAG:
+        o << "        { " << diag_mask(P, op, lo) << " flip_lanes<SB, " << (rev ? "true" : "false") << ">(p, q, m); }\n";
+        break;
+    case OP_CNOT: {
+        const int rt = op.b - lo;
+        if (has_reg_bit(op.a, lo)) {
+            o << "        cnot_lanes_static<SB, " << (op.a - lo) << ", " << rt << ">(p);";
+            if (rev) o << " cnot_lanes_static<SB, " << (op.a - lo) << ", " << rt << ">(q);";
+            o << "\n";
+        } else {
+            o << "        { const int c = (int)(" << operand_bit(op.a) << " & 1u); cnot_lanes<SB, " << rt << ">(p, c);";
+            if (rev) o << " cnot_lanes<SB, " << rt << ">(q, c);";
+            o << " }\n";
+        }
+        break;
+    }
+    case OP_EXPVAL: gen_expval_lanes(o, P, pd, lo, sl); break;
+    case OP_COSTATE: gen_costate_lanes(o, P, pd, lo, sl); break;
+    default: break;
+    }
+}
+
+// Lane-paired pass as threaded code: every distinct routine (phase entry with
+// its register group and lane bit, one op with its register bits, phase exit)
+// is emitted once; a program of (routine, slot) pairs in constant memory
+// drives a dispatch loop.  The routines of a pass are far smaller than the
+// straight-line program, so they stay in the SM's instruction caches.
+std::string lanes_threaded_body(const Plan &P, const PassDesc &pd, int &n_routines, int &n_prog)
+{
+    const bool rev = pd.reverse != 0;
+    std::vector<std::string> routines;
+    std::vector<int> prog;
+    auto emit = [&](const std::string &body, int slot) {
+        size_t r = 0;
+        while (r < routines.size() && routines[r] != body) ++r;
+        if (r == routines.size()) routines.push_back(body);
+        prog.push_back((int)r);
+        prog.push_back(slot);
+    };
+    bool lam_valid = rev && pd.lam_src == SRC_LOAD;
+    for (int ph = pd.phase_begin; ph < pd.phase_end; ++ph) {
+        const DevPhase &phs = P.phases[ph];
+        const int lo = phs.lo, sl = choose_lane_bit(P, phs);
+        const std::string head = "        constexpr int LO = " + std::to_string(lo) + "; constexpr int SB = " +
+                                 std::to_string(sl) + "; (void)LO; (void)SB;\n";
+        {
+            std::ostringstream b;
+            b << head << "        xt = ((uint32_t)tid & ((1u << LO) - 1u)) | (((uint32_t)tid >> LO) << (LO + 4));\n";
+            b << "        regs_load_lanes<LO, SB, " << (lam_valid ? "true" : "false") << ", " << lanes_v64()
+              << ">(p, q, S, xt);\n";
+            emit(b.str(), 0);
+        }
+        for (int k = phs.op_begin; k < phs.op_end; ++k) {
+            std::ostringstream b;
+            b << head;
+            lanes_op(b, P, pd, k, lo, sl, "sl");
+            emit(b.str(), (P.ops[k].type == OP_U2 || P.ops[k].type == OP_GRAD) ? P.ops[k].slot : 0);
+        }
+        {
+            std::ostringstream b;
+            b << head << "        regs_store_lanes<LO, SB, " << (rev ? "true" : "false") << ", " << lanes_v64()
+              << ">(p, q, S, xt);\n        __syncthreads();\n";
+            emit(b.str(), 0);
+        }
+        if (rev) lam_valid = true;
+    }
+    n_routines = (int)routines.size();
+    n_prog = (int)prog.size() / 2;
+    std::ostringstream o;
+    o << "    uint32_t xt = 0;\n";
+    o << "#pragma unroll 1\n    for (int pc = 0; pc < " << n_prog << "; ++pc) {\n";
+    o << "        const int r = kProgram[2 * pc], sl = kProgram[2 * pc + 1];\n        (void)sl;\n";
+    o << "        switch (r) {\n";
+    for (size_t r = 0; r < routines.size(); ++r) {
+        o << "        " << (r + 1 < routines.size() ? "case " + std::to_string(r) + ":" : "default:") << " {\n";
+        o << routines[r] << "        } break;\n";
+    }
+    o << "        }\n    }\n";
+    std::ostringstream t;
+    t << "__constant__ int kProgram[" << (prog.empty() ? 2 : prog.size()) << "] = {";
+    for (size_t i = 0; i < prog.size(); ++i) t << (i ? ", " : "") << prog[i];
+    if (prog.empty()) t << "0, 0";
+    t << "};\n";
+    return t.str() + "\x01" + o.str();
+}
+
+// Phases emitted straight-line (default; measured 5 % faster at 12 and 20
+// qubits) or as a loop over a phase table with one copy of each distinct phase
+// program (QTM_JIT_PHASE_LOOP=1, a tuning switch).
+bool straight_phases(size_t, size_t)
+{
+    const char *v = std::getenv("QTM_JIT_PHASE_LOOP");
+    return !(v && *v == '1');
+}
+
+// threaded lane kernels (QTM_JIT_THREADED=1, a tuning switch)
+bool lanes_threaded()
+{
+    const char *v = std::getenv("QTM_JIT_THREADED");
+    return v && *v == '1';
+}
+
 // Body of one phase with its run slots written relative to the phase's first
 // slot `sb` (a runtime value): layers of a layered circuit repeat the same
 // body with other slots and then share one copy of the code.
@@ -295,57 +442,7 @@ std::string phase_body(const Plan &P, const PassDesc &pd, const DevPhase &phs, b
         const int sl = choose_lane_bit(P, phs);
         o << "        constexpr int SB = " << sl << ";\n";
         o << "        regs_load_lanes<LO, SB, " << (lam_valid ? "true" : "false") << ", " << lanes_v64() << ">(p, q, S, xt);\n";
-        for (int k = phs.op_begin; k < phs.op_end; ++k) {
-            const DevOp &op = P.ops[k];
-            const bool reg_a = has_reg_bit(op.a, lo);
-            const bool reg_b = has_reg_bit(op.b, lo);
-            if (((op.type == OP_U2 || op.type == OP_GRAD) && !reg_a) || (op.type == OP_CNOT && !reg_b) ||
-                ((op.type == OP_U2 || op.type == OP_GRAD) && (op.slot < 0 || op.slot >= nslots)) ||
-                (op.type == OP_DIAG && (op.a < 0 || op.a + op.b > (int)P.diag_pairs.size()))) {
-                o << "#error \"op " << k << " has an operand outside its phase\"\n";
-                continue;
-            }
-            const int rb = op.a - lo;
-            const std::string tab = "LT + " + std::to_string(kLaneSlotPairsHost) + " * " + slot(op.slot);
-            const std::string apply = rb == sl ? "u2_lanes_s(" : "u2_lanes<SB, " + std::to_string(rb) + ">(";
-            switch (op.type) {
-            case OP_U2:
-                o << "        " << apply << "p, " << tab << ");\n";
-                break;
-            case OP_GRAD:
-                o << "        { float vx, vy, vz; "
-                  << (rb == sl ? std::string("grad_lanes_s(") : "grad_lanes<SB, " + std::to_string(rb) + ">(")
-                  << "p, q, vx, vy, vz);"
-                  << " vx = warp_sum(vx, 32, 0xffffffffu); vy = warp_sum(vy, 32, 0xffffffffu);"
-                  << " vz = warp_sum(vz, 32, 0xffffffffu);"
-                  << " if (lane == 0) { float *g = S.redG + warp * " << 3 * nslots << " + 3 * " << slot(op.slot)
-                  << "; g[0] = vx; g[1] = vy; g[2] = vz; }";
-                if (!(op.flags & OPF_SKIP_APPLY)) o << " " << apply << "p, " << tab << "); " << apply << "q, " << tab << ");";
-                o << " }\n";
-                break;
-            case OP_DIAG:
-                o << "        { " << diag_mask(P, op, lo) << " flip_lanes<SB, " << (rev ? "true" : "false")
-                  << ">(p, q, m); }\n";
-                break;
-            case OP_CNOT: {
-                const int rt = op.b - lo;
-                if (has_reg_bit(op.a, lo)) {
-                    o << "        cnot_lanes_static<SB, " << (op.a - lo) << ", " << rt << ">(p);";
-                    if (rev) o << " cnot_lanes_static<SB, " << (op.a - lo) << ", " << rt << ">(q);";
-                    o << "\n";
-                } else {
-                    o << "        { const int c = (int)(" << operand_bit(op.a) << " & 1u); cnot_lanes<SB, " << rt
-                      << ">(p, c);";
-                    if (rev) o << " cnot_lanes<SB, " << rt << ">(q, c);";
-                    o << " }\n";
-                }
-                break;
-            }
-            case OP_EXPVAL: gen_expval_lanes(o, P, pd, lo, sl); break;
-            case OP_COSTATE: gen_costate_lanes(o, P, pd, lo, sl); break;
-            default: break;
-            }
-        }
+        for (int k = phs.op_begin; k < phs.op_end; ++k) lanes_op(o, P, pd, k, lo, sl, slot(P.ops[k].slot));
         o << "        regs_store_lanes<LO, SB, " << (rev ? "true" : "false") << ", " << lanes_v64() << ">(p, q, S, xt);\n";
         return o.str();
     }
@@ -463,6 +560,27 @@ std::string jit_source(const Plan &P, const PassDesc &pd, int min_blocks, JitMod
     if (table.empty()) o << "0, 0";
     o << "};\n";
     const int nslots = pd.slot_end - pd.slot_begin;
+    if (mode == JIT_LANES && lanes_threaded()) {
+        int nr = 0, np = 0;
+        const std::string tb = lanes_threaded_body(P, pd, nr, np);
+        const size_t cut = tb.find('\x01');
+        o << "// threaded: " << nr << " routines, " << np << " program steps\n" << tb.substr(0, cut);
+        o << "template <typename R>\n__device__ __forceinline__ void gen_phases(const TileJob &j, const TileSmem<R> &S, "
+             "bool)\n{\n    A2 p[kLanePairs];\n    A2 q[kLanePairs];\n"
+          << "    f2 *LT = reinterpret_cast<f2 *>(reinterpret_cast<unsigned char *>(S.phi) + " << lane_table_offset(P, pd)
+          << ");\n    stage_lane_table(S.mats, LT, " << nslots << ");\n    __syncthreads();\n";
+        o << "    const int tid = threadIdx.x;\n    const int warp = tid >> 5, lane = tid & 31;\n";
+        o << "    const uint32_t base = j.base;\n    (void)base; (void)lane; (void)warp; (void)j;\n";
+        o << tb.substr(cut + 1);
+        o << "}\n}  // namespace\n}  // namespace qtm\n\n";
+        o << "extern \"C\" __global__ void __launch_bounds__(256, " << min_blocks << ") qtm_gen_pass("
+          << "const __grid_constant__ qtm::PassArgs a, const __grid_constant__ CUtensorMap tm_phi, "
+          << "const __grid_constant__ CUtensorMap tm_lam)\n{\n";
+        o << "    qtm::pass_body<float, " << (rev ? "true" : "false") << ">(a, &tm_phi, &tm_lam, "
+          << "[](const qtm::TileJob &j, const qtm::TileSmem<float> &S, bool lv) { qtm::gen_phases<float>(j, S, lv); "
+             "});\n}\n";
+        return o.str();
+    }
     if (pairs)
         o << "__device__ __forceinline__ void gen_phases(const TileJobX2 &j, const TileSmemX2 &S)\n{\n"
           << "    using R = float;\n    A2 p[kRegs];\n    A2 q[kRegs];\n";
@@ -477,14 +595,21 @@ std::string jit_source(const Plan &P, const PassDesc &pd, int min_blocks, JitMod
              "bool)\n{\n    Cx<R> p[kRegs];\n    Cx<R> q[kRegs];\n";
     o << "    const int tid = threadIdx.x;\n    const int warp = tid >> 5, lane = tid & 31;\n";
     o << "    const uint32_t base = j.base;\n    (void)base; (void)lane; (void)warp; (void)j;\n";
-    o << "#pragma unroll 1\n    for (int ph = 0; ph < " << nph << "; ++ph) {\n";
-    o << "        const int sb = kPhaseTable[2 * ph + 1];\n        (void)sb;\n";
-    o << "        switch (kPhaseTable[2 * ph]) {\n";
-    for (size_t t = 0; t < tpl.size(); ++t) {
-        o << "        " << (t + 1 < tpl.size() ? "case " + std::to_string(t) + ":" : "default:") << " {\n";
-        o << tpl[t] << "        } break;\n";
+    if (straight_phases(tpl.size(), (size_t)nph)) {
+        // every phase its own block, in order (slots as constants through sb)
+        for (int ph = 0; ph < nph; ++ph)
+            o << "    {\n        const int sb = " << table[2 * ph + 1] << ";\n        (void)sb;\n"
+              << tpl[table[2 * ph]] << "        __syncthreads();\n    }\n";
+    } else {
+        o << "#pragma unroll 1\n    for (int ph = 0; ph < " << nph << "; ++ph) {\n";
+        o << "        const int sb = kPhaseTable[2 * ph + 1];\n        (void)sb;\n";
+        o << "        switch (kPhaseTable[2 * ph]) {\n";
+        for (size_t t = 0; t < tpl.size(); ++t) {
+            o << "        " << (t + 1 < tpl.size() ? "case " + std::to_string(t) + ":" : "default:") << " {\n";
+            o << tpl[t] << "        } break;\n";
+        }
+        o << "        }\n        __syncthreads();\n    }\n";
     }
-    o << "        }\n        __syncthreads();\n    }\n";
     o << "}\n}  // namespace\n}  // namespace qtm\n\n";
     o << "extern \"C\" __global__ void __launch_bounds__(256, " << min_blocks << ") qtm_gen_pass("
       << "const __grid_constant__ qtm::PassArgs a, const __grid_constant__ CUtensorMap tm_phi, "

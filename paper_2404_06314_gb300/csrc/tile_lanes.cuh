@@ -28,11 +28,19 @@ __host__ __device__ constexpr int lane_jj(int k, int h)
     return ((k >> S) << (S + 1)) | (h << S) | (k & ((1 << S) - 1));
 }
 
-// 32-byte table read that the compiler may not merge with an earlier one, so
-// the table's registers are free between two applications
+// 16-byte table read.  VT: one the compiler may not merge with an earlier
+// read (the table's registers are free between two applications), else a
+// plain load the compiler may schedule and reuse freely.
+template <bool VT>
 __device__ __forceinline__ void lds_table2(const f2 *t, f2 &a, f2 &b)
 {
-    asm volatile("ld.shared.v2.b64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "r"(smem_u32(t)));
+    if constexpr (VT) {
+        asm volatile("ld.shared.v2.b64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "r"(smem_u32(t)));
+    } else {
+        const ulonglong2 v = *reinterpret_cast<const ulonglong2 *>(t);
+        a = v.x;
+        b = v.y;
+    }
 }
 
 __device__ __forceinline__ f2 swap2(f2 v)
@@ -198,13 +206,13 @@ __device__ __forceinline__ void regs_store_lanes(const A2 (&p)[kLanePairs], cons
 }
 
 // a <- U a on register bit RB != S (whole registers pair up)
-template <int S, int RB>
+template <int S, int RB, bool VT = true>
 __device__ __forceinline__ void u2_lanes(A2 (&a)[kLanePairs], const f2 *t)
 {
     constexpr int kb = RB < S ? RB : RB - 1;
     f2 a_r, a_i, a_n, b_r, b_i, b_n, c_r, c_i, c_n, d_r, d_i, d_n;
-    lds_table2(t, a_r, a_i); lds_table2(t + 2, a_n, b_r); lds_table2(t + 4, b_i, b_n);
-    lds_table2(t + 6, c_r, c_i); lds_table2(t + 8, c_n, d_r); lds_table2(t + 10, d_i, d_n);
+    lds_table2<VT>(t, a_r, a_i); lds_table2<VT>(t + 2, a_n, b_r); lds_table2<VT>(t + 4, b_i, b_n);
+    lds_table2<VT>(t + 6, c_r, c_i); lds_table2<VT>(t + 8, c_n, d_r); lds_table2<VT>(t + 10, d_i, d_n);
 #pragma unroll
     for (int k = 0; k < kLanePairs; ++k) {
         if (k & (1 << kb)) continue;
@@ -217,10 +225,11 @@ __device__ __forceinline__ void u2_lanes(A2 (&a)[kLanePairs], const f2 *t)
 }
 
 // a <- U a on the lane bit S: Y = D X + O swap(X)
+template <bool VT = true>
 __device__ __forceinline__ void u2_lanes_s(A2 (&a)[kLanePairs], const f2 *t)
 {
     f2 D_r, D_i, D_n, O_r, O_i, O_n;
-    lds_table2(t + 12, D_r, D_i); lds_table2(t + 14, D_n, O_r); lds_table2(t + 16, O_i, O_n);
+    lds_table2<VT>(t + 12, D_r, D_i); lds_table2<VT>(t + 14, D_n, O_r); lds_table2<VT>(t + 16, O_i, O_n);
 #pragma unroll
     for (int k = 0; k < kLanePairs; ++k) {
         const A2 x = a[k];
@@ -237,17 +246,24 @@ __device__ __forceinline__ void grad_lanes(const A2 (&a)[kLanePairs], const A2 (
                                            float &vz)
 {
     constexpr int kb = RB < S ? RB : RB - 1;
-    f2 xp = 0, xn = 0, yp = 0, yn = 0, zp = 0, zn = 0;
+    f2 xp, xn, yp, yn, zp, zn;
 #pragma unroll
-    for (int k = 0; k < kLanePairs; ++k) {
+    for (int k = 0, first = 1; k < kLanePairs; ++k) {
         if (k & (1 << kb)) continue;
         const A2 a0 = a[k], a1 = a[k | (1 << kb)], b0 = b[k], b1 = b[k | (1 << kb)];
-        zp = fma2(b0.r, a0.i, zp); zn = fma2(b0.i, a0.r, zn);
+        if (first) {   // the first pair starts the accumulators (no zero fill)
+            zp = mul2(b0.r, a0.i); zn = mul2(b0.i, a0.r);
+            xp = mul2(b0.r, a1.i); xn = mul2(b0.i, a1.r);
+            yp = mul2(b1.r, a0.r); yn = mul2(b0.r, a1.r);
+            first = 0;
+        } else {
+            zp = fma2(b0.r, a0.i, zp); zn = fma2(b0.i, a0.r, zn);
+            xp = fma2(b0.r, a1.i, xp); xn = fma2(b0.i, a1.r, xn);
+            yp = fma2(b1.r, a0.r, yp); yn = fma2(b0.r, a1.r, yn);
+        }
         zn = fma2(b1.r, a1.i, zn); zp = fma2(b1.i, a1.r, zp);
-        xp = fma2(b0.r, a1.i, xp); xn = fma2(b0.i, a1.r, xn);
         xp = fma2(b1.r, a0.i, xp); xn = fma2(b1.i, a0.r, xn);
-        yp = fma2(b1.r, a0.r, yp); yp = fma2(b1.i, a0.i, yp);
-        yn = fma2(b0.r, a1.r, yn); yn = fma2(b0.i, a1.i, yn);
+        yp = fma2(b1.i, a0.i, yp); yn = fma2(b0.i, a1.i, yn);
     }
     const f2 X = sub2(xp, xn), Y = sub2(yp, yn), Z = sub2(zp, zn);
     vx = lane0(X) + lane1(X);
@@ -259,14 +275,21 @@ __device__ __forceinline__ void grad_lanes(const A2 (&a)[kLanePairs], const A2 (
 __device__ __forceinline__ void grad_lanes_s(const A2 (&a)[kLanePairs], const A2 (&b)[kLanePairs], float &vx,
                                              float &vy, float &vz)
 {
-    f2 zp = 0, zn = 0, xp = 0, xn = 0, yy = 0;
+    f2 zp, zn, xp, xn, yy;
 #pragma unroll
     for (int k = 0; k < kLanePairs; ++k) {
         const A2 x = a[k], l = b[k];
         const f2 sr = swap2(x.r), si = swap2(x.i);
-        zp = fma2(l.r, x.i, zp); zn = fma2(l.i, x.r, zn);   // lane-wise Im(conj(lam) phi)
-        xp = fma2(l.r, si, xp); xn = fma2(l.i, sr, xn);     // lane-wise Im(conj(lam) swap(phi))
-        yy = fma2(l.r, sr, yy); yy = fma2(l.i, si, yy);     // lane-wise Re(conj(lam) swap(phi))
+        if (k == 0) {   // the first register starts the accumulators
+            zp = mul2(l.r, x.i); zn = mul2(l.i, x.r);
+            xp = mul2(l.r, si); xn = mul2(l.i, sr);
+            yy = mul2(l.r, sr);
+        } else {
+            zp = fma2(l.r, x.i, zp); zn = fma2(l.i, x.r, zn);   // lane-wise Im(conj(lam) phi)
+            xp = fma2(l.r, si, xp); xn = fma2(l.i, sr, xn);     // lane-wise Im(conj(lam) swap(phi))
+            yy = fma2(l.r, sr, yy);                             // lane-wise Re(conj(lam) swap(phi))
+        }
+        yy = fma2(l.i, si, yy);
     }
     const f2 Z = sub2(zp, zn), X = sub2(xp, xn);
     vz = lane0(Z) - lane1(Z);

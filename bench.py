@@ -127,8 +127,8 @@ class ClockSampler:
 # kernel kind the bench runs (profiles/ holds the summaries and commands);
 # reported as null for any other kernel kind.
 PROFILED_TRAFFIC = {
-    ("qnn12", "lanes"): (36.274432e6 + 0.700928e6, "profiles/qtm_gen_pass_lanes_qnn12_l6_b1024.md"),
-    ("qnn20", "lanes"): ((1.563446e9 + 2.098285e9 + 1.575316e9) / 3,
+    ("qnn12", "lanes"): (36.324352e6 + 0.030208e6, "profiles/qtm_gen_pass_lanes_qnn12_l6_b1024.md"),
+    ("qnn20", "lanes"): ((1.560116e9 + 2.095630e9 + 1.575998e9) / 3,
                          "profiles/qtm_gen_pass_lanes_qnn20_l4_b64.md (mean of reverse passes 1-3)"),
 }
 

@@ -375,7 +375,8 @@ def measure_training(device, steps=100):
     return {"value": steps / (ms / 1e3), "unit": "steps/s", "samples_per_s": 256 * steps / (ms / 1e3),
             "ms_per_step": ms / steps, "loss_first": float(lc[0]), "loss_last": float(lc[-1]),
             "config": {"workload": "qnn16_l8_train: 16 qubits, 8 re-uploading layers + CZ ring, B=256, "
-                                   "MSE on sum_i <Z_i>, Adam lr 1e-2", "steps": steps}}
+                                   "MSE on sum_i <Z_i>, Adam lr 1e-2", "steps": steps,
+                       "pass_kernels": "QuantumModule(kernels='auto'): lane-paired specialised"}}
 
 
 def measure_e2e(name, steps, device, seed_offset=0, kernels="lanes"):

@@ -68,14 +68,31 @@ class QuantumModule(torch.nn.Module):
     groups: name -> list of weight indices of the circuit (together a partition
     of range(n_weights)); default one group "weights".  init: name -> "uniform"
     (U[0, 2 pi]), "normal" (N(0, 1)), "ones", "zeros" or a tensor.
+    kernels: "general" (the plan's general pass kernels), "paired-general"
+    (two samples per CTA), "lanes" / "one" / "pairs" (plan-specialised kernels,
+    compiled once here; see Plan.compile) or "auto" (lane-paired specialised
+    kernels when the plan has them, else the general kernels).
     """
 
     def __init__(self, circuit, groups: Optional[Dict[str, Sequence[int]]] = None,
                  init: Optional[Dict[str, object]] = None, dtype: str = "c64",
-                 path: str = "auto", device=None, generator: Optional[torch.Generator] = None):
+                 path: str = "auto", device=None, generator: Optional[torch.Generator] = None,
+                 kernels: str = "general"):
         super().__init__()
         self.circuit = circuit
         self.plan = capi.Plan(circuit, dtype=dtype, path=path)
+        if kernels == "auto":
+            try:
+                self.plan.compile("lanes")
+            except capi.QtmError as e:
+                if e.status != capi.QTM_EUNSUPPORTED:
+                    raise
+        elif kernels == "paired-general":
+            self.plan.set_pairing(True)
+        elif kernels in ("lanes", "one", "pairs"):
+            self.plan.compile(kernels)
+        elif kernels != "general":
+            raise ValueError(f"unknown kernels {kernels!r}")
         P = circuit.n_weights
         groups = dict(groups) if groups else {"weights": list(range(P))}
         seen = sorted(i for idx in groups.values() for i in idx)

@@ -11,11 +11,12 @@ from . import workloads as W
 from .autograd import QuantumModule
 
 
-def setup_qnn16(B: int = 256, seed: int = W.WORKLOAD_SEEDS["qnn16_l8_train"], device="cuda"):
+def setup_qnn16(B: int = 256, seed: int = W.WORKLOAD_SEEDS["qnn16_l8_train"], device="cuda",
+                kernels: str = "auto"):
     c = W.workload_16q_train()
     inp = W.make_inputs(c, B, seed, real_dtype=np.float32)
     y = W.make_targets(B, c.n, seed).astype(np.float32).astype(np.float64)
-    mod = QuantumModule(c, init={"weights": torch.tensor(inp.w)}, device=torch.device(device))
+    mod = QuantumModule(c, init={"weights": torch.tensor(inp.w)}, device=torch.device(device), kernels=kernels)
     x = torch.tensor(inp.x, dtype=torch.float32, device=device)
     t = torch.tensor(y, dtype=torch.float32, device=device)
     return c, inp, y, mod, x, t

@@ -63,10 +63,11 @@ def test_module_groups_and_learning_rates():
     assert not torch.equal(w1[scale_w], w0[scale_w])  # the scaling group moved
 
 
-def test_training_first_steps_match_oracle():
+@pytest.mark.parametrize("kernels", ["general", "auto"])
+def test_training_first_steps_match_oracle(kernels):
     import torch
     from paper_2404_06314_gb300 import train as T
-    c, inp, y, mod, x, t = T.setup_qnn16(B=16)
+    c, inp, y, mod, x, t = T.setup_qnn16(B=16, kernels=kernels)
     losses = T.train(mod, x, t, steps=3).double().cpu().numpy()
     # FP64 oracle-driven Adam with torch's defaults
     w = inp.w.copy(); m = np.zeros_like(w); v = np.zeros_like(w)

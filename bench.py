@@ -179,9 +179,10 @@ def dist_env():
 # CPU oracle timing (the reported baseline and the reference arm)
 # ------------------------------------------------------------------------------
 
-def oracle_rate(c, inp_full, budget_s: float, threads: int):
+def oracle_rate(c, inp_full, budget_s: float, threads: int, keep=None):
     """Time the FP64 oracle (forward + adjoint) on growing bounded samples of
-    the workload until about `budget_s` of CPU work; returns samples/s."""
+    the workload until about `budget_s` of CPU work; returns samples/s.  keep
+    (a dict, optional) receives the first chunk's rows and outputs."""
     import oracle
     S = max(1, threads)
     done, spent = 0, 0.0
@@ -190,20 +191,32 @@ def oracle_rate(c, inp_full, budget_s: float, threads: int):
         rows = [(done + i) % B for i in range(S)]
         x, gE = inp_full.x[rows], inp_full.gE[rows]
         t = time.perf_counter()
-        oracle.forward(c, x, inp_full.w, threads=threads)
-        oracle.adjoint(c, gE, x, inp_full.w, threads=threads)
+        E = oracle.forward(c, x, inp_full.w, threads=threads)
+        _, gx, gw = oracle.adjoint(c, gE, x, inp_full.w, threads=threads)
         spent += time.perf_counter() - t
+        if keep is not None and not keep:
+            keep.update(rows=rows, E=E, gx=gx, gw=gw)
         done += S
         if spent < budget_s / 8:
             S *= 2
     return done / spent, done, spent
 
 
+def accuracy(outputs, ref):
+    """Max abs error of E, grad_x and per-sample grad_w on the oracle's rows."""
+    import numpy as np
+    rows = np.array(ref["rows"])
+    E, gx, gw = outputs
+    err = lambda a, b: float(np.max(np.abs(a - b))) if b.size else 0.0
+    return {"rows": len(rows), "E": err(E[rows], ref["E"]), "grad_x": err(gx[rows], ref["gx"]),
+            "grad_w_per_sample": err(gw[rows], ref["gw"]), "reference": "FP64 oracle"}
+
+
 # ------------------------------------------------------------------------------
 # GPU measurement
 # ------------------------------------------------------------------------------
 
-KERNEL_LABEL = {"paired": "qtm_gen_pass (plan-specialised, two samples per CTA on f32x2 pairs), reverse",
+KERNEL_LABEL = {"naive": "naive one-gate-per-launch path","paired": "qtm_gen_pass (plan-specialised, two samples per CTA on f32x2 pairs), reverse",
                 "paired-general": "k_pass_x2<reverse> (general, two samples per CTA on f32x2 pairs)",
                 "one-sample": "qtm_gen_pass (plan-specialised, one sample per CTA), reverse",
                 "lanes": "qtm_gen_pass (plan-specialised, one sample per CTA, amplitudes paired in f32x2), reverse",
@@ -214,7 +227,7 @@ def prepare(plan, kernels):
     """Load the plan's specialised pass kernels unless the general kernel is asked for."""
     if kernels == "paired-general":
         plan.set_pairing(True)
-    elif kernels != "general":
+    elif kernels not in ("general", "naive"):
         plan.compile(kind={"paired": "pairs", "one-sample": "one", "lanes": "lanes"}[kernels])
         assert plan.compiled_passes() > 0, "no specialised pass kernel loaded"
     return plan
@@ -229,7 +242,7 @@ def measure_gpu(name, steps, warmup, device, seed_offset=0, profile=True, kernel
     cfg = WORKLOADS[name]
     c = getattr(W, cfg["builder"])()
     B = cfg["B"]
-    plan = prepare(capi.Plan(c, dtype=cfg["dtype"], path="fused"), kernels)
+    plan = prepare(capi.Plan(c, dtype=cfg["dtype"], path="naive" if kernels == "naive" else "fused"), kernels)
     rd = plan.real_dtype()
     inp = W.make_inputs(c, B, W.WORKLOAD_SEEDS[c.name] + seed_offset,
                         real_dtype=np.float32 if rd == torch.float32 else np.float64)
@@ -284,7 +297,14 @@ def measure_gpu(name, steps, warmup, device, seed_offset=0, profile=True, kernel
     lib.qtm_set_profiling(plan.handle, 0)
     plan.sync()
     info = plan.info
+    # outputs of the measured configuration (after the timed region): E, grad_x
+    # and per-sample grad_w, for the accuracy report against the oracle
+    plan.forward(x, w, out=E)
+    gx_o, gw_ps = plan.adjoint(gE, x, w, per_sample_w=True)
+    plan.sync()
+    outputs = (E.double().cpu().numpy(), gx_o.double().cpu().numpy(), gw_ps.double().cpu().numpy())
     return dict(c=c, B=B, plan=plan, inp=inp, step_ms=step_ms, info=info, kernels=kernels, workload=name,
+                outputs=outputs,
                 pass_fwd_ms=pass_fwd_ms, pass_rev_ms=pass_rev_ms, n_fwd_pass=n_fwd_pass,
                 n_rev_pass=n_rev_pass, launches=launches)
 
@@ -478,6 +498,16 @@ def gpu_main(args):
 
     extra = {}
     if args.workload == "qnn12" and not args.skip_extra:
+        # the one-gate-per-launch baseline on the same box and workloads
+        nv = {}
+        for wl, k in (("qnn12", 10), ("qnn20", 3)):
+            rn = measure_gpu(wl, k, 2, device, seed_offset=rank, profile=False, kernels="naive")
+            tn = sum(rn["step_ms"])
+            nv[wl] = {"value": rn["B"] * len(rn["step_ms"]) / (tn / 1e3), "unit": "samples/s",
+                      "ms_per_step": tn / len(rn["step_ms"]), "steps": len(rn["step_ms"]),
+                      "path": "naive: one kernel per gate over the batch, state in HBM"}
+            del rn
+        extra["naive"] = nv
         extra["uneven"] = measure_uneven(max(3, args.steps // 4), device, seed_offset=rank)
         extra["train16"] = measure_training(device)
     e2e = measure_e2e(args.workload, max(3, args.steps // 4), device, seed_offset=rank, kernels=args.kernels)
@@ -526,14 +556,25 @@ def gpu_main(args):
         }
     line.update(extra)
     if not args.no_cpu_baseline:
-        from paper_2404_06314_gb300 import workloads as W
         threads = os.cpu_count() or 1
         c = r12["c"]
-        rate, done, spent = oracle_rate(c, r12["inp"], args.cpu_budget, threads)
+        ref = {}
+        rate, done, spent = oracle_rate(c, r12["inp"], args.cpu_budget, threads, keep=ref)
+        rate1, done1, spent1 = oracle_rate(c, r12["inp"], max(1.0, args.cpu_budget / 4), 1)
         line["cpu_baseline"] = {"value": rate, "unit": "samples/s", "cores": threads, "kind": "oracle",
                                 "sample": f"{done} samples of the {c.name} batch, FP64 oracle forward + "
-                                          f"adjoint, {spent:.1f} s on {threads} threads"}
-        del W
+                                          f"adjoint, {spent:.1f} s on {threads} threads",
+                                "one_core": {"value": rate1, "unit": "samples/s", "cores": 1,
+                                             "sample": f"{done1} samples, {spent1:.1f} s"}}
+        # accuracy of the GPU outputs against the same oracle rows
+        line["accuracy"] = accuracy(r12["outputs"], ref)
+        if n20 is not None:   # two rows of the 20-qubit batch (about a second of oracle work each)
+            import oracle
+            c20, inp20 = n20[0]["c"], n20[0]["inp"]
+            rows = [0, inp20.x.shape[0] - 1]
+            E = oracle.forward(c20, inp20.x[rows], inp20.w, threads=threads)
+            _, gx, gw = oracle.adjoint(c20, inp20.gE[rows], inp20.x[rows], inp20.w, threads=threads)
+            line["n20"]["accuracy"] = accuracy(n20[0]["outputs"], {"rows": rows, "E": E, "gx": gx, "gw": gw})
     print(json.dumps(line), flush=True)
 
 

@@ -143,3 +143,24 @@ class QuantumModule(torch.nn.Module):
 
     def forward(self, x: torch.Tensor) -> torch.Tensor:
         return qnn(x, self.weight_vector(), self.plan)
+
+
+class HybridModule(torch.nn.Module):
+    """Classical layers around a quantum layer: y = post(quantum(pre(x))).
+
+    pre maps the sample features to the circuit's n_inputs angles, post maps
+    the M expectation values to the model output; either may be None (the
+    identity).  Gradients flow through all three (the quantum layer's through
+    the adjoint method)."""
+
+    def __init__(self, quantum: QuantumModule, pre: Optional[torch.nn.Module] = None,
+                 post: Optional[torch.nn.Module] = None):
+        super().__init__()
+        self.quantum = quantum
+        self.pre = pre
+        self.post = post
+
+    def forward(self, x: torch.Tensor) -> torch.Tensor:
+        h = self.pre(x) if self.pre is not None else x
+        e = self.quantum(h.contiguous())
+        return self.post(e) if self.post is not None else e

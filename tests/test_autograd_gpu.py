@@ -85,3 +85,29 @@ def test_training_first_steps_match_oracle(kernels):
     ref = np.array(ref)
     assert np.all(np.abs(losses - ref) <= 1e-4 * np.abs(ref)), (losses, ref)
     assert losses[2] < losses[0]
+
+
+def test_hybrid_module_chain_rule():
+    """Linear -> quantum layer -> Linear: the first layer's weight gradient is
+    (dL/dangles)^T x with dL/dangles from the FP64 oracle's adjoint."""
+    import torch
+    from paper_2404_06314_gb300.autograd import HybridModule, QuantumModule
+    c = W.layered_ansatz(6, 2, 6, "cz_ring", encode="every", terms=W.z_each(6), name="hyb6")
+    rng = np.random.default_rng(41)
+    B, F = 5, 4
+    w = rng.standard_normal(c.n_weights)
+    q = QuantumModule(c, init={"weights": torch.tensor(w)}, dtype="c128")
+    pre = torch.nn.Linear(F, c.n_inputs, dtype=torch.float64).cuda()
+    post = torch.nn.Linear(c.n_obs, 1, dtype=torch.float64).cuda()
+    model = HybridModule(q, pre, post)
+    x = torch.tensor(rng.uniform(-1, 1, size=(B, F)), device="cuda")
+    y = model(x)
+    y.sum().backward()
+    h = pre(x).detach().cpu().numpy()
+    E = oracle.forward(c, h, w, threads=0)
+    yo = E @ post.weight.detach().cpu().numpy().T + post.bias.detach().cpu().numpy()
+    assert np.max(np.abs(y.detach().cpu().numpy() - yo)) < 1e-12
+    gE = np.repeat(post.weight.detach().cpu().numpy(), B, axis=0)   # dL/dE = post.weight per sample
+    _, gx, gw = oracle.adjoint(c, gE, h, w, threads=0)
+    assert np.max(np.abs(pre.weight.grad.cpu().numpy() - gx.T @ x.cpu().numpy())) < 1e-11
+    assert np.max(np.abs(q.weights.grad.cpu().numpy() - gw.sum(0))) < 1e-11

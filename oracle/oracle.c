@@ -16,6 +16,9 @@
  *   - qubit q is bit q of the amplitude index (little endian);
  *   - a rotation about Pauli P by angle t is R_P(t) = exp(-i t P / 2)
  *     = cos(t/2) I - i sin(t/2) P;
+ *   - H is the Hadamard gate (|0> + |1>)/sqrt2 <- |0>; RZZ(t) = exp(-i t Z_a Z_b / 2)
+ *     multiplies amplitude x by exp(-i t/2) when bits a and b of x agree and by
+ *     exp(+i t/2) when they differ;
  *   - the angle of gate g for sample b is
  *       theta = coef[g] * (w_idx >= 0 ? w[w_idx] : 1) * (x_idx >= 0 ? x[b][x_idx] : 1)
  *     (trainable variational weights and trainable input scaling, Sec. II-C,
@@ -41,7 +44,7 @@ typedef double complex cplx;
 static const double OR_PI = 3.14159265358979323846264338327950288;
 
 /* Gate kinds of the circuit description. */
-enum { OR_RX = 0, OR_RY = 1, OR_RZ = 2, OR_CZ = 3, OR_CNOT = 4 };
+enum { OR_RX = 0, OR_RY = 1, OR_RZ = 2, OR_CZ = 3, OR_CNOT = 4, OR_H = 5, OR_RZZ = 6 };
 
 typedef struct {
     int32_t n;          /* qubits */
@@ -70,6 +73,8 @@ void oracle_partition(int B, int T, int t, int *start, int *count)
 }
 
 static int is_rotation(int k) { return k == OR_RX || k == OR_RY || k == OR_RZ; }
+/* gates with an angle (rotations and RZZ) */
+static int has_angle(int k) { return is_rotation(k) || k == OR_RZZ; }
 
 static double gate_angle(const or_circuit *c, int g, const double *xb, const double *w)
 {
@@ -141,6 +146,16 @@ static void apply_gate(const or_circuit *c, int g, double t, int adjoint, cplx *
         rotation(k, t, m);
         if (adjoint) dagger(m);
         apply_1q(psi, n, c->q0[g], m);
+    } else if (k == OR_H) {    /* self-inverse */
+        const double r = 1.0 / sqrt(2.0);
+        cplx m[2][2] = {{r, r}, {r, -r}};
+        apply_1q(psi, n, c->q0[g], m);
+    } else if (k == OR_RZZ) {  /* diagonal phase by the parity of bits q0, q1 */
+        uint64_t ba = 1ull << c->q0[g], bb = 1ull << c->q1[g];
+        cplx same = cexp(-I * 0.5 * t), diff = cexp(I * 0.5 * t);
+        if (adjoint) { same = conj(same); diff = conj(diff); }
+        for (uint64_t x = 0; x < N; ++x)
+            psi[x] *= (((x & ba) != 0) == ((x & bb) != 0)) ? same : diff;
     } else if (k == OR_CZ) {
         uint64_t ba = 1ull << c->q0[g], bb = 1ull << c->q1[g];
         for (uint64_t x = 0; x < N; ++x)
@@ -153,6 +168,24 @@ static void apply_gate(const or_circuit *c, int g, double t, int adjoint, cplx *
                 psi[x] = psi[x | bt];
                 psi[x | bt] = tmp;
             }
+    }
+}
+
+/* mu <- (dU_g/dtheta) mu for an angle gate g at angle t (mu holds the state
+ * before gate g on entry). */
+static void apply_gate_derivative(const or_circuit *c, int g, double t, cplx *mu)
+{
+    int n = c->n, k = c->kind[g];
+    if (is_rotation(k)) {
+        cplx dm[2][2];
+        rotation_derivative(k, t, dm);
+        apply_1q(mu, n, c->q0[g], dm);
+    } else { /* RZZ: d/dt exp(-i t z / 2) = (-i z / 2) exp(-i t z / 2), z = +-1 */
+        uint64_t N = 1ull << n, ba = 1ull << c->q0[g], bb = 1ull << c->q1[g];
+        for (uint64_t x = 0; x < N; ++x) {
+            double z = (((x & ba) != 0) == ((x & bb) != 0)) ? 1.0 : -1.0;
+            mu[x] *= -I * 0.5 * z * cexp(-I * 0.5 * t * z);
+        }
     }
 }
 
@@ -210,7 +243,7 @@ static void chain_rule(const or_circuit *c, const double *xb, const double *w,
     if (gx_b) for (int i = 0; i < c->n_in; ++i) gx_b[i] = 0.0;
     if (gw_b) for (int j = 0; j < c->P; ++j) gw_b[j] = 0.0;
     for (int g = 0; g < c->G; ++g) {
-        if (!is_rotation(c->kind[g])) continue;
+        if (!has_angle(c->kind[g])) continue;
         double W = c->widx[g] >= 0 ? w[c->widx[g]] : 1.0;
         double X = c->xidx[g] >= 0 ? xb[c->xidx[g]] : 1.0;
         if (gw_b && c->widx[g] >= 0) gw_b[c->widx[g]] += dtheta[g] * c->coef[g] * X;
@@ -232,11 +265,11 @@ static int nthreads_or_default(int threads)
 /* public entry points                                                 */
 /* ------------------------------------------------------------------ */
 
-/* Angles of every gate for one sample (0 for CZ/CNOT). */
+/* Angles of every gate for one sample (0 for CZ, CNOT and H). */
 void oracle_angles(const or_circuit *c, const double *xb, const double *w, double *theta)
 {
     for (int g = 0; g < c->G; ++g)
-        theta[g] = is_rotation(c->kind[g]) ? gate_angle(c, g, xb, w) : 0.0;
+        theta[g] = has_angle(c->kind[g]) ? gate_angle(c, g, xb, w) : 0.0;
 }
 
 /* Final state of one sample, interleaved (re, im), length 2 * 2^n. */
@@ -336,11 +369,9 @@ int oracle_adjoint(const or_circuit *c, int B, const double *gE, const double *x
                 for (int g = c->G - 1; g >= 0; --g) {
                     apply_gate(c, g, theta[g], 1, phi);
                     dth[g] = 0.0;
-                    if (is_rotation(c->kind[g])) {
-                        cplx dm[2][2];
+                    if (has_angle(c->kind[g])) {
                         memcpy(mu, phi, sizeof(cplx) * N);
-                        rotation_derivative(c->kind[g], theta[g], dm);
-                        apply_1q(mu, c->n, c->q0[g], dm);
+                        apply_gate_derivative(c, g, theta[g], mu);
                         dth[g] = 2.0 * inner_re(lam, mu, N);
                     }
                     apply_gate(c, g, theta[g], 1, lam);
@@ -395,11 +426,9 @@ int oracle_jacobian(const or_circuit *c, int B, const double *x, const double *w
                     for (int g = c->G - 1; g >= 0; --g) {
                         apply_gate(c, g, theta[g], 1, phi);
                         Jbm[g] = 0.0;
-                        if (is_rotation(c->kind[g])) {
-                            cplx dm[2][2];
+                        if (has_angle(c->kind[g])) {
                             memcpy(mu, phi, sizeof(cplx) * N);
-                            rotation_derivative(c->kind[g], theta[g], dm);
-                            apply_1q(mu, c->n, c->q0[g], dm);
+                            apply_gate_derivative(c, g, theta[g], mu);
                             Jbm[g] = 2.0 * inner_re(lam, mu, N);
                         }
                         apply_gate(c, g, theta[g], 1, lam);
@@ -412,7 +441,8 @@ int oracle_jacobian(const or_circuit *c, int B, const double *x, const double *w
 }
 
 /*
- * Parameter-shift rule (Crooks, cited in Sec. II-A): for each rotation gate,
+ * Parameter-shift rule (Crooks, cited in Sec. II-A): for each angle gate
+ * (rotations and RZZ, generators with eigenvalues +-1),
  *     d<O_m>/d theta_g = ( <O_m>(theta_g + pi/2) - <O_m>(theta_g - pi/2) ) / 2,
  * shifting the gate angle (never a weight shared by several gates), then the
  * cotangent gE and the chain rule.  2 |Theta| evolutions per sample.
@@ -449,7 +479,7 @@ int oracle_param_shift(const or_circuit *c, int B, const double *gE, const doubl
                 oracle_angles(c, xb, w, theta);
                 for (int g = 0; g < c->G; ++g) {
                     dth[g] = 0.0;
-                    if (!is_rotation(c->kind[g])) continue;
+                    if (!has_angle(c->kind[g])) continue;   /* generators with eigenvalues +-1 */
                     double t0 = theta[g];
                     theta[g] = t0 + 0.5 * OR_PI;
                     evolve(c, theta, psi);

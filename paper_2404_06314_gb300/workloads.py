@@ -23,6 +23,7 @@ from typing import List, Sequence, Tuple
 import numpy as np
 
 RX, RY, RZ, CZ, CNOT = 0, 1, 2, 3, 4
+H, RZZ = 5, 6          # Hadamard (no angle); RZZ(t) = exp(-i t Z_a Z_b / 2) on qubits (q0, q1)
 KIND_NAMES = {RX: "RX", RY: "RY", RZ: "RZ", CZ: "CZ", CNOT: "CNOT"}
 AXIS = {"X": RX, "Y": RY, "Z": RZ}
 

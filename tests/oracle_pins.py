@@ -54,6 +54,11 @@ def dense_gate(n, kind, q0, q1, theta):
     N = 1 << n
     if kind in PAULI:
         return embed(n, q0, scipy.linalg.expm(-0.5j * theta * PAULI[kind]))
+    if kind == W.H:
+        return embed(n, q0, np.array([[1, 1], [1, -1]], dtype=complex) / np.sqrt(2))
+    if kind == W.RZZ:   # expm of the generator Z_q0 Z_q1 (a diagonal matrix)
+        G = embed(n, q0, PAULI[W.RZ]) @ embed(n, q1, PAULI[W.RZ])
+        return scipy.linalg.expm(-0.5j * theta * G)
     if kind == W.CZ:
         d = np.array([-1.0 if ((x >> q0) & 1) and ((x >> q1) & 1) else 1.0 for x in range(N)])
         return np.diag(d).astype(complex)
@@ -91,14 +96,23 @@ def angles_py(c, xb, w):
     th = []
     for (k, q0, q1, wi, xi, coef) in c.gates:
         t = coef * (w[wi] if wi >= 0 else 1.0) * (xb[xi] if xi >= 0 else 1.0)
-        th.append(t if k in PAULI else 0.0)
+        th.append(t if (k in PAULI or k == W.RZZ) else 0.0)
     return np.array(th)
 
 
-def rand_small_circuit(rng, n, G, n_obs=3, P=5, n_in=3, shared=True):
+def rand_small_circuit(rng, n, G, n_obs=3, P=5, n_in=3, shared=True, extra=False):
+    """Random gate list over RX/RY/RZ/CZ/CNOT (extra: also H and RZZ)."""
     gates = []
     for _ in range(G):
         r = rng.random()
+        if extra and r < 0.12:
+            gates.append((W.H, int(rng.integers(0, n)), -1, -1, -1, 0.0))
+            continue
+        if extra and r < 0.24 and n > 1:
+            a, b = rng.choice(n, size=2, replace=False)
+            wi = int(rng.integers(-1, P)) if shared else -1
+            gates.append((W.RZZ, int(a), int(b), wi, int(rng.integers(-1, n_in)), float(rng.uniform(0.5, 1.5))))
+            continue
         if r < 0.65 or n == 1:
             k = int(rng.integers(0, 3))
             q = int(rng.integers(0, n))
@@ -361,7 +375,59 @@ def pin_paper_parameter_count(O=None):
         assert c.n_weights == case["trainable_parameters"], (case, c.n_weights)
 
 
+
+
+def pin_h_rzz_closed_form(O):
+    """H on both qubits, RZZ(t), H on qubit 0: <Z_0> = cos t (the X_0
+    expectation of RZZ(t)|++>), d<Z_0>/dt = -sin t; H|0> = (|0> + |1>)/sqrt2."""
+    for t in (0.0, 0.4, 1.3, np.pi / 2, 2.9):
+        c = W.Circuit(n=2, gates=[(W.H, 0, -1, -1, -1, 0.0), (W.H, 1, -1, -1, -1, 0.0),
+                                  (W.RZZ, 0, 1, 0, -1, 1.0), (W.H, 0, -1, -1, -1, 0.0)],
+                      terms=[(1, 1.0, 0)], n_obs=1, n_weights=1, n_inputs=0, name="hrzz")
+        x = np.zeros((1, 0)); w = np.array([t])
+        close(O.forward(c, x, w)[0], [np.cos(t)], 1e-14, f"H RZZ E t={t}")
+        J = O.jacobian(c, x, w)[0][0]
+        close(J, [0.0, 0.0, -np.sin(t), 0.0], 1e-13, f"H RZZ J t={t}")
+    c1 = W.Circuit(n=1, gates=[(W.H, 0, -1, -1, -1, 0.0)], terms=[(1, 1.0, 0)], n_obs=1, n_weights=0,
+                   n_inputs=0, name="h")
+    close(O.state(c1, np.zeros(0), np.zeros(0)), [1 / np.sqrt(2), 1 / np.sqrt(2)], 1e-15, "H|0>")
+
+
+def pin_dense_unitary_h_rzz(O, seeds=range(4)):
+    """States and expectation values with H and RZZ mixed into random
+    circuits, against dense expm / Kronecker unitaries, n = 1..6."""
+    for s in seeds:
+        rng = np.random.default_rng(700 + s)
+        for n in range(1, 7):
+            c = rand_small_circuit(rng, n, G=int(rng.integers(2, 20)), extra=True)
+            x = rng.uniform(-np.pi, np.pi, size=(2, c.n_inputs))
+            w = rng.normal(size=c.n_weights)
+            for b in range(2):
+                th = angles_py(c, x[b], w)
+                close(O.angles(c, x[b], w), th, 1e-15, "angles (H, RZZ)")
+                ref = dense_state(c, th)
+                close(O.state(c, x[b], w), ref, 1e-12, f"state (H, RZZ) n={n} seed={s}")
+                Eref = [np.real(np.vdot(ref, dense_observable(c, m) @ ref)) for m in range(c.n_obs)]
+                close(O.forward(c, x[b:b + 1], w)[0], Eref, 1e-12, f"E (H, RZZ) n={n} seed={s}")
+
+
+def pin_adjoint_equals_param_shift_h_rzz(O):
+    """Adjoint gradients (per gate angle, grad_x, grad_w) equal the exact
+    parameter-shift rule on circuits with H and RZZ."""
+    for s in range(3):
+        rng = np.random.default_rng(900 + s)
+        c = rand_small_circuit(rng, 5, G=30, extra=True)
+        x = rng.uniform(-np.pi, np.pi, size=(3, c.n_inputs)); w = rng.normal(size=c.n_weights)
+        gE = rng.normal(size=(3, c.n_obs))
+        dth_a, gx_a, gw_a = O.adjoint(c, gE, x, w)
+        dth_p, gx_p, gw_p = O.param_shift(c, gE, x, w)
+        close(dth_a, dth_p, 1e-12, "dtheta adjoint vs shift (H, RZZ)")
+        close(gx_a, gx_p, 1e-12, "gx adjoint vs shift (H, RZZ)")
+        close(gw_a, gw_p, 1e-12, "gw adjoint vs shift (H, RZZ)")
+
+
 ALL_PINS = [pin_single_rotation_closed_form, pin_bell, pin_dense_unitary, pin_norm,
             pin_product_state_bloch, pin_basis_state_cnot_chain, pin_trailing_diagonal,
             pin_finite_differences, pin_adjoint_equals_param_shift,
-            pin_threads_and_partition]
+            pin_threads_and_partition, pin_h_rzz_closed_form, pin_dense_unitary_h_rzz,
+            pin_adjoint_equals_param_shift_h_rzz]

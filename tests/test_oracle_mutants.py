@@ -42,6 +42,11 @@ MUTANTS = {
     "partition_extra_on_last": ("*count = base + (t < extra ? 1 : 0);",
                                 "*count = base + (t >= T - extra ? 1 : 0);"),
     "angle_ignores_input": ("if (c->xidx[g] >= 0) th *= xb[c->xidx[g]];", ""),
+    "rzz_phase_sign": ("cplx same = cexp(-I * 0.5 * t), diff = cexp(I * 0.5 * t);",
+                       "cplx same = cexp(I * 0.5 * t), diff = cexp(-I * 0.5 * t);"),
+    "rzz_derivative_sign": ("mu[x] *= -I * 0.5 * z * cexp(-I * 0.5 * t * z);",
+                            "mu[x] *= I * 0.5 * z * cexp(-I * 0.5 * t * z);"),
+    "hadamard_rows_swapped": ("cplx m[2][2] = {{r, r}, {r, -r}};", "cplx m[2][2] = {{r, -r}, {r, r}};"),
 }
 
 

@@ -57,7 +57,7 @@ typedef enum {
     QTM_ESTATE = 6         /* call order violated (e.g. adjoint without forward) */
 } qtm_status;
 
-typedef enum { QTM_RX = 0, QTM_RY = 1, QTM_RZ = 2, QTM_CZ = 3, QTM_CNOT = 4 } qtm_gate_kind;
+typedef enum { QTM_RX = 0, QTM_RY = 1, QTM_RZ = 2, QTM_CZ = 3, QTM_CNOT = 4, QTM_HADAMARD = 5, QTM_RZZ = 6 } qtm_gate_kind;
 
 typedef enum { QTM_C64 = 0, QTM_C128 = 1 } qtm_dtype;
 
@@ -69,7 +69,12 @@ typedef enum { QTM_PATH_AUTO = 0, QTM_PATH_FUSED = 1, QTM_PATH_NAIVE = 2 } qtm_p
 /* One gate (32 bytes).
  *   rotations (QTM_RX/RY/RZ): q0 = target, q1 = -1;
  *   QTM_CZ:   q0, q1 = the two qubits (symmetric);
- *   QTM_CNOT: q0 = control, q1 = target.
+ *   QTM_CNOT: q0 = control, q1 = target;
+ *   QTM_HADAMARD: Hadamard on q0, q1 = -1, no parameters (coef unused);
+ *   QTM_RZZ:  exp(-i theta Z_q0 Z_q1 / 2) on q0 != q1, theta as for rotations.
+ * The planner lowers H to RX(pi) RY(pi/2) (equal up to a global phase) and
+ * RZZ to CNOT(q0, q1) RZ_q1(theta) CNOT(q0, q1) (equal); gradients and
+ * Jacobian columns refer to the gates as given.
  * w_idx / x_idx = -1 means "factor 1" (Sec. II-C bindings, see above). */
 typedef struct {
     int32_t kind;

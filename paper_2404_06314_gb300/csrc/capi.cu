@@ -682,7 +682,7 @@ qtm_status qtm_jacobian(qtm_plan *p, int B, const void *x, const void *w, void *
     if (st != QTM_OK) return st;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const size_t rsize = elem_bytes(P.dtype) / 2;
-    const int G = (int)P.gates.size();
+    const int G = P.n_user_gates;   // Jacobian columns: the gates as given
     cudaError_t e = cudaMemsetAsync(jac, 0, rsize * (size_t)B * P.n_obs * (G > 0 ? G : 1), s);
     if (e != cudaSuccess) return cuda_fail(p, e, "jacobian clear");
     bool consumes = false;

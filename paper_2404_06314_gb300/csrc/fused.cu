@@ -113,7 +113,8 @@ __global__ void k_jac_scatter(const double *abar, const int32_t *gate_of_rot, in
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= B * n_rots) return;
     const int b = i / n_rots, r = i % n_rots;
-    J[((size_t)b * M + m) * G + gate_of_rot[r]] = (R)abar[(size_t)b * n_rots + r];
+    const int g = gate_of_rot[r];   // -1: a constant rotation from a lowered H (no column)
+    if (g >= 0) J[((size_t)b * M + m) * G + g] = (R)abar[(size_t)b * n_rots + r];
 }
 
 }  // namespace

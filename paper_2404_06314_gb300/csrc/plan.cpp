@@ -32,6 +32,7 @@ namespace qtm {
 namespace {
 
 bool is_rot(int k) { return k == QTM_RX || k == QTM_RY || k == QTM_RZ; }
+constexpr double kPi = 3.14159265358979323846264338327950288;
 
 struct Node {
     int type;      // 0 = run, 1 = entangler
@@ -359,6 +360,15 @@ qtm_status make_plan(int n, const qtm_gate *gates, int n_gates, const qtm_zterm 
             if (G.q0 < 0 || G.q0 >= n || G.q1 < 0 || G.q1 >= n) return bad(s.str() + "qubit out of range");
             if (G.q0 == G.q1) return bad(s.str() + "two-qubit gate on one qubit");
             if (G.w_idx != -1 || G.x_idx != -1) return bad(s.str() + "CZ/CNOT take no parameters");
+        } else if (G.kind == QTM_HADAMARD) {
+            if (G.q0 < 0 || G.q0 >= n) return bad(s.str() + "qubit out of range");
+            if (G.q1 != -1) return bad(s.str() + "H must have q1 = -1");
+            if (G.w_idx != -1 || G.x_idx != -1) return bad(s.str() + "H takes no parameters");
+        } else if (G.kind == QTM_RZZ) {
+            if (G.q0 < 0 || G.q0 >= n || G.q1 < 0 || G.q1 >= n) return bad(s.str() + "qubit out of range");
+            if (G.q0 == G.q1) return bad(s.str() + "two-qubit gate on one qubit");
+            if (G.w_idx < -1 || G.w_idx >= n_weights) return bad(s.str() + "w_idx out of range");
+            if (G.x_idx < -1 || G.x_idx >= n_inputs) return bad(s.str() + "x_idx out of range");
         } else {
             return bad(s.str() + "unknown gate kind");
         }
@@ -376,7 +386,37 @@ qtm_status make_plan(int n, const qtm_gate *gates, int n_gates, const qtm_zterm 
     P = Plan();
     P.n = n; P.dtype = dtype; P.n_obs = n_obs; P.n_weights = n_weights; P.n_inputs = n_inputs;
     P.path = (path == QTM_PATH_NAIVE) ? QTM_PATH_NAIVE : QTM_PATH_FUSED;
-    P.gates.assign(gates, gates + n_gates);
+    P.n_user_gates = n_gates;
+
+    // ---- 0. lower H and RZZ to the native gate set -------------------------
+    // H = RX(pi) RY(pi/2) up to the global phase -i (no expectation value or
+    // gradient sees a global phase); RZZ(t) = CNOT(q0 -> q1) RZ_q1(t) CNOT,
+    // exactly (CNOT Z_q1 CNOT = Z_q0 Z_q1), so RZ's angle gradient is RZZ's.
+    // origin[g]: the user gate whose angle lowered gate g carries (-1: none).
+    std::vector<qtm_gate> lowered;
+    std::vector<int> origin;
+    for (int g = 0; g < n_gates; ++g) {
+        const qtm_gate &G = gates[g];
+        if (G.kind == QTM_HADAMARD) {
+            lowered.push_back({QTM_RY, G.q0, -1, -1, -1, 0, 0.5 * kPi});
+            origin.push_back(-1);
+            lowered.push_back({QTM_RX, G.q0, -1, -1, -1, 0, kPi});
+            origin.push_back(-1);
+        } else if (G.kind == QTM_RZZ) {
+            lowered.push_back({QTM_CNOT, G.q0, G.q1, -1, -1, 0, 1.0});
+            origin.push_back(-1);
+            lowered.push_back({QTM_RZ, G.q1, -1, G.w_idx, G.x_idx, 0, G.coef});
+            origin.push_back(g);
+            lowered.push_back({QTM_CNOT, G.q0, G.q1, -1, -1, 0, 1.0});
+            origin.push_back(-1);
+        } else {
+            lowered.push_back(G);
+            origin.push_back(is_rot(G.kind) ? g : -1);
+        }
+    }
+    gates = lowered.data();
+    n_gates = (int)lowered.size();
+    P.gates = lowered;
     for (int t = 0; t < n_terms; ++t)
         P.terms.push_back({terms[t].zmask, terms[t].coef, terms[t].obs, 0});
     std::stable_sort(P.terms.begin(), P.terms.end(),
@@ -414,7 +454,7 @@ qtm_status make_plan(int n, const qtm_gate *gates, int n_gates, const qtm_zterm 
     auto add_rot = [&](int g) {
         const qtm_gate &G = gates[g];
         P.rot_of_gate[g] = (int)P.rots.size();
-        P.rots.push_back({G.kind, g, G.w_idx, G.x_idx, G.coef});
+        P.rots.push_back({G.kind, origin[g], G.w_idx, G.x_idx, G.coef});   // gate = user gate (or -1)
     };
     for (int q = 0; q < n; ++q) {
         if (prefix_rots[q].empty()) continue;

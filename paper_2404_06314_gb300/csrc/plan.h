@@ -15,7 +15,8 @@ struct Plan {
     // circuit
     int n = 0, dtype = QTM_C64, path = QTM_PATH_FUSED;
     int n_obs = 0, n_weights = 0, n_inputs = 0;
-    std::vector<qtm_gate> gates;
+    std::vector<qtm_gate> gates;        // lowered to RX/RY/RZ/CZ/CNOT (H and RZZ expanded)
+    int n_user_gates = 0;               // gates as given to qtm_build (Jacobian columns)
     std::vector<Term> terms;            // sorted by obs
 
     // runs and rotations

@@ -69,6 +69,11 @@ def _build_raw(n, gates, terms, n_obs=1, P_=2, n_in=2, dtype=0, path=0):
     dict(n=3, gates=[], terms=[], n_obs=0),
     dict(n=3, gates=[], terms=[], dtype=5),
     dict(n=3, gates=[], terms=[], path=9),
+    dict(n=3, gates=[(5, 0, -1, 0, -1, 0, 1.0)], terms=[]),           # H with a weight
+    dict(n=3, gates=[(5, 0, 1, -1, -1, 0, 1.0)], terms=[]),           # H with q1
+    dict(n=3, gates=[(6, 1, 1, 0, -1, 0, 1.0)], terms=[]),            # RZZ on one qubit
+    dict(n=3, gates=[(6, 0, 3, 0, -1, 0, 1.0)], terms=[]),            # RZZ qubit out of range
+    dict(n=3, gates=[(6, 0, 1, 2, -1, 0, 1.0)], terms=[]),            # RZZ w_idx out of range
 ])
 def test_build_rejects_bad_arguments(case):
     assert _build_raw(**case) == capi.QTM_EINVAL
@@ -112,6 +117,16 @@ def test_schedule_matches_oracle_random(n):
     rng = np.random.default_rng(40 + n)
     c = P.rand_small_circuit(rng, n, G=6 * n + 8, n_obs=3)
     c.name = f"rand{n}"
+    _emulate_vs_oracle(c, 2, n)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 8, 12, 13, 16])
+def test_schedule_with_h_and_rzz_matches_oracle(n):
+    """H and RZZ are lowered by the planner (RX(pi) RY(pi/2); CNOT RZ CNOT);
+    the oracle applies them from their definitions."""
+    rng = np.random.default_rng(400 + n)
+    c = P.rand_small_circuit(rng, n, G=6 * n + 8, n_obs=3, extra=True)
+    c.name = f"hrzz{n}"
     _emulate_vs_oracle(c, 2, n)
 
 

@@ -210,3 +210,20 @@ def test_paired_general_jacobian_and_toggle():
     plan.set_pairing(False)
     E0 = plan.forward(x, w).double().cpu().numpy()
     assert np.max(np.abs(E1 - E0)) <= 2e-6
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("kind", ["lanes", "one", "pairs"])
+@pytest.mark.parametrize("n", [9, 12, 14])
+def test_compiled_plan_with_h_and_rzz(n, kind):
+    rng = np.random.default_rng(950 + n)
+    c = P.rand_small_circuit(rng, n, G=5 * n + 10, n_obs=3, extra=True)
+    inp = W.make_inputs(c, 3, 17, real_dtype=np.float32)
+    plan = capi.Plan(c, dtype="c64")
+    plan.compile(kind=kind)
+    got = _run(plan, c, inp)
+    Eo = oracle.forward(c, inp.x, inp.w, threads=0)
+    _, gxo, gwo = oracle.adjoint(c, inp.gE, inp.x, inp.w, threads=0)
+    for what, g, r in zip(("E", "gx", "gw"), got, (Eo, gxo, gwo)):
+        err = float(np.max(np.abs(g - r))) if r.size else 0.0
+        assert err <= 1e-5, f"n={n} kind={kind} {what}: {err:.3e}"

@@ -219,3 +219,35 @@ def test_jacobian_paper_workload_tab1_shape():
     Jo = oracle.jacobian(c, inp.x, inp.w, threads=0)
     assert J.shape == (2, 12, c.n_gates)
     assert_close(J, Jo, 1e-5, "jacobian 12q depth 3")
+
+
+# ---- Hadamard and RZZ (lowered by the planner; the oracle applies them directly) ----
+
+@pytest.mark.parametrize("n", [2, 5, 9, 12, 13, 16])
+def test_h_rzz_random_circuits(n):
+    rng = np.random.default_rng(800 + n)
+    c = P.rand_small_circuit(rng, n, G=5 * n + 10, n_obs=3, extra=True)
+    c.name = f"hrzz{n}"
+    check(c, 3, "c64")
+    check(c, 2, "c128", tol=1e-11)
+    if n <= 9:
+        check(c, 2, "c64", "naive")
+
+
+def test_h_rzz_jacobian_columns():
+    """J has one column per gate as given: RZZ columns carry the angle
+    gradient, H / CZ / CNOT columns are zero."""
+    import torch
+    rng = np.random.default_rng(881)
+    c = P.rand_small_circuit(rng, 7, G=45, n_obs=2, extra=True)
+    plan = capi.Plan(c, dtype="c128")
+    inp = W.make_inputs(c, 2, 3, real_dtype=np.float64)
+    x = torch.tensor(inp.x, device="cuda")
+    w = torch.tensor(inp.w, device="cuda")
+    J = plan.jacobian(x, w)
+    plan.sync()
+    Jo = oracle.jacobian(c, inp.x, inp.w, threads=0)
+    assert J.shape == (2, 2, c.n_gates)
+    assert_close(J.cpu().numpy(), Jo, 1e-11, "jacobian with H and RZZ")
+    no_angle = [g for g, gt in enumerate(c.gates) if gt[0] in (W.H, W.CZ, W.CNOT)]
+    assert np.all(J.cpu().numpy()[:, :, no_angle] == 0)

@@ -26,7 +26,7 @@ class _Circ(ctypes.Structure):
         ("widx", ctypes.c_void_p), ("xidx", ctypes.c_void_p), ("coef", ctypes.c_void_p),
         ("T", ctypes.c_int32), ("zmask", ctypes.c_void_p), ("zcoef", ctypes.c_void_p),
         ("zobs", ctypes.c_void_p), ("M", ctypes.c_int32), ("P", ctypes.c_int32),
-        ("n_in", ctypes.c_int32),
+        ("n_in", ctypes.c_int32), ("xmask", ctypes.c_void_p),
     ]
 
 
@@ -34,12 +34,14 @@ class _Bound:
     """Keeps the numpy arrays alive while the C struct points into them."""
 
     def __init__(self, c):
-        arrs = [np.ascontiguousarray(a) for a in list(c.gate_arrays()) + list(c.term_arrays())]
+        xm = c.xmask_array() if hasattr(c, "xmask_array") else np.zeros(len(c.terms), dtype=np.uint64)
+        arrs = [np.ascontiguousarray(a) for a in list(c.gate_arrays()) + list(c.term_arrays()) + [xm]]
         self.arrs = arrs
-        k, q0, q1, wi, xi, co, zm, zc, zo = arrs
+        k, q0, q1, wi, xi, co, zm, zc, zo, xa = arrs
         p = lambda a: a.ctypes.data if a.size else None
         self.s = _Circ(c.n, len(k), p(k), p(q0), p(q1), p(wi), p(xi), p(co),
-                       len(zm), p(zm), p(zc), p(zo), c.n_obs, c.n_weights, c.n_inputs)
+                       len(zm), p(zm), p(zc), p(zo), c.n_obs, c.n_weights, c.n_inputs,
+                       p(xa) if np.any(xa) else None)
 
     @property
     def ref(self):

@@ -23,8 +23,12 @@
  *       theta = coef[g] * (w_idx >= 0 ? w[w_idx] : 1) * (x_idx >= 0 ? x[b][x_idx] : 1)
  *     (trainable variational weights and trainable input scaling, Sec. II-C,
  *     Eq. (concrete_ansatz));
- *   - observable m is a real combination of Z strings,
- *       O_m = sum_{t : obs_t = m} c_t Z^{mask_t}.
+ *   - observable m is a real combination of Pauli strings,
+ *       O_m = sum_{t : obs_t = m} c_t P_t,
+ *     P_t = prod_q sigma_q with sigma_q = X where only xmask_t has bit q,
+ *     Y where both xmask_t and zmask_t have it, Z where only zmask_t has it;
+ *     Z strings (xmask = 0, or no xmask array) are diagonal:
+ *       P|x> = i^(#Y) (-1)^popcount(x & zmask) |x ^ xmask>.
  *
  * Parity is pinned by tests/test_oracle_pins.py (closed forms, dense
  * Kronecker-product unitaries, product-state Bloch rotations, parameter shift
@@ -58,6 +62,7 @@ typedef struct {
     int32_t M;          /* observables */
     int32_t P;          /* weights */
     int32_t n_in;       /* inputs per sample */
+    const uint64_t *xmask;   /* per term X/Y qubits, or NULL: all terms are Z strings */
 } or_circuit;
 
 /* ------------------------------------------------------------------ */
@@ -206,6 +211,40 @@ static double obs_diag(const or_circuit *c, int m, uint64_t x)
     return d;
 }
 
+static int has_xy(const or_circuit *c)
+{
+    if (!c->xmask) return 0;
+    for (int t = 0; t < c->T; ++t)
+        if (c->xmask[t]) return 1;
+    return 0;
+}
+
+/* out += s * P_t in, for one Pauli string (see the conventions above). */
+static void add_pauli(const or_circuit *c, int t, double s, const cplx *in, cplx *out)
+{
+    uint64_t N = 1ull << c->n, xm = c->xmask ? c->xmask[t] : 0, zm = c->zmask[t];
+    int ny = popcount64(xm & zm);
+    cplx ph = 1;
+    for (int k = 0; k < (ny & 3); ++k) ph *= I;       /* i^(#Y) */
+    for (uint64_t y = 0; y < N; ++y) {
+        uint64_t x = y ^ xm;                            /* <y|P|x> != 0 only for x = y ^ xmask */
+        double sg = (popcount64(x & zm) & 1) ? -1.0 : 1.0;
+        out[y] += s * ph * sg * in[x];
+    }
+}
+
+/* out = (sum_m g_m O_m) in, g = NULL: observable m_only alone. */
+static void apply_observables(const or_circuit *c, const double *g, int m_only, const cplx *in, cplx *out)
+{
+    uint64_t N = 1ull << c->n;
+    for (uint64_t y = 0; y < N; ++y) out[y] = 0;
+    for (int t = 0; t < c->T; ++t) {
+        int m = c->zobs[t];
+        if (g) add_pauli(c, t, g[m] * c->zcoef[t], in, out);
+        else if (m == m_only) add_pauli(c, t, c->zcoef[t], in, out);
+    }
+}
+
 /* |psi> = U_{G-1} ... U_0 |0>, with the angles given per gate. */
 static void evolve(const or_circuit *c, const double *theta, cplx *psi)
 {
@@ -215,10 +254,28 @@ static void evolve(const or_circuit *c, const double *theta, cplx *psi)
     for (int g = 0; g < c->G; ++g) apply_gate(c, g, theta[g], 0, psi);
 }
 
-/* Eq. (qnn): <O_m> = <psi|O_m|psi>, all M from one evolved state (Sec. II-A). */
+/* Eq. (qnn): <O_m> = <psi|O_m|psi>, all M from one evolved state (Sec. II-A).
+ * scratch (2^n, used only with X/Y terms) receives O_m psi. */
+static void expvals_general(const or_circuit *c, const cplx *psi, double *E, cplx *scratch)
+{
+    uint64_t N = 1ull << c->n;
+    for (int m = 0; m < c->M; ++m) {
+        apply_observables(c, NULL, m, psi, scratch);
+        double s = 0.0;
+        for (uint64_t x = 0; x < N; ++x) s += creal(conj(psi[x]) * scratch[x]);
+        E[m] = s;
+    }
+}
+
 static void expvals(const or_circuit *c, const cplx *psi, double *E)
 {
     uint64_t N = 1ull << c->n;
+    if (has_xy(c)) {
+        cplx *scratch = malloc(sizeof(cplx) * N);
+        if (scratch) expvals_general(c, psi, E, scratch);
+        free(scratch);
+        return;
+    }
     for (int m = 0; m < c->M; ++m) {
         double s = 0.0;
         for (uint64_t x = 0; x < N; ++x) {
@@ -361,6 +418,9 @@ int oracle_adjoint(const or_circuit *c, int B, const double *gE, const double *x
                 const double *gEb = gE + (size_t)b * c->M;
                 oracle_angles(c, xb, w, theta);
                 evolve(c, theta, phi);
+                if (has_xy(c)) {
+                    apply_observables(c, gEb, -1, phi, lam);   /* lambda = (sum_m gE_m O_m) phi */
+                } else
                 for (uint64_t xx = 0; xx < N; ++xx) {
                     double d = 0.0;
                     for (int m = 0; m < c->M; ++m) d += gEb[m] * obs_diag(c, m, xx);
@@ -422,7 +482,9 @@ int oracle_jacobian(const or_circuit *c, int B, const double *x, const double *w
                 for (int m = 0; m < c->M; ++m) {
                     double *Jbm = J + ((size_t)b * c->M + m) * c->G;
                     memcpy(phi, psi, sizeof(cplx) * N);
-                    for (uint64_t xx = 0; xx < N; ++xx) lam[xx] = obs_diag(c, m, xx) * phi[xx];
+                    if (has_xy(c)) apply_observables(c, NULL, m, phi, lam);   /* lambda_m = O_m phi */
+                    else
+                        for (uint64_t xx = 0; xx < N; ++xx) lam[xx] = obs_diag(c, m, xx) * phi[xx];
                     for (int g = c->G - 1; g >= 0; --g) {
                         apply_gate(c, g, theta[g], 1, phi);
                         Jbm[g] = 0.0;

@@ -63,6 +63,16 @@ class Circuit:
         zobs = np.array([t[2] for t in self.terms], dtype=np.int32).reshape(T)
         return zmask, zcoef, zobs
 
+    def xmask_array(self):
+        """Per term, the qubits carrying X or Y (a term (zmask, coef, obs, xmask)
+        is the Pauli string with X on xmask & ~zmask, Y on xmask & zmask and Z
+        on zmask & ~xmask; three-element terms are Z strings)."""
+        return np.array([t[3] if len(t) > 3 else 0 for t in self.terms], dtype=np.uint64).reshape(len(self.terms))
+
+    @property
+    def has_xy(self) -> bool:
+        return any(len(t) > 3 and t[3] for t in self.terms)
+
     @property
     def n_gates(self) -> int:
         return len(self.gates)

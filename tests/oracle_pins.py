@@ -80,14 +80,20 @@ def dense_state(c, theta):
 
 
 def dense_observable(c, m):
-    Z = np.diag([1.0, -1.0]); I2 = np.eye(2)
-    O = np.zeros((1 << c.n, 1 << c.n))
-    for mask, coef, obs in c.terms:
+    """O_m from Kronecker products of 2x2 Pauli matrices (terms (zmask, coef,
+    obs[, xmask]): X where only xmask has the qubit, Y where both, Z where only
+    zmask)."""
+    X = PAULI[W.RX]; Y = PAULI[W.RY]; Z = PAULI[W.RZ]; I2 = np.eye(2, dtype=complex)
+    O = np.zeros((1 << c.n, 1 << c.n), dtype=complex)
+    for t in c.terms:
+        zmask, coef, obs = t[0], t[1], t[2]
+        xmask = t[3] if len(t) > 3 else 0
         if obs != m:
             continue
-        op = np.array([[1.0]])
+        op = np.array([[1.0 + 0j]])
         for q in reversed(range(c.n)):          # most significant factor first
-            op = np.kron(op, Z if (mask >> q) & 1 else I2)
+            zb, xb = (zmask >> q) & 1, (xmask >> q) & 1
+            op = np.kron(op, Y if (zb and xb) else X if xb else Z if zb else I2)
         O += coef * op
     return O
 
@@ -100,8 +106,9 @@ def angles_py(c, xb, w):
     return np.array(th)
 
 
-def rand_small_circuit(rng, n, G, n_obs=3, P=5, n_in=3, shared=True, extra=False):
-    """Random gate list over RX/RY/RZ/CZ/CNOT (extra: also H and RZZ)."""
+def rand_small_circuit(rng, n, G, n_obs=3, P=5, n_in=3, shared=True, extra=False, pauli=False):
+    """Random gate list over RX/RY/RZ/CZ/CNOT (extra: also H and RZZ); pauli:
+    observables are random X/Y/Z strings instead of Z strings."""
     gates = []
     for _ in range(G):
         r = rng.random()
@@ -125,7 +132,13 @@ def rand_small_circuit(rng, n, G, n_obs=3, P=5, n_in=3, shared=True, extra=False
     terms = []
     for m in range(n_obs):
         for _ in range(int(rng.integers(1, 4))):
-            terms.append((int(rng.integers(1, 1 << n)), float(rng.normal()), m))
+            if pauli:
+                zm = int(rng.integers(0, 1 << n)); xm = int(rng.integers(0, 1 << n))
+                if zm == 0 and xm == 0:
+                    xm = 1
+                terms.append((zm, float(rng.normal()), m, xm))
+            else:
+                terms.append((int(rng.integers(1, 1 << n)), float(rng.normal()), m))
     return W.Circuit(n=n, gates=gates, terms=terms, n_obs=n_obs, n_weights=P, n_inputs=n_in,
                      name="rand")
 
@@ -426,8 +439,61 @@ def pin_adjoint_equals_param_shift_h_rzz(O):
         close(gw_a, gw_p, 1e-12, "gw adjoint vs shift (H, RZZ)")
 
 
+def pin_pauli_closed_form(O):
+    """RY(t)|0>: <X> = sin t (d/dt cos t), <Y> = 0; RX(t)|0>: <Y> = -sin t;
+    Bell pair RY(pi/2), CNOT(0,1): <X0 X1> = 1, <Y0 Y1> = -1, <Z0 Z1> = 1."""
+    for t in (0.0, 0.3, 1.1, 2.5):
+        w = np.array([t])
+        for kind, terms, e, d in ((W.RY, [(0, 1.0, 0, 1)], np.sin(t), np.cos(t)),
+                                  (W.RY, [(1, 1.0, 0, 1)], 0.0, 0.0),
+                                  (W.RX, [(1, 1.0, 0, 1)], -np.sin(t), -np.cos(t))):
+            c = W.Circuit(n=1, gates=[(kind, 0, -1, 0, -1, 1.0)], terms=terms, n_obs=1, n_weights=1,
+                          n_inputs=0, name="pauli1")
+            x = np.zeros((1, 0))
+            close(O.forward(c, x, w)[0], [e], 1e-14, f"pauli E t={t}")
+            _, _, gw = O.adjoint(c, np.ones((1, 1)), x, w)
+            close(gw[0], [d], 1e-13, f"pauli grad t={t}")
+    c = W.Circuit(n=2, gates=[(W.RY, 0, -1, -1, -1, np.pi / 2), (W.CNOT, 0, 1, -1, -1, 1.0)],
+                  terms=[(0, 1.0, 0, 3), (3, 1.0, 1, 3), (3, 1.0, 2)], n_obs=3, n_weights=0, n_inputs=0,
+                  name="bellxy")
+    close(O.forward(c, np.zeros((1, 0)), np.zeros(0))[0], [1.0, -1.0, 1.0], 1e-14, "bell XX YY ZZ")
+
+
+def pin_pauli_dense(O, seeds=range(4)):
+    """Expectation values of random X/Y/Z strings on random circuits against
+    Kronecker-built dense observables, n = 1..6."""
+    for s in seeds:
+        rng = np.random.default_rng(1200 + s)
+        for n in range(1, 7):
+            c = rand_small_circuit(rng, n, G=int(rng.integers(2, 18)), extra=True, pauli=True)
+            x = rng.uniform(-np.pi, np.pi, size=(2, c.n_inputs)); w = rng.normal(size=c.n_weights)
+            for b in range(2):
+                ref = dense_state(c, angles_py(c, x[b], w))
+                Eref = [np.vdot(ref, dense_observable(c, m) @ ref) for m in range(c.n_obs)]
+                assert max(abs(np.imag(e)) for e in Eref) < 1e-12
+                close(O.forward(c, x[b:b + 1], w)[0], np.real(Eref), 1e-12, f"pauli E n={n} seed={s}")
+
+
+def pin_pauli_adjoint_equals_param_shift(O):
+    """Adjoint gradients (per gate, grad_x, grad_w) and the Jacobian equal the
+    exact parameter-shift rule with X/Y/Z-string observables."""
+    for s in range(3):
+        rng = np.random.default_rng(1300 + s)
+        c = rand_small_circuit(rng, 5, G=30, extra=True, pauli=True)
+        x = rng.uniform(-np.pi, np.pi, size=(2, c.n_inputs)); w = rng.normal(size=c.n_weights)
+        gE = rng.normal(size=(2, c.n_obs))
+        dth_a, gx_a, gw_a = O.adjoint(c, gE, x, w)
+        dth_p, gx_p, gw_p = O.param_shift(c, gE, x, w)
+        close(dth_a, dth_p, 1e-12, "pauli dtheta adjoint vs shift")
+        close(gx_a, gx_p, 1e-12, "pauli gx adjoint vs shift")
+        close(gw_a, gw_p, 1e-12, "pauli gw adjoint vs shift")
+        J = O.jacobian(c, x, w)
+        close(np.einsum("bm,bmg->bg", gE, J), dth_a, 1e-12, "pauli VJP = gE . J")
+
+
 ALL_PINS = [pin_single_rotation_closed_form, pin_bell, pin_dense_unitary, pin_norm,
             pin_product_state_bloch, pin_basis_state_cnot_chain, pin_trailing_diagonal,
             pin_finite_differences, pin_adjoint_equals_param_shift,
             pin_threads_and_partition, pin_h_rzz_closed_form, pin_dense_unitary_h_rzz,
-            pin_adjoint_equals_param_shift_h_rzz]
+            pin_adjoint_equals_param_shift_h_rzz, pin_pauli_closed_form, pin_pauli_dense,
+            pin_pauli_adjoint_equals_param_shift]

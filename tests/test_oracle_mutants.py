@@ -47,6 +47,11 @@ MUTANTS = {
     "rzz_derivative_sign": ("mu[x] *= -I * 0.5 * z * cexp(-I * 0.5 * t * z);",
                             "mu[x] *= I * 0.5 * z * cexp(-I * 0.5 * t * z);"),
     "hadamard_rows_swapped": ("cplx m[2][2] = {{r, r}, {r, -r}};", "cplx m[2][2] = {{r, -r}, {r, r}};"),
+    "pauli_y_phase_missing": ("for (int k = 0; k < (ny & 3); ++k) ph *= I;", ""),
+    "pauli_sign_on_output_index": ("double sg = (popcount64(x & zm) & 1) ? -1.0 : 1.0;",
+                                   "double sg = (popcount64(y & zm) & 1) ? -1.0 : 1.0;"),
+    "pauli_costate_unweighted": ("if (g) add_pauli(c, t, g[m] * c->zcoef[t], in, out);",
+                                 "if (g) add_pauli(c, t, c->zcoef[t], in, out);"),
 }
 
 

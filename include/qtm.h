@@ -94,6 +94,17 @@ typedef struct {
     int32_t reserved;   /* must be 0 */
 } qtm_zterm;
 
+/* One Pauli-string term (32 bytes): O_obs += coef * P with P = prod_q sigma_q,
+ * sigma_q = X where only xmask has bit q, Y where xmask and zmask both have
+ * it, Z where only zmask has it (identity elsewhere). */
+typedef struct {
+    uint64_t xmask;
+    uint64_t zmask;
+    double coef;
+    int32_t obs;
+    int32_t reserved;   /* must be 0 */
+} qtm_pauli_term;
+
 typedef struct qtm_plan qtm_plan;
 
 /* Static description of a plan's schedule (host-side; no GPU needed). */
@@ -131,6 +142,24 @@ typedef struct {
 qtm_status qtm_build(int n_qubits, const qtm_gate *gates, int n_gates,
                      const qtm_zterm *terms, int n_terms, int n_obs,
                      int n_weights, int n_inputs, int dtype, int path, qtm_plan **out);
+
+/*
+ * qtm_build_pauli: as qtm_build, with observables that are real combinations
+ * of Pauli strings (X, Y and Z terms; Sec. II-A's expectation values of
+ * general observables).  Terms are grouped by their X and Y qubits; each group
+ * is measured on its own plan of the circuit followed by the basis change
+ * V = RY(-pi/2) on X qubits and RX(pi/2) on Y qubits (V sigma V^dagger = Z),
+ * as a Z string on the term's support.  Expectation values, vector-Jacobian
+ * products and Jacobians are the sums over the groups (fixed group order, on
+ * the stream), so every entry point below applies; qtm_forward_noalloc returns
+ * QTM_EUNSUPPORTED for such plans.  With Z strings only this is qtm_build.
+ */
+qtm_status qtm_build_pauli(int n_qubits, const qtm_gate *gates, int n_gates,
+                           const qtm_pauli_term *terms, int n_terms, int n_obs,
+                           int n_weights, int n_inputs, int dtype, int path, qtm_plan **out);
+
+/* Number of measurement groups of a plan (1 unless built from X/Y terms). */
+int qtm_plan_parts(const qtm_plan *plan);
 
 /*
  * qtm_forward: expectation values, Eq. (qnn) for every sample of the batch

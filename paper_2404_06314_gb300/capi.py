@@ -38,6 +38,11 @@ class qtm_zterm(ctypes.Structure):
                 ("reserved", ctypes.c_int32)]
 
 
+class qtm_pauli_term(ctypes.Structure):
+    _fields_ = [("xmask", ctypes.c_uint64), ("zmask", ctypes.c_uint64), ("coef", ctypes.c_double),
+                ("obs", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
 class qtm_plan_info(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int32) for k in (
         "n_qubits", "dtype", "path", "tile_qubits", "fwd_passes", "adj_passes", "fwd_launches",
@@ -71,6 +76,9 @@ def lib(build_if_missing: bool = True):
         L = ctypes.CDLL(path)
         vp, i, P = ctypes.c_void_p, ctypes.c_int, ctypes.POINTER
         L.qtm_build.argtypes = [i, vp, i, vp, i, i, i, i, i, i, P(vp)]
+        L.qtm_build_pauli.argtypes = [i, vp, i, vp, i, i, i, i, i, i, P(vp)]
+        L.qtm_plan_parts.argtypes = [vp]
+        L.qtm_plan_parts.restype = ctypes.c_int
         L.qtm_forward.argtypes = [vp, i, vp, vp, vp, vp]
         L.qtm_adjoint.argtypes = [vp, i, vp, vp, vp, vp, vp, i, vp]
         L.qtm_jacobian.argtypes = [vp, i, vp, vp, vp, vp]
@@ -114,13 +122,34 @@ def _status_str(st: int) -> str:
 
 # ---- C-named wrappers (raw pointers) ---------------------------------------
 
+def _gate_array(gates):
+    G = (qtm_gate * max(len(gates), 1))()
+    for i, (k, q0, q1, wi, xi, c) in enumerate(gates):
+        G[i] = qtm_gate(int(k), int(q0), int(q1), int(wi), int(xi), 0, float(c))
+    return G
+
+
+def qtm_build_pauli(n_qubits, gates, terms, n_obs, n_weights, n_inputs, dtype=QTM_C64,
+                    path=QTM_PATH_AUTO):
+    """terms: (zmask, coef, obs[, xmask]) Pauli strings (X on xmask & ~zmask, Y
+    on xmask & zmask, Z on zmask & ~xmask).  Returns a plan handle."""
+    G = _gate_array(gates)
+    T = (qtm_pauli_term * max(len(terms), 1))()
+    for i, t in enumerate(terms):
+        T[i] = qtm_pauli_term(int(t[3]) if len(t) > 3 else 0, int(t[0]), float(t[1]), int(t[2]), 0)
+    h = ctypes.c_void_p()
+    st = lib().qtm_build_pauli(int(n_qubits), G, len(gates), T, len(terms), int(n_obs), int(n_weights),
+                               int(n_inputs), int(dtype), int(path), ctypes.byref(h))
+    if st != QTM_OK:
+        raise QtmError(st, "qtm_build_pauli")
+    return h.value
+
+
 def qtm_build(n_qubits, gates, terms, n_obs, n_weights, n_inputs, dtype=QTM_C64,
               path=QTM_PATH_AUTO):
     """gates: sequence of (kind, q0, q1, w_idx, x_idx, coef); terms: (zmask, coef, obs).
     Returns a plan handle (int).  Host-only: no GPU needed."""
-    G = (qtm_gate * max(len(gates), 1))()
-    for i, (k, q0, q1, wi, xi, c) in enumerate(gates):
-        G[i] = qtm_gate(int(k), int(q0), int(q1), int(wi), int(xi), 0, float(c))
+    G = _gate_array(gates)
     T = (qtm_zterm * max(len(terms), 1))()
     for i, (m, c, o) in enumerate(terms):
         T[i] = qtm_zterm(int(m), float(c), int(o), 0)
@@ -210,8 +239,9 @@ class Plan:
         self.circuit = circuit
         self.dtype = QTM_C128 if dtype in ("c128", "complex128") else QTM_C64
         self.path = {"auto": QTM_PATH_AUTO, "fused": QTM_PATH_FUSED, "naive": QTM_PATH_NAIVE}[path]
-        self.handle = qtm_build(circuit.n, circuit.gates, circuit.terms, circuit.n_obs,
-                                circuit.n_weights, circuit.n_inputs, self.dtype, self.path)
+        build = qtm_build_pauli if getattr(circuit, "has_xy", False) else qtm_build
+        self.handle = build(circuit.n, circuit.gates, circuit.terms, circuit.n_obs,
+                            circuit.n_weights, circuit.n_inputs, self.dtype, self.path)
 
     def __del__(self):
         h = getattr(self, "handle", None)
@@ -306,6 +336,11 @@ class Plan:
     @property
     def pairing(self) -> bool:
         return bool(lib().qtm_get_sample_pairing(self.handle))
+
+    @property
+    def parts(self) -> int:
+        """Measurement groups (1 unless the observables have X/Y terms)."""
+        return int(lib().qtm_plan_parts(self.handle))
 
     def compiled_passes(self) -> int:
         return int(lib().qtm_compiled_passes(self.handle))

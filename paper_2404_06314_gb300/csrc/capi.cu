@@ -3,6 +3,8 @@
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <cmath>
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
@@ -66,6 +68,11 @@ struct qtm_plan {
     std::vector<size_t> smem_fwd, smem_rev;
     std::vector<size_t> smem_fwd_x2, smem_rev_x2;   // paired-sample kernels (eligible plans)
     int pairing = 0;                   // general passes run two samples per CTA (k_pass_x2)
+    // Pauli-string observables (qtm_build_pauli): one Z-observable plan per
+    // group of terms sharing their X/Y qubits, outputs summed in part order
+    std::vector<qtm_plan *> parts;
+    void *d_tmp = nullptr;             // scratch for the parts' outputs
+    size_t tmp_bytes = 0;
     bool needs_lam = false;
     // stored forward
     bool fwd_valid = false;
@@ -480,6 +487,8 @@ NaiveArgs naive_args(qtm_plan *p, int B, const void *x, const void *w, const voi
 
 }  // namespace
 
+bool qtm_internal_is_composite(const qtm_plan *plan) { return plan && !plan->parts.empty(); }
+
 const qtm::Plan *qtm_internal_plan(const qtm_plan *plan) { return &plan->P; }
 
 extern "C" {
@@ -501,6 +510,168 @@ const char *qtm_status_str(int st)
 const char *qtm_version(void) { return "qtm 0.1 sm_103a"; }
 
 const char *qtm_last_error(const qtm_plan *plan) { return plan ? plan->err.c_str() : ""; }
+
+
+namespace {
+
+bool is_composite(const qtm_plan *p) { return !p->parts.empty(); }
+
+qtm_status part_fail(qtm_plan *p, qtm_plan *part, qtm_status st)
+{
+    return fail(p, st, part->err);
+}
+
+// device scratch of at least `bytes` for the parts' outputs
+qtm_status ensure_tmp(qtm_plan *p, size_t bytes)
+{
+    if (bytes <= p->tmp_bytes && p->d_tmp) return QTM_OK;
+    if (p->d_tmp) cudaFree(p->d_tmp);
+    p->d_tmp = nullptr;
+    p->tmp_bytes = 0;
+    cudaError_t e = cudaMalloc(&p->d_tmp, bytes ? bytes : 16);
+    if (e != cudaSuccess) return fail(p, QTM_ENOMEM, "composite scratch allocation failed");
+    p->tmp_bytes = bytes;
+    return QTM_OK;
+}
+
+}  // namespace
+
+qtm_status qtm_build_pauli(int n_qubits, const qtm_gate *gates, int n_gates, const qtm_pauli_term *terms,
+                           int n_terms, int n_obs, int n_weights, int n_inputs, int dtype, int path,
+                           qtm_plan **out)
+{
+    if (!out) return QTM_EINVAL;
+    *out = nullptr;
+    if (n_terms < 0 || (n_terms > 0 && !terms)) return QTM_EINVAL;
+    if (n_qubits < 1 || n_qubits > kMaxQubits) return QTM_EINVAL;
+    if (n_gates < 0 || (n_gates > 0 && !gates)) return QTM_EINVAL;
+    const uint64_t all = n_qubits >= 64 ? ~0ull : ((1ull << n_qubits) - 1ull);
+    for (int t = 0; t < n_terms; ++t) {
+        const qtm_pauli_term &T = terms[t];
+        if (T.reserved != 0 || (T.xmask & ~all) || (T.zmask & ~all) || T.obs < 0 || T.obs >= n_obs ||
+            !std::isfinite(T.coef))
+            return QTM_EINVAL;
+    }
+    // group by the basis change: X qubits (xmask & ~zmask) and Y qubits (xmask & zmask)
+    std::vector<std::pair<uint64_t, uint64_t>> keys;
+    std::vector<std::vector<qtm_zterm>> zterms;
+    for (int t = 0; t < n_terms; ++t) {
+        const qtm_pauli_term &T = terms[t];
+        const std::pair<uint64_t, uint64_t> key{T.xmask & ~T.zmask, T.xmask & T.zmask};
+        size_t g = 0;
+        while (g < keys.size() && keys[g] != key) ++g;
+        if (g == keys.size()) { keys.push_back(key); zterms.emplace_back(); }
+        // after the basis change the string is Z on its whole support
+        zterms[g].push_back(qtm_zterm{T.zmask | T.xmask, T.coef, T.obs, 0});
+    }
+    if (keys.empty()) { keys.push_back({0, 0}); zterms.emplace_back(); }
+    if (keys.size() == 1 && keys[0].first == 0 && keys[0].second == 0)   // Z strings only: an ordinary plan
+        return qtm_build(n_qubits, gates, n_gates, zterms[0].data(), (int)zterms[0].size(), n_obs, n_weights,
+                         n_inputs, dtype, path, out);
+    qtm_plan *p = new (std::nothrow) qtm_plan();
+    if (!p) return QTM_ENOMEM;
+    constexpr double kPi = 3.14159265358979323846264338327950288;
+    for (size_t g = 0; g < keys.size(); ++g) {
+        // V = RY(-pi/2) on X qubits (V X V^dagger = Z), RX(pi/2) on Y qubits (V Y V^dagger = Z)
+        std::vector<qtm_gate> gl(gates, gates + n_gates);
+        for (int q = 0; q < n_qubits; ++q) {
+            if ((keys[g].first >> q) & 1ull) gl.push_back({QTM_RY, q, -1, -1, -1, 0, -0.5 * kPi});
+            if ((keys[g].second >> q) & 1ull) gl.push_back({QTM_RX, q, -1, -1, -1, 0, 0.5 * kPi});
+        }
+        qtm_plan *part = nullptr;
+        qtm_status st = qtm_build(n_qubits, gl.data(), (int)gl.size(), zterms[g].data(), (int)zterms[g].size(),
+                                  n_obs, n_weights, n_inputs, dtype, path, &part);
+        if (st != QTM_OK) {
+            for (qtm_plan *q : p->parts) qtm_destroy(q);
+            p->parts.clear();
+            delete p;
+            return st;
+        }
+        p->parts.push_back(part);
+    }
+    p->P = p->parts[0]->P;            // shape fields (n, dtype, n_obs, n_weights, n_inputs, path)
+    p->P.n_user_gates = n_gates;      // Jacobian columns: the gates as given
+    *out = p;
+    return QTM_OK;
+}
+
+int qtm_plan_parts(const qtm_plan *p) { return p ? (p->parts.empty() ? 1 : (int)p->parts.size()) : 0; }
+
+namespace {
+
+qtm_status composite_forward(qtm_plan *p, int B, const void *x, const void *w, void *expvals, void *stream)
+{
+    const Plan &P = p->P;
+    const size_t n = (size_t)B * P.n_obs, es = elem_bytes(P.dtype) / 2;
+    if (p->parts.size() > 1) {
+        qtm_status st = ensure_tmp(p, n * es);
+        if (st != QTM_OK) return st;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    for (size_t i = 0; i < p->parts.size(); ++i) {
+        qtm_plan *part = p->parts[i];
+        qtm_status st = qtm_forward(part, B, x, w, i == 0 ? expvals : p->d_tmp, stream);
+        if (st != QTM_OK) return part_fail(p, part, st);
+        if (i > 0) {
+            cudaError_t e = launch_accumulate(P.dtype, p->d_tmp, expvals, n, s);
+            if (e != cudaSuccess) return cuda_fail(p, e, "composite accumulate");
+        }
+    }
+    return QTM_OK;
+}
+
+qtm_status composite_adjoint(qtm_plan *p, int B, const void *gE, const void *x, const void *w, void *gx, void *gw,
+                             int flags, void *stream)
+{
+    const Plan &P = p->P;
+    const size_t es = elem_bytes(P.dtype) / 2;
+    const size_t ngx = gx ? (size_t)B * P.n_inputs : 0;
+    const size_t ngw = gw ? ((flags & QTM_ADJ_GW_PER_SAMPLE) ? (size_t)B : 1) * P.n_weights : 0;
+    if (p->parts.size() > 1) {
+        qtm_status st = ensure_tmp(p, (ngx + ngw) * es + 256);
+        if (st != QTM_OK) return st;
+    }
+    char *tgx = static_cast<char *>(p->d_tmp);
+    char *tgw = tgx + ((ngx * es + 255) & ~size_t(255));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    for (size_t i = 0; i < p->parts.size(); ++i) {
+        qtm_plan *part = p->parts[i];
+        qtm_status st = qtm_adjoint(part, B, gE, x, w, gx ? (i == 0 ? gx : (void *)tgx) : nullptr,
+                                    gw ? (i == 0 ? gw : (void *)tgw) : nullptr, flags, stream);
+        if (st != QTM_OK) return part_fail(p, part, st);
+        if (i > 0) {
+            cudaError_t e = cudaSuccess;
+            if (gx) e = launch_accumulate(P.dtype, tgx, gx, ngx, s);
+            if (e == cudaSuccess && gw) e = launch_accumulate(P.dtype, tgw, gw, ngw, s);
+            if (e != cudaSuccess) return cuda_fail(p, e, "composite accumulate");
+        }
+    }
+    return QTM_OK;
+}
+
+qtm_status composite_jacobian(qtm_plan *p, int B, const void *x, const void *w, void *jac, void *stream)
+{
+    const Plan &P = p->P;
+    const size_t es = elem_bytes(P.dtype) / 2;
+    const int G = P.n_user_gates;
+    size_t need = 0;
+    for (qtm_plan *part : p->parts) need = std::max(need, (size_t)B * P.n_obs * (size_t)std::max(1, part->P.n_user_gates) * es);
+    qtm_status st = ensure_tmp(p, need);
+    if (st != QTM_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemsetAsync(jac, 0, es * (size_t)B * P.n_obs * (G > 0 ? G : 1), s);
+    if (e != cudaSuccess) return cuda_fail(p, e, "jacobian clear");
+    for (qtm_plan *part : p->parts) {
+        // a part's columns: the gates as given, then its basis-change rotations (dropped)
+        st = qtm_jacobian(part, B, x, w, p->d_tmp, stream);
+        if (st != QTM_OK) return part_fail(p, part, st);
+        e = launch_accumulate_cols(P.dtype, p->d_tmp, part->P.n_user_gates, jac, G, (size_t)B * P.n_obs, s);
+        if (e != cudaSuccess) return cuda_fail(p, e, "composite accumulate");
+    }
+    return QTM_OK;
+}
+
+}  // namespace
 
 qtm_status qtm_build(int n_qubits, const qtm_gate *gates, int n_gates, const qtm_zterm *terms,
                      int n_terms, int n_obs, int n_weights, int n_inputs, int dtype, int path,
@@ -574,6 +745,7 @@ qtm_status qtm_get_plan_info(const qtm_plan *p, qtm_plan_info *info)
 qtm_status qtm_forward(qtm_plan *p, int B, const void *x, const void *w, void *expvals, void *stream)
 {
     if (!p) return QTM_EINVAL;
+    if (is_composite(p)) return composite_forward(p, B, x, w, expvals, stream);
     const Plan &P = p->P;
     if (B < 1) return fail(p, QTM_EINVAL, "B must be >= 1");
     if ((P.n_inputs > 0 && !x) || (P.n_weights > 0 && !w) || !expvals)
@@ -608,6 +780,7 @@ qtm_status qtm_adjoint(qtm_plan *p, int B, const void *gE, const void *x, const 
                        void *gw, int flags, void *stream)
 {
     if (!p) return QTM_EINVAL;
+    if (is_composite(p)) return composite_adjoint(p, B, gE, x, w, gx, gw, flags, stream);
     const Plan &P = p->P;
     if (B < 1) return fail(p, QTM_EINVAL, "B must be >= 1");
     if (!gE || (P.n_inputs > 0 && !x) || (P.n_weights > 0 && !w))
@@ -672,6 +845,7 @@ qtm_status qtm_adjoint(qtm_plan *p, int B, const void *gE, const void *x, const 
 qtm_status qtm_jacobian(qtm_plan *p, int B, const void *x, const void *w, void *jac, void *stream)
 {
     if (!p) return QTM_EINVAL;
+    if (is_composite(p)) return composite_jacobian(p, B, x, w, jac, stream);
     const Plan &P = p->P;
     if (B < 1) return fail(p, QTM_EINVAL, "B must be >= 1");
     if ((P.n_inputs > 0 && !x) || (P.n_weights > 0 && !w) || !jac) return fail(p, QTM_EINVAL, "null pointer");
@@ -764,6 +938,14 @@ qtm_status compile_all(qtm_plan *p, JitMode mode, std::vector<std::vector<char>>
 qtm_status qtm_set_sample_pairing(qtm_plan *p, int on)
 {
     if (!p) return QTM_EINVAL;
+    if (is_composite(p)) {
+        for (qtm_plan *part : p->parts) {
+            qtm_status st = qtm_set_sample_pairing(part, on);
+            if (st != QTM_OK) return part_fail(p, part, st);
+        }
+        p->pairing = on;
+        return QTM_OK;
+    }
     if (on != 0 && on != 1) return fail(p, QTM_EINVAL, "on must be 0 or 1");
     if (on && !pairable(p->P)) return fail(p, QTM_EUNSUPPORTED, "pairing needs a fused complex64 plan with tiles of >= 9 qubits");
     if (on) {
@@ -789,6 +971,13 @@ int qtm_get_sample_pairing(const qtm_plan *p) { return p ? p->pairing : 0; }
 qtm_status qtm_compile(qtm_plan *p, int flags)
 {
     if (!p) return QTM_EINVAL;
+    if (is_composite(p)) {
+        for (qtm_plan *part : p->parts) {
+            qtm_status st = qtm_compile(part, flags);
+            if (st != QTM_OK) return part_fail(p, part, st);
+        }
+        return QTM_OK;
+    }
     if (flags != 0 && flags != QTM_COMPILE_SCALAR && flags != QTM_COMPILE_SAMPLE_PAIRS)
         return fail(p, QTM_EINVAL, "unknown flags");
     if (!jit_available()) return fail(p, QTM_EUNSUPPORTED, "NVRTC or driver entry points not available");
@@ -843,6 +1032,11 @@ qtm_status qtm_compile(qtm_plan *p, int flags)
 int qtm_compiled_passes(const qtm_plan *p)
 {
     if (!p) return 0;
+    if (is_composite(p)) {
+        int n = 0;
+        for (const qtm_plan *part : p->parts) n += qtm_compiled_passes(part);
+        return n;
+    }
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev != p->jit_device) {
         cudaGetLastError();
@@ -879,6 +1073,13 @@ qtm_status qtm_debug_jit_compile(qtm_plan *p, int flags)
 qtm_status qtm_sync(qtm_plan *p, void *stream)
 {
     if (!p) return QTM_EINVAL;
+    if (is_composite(p)) {
+        for (qtm_plan *part : p->parts) {
+            qtm_status st = qtm_sync(part, stream);
+            if (st != QTM_OK) return part_fail(p, part, st);
+        }
+        return QTM_OK;
+    }
     cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(p, e, "stream synchronize");
     if (!p->d_status) return QTM_OK;
@@ -918,6 +1119,10 @@ qtm_status qtm_get_launch_times(qtm_plan *p, int which, float *ms, int *kinds, i
 qtm_status qtm_destroy(qtm_plan *p)
 {
     if (!p) return QTM_EINVAL;
+    for (qtm_plan *part : p->parts) qtm_destroy(part);
+    p->parts.clear();
+    if (p->d_tmp) cudaFree(p->d_tmp);
+    p->d_tmp = nullptr;
     for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
     for (auto *v : {&p->jit_fwd, &p->jit_rev})
         for (auto &k : *v) jit_unload(k);
@@ -946,6 +1151,22 @@ qtm_status qtm_debug_emulate(const qtm_plan *p, int B, const double *x, const do
                              const double *gE, double *E, double *gx, double *gw)
 {
     if (!p || B < 1) return QTM_EINVAL;
+    if (is_composite(p)) {   // sum of the parts, in part order
+        const Plan &P = p->P;
+        std::vector<double> e((size_t)B * P.n_obs), a((size_t)B * P.n_inputs), b((size_t)B * P.n_weights);
+        if (E) std::fill(E, E + e.size(), 0.0);
+        if (gx) std::fill(gx, gx + a.size(), 0.0);
+        if (gw) std::fill(gw, gw + b.size(), 0.0);
+        for (const qtm_plan *part : p->parts) {
+            qtm_status st = qtm_debug_emulate(part, B, x, w, gE, E ? e.data() : nullptr, gx ? a.data() : nullptr,
+                                              gw ? b.data() : nullptr);
+            if (st != QTM_OK) { const_cast<qtm_plan *>(p)->err = part->err; return st; }
+            for (size_t i = 0; E && i < e.size(); ++i) E[i] += e[i];
+            for (size_t i = 0; gx && i < a.size(); ++i) gx[i] += a[i];
+            for (size_t i = 0; gw && i < b.size(); ++i) gw[i] += b[i];
+        }
+        return QTM_OK;
+    }
     std::string err;
     qtm_status st = emulate_plan(p->P, B, x, w, gE, E, gx, gw, err);
     if (st != QTM_OK) const_cast<qtm_plan *>(p)->err = err;

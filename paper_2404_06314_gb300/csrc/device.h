@@ -56,6 +56,10 @@ cudaError_t launch_grad_finalize(int dtype, const FinalizeArgs &f, cudaStream_t 
 cudaError_t launch_gw_reduce(int dtype, const double *gw_ws, int B, int P, void *gw,
                              cudaStream_t s);
 
+// composite plans: dst[i] += src[i]; dst[r][g] += src[r][g] for g < Gd
+cudaError_t launch_accumulate(int dtype, const void *src, void *dst, size_t n, cudaStream_t s);
+cudaError_t launch_accumulate_cols(int dtype, const void *src, int Gs, void *dst, int Gd, size_t rows, cudaStream_t s);
+
 cudaError_t launch_onehot(int dtype, void *gE, int B, int M, int m, cudaStream_t s);
 cudaError_t launch_jac_scatter(int dtype, const double *abar, const int32_t *gate_of_rot, int n_rots, int B,
                                int M, int m, int G, void *J, cudaStream_t s);

@@ -10,6 +10,7 @@
 // to the state phi and the costate lam and accumulates v = Im<lam|sigma phi>
 // per run (Sec. II-A adjoint method).  Partial sums per tile are written to
 // global memory and reduced in fixed order by the finalize kernels.
+#include <algorithm>
 #include <cstdint>
 
 #include "device.h"
@@ -81,6 +82,25 @@ __global__ void k_grad_finalize(const FinalizeArgs f)
 
 // grad_w[j] = sum_b gw_ws[b][j]: one CTA per weight, each thread a fixed
 // strided subset of samples, then a fixed-shape tree: deterministic.
+// dst[i] += src[i] (composite plans: sum of the parts' outputs, part order)
+template <typename R>
+__global__ void k_accumulate(const R *src, R *dst, size_t n)
+{
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        dst[i] += src[i];
+}
+
+// dst[r][g] += src[r][g] for g < Gd (src rows have Gs >= Gd columns)
+template <typename R>
+__global__ void k_accumulate_cols(const R *src, int Gs, R *dst, int Gd, size_t rows)
+{
+    const size_t n = rows * (size_t)Gd;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t r = i / Gd, g = i % Gd;
+        dst[i] += src[r * Gs + g];
+    }
+}
+
 template <typename R>
 __global__ void k_gw_reduce(const double *gw_ws, int B, int P, R *gw)
 {
@@ -214,6 +234,30 @@ cudaError_t launch_grad_finalize(int dtype, const FinalizeArgs &f, cudaStream_t 
 {
     if (dtype == QTM_C128) k_grad_finalize<double><<<f.B, 256, 0, s>>>(f);
     else k_grad_finalize<float><<<f.B, 256, 0, s>>>(f);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_accumulate(int dtype, const void *src, void *dst, size_t n, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    const unsigned grid = (unsigned)std::min<size_t>((n + 255) / 256, 1216);
+    if (dtype == QTM_C128)
+        k_accumulate<double><<<grid, 256, 0, s>>>(static_cast<const double *>(src), static_cast<double *>(dst), n);
+    else
+        k_accumulate<float><<<grid, 256, 0, s>>>(static_cast<const float *>(src), static_cast<float *>(dst), n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_accumulate_cols(int dtype, const void *src, int Gs, void *dst, int Gd, size_t rows, cudaStream_t s)
+{
+    if (rows == 0 || Gd <= 0) return cudaSuccess;
+    const unsigned grid = (unsigned)std::min<size_t>((rows * Gd + 255) / 256, 1216);
+    if (dtype == QTM_C128)
+        k_accumulate_cols<double><<<grid, 256, 0, s>>>(static_cast<const double *>(src), Gs,
+                                                        static_cast<double *>(dst), Gd, rows);
+    else
+        k_accumulate_cols<float><<<grid, 256, 0, s>>>(static_cast<const float *>(src), Gs,
+                                                       static_cast<float *>(dst), Gd, rows);
     return cudaGetLastError();
 }
 

@@ -62,11 +62,13 @@ struct Carve {
 // Host-side description of the plan, reachable without the plan's own device
 // tables (defined in capi.cu).
 const qtm::Plan *qtm_internal_plan(const qtm_plan *plan);
+bool qtm_internal_is_composite(const qtm_plan *plan);
 
 extern "C" qtm_status qtm_forward_noalloc(qtm_plan *plan, int B, const void *x, const void *w,
                                           void *expvals, void *stream)
 {
     if (!plan) return QTM_EINVAL;
+    if (qtm_internal_is_composite(plan)) return QTM_EUNSUPPORTED;   // Pauli-string observables: several plans
     const Plan &P = *qtm_internal_plan(plan);
     if (B < 1) return QTM_EINVAL;
     if ((P.n_inputs > 0 && !x) || (P.n_weights > 0 && !w) || !expvals) return QTM_EINVAL;

@@ -664,7 +664,8 @@ qtm_status make_plan(int n, const qtm_gate *gates, int n_gates, const qtm_zterm 
             std::vector<MaskTerm> t;
             int nl, nq;
             uint32_t dl;
-            if (!closed_form(P.prefix_ents, pd.analytic_ents, P.n, t, nl, nq, dl)) continue;
+            // over all state qubits: those above n (padding when n < 4) keep identity rows
+            if (!closed_form(P.prefix_ents, pd.analytic_ents, P.state_qubits, t, nl, nq, dl)) continue;
             pd.amap_begin = (int)P.amap_terms.size();
             pd.amap_lin = nl;
             pd.amap_quad = nq;

@@ -150,3 +150,48 @@ def test_no_gpu_fails_loudly():
     st = capi.qtm_forward(plan.handle, 2, fake, fake, fake, None)
     assert st == capi.QTM_ECUDA
     assert "CUDA" in capi.qtm_last_error(plan.handle) or "device" in capi.qtm_last_error(plan.handle)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3])
+def test_closed_form_prefix_keeps_padding_qubits(n):
+    """Circuits below 4 qubits are padded to a 4-qubit state; the closed form
+    of a folded CNOT/CZ prefix must leave the padding bits untouched (a
+    regression: x = A^-1 y once dropped them and doubled the norm)."""
+    if n == 1:
+        gates = [(W.RY, 0, -1, 0, -1, 1.0)]
+    else:
+        top = n - 1
+        gates = [(W.RZ, top, -1, 1, -1, 0.8), (W.RY, top, -1, 0, -1, 1.1), (W.CNOT, top, 0, -1, -1, 1.0)]
+        gates += [(W.CZ, q, q + 1, -1, -1, 1.0) for q in range(n - 1)]
+    c = W.Circuit(n=n, gates=gates, terms=[(0, 1.0, 0), (1, 1.0, 1), ((1 << n) - 1, 0.7, 1)], n_obs=2,
+                  n_weights=2, n_inputs=0, name=f"pad{n}")
+    _emulate_vs_oracle(c, 2, 3)
+
+
+# ---- Pauli-string observables (qtm_build_pauli): one Z plan per X/Y group ----
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 6, 9, 12, 13, 14])
+def test_pauli_observables_schedule_matches_oracle(n):
+    """Sum over the measurement groups (circuit + basis change, Z strings),
+    interpreted on the host, against the oracle's direct Pauli strings."""
+    rng = np.random.default_rng(3200 + n)
+    c = P.rand_small_circuit(rng, n, G=5 * n + 8, n_obs=3, extra=True, pauli=True)
+    c.name = f"pauli{n}"
+    plan = capi.Plan(c)
+    assert plan.parts >= 1
+    _emulate_vs_oracle(c, 2, n)
+
+
+def test_pauli_build_validates_and_groups():
+    X, Y = 1, 1   # xmask bit for qubit 0
+    gates = [(W.RY, 0, -1, 0, -1, 1.0)]
+    # Z only: an ordinary plan (one part)
+    assert capi.Plan(W.Circuit(n=2, gates=gates, terms=[(1, 1.0, 0)], n_obs=1, n_weights=1, n_inputs=0,
+                               name="z")).parts == 1
+    # X0, Y0, X0 X1, Z1: groups {X0}, {Y0}, {X0 X1}, {} -> 4 parts
+    c = W.Circuit(n=2, gates=gates, terms=[(0, 1.0, 0, 1), (1, 1.0, 0, 1), (0, 0.5, 0, 3), (2, 1.0, 0)],
+                  n_obs=1, n_weights=1, n_inputs=0, name="g")
+    assert capi.Plan(c).parts == 4
+    bad = [(0, 1.0, 0, 4)]    # xmask beyond n
+    with pytest.raises(capi.QtmError):
+        capi.Plan(W.Circuit(n=2, gates=gates, terms=bad, n_obs=1, n_weights=1, n_inputs=0, name="b"))

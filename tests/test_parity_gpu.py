@@ -251,3 +251,33 @@ def test_h_rzz_jacobian_columns():
     assert_close(J.cpu().numpy(), Jo, 1e-11, "jacobian with H and RZZ")
     no_angle = [g for g, gt in enumerate(c.gates) if gt[0] in (W.H, W.CZ, W.CNOT)]
     assert np.all(J.cpu().numpy()[:, :, no_angle] == 0)
+
+
+# ---- Pauli-string observables (composite plans) --------------------------------------
+
+@pytest.mark.parametrize("n", [3, 6, 12, 14])
+def test_pauli_observables_match_oracle(n):
+    rng = np.random.default_rng(3300 + n)
+    c = P.rand_small_circuit(rng, n, G=5 * n + 8, n_obs=3, extra=True, pauli=True)
+    c.name = f"pauli{n}"
+    check(c, 3, "c64")
+    check(c, 2, "c128", tol=1e-11)
+
+
+def test_pauli_jacobian_and_compiled():
+    import torch
+    rng = np.random.default_rng(3401)
+    c = P.rand_small_circuit(rng, 10, G=50, n_obs=2, extra=True, pauli=True)
+    inp = W.make_inputs(c, 3, 5, real_dtype=np.float64)
+    plan = capi.Plan(c, dtype="c128")
+    J = plan.jacobian(torch.tensor(inp.x, device="cuda"), torch.tensor(inp.w, device="cuda"))
+    plan.sync()
+    assert_close(J.cpu().numpy(), oracle.jacobian(c, inp.x, inp.w, threads=0), 1e-11, "pauli jacobian")
+    inp32 = W.make_inputs(c, 3, 6, real_dtype=np.float32)
+    plan32 = capi.Plan(c, dtype="c64").compile()
+    assert plan32.compiled_passes() > 0
+    E, gx, gw = run_gpu(c, inp32, plan=plan32)
+    Eo, gxo, gwo = oracle_ref(c, inp32)
+    assert_close(E, Eo, 1e-5, "pauli compiled E")
+    assert_close(gx, gxo, 1e-5, "pauli compiled gx")
+    assert_close(gw, gwo, 1e-5, "pauli compiled gw")

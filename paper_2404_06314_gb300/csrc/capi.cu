@@ -242,7 +242,7 @@ qtm_status ensure_device(qtm_plan *p)
     UP(p->d_runs, P.runs);
     UP(p->d_rots, P.rots);
     UP(p->d_prefix_run_of_q, P.prefix_run_of_q);
-    UP(p->d_prefix_ents, P.prefix_ents);
+    UP(p->d_prefix_ents, P.pass_ents);   // per-pass entangler subsets (ents_begin offsets)
     UP(p->d_terms, P.terms);
     UP(p->d_w_ptr, P.w_ptr);
     UP(p->d_w_rots, P.w_rots);
@@ -415,7 +415,7 @@ PassArgs pass_args(qtm_plan *p, const PassDesc &pd, const TmGeom &g, size_t smem
     a.slot_runs = p->d_slot_runs; a.slot_begin = pd.slot_begin; a.nslots = pd.slot_end - pd.slot_begin;
     a.n_runs = (int)P.runs.size();
     a.mats = p->d_mats; a.tabs = p->d_tabs;
-    a.prefix_ents = p->d_prefix_ents;
+    a.prefix_ents = p->d_prefix_ents + pd.ents_begin;
     a.analytic_ents = pd.phi_src == SRC_ANALYTIC ? pd.analytic_ents : 0;
     a.amap = p->d_amap + (pd.amap_lin >= 0 ? pd.amap_begin : 0);
     a.amap_lin = pd.phi_src == SRC_ANALYTIC ? pd.amap_lin : -1;

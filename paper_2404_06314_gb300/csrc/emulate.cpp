@@ -119,7 +119,7 @@ struct Emu {
             sign = par & 1;
         } else {
             for (int k = pd.analytic_ents - 1; k >= 0; --k) {
-                const Ent &e = P.prefix_ents[k];
+                const Ent &e = P.pass_ents[pd.ents_begin + k];
                 if (e.kind == QTM_CNOT) xx ^= ((xx >> e.a) & 1ull) << e.b;
                 else sign ^= (int)((xx >> e.a) & (xx >> e.b) & 1ull);
             }

@@ -89,7 +89,7 @@ __device__ __forceinline__ TileJob make_job(const MultiArgs &m, const CircDev &c
     j.nslots = pd.slot_end - pd.slot_begin;
     j.mats = static_cast<const Cx<R> *>(m.mats) + cd.mats_off + (size_t)b * cd.n_runs * 4;
     j.tabs = static_cast<const Cx<R> *>(m.tabs) + cd.tabs_off + (size_t)b * ((cd.sq + 3) >> 2) * 16;
-    j.prefix_ents = m.ents + cd.ents_off;
+    j.prefix_ents = m.ents + cd.ents_off + pd.ents_begin;
     j.analytic_ents = pd.phi_src == SRC_ANALYTIC ? pd.analytic_ents : 0;
     j.amap = m.amap + cd.amap_off + (pd.amap_lin >= 0 ? pd.amap_begin : 0);
     j.amap_lin = pd.phi_src == SRC_ANALYTIC ? pd.amap_lin : -1;
@@ -431,7 +431,7 @@ qtm_status plan_all(qtm_multi *m)
         APPEND(runs_off, m->runs, P.runs);
         APPEND(rots_off, m->rots, P.rots);
         APPEND(prq_off, m->prq, P.prefix_run_of_q);
-        APPEND(ents_off, m->ents, P.prefix_ents);
+        APPEND(ents_off, m->ents, P.pass_ents);
         APPEND(terms_off, m->tms, P.terms);
         APPEND(amap_off, m->amap, P.amap_terms);
         APPEND(wptr_off, m->wptr, P.w_ptr);

@@ -88,7 +88,7 @@ extern "C" qtm_status qtm_forward_noalloc(qtm_plan *plan, int B, const void *x, 
     const size_t o_runs = c.take(sizeof(Run) * P.runs.size());
     const size_t o_rots = c.take(sizeof(Rot) * P.rots.size());
     const size_t o_prq = c.take(sizeof(int32_t) * P.prefix_run_of_q.size());
-    const size_t o_ents = c.take(sizeof(Ent) * P.prefix_ents.size());
+    const size_t o_ents = c.take(sizeof(Ent) * P.pass_ents.size());
     const size_t o_terms = c.take(sizeof(Term) * P.terms.size());
     const size_t o_amap = c.take(sizeof(MaskTerm) * P.amap_terms.size());
     const size_t o_status = c.take(sizeof(unsigned));
@@ -114,7 +114,7 @@ extern "C" qtm_status qtm_forward_noalloc(qtm_plan *plan, int B, const void *x, 
     put(o_runs, P.runs.data(), sizeof(Run) * P.runs.size());
     put(o_rots, P.rots.data(), sizeof(Rot) * P.rots.size());
     put(o_prq, P.prefix_run_of_q.data(), sizeof(int32_t) * P.prefix_run_of_q.size());
-    put(o_ents, P.prefix_ents.data(), sizeof(Ent) * P.prefix_ents.size());
+    put(o_ents, P.pass_ents.data(), sizeof(Ent) * P.pass_ents.size());
     put(o_terms, P.terms.data(), sizeof(Term) * P.terms.size());
     put(o_amap, P.amap_terms.data(), sizeof(MaskTerm) * P.amap_terms.size());
     if (e == cudaSuccess) e = cudaMemsetAsync(sb + o_status, 0, sizeof(unsigned), s);   // starts at zero
@@ -143,7 +143,7 @@ extern "C" qtm_status qtm_forward_noalloc(qtm_plan *plan, int B, const void *x, 
     a.slot_begin = pd.slot_begin; a.nslots = pd.slot_end - pd.slot_begin;
     a.n_runs = (int)P.runs.size();
     a.mats = sb + o_mats; a.tabs = sb + o_tabs;
-    a.prefix_ents = reinterpret_cast<const Ent *>(sb + o_ents);
+    a.prefix_ents = reinterpret_cast<const Ent *>(sb + o_ents) + pd.ents_begin;
     a.analytic_ents = pd.analytic_ents;
     a.amap = reinterpret_cast<const MaskTerm *>(sb + o_amap) + (pd.amap_lin >= 0 ? pd.amap_begin : 0);
     a.amap_lin = pd.amap_lin; a.amap_quad = pd.amap_quad; a.amap_dlin = pd.amap_dlin;

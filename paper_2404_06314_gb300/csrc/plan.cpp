@@ -226,8 +226,10 @@ struct Builder {
     }
 
     // Greedy sweep selection over the nodes [begin, end) of `nodes` not done.
+    // pass_nodes (optional) receives each emitted pass's node list.
     void schedule_stage(const std::vector<Node> &nodes, int begin, int end, int K, bool reverse,
-                        const std::vector<int> &last_touch, std::vector<PassDesc> &out)
+                        const std::vector<int> &last_touch, std::vector<PassDesc> &out,
+                        std::vector<std::vector<int>> *pass_nodes = nullptr)
     {
         const int N = (int)nodes.size();
         const int n = P.n;
@@ -242,6 +244,7 @@ struct Builder {
             if (!all.empty() || out.empty()) {
                 // emit in a topological order that the phase greedy will refine
                 out.push_back(emit_pass(nodes, all, S, K, reverse, last_touch));
+                if (pass_nodes) pass_nodes->push_back(all);
             }
             return;
         }
@@ -263,6 +266,7 @@ struct Builder {
             }
             if (best.empty()) break;
             out.push_back(emit_pass(nodes, best, bestS, K, reverse, last_touch));
+            if (pass_nodes) pass_nodes->push_back(best);
             for (int i : best) done[i] = 1;
             remaining -= (int)best.size();
         }
@@ -538,6 +542,7 @@ qtm_status make_plan(int n, const qtm_gate *gates, int n_gates, const qtm_zterm 
     P.K = (P.state_qubits <= smem_limit) ? P.state_qubits : Kmax;
     P.tiles_per_sample = 1 << (P.state_qubits - P.K);
 
+    P.pass_ents = P.prefix_ents;   // [0, |prefix_ents|): the forward's analytic state
     Builder bld(P);
     // forward
     build_deps(fwd_nodes, P.runs, n);
@@ -583,15 +588,23 @@ qtm_status make_plan(int n, const qtm_gate *gates, int n_gates, const qtm_zterm 
     } else {
         bld.schedule_stage(rev_nodes, 0, n_main, P.K, true, last_touch, P.rev);
         size_t first_prefix_pass = P.rev.size();
-        bld.schedule_stage(rev_nodes, n_main, (int)rev_nodes.size(), P.K, true, last_touch, P.rev);
-        // analytic phi for prefix-only passes: count folded entanglers still applied
-        int ents_left = (int)P.prefix_ents.size();
+        std::vector<std::vector<int>> prefix_pass_nodes;
+        bld.schedule_stage(rev_nodes, n_main, (int)rev_nodes.size(), P.K, true, last_touch, P.rev,
+                           &prefix_pass_nodes);
+        // analytic phi for prefix-only passes: the folded entanglers not undone
+        // by an earlier pass, in circuit order.  rev node n_main + k undoes
+        // prefix entangler |prefix_ents| - 1 - k.
+        const int ne = (int)P.prefix_ents.size();
+        std::vector<char> undone(ne, 0);
         for (size_t i = first_prefix_pass; i < P.rev.size(); ++i) {
-            P.rev[i].phi_src = SRC_ANALYTIC;
-            P.rev[i].analytic_ents = ents_left;
-            for (int ph = P.rev[i].phase_begin; ph < P.rev[i].phase_end; ++ph)
-                for (int o = P.phases[ph].op_begin; o < P.phases[ph].op_end; ++o)
-                    if (P.ops[o].type == OP_CZ || P.ops[o].type == OP_CNOT) --ents_left;
+            PassDesc &pd = P.rev[i];
+            pd.phi_src = SRC_ANALYTIC;
+            pd.ents_begin = (int)P.pass_ents.size();
+            for (int k = 0; k < ne; ++k)
+                if (!undone[k]) P.pass_ents.push_back(P.prefix_ents[k]);
+            pd.analytic_ents = (int)P.pass_ents.size() - pd.ents_begin;
+            for (int node : prefix_pass_nodes[i - first_prefix_pass])
+                if (rev_nodes[node].type == 1) undone[ne - 1 - (node - n_main)] = 1;
         }
         if (P.rev.empty()) {
             P.rev.push_back(bld.emit_pass(rev_nodes, {}, TileSet{P.K, P.K, 0}, P.K, true, last_touch));
@@ -604,6 +617,7 @@ qtm_status make_plan(int n, const qtm_gate *gates, int n_gates, const qtm_zterm 
         PassDesc &pd = P.fwd[i];
         pd.phi_src = (i == 0) ? SRC_ANALYTIC : SRC_LOAD;
         pd.analytic_ents = (int)P.prefix_ents.size();
+        pd.ents_begin = 0;
         pd.lam_src = SRC_NONE;
         pd.store_phi = 1;
         pd.store_lam = 0;
@@ -665,7 +679,9 @@ qtm_status make_plan(int n, const qtm_gate *gates, int n_gates, const qtm_zterm 
             int nl, nq;
             uint32_t dl;
             // over all state qubits: those above n (padding when n < 4) keep identity rows
-            if (!closed_form(P.prefix_ents, pd.analytic_ents, P.state_qubits, t, nl, nq, dl)) continue;
+            const std::vector<Ent> sub(P.pass_ents.begin() + pd.ents_begin,
+                                       P.pass_ents.begin() + pd.ents_begin + pd.analytic_ents);
+            if (!closed_form(sub, pd.analytic_ents, P.state_qubits, t, nl, nq, dl)) continue;
             pd.amap_begin = (int)P.amap_terms.size();
             pd.amap_lin = nl;
             pd.amap_quad = nq;

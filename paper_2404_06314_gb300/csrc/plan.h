@@ -24,6 +24,11 @@ struct Plan {
     std::vector<Rot> rots;
     std::vector<int32_t> prefix_run_of_q;   // [n] run id or -1
     std::vector<Ent> prefix_ents;           // folded CZ/CNOT, in circuit order
+    // per analytic pass, the folded entanglers still applied (circuit order):
+    // [0, |prefix_ents|) is the forward's full list; reverse prefix passes append
+    // the subset not yet undone (undone ones may leave out of list order when
+    // they commute, so a pass's subset is not a list prefix in general)
+    std::vector<Ent> pass_ents;
     std::vector<int32_t> rot_of_gate;       // [G] rotation id or -1
 
     // chain rule: CSR over weights and inputs -> rotation ids

@@ -85,6 +85,7 @@ struct PassDesc {
     int32_t phi_src;            // SRC_LOAD / SRC_ANALYTIC
     int32_t lam_src;            // reverse only: SRC_COSTATE (first pass) / SRC_LOAD
     int32_t analytic_ents;      // prefix entanglers still applied to the analytic phi
+    int32_t ents_begin;         // ... listed (circuit order) at plan.pass_ents[ents_begin ..)
     int32_t store_phi, store_lam;
     int32_t phase_begin, phase_end;
     int32_t slot_begin, slot_end;   // pass-local run slots -> run ids (plan.slot_runs)

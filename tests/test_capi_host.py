@@ -195,3 +195,20 @@ def test_pauli_build_validates_and_groups():
     bad = [(0, 1.0, 0, 4)]    # xmask beyond n
     with pytest.raises(capi.QtmError):
         capi.Plan(W.Circuit(n=2, gates=gates, terms=bad, n_obs=1, n_weights=1, n_inputs=0, name="b"))
+
+
+def test_prefix_entanglers_undone_out_of_order():
+    """Reverse passes that regenerate phi analytically use the folded
+    entanglers not yet undone; the scheduler may undo commuting ones out of
+    list order (a regression: the count-based prefix once applied the wrong
+    entangler).  Minimal 16-qubit case: RZZ(5,7) folds CNOT(5,7); CNOT(6,15)
+    and CNOT(1,11) follow; the tiles undo them in another order."""
+    gates = [(W.RZZ, 5, 7, 0, 1, 1.4243), (W.RY, 6, -1, 1, 2, 1.3828), (W.CNOT, 6, 15, -1, -1, 1.0),
+             (W.CNOT, 1, 11, -1, -1, 1.0), (W.RX, 12, -1, 3, -1, 1.4519), (W.RX, 9, -1, 0, 0, 1.4464)]
+    c = W.Circuit(n=16, gates=gates, terms=[(1 << 6, 1.0, 0), ((1 << 15) | (1 << 7), 0.5, 1), (1 << 12, 1.0, 2)],
+                  n_obs=3, n_weights=4, n_inputs=3, name="undo_order")
+    _emulate_vs_oracle(c, 2, 5)
+    rng = np.random.default_rng(816)
+    c2 = P.rand_small_circuit(rng, 16, G=90, n_obs=3, extra=True)
+    c2.name = "hrzz16"
+    _emulate_vs_oracle(c2, 2, 7)

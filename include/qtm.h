@@ -274,7 +274,9 @@ typedef struct {
     int32_t ctas_per_sm;   /* persistent grid = ctas_per_sm x SM count (capped by the work) */
     int32_t order;         /* 0: costliest (circuit, sample) items first; 1: as given */
     int32_t fuse_width;    /* most rotations fused into one run (1 .. 32) */
-    int32_t reserved;
+    int32_t split;         /* 0: one CTA runs a whole item; 1 (default): items of n > 12
+                            * qubits are split into one task per (pass, tile), spread over
+                            * CTAs; a task waits (bounded) for its item's previous pass */
 } qtm_multi_config;
 
 /* Build plans for n_circuits circuits (validated as in qtm_build), batch >= 1
@@ -287,9 +289,12 @@ qtm_status qtm_build_multi(const qtm_circuit *circuits, int n_circuits, int batc
 qtm_status qtm_multi_offsets(const qtm_multi *multi, int which, int64_t *offsets);
 
 /* Forward + adjoint of every (circuit, sample) in one persistent launch: a
- * device work counter hands (circuit, sample) items to CTAs; circuits with
- * n <= 12 run both directions in shared memory, larger ones sweep tiles of
- * their own states (no inter-CTA waits).  Device pointers, plan real type.
+ * device work counter hands tasks to CTAs in a fixed list order; circuits with
+ * n <= 12 run both directions in shared memory as one task, larger ones sweep
+ * tiles of their own states, either inside one CTA (split = 0) or as one task
+ * per (pass, tile) that waits, bounded, for the tiles of the item's previous
+ * pass (split = 1; every wait is on a task listed earlier, so waits end).
+ * Device pointers, plan real type.
  * flags: QTM_MULTI_GRAPH replays a CUDA graph captured on first use for
  * these buffers (re-captured when a pointer changes). */
 #define QTM_MULTI_GRAPH 1
@@ -297,7 +302,7 @@ qtm_status qtm_multi_run(qtm_multi *multi, const void *x, const void *w, const v
                          void *expvals, void *grad_x, void *grad_w, int flags, void *stream);
 
 /* Autotune the launch configuration on these buffers: time each candidate
- * (CTAs per SM x item order x fusion width) with CUDA events and keep the
+ * (CTAs per SM x item order x fusion width x split) with CUDA events and keep the
  * fastest.  cache_path (or NULL): a JSON file of earlier choices keyed by the
  * batch's signature and the device name; a hit skips the timing. */
 qtm_status qtm_multi_tune(qtm_multi *multi, const void *x, const void *w, const void *grad_expvals,
@@ -305,7 +310,8 @@ qtm_status qtm_multi_tune(qtm_multi *multi, const void *x, const void *w, const 
                           const char *cache_path);
 
 /* Synchronise `stream`, then report the persistent kernel's self-checks:
- * QTM_ETIMEOUT if a CTA ran past its 20 s deadline (it stops taking work),
+ * QTM_ETIMEOUT if a CTA ran past its 20 s deadline or a task's wait for its
+ * item's previous pass gave up after 10 s (the run stops taking work),
  * QTM_EINVAL if an index check failed; the status is cleared after reading. */
 qtm_status qtm_multi_sync(qtm_multi *multi, void *stream);
 

@@ -38,6 +38,26 @@ const char *qtm_debug_jit_source(const qtm_plan *plan, int which, int index, int
  * log in qtm_last_error on failure. */
 qtm_status qtm_debug_jit_compile(qtm_plan *plan, int flags);
 
+/* The uneven batch's task list (host only), in the order the persistent
+ * kernel hands tasks out: tasks[3i .. 3i+2] = (item, step, tile); step = -1
+ * is a whole item, step >= 0 one pass (forward passes, then reverse passes)
+ * of an item whose state spans several tiles, and tile its tile.
+ * items[2i .. 2i+1] = (circuit, sample) of item i.  At most `capacity` tasks
+ * and `item_capacity` items are written; *n_tasks and *n_items (each may be
+ * NULL) receive the full counts. */
+qtm_status qtm_debug_multi_tasks(const qtm_multi *multi, int32_t *tasks, int capacity, int *n_tasks,
+                                 int32_t *items, int item_capacity, int *n_items);
+
+/* Failure injection for the persistent kernel's bounded waits: replace the
+ * task list by n (item, step, tile) triples and set the limit of one task's
+ * wait to wait_ns (> 0; 10 s by default).  Every index is range-checked, but
+ * not the order or completeness: a tile task whose item's previous pass is
+ * never listed waits out the limit, the run drains, and qtm_multi_sync
+ * reports QTM_ETIMEOUT.  Waits for the device when tables were uploaded.  The
+ * next qtm_multi_set_config (or qtm_multi_tune) restores the normal list and
+ * limit. */
+qtm_status qtm_debug_multi_inject(qtm_multi *multi, const int32_t *tasks, int n, long long wait_ns);
+
 #ifdef __cplusplus
 }
 #endif

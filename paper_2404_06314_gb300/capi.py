@@ -383,7 +383,7 @@ class qtm_circuit(ctypes.Structure):
 
 class qtm_multi_config(ctypes.Structure):
     _fields_ = [("ctas_per_sm", ctypes.c_int32), ("order", ctypes.c_int32),
-                ("fuse_width", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("fuse_width", ctypes.c_int32), ("split", ctypes.c_int32)]
 
 
 def _multi_lib():
@@ -398,7 +398,9 @@ def _multi_lib():
         L.qtm_multi_set_config.argtypes = [vp, P(qtm_multi_config)]
         L.qtm_multi_destroy.argtypes = [vp]
         L.qtm_multi_sync.argtypes = [vp, vp]
-        for f in ("qtm_multi_sync", "qtm_build_multi", "qtm_multi_offsets", "qtm_multi_run", "qtm_multi_tune",
+        L.qtm_debug_multi_tasks.argtypes = [vp, vp, i, P(i), vp, i, P(i)]
+        L.qtm_debug_multi_inject.argtypes = [vp, vp, i, ctypes.c_longlong]
+        for f in ("qtm_debug_multi_tasks", "qtm_debug_multi_inject", "qtm_multi_sync", "qtm_build_multi", "qtm_multi_offsets", "qtm_multi_run", "qtm_multi_tune",
                   "qtm_multi_get_config", "qtm_multi_set_config", "qtm_multi_destroy"):
             getattr(L, f).restype = ctypes.c_int
         L._multi_ready = True
@@ -509,11 +511,33 @@ class MultiPlan:
         st = _multi_lib().qtm_multi_get_config(self.handle, ctypes.byref(c))
         if st != QTM_OK:
             raise QtmError(st, "qtm_multi_get_config")
-        return {"ctas_per_sm": c.ctas_per_sm, "order": c.order, "fuse_width": c.fuse_width}
+        return {"ctas_per_sm": c.ctas_per_sm, "order": c.order, "fuse_width": c.fuse_width, "split": c.split}
+
+    def debug_tasks(self):
+        """(tasks [n, 3] of (item, step, tile) in hand-out order, items [m, 2]
+        of (circuit, sample)); host only."""
+        L = _multi_lib()
+        nt, ni = ctypes.c_int(), ctypes.c_int()
+        st = L.qtm_debug_multi_tasks(self.handle, None, 0, ctypes.byref(nt), None, 0, ctypes.byref(ni))
+        if st != QTM_OK:
+            raise QtmError(st, "qtm_debug_multi_tasks")
+        t = np.zeros((max(1, nt.value), 3), dtype=np.int32)
+        it = np.zeros((max(1, ni.value), 2), dtype=np.int32)
+        st = L.qtm_debug_multi_tasks(self.handle, t.ctypes.data, nt.value, None, it.ctypes.data, ni.value, None)
+        if st != QTM_OK:
+            raise QtmError(st, "qtm_debug_multi_tasks")
+        return t[:nt.value], it[:ni.value]
+
+    def debug_inject(self, tasks, wait_ns: int):
+        """Replace the task list (bounded-wait failure injection)."""
+        t = np.ascontiguousarray(np.asarray(tasks, dtype=np.int32).reshape(-1, 3))
+        st = _multi_lib().qtm_debug_multi_inject(self.handle, t.ctypes.data, len(t), int(wait_ns))
+        if st != QTM_OK:
+            raise QtmError(st, "qtm_debug_multi_inject")
 
     @config.setter
     def config(self, d: dict):
-        c = qtm_multi_config(int(d["ctas_per_sm"]), int(d["order"]), int(d["fuse_width"]), 0)
+        c = qtm_multi_config(int(d["ctas_per_sm"]), int(d["order"]), int(d["fuse_width"]), int(d.get("split", 1)))
         st = _multi_lib().qtm_multi_set_config(self.handle, ctypes.byref(c))
         if st != QTM_OK:
             raise QtmError(st, "qtm_multi_set_config")

@@ -1,12 +1,17 @@
 // Uneven batches: many circuits (different n and depth), `batch` samples each,
 // forward + adjoint in one persistent kernel launch.
 //
-// Work items are (circuit, sample) pairs, handed to CTAs by a device counter
-// (atomicAdd; nothing ever waits on another CTA).  A circuit whose state fits
-// one shared-memory tile (n <= 12) runs its forward pass, expectation values,
+// Work items are (circuit, sample) pairs.  A circuit whose state fits one
+// shared-memory tile (n <= 12) runs its forward pass, expectation values,
 // costate and reverse pass back to back without leaving shared memory; a
-// larger circuit sweeps the tiles of its own state (kept in a per-item global
-// buffer, L2-resident for n <= 16) pass after pass inside the same CTA.  The
+// larger circuit's state lives in a per-item global buffer (L2-resident for
+// n <= 16).  Tasks are handed to CTAs by a device counter in list order.  With
+// split = 0 a task is a whole item (a tiled item sweeps its tiles pass after
+// pass in one CTA); with split = 1 every (item, pass, tile) of a tiled item is
+// its own task, listed level by level (pass k of every item before pass k + 1),
+// and a task waits (bounded) until all tiles of its item's previous pass are
+// done: each task depends only on tasks handed out before it, so the waits
+// end, and the largest circuits no longer run on one CTA alone.  The
 // run is prep -> counter reset -> persistent kernel -> finalize kernels, and
 // can be captured once into a CUDA graph and replayed.  An autotuner picks
 // the grid size, the item order and the fusion width by timing candidates.
@@ -22,6 +27,7 @@
 #include <vector>
 
 #include "../../include/qtm.h"
+#include "../../include/qtm_debug.h"
 #include "device.h"
 #include "tile.cuh"
 
@@ -40,6 +46,12 @@ struct CircDev {
 
 struct WorkItem {
     int c, b;
+};
+
+// One unit of work: a whole item (step < 0) or one tile of one pass of a
+// tiled item (step = pass index, forward passes then reverse passes).
+struct Task {
+    int item, step, tile;
 };
 
 struct MultiArgs {
@@ -64,6 +76,11 @@ struct MultiArgs {
     double *Epart, *Gpart, *abar, *gwws;
     unsigned *counter;
     unsigned *status;             // bit 0: deadline hit; bit 1: bad index (both skip work)
+    const Task *tasks;
+    int n_tasks;
+    unsigned long long wait_ns;   // limit of one task's wait for its item's previous pass
+    unsigned *abort;              // set when a wait of this run gave up: the others stop waiting
+    unsigned *done;               // [n_items] tile tasks completed per item (split schedule)
     int n_circ, n_passes, n_ops_total, n_phases_total;
     // shared-memory layout bounds (max over all passes of all circuits)
     int max_slots, max_terms, max_M, max_ents, max_sq;
@@ -72,6 +89,7 @@ struct MultiArgs {
 namespace {
 
 constexpr unsigned long long kMultiDeadlineNs = 20000000000ull;   // 20 s per CTA
+constexpr unsigned long long kMultiWaitNs = 10000000000ull;       // default limit of one task's wait
 
 template <typename R>
 __device__ __forceinline__ TileJob make_job(const MultiArgs &m, const CircDev &cd, const PassDesc &pd,
@@ -113,14 +131,27 @@ __device__ __forceinline__ uint32_t tile_base(const PassDesc &pd, int tile)
     return (gap << pd.l) | (rest << (pd.h + pd.m));
 }
 
-// global <-> shared tile copies (plain loads/stores; the item's state is L2-resident)
+__device__ __forceinline__ Cx<float> ld_cg(const Cx<float> *p)
+{
+    const float2 v = __ldcg(reinterpret_cast<const float2 *>(p));
+    return {v.x, v.y};
+}
+__device__ __forceinline__ Cx<double> ld_cg(const Cx<double> *p)
+{
+    const double2 v = __ldcg(reinterpret_cast<const double2 *>(p));
+    return {v.x, v.y};
+}
+
+// global <-> shared tile copies (the item's state is L2-resident).  Loads
+// bypass L1: with the split schedule the tile may have been written by a CTA
+// on another SM.
 template <typename R>
 __device__ __forceinline__ void load_tile(const TileJob &j, Cx<R> *dst, const Cx<R> *src)
 {
     const int E = 1 << j.K;
     for (int e = threadIdx.x; e < E; e += blockDim.x) {
         const uint32_t y = j.base | ((uint32_t)e & ((1u << j.l) - 1u)) | (((uint32_t)e >> j.l) << j.h);
-        dst[swz<R>(e)] = src[y];
+        dst[swz<R>(e)] = ld_cg(src + y);
     }
 }
 
@@ -148,6 +179,40 @@ __global__ void k_multi_prep(const MultiArgs m)
                    nullptr);
 }
 
+// One tile of one pass: load (or generate) phi / lam, run the pass's phases,
+// write the partial sums and store the tile.  `resident`: the item's whole
+// state is this one tile and stays in shared memory from pass to pass (no
+// global loads or stores).  Ends with a barrier.
+template <typename R>
+__device__ __forceinline__ void run_tile(const MultiArgs &m, const TileSmem<R> &S, const CircDev &cd, const PassDesc &pd,
+                                         bool rev, bool resident, int b, int t, Cx<R> *gphi, Cx<R> *glam,
+                                         double *Epart_b, double *Gpart_b)
+{
+    const TileJob j = make_job<R>(m, cd, pd, b, tile_base<R>(pd, t));
+    const int nw = (j.T + 31) >> 5;
+    if (rev) stage_tables<R, true>(j, S, nw);
+    else stage_tables<R, false>(j, S, nw);
+    if (!resident) {
+        if (pd.phi_src == SRC_LOAD) load_tile<R>(j, S.phi, gphi);
+        if (rev && pd.lam_src == SRC_LOAD) load_tile<R>(j, S.lam, glam);
+    }
+    __syncthreads();
+    if (pd.phi_src == SRC_ANALYTIC) fill_analytic<R>(j, S);
+    __syncthreads();
+    if (rev) {
+        run_phases<R, true>(j, S, pd.lam_src == SRC_LOAD);
+        write_partials<R, true>(j, S, nw, false, nullptr, Gpart_b, cd.tiles, t);
+    } else {
+        run_phases<R, false>(j, S, false);
+        write_partials<R, false>(j, S, nw, pd.has_expval != 0, Epart_b + (size_t)t * cd.M, nullptr, cd.tiles, t);
+    }
+    if (!resident) {
+        if (pd.store_phi) store_tile<R>(j, S.phi, gphi);
+        if (rev && pd.store_lam) store_tile<R>(j, S.lam, glam);
+    }
+    __syncthreads();
+}
+
 // MINB: CTAs per SM the register budget is compiled for (1: no spills, 2: more
 // resident warps); the autotuner's ctas_per_sm picks the variant.
 template <typename R, int MINB>
@@ -166,93 +231,80 @@ __global__ void __launch_bounds__(256, MINB) k_multi(const MultiArgs m)
             int it = (int)atomicAdd(m.counter, 1u);
             if (global_ns() - t_start > kMultiDeadlineNs) {   // self-check: a run never takes this long
                 atomicOr(m.status, 1u);
-                it = m.n_items;
+                it = m.n_tasks;
             }
+            if (*(volatile unsigned *)m.abort) it = m.n_tasks;   // a wait of this run gave up: drain
             s_item = it;
         }
         __syncthreads();
-        const int item = s_item;
+        const int task = s_item;
         __syncthreads();
-        if (item >= m.n_items || item < 0) return;
-        const WorkItem wi = m.items[item];
+        if (task >= m.n_tasks || task < 0) return;
+        const Task tk = m.tasks[task];
+        if (tk.item < 0 || tk.item >= m.n_items) {
+            if (threadIdx.x == 0) atomicOr(m.status, 2u);
+            continue;
+        }
+        const WorkItem wi = m.items[tk.item];
         if (wi.c < 0 || wi.c >= m.n_circ) {
             if (threadIdx.x == 0) atomicOr(m.status, 2u);
             continue;
         }
         const CircDev cd = m.circ[wi.c];
         if (cd.fwd_begin < 0 || cd.rev_begin + cd.n_rev > m.n_passes || cd.tiles < 1 || cd.tiles > (1 << 18) ||
-            wi.b < 0 || wi.b >= m.B) {
+            wi.b < 0 || wi.b >= m.B || tk.step >= cd.n_fwd + cd.n_rev || tk.tile < 0 || tk.tile >= cd.tiles ||
+            (tk.step >= 0 && cd.tiles == 1)) {
             if (threadIdx.x == 0) atomicOr(m.status, 2u);
             continue;
         }
         const int b = wi.b;
         double *Epart_b = m.Epart + cd.Epart_off + (size_t)b * cd.tiles * cd.M;
         double *Gpart_b = m.Gpart + cd.Gpart_off + (size_t)b * cd.n_runs * cd.tiles * 3;
-        if (cd.tiles == 1) {
-            // whole state in shared memory: forward, expectation values, costate, reverse
-            for (int i = 0; i < cd.n_fwd; ++i) {   // a single pass for n <= 12
-                const PassDesc pd = m.passes[cd.fwd_begin + i];
-                const TileJob j = make_job<R>(m, cd, pd, b, 0u);
-                const int nw = (j.T + 31) >> 5;
-                stage_tables<R, false>(j, S, nw);
-                __syncthreads();
-                if (pd.phi_src == SRC_ANALYTIC) fill_analytic<R>(j, S);
-                __syncthreads();
-                run_phases<R, false>(j, S, false);
-                write_partials<R, false>(j, S, nw, pd.has_expval != 0, Epart_b, nullptr, 1, 0);
-                __syncthreads();
-            }
-            for (int i = 0; i < cd.n_rev; ++i) {
-                const PassDesc pd = m.passes[cd.rev_begin + i];
-                const TileJob j = make_job<R>(m, cd, pd, b, 0u);
-                const int nw = (j.T + 31) >> 5;
-                stage_tables<R, true>(j, S, nw);
-                __syncthreads();
-                if (pd.phi_src == SRC_ANALYTIC) fill_analytic<R>(j, S);   // else phi is still in smem
-                __syncthreads();
-                run_phases<R, true>(j, S, false);
-                write_partials<R, true>(j, S, nw, false, nullptr, Gpart_b, 1, 0);
-                __syncthreads();
-            }
-            continue;
-        }
-        // tiled: this item's phi and lam live in global memory
         Cx<R> *gphi = static_cast<Cx<R> *>(m.state) + cd.state_off + (size_t)b * (2ull << cd.sq);
         Cx<R> *glam = gphi + (1ull << cd.sq);
-        for (int i = 0; i < cd.n_fwd; ++i) {
-            const PassDesc pd = m.passes[cd.fwd_begin + i];
-            for (int t = 0; t < cd.tiles; ++t) {
-                const TileJob j = make_job<R>(m, cd, pd, b, tile_base<R>(pd, t));
-                const int nw = (j.T + 31) >> 5;
-                stage_tables<R, false>(j, S, nw);
-                if (pd.phi_src == SRC_LOAD) load_tile<R>(j, S.phi, gphi);
-                __syncthreads();
-                if (pd.phi_src == SRC_ANALYTIC) fill_analytic<R>(j, S);
-                __syncthreads();
-                run_phases<R, false>(j, S, false);
-                write_partials<R, false>(j, S, nw, pd.has_expval != 0, Epart_b + (size_t)t * cd.M, nullptr,
-                                         cd.tiles, t);
-                if (pd.store_phi) store_tile<R>(j, S.phi, gphi);
-                __syncthreads();
+        if (tk.step >= 0) {
+            // one tile of one pass: wait (bounded) for every tile of the item's
+            // previous pass, run it, then count it done
+            if (threadIdx.x == 0) {
+                const unsigned need = (unsigned)tk.step * (unsigned)cd.tiles;
+                const unsigned long long t0 = global_ns();
+                unsigned have;
+                bool failed = false;
+                for (;;) {
+                    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(have) : "l"(m.done + tk.item) : "memory");
+                    if (have >= need) break;
+                    // give up after the limit, or at once when another wait already has
+                    if (global_ns() - t0 > m.wait_ns || *(volatile unsigned *)m.abort) {
+                        failed = true;
+                        break;
+                    }
+                    __nanosleep(64);
+                }
+                if (failed) {
+                    atomicOr(m.status, 1u);
+                    atomicExch(m.abort, 1u);
+                }
+                s_item = failed ? -1 : 0;
             }
+            __syncthreads();
+            const bool ready = s_item == 0;
+            __syncthreads();
+            if (!ready) continue;
         }
-        for (int i = 0; i < cd.n_rev; ++i) {
-            const PassDesc pd = m.passes[cd.rev_begin + i];
-            for (int t = 0; t < cd.tiles; ++t) {
-                const TileJob j = make_job<R>(m, cd, pd, b, tile_base<R>(pd, t));
-                const int nw = (j.T + 31) >> 5;
-                stage_tables<R, true>(j, S, nw);
-                if (pd.phi_src == SRC_LOAD) load_tile<R>(j, S.phi, gphi);
-                if (pd.lam_src == SRC_LOAD) load_tile<R>(j, S.lam, glam);
-                __syncthreads();
-                if (pd.phi_src == SRC_ANALYTIC) fill_analytic<R>(j, S);
-                __syncthreads();
-                run_phases<R, true>(j, S, pd.lam_src == SRC_LOAD);
-                write_partials<R, true>(j, S, nw, false, nullptr, Gpart_b, cd.tiles, t);
-                if (pd.store_phi) store_tile<R>(j, S.phi, gphi);
-                if (pd.store_lam) store_tile<R>(j, S.lam, glam);
-                __syncthreads();
-            }
+        // a whole item (every pass, every tile, in order) or one (pass, tile) task
+        const bool whole = tk.step < 0;
+        const int k0 = whole ? 0 : tk.step, k1 = whole ? cd.n_fwd + cd.n_rev : tk.step + 1;
+        const int t0 = whole ? 0 : tk.tile, t1 = whole ? cd.tiles : tk.tile + 1;
+        for (int k = k0; k < k1; ++k) {
+            const bool rev = k >= cd.n_fwd;
+            const PassDesc pd = m.passes[rev ? cd.rev_begin + (k - cd.n_fwd) : cd.fwd_begin + k];
+            for (int t = t0; t < t1; ++t)
+                run_tile<R>(m, S, cd, pd, rev, cd.tiles == 1, b, t, gphi, glam, Epart_b, Gpart_b);
+        }
+        if (!whole) {
+            __threadfence();   // this tile's state writes before the count (release)
+            __syncthreads();
+            if (threadIdx.x == 0) atomicAdd(m.done + tk.item, 1u);
         }
     }
 }
@@ -313,10 +365,11 @@ struct qtm_multi {
     std::vector<std::vector<qtm_zterm>> terms;
     std::vector<qtm_circuit> desc;
     std::vector<Plan> plans;
-    qtm_multi_config cfg{2, 0, kMaxRunLen, 0};
+    qtm_multi_config cfg{2, 0, kMaxRunLen, 1};
     // host-side images
     std::vector<CircDev> circ;
     std::vector<WorkItem> items;
+    std::vector<Task> tasks;
     std::vector<PassDesc> passes;
     std::vector<DevOp> ops;
     std::vector<DiagPair> diag;
@@ -331,13 +384,15 @@ struct qtm_multi {
     long long n_mats = 0, n_tabs = 0, n_epart = 0, n_gpart = 0, n_abar = 0, n_gwws = 0, n_state = 0;
     int max_slots = 1, max_terms = 1, max_M = 1, max_ents = 1, max_sq = 4;
     size_t smem = 0;
+    unsigned long long wait_ns = kMultiWaitNs;
+    bool injected = false;   // task list replaced by qtm_debug_multi_inject
     // device
     int device = -1;
     bool dirty = true;
     void *dev_block = nullptr;      // all tables in one allocation
     void *d_ws = nullptr;           // workspace (mats, tabs, state)
     double *d_dbl = nullptr;        // Epart, Gpart, abar, gwws
-    unsigned *d_counter = nullptr;   // [0] work counter, [1] status
+    unsigned *d_counter = nullptr;   // [0] status, [1] task counter, [2] abort, [3 ..] per-item done counters
     MultiArgs args{};
     // graph cache
     cudaGraphExec_t gexec = nullptr;
@@ -377,6 +432,54 @@ double item_cost(const Plan &P)
     double fb, ab, ff, af;
     plan_costs(P, fb, ab, ff, af);
     return ff + af + 4.0 * (fb + ab);
+}
+
+// The task list.  split = 0: one whole task per item, in item order.
+// split = 1: a tiled item becomes one task per (pass, tile).  With order 0
+// the tasks are listed highest level first (a list schedule): a task's level
+// is the estimated time from its start to the end of its item's chain, i.e.
+// the item's cost for a whole task and (passes left) x (cost of one pass's
+// tile) for a tile task, so the long chains of the largest circuits start
+// first and whole small items fill in between their passes.  With order 1 they
+// are listed pass by pass: every item's pass 0 (whole items there too), then
+// every item's pass 1, ...  Either way a tile task comes after every tile of
+// its item's previous pass, which the kernel's waits rely on.
+void build_tasks(qtm_multi *m)
+{
+    m->tasks.clear();
+    const int ni = (int)m->items.size();
+    if (m->cfg.split == 0) {
+        for (int i = 0; i < ni; ++i) m->tasks.push_back({i, -1, 0});
+        return;
+    }
+    struct Key {
+        double level;
+        int item, step, tile;
+    };
+    std::vector<Key> keys;
+    for (int i = 0; i < ni; ++i) {
+        const Plan &P = m->plans[m->items[i].c];
+        const int tiles = P.tiles_per_sample, steps = (int)(P.fwd.size() + P.rev.size());
+        const double cost = item_cost(P);
+        if (tiles <= 1 || steps < 1) {
+            keys.push_back({cost, i, -1, 0});
+            continue;
+        }
+        for (int k = 0; k < steps; ++k)
+            for (int t = 0; t < tiles; ++t)
+                keys.push_back({(double)(steps - k) * cost / ((double)steps * tiles), i, k, t});
+    }
+    if (m->cfg.order == 0)
+        std::sort(keys.begin(), keys.end(), [](const Key &a, const Key &b) {
+            if (a.level != b.level) return a.level > b.level;
+            if (a.item != b.item) return a.item < b.item;
+            if (a.step != b.step) return a.step < b.step;
+            return a.tile < b.tile;
+        });
+    else
+        std::stable_sort(keys.begin(), keys.end(),
+                         [](const Key &a, const Key &b) { return std::max(a.step, 0) < std::max(b.step, 0); });
+    for (const Key &k : keys) m->tasks.push_back({k.item, k.step, k.tile});
 }
 
 // (Re)plan every circuit with the current fusion width and lay out the tables.
@@ -468,6 +571,9 @@ qtm_status plan_all(qtm_multi *m)
         std::stable_sort(m->items.begin(), m->items.end(),
                          [&](const WorkItem &a, const WorkItem &b) { return cost[a.c] > cost[b.c]; });
     }
+    build_tasks(m);
+    m->wait_ns = kMultiWaitNs;
+    m->injected = false;
     const int csize = elem_bytes(m->dtype);
     const Layout L = make_layout(kMaxTileQubits, csize, true, m->max_slots, m->max_terms, m->max_M,
                                  m->max_sq, m->max_ents, 8, csize / 2);
@@ -493,6 +599,7 @@ qtm_status upload(qtm_multi *m)
     if (!m->dirty && dev == m->device) return QTM_OK;
     release_device(m);
     std::vector<unsigned char> blob;
+    const size_t o_tasks = put(blob, m->tasks);
     const size_t o_items = put(blob, m->items), o_circ = put(blob, m->circ), o_passes = put(blob, m->passes),
                  o_ops = put(blob, m->ops), o_diag = put(blob, m->diag), o_phases = put(blob, m->phases),
                  o_slots = put(blob, m->slots), o_runs = put(blob, m->runs), o_rots = put(blob, m->rots),
@@ -509,8 +616,8 @@ qtm_status upload(qtm_multi *m)
     const size_t ws = csize * (size_t)(m->n_mats + m->n_tabs + m->n_state);
     const size_t nd = (size_t)(m->n_epart + m->n_gpart + m->n_abar + m->n_gwws);
     if (cudaMalloc(&m->d_ws, ws ? ws : 16) != cudaSuccess || cudaMalloc(&m->d_dbl, 8 * (nd ? nd : 1)) != cudaSuccess ||
-        cudaMalloc(&m->d_counter, 2 * sizeof(unsigned)) != cudaSuccess ||
-        cudaMemset(m->d_counter, 0, 2 * sizeof(unsigned)) != cudaSuccess) {
+        cudaMalloc(&m->d_counter, (3 + m->items.size()) * sizeof(unsigned)) != cudaSuccess ||
+        cudaMemset(m->d_counter, 0, (3 + m->items.size()) * sizeof(unsigned)) != cudaSuccess) {
         release_device(m);
         m->err = "workspace allocation failed";
         return QTM_ENOMEM;
@@ -521,6 +628,9 @@ qtm_status upload(qtm_multi *m)
     a.n_items = (int)m->items.size();
     a.B = m->B;
     a.items = reinterpret_cast<const WorkItem *>(db + o_items);
+    a.tasks = reinterpret_cast<const Task *>(db + o_tasks);
+    a.n_tasks = (int)m->tasks.size();
+    a.wait_ns = m->wait_ns;
     a.circ = reinterpret_cast<const CircDev *>(db + o_circ);
     a.passes = reinterpret_cast<const PassDesc *>(db + o_passes);
     a.ops = reinterpret_cast<const DevOp *>(db + o_ops);
@@ -545,8 +655,10 @@ qtm_status upload(qtm_multi *m)
     a.Gpart = a.Epart + m->n_epart;
     a.abar = a.Gpart + m->n_gpart;
     a.gwws = a.abar + m->n_abar;
-    a.counter = m->d_counter;
-    a.status = m->d_counter + 1;
+    a.status = m->d_counter;
+    a.counter = m->d_counter + 1;
+    a.abort = m->d_counter + 2;
+    a.done = m->d_counter + 3;
     a.n_circ = (int)m->circ.size();
     a.n_passes = (int)m->passes.size();
     a.n_ops_total = (int)m->ops.size();
@@ -568,13 +680,13 @@ cudaError_t enqueue_t(qtm_multi *m, cudaStream_t s)
 {
     const MultiArgs &a = m->args;
     const int ni = a.n_items;
-    cudaError_t e = cudaMemsetAsync(a.counter, 0, sizeof(unsigned), s);
+    cudaError_t e = cudaMemsetAsync(a.counter, 0, (2 + (size_t)ni) * sizeof(unsigned), s);   // counter, abort, done[]
     if (e != cudaSuccess) return e;
     k_multi_prep<R><<<ni, 128, 0, s>>>(a);
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device);
     const int cps = m->cfg.ctas_per_sm >= 2 ? 2 : 1;
-    const int grid = std::max(1, std::min(ni, cps * sms));
+    const int grid = std::max(1, std::min(a.n_tasks, cps * sms));
     if (cps == 2) k_multi<R, 2><<<grid, 256, m->smem, s>>>(a);
     else k_multi<R, 1><<<grid, 256, m->smem, s>>>(a);
     k_multi_expval<R><<<ni, 32, 0, s>>>(a);
@@ -680,8 +792,8 @@ bool cache_lookup(const char *path, const std::string &sig, qtm_multi_config &cf
             size_t at = line.find(k);
             return at == std::string::npos ? -1 : std::atoi(line.c_str() + at + k.size());
         };
-        qtm_multi_config c{num("ctas_per_sm"), num("order"), num("fuse_width"), 0};
-        if (c.ctas_per_sm < 1 || c.order < 0 || c.fuse_width < 1) continue;
+        qtm_multi_config c{num("ctas_per_sm"), num("order"), num("fuse_width"), num("split")};
+        if (c.ctas_per_sm < 1 || c.order < 0 || c.fuse_width < 1 || c.split < 0 || c.split > 1) continue;
         cfg = c;
         return true;
     }
@@ -693,12 +805,14 @@ void cache_store(const char *path, const std::string &sig, const qtm_multi_confi
     if (!path) return;
     std::ofstream f(path, std::ios::app);
     f << "{\"signature\": \"" << sig << "\", \"ctas_per_sm\": " << cfg.ctas_per_sm << ", \"order\": " << cfg.order
-      << ", \"fuse_width\": " << cfg.fuse_width << ", \"ms\": " << ms << "}\n";
+      << ", \"fuse_width\": " << cfg.fuse_width << ", \"split\": " << cfg.split << ", \"ms\": " << ms
+      << "}\n";
 }
 
 qtm_status apply_config(qtm_multi *m, const qtm_multi_config &c)
 {
-    const bool replan = c.fuse_width != m->cfg.fuse_width || c.order != m->cfg.order;
+    const bool replan = c.fuse_width != m->cfg.fuse_width || c.order != m->cfg.order || c.split != m->cfg.split ||
+                        m->injected;
     m->cfg = c;
     release_graph(m);   // the grid size and the tables are baked into a captured graph
     if (replan) {
@@ -769,8 +883,9 @@ qtm_status qtm_multi_tune(qtm_multi *m, const void *x, const void *w, const void
     qtm_status result = QTM_OK;
     for (int fuse : {32, 3, 1})
         for (int order : {0, 1})
-            for (int cps : {1, 2}) {
-                qtm_multi_config c{cps, order, fuse, 0};
+            for (int cps : {1, 2})
+                for (int split : {0, 1}) {
+                qtm_multi_config c{cps, order, fuse, split};
                 qtm_status st = apply_config(m, c);
                 if (st != QTM_OK) continue;
                 std::vector<float> t;
@@ -787,7 +902,7 @@ qtm_status qtm_multi_tune(qtm_multi *m, const void *x, const void *w, const void
                 std::sort(t.begin(), t.end());
                 const double med = t[t.size() / 2];
                 if (med < best_ms) { best_ms = med; best = c; }
-            }
+                }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (best_ms >= 1e30) return result != QTM_OK ? result : QTM_ECUDA;
@@ -805,9 +920,9 @@ qtm_status qtm_multi_sync(qtm_multi *m, void *stream)
     if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess) return QTM_ECUDA;
     if (!m->d_counter) return QTM_OK;
     unsigned st = 0;
-    if (cudaMemcpy(&st, m->d_counter + 1, sizeof(unsigned), cudaMemcpyDeviceToHost) != cudaSuccess) return QTM_ECUDA;
+    if (cudaMemcpy(&st, m->d_counter, sizeof(unsigned), cudaMemcpyDeviceToHost) != cudaSuccess) return QTM_ECUDA;
     if (!st) return QTM_OK;
-    cudaMemset(m->d_counter + 1, 0, sizeof(unsigned));
+    cudaMemset(m->d_counter, 0, sizeof(unsigned));
     return (st & 1u) ? QTM_ETIMEOUT : QTM_EINVAL;
 }
 
@@ -821,9 +936,51 @@ qtm_status qtm_multi_get_config(const qtm_multi *m, qtm_multi_config *cfg)
 qtm_status qtm_multi_set_config(qtm_multi *m, const qtm_multi_config *cfg)
 {
     if (!m || !cfg || cfg->ctas_per_sm < 1 || cfg->ctas_per_sm > 8 || cfg->order < 0 || cfg->order > 1 ||
-        cfg->fuse_width < 1 || cfg->fuse_width > kMaxRunLen)
+        cfg->fuse_width < 1 || cfg->fuse_width > kMaxRunLen || cfg->split < 0 || cfg->split > 1)
         return QTM_EINVAL;
     return apply_config(m, *cfg);
+}
+
+qtm_status qtm_debug_multi_tasks(const qtm_multi *m, int32_t *tasks, int capacity, int *n_tasks, int32_t *items,
+                                 int item_capacity, int *n_items)
+{
+    if (!m || capacity < 0 || item_capacity < 0 || (capacity > 0 && !tasks) || (item_capacity > 0 && !items))
+        return QTM_EINVAL;
+    for (int i = 0; i < capacity && i < (int)m->tasks.size(); ++i) {
+        tasks[3 * i] = m->tasks[i].item;
+        tasks[3 * i + 1] = m->tasks[i].step;
+        tasks[3 * i + 2] = m->tasks[i].tile;
+    }
+    for (int i = 0; i < item_capacity && i < (int)m->items.size(); ++i) {
+        items[2 * i] = m->items[i].c;
+        items[2 * i + 1] = m->items[i].b;
+    }
+    if (n_tasks) *n_tasks = (int)m->tasks.size();
+    if (n_items) *n_items = (int)m->items.size();
+    return QTM_OK;
+}
+
+qtm_status qtm_debug_multi_inject(qtm_multi *m, const int32_t *tasks, int n, long long wait_ns)
+{
+    if (!m || n < 1 || !tasks || wait_ns <= 0) return QTM_EINVAL;
+    std::vector<Task> t(n);
+    for (int i = 0; i < n; ++i) {
+        t[i] = {tasks[3 * i], tasks[3 * i + 1], tasks[3 * i + 2]};
+        if (t[i].item < 0 || t[i].item >= (int)m->items.size()) return QTM_EINVAL;
+        const Plan &P = m->plans[m->items[t[i].item].c];
+        const int steps = (int)(P.fwd.size() + P.rev.size());
+        if (t[i].step < -1 || t[i].step >= steps) return QTM_EINVAL;
+        if (t[i].step < 0 ? t[i].tile != 0 : (P.tiles_per_sample < 2 || t[i].tile < 0 ||
+                                              t[i].tile >= P.tiles_per_sample))
+            return QTM_EINVAL;
+    }
+    if (m->dev_block) cudaDeviceSynchronize();
+    m->tasks = t;
+    m->wait_ns = (unsigned long long)wait_ns;
+    m->injected = true;
+    release_graph(m);
+    m->dirty = true;
+    return QTM_OK;
 }
 
 qtm_status qtm_multi_destroy(qtm_multi *m)

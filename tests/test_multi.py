@@ -19,10 +19,67 @@ def test_multi_offsets_and_config_host():
     assert list(np.diff(ox)) == [3 * c.n_inputs for c in cs]
     assert list(np.diff(ow)) == [c.n_weights for c in cs]
     assert list(np.diff(oe)) == [3 * c.n_obs for c in cs]
-    mp.config = {"ctas_per_sm": 1, "order": 1, "fuse_width": 1}
-    assert mp.config == {"ctas_per_sm": 1, "order": 1, "fuse_width": 1}
+    mp.config = {"ctas_per_sm": 1, "order": 1, "fuse_width": 1, "split": 0}
+    assert mp.config == {"ctas_per_sm": 1, "order": 1, "fuse_width": 1, "split": 0}
     with pytest.raises(capi.QtmError):
         mp.config = {"ctas_per_sm": 0, "order": 0, "fuse_width": 1}
+    with pytest.raises(capi.QtmError):
+        mp.config = {"ctas_per_sm": 1, "order": 0, "fuse_width": 1, "split": 2}
+
+
+def _plan_steps(c):
+    info = capi.Plan(c, dtype="c64").info
+    return info["fwd_passes"] + info["adj_passes"], 1 << max(0, info["n_qubits"] - info["tile_qubits"])
+
+
+@pytest.mark.parametrize("split,order", [(0, 0), (0, 1), (1, 0), (1, 1)])
+def test_multi_task_list_host(split, order):
+    """The hand-out order the persistent kernel relies on: every item's work
+    listed exactly once, and every (pass, tile) task after all tiles of its
+    item's previous pass (a task only ever waits on tasks handed out before
+    it, so the bounded waits end)."""
+    cs = W.workload_uneven(count=10, seed=21, n_lo=11, n_hi=16)
+    mp = capi.MultiPlan(cs, batch=2)
+    mp.config = {"ctas_per_sm": 2, "order": order, "fuse_width": 32, "split": split}
+    tasks, items = mp.debug_tasks()
+    assert len(items) == 2 * len(cs)
+    assert sorted(map(tuple, items.tolist())) == [(c, b) for c in range(len(cs)) for b in range(2)]
+    geo = [_plan_steps(c) for c in cs]
+    expect = set()
+    for i, (c, b) in enumerate(items.tolist()):
+        steps, tiles = geo[c]
+        if split == 0 or tiles == 1:
+            expect.add((i, -1, 0))
+        else:
+            expect |= {(i, k, t) for k in range(steps) for t in range(tiles)}
+    listed = list(map(tuple, tasks.tolist()))
+    assert len(listed) == len(set(listed)) and set(listed) == expect
+    done = {}
+    for (i, k, t) in listed:
+        if k >= 0:
+            tiles = geo[items[i][0]][1]
+            assert done.get((i, k - 1), 0) == (tiles if k > 0 else 0), (i, k, t)
+            done[(i, k)] = done.get((i, k), 0) + 1
+    if split == 1:
+        assert any(k > 0 for _, k, _ in listed)
+        if order == 0:   # highest level first: the first task starts the longest chain
+            assert listed[0][1] in (-1, 0)
+
+
+def test_multi_inject_validates_host():
+    cs = W.workload_uneven(count=3, seed=9, n_lo=13, n_hi=13)
+    mp = capi.MultiPlan(cs, batch=1)
+    steps, tiles = _plan_steps(cs[0])
+    for bad in ([(3, 0, 0)], [(0, steps, 0)], [(0, 0, tiles)], [(0, -1, 1)], [(0, -2, 0)]):
+        with pytest.raises(capi.QtmError):
+            mp.debug_inject(bad, 1000000)
+    with pytest.raises(capi.QtmError):
+        mp.debug_inject([(0, 1, 0)], 0)
+    mp.debug_inject([(0, 1, 0)], 1000000)
+    tasks, _ = mp.debug_tasks()
+    assert tasks.tolist() == [[0, 1, 0]]
+    mp.config = mp.config   # any configuration call restores the normal list
+    assert len(mp.debug_tasks()[0]) == sum(k * t for k, t in map(_plan_steps, cs))
 
 
 def test_multi_rejects_invalid_circuit():
@@ -63,13 +120,55 @@ def _check(cs, xs, ws, gs, Es, gxs, gws, tol=1e-5):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("fuse_width", [32, 3, 1])
-def test_multi_matches_oracle(fuse_width):
+@pytest.mark.parametrize("fuse_width,split,order,cps", [(32, 1, 0, 2), (3, 1, 0, 2), (1, 1, 1, 1),
+                                                        (32, 0, 0, 2), (3, 0, 1, 1), (32, 1, 1, 2)])
+def test_multi_matches_oracle(fuse_width, split, order, cps):
     cs = W.workload_uneven(count=20, seed=77, n_lo=4, n_hi=15)
     mp = capi.MultiPlan(cs, batch=2)
-    mp.config = {"ctas_per_sm": 2, "order": 0, "fuse_width": fuse_width}
+    mp.config = {"ctas_per_sm": cps, "order": order, "fuse_width": fuse_width, "split": split}
     xs, ws, gs = _inputs(cs, 2, 5)
     Es, gxs, gws, _ = _run(mp, cs, xs, ws, gs)
+    mp.sync()
+    _check(cs, xs, ws, gs, Es, gxs, gws)
+
+
+@pytest.mark.gpu
+def test_multi_split_bitwise_equal_to_whole_items():
+    """Splitting an item into (pass, tile) tasks changes who runs a tile, not
+    its arithmetic: outputs are bit-identical to whole items on one CTA."""
+    cs = W.workload_uneven(count=8, seed=31, n_lo=13, n_hi=16) + W.workload_uneven(count=8, seed=32, n_lo=5, n_hi=12)
+    xs, ws, gs = _inputs(cs, 2, 8)
+    outs = []
+    for split in (0, 1):
+        mp = capi.MultiPlan(cs, batch=2)
+        mp.config = {"ctas_per_sm": 2, "order": 0, "fuse_width": 32, "split": split}
+        outs.append(_run(mp, cs, xs, ws, gs)[:3])
+        mp.sync()
+    for a_list, b_list in zip(*outs):
+        for a, b in zip(a_list, b_list):
+            assert np.array_equal(a, b)
+    _check(cs, xs, ws, gs, *outs[1])
+
+
+@pytest.mark.gpu
+def test_multi_wait_limit_reports_timeout_and_recovers():
+    """Bounded waits: a tile task whose item's previous pass is never listed
+    gives up after the (shortened) limit; the run drains, qtm_multi_sync reports
+    QTM_ETIMEOUT, and the next normal run is correct."""
+    cs = W.workload_uneven(count=2, seed=9, n_lo=13, n_hi=13)
+    mp = capi.MultiPlan(cs, batch=1)
+    xs, ws, gs = _inputs(cs, 1, 10)
+    *_, bufs = _run(mp, cs, xs, ws, gs)
+    mp.sync()
+    mp.debug_inject([(0, 1, 0), (1, -1, 0)], 20_000_000)   # 20 ms
+    mp.run(*bufs)
+    with pytest.raises(capi.QtmError) as ei:
+        mp.sync()
+    assert ei.value.status == capi.QTM_ETIMEOUT
+    mp.sync()   # status cleared after reading
+    mp.config = mp.config   # restores the normal list and limit
+    Es, gxs, gws, _ = _run(mp, cs, xs, ws, gs)
+    mp.sync()
     _check(cs, xs, ws, gs, Es, gxs, gws)
 
 
@@ -99,6 +198,7 @@ def test_multi_tune_and_cache(tmp_path):
     cache = str(tmp_path / "tune.jsonl")
     cfg = mp.tune(*bufs, cache_path=cache)
     assert cfg["ctas_per_sm"] in (1, 2) and cfg["order"] in (0, 1) and cfg["fuse_width"] in (1, 3, 32)
+    assert cfg["split"] in (0, 1)
     lines = [json.loads(l) for l in open(cache)]
     assert len(lines) == 1 and lines[0]["fuse_width"] == cfg["fuse_width"]
     mp2 = capi.MultiPlan(cs, batch=1)

@@ -220,6 +220,7 @@ KERNEL_LABEL = {"naive": "naive one-gate-per-launch path","paired": "qtm_gen_pas
                 "paired-general": "k_pass_x2<reverse> (general, two samples per CTA on f32x2 pairs)",
                 "one-sample": "qtm_gen_pass (plan-specialised, one sample per CTA), reverse",
                 "lanes": "qtm_gen_pass (plan-specialised, one sample per CTA, amplitudes paired in f32x2), reverse",
+                "cpx": "qtm_gen_pass (plan-specialised, one sample per CTA, complex amplitudes as f32x2 pairs), reverse",
                 "general": "k_pass<float, reverse> (general pass kernel)"}
 
 
@@ -228,12 +229,12 @@ def prepare(plan, kernels):
     if kernels == "paired-general":
         plan.set_pairing(True)
     elif kernels not in ("general", "naive"):
-        plan.compile(kind={"paired": "pairs", "one-sample": "one", "lanes": "lanes"}[kernels])
+        plan.compile(kind={"paired": "pairs", "one-sample": "one", "lanes": "lanes", "cpx": "cpx"}[kernels])
         assert plan.compiled_passes() > 0, "no specialised pass kernel loaded"
     return plan
 
 
-def measure_gpu(name, steps, warmup, device, seed_offset=0, profile=True, kernels="lanes"):
+def measure_gpu(name, steps, warmup, device, seed_offset=0, profile=True, kernels="cpx"):
     import numpy as np
     import torch
 
@@ -396,10 +397,10 @@ def measure_training(device, steps=100):
             "ms_per_step": ms / steps, "loss_first": float(lc[0]), "loss_last": float(lc[-1]),
             "config": {"workload": "qnn16_l8_train: 16 qubits, 8 re-uploading layers + CZ ring, B=256, "
                                    "MSE on sum_i <Z_i>, Adam lr 1e-2", "steps": steps,
-                       "pass_kernels": "QuantumModule(kernels='auto'): lane-paired specialised"}}
+                       "pass_kernels": "QuantumModule(kernels='auto'): complex-pair specialised"}}
 
 
-def measure_e2e(name, steps, device, seed_offset=0, kernels="lanes"):
+def measure_e2e(name, steps, device, seed_offset=0, kernels="cpx"):
     """End to end through the public API: pinned host inputs -> device,
     forward, adjoint, results -> pinned host, every step."""
     import numpy as np
@@ -626,10 +627,12 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="qnn12")
     ap.add_argument("--skip-n20", action="store_true")
-    ap.add_argument("--kernels", choices=["paired", "one-sample", "lanes", "paired-general", "general"], default="lanes",
+    ap.add_argument("--kernels", choices=["paired", "one-sample", "lanes", "cpx", "paired-general", "general"],
+                    default="cpx",
                     help="plan-specialised pass kernels (qtm_compile: lanes = one sample per CTA with "
-                         "amplitudes paired in f32x2 registers, one-sample = scalar, paired = two samples per "
-                         "CTA), or the general pass kernels (paired-general / general)")
+                         "amplitudes paired in f32x2 registers, cpx = one sample per CTA with each complex "
+                         "amplitude an f32x2 pair, one-sample = scalar, paired = two samples per CTA), or the "
+                         "general pass kernels (paired-general / general)")
     ap.add_argument("--skip-extra", action="store_true", help="skip the uneven-batch and training lines")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle CPU work")

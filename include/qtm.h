@@ -337,16 +337,19 @@ int qtm_get_sample_pairing(const qtm_plan *plan);
  * on disk under $QTM_JIT_CACHE, default /tmp/qtm_jit_cache) and loaded on the
  * current device; later qtm_forward / qtm_adjoint / qtm_jacobian calls on that
  * device launch them in place of the general pass kernel.  Kinds (flags): 0
- * (default), one sample per CTA with the thread's amplitudes paired in
- * Blackwell's f32x2 registers (paired fma / mul / add); QTM_COMPILE_SCALAR,
- * one sample per CTA with scalar FP32 registers; QTM_COMPILE_SAMPLE_PAIRS, two
- * samples per CTA, one per half of each f32x2 register pair.  Applies
+ * (default), one sample per CTA with each complex amplitude one of Blackwell's
+ * f32x2 register pairs (re, im; paired fma / mul / add);
+ * QTM_COMPILE_SCALAR, one sample per CTA with scalar FP32 registers;
+ * QTM_COMPILE_SAMPLE_PAIRS, two samples per CTA, one per half of each f32x2
+ * register pair; QTM_COMPILE_LANE_PAIRS, one sample per CTA with two
+ * amplitudes (one register bit apart) per f32x2 pair.  Applies
  * to complex64 fused plans with tiles of >= 9 qubits (QTM_EUNSUPPORTED
  * otherwise, or when NVRTC is unavailable; the plan keeps the general
  * kernels).  Synchronises the device and drops the workspace and any stored
  * forward state (the state layout changes). */
 #define QTM_COMPILE_SCALAR 1
 #define QTM_COMPILE_SAMPLE_PAIRS 2
+#define QTM_COMPILE_LANE_PAIRS 3
 qtm_status qtm_compile(qtm_plan *plan, int flags);
 
 /* Number of specialised pass kernels loaded for the current device (0 before

@@ -24,7 +24,9 @@ QTM_PATH_AUTO, QTM_PATH_FUSED, QTM_PATH_NAIVE = 0, 1, 2
 QTM_ADJ_GW_PER_SAMPLE, QTM_ADJ_RECOMPUTE = 1, 2
 QTM_COMPILE_SCALAR = 1
 QTM_COMPILE_SAMPLE_PAIRS = 2
-_COMPILE_KIND = {"lanes": 0, "one": QTM_COMPILE_SCALAR, "pairs": QTM_COMPILE_SAMPLE_PAIRS}
+QTM_COMPILE_LANE_PAIRS = 3
+_COMPILE_KIND = {"cpx": 0, "one": QTM_COMPILE_SCALAR, "pairs": QTM_COMPILE_SAMPLE_PAIRS,
+                 "lanes": QTM_COMPILE_LANE_PAIRS}
 
 
 class qtm_gate(ctypes.Structure):
@@ -320,11 +322,12 @@ class Plan:
         self._raise(st, "qtm_adjoint")
         return gx, gw
 
-    def compile(self, kind: str = "lanes"):
+    def compile(self, kind: str = "cpx"):
         """Specialise and load this plan's pass kernels (qtm_compile).  kind:
-        "lanes" (default: one sample per CTA, amplitudes paired in f32x2
-        registers), "one" (one sample per CTA, scalar registers) or "pairs"
-        (two samples per CTA on f32x2 register pairs)."""
+        "cpx" (default: one sample per CTA, each complex amplitude one f32x2
+        register pair), "lanes" (one sample per CTA, two amplitudes per f32x2
+        pair), "one" (one sample per CTA, scalar registers) or "pairs" (two
+        samples per CTA on f32x2 register pairs)."""
         self._raise(lib().qtm_compile(self.handle, _COMPILE_KIND[kind]), "qtm_compile")
         return self
 
@@ -345,10 +348,10 @@ class Plan:
     def compiled_passes(self) -> int:
         return int(lib().qtm_compiled_passes(self.handle))
 
-    def jit_source(self, which: int, index: int, kind: str = "lanes") -> str:
+    def jit_source(self, which: int, index: int, kind: str = "cpx") -> str:
         return lib().qtm_debug_jit_source(self.handle, int(which), int(index), _COMPILE_KIND[kind]).decode()
 
-    def jit_compile_check(self, kind: str = "lanes"):
+    def jit_compile_check(self, kind: str = "cpx"):
         """Compile every specialised pass with NVRTC, host only (no load)."""
         self._raise(lib().qtm_debug_jit_compile(self.handle, _COMPILE_KIND[kind]), "qtm_debug_jit_compile")
 

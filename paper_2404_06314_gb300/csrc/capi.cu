@@ -891,7 +891,10 @@ namespace {
 // Generate and compile every pass (host only; NVRTC, no device).
 JitMode jit_mode(int flags)
 {
-    return flags == QTM_COMPILE_SAMPLE_PAIRS ? JIT_PAIRS : flags == QTM_COMPILE_SCALAR ? JIT_ONE : JIT_LANES;
+    return flags == QTM_COMPILE_SAMPLE_PAIRS ? JIT_PAIRS
+           : flags == QTM_COMPILE_SCALAR     ? JIT_ONE
+           : flags == QTM_COMPILE_LANE_PAIRS ? JIT_LANES
+                                             : JIT_CPX;
 }
 
 qtm_status compile_all(qtm_plan *p, JitMode mode, std::vector<std::vector<char>> &fwd_bin,
@@ -978,7 +981,8 @@ qtm_status qtm_compile(qtm_plan *p, int flags)
         }
         return QTM_OK;
     }
-    if (flags != 0 && flags != QTM_COMPILE_SCALAR && flags != QTM_COMPILE_SAMPLE_PAIRS)
+    if (flags != 0 && flags != QTM_COMPILE_SCALAR && flags != QTM_COMPILE_SAMPLE_PAIRS &&
+        flags != QTM_COMPILE_LANE_PAIRS)
         return fail(p, QTM_EINVAL, "unknown flags");
     if (!jit_available()) return fail(p, QTM_EUNSUPPORTED, "NVRTC or driver entry points not available");
     const JitMode mode = jit_mode(flags);
@@ -1012,7 +1016,9 @@ qtm_status qtm_compile(qtm_plan *p, int flags)
         const auto &gsm = rev ? p->smem_rev : p->smem_fwd;
         for (size_t i = 0; i < pds.size(); ++i) {
             const int smem = (int)(pairs ? jit_smem_bytes_x2(P, pds[i])
-                                         : mode == JIT_LANES ? jit_smem_bytes_lanes(P, pds[i]) : gsm[i]);
+                                         : mode == JIT_LANES ? jit_smem_bytes_lanes(P, pds[i])
+                                         : mode == JIT_CPX   ? jit_smem_bytes_cpx(P, pds[i])
+                                                             : gsm[i]);
             if ((size_t)smem > kMaxDynSmem) {
                 unload_all();
                 return fail(p, QTM_EUNSUPPORTED, "specialised kernel needs more shared memory than a CTA has");

@@ -316,10 +316,9 @@ void lanes_op(std::ostringstream &o, const Plan &P, const PassDesc &pd, int k, i
         o << "        { float vx, vy, vz; "
           << (rb == sl ? std::string("grad_lanes_s(") : "grad_lanes<SB, " + std::to_string(rb) + ">(")
           << "p, q, vx, vy, vz);"
-          << " vx = warp_sum(vx, 32, 0xffffffffu); vy = warp_sum(vy, 32, 0xffffffffu);"
-          << " vz = warp_sum(vz, 32, 0xffffffffu);"
-          << " if (lane == 0) { float *g = S.redG + warp * " << 3 * nslots << " + 3 * " << slot
-          << "; g[0] = vx; g[1] = vy; g[2] = vz; }";
+          << " const float v = warp_sum3(vx, vy, vz, lane);"
+          << " if ((lane & 7) == 0 && lane < 24) S.redG[warp * " << 3 * nslots << " + 3 * " << slot
+          << " + (lane >> 3)] = v;";
         if (!(op.flags & OPF_SKIP_APPLY)) o << " " << apply << "p, " << tab << "); " << apply << "q, " << tab << ");";
         o << " }\n";
         break;
@@ -428,6 +427,122 @@ bool lanes_threaded()
 // Body of one phase with its run slots written relative to the phase's first
 // slot `sb` (a runtime value): layers of a layered circuit repeat the same
 // body with other slots and then share one copy of the code.
+// ---- complex-pair one-sample kernels (tile_cpx.cuh) ----------------------------------
+
+constexpr int kCpxSlotPairsHost = 8;   // f32x2 pairs per run slot in the complex-pair table
+
+void gen_expval_cpx(std::ostringstream &o, const Plan &P, const PassDesc &pd, int lo)
+{
+    // per register sign pattern rm: sum of |p_jj|^2 with sign (-1)^popc(jj & rm),
+    // as two FMA chains (plus / minus) straight from the amplitudes
+    o << "        {\n";
+    std::vector<int> seen(16, 0);
+    for (const Term &t : P.terms) {
+        const int rm = (int)((local_mask(pd, t.zmask) >> lo) & 15u);
+        if (seen[rm]) continue;
+        seen[rm] = 1;
+        std::string pos = "", neg = "";
+        for (int jj = 0; jj < 16; ++jj) {
+            std::string &acc = (__builtin_popcount(jj & rm) & 1) ? neg : pos;
+            const std::string pj = "p[" + std::to_string(jj) + "]";
+            acc = acc.empty() ? "mul2(" + pj + ", " + pj + ")" : "fma2(" + pj + ", " + pj + ", " + acc + ")";
+        }
+        o << "            const f2 a" << rm << " = " << (neg.empty() ? pos : "sub2(" + pos + ", " + neg + ")") << ";\n";
+        o << "            const float s" << rm << " = lane0(a" << rm << ") + lane1(a" << rm << ");\n";
+    }
+    for (int m = 0; m < P.n_obs; ++m) {
+        bool any = false;
+        for (size_t t = 0; t < P.terms.size(); ++t) {
+            if (P.terms[t].obs != m) continue;
+            if (!any) o << "            { float e = 0.f;\n";
+            any = true;
+            const uint32_t lm = local_mask(pd, P.terms[t].zmask);
+            const int rm = (int)((lm >> lo) & 15u);
+            o << "              e = fmaf((__popc(xt & 0x" << std::hex << lm << std::dec << "u) & 1u) ? -S.tcoef[" << t
+              << "] : S.tcoef[" << t << "], s" << rm << ", e);\n";
+        }
+        if (any)
+            o << "              e = warp_sum(e, 32, 0xffffffffu); if (lane == 0) S.redE[warp * " << P.n_obs << " + "
+              << m << "] = e; }\n";
+    }
+    o << "        }\n";
+}
+
+void gen_costate_cpx(std::ostringstream &o, const Plan &P, const PassDesc &pd, int lo)
+{
+    o << "        {\n";
+    std::vector<std::vector<size_t>> by_rm(16);
+    for (size_t t = 0; t < P.terms.size(); ++t) by_rm[(local_mask(pd, P.terms[t].zmask) >> lo) & 15u].push_back(t);
+    std::vector<int> rms;
+    for (int rm = 0; rm < 16; ++rm) {
+        if (by_rm[rm].empty()) continue;
+        rms.push_back(rm);
+        o << "            const float c" << rm << " = 0.f";
+        for (size_t t : by_rm[rm])
+            o << " + ((__popc(xt & 0x" << std::hex << local_mask(pd, P.terms[t].zmask) << std::dec
+              << "u) & 1u) ? -S.tcoef[" << t << "] : S.tcoef[" << t << "])";
+        o << ";\n";
+    }
+    for (int jj = 0; jj < 16; ++jj) {
+        std::string e = "0.f";
+        for (int rm : rms) e += std::string(__builtin_popcount(jj & rm) & 1 ? " - c" : " + c") + std::to_string(rm);
+        o << "            { const float d = " << e << "; q[" << jj << "] = mul2(pack2(d, d), p[" << jj << "]); }\n";
+    }
+    o << "        }\n";
+}
+
+// One op of a complex-pair phase (register group lo); `slot` is the C
+// expression of its run slot.
+void cpx_op(std::ostringstream &o, const Plan &P, const PassDesc &pd, int k, int lo, const std::string &slot)
+{
+    const bool rev = pd.reverse != 0;
+    const int nslots = pd.slot_end - pd.slot_begin;
+    const DevOp &op = P.ops[k];
+    const bool reg_a = has_reg_bit(op.a, lo);
+    const bool reg_b = has_reg_bit(op.b, lo);
+    if (((op.type == OP_U2 || op.type == OP_GRAD) && !reg_a) || (op.type == OP_CNOT && !reg_b) ||
+        ((op.type == OP_U2 || op.type == OP_GRAD) && (op.slot < 0 || op.slot >= nslots)) ||
+        (op.type == OP_DIAG && (op.a < 0 || op.a + op.b > (int)P.diag_pairs.size()))) {
+        o << "#error \"op " << k << " has an operand outside its phase\"\n";
+        return;
+    }
+    const int rb = op.a - lo;
+    const std::string tab = "CT + " + std::to_string(kCpxSlotPairsHost) + " * " + slot;
+    switch (op.type) {
+    case OP_U2:
+        o << "        u2_cpx<" << rb << ">(p, " << tab << ");\n";
+        break;
+    case OP_GRAD:
+        o << "        { float vx, vy, vz; grad_cpx<" << rb << ">(p, q, vx, vy, vz);"
+          << " const float v = warp_sum3(vx, vy, vz, lane);"
+          << " if ((lane & 7) == 0 && lane < 24) S.redG[warp * " << 3 * nslots << " + 3 * " << slot
+          << " + (lane >> 3)] = v;";
+        if (!(op.flags & OPF_SKIP_APPLY))
+            o << " u2_cpx<" << rb << ">(p, " << tab << "); u2_cpx<" << rb << ">(q, " << tab << ");";
+        o << " }\n";
+        break;
+    case OP_DIAG:
+        o << "        { " << diag_mask(P, op, lo) << " flip_cpx<" << (rev ? "true" : "false") << ">(p, q, m); }\n";
+        break;
+    case OP_CNOT: {
+        const int rt = op.b - lo;
+        if (has_reg_bit(op.a, lo)) {
+            o << "        cnot_static_cpx<" << (op.a - lo) << ", " << rt << ">(p);";
+            if (rev) o << " cnot_static_cpx<" << (op.a - lo) << ", " << rt << ">(q);";
+            o << "\n";
+        } else {
+            o << "        { const int c = (int)(" << operand_bit(op.a) << " & 1u); cnot_cpx<" << rt << ">(p, c);";
+            if (rev) o << " cnot_cpx<" << rt << ">(q, c);";
+            o << " }\n";
+        }
+        break;
+    }
+    case OP_EXPVAL: gen_expval_cpx(o, P, pd, lo); break;
+    case OP_COSTATE: gen_costate_cpx(o, P, pd, lo); break;
+    default: break;
+    }
+}
+
 std::string phase_body(const Plan &P, const PassDesc &pd, const DevPhase &phs, bool lam_valid, JitMode mode, int sb)
 {
     const bool rev = pd.reverse != 0;
@@ -438,6 +553,12 @@ std::string phase_body(const Plan &P, const PassDesc &pd, const DevPhase &phs, b
     auto slot = [&](int s) { return "(sb + " + std::to_string(s - sb) + ")"; };
     o << "        constexpr int LO = " << lo << ";\n";
     o << "        const uint32_t xt = ((uint32_t)tid & ((1u << LO) - 1u)) | (((uint32_t)tid >> LO) << (LO + 4));\n";
+    if (mode == JIT_CPX) {
+        o << "        regs_load_cpx<LO, " << (lam_valid ? "true" : "false") << ">(p, q, S, xt);\n";
+        for (int k = phs.op_begin; k < phs.op_end; ++k) cpx_op(o, P, pd, k, lo, slot(P.ops[k].slot));
+        o << "        regs_store_cpx<LO, " << (rev ? "true" : "false") << ">(p, q, S, xt);\n";
+        return o.str();
+    }
     if (mode == JIT_LANES) {
         const int sl = choose_lane_bit(P, phs);
         o << "        constexpr int SB = " << sl << ";\n";
@@ -476,10 +597,9 @@ std::string phase_body(const Plan &P, const PassDesc &pd, const DevPhase &phs, b
                 o << " }\n";
             } else {
                 o << "        { R vx = 0, vy = 0, vz = 0; grad_acc<" << rb << ">(p, q, vx, vy, vz);"
-                  << " vx = warp_sum(vx, 32, 0xffffffffu); vy = warp_sum(vy, 32, 0xffffffffu);"
-                  << " vz = warp_sum(vz, 32, 0xffffffffu);"
-                  << " if (lane == 0) { R *g = S.redG + warp * " << 3 * nslots << " + 3 * " << slot(op.slot)
-                  << "; g[0] = vx; g[1] = vy; g[2] = vz; }";
+                  << " const R v = warp_sum3(vx, vy, vz, lane);"
+                  << " if ((lane & 7) == 0 && lane < 24) S.redG[warp * " << 3 * nslots << " + 3 * " << slot(op.slot)
+                  << " + (lane >> 3)] = v;";
                 if (!(op.flags & OPF_SKIP_APPLY))
                     o << " u2<" << rb << ">(p, S.mats + 4 * " << slot(op.slot) << "); u2<" << rb << ">(q, S.mats + 4 * "
                       << slot(op.slot) << ");";
@@ -584,6 +704,12 @@ std::string jit_source(const Plan &P, const PassDesc &pd, int min_blocks, JitMod
     if (pairs)
         o << "__device__ __forceinline__ void gen_phases(const TileJobX2 &j, const TileSmemX2 &S)\n{\n"
           << "    using R = float;\n    A2 p[kRegs];\n    A2 q[kRegs];\n";
+    else if (mode == JIT_CPX)
+        o << "template <typename R>\n__device__ __forceinline__ void gen_phases(const TileJob &j, const TileSmem<R> &S, "
+             "bool)\n{\n    f2 p[kRegs];\n    f2 q[kRegs];\n"
+          << "    // complex-pair matrix table after the tile program's shared memory\n"
+          << "    f2 *CT = reinterpret_cast<f2 *>(reinterpret_cast<unsigned char *>(S.phi) + " << lane_table_offset(P, pd)
+          << ");\n    stage_cpx_table(S.mats, CT, " << nslots << ");\n    __syncthreads();\n";
     else if (mode == JIT_LANES)
         o << "template <typename R>\n__device__ __forceinline__ void gen_phases(const TileJob &j, const TileSmem<R> &S, "
              "bool)\n{\n    A2 p[kLanePairs];\n    A2 q[kLanePairs];\n"
@@ -627,6 +753,11 @@ std::string jit_source(const Plan &P, const PassDesc &pd, int min_blocks, JitMod
 size_t jit_smem_bytes_lanes(const Plan &P, const PassDesc &pd)
 {
     return lane_table_offset(P, pd) + 1024 + (size_t)8 * kLaneSlotPairsHost * std::max(1, pd.slot_end - pd.slot_begin);
+}
+
+size_t jit_smem_bytes_cpx(const Plan &P, const PassDesc &pd)
+{
+    return lane_table_offset(P, pd) + 1024 + (size_t)8 * kCpxSlotPairsHost * std::max(1, pd.slot_end - pd.slot_begin);
 }
 
 size_t jit_smem_bytes_x2(const Plan &P, const PassDesc &pd)

@@ -25,13 +25,15 @@ bool jit_available();
 bool jit_nvrtc_available();
 // Kinds of specialised kernel: two samples per CTA on f32x2 register pairs
 // (tile_x2.cuh); one sample per CTA with scalar registers (tile.cuh); one
-// sample per CTA with amplitudes paired in f32x2 registers (tile_lanes.cuh).
-enum JitMode { JIT_PAIRS = 0, JIT_ONE = 1, JIT_LANES = 2 };
+// sample per CTA with amplitudes paired in f32x2 registers (tile_lanes.cuh);
+// one sample per CTA with each complex amplitude one f32x2 pair (tile_cpx.cuh).
+enum JitMode { JIT_PAIRS = 0, JIT_ONE = 1, JIT_LANES = 2, JIT_CPX = 3 };
 
 // Generated source of one pass.
 std::string jit_source(const Plan &P, const PassDesc &pd, int min_blocks, JitMode mode);
 size_t jit_smem_bytes_x2(const Plan &P, const PassDesc &pd);
 size_t jit_smem_bytes_lanes(const Plan &P, const PassDesc &pd);
+size_t jit_smem_bytes_cpx(const Plan &P, const PassDesc &pd);
 bool jit_compile(const std::string &body, std::vector<char> &cubin, std::string &log);
 bool jit_load(const std::vector<char> &cubin, int smem, JitKernel &k, std::string &err);
 void jit_unload(JitKernel &k);

@@ -268,6 +268,25 @@ __device__ __forceinline__ R warp_sum(R v, int width, unsigned mask)
     return v;
 }
 
+// Full-warp sums of three values in one butterfly of 6 shuffles instead of 15:
+// the first level trades half the values (lanes 0-15 keep a and b, lanes
+// 16-31 keep c and a zero pad), the second level half of what is left, and
+// three more levels sum the single value.  Lanes 0, 8 and 16 end with the
+// sums of a, b and c.
+template <typename R>
+__device__ __forceinline__ R warp_sum3(R a, R b, R c, int lane)
+{
+    const bool hi = (lane & 16) != 0;
+    const R x0 = (hi ? c : a) + __shfl_xor_sync(0xffffffffu, hi ? a : c, 16);
+    const R x1 = (hi ? (R)0 : b) + __shfl_xor_sync(0xffffffffu, hi ? b : (R)0, 16);
+    const bool h8 = (lane & 8) != 0;
+    R y = (h8 ? x1 : x0) + __shfl_xor_sync(0xffffffffu, h8 ? x0 : x1, 8);
+    y += __shfl_xor_sync(0xffffffffu, y, 4);
+    y += __shfl_xor_sync(0xffffffffu, y, 2);
+    y += __shfl_xor_sync(0xffffffffu, y, 1);
+    return y;
+}
+
 // Shared-memory layout of a pass CTA (offsets from a 1024-byte aligned base).
 struct Layout {
     int phi, lam, mats, tabs, tmask, tcoef, tobs, ents, redE, redG, bar, total;

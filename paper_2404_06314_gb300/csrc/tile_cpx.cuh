@@ -1,0 +1,190 @@
+// Complex-pair registers for the one-sample specialised pass kernels.
+//
+// A thread's 16 amplitudes (register bits [lo, lo+4) of a phase) are held as
+// 16 f32x2 register pairs, each one complex amplitude (re, im): the layout of
+// the amplitude in shared memory, so loads and stores move whole pairs.  A
+// complex product is two f32x2 instructions on the pair and its lane swap:
+//     u x = (u.re, u.re) * (x.re, x.im) + (-u.im, u.im) * (x.im, x.re),
+// and Blackwell's f32x2 FMA takes the swapped operand without a register move.
+// Every register bit is then alike (no lane bit as in tile_lanes.cuh): a gate
+// on register bit RB pairs whole registers, a CNOT permutes them, a CZ sign
+// flips both lanes of a register.  The sample, the shared-memory layout and
+// the tile program (tile.cuh) are those of the one-sample kernel.
+#pragma once
+
+#include "tile_lanes.cuh"
+
+namespace qtm {
+
+namespace {
+
+constexpr int kCpxSlotPairs = 8;   // per run slot, for e = u00, u01, u10, u11: (e.re, e.re), (-e.im, e.im)
+
+// Complex-pair table of every run slot from the staged matrices (U or U^dagger).
+__device__ __forceinline__ void stage_cpx_table(const Cx<float> *mats, f2 *tab, int nslots)
+{
+    for (int s = threadIdx.x; s < nslots; s += blockDim.x) {
+        f2 *t = tab + kCpxSlotPairs * s;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const Cx<float> e = mats[4 * s + k];
+            t[2 * k] = pack2(e.x, e.x);
+            t[2 * k + 1] = pack2(-e.y, e.y);
+        }
+    }
+}
+
+// Shared-space accesses of one amplitude (8 bytes) or two neighbouring ones (16 bytes).
+__device__ __forceinline__ f2 lds_f2(uint32_t addr)
+{
+    f2 v;
+    asm volatile("ld.shared.b64 %0, [%1];" : "=l"(v) : "r"(addr));
+    return v;
+}
+__device__ __forceinline__ void lds_f2x2(uint32_t addr, f2 &a, f2 &b)
+{
+    asm volatile("ld.shared.v2.b64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "r"(addr));
+}
+__device__ __forceinline__ void sts_f2(uint32_t addr, f2 v)
+{
+    asm volatile("st.shared.b64 [%0], %1;" ::"r"(addr), "l"(v) : "memory");
+}
+__device__ __forceinline__ void sts_f2x2(uint32_t addr, f2 a, f2 b)
+{
+    asm volatile("st.shared.v2.b64 [%0], {%1, %2};" ::"r"(addr), "l"(a), "l"(b) : "memory");
+}
+
+// Registers <-> shared tile for register group LO (compile time).  Group 0:
+// two neighbouring amplitudes per 16-byte access (the swizzle keeps 16-byte
+// chunks whole); other groups: one 8-byte access per amplitude.
+template <int LO, bool LAM>
+__device__ __forceinline__ void regs_load_cpx(f2 (&p)[kRegs], f2 (&q)[kRegs], const TileSmem<float> &T, uint32_t xt)
+{
+    const uint32_t ph = smem_u32(T.phi), lm = smem_u32(T.lam);
+    if constexpr (LO == 0) {
+#pragma unroll
+        for (int k = 0; k < kRegs / 2; ++k) {
+            const uint32_t o = 8u * (uint32_t)swz<float>((int)xt + 2 * k);
+            lds_f2x2(ph + o, p[2 * k], p[2 * k + 1]);
+            if (LAM) lds_f2x2(lm + o, q[2 * k], q[2 * k + 1]);
+        }
+    } else {
+#pragma unroll
+        for (int jj = 0; jj < kRegs; ++jj) {
+            const uint32_t o = 8u * (uint32_t)swz<float>((int)(xt | ((uint32_t)jj << LO)));
+            p[jj] = lds_f2(ph + o);
+            if (LAM) q[jj] = lds_f2(lm + o);
+        }
+    }
+}
+
+template <int LO, bool LAM>
+__device__ __forceinline__ void regs_store_cpx(const f2 (&p)[kRegs], const f2 (&q)[kRegs], const TileSmem<float> &T,
+                                               uint32_t xt)
+{
+    const uint32_t ph = smem_u32(T.phi), lm = smem_u32(T.lam);
+    if constexpr (LO == 0) {
+#pragma unroll
+        for (int k = 0; k < kRegs / 2; ++k) {
+            const uint32_t o = 8u * (uint32_t)swz<float>((int)xt + 2 * k);
+            sts_f2x2(ph + o, p[2 * k], p[2 * k + 1]);
+            if (LAM) sts_f2x2(lm + o, q[2 * k], q[2 * k + 1]);
+        }
+    } else {
+#pragma unroll
+        for (int jj = 0; jj < kRegs; ++jj) {
+            const uint32_t o = 8u * (uint32_t)swz<float>((int)(xt | ((uint32_t)jj << LO)));
+            sts_f2(ph + o, p[jj]);
+            if (LAM) sts_f2(lm + o, q[jj]);
+        }
+    }
+}
+
+// a <- U a on register bit RB: per register pair (x0, x1),
+// y0 = u00 x0 + u01 x1, y1 = u10 x0 + u11 x1.
+template <int RB>
+__device__ __forceinline__ void u2_cpx(f2 (&a)[kRegs], const f2 *t)
+{
+    f2 A_r, A_n, B_r, B_n, C_r, C_n, D_r, D_n;
+    lds_table2<true>(t, A_r, A_n); lds_table2<true>(t + 2, B_r, B_n);
+    lds_table2<true>(t + 4, C_r, C_n); lds_table2<true>(t + 6, D_r, D_n);
+#pragma unroll
+    for (int j = 0; j < kRegs; ++j) {
+        if (j & (1 << RB)) continue;
+        const f2 x0 = a[j], x1 = a[j | (1 << RB)];
+        const f2 s0 = swap2(x0), s1 = swap2(x1);
+        a[j] = fma2(A_r, x0, fma2(A_n, s0, fma2(B_r, x1, mul2(B_n, s1))));
+        a[j | (1 << RB)] = fma2(C_r, x0, fma2(C_n, s0, fma2(D_r, x1, mul2(D_n, s1))));
+    }
+}
+
+// (vx, vy, vz) on register bit RB, the same sums as grad_acc in tile.cuh:
+// with b = lam and a = phi, Im(conj(b) a) = lane0 - lane1 of b * swap(a) and
+// Re(conj(b) a) = lane0 + lane1 of b * a.
+template <int RB>
+__device__ __forceinline__ void grad_cpx(const f2 (&a)[kRegs], const f2 (&b)[kRegs], float &vx, float &vy, float &vz)
+{
+    f2 zp, zn, xp, xq, yp, yn;
+#pragma unroll
+    for (int j = 0, first = 1; j < kRegs; ++j) {
+        if (j & (1 << RB)) continue;
+        const f2 a0 = a[j], a1 = a[j | (1 << RB)], b0 = b[j], b1 = b[j | (1 << RB)];
+        const f2 s0 = swap2(a0), s1 = swap2(a1);
+        if (first) {   // the first pair starts the accumulators (no zero fill)
+            zp = mul2(b0, s0); zn = mul2(b1, s1);
+            xp = mul2(b0, s1); xq = mul2(b1, s0);
+            yp = mul2(b1, a0); yn = mul2(b0, a1);
+            first = 0;
+        } else {
+            zp = fma2(b0, s0, zp); zn = fma2(b1, s1, zn);
+            xp = fma2(b0, s1, xp); xq = fma2(b1, s0, xq);
+            yp = fma2(b1, a0, yp); yn = fma2(b0, a1, yn);
+        }
+    }
+    const f2 Z = sub2(zp, zn), X = add2(xp, xq), Y = sub2(yp, yn);
+    vz = lane0(Z) - lane1(Z);
+    vx = lane0(X) - lane1(X);
+    vy = lane0(Y) + lane1(Y);
+}
+
+// CNOT with control and target both register bits: a fixed register permutation.
+template <int RC, int RT>
+__device__ __forceinline__ void cnot_static_cpx(f2 (&a)[kRegs])
+{
+#pragma unroll
+    for (int jj = 0; jj < kRegs; ++jj) {
+        if ((jj & (1 << RT)) || !(jj & (1 << RC))) continue;
+        const f2 t = a[jj];
+        a[jj] = a[jj | (1 << RT)];
+        a[jj | (1 << RT)] = t;
+    }
+}
+
+// CNOT on target register bit RT with a control bit c known per thread.
+template <int RT>
+__device__ __forceinline__ void cnot_cpx(f2 (&a)[kRegs], int c)
+{
+#pragma unroll
+    for (int j = 0; j < kRegs; ++j) {
+        if (j & (1 << RT)) continue;
+        const f2 t0 = a[j], t1 = a[j | (1 << RT)];
+        a[j] = c ? t1 : t0;
+        a[j | (1 << RT)] = c ? t0 : t1;
+    }
+}
+
+// Negate amplitude jj where bit jj of m is set (phi, and lam in reverse).
+template <bool REV>
+__device__ __forceinline__ void flip_cpx(f2 (&p)[kRegs], f2 (&q)[kRegs], uint32_t m)
+{
+#pragma unroll
+    for (int jj = 0; jj < kRegs; ++jj) {
+        const f2 s = (f2)((m >> jj) & 1u) * kSign2;   // both lanes' sign bits, or 0
+        p[jj] ^= s;
+        if (REV) q[jj] ^= s;
+    }
+}
+
+}  // namespace
+
+}  // namespace qtm

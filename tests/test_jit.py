@@ -1,8 +1,10 @@
 """Run-time specialised pass kernels (qtm_compile).
 
-Three kinds of specialised kernel: lane-paired (default; one sample per CTA,
-the thread's amplitudes paired in f32x2 registers), scalar one-sample, and
-sample-paired (two samples per CTA, one per half of an f32x2 register pair).
+Four kinds of specialised kernel: lane-paired (default; one sample per CTA,
+the thread's amplitudes paired in f32x2 registers), complex-paired (one
+sample per CTA, each complex amplitude one f32x2 pair), scalar one-sample,
+and sample-paired (two samples per CTA, one per half of an f32x2 register
+pair).
 
 Host part (no GPU): the source written for every pass of the benchmark
 workloads and of random circuits compiles with NVRTC for sm_103a in both
@@ -46,7 +48,7 @@ def _nvrtc_kind_or_skip(plan, kind):
         raise
 
 
-@pytest.mark.parametrize("kind", ["pairs", "one", "lanes"])
+@pytest.mark.parametrize("kind", ["pairs", "one", "lanes", "cpx"])
 def test_generated_source_compiles_benchmarks(kind):
     for c in [W.workload_12q(), W.workload_20q(), W.workload_16q_train()]:
         plan = capi.Plan(c, dtype="c64")
@@ -57,6 +59,7 @@ def test_generated_source_compiles_benchmarks(kind):
                 assert "qtm_gen_pass" in src and "gen_phases" in src, (c.name, which, i)
                 assert ("pass_body_x2" in src) == (kind == "pairs")
                 assert ("regs_load_lanes" in src) == (kind == "lanes")
+                assert ("regs_load_cpx" in src) == (kind == "cpx")
                 assert "#error" not in src
         _nvrtc_kind_or_skip(plan, kind)
 
@@ -66,6 +69,7 @@ def test_generated_source_compiles_random(n):
     plan = capi.Plan(_rand(n, 500 + n), dtype="c64")
     _nvrtc_or_skip(plan, "pairs")
     _nvrtc_kind_or_skip(plan, "lanes")
+    _nvrtc_kind_or_skip(plan, "cpx")
 
 
 def test_not_specialised():
@@ -98,7 +102,7 @@ def _circuit(name):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("kind", ["pairs", "one", "lanes"])
+@pytest.mark.parametrize("kind", ["pairs", "one", "lanes", "cpx"])
 @pytest.mark.parametrize("name,B", CASES)
 def test_compiled_plan_matches_oracle(name, B, kind):
     c = _circuit(name)
@@ -213,7 +217,7 @@ def test_paired_general_jacobian_and_toggle():
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("kind", ["lanes", "one", "pairs"])
+@pytest.mark.parametrize("kind", ["lanes", "cpx", "one", "pairs"])
 @pytest.mark.parametrize("n", [9, 12, 14])
 def test_compiled_plan_with_h_and_rzz(n, kind):
     rng = np.random.default_rng(950 + n)

@@ -444,13 +444,40 @@ qtm_status run_prep(qtm_plan *p, int B, const void *x, const void *w, cudaStream
     return QTM_OK;
 }
 
+// Plans of one tile per sample run the per-sample prep inside their first
+// forward pass and the gradient finalize inside their last reverse pass (one
+// CTA holds a whole sample); the two-samples-per-CTA kernels keep them apart.
+// QTM_FUSE_SAMPLE_STEPS=0 (a tuning switch) keeps them apart always.
+bool fuse_sample_steps(const qtm_plan *p)
+{
+    const char *e = std::getenv("QTM_FUSE_SAMPLE_STEPS");
+    if (e && *e == '0') return false;
+    return p->P.path == QTM_PATH_FUSED && p->P.tiles_per_sample == 1 && !use_x2(p);
+}
+
+void set_prep_fields(qtm_plan *p, PassArgs &a)
+{
+    const Plan &P = p->P;
+    a.runs = p->d_runs; a.rots = p->d_rots; a.prq = p->d_prefix_run_of_q;
+    a.cs = p->d_cs; a.n_rots = (int)P.rots.size(); a.n_weights = P.n_weights;
+    a.w_ptr = p->d_w_ptr; a.w_rots = p->d_w_rots; a.x_ptr = p->d_x_ptr; a.x_rots = p->d_x_rots;
+    a.abar = p->d_abar;
+}
+
 qtm_status run_forward_passes(qtm_plan *p, int B, const void *x, const void *w, cudaStream_t s)
 {
     const Plan &P = p->P;
-    qtm_status st = run_prep(p, B, x, w, s);
-    if (st != QTM_OK) return st;
+    const bool fused = fuse_sample_steps(p) && !P.fwd.empty();
+    if (!fused) {
+        qtm_status st = run_prep(p, B, x, w, s);
+        if (st != QTM_OK) return st;
+    }
     for (size_t i = 0; i < P.fwd.size(); ++i) {
         PassArgs a = pass_args(p, P.fwd[i], p->g_fwd[i], p->smem_fwd[i], B, x, w, nullptr);
+        if (fused && i == 0) {
+            set_prep_fields(p, a);
+            a.prep_fused = 1;
+        }
         ProfScope ps(p, 0);
         cudaError_t e = launch_any(p, false, i, a, p->tm_fwd[i], p->tm_fwd[i], s);
         if (e != cudaSuccess) return cuda_fail(p, e, "forward pass launch");
@@ -815,22 +842,32 @@ qtm_status qtm_adjoint(qtm_plan *p, int B, const void *gE, const void *x, const 
         if (st != QTM_OK) return st;
     }
     bool consumes = false;
+    const bool fused = fuse_sample_steps(p) && !P.rev.empty();
     for (size_t i = 0; i < P.rev.size(); ++i) {
         PassArgs a = pass_args(p, P.rev[i], p->g_rev[i], p->smem_rev[i], B, x, w, gE);
+        if (fused && i + 1 == P.rev.size()) {
+            set_prep_fields(p, a);
+            a.finalize_fused = 1;
+            a.gx = gx;
+            a.gw_out = per_sample ? gw : nullptr;
+            a.gw_ws = (!per_sample && gw) ? p->d_gw_ws : nullptr;
+        }
         if (P.rev[i].store_phi) consumes = true;
         ProfScope ps(p, 0);
         e = launch_any(p, true, i, a, p->tm_rev_phi[i], p->tm_rev_lam[i], s);
         if (e != cudaSuccess) return cuda_fail(p, e, "reverse pass launch");
     }
-    FinalizeArgs f = finalize_args(p, B, x, w);
-    f.gx = gx;
-    f.gw_out = per_sample ? gw : nullptr;
-    f.gw_ws = (!per_sample && gw) ? p->d_gw_ws : nullptr;
-    {
-        ProfScope ps(p, 1);
-        e = launch_grad_finalize(P.dtype, f, s);
+    if (!fused) {
+        FinalizeArgs f = finalize_args(p, B, x, w);
+        f.gx = gx;
+        f.gw_out = per_sample ? gw : nullptr;
+        f.gw_ws = (!per_sample && gw) ? p->d_gw_ws : nullptr;
+        {
+            ProfScope ps(p, 1);
+            e = launch_grad_finalize(P.dtype, f, s);
+        }
+        if (e != cudaSuccess) return cuda_fail(p, e, "gradient finalize");
     }
-    if (e != cudaSuccess) return cuda_fail(p, e, "gradient finalize");
     if (!per_sample && gw) {
         ProfScope ps(p, 1);
         e = launch_gw_reduce(P.dtype, p->d_gw_ws, B, P.n_weights, gw, s);

@@ -200,6 +200,22 @@ struct PassArgs {
     double *Gpart;                // [B][n_runs][tiles][3]
     unsigned *status;
     int smem_bytes;
+    // Per-sample steps fused into the pass (plans of one tile per sample,
+    // where a CTA holds a whole sample): prep_fused, the first forward pass
+    // also computes its sample's run matrices, product-state tables and half
+    // angles (mats, tabs, cs; as k_prep); finalize_fused, the last reverse
+    // pass also turns its sample's run sums into angle gradients and applies
+    // the chain rule (abar, gx, gw_out / gw_ws; as k_grad_finalize).
+    int prep_fused, finalize_fused;
+    const Run *runs;
+    const Rot *rots;
+    const int32_t *prq;           // prefix run of each qubit (-1: none)
+    void *cs;                     // [B][n_rots] (cos, sin) of half angles, FP64 pairs (may be null)
+    int n_rots, n_weights;
+    const int32_t *w_ptr, *w_rots, *x_ptr, *x_rots;
+    double *abar;                 // [B][n_rots]
+    void *gx, *gw_out;            // [B][n_in], [B][n_weights] plan real type (may be null)
+    double *gw_ws;                // [B][n_weights] (may be null)
 };
 
 }  // namespace qtm

@@ -886,6 +886,19 @@ __device__ __forceinline__ void pass_body(const PassArgs &a, const CUtensorMap *
     const uint32_t gap = tile & ((1u << gapbits) - 1u);
     const uint32_t rest = tile >> gapbits;
 
+    if constexpr (!REV) {
+        if (a.prep_fused) {   // this CTA's sample: run matrices and tables before anything reads them
+            __shared__ double2 ufac[2 * 32];
+            prep_sample<R>(a.runs, a.rots, a.prq, a.n_runs, a.n, a.state_qubits,
+                           static_cast<const R *>(a.x) + (size_t)b * a.n_in, static_cast<const R *>(a.w),
+                           static_cast<Cx<R> *>(const_cast<void *>(a.mats)) + (size_t)b * a.n_runs * 4,
+                           static_cast<Cx<R> *>(const_cast<void *>(a.tabs)) +
+                               (size_t)b * ((a.state_qubits + 3) >> 2) * 16,
+                           ufac, a.cs ? static_cast<double2 *>(a.cs) + (size_t)b * a.n_rots : nullptr);
+            __syncthreads();
+        }
+    }
+
     TileJob j;
     j.T = blockDim.x;
     j.K = a.K; j.l = a.l; j.h = a.h; j.m = a.m; j.sq = a.state_qubits;
@@ -952,6 +965,21 @@ __device__ __forceinline__ void pass_body(const PassArgs &a, const CUtensorMap *
             if (a.store_phi) tma_store(tm_phi, coord, a.rank, S.phi);
             if (REV && a.store_lam) tma_store(tm_lam, coord, a.rank, S.lam);
             tma_store_commit_and_drain();
+        }
+    }
+
+    if constexpr (REV) {
+        if (a.finalize_fused) {   // this CTA's sample: every run's sums are written (one tile)
+            __syncthreads();
+            const R *xb = static_cast<const R *>(a.x) + (size_t)b * a.n_in;
+            grad_finalize_sample<R>(a.runs, a.rots, a.n_runs, a.w_ptr, a.w_rots, a.x_ptr, a.x_rots, a.n_weights,
+                                    a.n_in, xb, static_cast<const R *>(a.w),
+                                    a.Gpart + (size_t)b * a.n_runs * a.tiles * 3, a.tiles,
+                                    a.abar + (size_t)b * a.n_rots,
+                                    a.gx ? static_cast<R *>(a.gx) + (size_t)b * a.n_in : nullptr,
+                                    a.gw_out ? static_cast<R *>(a.gw_out) + (size_t)b * a.n_weights : nullptr,
+                                    a.gw_ws ? a.gw_ws + (size_t)b * a.n_weights : nullptr,
+                                    a.cs ? static_cast<const double2 *>(a.cs) + (size_t)b * a.n_rots : nullptr);
         }
     }
 }

@@ -491,6 +491,102 @@ void gen_costate_cpx(std::ostringstream &o, const Plan &P, const PassDesc &pd, i
     o << "        }\n";
 }
 
+// An analytic pass whose closed form is known (or that has no folded
+// entangler): the complex-pair kernel computes phi straight into its first
+// phase's registers instead of the tile program filling shared memory.
+bool cpx_fill(const PassDesc &pd)
+{
+    return pd.phi_src == SRC_ANALYTIC && (pd.amap_lin >= 0 || pd.analytic_ents == 0);
+}
+
+// Closed form of the analytic phi (the tile program's fill_analytic, with
+// every constant of the pass written out).  Amplitude index y (global bits)
+// of register jj of a thread: y = y_t | Y_jj with Y_jj the tile bits of jj,
+// so the linear part x = X(y_t) ^ X(Y_jj) and the linear sign parity split
+// into a per-thread value and a per-register constant; the quadratic parity
+// terms are evaluated per register.  phi_y = sign * prod_q T_q[nibble q of x]:
+// tables whose nibble no register changes are multiplied once per thread.
+void gen_fill_cpx(std::ostringstream &o, const Plan &P, const PassDesc &pd, int lo)
+{
+    const int L = pd.l, H = pd.h;
+    const uint32_t LM = (1u << L) - 1u;
+    auto yloc = [&](uint32_t v) { return (v & LM) | ((v >> L) << H); };
+    std::vector<MaskTerm> lin, quad;
+    uint32_t dlin = 0;
+    const bool identity = pd.amap_lin < 0;   // no folded entangler: x = y
+    if (!identity) {
+        for (int k = 0; k < pd.amap_lin; ++k) lin.push_back(P.amap_terms[pd.amap_begin + k]);
+        for (int k = 0; k < pd.amap_quad; ++k) quad.push_back(P.amap_terms[pd.amap_begin + pd.amap_lin + k]);
+        dlin = pd.amap_dlin;
+    }
+    auto X = [&](uint32_t y) {
+        if (identity) return y;
+        uint32_t x = 0;
+        for (const MaskTerm &t : lin) x ^= (t.d >= 0 ? (y >> t.d) : (y << -t.d)) & t.mask;
+        return x;
+    };
+    const int ntab = (P.state_qubits + 3) >> 2;
+    std::vector<uint32_t> C(16);
+    std::vector<int> PC(16);
+    for (int jj = 0; jj < 16; ++jj) {
+        C[jj] = X(yloc((uint32_t)jj << lo));
+        PC[jj] = __builtin_popcount(C[jj] & dlin) & 1;
+    }
+    std::vector<int> vary, fixed;
+    for (int q = 0; q < ntab; ++q) {
+        bool v = false;
+        for (int jj = 0; jj < 16; ++jj) v |= ((C[jj] >> (4 * q)) & 15u) != 0;
+        (v ? vary : fixed).push_back(q);
+    }
+    o << "        {   // analytic phi, closed form, straight into the registers\n";
+    o << "            const uint32_t yt = base | (xt & 0x" << std::hex << LM << "u) | ((xt >> " << std::dec << L
+      << ") << " << H << ");\n";
+    if (identity) {
+        o << "            const uint32_t x0 = yt;\n";
+    } else {
+        o << "            uint32_t x0 = 0u;\n";
+        for (const MaskTerm &t : lin)
+            o << "            x0 ^= (yt " << (t.d >= 0 ? ">> " : "<< ") << std::abs(t.d) << ") & 0x" << std::hex << t.mask
+              << std::dec << "u;\n";
+    }
+    o << "            const uint32_t s0 = " << (dlin ? "__popc(x0 & 0x" : "0u") ;
+    if (dlin) o << std::hex << dlin << std::dec << "u) & 1u";
+    o << ";\n";
+    o << "            const uint32_t tb = smem_u32(S.tabs), tt = smem_u32(TT);\n";
+    for (int q = 0; q < ntab; ++q)
+        o << "            const uint32_t n" << q << " = (x0 >> " << 4 * q << ") & 15u;\n";
+    // thread-constant product of the tables no register changes
+    if (!fixed.empty()) {
+        o << "            f2 pt = lds_f2(tb + 8u * (" << 16 * fixed[0] << "u + n" << fixed[0] << "));\n";
+        for (size_t i = 1; i < fixed.size(); ++i)
+            o << "            pt = cmul_tab(tt + 16u * (" << 16 * fixed[i] << "u + n" << fixed[i] << "), pt);\n";
+    }
+    for (int jj = 0; jj < 16; ++jj) {
+        o << "            { ";
+        size_t first = 0;
+        if (!fixed.empty()) {
+            o << "f2 a = pt;";
+        } else {
+            const int q = vary[0];
+            o << "f2 a = lds_f2(tb + 8u * (" << 16 * q << "u + (n" << q << " ^ " << ((C[jj] >> (4 * q)) & 15u) << "u)));";
+            first = 1;
+        }
+        for (size_t i = first; i < vary.size(); ++i) {
+            const int q = vary[i];
+            o << " a = cmul_tab(tt + 16u * (" << 16 * q << "u + (n" << q << " ^ " << ((C[jj] >> (4 * q)) & 15u)
+              << "u)), a);";
+        }
+        o << " uint32_t s = s0 ^ " << PC[jj] << "u;";
+        if (!quad.empty()) {
+            o << " const uint32_t xx = x0 ^ 0x" << std::hex << C[jj] << std::dec << "u;";
+            for (const MaskTerm &t : quad)
+                o << " s ^= __popc(xx & (xx >> " << t.d << ") & 0x" << std::hex << t.mask << std::dec << "u) & 1u;";
+        }
+        o << " p[" << jj << "] = a ^ ((f2)s * kSign2); }\n";
+    }
+    o << "        }\n";
+}
+
 // One op of a complex-pair phase (register group lo); `slot` is the C
 // expression of its run slot.
 void cpx_op(std::ostringstream &o, const Plan &P, const PassDesc &pd, int k, int lo, const std::string &slot)
@@ -543,7 +639,8 @@ void cpx_op(std::ostringstream &o, const Plan &P, const PassDesc &pd, int k, int
     }
 }
 
-std::string phase_body(const Plan &P, const PassDesc &pd, const DevPhase &phs, bool lam_valid, JitMode mode, int sb)
+std::string phase_body(const Plan &P, const PassDesc &pd, const DevPhase &phs, bool lam_valid, JitMode mode, int sb,
+                       bool fill = false)
 {
     const bool rev = pd.reverse != 0;
     const bool pairs = mode == JIT_PAIRS;
@@ -554,7 +651,12 @@ std::string phase_body(const Plan &P, const PassDesc &pd, const DevPhase &phs, b
     o << "        constexpr int LO = " << lo << ";\n";
     o << "        const uint32_t xt = ((uint32_t)tid & ((1u << LO) - 1u)) | (((uint32_t)tid >> LO) << (LO + 4));\n";
     if (mode == JIT_CPX) {
-        o << "        regs_load_cpx<LO, " << (lam_valid ? "true" : "false") << ">(p, q, S, xt);\n";
+        if (fill) {   // phi from the closed form, lam (if any) from shared memory
+            if (lam_valid) o << "        regs_load_cpx_lam<LO>(q, S, xt);\n";
+            gen_fill_cpx(o, P, pd, lo);
+        } else {
+            o << "        regs_load_cpx<LO, " << (lam_valid ? "true" : "false") << ">(p, q, S, xt);\n";
+        }
         for (int k = phs.op_begin; k < phs.op_end; ++k) cpx_op(o, P, pd, k, lo, slot(P.ops[k].slot));
         o << "        regs_store_cpx<LO, " << (rev ? "true" : "false") << ">(p, q, S, xt);\n";
         return o.str();
@@ -663,7 +765,8 @@ std::string jit_source(const Plan &P, const PassDesc &pd, int min_blocks, JitMod
             if ((P.ops[k].type == OP_U2 || P.ops[k].type == OP_GRAD) && (sb < 0 || P.ops[k].slot < sb))
                 sb = P.ops[k].slot;
         if (sb < 0) sb = 0;
-        const std::string body = phase_body(P, pd, phs, lam_valid, mode, sb);
+        const bool fill = mode == JIT_CPX && cpx_fill(pd) && ph == pd.phase_begin;
+        const std::string body = phase_body(P, pd, phs, lam_valid, mode, sb, fill);
         size_t t = 0;
         while (t < tpl.size() && tpl[t] != body) ++t;
         if (t == tpl.size()) tpl.push_back(body);
@@ -709,7 +812,12 @@ std::string jit_source(const Plan &P, const PassDesc &pd, int min_blocks, JitMod
              "bool)\n{\n    f2 p[kRegs];\n    f2 q[kRegs];\n"
           << "    // complex-pair matrix table after the tile program's shared memory\n"
           << "    f2 *CT = reinterpret_cast<f2 *>(reinterpret_cast<unsigned char *>(S.phi) + " << lane_table_offset(P, pd)
-          << ");\n    stage_cpx_table(S.mats, CT, " << nslots << ");\n    __syncthreads();\n";
+          << ");\n    stage_cpx_table(S.mats, CT, " << nslots << ");\n"
+          << (cpx_fill(pd) ? "    f2 *TT = CT + " + std::to_string(kCpxSlotPairsHost * std::max(1, nslots)) +
+                                 ";   // product-state tables, broadcast form\n    stage_cpx_tabs(S.tabs, TT, " +
+                                 std::to_string(16 * ((P.state_qubits + 3) >> 2)) + ");\n"
+                           : std::string())
+          << "    __syncthreads();\n";
     else if (mode == JIT_LANES)
         o << "template <typename R>\n__device__ __forceinline__ void gen_phases(const TileJob &j, const TileSmem<R> &S, "
              "bool)\n{\n    A2 p[kLanePairs];\n    A2 q[kLanePairs];\n"
@@ -744,7 +852,8 @@ std::string jit_source(const Plan &P, const PassDesc &pd, int min_blocks, JitMod
         o << "    qtm::pass_body_x2<" << (rev ? "true" : "false") << ">(a, &tm_phi, &tm_lam, "
           << "[](const qtm::TileJobX2 &j, const qtm::TileSmemX2 &S, bool) { qtm::gen_phases(j, S); });\n}\n";
     else
-        o << "    qtm::pass_body<float, " << (rev ? "true" : "false") << ">(a, &tm_phi, &tm_lam, "
+        o << "    qtm::pass_body<float, " << (rev ? "true" : "false")
+          << (mode == JIT_CPX && cpx_fill(pd) ? ", false" : "") << ">(a, &tm_phi, &tm_lam, "
           << "[](const qtm::TileJob &j, const qtm::TileSmem<float> &S, bool lv) { qtm::gen_phases<float>(j, S, lv); "
              "});\n}\n";
     return o.str();
@@ -757,7 +866,8 @@ size_t jit_smem_bytes_lanes(const Plan &P, const PassDesc &pd)
 
 size_t jit_smem_bytes_cpx(const Plan &P, const PassDesc &pd)
 {
-    return lane_table_offset(P, pd) + 1024 + (size_t)8 * kCpxSlotPairsHost * std::max(1, pd.slot_end - pd.slot_begin);
+    return lane_table_offset(P, pd) + 1024 + (size_t)8 * kCpxSlotPairsHost * std::max(1, pd.slot_end - pd.slot_begin) +
+           (cpx_fill(pd) ? (size_t)256 * ((P.state_qubits + 3) >> 2) : 0);
 }
 
 size_t jit_smem_bytes_x2(const Plan &P, const PassDesc &pd)

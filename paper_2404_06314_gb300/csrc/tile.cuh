@@ -871,7 +871,9 @@ __device__ __forceinline__ void grad_finalize_sample(
 // The body of a pass kernel: tile coordinates, TMA loads (or the analytic
 // state), table staging, the pass's phases (`phases`, the interpreter or a
 // generated specialisation), per-tile partial sums and the TMA stores.
-template <typename R, bool REV, typename PhaseFn>
+// FILL = false: the phases compute an analytic phi themselves (the tables
+// are staged, the tile is not filled).
+template <typename R, bool REV, bool FILL = true, typename PhaseFn>
 __device__ __forceinline__ void pass_body(const PassArgs &a, const CUtensorMap *tm_phi,
                                           const CUtensorMap *tm_lam, PhaseFn phases)
 {
@@ -937,7 +939,7 @@ __device__ __forceinline__ void pass_body(const PassArgs &a, const CUtensorMap *
     }
     stage_tables<R, REV>(j, S, nwarps);
     __syncthreads();
-    if (a.phi_src == SRC_ANALYTIC) fill_analytic<R>(j, S);
+    if (FILL && a.phi_src == SRC_ANALYTIC) fill_analytic<R>(j, S);
     if (load_phi || load_lam) {
         bool ok = false;
         const unsigned long long t0 = global_ns();

@@ -100,6 +100,41 @@ __device__ __forceinline__ void regs_store_cpx(const f2 (&p)[kRegs], const f2 (&
     }
 }
 
+// lam only (the generated first phase of an analytic pass computes phi itself).
+template <int LO>
+__device__ __forceinline__ void regs_load_cpx_lam(f2 (&q)[kRegs], const TileSmem<float> &T, uint32_t xt)
+{
+    const uint32_t lm = smem_u32(T.lam);
+    if constexpr (LO == 0) {
+#pragma unroll
+        for (int k = 0; k < kRegs / 2; ++k)
+            lds_f2x2(lm + 8u * (uint32_t)swz<float>((int)xt + 2 * k), q[2 * k], q[2 * k + 1]);
+    } else {
+#pragma unroll
+        for (int jj = 0; jj < kRegs; ++jj) q[jj] = lds_f2(lm + 8u * (uint32_t)swz<float>((int)(xt | ((uint32_t)jj << LO))));
+    }
+}
+
+// Product-state tables in broadcast form for complex products: entry e as
+// (e.re, e.re), (-e.im, e.im), so that amp <- e * amp is
+// fma2((e.re, e.re), amp, (-e.im, e.im) * swap(amp)).
+__device__ __forceinline__ void stage_cpx_tabs(const Cx<float> *tabs, f2 *tt, int n)
+{
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const Cx<float> e = tabs[i];
+        tt[2 * i] = pack2(e.x, e.x);
+        tt[2 * i + 1] = pack2(-e.y, e.y);
+    }
+}
+
+// amp <- e * amp with e read in broadcast form at shared address addr.
+__device__ __forceinline__ f2 cmul_tab(uint32_t addr, f2 amp)
+{
+    f2 er, en;
+    lds_f2x2(addr, er, en);
+    return fma2(er, amp, mul2(en, swap2(amp)));
+}
+
 // a <- U a on register bit RB: per register pair (x0, x1),
 // y0 = u00 x0 + u01 x1, y1 = u10 x0 + u11 x1.
 template <int RB>

@@ -15,6 +15,7 @@
 
 #include "device.h"
 #include "tile.cuh"
+#include "tile_cpx.cuh"
 #include "tile_x2.cuh"
 
 namespace qtm {
@@ -40,7 +41,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 1 : (REV ? 2 : 3)) k_pas
                                               const __grid_constant__ CUtensorMap tm_lam)
 {
     pass_body<R, REV>(a, &tm_phi, &tm_lam, [](const TileJob &j, const TileSmem<R> &S, bool lam_valid) {
-        run_phases<R, REV>(j, S, lam_valid);
+        run_phases_any<R, REV>(j, S, lam_valid);
     });
 }
 

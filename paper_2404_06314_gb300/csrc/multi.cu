@@ -30,6 +30,7 @@
 #include "../../include/qtm_debug.h"
 #include "device.h"
 #include "tile.cuh"
+#include "tile_cpx.cuh"
 
 namespace qtm {
 
@@ -200,10 +201,10 @@ __device__ __forceinline__ void run_tile(const MultiArgs &m, const TileSmem<R> &
     if (pd.phi_src == SRC_ANALYTIC) fill_analytic<R>(j, S);
     __syncthreads();
     if (rev) {
-        run_phases<R, true>(j, S, pd.lam_src == SRC_LOAD);
+        run_phases_any<R, true>(j, S, pd.lam_src == SRC_LOAD);
         write_partials<R, true>(j, S, nw, false, nullptr, Gpart_b, cd.tiles, t);
     } else {
-        run_phases<R, false>(j, S, false);
+        run_phases_any<R, false>(j, S, false);
         write_partials<R, false>(j, S, nw, pd.has_expval != 0, Epart_b + (size_t)t * cd.M, nullptr, cd.tiles, t);
     }
     if (!resident) {

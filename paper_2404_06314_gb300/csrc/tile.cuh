@@ -527,13 +527,11 @@ __device__ __forceinline__ void fill_analytic(const TileJob &j, const TileSmem<R
 
 // <O_m> partials over the thread's 16 registers (terms sorted by observable),
 // warp-reduced, one value per (warp, observable) in S.redE.
+// pr: |amplitude|^2 of the thread's registers.
 template <typename R>
-__device__ __forceinline__ void op_expval(const Cx<R> (&p)[kRegs], const TileSmem<R> &S, const TileJob &j,
-                                          uint32_t xt, int lo, int warp, int lane, int wwidth, unsigned wmask)
+__device__ __forceinline__ void op_expval_pr(const R (&pr)[kRegs], const TileSmem<R> &S, const TileJob &j,
+                                             uint32_t xt, int lo, int warp, int lane, int wwidth, unsigned wmask)
 {
-    R pr[kRegs];
-#pragma unroll
-    for (int jj = 0; jj < kRegs; ++jj) pr[jj] = p[jj].x * p[jj].x + p[jj].y * p[jj].y;
     int cur = -1;
     R acc = 0;
     for (int t = 0; t < j.n_terms; ++t) {
@@ -561,12 +559,22 @@ __device__ __forceinline__ void op_expval(const Cx<R> (&p)[kRegs], const TileSme
     }
 }
 
-// lam = (sum_m gE_m O_m) phi on the thread's registers (Sec. II-A costate).
 template <typename R>
-__device__ __forceinline__ void op_costate(const Cx<R> (&p)[kRegs], Cx<R> (&q)[kRegs], const TileSmem<R> &S,
-                                           const TileJob &j, uint32_t xt, int lo)
+__device__ __forceinline__ void op_expval(const Cx<R> (&p)[kRegs], const TileSmem<R> &S, const TileJob &j,
+                                          uint32_t xt, int lo, int warp, int lane, int wwidth, unsigned wmask)
 {
-    R d[kRegs];
+    R pr[kRegs];
+#pragma unroll
+    for (int jj = 0; jj < kRegs; ++jj) pr[jj] = p[jj].x * p[jj].x + p[jj].y * p[jj].y;
+    op_expval_pr<R>(pr, S, j, xt, lo, warp, lane, wwidth, wmask);
+}
+
+// lam = (sum_m gE_m O_m) phi on the thread's registers (Sec. II-A costate).
+// d[jj]: the diagonal of sum_m gE_m O_m on the thread's registers.
+template <typename R>
+__device__ __forceinline__ void costate_diag(R (&d)[kRegs], const TileSmem<R> &S, const TileJob &j, uint32_t xt,
+                                             int lo)
+{
 #pragma unroll
     for (int jj = 0; jj < kRegs; ++jj) d[jj] = 0;
     for (int t = 0; t < j.n_terms; ++t) {
@@ -578,6 +586,14 @@ __device__ __forceinline__ void op_costate(const Cx<R> (&p)[kRegs], Cx<R> (&q)[k
         for (int jj = 0; jj < kRegs; ++jj)
             d[jj] += ((tpar + __popc((uint32_t)jj & rm)) & 1) ? -k : k;
     }
+}
+
+template <typename R>
+__device__ __forceinline__ void op_costate(const Cx<R> (&p)[kRegs], Cx<R> (&q)[kRegs], const TileSmem<R> &S,
+                                           const TileJob &j, uint32_t xt, int lo)
+{
+    R d[kRegs];
+    costate_diag<R>(d, S, j, xt, lo);
 #pragma unroll
     for (int jj = 0; jj < kRegs; ++jj) q[jj] = {d[jj] * p[jj].x, d[jj] * p[jj].y};
 }

@@ -220,6 +220,209 @@ __device__ __forceinline__ void flip_cpx(f2 (&p)[kRegs], f2 (&q)[kRegs], uint32_
     }
 }
 
+// ---- the phase interpreter on complex pairs (complex64 general kernels) ----
+
+// a <- U a on register bit RB with U read as four complex entries (the
+// general kernels' staged matrices) and put in broadcast form here.
+template <int RB>
+__device__ __forceinline__ void u2_cpx_m(f2 (&a)[kRegs], const Cx<float> *m)
+{
+    const Cx<float> u00 = m[0], u01 = m[1], u10 = m[2], u11 = m[3];
+    const f2 A_r = pack2(u00.x, u00.x), A_n = pack2(-u00.y, u00.y), B_r = pack2(u01.x, u01.x),
+             B_n = pack2(-u01.y, u01.y), C_r = pack2(u10.x, u10.x), C_n = pack2(-u10.y, u10.y),
+             D_r = pack2(u11.x, u11.x), D_n = pack2(-u11.y, u11.y);
+#pragma unroll
+    for (int j = 0; j < kRegs; ++j) {
+        if (j & (1 << RB)) continue;
+        const f2 x0 = a[j], x1 = a[j | (1 << RB)];
+        const f2 s0 = swap2(x0), s1 = swap2(x1);
+        a[j] = fma2(A_r, x0, fma2(A_n, s0, fma2(B_r, x1, mul2(B_n, s1))));
+        a[j | (1 << RB)] = fma2(C_r, x0, fma2(C_n, s0, fma2(D_r, x1, mul2(D_n, s1))));
+    }
+}
+
+__device__ __forceinline__ void u2_cpx_dispatch(int rb, f2 (&a)[kRegs], const Cx<float> *m)
+{
+    switch (rb) {
+    case 0: u2_cpx_m<0>(a, m); break;
+    case 1: u2_cpx_m<1>(a, m); break;
+    case 2: u2_cpx_m<2>(a, m); break;
+    default: u2_cpx_m<3>(a, m); break;
+    }
+}
+
+__device__ __forceinline__ void grad_cpx_dispatch(int rb, const f2 (&a)[kRegs], const f2 (&b)[kRegs], float &vx,
+                                                  float &vy, float &vz)
+{
+    switch (rb) {
+    case 0: grad_cpx<0>(a, b, vx, vy, vz); break;
+    case 1: grad_cpx<1>(a, b, vx, vy, vz); break;
+    case 2: grad_cpx<2>(a, b, vx, vy, vz); break;
+    default: grad_cpx<3>(a, b, vx, vy, vz); break;
+    }
+}
+
+// CNOT on target register bit RT; control a register bit rc (>= 0) or the
+// thread-known bit vc.
+template <int RT>
+__device__ __forceinline__ void cnot_regs_cpx(f2 (&a)[kRegs], int rc, int vc)
+{
+#pragma unroll
+    for (int j = 0; j < kRegs; ++j) {
+        if (j & (1 << RT)) continue;
+        const int c = rc >= 0 ? ((j >> rc) & 1) : vc;
+        const f2 t0 = a[j], t1 = a[j | (1 << RT)];
+        a[j] = c ? t1 : t0;
+        a[j | (1 << RT)] = c ? t0 : t1;
+    }
+}
+
+__device__ __forceinline__ void cnot_cpx_dispatch(int rt, f2 (&a)[kRegs], int rc, int vc)
+{
+    switch (rt) {
+    case 0: cnot_regs_cpx<0>(a, rc, vc); break;
+    case 1: cnot_regs_cpx<1>(a, rc, vc); break;
+    case 2: cnot_regs_cpx<2>(a, rc, vc); break;
+    default: cnot_regs_cpx<3>(a, rc, vc); break;
+    }
+}
+
+// The pass's phases over the tile in shared memory (after a barrier), the op
+// records read at run time as in run_phases (tile.cuh), with each amplitude an
+// f32x2 pair; ends with a barrier.  lam_valid: the costate tile holds lam.
+template <bool REV>
+__device__ __forceinline__ void run_phases_cpx(const TileJob &j, const TileSmem<float> &S, bool lam_valid)
+{
+    const int tid = threadIdx.x, T = j.T;
+    const bool active = tid < T;
+    const int warp = tid >> 5, lane = tid & 31;
+    const int wwidth = T < 32 ? T : 32;
+    const unsigned wmask = T < 32 ? ((1u << T) - 1u) : 0xffffffffu;
+    const uint32_t base = j.base;
+    const uint32_t ph_s = smem_u32(S.phi), lm_s = smem_u32(S.lam);
+    f2 p[kRegs];
+    f2 q[kRegs];
+    for (int phz = j.phase_begin; phz < j.phase_end; ++phz) {
+        // threads beyond the tile's 2^(K-4) skip the work but reach the same
+        // barrier instruction at the end of the phase
+        if (active) {
+        const DevPhase ph = j.phases[phz];
+        const int lo = ph.lo;
+        const uint32_t xt = ((uint32_t)tid & ((1u << lo) - 1u)) | (((uint32_t)tid >> lo) << (lo + 4));
+        if (lo == 0) {
+#pragma unroll
+            for (int k = 0; k < kRegs / 2; ++k) {
+                const uint32_t o = 8u * (uint32_t)swz<float>((int)xt + 2 * k);
+                lds_f2x2(ph_s + o, p[2 * k], p[2 * k + 1]);
+                if (REV && lam_valid) lds_f2x2(lm_s + o, q[2 * k], q[2 * k + 1]);
+            }
+        } else {
+#pragma unroll
+            for (int jj = 0; jj < kRegs; ++jj) {
+                const uint32_t o = 8u * (uint32_t)swz<float>((int)(xt | ((uint32_t)jj << lo)));
+                p[jj] = lds_f2(ph_s + o);
+                if (REV && lam_valid) q[jj] = lds_f2(lm_s + o);
+            }
+        }
+        DevOp nxt = j.ops[ph.op_begin < ph.op_end ? ph.op_begin : 0];
+        for (int o = ph.op_begin; o < ph.op_end; ++o) {
+            const DevOp op = nxt;
+            if (o + 1 < ph.op_end) nxt = j.ops[o + 1];
+            switch (op.type) {
+            case OP_DIAG: {
+                uint32_t msk = 0;
+#pragma unroll 4
+                for (int k = op.a; k < op.a + op.b; ++k) {
+                    const DiagPair dp = j.diag[k];
+                    msk ^= operand_pattern(dp.a, lo, xt, base) & operand_pattern(dp.b, lo, xt, base);
+                }
+                flip_cpx<REV>(p, q, msk);
+                break;
+            }
+            case OP_U2:
+                u2_cpx_dispatch(op.a - lo, p, S.mats + 4 * op.slot);
+                break;
+            case OP_GRAD:
+                if constexpr (REV) {
+                    float vx, vy, vz;
+                    grad_cpx_dispatch(op.a - lo, p, q, vx, vy, vz);
+                    float *g = S.redG + (size_t)warp * 3 * j.nslots + 3 * op.slot;
+                    if (T >= 32) {
+                        const float v = warp_sum3(vx, vy, vz, lane);
+                        if ((lane & 7) == 0 && lane < 24) g[lane >> 3] = v;
+                    } else {
+                        vx = warp_sum(vx, wwidth, wmask);
+                        vy = warp_sum(vy, wwidth, wmask);
+                        vz = warp_sum(vz, wwidth, wmask);
+                        if (lane == 0) { g[0] = vx; g[1] = vy; g[2] = vz; }
+                    }
+                    if (!(op.flags & OPF_SKIP_APPLY)) {
+                        u2_cpx_dispatch(op.a - lo, p, S.mats + 4 * op.slot);
+                        u2_cpx_dispatch(op.a - lo, q, S.mats + 4 * op.slot);
+                    }
+                }
+                break;
+            case OP_CNOT: {
+                int rc = -1, vc = 0;
+                if (op.a >= kFixed) vc = (int)((base >> (op.a - kFixed)) & 1u);
+                else if (op.a >= lo && op.a < lo + kRegBits) rc = op.a - lo;
+                else vc = (int)((xt >> op.a) & 1u);
+                cnot_cpx_dispatch(op.b - lo, p, rc, vc);
+                if (REV) cnot_cpx_dispatch(op.b - lo, q, rc, vc);
+                break;
+            }
+            case OP_EXPVAL: {
+                float pr[kRegs];
+#pragma unroll
+                for (int jj = 0; jj < kRegs; ++jj) {
+                    const f2 t = mul2(p[jj], p[jj]);
+                    pr[jj] = lane0(t) + lane1(t);
+                }
+                op_expval_pr<float>(pr, S, j, xt, lo, warp, lane, wwidth, wmask);
+                break;
+            }
+            case OP_COSTATE:
+                if constexpr (REV) {
+                    float d[kRegs];
+                    costate_diag<float>(d, S, j, xt, lo);
+#pragma unroll
+                    for (int jj = 0; jj < kRegs; ++jj) q[jj] = mul2(pack2(d[jj], d[jj]), p[jj]);
+                    lam_valid = true;
+                }
+                break;
+            default:
+                break;
+            }
+        }
+        if (lo == 0) {
+#pragma unroll
+            for (int k = 0; k < kRegs / 2; ++k) {
+                const uint32_t o = 8u * (uint32_t)swz<float>((int)xt + 2 * k);
+                sts_f2x2(ph_s + o, p[2 * k], p[2 * k + 1]);
+                if (REV) sts_f2x2(lm_s + o, q[2 * k], q[2 * k + 1]);
+            }
+        } else {
+#pragma unroll
+            for (int jj = 0; jj < kRegs; ++jj) {
+                const uint32_t o = 8u * (uint32_t)swz<float>((int)(xt | ((uint32_t)jj << lo)));
+                sts_f2(ph_s + o, p[jj]);
+                if (REV) sts_f2(lm_s + o, q[jj]);
+            }
+        }
+        if (REV) lam_valid = true;
+        }
+        __syncthreads();
+    }
+}
+
+// The interpreter for a plan's real type: complex pairs for complex64.
+template <typename R, bool REV>
+__device__ __forceinline__ void run_phases_any(const TileJob &j, const TileSmem<R> &S, bool lam_valid)
+{
+    if constexpr (sizeof(R) == 4) run_phases_cpx<REV>(j, S, lam_valid);
+    else run_phases<R, REV>(j, S, lam_valid);
+}
+
 }  // namespace
 
 }  // namespace qtm

@@ -582,7 +582,7 @@ void gen_fill_cpx(std::ostringstream &o, const Plan &P, const PassDesc &pd, int 
             for (const MaskTerm &t : quad)
                 o << " s ^= __popc(xx & (xx >> " << t.d << ") & 0x" << std::hex << t.mask << std::dec << "u) & 1u;";
         }
-        o << " p[" << jj << "] = a ^ ((f2)s * kSign2); }\n";
+        o << " p[" << jj << "] = a ^ (((f2)s << 63) | ((f2)s << 31)); }\n";
     }
     o << "        }\n";
 }

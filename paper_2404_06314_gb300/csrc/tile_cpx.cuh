@@ -214,7 +214,8 @@ __device__ __forceinline__ void flip_cpx(f2 (&p)[kRegs], f2 (&q)[kRegs], uint32_
 {
 #pragma unroll
     for (int jj = 0; jj < kRegs; ++jj) {
-        const f2 s = (f2)((m >> jj) & 1u) * kSign2;   // both lanes' sign bits, or 0
+        const uint32_t sb = (m << (31 - jj)) & 0x80000000u;   // bit jj of m as a sign bit
+        const f2 s = ((f2)sb << 32) | sb;                     // in both lanes
         p[jj] ^= s;
         if (REV) q[jj] ^= s;
     }

@@ -72,6 +72,31 @@ def test_generated_source_compiles_random(n):
     _nvrtc_kind_or_skip(plan, "cpx")
 
 
+def test_analytic_phi_in_registers_exactly_with_a_closed_form():
+    """Complex-pair kernels compute an analytic pass's phi in the registers of
+    its first phase when the plan has a closed form of the folded prefix (or
+    no folded entangler); otherwise the tile program fills shared memory.
+    Both branches run in the GPU parity cases (qnn12/16/20, rand9 closed;
+    rand11-16 not)."""
+    import re
+    for name, want in (("qnn12", True), ("qnn20", True), ("qnn16", True), ("rand9", True), ("rand11", False),
+                       ("rand13", False)):
+        plan = capi.Plan(_circuit(name), dtype="c64")
+        desc = capi.qtm_debug_describe(plan.handle)
+        info = plan.info
+        for which, n in ((0, info["fwd_passes"]), (1, info["adj_passes"])):
+            lines = [l for l in desc.splitlines() if l.startswith("fwd[" if which == 0 else "rev[")]
+            for i in range(n):
+                m = re.search(r"phi=(\d+) lam=\d+ ents=(\d+)( closed=(-?\d+))?", lines[i])
+                analytic, ents = m.group(1) == "2", int(m.group(2))
+                closed = m.group(4) is not None and int(m.group(4)) >= 0
+                src = plan.jit_source(which, i, kind="cpx")
+                in_regs = "straight into the registers" in src
+                assert in_regs == (analytic and (closed or ents == 0)), (name, which, i)
+                if analytic:
+                    assert in_regs == want or ents == 0, (name, which, i)
+
+
 def test_not_specialised():
     c = W.workload_12q()
     assert capi.Plan(c, dtype="c128").jit_source(0, 0) == ""   # complex128 keeps the interpreter

@@ -137,8 +137,10 @@ PROFILED_TRAFFIC = {
 
 
 def roofline(r, peaks, peak_src):
-    """Roofline of the dominant kernel, the reverse pass k_pass<float, reverse>,
-    from its live CUDA-event durations inside the timed region.  Algorithmic
+    """Roofline of the dominant kernel, the reverse pass (the specialised
+    qtm_gen_pass by default; for one-tile-per-sample plans its launch also
+    runs the sample's gradient finalize), from its live CUDA-event durations
+    inside the timed region.  Algorithmic
     work per launch = the plan's per-sample adjoint flops (or state bytes) x B
     / reverse passes; both the FP32-ALU and the HBM fraction are computed and
     the larger one names the binding resource."""

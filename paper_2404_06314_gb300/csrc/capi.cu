@@ -934,6 +934,14 @@ JitMode jit_mode(int flags)
                                              : JIT_CPX;
 }
 
+bool applies_udagger(const Plan &P, const PassDesc &pd)
+{
+    for (int ph = pd.phase_begin; ph < pd.phase_end; ++ph)
+        for (int o = P.phases[ph].op_begin; o < P.phases[ph].op_end; ++o)
+            if (P.ops[o].type == OP_GRAD && !(P.ops[o].flags & OPF_SKIP_APPLY)) return true;
+    return false;
+}
+
 qtm_status compile_all(qtm_plan *p, JitMode mode, std::vector<std::vector<char>> &fwd_bin,
                        std::vector<std::vector<char>> &rev_bin)
 {
@@ -958,7 +966,9 @@ qtm_status compile_all(qtm_plan *p, JitMode mode, std::vector<std::vector<char>>
     }
     for (size_t i = 0; i < P.rev.size(); ++i) {
         if (!jit_eligible(P, P.rev[i])) return fail(p, QTM_EUNSUPPORTED, "plan has passes the specialiser does not cover");
-        jobs.push_back({&P.rev[i], &rev_bin[i], minb_r});
+        // a reverse pass that applies no U^dagger (every gradient is its qubit's
+        // last) holds no second register state: the forward budget, more CTAs
+        jobs.push_back({&P.rev[i], &rev_bin[i], applies_udagger(P, P.rev[i]) ? minb_r : std::max(minb_r, minb_f)});
     }
     std::vector<std::string> logs(jobs.size());
     std::vector<char> ok(jobs.size(), 0);
@@ -1101,7 +1111,9 @@ const char *qtm_debug_jit_source(const qtm_plan *p, int which, int index, int fl
     const JitMode mode = jit_mode(flags);
     const bool pairs = mode == JIT_PAIRS;
     m->jit_src_cache = jit_eligible(P, v[index])
-                           ? jit_source(P, v[index], pairs ? (which ? 1 : 2) : (which ? 2 : 3), mode)
+                           ? jit_source(P, v[index],
+                                        pairs ? (which ? 1 : 2) : (which && applies_udagger(P, v[index]) ? 2 : 3),
+                                        mode)
                            : std::string();
     return m->jit_src_cache.c_str();
 }

@@ -15,7 +15,7 @@ struct FinalizeArgs {
     const int32_t *w_ptr, *w_rots, *x_ptr, *x_rots;
     const void *x, *w;            // plan real type
     const double *Epart;
-    const double *Gpart;
+    double *Gpart;                // [B][n_runs][tiles][3]; the finalize sums tiles in place
     void *E;                      // [B][M] real type (may be null)
     double *abar;                 // [B][n_rots] workspace
     void *gx;                     // [B][n_in] real (may be null)

@@ -56,15 +56,18 @@ __global__ void __launch_bounds__(256, REV ? 1 : 2) k_pass_x2(const __grid_const
     });
 }
 
+// One warp per (sample, observable): lanes take every 32nd tile, then a
+// fixed butterfly (deterministic order).
 template <typename R>
 __global__ void k_expval_finalize(const double *Epart, int B, int tiles, int M, R *E)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= B * M) return;
+    const int i = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (i >= B * M) return;   // whole warps leave together
     const int b = i / M, m = i % M;
     double s = 0.0;
-    for (int t = 0; t < tiles; ++t) s += Epart[((size_t)b * tiles + t) * M + m];
-    E[i] = (R)s;
+    for (int t = lane; t < tiles; t += 32) s += Epart[((size_t)b * tiles + t) * M + m];
+    s = warp_sum(s, 32, 0xffffffffu);
+    if (lane == 0) E[i] = (R)s;
 }
 
 template <typename R>
@@ -223,7 +226,7 @@ cudaError_t launch_prep(int dtype, const PrepArgs &a, cudaStream_t s)
 cudaError_t launch_expval_finalize(int dtype, const FinalizeArgs &f, cudaStream_t s)
 {
     const int n = f.B * f.M;
-    const int blk = 256, grd = (n + blk - 1) / blk;
+    const int blk = 256, grd = (n + 7) / 8;   // 8 warps per block, one per output
     if (dtype == QTM_C128)
         k_expval_finalize<double><<<grd, blk, 0, s>>>(f.Epart, f.B, f.tiles, f.M, static_cast<double *>(f.E));
     else

@@ -840,11 +840,26 @@ template <typename R>
 __device__ __forceinline__ void grad_finalize_sample(
     const Run *runs, const Rot *rots, int n_runs, const int32_t *w_ptr, const int32_t *w_rots,
     const int32_t *x_ptr, const int32_t *x_rots, int P, int n_in, const R *xb, const R *w,
-    const double *Gpart_b, int tiles, double *abar, R *gx_b, R *gw_b, double *gwws_b, const double2 *cs_b)
+    double *Gpart_b, int tiles, double *abar, R *gx_b, R *gw_b, double *gwws_b, const double2 *cs_b)
 {
+    const bool warp_sums = tiles >= 32 && blockDim.x >= 32;
+    if (warp_sums) {
+        // many tiles: sum every run's tiles first, one warp per run (lanes take
+        // every 32nd tile, fixed butterfly), into the run's tile-0 slot
+        const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+        for (int r = threadIdx.x >> 5; r < n_runs; r += nw)
+            for (int c = 0; c < 3; ++c) {
+                double s = 0.0;
+                for (int t = lane; t < tiles; t += 32) s += Gpart_b[((size_t)r * tiles + t) * 3 + c];
+                s = warp_sum(s, 32, 0xffffffffu);
+                if (lane == 0) Gpart_b[(size_t)r * tiles * 3 + c] = s;
+            }
+        __syncthreads();
+    }
+    const int tiles_left = warp_sums ? 1 : tiles;
     for (int r = threadIdx.x; r < n_runs; r += blockDim.x) {
         double v[3] = {0.0, 0.0, 0.0};
-        for (int t = 0; t < tiles; ++t)
+        for (int t = 0; t < tiles_left; ++t)
             for (int c = 0; c < 3; ++c) v[c] += Gpart_b[((size_t)r * tiles + t) * 3 + c];
         const Run rr = runs[r];
         for (int i = rr.rot_end - 1; i >= rr.rot_begin; --i) {

@@ -163,11 +163,19 @@ def test_recompute_hbm_path():
 
 # ---- full-size configurations, sampled rows --------------------------------------
 
-def test_full_12q_batch_sampled():
+def _bench_plan(c, compiled):
+    """The plan as bench.py times it (complex-pair specialised kernels) or
+    with the general kernels."""
+    plan = capi.Plan(c, dtype="c64")
+    return plan.compile() if compiled else plan
+
+
+@pytest.mark.parametrize("compiled", [False, True])
+def test_full_12q_batch_sampled(compiled):
     c = W.workload_12q()
     B = 1024
     inp = W.make_inputs(c, B, W.WORKLOAD_SEEDS[c.name], real_dtype=np.float32)
-    E, gx, gw = run_gpu(c, inp, "c64")
+    E, gx, gw = run_gpu(c, inp, "c64", plan=_bench_plan(c, compiled))
     rows = np.array([0, 1, 255, 256, 511, 700, 1022, 1023])
     Eo, gxo, gwo = oracle_ref(c, inp, rows)
     assert_close(E[rows], Eo, 1e-5, "12q full E")
@@ -175,11 +183,12 @@ def test_full_12q_batch_sampled():
     assert_close(gw[rows], gwo, 1e-5, "12q full gw")
 
 
-def test_full_20q_batch_sampled():
+@pytest.mark.parametrize("compiled", [False, True])
+def test_full_20q_batch_sampled(compiled):
     c = W.workload_20q()
     B = 64
     inp = W.make_inputs(c, B, W.WORKLOAD_SEEDS[c.name], real_dtype=np.float32)
-    E, gx, gw = run_gpu(c, inp, "c64")
+    E, gx, gw = run_gpu(c, inp, "c64", plan=_bench_plan(c, compiled))
     rows = np.array([0, 63])
     Eo, gxo, gwo = oracle_ref(c, inp, rows)
     assert_close(E[rows], Eo, 1e-5, "20q full E")

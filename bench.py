@@ -382,6 +382,36 @@ def measure_uneven(steps, device, count=256, seed_offset=0):
                        "autotuned": cfg, "tune_seconds": tune_s}}
 
 
+def uneven_only(steps):
+    """The uneven batch of measure_uneven (same circuits and inputs) run
+    `steps` times with the autotuner's usual choice on a GB300 (2 CTAs per
+    SM, costliest items first, fuse width 32, split tasks), without a graph:
+    a fixed launch sequence for ncu."""
+    import numpy as np
+    import torch
+
+    from paper_2404_06314_gb300 import capi, workloads as W
+
+    cs = W.workload_uneven(seed=W.WORKLOAD_SEEDS["uneven"], count=256)
+    rng = np.random.default_rng(W.WORKLOAD_SEEDS["uneven"] + 17)
+    xs = [rng.uniform(-np.pi, np.pi, size=(1, c.n_inputs)) for c in cs]
+    ws = [rng.standard_normal(c.n_weights) for c in cs]
+    gs = [rng.standard_normal((1, c.n_obs)) for c in cs]
+    mp = capi.MultiPlan(cs, batch=1)
+    mp.config = {"ctas_per_sm": 2, "order": 0, "fuse_width": 32, "split": 1}
+    x, w, g = mp.pack(xs, capi.QTM_MULTI_X), mp.pack(ws, capi.QTM_MULTI_W), mp.pack(gs, capi.QTM_MULTI_GE)
+    E, gx, gw = mp.empty(capi.QTM_MULTI_E), mp.empty(capi.QTM_MULTI_GX), mp.empty(capi.QTM_MULTI_GW)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        mp.run(x, w, g, E, gx, gw)
+    e1.record()
+    mp.sync()
+    torch.cuda.synchronize()
+    print(json.dumps({"uneven_only": True, "steps": steps, "ms_per_step": e0.elapsed_time(e1) / max(1, steps),
+                      "config": mp.config}))
+
+
 def measure_training(device, steps=100):
     """16-qubit training loop: QuantumModule + MSE + Adam, `steps` steps."""
     import torch
@@ -641,10 +671,15 @@ def main():
     ap.add_argument("--skip-extra", action="store_true", help="skip the uneven-batch and training lines")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle CPU work")
+    ap.add_argument("--uneven-only", action="store_true",
+                    help="profiling aid: run the uneven batch --steps times with the configuration the "
+                         "autotuner picks on this box (no tuning, no graph) and print one JSON line")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    if args.impl == "reference":
+    if args.uneven_only:
+        uneven_only(args.steps)
+    elif args.impl == "reference":
         reference_main(args)
     else:
         gpu_main(args)

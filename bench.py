@@ -518,8 +518,6 @@ def gpu_main(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
         dist.barrier()
-    sampler.stop()
-    clocks = sampler.summary()
 
     n20 = None
     if args.workload == "qnn12" and not args.skip_n20:
@@ -531,6 +529,9 @@ def gpu_main(args):
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             tot20 = float(t.item())
         n20 = (r20, tot20)
+    # the clock record spans both timed workloads (12 and 20 qubits)
+    sampler.stop()
+    clocks = sampler.summary()
 
     extra = {}
     if args.workload == "qnn12" and not args.skip_extra:
@@ -629,7 +630,7 @@ def reference_main(args):
     inp = W.make_inputs(c, cfg["B"], W.WORKLOAD_SEEDS[c.name], real_dtype=np.float32)
     threads = os.cpu_count() or 1
     # bounded sample per step: about args.cpu_budget / (steps + warmup) seconds
-    per_step = max(0.5, args.cpu_budget / max(1, args.steps + args.warmup))
+    per_step = max(0.05, args.cpu_budget / max(1, args.steps + args.warmup))
     probe_rate, _, _ = oracle_rate(c, inp, min(2.0, per_step), threads)
     S = max(threads, int(probe_rate * per_step))
     rows = [i % cfg["B"] for i in range(S)]
@@ -657,7 +658,7 @@ def reference_main(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="qnn12")

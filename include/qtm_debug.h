@@ -20,10 +20,10 @@ extern "C" {
  * valid until the next call on it or qtm_destroy. */
 const char *qtm_debug_describe(const qtm_plan *plan);
 
-/* Interpret the fused schedule in FP64 on the host (n <= 20).  HOST pointers:
+/* Interpret the fused schedule in FP64 on the host (n <= 24).  HOST pointers:
  * x [B][n_inputs], w [n_weights], gE [B][n_obs] (NULL: forward only);
  * outputs E [B][n_obs], gx [B][n_inputs], gw [B][n_weights] (per sample), each
- * may be NULL.  Returns QTM_EUNSUPPORTED for naive-path plans or n > 20 and
+ * may be NULL.  Returns QTM_EUNSUPPORTED for naive-path plans or n > 24 and
  * QTM_EINVAL if the schedule breaks a locality rule (see qtm_last_error). */
 qtm_status qtm_debug_emulate(const qtm_plan *plan, int B, const double *x, const double *w,
                              const double *gE, double *E, double *gx, double *gw);

@@ -289,7 +289,7 @@ qtm_status emulate_plan(const Plan &P, int B, const double *x, const double *w, 
                         double *E, double *gx, double *gw, std::string &err)
 {
     if (P.path != QTM_PATH_FUSED) { err = "emulation covers the fused path"; return QTM_EUNSUPPORTED; }
-    if (P.state_qubits > 20) { err = "emulation limited to n <= 20"; return QTM_EUNSUPPORTED; }
+    if (P.state_qubits > 24) { err = "emulation limited to n <= 24"; return QTM_EUNSUPPORTED; }
     try {
         Emu em(P, B, x, w, gE);
         for (const auto &pd : P.fwd) em.run_pass(pd);

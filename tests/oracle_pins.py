@@ -193,6 +193,48 @@ def bloch_expvals_and_grads(c, theta):
     return E, J
 
 
+def cancelling_circuit(n, n_in=5):
+    """RX(x) RY(w) per qubit, a CNOT chain and its inverse, two CZ rings, then
+    RZ(w) RY(w x) per qubit.  The entanglers multiply to the identity (CNOT and
+    CZ are their own inverses), so the state is a product state whose
+    expectation values and gradients have the Bloch-vector closed form at any
+    n; the planner does not know that and runs its full entangler machinery."""
+    g = []
+    for q in range(n):
+        g.append((W.RX, q, -1, -1, q % n_in, 1.0))
+        g.append((W.RY, q, -1, q, -1, 1.0))
+    g += [(W.CNOT, i, i + 1, -1, -1, 1.0) for i in range(n - 1)]
+    g += [(W.CNOT, i, i + 1, -1, -1, 1.0) for i in reversed(range(n - 1))]
+    g += W.cz_ring(n) + W.cz_ring(n)
+    for q in range(n):
+        g.append((W.RZ, q, -1, n + q, -1, 0.7))
+        g.append((W.RY, q, -1, 2 * n + q, q % n_in, 0.9))
+    terms = [(1 << 0, 1.0, 0), (1 << (n - 1), 1.0, 1), ((1 << 0) | (1 << (n - 1)), 0.5, 2), (1 << 12, -1.0, 2)]
+    return W.Circuit(n=n, gates=g, terms=terms, n_obs=3, n_weights=3 * n, n_inputs=n_in, name=f"cancel{n}")
+
+
+def closed_form_vjp(c, xb, w, gEb):
+    """E, grad_x, per-sample grad_w of one sample from the product-state closed
+    form: J over the rotation gates, then the chain rule of the angle binding
+    t = coef * w[j] * x[k]."""
+    rot = [g for g in c.gates if g[0] in (W.RX, W.RY, W.RZ)]
+    prod = W.Circuit(n=c.n, gates=rot, terms=c.terms, n_obs=c.n_obs, n_weights=c.n_weights,
+                     n_inputs=c.n_inputs, name="product")
+    theta = angles_py(prod, xb, w)
+    E, J = bloch_expvals_and_grads(prod, theta)
+    abar = gEb @ J
+    gx = np.zeros(c.n_inputs)
+    gw = np.zeros(c.n_weights)
+    for g, (_, _, _, wi, xi, coef) in enumerate(rot):
+        wv = w[wi] if wi >= 0 else 1.0
+        xv = xb[xi] if xi >= 0 else 1.0
+        if wi >= 0:
+            gw[wi] += abar[g] * coef * xv
+        if xi >= 0:
+            gx[xi] += abar[g] * coef * wv
+    return E, gx, gw
+
+
 # ----------------------------------------------------------------------------
 # pins
 # ----------------------------------------------------------------------------
@@ -491,9 +533,29 @@ def pin_pauli_adjoint_equals_param_shift(O):
         close(np.einsum("bm,bmg->bg", gE, J), dth_a, 1e-12, "pauli VJP = gE . J")
 
 
+def pin_cancelling_entanglers(O):
+    """A CNOT chain followed by its inverse and two CZ rings between rotation
+    layers leave a product state: expectation values, grad_x and per-sample
+    grad_w equal the Bloch closed form (CNOT and CZ are involutions; a phase or
+    permutation that is not one breaks this)."""
+    for n in (2, 5, 9):
+        c = cancelling_circuit(n, n_in=3)
+        rng = np.random.default_rng(500 + n)
+        x = rng.uniform(-np.pi, np.pi, size=(2, c.n_inputs))
+        w = rng.normal(size=c.n_weights)
+        gE = rng.normal(size=(2, c.n_obs))
+        E = O.forward(c, x, w)
+        _, gx, gw = O.adjoint(c, gE, x, w)
+        for b in range(2):
+            Ec, gxc, gwc = closed_form_vjp(c, x[b], w, gE[b])
+            close(E[b], Ec, 1e-13, f"cancel n={n} E")
+            close(gx[b], gxc, 1e-12, f"cancel n={n} gx")
+            close(gw[b], gwc, 1e-12, f"cancel n={n} gw")
+
+
 ALL_PINS = [pin_single_rotation_closed_form, pin_bell, pin_dense_unitary, pin_norm,
             pin_product_state_bloch, pin_basis_state_cnot_chain, pin_trailing_diagonal,
             pin_finite_differences, pin_adjoint_equals_param_shift,
             pin_threads_and_partition, pin_h_rzz_closed_form, pin_dense_unitary_h_rzz,
             pin_adjoint_equals_param_shift_h_rzz, pin_pauli_closed_form, pin_pauli_dense,
-            pin_pauli_adjoint_equals_param_shift]
+            pin_pauli_adjoint_equals_param_shift, pin_cancelling_entanglers]

@@ -112,6 +112,23 @@ def test_schedule_matches_oracle_20q():
     _emulate_vs_oracle(W.workload_20q(), 1, 5)
 
 
+@pytest.mark.parametrize("n,dtype", [(22, "c64"), (21, "c128")])
+def test_schedule_cancelling_circuit_closed_form(n, dtype):
+    """Above the oracle's quick sizes: the emulated schedule of a circuit whose
+    entanglers cancel (product state) against the Bloch closed form."""
+    c = P.cancelling_circuit(n)
+    plan = capi.Plan(c, dtype=dtype)
+    rng = np.random.default_rng(60 + n)
+    x = rng.uniform(-np.pi, np.pi, size=(1, c.n_inputs))
+    w = rng.normal(size=c.n_weights)
+    gE = rng.normal(size=(1, c.n_obs))
+    E, gx, gw = capi.qtm_debug_emulate(plan.handle, x, w, gE, circuit=c)
+    Ec, gxc, gwc = P.closed_form_vjp(c, x[0], w, gE[0])
+    for got, ref, nm in ((E[0], Ec, "E"), (gx[0], gxc, "gx"), (gw[0], gwc, "gw")):
+        err = float(np.max(np.abs(got - ref)))
+        assert err < 1e-12, f"{c.name} {nm}: {err:.3e}"
+
+
 @pytest.mark.parametrize("n", [1, 2, 3, 4, 6, 9, 12, 13, 14, 15])
 def test_schedule_matches_oracle_random(n):
     rng = np.random.default_rng(40 + n)

@@ -77,8 +77,16 @@ def test_workload_20q_c64():
     check(W.workload_20q(), 2, "c64")
 
 
+def test_workload_20q_c128():
+    check(W.workload_20q(), 1, "c128")
+
+
 def test_workload_16q_train_c64():
     check(W.workload_16q_train(), 3, "c64")
+
+
+def test_workload_16q_train_c128():
+    check(W.workload_16q_train(), 2, "c128")
 
 
 def test_uneven_members():
@@ -196,6 +204,27 @@ def test_full_20q_batch_sampled(compiled):
     assert_close(gw[rows], gwo, 1e-5, "20q full gw")
     # property at any size: |E| <= sum |c_t|
     assert np.all(np.abs(E) <= 1.0 + 1e-5)
+
+
+# ---- maximum state size: closed form at any n ------------------------------------
+
+@pytest.mark.parametrize("n,dtype,compiled", [(30, "c64", False), (30, "c64", True), (24, "c128", False)])
+def test_maximum_size_closed_form(n, dtype, compiled):
+    """The largest state the library accepts (30 qubits: 8 GiB per complex64
+    state) and a 24-qubit complex128 state, against the closed form."""
+    c = P.cancelling_circuit(n)
+    inp = W.make_inputs(c, 1, 40 + n, real_dtype=np.float32 if dtype == "c64" else np.float64)
+    plan = capi.Plan(c, dtype=dtype)
+    if compiled:
+        plan.compile()
+    E, gx, gw = run_gpu(c, inp, dtype, plan=plan)
+    Eo, gxo, gwo = P.closed_form_vjp(c, inp.x[0].astype(np.float64), inp.w.astype(np.float64),
+                                    inp.gE[0].astype(np.float64))
+    tol = TOL[dtype]
+    assert_close(E[0], Eo, tol, f"{n}q {dtype} E")
+    assert_close(gx[0], gxo, tol, f"{n}q {dtype} gx")
+    assert_close(gw[0], gwo, tol, f"{n}q {dtype} gw")
+    del plan
 
 
 # ---- full Jacobian (one costate per observable) -----------------------------------

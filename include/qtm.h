@@ -164,8 +164,10 @@ int qtm_plan_parts(const qtm_plan *plan);
 /*
  * qtm_forward: expectation values, Eq. (qnn) for every sample of the batch
  * (Eq. (qnn_batched)).  x: [B][n_inputs], w: [n_weights], expvals: [B][n_obs]
- * (device, plan real type).  B >= 1.  Keeps the final states in the plan's
- * workspace for a following qtm_adjoint on the same stream.
+ * (device, plan real type).  B >= 0; B = 0 is an empty batch: nothing is
+ * computed and no pointer is read (QTM_ECUDA still without a CUDA device).
+ * Keeps the final states in the plan's workspace for a following qtm_adjoint
+ * on the same stream.
  */
 qtm_status qtm_forward(qtm_plan *plan, int B, const void *x, const void *w,
                        void *expvals, void *stream);
@@ -179,7 +181,8 @@ qtm_status qtm_forward(qtm_plan *plan, int B, const void *x, const void *w,
  * had the same B, x and w, on the same stream; pass QTM_ADJ_RECOMPUTE to
  * evolve them again (required if anything else ran on the plan since).  Returns
  * QTM_ESTATE when no stored forward matches (B, x, w pointers).  The stored
- * states are consumed.
+ * states are consumed.  B = 0 (empty batch): no stored forward is needed,
+ * nothing is computed, and a batch-summed grad_w is set to zero on the stream.
  */
 qtm_status qtm_adjoint(qtm_plan *plan, int B, const void *grad_expvals, const void *x,
                        const void *w, void *grad_x, void *grad_w, int flags, void *stream);
@@ -190,7 +193,7 @@ qtm_status qtm_adjoint(qtm_plan *plan, int B, const void *grad_expvals, const vo
  * CZ/CNOT): the (B, M, |Theta|) output of Sec. II-B, one costate per
  * observable (the reverse passes run once per observable with cotangent
  * e_m).  Runs the forward itself; fused plans only (QTM_EUNSUPPORTED on the
- * naive path).  Leaves no stored forward state behind.
+ * naive path).  Leaves no stored forward state behind.  B = 0: nothing.
  */
 qtm_status qtm_jacobian(qtm_plan *plan, int B, const void *x, const void *w, void *jac,
                         void *stream);
@@ -209,7 +212,7 @@ qtm_status qtm_jacobian(qtm_plan *plan, int B, const void *x, const void *w, voi
  * Instead of plan-owned buffers it uses one file-scope device array of
  * QTM_NOALLOC_SCRATCH_BYTES (8 MiB) that the library keeps on every GPU it is
  * loaded on until the process exits.  Arguments are those of qtm_forward
- * (device pointers, plan real type).  Supported for fused plans whose state
+ * (device pointers, plan real type), with B >= 1.  Supported for fused plans whose state
  * fits one shared-memory tile (n <= 12): otherwise QTM_EUNSUPPORTED.  A batch
  * whose tables and scratch exceed the array returns QTM_EINVAL before any
  * work is enqueued (about 2.8 MB for 12 qubits, 6 layers, B = 1024).

@@ -769,12 +769,41 @@ qtm_status qtm_get_plan_info(const qtm_plan *p, qtm_plan_info *info)
     return QTM_OK;
 }
 
+namespace {
+
+// B = 0 is an empty batch: nothing is computed, but a CUDA device is still
+// required (a missing GPU fails the same way at every batch size).  B < 0 is
+// an argument error, caught before the composite dispatch.
+qtm_status check_batch(qtm_plan *p, int B)
+{
+    if (B < 0) return fail(p, QTM_EINVAL, "B must be >= 0");
+    if (B == 0) {
+        int count = 0;
+        const cudaError_t e = cudaGetDeviceCount(&count);
+        if (e != cudaSuccess || count == 0) return fail(p, QTM_ECUDA, "no CUDA device");
+    }
+    return QTM_OK;
+}
+
+void drop_stored_forward(qtm_plan *p)
+{
+    p->fwd_valid = false;
+    for (qtm_plan *part : p->parts) drop_stored_forward(part);
+}
+
+}  // namespace
+
 qtm_status qtm_forward(qtm_plan *p, int B, const void *x, const void *w, void *expvals, void *stream)
 {
     if (!p) return QTM_EINVAL;
+    qtm_status bs = check_batch(p, B);
+    if (bs != QTM_OK) return bs;
+    if (B == 0) {   // nothing to evolve; an earlier stored forward is no longer the last one
+        drop_stored_forward(p);
+        return QTM_OK;
+    }
     if (is_composite(p)) return composite_forward(p, B, x, w, expvals, stream);
     const Plan &P = p->P;
-    if (B < 1) return fail(p, QTM_EINVAL, "B must be >= 1");
     if ((P.n_inputs > 0 && !x) || (P.n_weights > 0 && !w) || !expvals)
         return fail(p, QTM_EINVAL, "null pointer");
     qtm_status st = ensure_device(p);
@@ -807,9 +836,20 @@ qtm_status qtm_adjoint(qtm_plan *p, int B, const void *gE, const void *x, const 
                        void *gw, int flags, void *stream)
 {
     if (!p) return QTM_EINVAL;
+    qtm_status bs = check_batch(p, B);
+    if (bs != QTM_OK) return bs;
+    if (B == 0) {   // empty batch: a batch-summed grad_w is the zero vector
+        if (flags & ~(QTM_ADJ_GW_PER_SAMPLE | QTM_ADJ_RECOMPUTE)) return fail(p, QTM_EINVAL, "unknown flags");
+        drop_stored_forward(p);
+        if (gw && !(flags & QTM_ADJ_GW_PER_SAMPLE) && p->P.n_weights > 0) {
+            const cudaError_t e = cudaMemsetAsync(gw, 0, elem_bytes(p->P.dtype) / 2 * (size_t)p->P.n_weights,
+                                                  static_cast<cudaStream_t>(stream));
+            if (e != cudaSuccess) return cuda_fail(p, e, "grad_w clear");
+        }
+        return QTM_OK;
+    }
     if (is_composite(p)) return composite_adjoint(p, B, gE, x, w, gx, gw, flags, stream);
     const Plan &P = p->P;
-    if (B < 1) return fail(p, QTM_EINVAL, "B must be >= 1");
     if (!gE || (P.n_inputs > 0 && !x) || (P.n_weights > 0 && !w))
         return fail(p, QTM_EINVAL, "null pointer");
     if (flags & ~(QTM_ADJ_GW_PER_SAMPLE | QTM_ADJ_RECOMPUTE)) return fail(p, QTM_EINVAL, "unknown flags");
@@ -882,9 +922,14 @@ qtm_status qtm_adjoint(qtm_plan *p, int B, const void *gE, const void *x, const 
 qtm_status qtm_jacobian(qtm_plan *p, int B, const void *x, const void *w, void *jac, void *stream)
 {
     if (!p) return QTM_EINVAL;
+    qtm_status bs = check_batch(p, B);
+    if (bs != QTM_OK) return bs;
+    if (B == 0) {   // the Jacobian of an empty batch has no elements
+        drop_stored_forward(p);
+        return QTM_OK;
+    }
     if (is_composite(p)) return composite_jacobian(p, B, x, w, jac, stream);
     const Plan &P = p->P;
-    if (B < 1) return fail(p, QTM_EINVAL, "B must be >= 1");
     if ((P.n_inputs > 0 && !x) || (P.n_weights > 0 && !w) || !jac) return fail(p, QTM_EINVAL, "null pointer");
     if (P.path != QTM_PATH_FUSED) return fail(p, QTM_EUNSUPPORTED, "qtm_jacobian runs on the fused path");
     qtm_status st = ensure_device(p);

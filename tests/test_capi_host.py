@@ -169,6 +169,29 @@ def test_no_gpu_fails_loudly():
     assert "CUDA" in capi.qtm_last_error(plan.handle) or "device" in capi.qtm_last_error(plan.handle)
 
 
+def test_batch_size_checked_before_any_work():
+    """B < 0 is QTM_EINVAL on plain and composite (X/Y observable) plans, for
+    every compute entry point, before any device is touched; an empty batch
+    (B = 0) still needs a CUDA device and fails loudly without one."""
+    import torch
+    fake = ctypes.c_void_p(256)   # never dereferenced
+    plain = capi.Plan(W.workload_4q())
+    pauli = capi.Plan(W.Circuit(n=2, gates=[(W.RY, 0, -1, 0, -1, 1.0), (W.CNOT, 0, 1, -1, -1, 1.0)],
+                                terms=[(0, 1.0, 0, 1), (2, 0.5, 0)], n_obs=1, n_weights=1, n_inputs=0,
+                                name="xz"))
+    assert pauli.parts == 2
+    for plan in (plain, pauli):
+        for B in (-1, -7):
+            assert capi.qtm_forward(plan.handle, B, fake, fake, fake, None) == capi.QTM_EINVAL
+            assert capi.qtm_adjoint(plan.handle, B, fake, fake, fake, fake, fake, 0, None) == capi.QTM_EINVAL
+            assert capi.qtm_jacobian(plan.handle, B, fake, fake, fake, None) == capi.QTM_EINVAL
+            assert "B must be" in capi.qtm_last_error(plan.handle)
+        if not torch.cuda.is_available():
+            assert capi.qtm_forward(plan.handle, 0, None, None, None, None) == capi.QTM_ECUDA
+            assert capi.qtm_adjoint(plan.handle, 0, None, None, None, None, fake, 0, None) == capi.QTM_ECUDA
+            assert capi.qtm_jacobian(plan.handle, 0, None, None, None, None) == capi.QTM_ECUDA
+
+
 @pytest.mark.parametrize("n", [1, 2, 3])
 def test_closed_form_prefix_keeps_padding_qubits(n):
     """Circuits below 4 qubits are padded to a 4-qubit state; the closed form

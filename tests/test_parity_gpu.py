@@ -45,10 +45,10 @@ def assert_close(got, ref, tol, what):
     assert err <= tol, f"{what}: max abs err {err:.3e} > {tol:.1e}"
 
 
-def check(c, B, dtype, path="fused", seed=7, tol=None):
+def check(c, B, dtype, path="fused", seed=7, tol=None, plan=None):
     tol = tol or TOL[dtype]
     inp = W.make_inputs(c, B, seed, real_dtype=np.float32 if dtype == "c64" else np.float64)
-    E, gx, gw = run_gpu(c, inp, dtype, path)
+    E, gx, gw = run_gpu(c, inp, dtype, path, plan=plan)
     Eo, gxo, gwo = oracle_ref(c, inp)
     assert_close(E, Eo, tol, f"{c.name} {dtype} {path} E")
     assert_close(gx, gxo, tol, f"{c.name} {dtype} {path} gx")
@@ -167,6 +167,42 @@ def test_recompute_hbm_path():
     E2, gx2, gw2 = run_gpu(c, inp, plan=plan, recompute=True)
     assert_close(gx2, gx, 1e-6, "recompute equals stored gx")
     assert_close(gw2, gw, 1e-6, "recompute equals stored gw")
+
+
+def test_empty_batch():
+    """B = 0: the forward gives an empty [0, M], the adjoint needs no stored
+    forward and sets a batch-summed grad_w to zero (also through autograd),
+    per-sample outputs and the Jacobian are empty; the same plan then runs an
+    ordinary batch against the oracle."""
+    import torch
+    from paper_2404_06314_gb300.autograd import qnn
+    rng = np.random.default_rng(3310)
+    pauli = P.rand_small_circuit(rng, 6, G=38, n_obs=3, extra=True, pauli=True)
+    pauli.name = "pauli6"
+    for c, dtype, compiled in ((W.workload_12q(), "c64", True), (W.workload_20q(), "c64", False),
+                               (pauli, "c128", False)):
+        plan = capi.Plan(c, dtype=dtype)
+        if compiled:
+            plan.compile()
+        rd = plan.real_dtype()
+        x0 = torch.empty((0, c.n_inputs), dtype=rd, device="cuda")
+        w = torch.linspace(-1.0, 1.0, c.n_weights, dtype=rd, device="cuda")
+        gE0 = torch.empty((0, c.n_obs), dtype=rd, device="cuda")
+        E = plan.forward(x0, w)
+        assert tuple(E.shape) == (0, c.n_obs)
+        gw = torch.full((c.n_weights,), float("nan"), dtype=rd, device="cuda")
+        gx, gw = plan.adjoint(gE0, x0, w, gw=gw)
+        _, gws = plan.adjoint(gE0, x0, w, per_sample_w=True)
+        J = plan.jacobian(x0, w)
+        plan.sync()
+        assert tuple(gx.shape) == (0, c.n_inputs) and tuple(gws.shape) == (0, c.n_weights)
+        assert tuple(J.shape) == (0, c.n_obs, c.n_gates)
+        assert bool(torch.all(gw == 0)), f"{c.name}: batch-summed grad_w of an empty batch"
+        wv = w.clone().requires_grad_(True)
+        qnn(x0, wv, plan).sum().backward()
+        plan.sync()
+        assert bool(torch.all(wv.grad == 0))
+        check(c, 3, dtype, plan=plan, tol=1e-11 if dtype == "c128" else None)
 
 
 # ---- full-size configurations, sampled rows --------------------------------------

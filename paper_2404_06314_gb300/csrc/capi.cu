@@ -464,10 +464,14 @@ void set_prep_fields(qtm_plan *p, PassArgs &a)
     a.abar = p->d_abar;
 }
 
-qtm_status run_forward_passes(qtm_plan *p, int B, const void *x, const void *w, cudaStream_t s)
+// expvals (may be null): where a plan of one tile per sample writes its
+// expectation values straight from the measuring pass (returns true if so).
+qtm_status run_forward_passes(qtm_plan *p, int B, const void *x, const void *w, cudaStream_t s,
+                              void *expvals = nullptr, bool *wrote_expvals = nullptr)
 {
     const Plan &P = p->P;
     const bool fused = fuse_sample_steps(p) && !P.fwd.empty();
+    if (wrote_expvals) *wrote_expvals = fused && expvals;
     if (!fused) {
         qtm_status st = run_prep(p, B, x, w, s);
         if (st != QTM_OK) return st;
@@ -478,6 +482,7 @@ qtm_status run_forward_passes(qtm_plan *p, int B, const void *x, const void *w, 
             set_prep_fields(p, a);
             a.prep_fused = 1;
         }
+        if (fused) a.E_out = expvals;
         ProfScope ps(p, 0);
         cudaError_t e = launch_any(p, false, i, a, p->tm_fwd[i], p->tm_fwd[i], s);
         if (e != cudaSuccess) return cuda_fail(p, e, "forward pass launch");
@@ -819,13 +824,16 @@ qtm_status qtm_forward(qtm_plan *p, int B, const void *x, const void *w, void *e
         cudaError_t e = naive_forward(P.dtype, a, s, nullptr);
         if (e != cudaSuccess) return cuda_fail(p, e, "naive forward");
     } else {
-        st = run_forward_passes(p, B, x, w, s);
+        bool direct = false;
+        st = run_forward_passes(p, B, x, w, s, expvals, &direct);
         if (st != QTM_OK) return st;
-        FinalizeArgs f = finalize_args(p, B, x, w);
-        f.E = expvals;
-        ProfScope ps(p, 1);
-        cudaError_t e = launch_expval_finalize(P.dtype, f, s);
-        if (e != cudaSuccess) return cuda_fail(p, e, "expval finalize");
+        if (!direct) {
+            FinalizeArgs f = finalize_args(p, B, x, w);
+            f.E = expvals;
+            ProfScope ps(p, 1);
+            cudaError_t e = launch_expval_finalize(P.dtype, f, s);
+            if (e != cudaSuccess) return cuda_fail(p, e, "expval finalize");
+        }
     }
     p->fwd_valid = true;
     p->fwd_B = B; p->fwd_x = x; p->fwd_w = w; p->fwd_stream = stream;

@@ -216,6 +216,10 @@ struct PassArgs {
     double *abar;                 // [B][n_rots]
     void *gx, *gw_out;            // [B][n_in], [B][n_weights] plan real type (may be null)
     double *gw_ws;                // [B][n_weights] (may be null)
+    // Plans of one tile per sample: the forward pass that measures also writes
+    // the expectation values [B][M] (plan real type) here, so no separate
+    // finalize runs; null otherwise.
+    void *E_out;
 };
 
 }  // namespace qtm

@@ -810,7 +810,7 @@ __device__ __forceinline__ void run_phases(const TileJob &j, const TileSmem<R> &
 template <typename R, bool REV>
 __device__ __forceinline__ void write_partials(const TileJob &j, const TileSmem<R> &S, int nwarps,
                                                bool has_expval, double *Epart_row, double *Gpart_b,
-                                               int tiles, int tile)
+                                               int tiles, int tile, R *E_row = nullptr)
 {
     const int tid = threadIdx.x, T = blockDim.x;   // nwarps: warps that ran the phases
     if (!REV) {
@@ -819,6 +819,7 @@ __device__ __forceinline__ void write_partials(const TileJob &j, const TileSmem<
             double s = 0.0;
             for (int w = 0; w < nwarps; ++w) s += (double)S.redE[w * j.M + i];
             Epart_row[i] = s;
+            if (E_row) E_row[i] = (R)s;   // one tile per sample: the tile's sum is the value
         }
     } else {
         const int nv = 3 * j.nslots;
@@ -988,7 +989,8 @@ __device__ __forceinline__ void pass_body(const PassArgs &a, const CUtensorMap *
 
     write_partials<R, REV>(j, S, nwarps, a.has_expval != 0,
                            a.Epart + ((size_t)b * a.tiles + tile) * a.M,
-                           REV ? a.Gpart + (size_t)b * a.n_runs * a.tiles * 3 : nullptr, a.tiles, tile);
+                           REV ? a.Gpart + (size_t)b * a.n_runs * a.tiles * 3 : nullptr, a.tiles, tile,
+                           (!REV && a.E_out) ? static_cast<R *>(a.E_out) + (size_t)b * a.M : nullptr);
 
     // ---- write the tile back ----
     if (a.store_phi || (REV && a.store_lam)) {

@@ -435,6 +435,98 @@ def measure_training(device, steps=100):
                        "pass_kernels": "QuantumModule(kernels='auto'): complex-pair specialised"}}
 
 
+# The paper's own CPU figures for two of its workloads (Sec. III, Tab. II;
+# Sec. IV), quoted as context beside the same workload shapes run here.  The
+# hardware differs (desktop CPUs there), so these are not targets.
+PAPER_CONTEXT = {
+    "mnist10_train_step": {"ms_per_step": 69.8, "baseline_ms_per_step": 4233.7,
+                           "hardware": "AMD Ryzen 9 5900X, 12 cores (qtm, CPU statevector, complex128)",
+                           "source": "Tab. II: 838 s / 12000 steps (qiskit-machine-learning 50804 s)"},
+    "jacobian16_b96": {"s_per_batch": 21.0, "baseline_s_per_batch": 49 * 60.0,
+                       "hardware": "AMD Ryzen 5965WX, 24 cores (qtm, CPU statevector)",
+                       "source": "Sec. IV: forward + full Jacobian of one 96-sample batch, 16 qubits, "
+                                 "16 observables (qiskit-machine-learning 49 min)"},
+}
+
+
+def measure_paper_context(device, steps=50):
+    """Two of the paper's workload shapes on this GPU, beside its CPU figures:
+    (1) the MNIST classifier's training step: 10 qubits, the benchmark ansatz
+    of depth 5 (220 parameters), 10 Z_i observables as class scores, batch 48,
+    cross-entropy, Adam; synthetic 10-feature inputs and labels stand in for
+    the dataset; (2) forward + full Jacobian (qtm_jacobian) of a 96-sample
+    batch at 16 qubits (benchmark ansatz, depth 3, 16 Z_i observables).
+    Both in complex128 (the precision of the paper's simulator) and
+    complex64."""
+    import numpy as np
+    import torch
+
+    from paper_2404_06314_gb300 import capi, workloads as W
+    from paper_2404_06314_gb300.autograd import QuantumModule
+
+    out = {}
+    g = torch.Generator().manual_seed(1010)
+    c10 = W.jerbi_ansatz(10, 5)
+    res = {}
+    for dtype in ("c128", "c64"):
+        mod = QuantumModule(c10, dtype=dtype, init={"weights": "uniform"}, generator=g,
+                            kernels="auto", device=device)
+        rd = mod.plan.real_dtype()
+        x = ((torch.rand((48, 10), generator=g, dtype=torch.float64) * 2 - 1) * np.pi).to(device, rd)
+        y = torch.randint(0, 10, (48,), generator=g).to(device)
+        opt = torch.optim.Adam(mod.parameters(), lr=1e-2)
+
+        def step():
+            opt.zero_grad(set_to_none=True)
+            loss = torch.nn.functional.cross_entropy(mod(x), y)
+            loss.backward()
+            opt.step()
+            return loss
+
+        for _ in range(3):
+            step()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            step()
+        e1.record()
+        torch.cuda.synchronize()
+        res[dtype] = e0.elapsed_time(e1) / steps
+    out["mnist10_train_step"] = {
+        "ms_per_step": res, "steps": steps,
+        "config": f"{c10.name}: 10 qubits, {c10.n_weights} parameters, 10 Z_i observables, B=48, "
+                  "cross-entropy, Adam lr 1e-2, synthetic inputs and labels",
+        "paper": PAPER_CONTEXT["mnist10_train_step"]}
+
+    c16 = W.jerbi_ansatz(16, 3)
+    res = {}
+    for dtype in ("c128", "c64"):
+        plan = capi.Plan(c16, dtype=dtype)
+        if dtype == "c64":
+            plan.compile()
+        rd = plan.real_dtype()
+        inp = W.make_inputs(c16, 96, 1016, real_dtype=np.float32 if dtype == "c64" else np.float64)
+        x = torch.tensor(inp.x, dtype=rd, device=device)
+        w = torch.tensor(inp.w, dtype=rd, device=device)
+        J = plan.jacobian(x, w)
+        plan.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(3):
+            plan.jacobian(x, w, out=J)
+        e1.record()
+        plan.sync()
+        res[dtype] = e0.elapsed_time(e1) / 3 / 1e3
+        del plan, J
+    out["jacobian16_b96"] = {
+        "s_per_batch": res,
+        "config": f"{c16.name}: 16 qubits, {c16.n_weights} parameters, 16 Z_i observables, B=96, "
+                  "qtm_jacobian (forward + one reverse sweep per observable)",
+        "paper": PAPER_CONTEXT["jacobian16_b96"]}
+    return out
+
+
 def measure_e2e(name, steps, device, seed_offset=0, kernels="cpx"):
     """End to end through the public API: pinned host inputs -> device,
     forward, adjoint, results -> pinned host, every step."""
@@ -547,6 +639,7 @@ def gpu_main(args):
         extra["naive"] = nv
         extra["uneven"] = measure_uneven(max(3, args.steps // 4), device, seed_offset=rank)
         extra["train16"] = measure_training(device)
+        extra["paper_context"] = measure_paper_context(device)
     e2e = measure_e2e(args.workload, max(3, args.steps // 4), device, seed_offset=rank, kernels=args.kernels)
     if ws > 1:
         t = torch.tensor([e2e[0]], device=device, dtype=torch.float64)

@@ -417,6 +417,33 @@ bool straight_phases(size_t, size_t)
     return !(v && *v == '1');
 }
 
+// Phase transitions inside one warp.  A thread of a phase with register
+// group [lo, lo + 4) holds the tile amplitudes whose other K - 4 bits are its
+// index bits in order (thread bit k is tile bit k below lo, k + 4 above), so
+// warp w of 2^(K-4) threads holds the amplitudes whose bits at the positions
+// of thread bits 5 .. K-5 spell w.  When two consecutive phases put those
+// warp bits on the same tile bits, every amplitude a warp stores is loaded
+// back by the same warp, and a warp barrier orders the shared-memory store
+// and load; other state shared across warps (tables, per-warp partial sums)
+// is not written between phases.
+bool warp_local_transition(int K, int lo_a, int lo_b)
+{
+    if (K - 4 <= 5) return true;   // one warp per CTA
+    for (int k = 5; k < K - 4; ++k) {
+        const int ba = k < lo_a ? k : k + 4, bb = k < lo_b ? k : k + 4;
+        if (ba != bb) return false;
+    }
+    return true;
+}
+
+// warp barriers between phases that stay within a warp (default) or CTA
+// barriers everywhere (QTM_JIT_WARP_BARRIERS=0, a tuning switch)
+bool warp_local_barriers()
+{
+    const char *v = std::getenv("QTM_JIT_WARP_BARRIERS");
+    return !(v && *v == '0');
+}
+
 // threaded lane kernels (QTM_JIT_THREADED=1, a tuning switch)
 bool lanes_threaded()
 {
@@ -830,10 +857,16 @@ std::string jit_source(const Plan &P, const PassDesc &pd, int min_blocks, JitMod
     o << "    const int tid = threadIdx.x;\n    const int warp = tid >> 5, lane = tid & 31;\n";
     o << "    const uint32_t base = j.base;\n    (void)base; (void)lane; (void)warp; (void)j;\n";
     if (straight_phases(tpl.size(), (size_t)nph)) {
-        // every phase its own block, in order (slots as constants through sb)
-        for (int ph = 0; ph < nph; ++ph)
+        // every phase its own block, in order (slots as constants through sb);
+        // complex-pair kernels end a phase with a warp barrier where the next
+        // phase's warps hold the same amplitudes (see warp_local_transition)
+        for (int ph = 0; ph < nph; ++ph) {
+            const bool local = mode == JIT_CPX && ph + 1 < nph && warp_local_barriers() &&
+                               warp_local_transition(pd.K, P.phases[pd.phase_begin + ph].lo,
+                                                     P.phases[pd.phase_begin + ph + 1].lo);
             o << "    {\n        const int sb = " << table[2 * ph + 1] << ";\n        (void)sb;\n"
-              << tpl[table[2 * ph]] << "        __syncthreads();\n    }\n";
+              << tpl[table[2 * ph]] << (local ? "        __syncwarp();\n    }\n" : "        __syncthreads();\n    }\n");
+        }
     } else {
         o << "#pragma unroll 1\n    for (int ph = 0; ph < " << nph << "; ++ph) {\n";
         o << "        const int sb = kPhaseTable[2 * ph + 1];\n        (void)sb;\n";

@@ -123,8 +123,14 @@ typedef struct {
     int32_t reserved0;
     double fwd_state_bytes;  /* HBM bytes moved over the state per sample, forward */
     double adj_state_bytes;  /* same, adjoint */
-    double fwd_flops;        /* arithmetic per sample, forward (counting rule in DESIGN) */
-    double adj_flops;        /* arithmetic per sample, adjoint */
+    /* Arithmetic per sample, counted per operation of the schedule over the
+     * N = 2^n amplitudes with a complex multiply as 6 flop and a complex add
+     * as 2: a fused 2x2 rotation 14 N, an adjoint gradient step 12 N (the
+     * three inner products) plus 28 N (the rotation undone on phi and lam),
+     * expectation values (3 + terms) N, costate (terms + 2) N, the analytic
+     * product-state init 6 (ceil(n/4) - 1) N; sign flips and permutations 0. */
+    double fwd_flops;        /* forward */
+    double adj_flops;        /* adjoint */
 } qtm_plan_info;
 
 /* Flags of qtm_adjoint. */

@@ -52,7 +52,7 @@ typedef enum {
     QTM_EINVAL = 1,        /* bad argument (detected on the host, nothing launched) */
     QTM_ENOMEM = 2,        /* device or host allocation failed */
     QTM_ECUDA = 3,         /* a CUDA runtime/driver call failed */
-    QTM_EUNSUPPORTED = 4,  /* valid request outside what this build supports */
+    QTM_EUNSUPPORTED = 4,  /* valid request outside what the library supports */
     QTM_ETIMEOUT = 5,      /* a bounded device-side wait gave up (see qtm_sync) */
     QTM_ESTATE = 6         /* call order violated (e.g. adjoint without forward) */
 } qtm_status;

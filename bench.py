@@ -127,9 +127,10 @@ class ClockSampler:
 # kernel kind the bench runs (profiles/ holds the summaries and commands);
 # reported as null for any other kernel kind.
 PROFILED_TRAFFIC = {
-    ("qnn12", "cpx"): (39.778816e6 + 0.053248e6, "profiles/qtm_gen_pass_cpx_qnn12_l6_b1024.md"),
-    ("qnn20", "cpx"): ((1.560073e9 + 2.095445e9 + 1.574877e9) / 3,
-                       "profiles/qtm_gen_pass_cpx_qnn20_l4_b64.md (mean of reverse passes 0-2)"),
+    ("qnn12", "cpx"): (39.806208e6 + 0.005888e6, "profiles/qtm_gen_pass_cpx_qnn12_l6_b1024.md"),
+    ("qnn20", "cpx"): ((0.537211e9 + 1.022075e9 + 1.073937e9 + 1.018183e9 + 1.073976e9 + 0.497157e9 +
+                        0.537045e9 + 0.507352e9 + 0.537005e9 + 0.003969e9) / 5,
+                       "profiles/qtm_gen_pass_cpx_qnn20_l4_b64.md (mean of reverse passes 0-4)"),
     ("qnn12", "lanes"): (36.324352e6 + 0.030208e6, "profiles/qtm_gen_pass_lanes_qnn12_l6_b1024.md"),
     ("qnn20", "lanes"): ((1.560116e9 + 2.095630e9 + 1.575998e9) / 3,
                          "profiles/qtm_gen_pass_lanes_qnn20_l4_b64.md (mean of reverse passes 1-3)"),

@@ -152,13 +152,18 @@ qtm_status qtm_build(int n_qubits, const qtm_gate *gates, int n_gates,
 /*
  * qtm_build_pauli: as qtm_build, with observables that are real combinations
  * of Pauli strings (X, Y and Z terms; Sec. II-A's expectation values of
- * general observables).  Terms are grouped by their X and Y qubits; each group
- * is measured on its own plan of the circuit followed by the basis change
- * V = RY(-pi/2) on X qubits and RX(pi/2) on Y qubits (V sigma V^dagger = Z),
- * as a Z string on the term's support.  Expectation values, vector-Jacobian
- * products and Jacobians are the sums over the groups (fixed group order, on
- * the stream), so every entry point below applies; qtm_forward_noalloc returns
- * QTM_EUNSUPPORTED for such plans.  With Z strings only this is qtm_build.
+ * general observables, all from one evolved state).  Fused (and AUTO) plans
+ * evolve each sample once: Z strings are measured inside the pass kernels,
+ * strings with X/Y factors on the final state the last forward pass leaves
+ * in memory, and their part of the adjoint's costate is formed there before
+ * the reverse passes.  Naive-path plans instead group the terms by their X
+ * and Y qubits and measure each group on its own plan of the circuit followed
+ * by the basis change V = RY(-pi/2) on X qubits and RX(pi/2) on Y qubits
+ * (V sigma V^dagger = Z), summing the groups' outputs in group order
+ * (qtm_plan_parts counts them).  Every entry point below applies, except that
+ * qtm_forward_noalloc, the two-samples-per-CTA kernels (qtm_set_sample_pairing,
+ * QTM_COMPILE_SAMPLE_PAIRS) return QTM_EUNSUPPORTED for plans with X/Y terms.
+ * With Z strings only this is qtm_build.
  */
 qtm_status qtm_build_pauli(int n_qubits, const qtm_gate *gates, int n_gates,
                            const qtm_pauli_term *terms, int n_terms, int n_obs,

@@ -19,7 +19,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libqtm.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU_SOURCES = ["capi.cu", "fused.cu", "naive.cu", "noalloc.cu", "multi.cu"]
+CU_SOURCES = ["capi.cu", "fused.cu", "naive.cu", "noalloc.cu", "multi.cu", "pauli.cu"]
 CPP_SOURCES = ["plan.cpp", "emulate.cpp", "jit.cpp"]
 # device headers embedded as the prelude of run-time generated kernels (NVRTC)
 PRELUDE_HEADERS = ["pod.h", "finalize_math.h", "tile.cuh", "tile_x2.cuh", "tile_lanes.cuh", "tile_cpx.cuh"]

@@ -53,6 +53,7 @@ struct qtm_plan {
     int32_t *d_prefix_run_of_q = nullptr;
     Ent *d_prefix_ents = nullptr;
     Term *d_terms = nullptr;
+    PauliTerm *d_pterms = nullptr;     // terms with X/Y factors (evaluated on the final state)
     int32_t *d_w_ptr = nullptr, *d_w_rots = nullptr, *d_x_ptr = nullptr, *d_x_rots = nullptr;
     unsigned *d_status = nullptr;
     // workspace
@@ -61,6 +62,7 @@ struct qtm_plan {
     double *d_Epart = nullptr, *d_Gpart = nullptr, *d_abar = nullptr, *d_gw_ws = nullptr;
     void *d_mats = nullptr, *d_tabs = nullptr;
     double2 *d_cs = nullptr;           // [B][rots] (cos, sin) of half angles (prep -> grad finalize)
+    double *d_ppart = nullptr;         // [B][chunks][X/Y terms] expectation-value partial sums
     void *d_onehot = nullptr;          // [B][M] cotangent e_m (qtm_jacobian)
     int32_t *d_gate_of_rot = nullptr;  // rotation id -> gate index
     std::vector<CUtensorMap> tm_fwd, tm_rev_phi, tm_rev_lam;
@@ -122,26 +124,26 @@ cudaError_t upload(T **dst, const std::vector<T> &v)
 void free_tables(qtm_plan *p)
 {
     void *ptrs[] = {p->d_gate_of_rot, p->d_ops, p->d_diag, p->d_amap, p->d_phases, p->d_slot_runs, p->d_runs, p->d_rots,
-                    p->d_prefix_run_of_q, p->d_prefix_ents, p->d_terms, p->d_w_ptr,
+                    p->d_prefix_run_of_q, p->d_prefix_ents, p->d_terms, p->d_pterms, p->d_w_ptr,
                     p->d_w_rots, p->d_x_ptr, p->d_x_rots, p->d_status};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     p->d_gate_of_rot = nullptr;
     p->d_ops = nullptr; p->d_diag = nullptr; p->d_amap = nullptr; p->d_phases = nullptr; p->d_slot_runs = nullptr; p->d_runs = nullptr;
     p->d_rots = nullptr; p->d_prefix_run_of_q = nullptr; p->d_prefix_ents = nullptr;
-    p->d_terms = nullptr; p->d_w_ptr = p->d_w_rots = p->d_x_ptr = p->d_x_rots = nullptr;
+    p->d_terms = nullptr; p->d_pterms = nullptr; p->d_w_ptr = p->d_w_rots = p->d_x_ptr = p->d_x_rots = nullptr;
     p->d_status = nullptr;
 }
 
 void free_workspace(qtm_plan *p)
 {
     void *ptrs[] = {p->d_phi, p->d_lam, p->d_Escratch, p->d_Epart, p->d_Gpart, p->d_abar, p->d_gw_ws,
-                    p->d_mats, p->d_tabs, p->d_onehot, p->d_cs};
+                    p->d_mats, p->d_tabs, p->d_onehot, p->d_cs, p->d_ppart};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     p->d_phi = p->d_lam = p->d_Escratch = p->d_mats = p->d_tabs = p->d_onehot = nullptr;
     p->d_cs = nullptr;
-    p->d_Epart = p->d_Gpart = p->d_abar = p->d_gw_ws = nullptr;
+    p->d_Epart = p->d_Gpart = p->d_abar = p->d_gw_ws = p->d_ppart = nullptr;
     p->cap_B = 0;
     p->fwd_valid = false;
 }
@@ -244,6 +246,7 @@ qtm_status ensure_device(qtm_plan *p)
     UP(p->d_prefix_run_of_q, P.prefix_run_of_q);
     UP(p->d_prefix_ents, P.pass_ents);   // per-pass entangler subsets (ents_begin offsets)
     UP(p->d_terms, P.terms);
+    UP(p->d_pterms, P.pterms);
     UP(p->d_w_ptr, P.w_ptr);
     UP(p->d_w_rots, P.w_rots);
     UP(p->d_x_ptr, P.x_ptr);
@@ -272,6 +275,7 @@ bool use_x2(const qtm_plan *p) { return jit_active(p) ? p->jit_pairs != 0 : p->p
 bool pairable(const Plan &P)
 {
     if (P.path != QTM_PATH_FUSED) return false;
+    if (!P.pterms.empty()) return false;   // X/Y terms read the state in its one-sample layout
     for (const auto *v : {&P.fwd, &P.rev})
         for (const auto &pd : *v)
             if (!jit_eligible(P, pd)) return false;
@@ -325,6 +329,8 @@ qtm_status ensure_workspace(qtm_plan *p, int B)
     AL(p->d_tabs, csize * 16 * (size_t)B * ((P.state_qubits + 3) / 4));
     AL(p->d_onehot, rsize * (size_t)B * P.n_obs);
     AL(p->d_cs, sizeof(double2) * (size_t)B * rots);
+    if (!P.pterms.empty())
+        AL(p->d_ppart, sizeof(double) * (size_t)B * pauli_chunks(P.state_qubits) * P.pterms.size());
 #undef AL
     p->cap_B = B;
     if (P.path == QTM_PATH_FUSED) {
@@ -568,6 +574,19 @@ qtm_status ensure_tmp(qtm_plan *p, size_t bytes)
 
 }  // namespace
 
+namespace {
+
+// Observables with X/Y factors as one plan per measurement group (circuit +
+// basis change, Z strings), summed: the naive path always; fused plans with
+// QTM_PAULI_GROUPS=1 (a comparison switch).
+bool pauli_groups_forced()
+{
+    const char *v = std::getenv("QTM_PAULI_GROUPS");
+    return v && *v == '1';
+}
+
+}  // namespace
+
 qtm_status qtm_build_pauli(int n_qubits, const qtm_gate *gates, int n_gates, const qtm_pauli_term *terms,
                            int n_terms, int n_obs, int n_weights, int n_inputs, int dtype, int path,
                            qtm_plan **out)
@@ -600,6 +619,24 @@ qtm_status qtm_build_pauli(int n_qubits, const qtm_gate *gates, int n_gates, con
     if (keys.size() == 1 && keys[0].first == 0 && keys[0].second == 0)   // Z strings only: an ordinary plan
         return qtm_build(n_qubits, gates, n_gates, zterms[0].data(), (int)zterms[0].size(), n_obs, n_weights,
                          n_inputs, dtype, path, out);
+    if (path != QTM_PATH_NAIVE && !pauli_groups_forced()) {   // AUTO plans are fused
+        // one evolution: Z strings in the pass kernels, X/Y strings on the final state
+        std::vector<qtm_zterm> zs;
+        std::vector<PauliTerm> ps;
+        for (int t = 0; t < n_terms; ++t) {
+            const qtm_pauli_term &T = terms[t];
+            if (T.xmask == 0) zs.push_back(qtm_zterm{T.zmask, T.coef, T.obs, 0});
+            else ps.push_back(PauliTerm{T.xmask, T.zmask, T.coef, T.obs, __builtin_popcountll(T.xmask & T.zmask)});
+        }
+        qtm_plan *p = nullptr;
+        qtm_status st = qtm_build(n_qubits, gates, n_gates, zs.data(), (int)zs.size(), n_obs, n_weights, n_inputs,
+                                  dtype, path, &p);
+        if (st != QTM_OK) return st;
+        attach_pauli_terms(p->P, ps);
+        p->needs_lam = true;
+        *out = p;
+        return QTM_OK;
+    }
     qtm_plan *p = new (std::nothrow) qtm_plan();
     if (!p) return QTM_ENOMEM;
     constexpr double kPi = 3.14159265358979323846264338327950288;
@@ -834,6 +871,12 @@ qtm_status qtm_forward(qtm_plan *p, int B, const void *x, const void *w, void *e
             cudaError_t e = launch_expval_finalize(P.dtype, f, s);
             if (e != cudaSuccess) return cuda_fail(p, e, "expval finalize");
         }
+        if (!P.pterms.empty()) {   // X/Y strings on the final state
+            ProfScope ps(p, 1);
+            cudaError_t e = launch_pauli_expval(P.dtype, p->d_phi, P.state_qubits, p->d_pterms, (int)P.pterms.size(),
+                                                B, P.n_obs, p->d_ppart, expvals, s);
+            if (e != cudaSuccess) return cuda_fail(p, e, "pauli expectation values");
+        }
     }
     p->fwd_valid = true;
     p->fwd_B = B; p->fwd_x = x; p->fwd_w = w; p->fwd_stream = stream;
@@ -888,6 +931,12 @@ qtm_status qtm_adjoint(qtm_plan *p, int B, const void *gE, const void *x, const 
     if (recompute) {
         st = run_forward_passes(p, B, x, w, s);
         if (st != QTM_OK) return st;
+    }
+    if (!P.pterms.empty()) {   // the costate's X/Y part, which the first reverse pass loads
+        ProfScope ps(p, 1);
+        e = launch_pauli_costate(P.dtype, p->d_phi, P.state_qubits, p->d_pterms, (int)P.pterms.size(), gE, P.n_obs,
+                                 B, p->d_lam, s);
+        if (e != cudaSuccess) return cuda_fail(p, e, "pauli costate");
     }
     bool consumes = false;
     const bool fused = fuse_sample_steps(p) && !P.rev.empty();
@@ -962,6 +1011,11 @@ qtm_status qtm_jacobian(qtm_plan *p, int B, const void *x, const void *w, void *
         }
         e = launch_onehot(P.dtype, p->d_onehot, B, P.n_obs, m, s);
         if (e != cudaSuccess) return cuda_fail(p, e, "one-hot cotangent");
+        if (!P.pterms.empty()) {
+            e = launch_pauli_costate(P.dtype, p->d_phi, P.state_qubits, p->d_pterms, (int)P.pterms.size(),
+                                     p->d_onehot, P.n_obs, B, p->d_lam, s);
+            if (e != cudaSuccess) return cuda_fail(p, e, "pauli costate");
+        }
         for (size_t i = 0; i < P.rev.size(); ++i) {
             PassArgs a = pass_args(p, P.rev[i], p->g_rev[i], p->smem_rev[i], B, x, w, p->d_onehot);
             e = launch_any(p, true, i, a, p->tm_rev_phi[i], p->tm_rev_lam[i], s);
@@ -1087,6 +1141,8 @@ qtm_status qtm_compile(qtm_plan *p, int flags)
     if (!jit_available()) return fail(p, QTM_EUNSUPPORTED, "NVRTC or driver entry points not available");
     const JitMode mode = jit_mode(flags);
     const bool pairs = mode == JIT_PAIRS;
+    if (pairs && !p->P.pterms.empty())
+        return fail(p, QTM_EUNSUPPORTED, "X/Y observables need the one-sample state layout");
     qtm_status st = ensure_device(p);
     if (st != QTM_OK) return st;
     std::vector<std::vector<char>> fb, rb;

@@ -61,6 +61,15 @@ cudaError_t launch_accumulate(int dtype, const void *src, void *dst, size_t n, c
 cudaError_t launch_accumulate_cols(int dtype, const void *src, int Gs, void *dst, int Gd, size_t rows, cudaStream_t s);
 
 cudaError_t launch_onehot(int dtype, void *gE, int B, int M, int m, cudaStream_t s);
+
+// Pauli strings with X/Y factors on the final state phi [B][2^sq] (pauli.cu):
+// E[b][m] += their expectation values (Ppart: [B][pauli_chunks(sq)][T] FP64
+// scratch), and lam = their part of the costate for cotangents gE [B][M].
+int pauli_chunks(int sq);
+cudaError_t launch_pauli_expval(int dtype, const void *phi, int sq, const PauliTerm *terms, int T, int B, int M,
+                                double *Ppart, void *E, cudaStream_t s);
+cudaError_t launch_pauli_costate(int dtype, const void *phi, int sq, const PauliTerm *terms, int T, const void *gE,
+                                 int M, int B, void *lam, cudaStream_t s);
 cudaError_t launch_jac_scatter(int dtype, const double *abar, const int32_t *gate_of_rot, int n_rots, int B,
                                int M, int m, int G, void *J, cudaStream_t s);
 

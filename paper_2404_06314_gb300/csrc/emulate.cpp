@@ -129,6 +129,43 @@ struct Emu {
         return sign ? -a : a;
     }
 
+    // (P psi)_y of a string with X/Y factors: i^ny (-1)^popcount(x & zmask) psi_x, x = y ^ xmask
+    cd pauli_apply(const PauliTerm &t, const cd *psi, uint64_t y) const
+    {
+        const uint64_t xx = y ^ t.xmask;
+        cd v = psi[xx];
+        if (__builtin_popcountll(xx & t.zmask) & 1) v = -v;
+        static const cd ipow[4] = {cd(1, 0), cd(0, 1), cd(-1, 0), cd(0, -1)};
+        return ipow[t.ny & 3] * v;
+    }
+
+    // X/Y strings on the final state: expectation values added to E, and the
+    // costate part written to lam (what the device does between the passes)
+    void pauli_expvals(double *E) const
+    {
+        for (int b = 0; b < B; ++b) {
+            const cd *psi = &phi[(size_t)b * NS];
+            for (const PauliTerm &t : P.pterms) {
+                double s = 0.0;
+                for (uint64_t y = 0; y < (uint64_t)NS; ++y) s += std::real(std::conj(psi[y]) * pauli_apply(t, psi, y));
+                E[(size_t)b * P.n_obs + t.obs] += t.coef * s;
+            }
+        }
+    }
+
+    void pauli_costate()
+    {
+        for (int b = 0; b < B; ++b) {
+            const cd *psi = &phi[(size_t)b * NS];
+            cd *la = &lam[(size_t)b * NS];
+            for (uint64_t y = 0; y < (uint64_t)NS; ++y) {
+                cd v = 0.0;
+                for (const PauliTerm &t : P.pterms) v += gE[(size_t)b * P.n_obs + t.obs] * t.coef * pauli_apply(t, psi, y);
+                la[y] = v;
+            }
+        }
+    }
+
     std::vector<cd> prefix_factors(int b) const
     {
         std::vector<cd> u(2 * P.state_qubits);
@@ -263,7 +300,7 @@ struct Emu {
                                     double k = gE[(size_t)b * P.n_obs + tm.obs] * tm.coef;
                                     d += par ? -k : k;
                                 }
-                                tl[e] = d * tp[e];
+                                tl[e] = (op.flags & OPF_ACCUMULATE) ? tl[e] + d * tp[e] : d * tp[e];
                             }
                             break;
                         default:
@@ -301,7 +338,9 @@ qtm_status emulate_plan(const Plan &P, int B, const double *x, const double *w, 
                     for (int t = 0; t < tiles; ++t) s += em.Epart[((size_t)b * tiles + t) * P.n_obs + m];
                     E[(size_t)b * P.n_obs + m] = s;
                 }
+        if (E && !P.pterms.empty()) em.pauli_expvals(E);
         if (!gE) return QTM_OK;
+        if (!P.pterms.empty()) em.pauli_costate();
         for (const auto &pd : P.rev) em.run_pass(pd);
         std::vector<double> abar(P.rots.size());
         for (int b = 0; b < B; ++b) {

@@ -261,7 +261,8 @@ void gen_expval_lanes(std::ostringstream &o, const Plan &P, const PassDesc &pd, 
     o << "        }\n";
 }
 
-void gen_costate_lanes(std::ostringstream &o, const Plan &P, const PassDesc &pd, int lo, int S)
+// acc: q holds the costate's X/Y part (loaded from memory); add the Z part.
+void gen_costate_lanes(std::ostringstream &o, const Plan &P, const PassDesc &pd, int lo, int S, bool acc)
 {
     o << "        {\n";
     std::vector<std::vector<size_t>> by_rm(16);
@@ -283,7 +284,11 @@ void gen_costate_lanes(std::ostringstream &o, const Plan &P, const PassDesc &pd,
     };
     for (int k = 0; k < 8; ++k)
         o << "            { const f2 d = pack2(" << dexpr(lane_jj_host(S, k, 0)) << ", " << dexpr(lane_jj_host(S, k, 1))
-          << "); q[" << k << "].r = mul2(d, p[" << k << "].r); q[" << k << "].i = mul2(d, p[" << k << "].i); }\n";
+          << (acc ? "); q[" + std::to_string(k) + "].r = fma2(d, p[" + std::to_string(k) + "].r, q[" +
+                        std::to_string(k) + "].r); q[" + std::to_string(k) + "].i = fma2(d, p[" + std::to_string(k) +
+                        "].i, q[" + std::to_string(k) + "].i); }\n"
+                  : "); q[" + std::to_string(k) + "].r = mul2(d, p[" + std::to_string(k) + "].r); q[" +
+                        std::to_string(k) + "].i = mul2(d, p[" + std::to_string(k) + "].i); }\n");
     o << "        }\n";
 }
 
@@ -339,7 +344,7 @@ void lanes_op(std::ostringstream &o, const Plan &P, const PassDesc &pd, int k, i
         break;
     }
     case OP_EXPVAL: gen_expval_lanes(o, P, pd, lo, sl); break;
-    case OP_COSTATE: gen_costate_lanes(o, P, pd, lo, sl); break;
+    case OP_COSTATE: gen_costate_lanes(o, P, pd, lo, sl, (op.flags & OPF_ACCUMULATE) != 0); break;
     default: break;
     }
 }
@@ -495,7 +500,8 @@ void gen_expval_cpx(std::ostringstream &o, const Plan &P, const PassDesc &pd, in
     o << "        }\n";
 }
 
-void gen_costate_cpx(std::ostringstream &o, const Plan &P, const PassDesc &pd, int lo)
+// acc: q holds the costate's X/Y part (loaded from memory); add the Z part.
+void gen_costate_cpx(std::ostringstream &o, const Plan &P, const PassDesc &pd, int lo, bool acc)
 {
     o << "        {\n";
     std::vector<std::vector<size_t>> by_rm(16);
@@ -513,7 +519,9 @@ void gen_costate_cpx(std::ostringstream &o, const Plan &P, const PassDesc &pd, i
     for (int jj = 0; jj < 16; ++jj) {
         std::string e = "0.f";
         for (int rm : rms) e += std::string(__builtin_popcount(jj & rm) & 1 ? " - c" : " + c") + std::to_string(rm);
-        o << "            { const float d = " << e << "; q[" << jj << "] = mul2(pack2(d, d), p[" << jj << "]); }\n";
+        o << "            { const float d = " << e << "; q[" << jj << "] = "
+          << (acc ? "fma2(pack2(d, d), p[" + std::to_string(jj) + "], q[" + std::to_string(jj) + "]); }\n"
+                  : "mul2(pack2(d, d), p[" + std::to_string(jj) + "]); }\n");
     }
     o << "        }\n";
 }
@@ -661,7 +669,7 @@ void cpx_op(std::ostringstream &o, const Plan &P, const PassDesc &pd, int k, int
         break;
     }
     case OP_EXPVAL: gen_expval_cpx(o, P, pd, lo); break;
-    case OP_COSTATE: gen_costate_cpx(o, P, pd, lo); break;
+    case OP_COSTATE: gen_costate_cpx(o, P, pd, lo, (op.flags & OPF_ACCUMULATE) != 0); break;
     default: break;
     }
 }
@@ -764,7 +772,8 @@ std::string phase_body(const Plan &P, const PassDesc &pd, const DevPhase &phs, b
             break;
         case OP_COSTATE:
             if (pairs) gen_costate_x2(o, P, pd, lo);
-            else o << "        op_costate<R>(p, q, S, j, xt, LO);\n";
+            else o << "        op_costate<R>(p, q, S, j, xt, LO, " << ((op.flags & OPF_ACCUMULATE) ? "true" : "false")
+                   << ");\n";
             break;
         default:
             break;

@@ -70,6 +70,7 @@ extern "C" qtm_status qtm_forward_noalloc(qtm_plan *plan, int B, const void *x, 
     if (!plan) return QTM_EINVAL;
     if (qtm_internal_is_composite(plan)) return QTM_EUNSUPPORTED;   // Pauli-string observables: several plans
     const Plan &P = *qtm_internal_plan(plan);
+    if (!P.pterms.empty()) return QTM_EUNSUPPORTED;   // X/Y observables need the state in memory
     if (B < 1) return QTM_EINVAL;
     if ((P.n_inputs > 0 && !x) || (P.n_weights > 0 && !w) || !expvals) return QTM_EINVAL;
     if (P.path != QTM_PATH_FUSED || P.fwd.size() != 1 || P.tiles_per_sample != 1)

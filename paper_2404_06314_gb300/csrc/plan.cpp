@@ -722,6 +722,17 @@ qtm_status make_plan(int n, const qtm_gate *gates, int n_gates, const qtm_zterm 
     return QTM_OK;
 }
 
+void attach_pauli_terms(Plan &P, const std::vector<PauliTerm> &terms)
+{
+    P.pterms = terms;
+    if (terms.empty() || P.path != QTM_PATH_FUSED || P.fwd.empty() || P.rev.empty()) return;
+    P.fwd.back().store_phi = 1;
+    PassDesc &pd = P.rev.front();
+    pd.lam_src = SRC_LOAD;
+    for (int o = P.phases[pd.phase_begin].op_begin; o < P.phases[pd.phase_begin].op_end; ++o)
+        if (P.ops[o].type == OP_COSTATE) P.ops[o].flags |= OPF_ACCUMULATE;
+}
+
 void plan_costs(const Plan &p, double &fwd_bytes, double &adj_bytes, double &fwd_flops,
                 double &adj_flops)
 {

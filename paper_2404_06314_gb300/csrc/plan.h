@@ -18,6 +18,7 @@ struct Plan {
     std::vector<qtm_gate> gates;        // lowered to RX/RY/RZ/CZ/CNOT (H and RZZ expanded)
     int n_user_gates = 0;               // gates as given to qtm_build (Jacobian columns)
     std::vector<Term> terms;            // sorted by obs
+    std::vector<PauliTerm> pterms;      // terms with X/Y factors (fused plans of qtm_build_pauli)
 
     // runs and rotations
     std::vector<Run> runs;
@@ -56,6 +57,12 @@ struct Plan {
 qtm_status make_plan(int n, const qtm_gate *gates, int n_gates, const qtm_zterm *terms,
                      int n_terms, int n_obs, int n_weights, int n_inputs, int dtype, int path,
                      Plan &out, std::string &err, int max_run = kMaxRunLen);
+
+// Give a fused plan observables with X/Y factors: the last forward pass keeps
+// the final state in memory, where the X/Y terms' expectation values and
+// their part of the costate are evaluated, and the first reverse pass loads
+// that costate part and adds the Z part to it.
+void attach_pauli_terms(Plan &P, const std::vector<PauliTerm> &terms);
 
 // Per-sample cost model of a plan (bytes over the state, arithmetic).
 void plan_costs(const Plan &p, double &fwd_bytes, double &adj_bytes, double &fwd_flops,

@@ -43,6 +43,7 @@ enum OpType : int32_t {
     OP_DIAG = 7,     // product of CZ gates (diag_pairs[a .. a+b)): one sign mask
 };
 constexpr int32_t OPF_SKIP_APPLY = 1;   // GRAD: no later op touches this qubit
+constexpr int32_t OPF_ACCUMULATE = 2;   // COSTATE: add to the lam already in memory (its X/Y part)
 
 // Operand encoding: 0..31 = tile-local bit; kFixed + Q = global qubit Q that is
 // constant within the tile (outside S).
@@ -120,6 +121,15 @@ struct Term {
     double coef;
     int32_t obs;
     int32_t pad;
+};
+
+// Pauli string with X or Y factors, evaluated on the final state outside the
+// pass kernels: P|x> = i^ny (-1)^popcount(x & zmask) |x ^ xmask>, with Y where
+// both masks have the qubit (ny of them), X where only xmask has it.
+struct PauliTerm {
+    uint64_t xmask, zmask;
+    double coef;
+    int32_t obs, ny;
 };
 
 #if defined(__CUDACC__) || defined(__CUDACC_RTC__)

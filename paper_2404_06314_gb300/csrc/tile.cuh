@@ -588,14 +588,17 @@ __device__ __forceinline__ void costate_diag(R (&d)[kRegs], const TileSmem<R> &S
     }
 }
 
+// acc: q already holds the costate's X/Y part (loaded from memory); add to it.
 template <typename R>
 __device__ __forceinline__ void op_costate(const Cx<R> (&p)[kRegs], Cx<R> (&q)[kRegs], const TileSmem<R> &S,
-                                           const TileJob &j, uint32_t xt, int lo)
+                                           const TileJob &j, uint32_t xt, int lo, bool acc = false)
 {
     R d[kRegs];
     costate_diag<R>(d, S, j, xt, lo);
 #pragma unroll
-    for (int jj = 0; jj < kRegs; ++jj) q[jj] = {d[jj] * p[jj].x, d[jj] * p[jj].y};
+    for (int jj = 0; jj < kRegs; ++jj)
+        q[jj] = acc ? Cx<R>{q[jj].x + d[jj] * p[jj].x, q[jj].y + d[jj] * p[jj].y}
+                    : Cx<R>{d[jj] * p[jj].x, d[jj] * p[jj].y};
 }
 
 // CNOT with control and target both register bits: a fixed register permutation.
@@ -770,7 +773,7 @@ __device__ __forceinline__ void run_phases(const TileJob &j, const TileSmem<R> &
                 break;
             case OP_COSTATE:
                 if constexpr (REV) {
-                    op_costate<R>(p, q, S, j, xt, lo);
+                    op_costate<R>(p, q, S, j, xt, lo, (op.flags & OPF_ACCUMULATE) != 0);
                     lam_valid = true;
                 }
                 break;

@@ -386,8 +386,13 @@ __device__ __forceinline__ void run_phases_cpx(const TileJob &j, const TileSmem<
                 if constexpr (REV) {
                     float d[kRegs];
                     costate_diag<float>(d, S, j, xt, lo);
+                    if (op.flags & OPF_ACCUMULATE) {   // q holds the costate's X/Y part
 #pragma unroll
-                    for (int jj = 0; jj < kRegs; ++jj) q[jj] = mul2(pack2(d[jj], d[jj]), p[jj]);
+                        for (int jj = 0; jj < kRegs; ++jj) q[jj] = fma2(pack2(d[jj], d[jj]), p[jj], q[jj]);
+                    } else {
+#pragma unroll
+                        for (int jj = 0; jj < kRegs; ++jj) q[jj] = mul2(pack2(d[jj], d[jj]), p[jj]);
+                    }
                     lam_valid = true;
                 }
                 break;

@@ -178,7 +178,7 @@ def test_batch_size_checked_before_any_work():
     plain = capi.Plan(W.workload_4q())
     pauli = capi.Plan(W.Circuit(n=2, gates=[(W.RY, 0, -1, 0, -1, 1.0), (W.CNOT, 0, 1, -1, -1, 1.0)],
                                 terms=[(0, 1.0, 0, 1), (2, 0.5, 0)], n_obs=1, n_weights=1, n_inputs=0,
-                                name="xz"))
+                                name="xz"), path="naive")
     assert pauli.parts == 2
     for plan in (plain, pauli):
         for B in (-1, -7):
@@ -222,6 +222,31 @@ def test_pauli_observables_schedule_matches_oracle(n):
     _emulate_vs_oracle(c, 2, n)
 
 
+@pytest.mark.parametrize("n", [2, 5, 13])
+def test_pauli_direct_and_grouped_schedules_agree(n):
+    """One evolution with X/Y strings on the final state, and one plan per
+    measurement group, interpreted on the host, give the same expectation
+    values and gradients (and both equal the oracle)."""
+    rng = np.random.default_rng(3250 + n)
+    c = P.rand_small_circuit(rng, n, G=4 * n + 6, n_obs=3, extra=True, pauli=True)
+    x = rng.uniform(-np.pi, np.pi, size=(2, c.n_inputs))
+    w = rng.normal(size=c.n_weights)
+    gE = rng.normal(size=(2, c.n_obs))
+    direct = capi.Plan(c, dtype="c128")
+    assert direct.parts == 1
+    os.environ["QTM_PAULI_GROUPS"] = "1"
+    try:
+        grouped = capi.Plan(c, dtype="c128")
+    finally:
+        del os.environ["QTM_PAULI_GROUPS"]
+    a = capi.qtm_debug_emulate(direct.handle, x, w, gE, circuit=c)
+    b = capi.qtm_debug_emulate(grouped.handle, x, w, gE, circuit=c)
+    Eo = oracle.forward(c, x, w)
+    for u, v in zip(a, b):
+        assert np.max(np.abs(u - v)) < 1e-11
+    assert np.max(np.abs(a[0] - Eo)) < 1e-11
+
+
 def test_pauli_build_validates_and_groups():
     X, Y = 1, 1   # xmask bit for qubit 0
     gates = [(W.RY, 0, -1, 0, -1, 1.0)]
@@ -231,7 +256,15 @@ def test_pauli_build_validates_and_groups():
     # X0, Y0, X0 X1, Z1: groups {X0}, {Y0}, {X0 X1}, {} -> 4 parts
     c = W.Circuit(n=2, gates=gates, terms=[(0, 1.0, 0, 1), (1, 1.0, 0, 1), (0, 0.5, 0, 3), (2, 1.0, 0)],
                   n_obs=1, n_weights=1, n_inputs=0, name="g")
-    assert capi.Plan(c).parts == 4
+    # fused plans: one evolution, X/Y strings on the final state
+    assert capi.Plan(c).parts == 1
+    # the naive path (and QTM_PAULI_GROUPS=1) measure group by group
+    assert capi.Plan(c, path="naive").parts == 4
+    os.environ["QTM_PAULI_GROUPS"] = "1"
+    try:
+        assert capi.Plan(c).parts == 4
+    finally:
+        del os.environ["QTM_PAULI_GROUPS"]
     bad = [(0, 1.0, 0, 4)]    # xmask beyond n
     with pytest.raises(capi.QtmError):
         capi.Plan(W.Circuit(n=2, gates=gates, terms=bad, n_obs=1, n_weights=1, n_inputs=0, name="b"))

@@ -413,6 +413,63 @@ def uneven_only(steps):
                       "config": mp.config}))
 
 
+def measure_pauli(device, steps=20):
+    """Observables with X/Y factors: the 12-qubit workload's circuit measured
+    on H = sum_i (X_i X_{i+1} + Z_i Z_{i+1}) (11 X-strings, each its own basis
+    group, and the Z chain), B = 1024, forward + adjoint per step.  One
+    evolution (X/Y strings on the final state) against one plan per
+    measurement group (QTM_PAULI_GROUPS=1), both on the general kernels, and
+    the one-evolution plan on the default specialised kernels."""
+    import numpy as np
+    import torch
+
+    from paper_2404_06314_gb300 import capi, workloads as W
+
+    base = W.workload_12q()
+    n = base.n
+    terms = [((1 << i) | (1 << (i + 1)), 1.0, 0) for i in range(n - 1)] + \
+            [(0, 1.0, 0, (1 << i) | (1 << (i + 1))) for i in range(n - 1)]
+    c = W.Circuit(n=n, gates=base.gates, terms=terms, n_obs=1, n_weights=base.n_weights,
+                  n_inputs=base.n_inputs, name="qnn12_l6_xxzz")
+    B = 1024
+    inp = W.make_inputs(c, B, 1021, real_dtype=np.float32)
+    f32 = dict(dtype=torch.float32, device=device)
+    x, w, gE = (torch.tensor(a, **f32) for a in (inp.x, inp.w, inp.gE))
+
+    def rate(plan):
+        E = torch.empty((B, 1), **f32)
+        gx = torch.empty((B, c.n_inputs), **f32)
+        gw = torch.empty((c.n_weights,), **f32)
+        for _ in range(3):
+            plan.forward(x, w, out=E)
+            plan.adjoint(gE, x, w, gx=gx, gw=gw)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            plan.forward(x, w, out=E)
+            plan.adjoint(gE, x, w, gx=gx, gw=gw)
+        e1.record()
+        torch.cuda.synchronize()
+        return B * steps / (e0.elapsed_time(e1) / 1e3), E
+
+    one = capi.Plan(c, dtype="c64")
+    r_one, E1 = rate(one)
+    os.environ["QTM_PAULI_GROUPS"] = "1"
+    try:
+        grouped = capi.Plan(c, dtype="c64")
+    finally:
+        del os.environ["QTM_PAULI_GROUPS"]
+    r_grp, E2 = rate(grouped)
+    one.compile()
+    r_jit, E3 = rate(one)
+    return {"one_evolution_general": r_one, "groups_general": r_grp, "one_evolution_specialised": r_jit,
+            "unit": "samples/s", "groups": grouped.parts, "steps": steps,
+            "max_abs_diff_E": float(max((E1 - E2).abs().max(), (E3 - E2).abs().max())),
+            "config": f"{c.name}: the 12-qubit workload's circuit, H = sum_i X_i X_(i+1) + Z_i Z_(i+1), "
+                      f"B={B}, fwd + adjoint"}
+
+
 def measure_training(device, steps=100):
     """16-qubit training loop: QuantumModule + MSE + Adam, `steps` steps."""
     import torch
@@ -641,6 +698,7 @@ def gpu_main(args):
         extra["uneven"] = measure_uneven(max(3, args.steps // 4), device, seed_offset=rank)
         extra["train16"] = measure_training(device)
         extra["paper_context"] = measure_paper_context(device)
+        extra["pauli12"] = measure_pauli(device)
     e2e = measure_e2e(args.workload, max(3, args.steps // 4), device, seed_offset=rank, kernels=args.kernels)
     if ws > 1:
         t = torch.tensor([e2e[0]], device=device, dtype=torch.float64)

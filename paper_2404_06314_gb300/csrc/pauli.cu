@@ -21,28 +21,10 @@ namespace {
 
 constexpr int kChunkBits = 12;   // amplitudes per expectation-value CTA: 2^12
 
-// (P psi)_y for one string, from the amplitude psi_x, x = y ^ xmask.
-__device__ __forceinline__ double2 pauli_factor(const PauliTerm &t, uint64_t x, double re, double im)
-{
-    if (__popcll(x & t.zmask) & 1) { re = -re; im = -im; }
-    switch (t.ny & 3) {   // times i^ny
-    case 1: return make_double2(-im, re);
-    case 2: return make_double2(-re, -im);
-    case 3: return make_double2(im, -re);
-    default: return make_double2(re, im);
-    }
-}
-
-template <typename R>
-__device__ __forceinline__ void load_amp(const Cx<R> *psi, uint64_t i, double &re, double &im)
-{
-    const Cx<R> a = psi[i];
-    re = (double)a.x;
-    im = (double)a.y;
-}
-
-// Ppart[b][chunk][t] = Re sum over the chunk's y of conj(psi_y) (P_t psi)_y,
-// FP64; one CTA per (sample, chunk of 2^12 amplitudes), fixed reduction order.
+// Ppart[b][chunk][t] = Re sum over the chunk's y of conj(psi_y) (P_t psi)_y;
+// one CTA per (sample, chunk of 2^12 amplitudes).  A thread sums its (up to 16)
+// products in the plan's real type, the 256 thread sums are added in FP64 in
+// a fixed order.
 template <typename R>
 __global__ void k_pauli_partial(const Cx<R> *phi, int sq, const PauliTerm *terms, int T, int chunks,
                                 double *Ppart)
@@ -56,16 +38,21 @@ __global__ void k_pauli_partial(const Cx<R> *phi, int sq, const PauliTerm *terms
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int t = 0; t < T; ++t) {
         const PauliTerm pt = terms[t];
-        double s = 0.0;
+        R st = 0;
         for (uint64_t k = threadIdx.x; k < len; k += blockDim.x) {
             const uint64_t y = lo + k, x = y ^ pt.xmask;
-            double yr, yi, xr, xi;
-            load_amp<R>(psi, y, yr, yi);
-            load_amp<R>(psi, x, xr, xi);
-            const double2 v = pauli_factor(pt, x, xr, xi);
-            s += yr * v.x + yi * v.y;   // Re(conj(psi_y) v)
+            const Cx<R> a = psi[y];
+            Cx<R> v = psi[x];
+            if (__popcll(x & pt.zmask) & 1) { v.x = -v.x; v.y = -v.y; }
+            switch (pt.ny & 3) {   // times i^ny
+            case 1: v = Cx<R>{-v.y, v.x}; break;
+            case 2: v = Cx<R>{-v.x, -v.y}; break;
+            case 3: v = Cx<R>{v.y, -v.x}; break;
+            default: break;
+            }
+            st += a.x * v.x + a.y * v.y;   // Re(conj(psi_y) v)
         }
-        s = warp_sum(s, 32, 0xffffffffu);
+        double s = warp_sum((double)st, 32, 0xffffffffu);
         if (lane == 0) red[warp] = s;
         __syncthreads();
         if (threadIdx.x == 0) {

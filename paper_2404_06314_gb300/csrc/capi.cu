@@ -1104,6 +1104,8 @@ qtm_status qtm_set_sample_pairing(qtm_plan *p, int on)
         return QTM_OK;
     }
     if (on != 0 && on != 1) return fail(p, QTM_EINVAL, "on must be 0 or 1");
+    if (on && !p->P.pterms.empty())
+        return fail(p, QTM_EUNSUPPORTED, "X/Y observables need the one-sample state layout");
     if (on && !pairable(p->P)) return fail(p, QTM_EUNSUPPORTED, "pairing needs a fused complex64 plan with tiles of >= 9 qubits");
     if (on) {
         for (size_t v : p->smem_fwd_x2)

@@ -247,6 +247,23 @@ def test_pauli_direct_and_grouped_schedules_agree(n):
     assert np.max(np.abs(a[0] - Eo)) < 1e-11
 
 
+def test_pauli_plans_refuse_paired_layouts_and_noalloc():
+    """Plans with X/Y strings read the final state in its one-sample layout:
+    the two-samples-per-CTA kernels and the allocation-free forward refuse
+    them before touching a device."""
+    import ctypes
+    rng = np.random.default_rng(3290)
+    c = P.rand_small_circuit(rng, 10, G=46, n_obs=2, extra=True, pauli=True)
+    plan = capi.Plan(c, dtype="c64")
+    assert plan.parts == 1
+    with pytest.raises(capi.QtmError) as ei:
+        plan.set_pairing(True)
+    assert ei.value.status == capi.QTM_EUNSUPPORTED
+    assert "one-sample" in capi.qtm_last_error(plan.handle)
+    fake = ctypes.c_void_p(256)   # never dereferenced
+    assert capi.qtm_forward_noalloc(plan.handle, 2, fake, fake, fake, None) == capi.QTM_EUNSUPPORTED
+
+
 def test_pauli_build_validates_and_groups():
     X, Y = 1, 1   # xmask bit for qubit 0
     gates = [(W.RY, 0, -1, 0, -1, 1.0)]

@@ -337,7 +337,8 @@ qtm_status qtm_multi_destroy(qtm_multi *multi);
  * (on = 1: two samples per CTA, one per half of Blackwell's f32x2 register
  * pairs, op tables read at run time) or the one-sample kernel (on = 0, the
  * default).  Same results within rounding.  Needs a fused complex64 plan with
- * tiles of >= 9 qubits (QTM_EUNSUPPORTED otherwise).  Changing it drops the
+ * tiles of >= 9 qubits and no X/Y observables (QTM_EUNSUPPORTED otherwise:
+ * those read the final state in the one-sample layout).  Changing it drops the
  * workspace and any stored forward state (the state layout changes); it waits
  * for the device when a workspace exists.  Specialised kernels loaded by
  * qtm_compile take precedence while they are loaded. */
@@ -358,8 +359,8 @@ int qtm_get_sample_pairing(const qtm_plan *plan);
  * register pair; QTM_COMPILE_LANE_PAIRS, one sample per CTA with two
  * amplitudes (one register bit apart) per f32x2 pair.  Applies
  * to complex64 fused plans with tiles of >= 9 qubits (QTM_EUNSUPPORTED
- * otherwise, or when NVRTC is unavailable; the plan keeps the general
- * kernels).  Synchronises the device and drops the workspace and any stored
+ * otherwise, or when NVRTC is unavailable, or for QTM_COMPILE_SAMPLE_PAIRS on
+ * a plan with X/Y observables; the plan keeps the general kernels).  Synchronises the device and drops the workspace and any stored
  * forward state (the state layout changes). */
 #define QTM_COMPILE_SCALAR 1
 #define QTM_COMPILE_SAMPLE_PAIRS 2

@@ -149,12 +149,15 @@ def qtm_build_pauli(n_qubits, gates, terms, n_obs, n_weights, n_inputs, dtype=QT
 
 def qtm_build(n_qubits, gates, terms, n_obs, n_weights, n_inputs, dtype=QTM_C64,
               path=QTM_PATH_AUTO):
-    """gates: sequence of (kind, q0, q1, w_idx, x_idx, coef); terms: (zmask, coef, obs).
-    Returns a plan handle (int).  Host-only: no GPU needed."""
+    """gates: sequence of (kind, q0, q1, w_idx, x_idx, coef); terms: (zmask, coef, obs)
+    Z strings (a fourth entry, the xmask, must be 0 here: qtm_build_pauli takes
+    X/Y factors).  Returns a plan handle (int).  Host-only: no GPU needed."""
     G = _gate_array(gates)
     T = (qtm_zterm * max(len(terms), 1))()
-    for i, (m, c, o) in enumerate(terms):
-        T[i] = qtm_zterm(int(m), float(c), int(o), 0)
+    for i, t in enumerate(terms):
+        if len(t) > 3 and t[3]:
+            raise ValueError("qtm_build takes Z strings only; use qtm_build_pauli for X/Y factors")
+        T[i] = qtm_zterm(int(t[0]), float(t[1]), int(t[2]), 0)
     h = ctypes.c_void_p()
     st = lib().qtm_build(int(n_qubits), G, len(gates), T, len(terms), int(n_obs), int(n_weights),
                          int(n_inputs), int(dtype), int(path), ctypes.byref(h))

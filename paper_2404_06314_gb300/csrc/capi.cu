@@ -91,8 +91,10 @@ struct qtm_plan {
     bool profiling = false;
     struct Rec { cudaEvent_t a, b; int kind; };
     std::vector<Rec> recs[2];
-    std::vector<cudaEvent_t> ev_pool;
-    size_t ev_used = 0;
+    // one event pool per kind of call, so that an adjoint's records do not
+    // re-record the events of the forward before it
+    std::vector<cudaEvent_t> ev_pool[2];
+    size_t ev_used[2] = {0, 0};
     int cur_which = 0;
     cudaStream_t cur_stream = nullptr;
 };
@@ -369,17 +371,19 @@ void prof_begin_call(qtm_plan *p, int which, cudaStream_t s)
     p->cur_stream = s;
     if (!p->profiling) return;
     p->recs[which].clear();
-    p->ev_used = 0;
+    p->ev_used[which] = 0;
 }
 
 cudaEvent_t prof_event(qtm_plan *p)
 {
-    if (p->ev_used == p->ev_pool.size()) {
+    std::vector<cudaEvent_t> &pool = p->ev_pool[p->cur_which];
+    size_t &used = p->ev_used[p->cur_which];
+    if (used == pool.size()) {
         cudaEvent_t e;
         if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
-        p->ev_pool.push_back(e);
+        pool.push_back(e);
     }
-    return p->ev_pool[p->ev_used++];
+    return pool[used++];
 }
 
 struct ProfScope {
@@ -1289,7 +1293,8 @@ qtm_status qtm_destroy(qtm_plan *p)
     p->parts.clear();
     if (p->d_tmp) cudaFree(p->d_tmp);
     p->d_tmp = nullptr;
-    for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
+    for (const auto &pool : p->ev_pool)
+        for (cudaEvent_t e : pool) cudaEventDestroy(e);
     for (auto *v : {&p->jit_fwd, &p->jit_rev})
         for (auto &k : *v) jit_unload(k);
     if (p->d_status) {

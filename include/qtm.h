@@ -115,8 +115,9 @@ typedef struct {
     int32_t tile_qubits;     /* K: qubits per shared-memory tile */
     int32_t fwd_passes;      /* kernel passes over the state in qtm_forward */
     int32_t adj_passes;      /* passes in qtm_adjoint (without recompute) */
-    int32_t fwd_launches;    /* kernel launches per qtm_forward */
-    int32_t adj_launches;    /* kernel launches per qtm_adjoint (per-sample grad_w) */
+    int32_t fwd_launches;    /* kernel launches per qtm_forward (one-sample kernels) */
+    int32_t adj_launches;    /* kernel launches per qtm_adjoint (per-sample grad_w; one more
+                              * for the batch-summed grad_w) */
     int32_t n_runs;          /* fused single-qubit rotation runs */
     int32_t n_prefix_runs;   /* runs folded into the analytic product-state init */
     int32_t n_prefix_ents;   /* CZ/CNOT folded into the init */
@@ -128,7 +129,9 @@ typedef struct {
      * as 2: a fused 2x2 rotation 14 N, an adjoint gradient step 12 N (the
      * three inner products) plus 28 N (the rotation undone on phi and lam),
      * expectation values (3 + terms) N, costate (terms + 2) N, the analytic
-     * product-state init 6 (ceil(n/4) - 1) N; sign flips and permutations 0. */
+     * product-state init 6 (ceil(n/4) - 1) N, 4 N per string with X/Y factors
+     * (expectation value, and again for its costate part); sign flips and
+     * permutations 0. */
     double fwd_flops;        /* forward */
     double adj_flops;        /* adjoint */
 } qtm_plan_info;

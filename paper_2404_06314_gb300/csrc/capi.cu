@@ -798,8 +798,15 @@ qtm_status qtm_get_plan_info(const qtm_plan *p, qtm_plan_info *info)
     info->fwd_passes = (int)P.fwd.size();
     info->adj_passes = (int)P.rev.size();
     if (P.path == QTM_PATH_FUSED) {
-        info->fwd_launches = (int)P.fwd.size() + 2;
-        info->adj_launches = (int)P.rev.size() + 1;
+        // one-sample kernels: plans of one tile per sample run the prep in the
+        // first forward pass, write E from the measuring pass and run the
+        // gradient finalize in the last reverse pass; otherwise k_prep,
+        // k_expval_finalize and k_grad_finalize launch on their own.  X/Y
+        // strings add two launches forward and one to the adjoint.
+        const bool one_tile = P.tiles_per_sample == 1 && !P.fwd.empty();
+        const int xy = P.pterms.empty() ? 0 : 1;
+        info->fwd_launches = (int)P.fwd.size() + (one_tile ? 0 : 2) + 2 * xy;
+        info->adj_launches = (int)P.rev.size() + (one_tile ? 0 : 1) + xy;
     } else {
         int nrot = 0;
         for (const auto &g : P.gates) nrot += (g.kind <= QTM_RZ);

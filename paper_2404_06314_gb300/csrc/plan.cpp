@@ -777,6 +777,17 @@ void plan_costs(const Plan &p, double &fwd_bytes, double &adj_bytes, double &fwd
                            pd.store_lam);
         adj_flops += pass_flops(pd);
     }
+    // strings with X/Y factors on the final state: one read of it per string
+    // (its partner amplitudes come from the same cache lines or L2), 4 flop per
+    // amplitude and string (Re conj(a) b, or the cotangent-weighted add); the
+    // costate part is written once
+    const double TP = (double)p.pterms.size();
+    if (TP > 0) {
+        fwd_bytes += sb * TP;
+        fwd_flops += 4.0 * TP * N;
+        adj_bytes += sb * (TP + 1.0);
+        adj_flops += 4.0 * TP * N;
+    }
 }
 
 std::string Plan::describe() const

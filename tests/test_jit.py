@@ -97,6 +97,48 @@ def test_analytic_phi_in_registers_exactly_with_a_closed_form():
                     assert in_regs == want or ents == 0, (name, which, i)
 
 
+def _warp_sets(K, lo):
+    """Amplitudes each warp of a phase with register group [lo, lo + 4) holds,
+    enumerated from the thread layout the generated kernels use (thread
+    bits fill the non-register tile bits in order; 16 registers per thread)."""
+    T = 1 << (K - 4)
+    sets = []
+    for w in range((T + 31) // 32):
+        s = set()
+        for tid in range(32 * w, min(T, 32 * w + 32)):
+            xt = (tid & ((1 << lo) - 1)) | ((tid >> lo) << (lo + 4))
+            s.update(xt | (jj << lo) for jj in range(16))
+        sets.append(frozenset(s))
+    return sets
+
+
+@pytest.mark.parametrize("builder", ["workload_12q", "workload_20q", "workload_16q_train"])
+def test_warp_barriers_only_where_warps_keep_their_amplitudes(builder):
+    """The complex-pair kernels end a phase with __syncwarp instead of
+    __syncthreads only where every warp loads back exactly the amplitudes it
+    stored (checked here by enumerating the thread layout), and end the last
+    phase of a pass with a CTA barrier."""
+    import re
+    c = getattr(W, builder)()
+    plan = capi.Plan(c, dtype="c64")
+    info = plan.info
+    K = info["tile_qubits"]
+    local = total = 0
+    for which, n in ((0, info["fwd_passes"]), (1, info["adj_passes"])):
+        for i in range(n):
+            src = plan.jit_source(which, i, "cpx")
+            los = [int(v) for v in re.findall(r"constexpr int LO = (\d+);", src)]
+            ends = re.findall(r"__(syncwarp|syncthreads)\(\);\n    \}", src)
+            assert len(los) == len(ends) and los, (builder, which, i)
+            assert ends[-1] == "syncthreads"
+            for k in range(len(los) - 1):
+                same = _warp_sets(K, los[k]) == _warp_sets(K, los[k + 1])
+                assert (ends[k] == "syncwarp") == same, (builder, which, i, k, los[k], los[k + 1])
+                local += ends[k] == "syncwarp"
+                total += 1
+    assert 0 < local < total
+
+
 def test_not_specialised():
     c = W.workload_12q()
     assert capi.Plan(c, dtype="c128").jit_source(0, 0) == ""   # complex128 keeps the interpreter

@@ -264,6 +264,26 @@ def test_pauli_plans_refuse_paired_layouts_and_noalloc():
     assert capi.qtm_forward_noalloc(plan.handle, 2, fake, fake, fake, None) == capi.QTM_EUNSUPPORTED
 
 
+def test_plan_info_launch_counts_and_xy_costs():
+    """Launch counts as the calls launch them (one-tile plans fuse the prep,
+    the expectation values and the gradient finalize into their passes) and
+    the cost model's share of strings with X/Y factors."""
+    i12 = capi.Plan(W.workload_12q()).info
+    assert (i12["fwd_launches"], i12["adj_launches"]) == (i12["fwd_passes"], i12["adj_passes"])
+    i20 = capi.Plan(W.workload_20q()).info
+    assert (i20["fwd_launches"], i20["adj_launches"]) == (i20["fwd_passes"] + 2, i20["adj_passes"] + 1)
+    base = W.workload_12q()
+    xs = [(0, 1.0, 0, 3), (0, 0.5, 0, 12)]
+    c = W.Circuit(n=12, gates=base.gates, terms=list(base.terms) + xs, n_obs=1, n_weights=base.n_weights,
+                  n_inputs=base.n_inputs, name="xy")
+    ixy = capi.Plan(c).info
+    sb = 8 << 12
+    assert ixy["fwd_launches"] == i12["fwd_launches"] + 2 and ixy["adj_launches"] == i12["adj_launches"] + 1
+    assert ixy["fwd_state_bytes"] == i12["fwd_state_bytes"] + 2 * sb
+    assert ixy["adj_state_bytes"] == i12["adj_state_bytes"] + 3 * sb + sb   # + the costate part loaded
+    assert ixy["fwd_flops"] == i12["fwd_flops"] + 4 * 2 * 4096
+
+
 def test_pauli_build_validates_and_groups():
     X, Y = 1, 1   # xmask bit for qubit 0
     gates = [(W.RY, 0, -1, 0, -1, 1.0)]

@@ -55,9 +55,15 @@ def load_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-def fp32_alu_peak_tflops(sm_mhz: float) -> float:
-    # 152 SMs x 128 FP32 lanes x 2 flop (FMA) per clock
-    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+def sm_count(device=None) -> int:
+    """Streaming multiprocessors of the device (queried, not assumed)."""
+    import torch
+    return int(torch.cuda.get_device_properties(device if device is not None else 0).multi_processor_count)
+
+
+def fp32_alu_peak_tflops(sm_mhz: float, sms: int) -> float:
+    # SMs x 128 FP32 lanes x 2 flop (FMA) per clock
+    return sms * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
 class ClockSampler:
@@ -153,14 +159,16 @@ def roofline(r, peaks, peak_src):
     passes = max(1, info["adj_passes"])
     flops = info["adj_flops"] * B / passes
     bytes_ = info["adj_state_bytes"] * B / passes
-    alu_peak = fp32_alu_peak_tflops(peaks.get("sm_max_mhz", 2070.0))
+    sms = r["sm_count"]
+    alu_peak = fp32_alu_peak_tflops(peaks.get("sm_max_mhz", 2070.0), sms)
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     alu = flops / t / 1e12
     hbm = bytes_ / t / 1e9
     alu_obj = {"bound": "alu", "achieved": alu, "peak": alu_peak, "unit": "TFLOP/s",
                "frac": alu / alu_peak,
-               "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x %g MHz (sm_max_mhz of "
-                              "MEASURED_PEAKS.json)" % peaks.get("sm_max_mhz", 2070.0)}
+               "sm_count": sms,
+               "peak_source": "derived: %d SMs (queried) x 128 FP32 lanes x 2 flop x %g MHz (sm_max_mhz of "
+                              "MEASURED_PEAKS.json)" % (sms, peaks.get("sm_max_mhz", 2070.0))}
     hbm_obj = {"bound": "hbm", "achieved": hbm, "peak": hbm_peak, "unit": "GB/s",
                "frac": hbm / hbm_peak, "peak_source": f"{peak_src} hbm_gbs (burst copy)"}
     main, other = (alu_obj, hbm_obj) if alu_obj["frac"] >= hbm_obj["frac"] else (hbm_obj, alu_obj)
@@ -311,6 +319,7 @@ def measure_gpu(name, steps, warmup, device, seed_offset=0, profile=True, kernel
     plan.sync()
     outputs = (E.double().cpu().numpy(), gx_o.double().cpu().numpy(), gw_ps.double().cpu().numpy())
     return dict(c=c, B=B, plan=plan, inp=inp, step_ms=step_ms, info=info, kernels=kernels, workload=name,
+                sm_count=sm_count(device),
                 outputs=outputs,
                 pass_fwd_ms=pass_fwd_ms, pass_rev_ms=pass_rev_ms, n_fwd_pass=n_fwd_pass,
                 n_rev_pass=n_rev_pass, launches=launches)
@@ -351,6 +360,25 @@ def measure_uneven(steps, device, count=256, seed_offset=0):
         tot += e0.elapsed_time(e1)
     mp.sync()
     graph_rate = count * steps / (tot / 1e3)
+
+    def timed(fn, k):
+        fn()
+        torch.cuda.synchronize()
+        t = 0.0
+        for _ in range(k):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            t += a.elapsed_time(b)
+        return t / k
+
+    # inference alone (qtm_multi_forward), and the two split calls back to back
+    fwd_ms = timed(lambda: mp.forward(x, w, E, graph=True), steps)
+    split_ms = timed(lambda: (mp.forward(x, w, E, graph=True), mp.adjoint(x, w, g, gx, gw, graph=True)), steps)
+    mp.sync()
     # the same work as separate per-circuit launches (plans built up front)
     plans = [capi.Plan(c, dtype="c64") for c in cs]
     tens = [(torch.tensor(a, dtype=torch.float32, device=device), torch.tensor(b, dtype=torch.float32, device=device),
@@ -375,6 +403,12 @@ def measure_uneven(steps, device, count=256, seed_offset=0):
         tot2 += e0.elapsed_time(e1)
     ns = [c.n for c in cs]
     return {"value": graph_rate, "unit": "samples/s", "ms_per_step": tot / steps, "steps": steps,
+            "forward_only": {"value": count / (fwd_ms / 1e3), "unit": "samples/s", "ms_per_step": fwd_ms,
+                             "launch": "qtm_multi_forward, one persistent kernel, replayed from a CUDA graph"},
+            "split_forward_then_adjoint": {"value": count / (split_ms / 1e3), "unit": "samples/s",
+                                           "ms_per_step": split_ms,
+                                           "launch": "qtm_multi_forward + qtm_multi_adjoint (states stored "
+                                                     "between them), each graph-replayed"},
             "per_circuit_launches": {"value": count * k2 / (tot2 / 1e3), "unit": "samples/s",
                                      "ms_per_step": tot2 / k2},
             "config": {"workload": f"uneven: {count} circuits, n ~ U{{6..16}} (min {min(ns)}, max {max(ns)}), "

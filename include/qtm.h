@@ -218,24 +218,29 @@ qtm_status qtm_jacobian(qtm_plan *plan, int B, const void *x, const void *w, voi
 /*
  * qtm_forward_noalloc: the expectation values of qtm_forward, without any
  * device allocation.  The paper has no counterpart; this exists for callers
- * that cannot call cudaMalloc: code running while a stream is captured into a
- * CUDA graph (allocation is not capturable and may synchronise the device),
- * programs whose GPU memory is owned by another allocator with a fixed budget,
- * and latency-critical loops that must not stall on a first-call allocation.
+ * that cannot call cudaMalloc: host programs whose GPU memory is owned by
+ * another allocator with a fixed budget (a framework that reserves the
+ * device's memory up front, an application that forbids its plugins to
+ * allocate), and loops that must not stall on an allocation, which can
+ * synchronise the device.
  *
  * Instead of plan-owned buffers it uses one file-scope device array of
  * QTM_NOALLOC_SCRATCH_BYTES (8 MiB) that the library keeps on every GPU it is
  * loaded on until the process exits.  Arguments are those of qtm_forward
- * (device pointers, plan real type), with B >= 1.  Supported for fused plans whose state
- * fits one shared-memory tile (n <= 12): otherwise QTM_EUNSUPPORTED.  A batch
- * whose tables and scratch exceed the array returns QTM_EINVAL before any
- * work is enqueued (about 2.8 MB for 12 qubits, 6 layers, B = 1024).
+ * (device pointers, plan real type), with B >= 1.  Supported for fused plans
+ * whose state fits one shared-memory tile (n <= 12): otherwise
+ * QTM_EUNSUPPORTED.  A batch whose tables and scratch exceed the array returns
+ * QTM_EINVAL before any work is enqueued (about 2.8 MB for 12 qubits, 6
+ * layers, B = 1024).  The call copies the plan's tables (a few KB) from host
+ * memory each time; those copies return once the bytes are staged.
  *
- * The first call on each device resolves the array's device address there
- * (cudaGetSymbolAddress), so make that first call before any stream capture.
- * Every call shares the array: calls that overlap on the GPU (different
- * streams, or different plans at the same time) race and must be serialised
- * by the caller.  It stores no state for qtm_adjoint.
+ * Set-up: the first call on each device (and the first after that device's
+ * context was reset) loads the library's device code there and resolves the
+ * array's device address (cudaGetSymbolAddress, with that device current), so
+ * make that first call before any stream capture.  Every call shares the
+ * array and no call clears what an earlier one left in it: calls that overlap
+ * on the GPU (different streams, or different plans at the same time) race
+ * and must be serialised by the caller.  It stores no state for qtm_adjoint.
  */
 qtm_status qtm_forward_noalloc(qtm_plan *plan, int B, const void *x, const void *w,
                                void *expvals, void *stream);
@@ -305,7 +310,8 @@ qtm_status qtm_build_multi(const qtm_circuit *circuits, int n_circuits, int batc
  * offsets[n_circuits] = total elements. */
 qtm_status qtm_multi_offsets(const qtm_multi *multi, int which, int64_t *offsets);
 
-/* Forward + adjoint of every (circuit, sample) in one persistent launch: a
+/* Forward + adjoint of every (circuit, sample) in one persistent launch (the
+ * fused fast path; qtm_multi_forward and qtm_multi_adjoint below split it): a
  * device work counter hands tasks to CTAs in a fixed list order; circuits with
  * n <= 12 run both directions in shared memory as one task, larger ones sweep
  * tiles of their own states, either inside one CTA (split = 0) or as one task
@@ -317,6 +323,39 @@ qtm_status qtm_multi_offsets(const qtm_multi *multi, int which, int64_t *offsets
 #define QTM_MULTI_GRAPH 1
 qtm_status qtm_multi_run(qtm_multi *multi, const void *x, const void *w, const void *grad_expvals,
                          void *expvals, void *grad_x, void *grad_w, int flags, void *stream);
+
+/*
+ * qtm_multi_forward: the expectation values alone (Eq. (qnn) for every
+ * circuit's samples, Sec. II-B's batched forward) in one persistent launch:
+ * prep, the forward passes of every (circuit, sample), the fixed-order sums
+ * into E.  x, w, E: packed device buffers as for qtm_multi_run.  Every item's
+ * final state stays in the batch's workspace for one following
+ * qtm_multi_adjoint with the same x and w on the same stream (an inference-
+ * only caller just never calls it).  flags: QTM_MULTI_GRAPH (a graph of its
+ * own, captured on first use for these buffers).
+ */
+qtm_status qtm_multi_forward(qtm_multi *multi, const void *x, const void *w, void *expvals, int flags,
+                             void *stream);
+
+/*
+ * qtm_multi_adjoint: the vector-Jacobian product (Sec. II-A adjoint method,
+ * per circuit and sample as in Sec. II-B) from the states the last
+ * qtm_multi_forward stored: the reverse passes of every (circuit, sample) in
+ * one persistent launch, then grad_x [batch][n_inputs_c] and the batch-summed
+ * grad_w [n_weights_c] of every circuit (packed, overwritten).  The stored
+ * states are consumed.  Returns QTM_ESTATE, before any CUDA call, when no
+ * stored forward matches (x, w), or when qtm_multi_run, qtm_multi_tune or a
+ * configuration change ran since; with QTM_MULTI_RECOMPUTE the forward is
+ * evolved again inside the same launch instead (E is not written) and no
+ * stored forward is needed.  flags: QTM_MULTI_GRAPH | QTM_MULTI_RECOMPUTE.
+ */
+#define QTM_MULTI_RECOMPUTE 2
+qtm_status qtm_multi_adjoint(qtm_multi *multi, const void *x, const void *w, const void *grad_expvals,
+                             void *grad_x, void *grad_w, int flags, void *stream);
+
+/* Message of the last error recorded on this uneven batch ("" if none);
+ * owned by the batch, valid until the next call on it. */
+const char *qtm_multi_last_error(const qtm_multi *multi);
 
 /* Autotune the launch configuration on these buffers: time each candidate
  * (CTAs per SM x item order x fusion width x split) with CUDA events and keep the

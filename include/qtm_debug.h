@@ -48,6 +48,13 @@ qtm_status qtm_debug_jit_compile(qtm_plan *plan, int flags);
 qtm_status qtm_debug_multi_tasks(const qtm_multi *multi, int32_t *tasks, int capacity, int *n_tasks,
                                  int32_t *items, int item_capacity, int *n_items);
 
+/* The task list of one launch kind (host only): which = 0 qtm_multi_run
+ * (the list qtm_debug_multi_tasks returns), 1 qtm_multi_forward (forward
+ * passes only), 2 qtm_multi_adjoint (reverse passes only; a tile task's step
+ * still counts the forward passes first).  Triples as above. */
+qtm_status qtm_debug_multi_mode_tasks(const qtm_multi *multi, int which, int32_t *tasks, int capacity,
+                                      int *n_tasks);
+
 /* Failure injection for the persistent kernel's bounded waits: replace the
  * task list by n (item, step, tile) triples and set the limit of one task's
  * wait to wait_ns (> 0; 10 s by default).  Every index is range-checked, but

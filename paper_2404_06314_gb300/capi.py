@@ -379,6 +379,7 @@ class Plan:
 
 QTM_MULTI_X, QTM_MULTI_W, QTM_MULTI_GE, QTM_MULTI_E, QTM_MULTI_GX, QTM_MULTI_GW = range(6)
 QTM_MULTI_GRAPH = 1
+QTM_MULTI_RECOMPUTE = 2
 
 
 class qtm_circuit(ctypes.Structure):
@@ -399,6 +400,11 @@ def _multi_lib():
         L.qtm_build_multi.argtypes = [vp, i, i, i, P(vp)]
         L.qtm_multi_offsets.argtypes = [vp, i, vp]
         L.qtm_multi_run.argtypes = [vp, vp, vp, vp, vp, vp, vp, i, vp]
+        L.qtm_multi_forward.argtypes = [vp, vp, vp, vp, i, vp]
+        L.qtm_multi_adjoint.argtypes = [vp, vp, vp, vp, vp, vp, i, vp]
+        L.qtm_multi_last_error.argtypes = [vp]
+        L.qtm_multi_last_error.restype = ctypes.c_char_p
+        L.qtm_debug_multi_mode_tasks.argtypes = [vp, i, vp, i, P(i)]
         L.qtm_multi_tune.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, ctypes.c_char_p]
         L.qtm_multi_get_config.argtypes = [vp, P(qtm_multi_config)]
         L.qtm_multi_set_config.argtypes = [vp, P(qtm_multi_config)]
@@ -406,8 +412,9 @@ def _multi_lib():
         L.qtm_multi_sync.argtypes = [vp, vp]
         L.qtm_debug_multi_tasks.argtypes = [vp, vp, i, P(i), vp, i, P(i)]
         L.qtm_debug_multi_inject.argtypes = [vp, vp, i, ctypes.c_longlong]
-        for f in ("qtm_debug_multi_tasks", "qtm_debug_multi_inject", "qtm_multi_sync", "qtm_build_multi", "qtm_multi_offsets", "qtm_multi_run", "qtm_multi_tune",
-                  "qtm_multi_get_config", "qtm_multi_set_config", "qtm_multi_destroy"):
+        for f in ("qtm_debug_multi_tasks", "qtm_debug_multi_inject", "qtm_multi_sync", "qtm_build_multi",
+                  "qtm_multi_offsets", "qtm_multi_run", "qtm_multi_forward", "qtm_multi_adjoint", "qtm_multi_tune",
+                  "qtm_multi_get_config", "qtm_multi_set_config", "qtm_multi_destroy", "qtm_debug_multi_mode_tasks"):
             getattr(L, f).restype = ctypes.c_int
         L._multi_ready = True
     return L
@@ -494,6 +501,30 @@ class MultiPlan:
         if st != QTM_OK:
             raise QtmError(st, "qtm_multi_run")
 
+    def last_error(self) -> str:
+        return (_multi_lib().qtm_multi_last_error(self.handle) or b"").decode()
+
+    def forward(self, x, w, E, graph: bool = False, stream=None):
+        """qtm_multi_forward: expectation values only; the states stay for
+        one following adjoint with the same x and w."""
+        import torch
+        s = (stream or torch.cuda.current_stream()).cuda_stream
+        st = _multi_lib().qtm_multi_forward(self.handle, self._p(x), self._p(w), self._p(E),
+                                            QTM_MULTI_GRAPH if graph else 0, ctypes.c_void_p(s))
+        if st != QTM_OK:
+            raise QtmError(st, "qtm_multi_forward: " + self.last_error())
+
+    def adjoint(self, x, w, gE, gx, gw, graph: bool = False, recompute: bool = False, stream=None):
+        """qtm_multi_adjoint: gradients from the stored states (or, with
+        recompute, from a forward evolved again in the same launch)."""
+        import torch
+        s = (stream or torch.cuda.current_stream()).cuda_stream
+        flags = (QTM_MULTI_GRAPH if graph else 0) | (QTM_MULTI_RECOMPUTE if recompute else 0)
+        st = _multi_lib().qtm_multi_adjoint(self.handle, self._p(x), self._p(w), self._p(gE), self._p(gx),
+                                            self._p(gw), flags, ctypes.c_void_p(s))
+        if st != QTM_OK:
+            raise QtmError(st, "qtm_multi_adjoint: " + self.last_error())
+
     def sync(self, stream=None):
         import torch
         s = (stream or torch.cuda.current_stream()).cuda_stream
@@ -533,6 +564,20 @@ class MultiPlan:
         if st != QTM_OK:
             raise QtmError(st, "qtm_debug_multi_tasks")
         return t[:nt.value], it[:ni.value]
+
+    def debug_mode_tasks(self, which: int):
+        """Task list [n, 3] of (item, step, tile) of one launch kind: 0 run,
+        1 forward only, 2 adjoint only (host only)."""
+        L = _multi_lib()
+        nt = ctypes.c_int()
+        st = L.qtm_debug_multi_mode_tasks(self.handle, int(which), None, 0, ctypes.byref(nt))
+        if st != QTM_OK:
+            raise QtmError(st, "qtm_debug_multi_mode_tasks")
+        t = np.zeros((max(1, nt.value), 3), dtype=np.int32)
+        st = L.qtm_debug_multi_mode_tasks(self.handle, int(which), t.ctypes.data, nt.value, None)
+        if st != QTM_OK:
+            raise QtmError(st, "qtm_debug_multi_mode_tasks")
+        return t[:nt.value]
 
     def debug_inject(self, tasks, wait_ns: int):
         """Replace the task list (bounded-wait failure injection)."""

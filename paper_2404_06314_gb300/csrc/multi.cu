@@ -1,5 +1,7 @@
 // Uneven batches: many circuits (different n and depth), `batch` samples each,
-// forward + adjoint in one persistent kernel launch.
+// forward + adjoint in one persistent kernel launch (qtm_multi_run), or the
+// forward alone (qtm_multi_forward, states kept in the workspace) and the
+// adjoint alone (qtm_multi_adjoint, consuming them) as two launches.
 //
 // Work items are (circuit, sample) pairs.  A circuit whose state fits one
 // shared-memory tile (n <= 12) runs its forward pass, expectation values,
@@ -55,6 +57,11 @@ struct Task {
     int item, step, tile;
 };
 
+// Which passes one launch runs.  MODE_BOTH keeps a one-tile item's state in
+// shared memory from its forward into its reverse pass; MODE_FWD stores every
+// item's final state in the workspace and MODE_ADJ starts from it.
+enum { MODE_BOTH = 0, MODE_FWD = 1, MODE_ADJ = 2 };
+
 struct MultiArgs {
     int n_items, B;
     const WorkItem *items;
@@ -83,6 +90,7 @@ struct MultiArgs {
     unsigned *abort;              // set when a wait of this run gave up: the others stop waiting
     unsigned *done;               // [n_items] tile tasks completed per item (split schedule)
     int n_circ, n_passes, n_ops_total, n_phases_total;
+    int mode;                     // MODE_BOTH, MODE_FWD (forward passes only), MODE_ADJ (reverse only)
     // shared-memory layout bounds (max over all passes of all circuits)
     int max_slots, max_terms, max_M, max_ents, max_sq;
 };
@@ -117,7 +125,7 @@ __device__ __forceinline__ TileJob make_job(const MultiArgs &m, const CircDev &c
     j.terms = m.terms + cd.terms_off;
     j.n_terms = cd.n_terms;
     j.M = cd.M;
-    j.gE = static_cast<const R *>(m.gE) + cd.gE_off + (size_t)b * cd.M;
+    j.gE = m.gE ? static_cast<const R *>(m.gE) + cd.gE_off + (size_t)b * cd.M : nullptr;
     j.phi_src = pd.phi_src;
     j.lam_src = pd.lam_src;
     return j;
@@ -254,7 +262,9 @@ __global__ void __launch_bounds__(256, MINB) k_multi(const MultiArgs m)
         const CircDev cd = m.circ[wi.c];
         if (cd.fwd_begin < 0 || cd.rev_begin + cd.n_rev > m.n_passes || cd.tiles < 1 || cd.tiles > (1 << 18) ||
             wi.b < 0 || wi.b >= m.B || tk.step >= cd.n_fwd + cd.n_rev || tk.tile < 0 || tk.tile >= cd.tiles ||
-            (tk.step >= 0 && cd.tiles == 1)) {
+            (tk.step >= 0 && cd.tiles == 1) ||
+            (tk.step >= 0 && m.mode == MODE_FWD && tk.step >= cd.n_fwd) ||
+            (tk.step >= 0 && m.mode == MODE_ADJ && tk.step < cd.n_fwd)) {
             if (threadIdx.x == 0) atomicOr(m.status, 2u);
             continue;
         }
@@ -267,7 +277,10 @@ __global__ void __launch_bounds__(256, MINB) k_multi(const MultiArgs m)
             // one tile of one pass: wait (bounded) for every tile of the item's
             // previous pass, run it, then count it done
             if (threadIdx.x == 0) {
-                const unsigned need = (unsigned)tk.step * (unsigned)cd.tiles;
+                // the done counters start at zero in every launch: an adjoint-only
+                // launch counts its reverse passes from the first one
+                const int first = m.mode == MODE_ADJ ? cd.n_fwd : 0;
+                const unsigned need = (unsigned)(tk.step - first) * (unsigned)cd.tiles;
                 const unsigned long long t0 = global_ns();
                 unsigned have;
                 bool failed = false;
@@ -292,15 +305,22 @@ __global__ void __launch_bounds__(256, MINB) k_multi(const MultiArgs m)
             __syncthreads();
             if (!ready) continue;
         }
-        // a whole item (every pass, every tile, in order) or one (pass, tile) task
+        // a whole item (the launch's passes, every tile, in order) or one
+        // (pass, tile) task.  Only a launch that runs both directions keeps a
+        // one-tile item's state in shared memory between its passes; the
+        // one-direction launches store it to (forward) or load it from
+        // (adjoint) the item's state buffer as the pass descriptors say.
         const bool whole = tk.step < 0;
-        const int k0 = whole ? 0 : tk.step, k1 = whole ? cd.n_fwd + cd.n_rev : tk.step + 1;
+        const int kb = m.mode == MODE_ADJ ? cd.n_fwd : 0;
+        const int ke = m.mode == MODE_FWD ? cd.n_fwd : cd.n_fwd + cd.n_rev;
+        const int k0 = whole ? kb : tk.step, k1 = whole ? ke : tk.step + 1;
         const int t0 = whole ? 0 : tk.tile, t1 = whole ? cd.tiles : tk.tile + 1;
+        const bool resident = cd.tiles == 1 && m.mode == MODE_BOTH;
         for (int k = k0; k < k1; ++k) {
             const bool rev = k >= cd.n_fwd;
             const PassDesc pd = m.passes[rev ? cd.rev_begin + (k - cd.n_fwd) : cd.fwd_begin + k];
             for (int t = t0; t < t1; ++t)
-                run_tile<R>(m, S, cd, pd, rev, cd.tiles == 1, b, t, gphi, glam, Epart_b, Gpart_b);
+                run_tile<R>(m, S, cd, pd, rev, resident, b, t, gphi, glam, Epart_b, Gpart_b);
         }
         if (!whole) {
             __threadfence();   // this tile's state writes before the count (release)
@@ -370,7 +390,8 @@ struct qtm_multi {
     // host-side images
     std::vector<CircDev> circ;
     std::vector<WorkItem> items;
-    std::vector<Task> tasks;
+    std::vector<Task> tasks;                  // MODE_BOTH (qtm_multi_run)
+    std::vector<Task> tasks_fwd, tasks_adj;   // MODE_FWD, MODE_ADJ
     std::vector<PassDesc> passes;
     std::vector<DevOp> ops;
     std::vector<DiagPair> diag;
@@ -395,12 +416,17 @@ struct qtm_multi {
     double *d_dbl = nullptr;        // Epart, Gpart, abar, gwws
     unsigned *d_counter = nullptr;   // [0] status, [1] task counter, [2] abort, [3 ..] per-item done counters
     MultiArgs args{};
-    // graph cache
-    cudaGraphExec_t gexec = nullptr;
-    cudaGraph_t graph = nullptr;
+    const Task *dev_tasks[3] = {nullptr, nullptr, nullptr};   // per mode
+    int n_tasks[3] = {0, 0, 0};
+    // graph cache: qtm_multi_run, forward, adjoint, adjoint with recompute
+    cudaGraphExec_t gexec[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaGraph_t graph[4] = {nullptr, nullptr, nullptr, nullptr};
     cudaStream_t cap_stream = nullptr;
-    const void *gkey[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    const void *gkey[4][6] = {};
     const int *wcirc_dev = nullptr;
+    // the states a qtm_multi_forward left for qtm_multi_adjoint
+    bool fwd_valid = false;
+    const void *fwd_x = nullptr, *fwd_w = nullptr;
     std::string err;
 };
 
@@ -408,11 +434,13 @@ namespace {
 
 void release_graph(qtm_multi *m)
 {
-    if (m->gexec) cudaGraphExecDestroy(m->gexec);
-    if (m->graph) cudaGraphDestroy(m->graph);
-    m->gexec = nullptr;
-    m->graph = nullptr;
-    std::fill(std::begin(m->gkey), std::end(m->gkey), nullptr);
+    for (int k = 0; k < 4; ++k) {
+        if (m->gexec[k]) cudaGraphExecDestroy(m->gexec[k]);
+        if (m->graph[k]) cudaGraphDestroy(m->graph[k]);
+        m->gexec[k] = nullptr;
+        m->graph[k] = nullptr;
+        std::fill(std::begin(m->gkey[k]), std::end(m->gkey[k]), nullptr);
+    }
 }
 
 void release_device(qtm_multi *m)
@@ -426,49 +454,57 @@ void release_device(qtm_multi *m)
     m->d_dbl = nullptr;
     m->d_counter = nullptr;
     m->dirty = true;
+    m->fwd_valid = false;
 }
 
-double item_cost(const Plan &P)
+// Estimated cost of an item's passes in a launch of the given mode.
+double item_cost(const Plan &P, int mode = MODE_BOTH)
 {
     double fb, ab, ff, af;
     plan_costs(P, fb, ab, ff, af);
-    return ff + af + 4.0 * (fb + ab);
+    const double f = ff + 4.0 * fb, a = af + 4.0 * ab;
+    return mode == MODE_FWD ? f : mode == MODE_ADJ ? a : f + a;
 }
 
-// The task list.  split = 0: one whole task per item, in item order.
-// split = 1: a tiled item becomes one task per (pass, tile).  With order 0
-// the tasks are listed highest level first (a list schedule): a task's level
-// is the estimated time from its start to the end of its item's chain, i.e.
-// the item's cost for a whole task and (passes left) x (cost of one pass's
-// tile) for a tile task, so the long chains of the largest circuits start
-// first and whole small items fill in between their passes.  With order 1 they
-// are listed pass by pass: every item's pass 0 (whole items there too), then
-// every item's pass 1, ...  Either way a tile task comes after every tile of
-// its item's previous pass, which the kernel's waits rely on.
-void build_tasks(qtm_multi *m)
+// The task list of one launch mode (MODE_BOTH: every pass; MODE_FWD: the
+// forward passes; MODE_ADJ: the reverse passes).  split = 0: one whole task
+// per item, in item order.  split = 1: a tiled item becomes one task per
+// (pass, tile).  With order 0 the tasks are listed highest level first (a
+// list schedule): a task's level is the estimated time from its start to the
+// end of its item's chain in this launch, i.e. the item's cost for a whole
+// task and (passes left) x (cost of one pass's tile) for a tile task, so the
+// long chains of the largest circuits start first and whole small items fill
+// in between their passes.  With order 1 they are listed pass by pass: every
+// item's first pass (whole items there too), then every item's second pass,
+// ...  Either way a tile task comes after every tile of its item's previous
+// pass of the launch, which the kernel's waits rely on.
+std::vector<Task> build_tasks(const qtm_multi *m, int mode)
 {
-    m->tasks.clear();
+    std::vector<Task> out;
     const int ni = (int)m->items.size();
     if (m->cfg.split == 0) {
-        for (int i = 0; i < ni; ++i) m->tasks.push_back({i, -1, 0});
-        return;
+        for (int i = 0; i < ni; ++i) out.push_back({i, -1, 0});
+        return out;
     }
     struct Key {
         double level;
-        int item, step, tile;
+        int item, step, tile, rank;   // rank: pass index within this launch
     };
     std::vector<Key> keys;
     for (int i = 0; i < ni; ++i) {
         const Plan &P = m->plans[m->items[i].c];
-        const int tiles = P.tiles_per_sample, steps = (int)(P.fwd.size() + P.rev.size());
-        const double cost = item_cost(P);
-        if (tiles <= 1 || steps < 1) {
-            keys.push_back({cost, i, -1, 0});
+        const int nf = (int)P.fwd.size(), nr = (int)P.rev.size();
+        const int kb = mode == MODE_ADJ ? nf : 0;
+        const int ke = mode == MODE_FWD ? nf : nf + nr;
+        const int tiles = P.tiles_per_sample, steps = ke - kb;
+        const double cost = item_cost(P, mode);
+        if (tiles <= 1 || nf + nr < 1) {
+            keys.push_back({cost, i, -1, 0, 0});
             continue;
         }
-        for (int k = 0; k < steps; ++k)
+        for (int k = kb; k < ke; ++k)
             for (int t = 0; t < tiles; ++t)
-                keys.push_back({(double)(steps - k) * cost / ((double)steps * tiles), i, k, t});
+                keys.push_back({(double)(ke - k) * cost / ((double)steps * tiles), i, k, t, k - kb});
     }
     if (m->cfg.order == 0)
         std::sort(keys.begin(), keys.end(), [](const Key &a, const Key &b) {
@@ -478,9 +514,9 @@ void build_tasks(qtm_multi *m)
             return a.tile < b.tile;
         });
     else
-        std::stable_sort(keys.begin(), keys.end(),
-                         [](const Key &a, const Key &b) { return std::max(a.step, 0) < std::max(b.step, 0); });
-    for (const Key &k : keys) m->tasks.push_back({k.item, k.step, k.tile});
+        std::stable_sort(keys.begin(), keys.end(), [](const Key &a, const Key &b) { return a.rank < b.rank; });
+    for (const Key &k : keys) out.push_back({k.item, k.step, k.tile});
+    return out;
 }
 
 // (Re)plan every circuit with the current fusion width and lay out the tables.
@@ -558,7 +594,7 @@ qtm_status plan_all(qtm_multi *m)
         d.abar_off = ab; ab += B * std::max(1, d.n_rots);
         d.gwws_off = gw; gw += B * std::max(1, d.P);
         d.state_off = st;
-        if (d.tiles > 1) st += B * (2ll << d.sq);
+        st += B * (2ll << d.sq);   // phi and lam; one-tile items use them between split launches
     }
     m->n_mats = mats; m->n_tabs = tabs; m->n_epart = ep; m->n_gpart = gp; m->n_abar = ab; m->n_gwws = gw;
     m->n_state = st;
@@ -572,7 +608,9 @@ qtm_status plan_all(qtm_multi *m)
         std::stable_sort(m->items.begin(), m->items.end(),
                          [&](const WorkItem &a, const WorkItem &b) { return cost[a.c] > cost[b.c]; });
     }
-    build_tasks(m);
+    m->tasks = build_tasks(m, MODE_BOTH);
+    m->tasks_fwd = build_tasks(m, MODE_FWD);
+    m->tasks_adj = build_tasks(m, MODE_ADJ);
     m->wait_ns = kMultiWaitNs;
     m->injected = false;
     const int csize = elem_bytes(m->dtype);
@@ -601,6 +639,7 @@ qtm_status upload(qtm_multi *m)
     release_device(m);
     std::vector<unsigned char> blob;
     const size_t o_tasks = put(blob, m->tasks);
+    const size_t o_tasks_fwd = put(blob, m->tasks_fwd), o_tasks_adj = put(blob, m->tasks_adj);
     const size_t o_items = put(blob, m->items), o_circ = put(blob, m->circ), o_passes = put(blob, m->passes),
                  o_ops = put(blob, m->ops), o_diag = put(blob, m->diag), o_phases = put(blob, m->phases),
                  o_slots = put(blob, m->slots), o_runs = put(blob, m->runs), o_rots = put(blob, m->rots),
@@ -629,8 +668,15 @@ qtm_status upload(qtm_multi *m)
     a.n_items = (int)m->items.size();
     a.B = m->B;
     a.items = reinterpret_cast<const WorkItem *>(db + o_items);
-    a.tasks = reinterpret_cast<const Task *>(db + o_tasks);
-    a.n_tasks = (int)m->tasks.size();
+    m->dev_tasks[MODE_BOTH] = reinterpret_cast<const Task *>(db + o_tasks);
+    m->dev_tasks[MODE_FWD] = reinterpret_cast<const Task *>(db + o_tasks_fwd);
+    m->dev_tasks[MODE_ADJ] = reinterpret_cast<const Task *>(db + o_tasks_adj);
+    m->n_tasks[MODE_BOTH] = (int)m->tasks.size();
+    m->n_tasks[MODE_FWD] = (int)m->tasks_fwd.size();
+    m->n_tasks[MODE_ADJ] = (int)m->tasks_adj.size();
+    a.mode = MODE_BOTH;
+    a.tasks = m->dev_tasks[MODE_BOTH];
+    a.n_tasks = m->n_tasks[MODE_BOTH];
     a.wait_ns = m->wait_ns;
     a.circ = reinterpret_cast<const CircDev *>(db + o_circ);
     a.passes = reinterpret_cast<const PassDesc *>(db + o_passes);
@@ -676,24 +722,33 @@ qtm_status upload(qtm_multi *m)
 
 namespace {
 
+// One launch sequence.  MODE_BOTH: prep, forward + reverse passes, expectation
+// values (when with_E) and gradients; MODE_FWD: prep, forward passes,
+// expectation values; MODE_ADJ: reverse passes from the stored states and
+// gradients (the prep tables of the forward are reused).
 template <typename R>
-cudaError_t enqueue_t(qtm_multi *m, cudaStream_t s)
+cudaError_t enqueue_t(qtm_multi *m, cudaStream_t s, int mode, bool with_E)
 {
-    const MultiArgs &a = m->args;
+    MultiArgs a = m->args;
+    a.mode = mode;
+    a.tasks = m->dev_tasks[mode];
+    a.n_tasks = m->n_tasks[mode];
     const int ni = a.n_items;
     cudaError_t e = cudaMemsetAsync(a.counter, 0, (2 + (size_t)ni) * sizeof(unsigned), s);   // counter, abort, done[]
     if (e != cudaSuccess) return e;
-    k_multi_prep<R><<<ni, 128, 0, s>>>(a);
+    if (mode != MODE_ADJ) k_multi_prep<R><<<ni, 128, 0, s>>>(a);
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device);
     const int cps = m->cfg.ctas_per_sm >= 2 ? 2 : 1;
     const int grid = std::max(1, std::min(a.n_tasks, cps * sms));
     if (cps == 2) k_multi<R, 2><<<grid, 256, m->smem, s>>>(a);
     else k_multi<R, 1><<<grid, 256, m->smem, s>>>(a);
-    k_multi_expval<R><<<ni, 32, 0, s>>>(a);
-    k_multi_grad<R><<<ni, 256, 0, s>>>(a);
-    const int tw = (int)m->wcirc.size();
-    if (tw > 0) k_multi_gw<R><<<(tw + 255) / 256, 256, 0, s>>>(a, m->wcirc_dev, tw);
+    if (mode == MODE_FWD || (mode == MODE_BOTH && with_E)) k_multi_expval<R><<<ni, 32, 0, s>>>(a);
+    if (mode != MODE_FWD) {
+        k_multi_grad<R><<<ni, 256, 0, s>>>(a);
+        const int tw = (int)m->wcirc.size();
+        if (tw > 0) k_multi_gw<R><<<(tw + 255) / 256, 256, 0, s>>>(a, m->wcirc_dev, tw);
+    }
     return cudaGetLastError();
 }
 
@@ -712,46 +767,52 @@ cudaError_t set_smem_attr(qtm_multi *m)
     return e;
 }
 
-cudaError_t enqueue(qtm_multi *m, cudaStream_t s)
+cudaError_t enqueue(qtm_multi *m, cudaStream_t s, int mode, bool with_E)
 {
-    return m->dtype == QTM_C128 ? enqueue_t<double>(m, s) : enqueue_t<float>(m, s);
+    return m->dtype == QTM_C128 ? enqueue_t<double>(m, s, mode, with_E) : enqueue_t<float>(m, s, mode, with_E);
 }
 
+// Enqueue one launch sequence of `mode` (graph slot: 0 run, 1 forward, 2
+// adjoint, 3 adjoint with recompute).  Pointers not used by the mode are NULL.
 qtm_status run_impl(qtm_multi *m, const void *x, const void *w, const void *gE, void *E, void *gx, void *gw,
-                    int flags, cudaStream_t s)
+                    int flags, cudaStream_t s, int mode = MODE_BOTH, int slot = 0)
 {
     qtm_status st = upload(m);
     if (st != QTM_OK) return st;
     if (set_smem_attr(m) != cudaSuccess) { m->err = "shared-memory attribute"; return QTM_ECUDA; }
     MultiArgs &a = m->args;
     a.x = x; a.w = w; a.gE = gE; a.E = E; a.gx = gx; a.gw = gw;
+    const bool with_E = E != nullptr;
     if (!(flags & QTM_MULTI_GRAPH)) {
-        cudaError_t e = enqueue(m, s);
+        cudaError_t e = enqueue(m, s, mode, with_E);
         if (e != cudaSuccess) { m->err = cudaGetErrorString(e); return QTM_ECUDA; }
         return QTM_OK;
     }
     const void *key[6] = {x, w, gE, E, gx, gw};
-    if (!m->gexec || !std::equal(std::begin(key), std::end(key), std::begin(m->gkey))) {
-        release_graph(m);
+    if (!m->gexec[slot] || !std::equal(std::begin(key), std::end(key), std::begin(m->gkey[slot]))) {
+        if (m->gexec[slot]) cudaGraphExecDestroy(m->gexec[slot]);
+        if (m->graph[slot]) cudaGraphDestroy(m->graph[slot]);
+        m->gexec[slot] = nullptr;
+        m->graph[slot] = nullptr;
         if (!m->cap_stream && cudaStreamCreateWithFlags(&m->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
             m->err = "stream creation failed";
             return QTM_ECUDA;
         }
         cudaError_t e = cudaStreamBeginCapture(m->cap_stream, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            cudaError_t e2 = enqueue(m, m->cap_stream);
-            e = cudaStreamEndCapture(m->cap_stream, &m->graph);
+            cudaError_t e2 = enqueue(m, m->cap_stream, mode, with_E);
+            e = cudaStreamEndCapture(m->cap_stream, &m->graph[slot]);
             if (e == cudaSuccess) e = e2;
         }
-        if (e == cudaSuccess) e = cudaGraphInstantiate(&m->gexec, m->graph, 0);
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&m->gexec[slot], m->graph[slot], 0);
         if (e != cudaSuccess) {
             release_graph(m);
             m->err = std::string("graph capture: ") + cudaGetErrorString(e);
             return QTM_ECUDA;
         }
-        std::copy(std::begin(key), std::end(key), std::begin(m->gkey));
+        std::copy(std::begin(key), std::end(key), std::begin(m->gkey[slot]));
     }
-    cudaError_t e = cudaGraphLaunch(m->gexec, s);
+    cudaError_t e = cudaGraphLaunch(m->gexec[slot], s);
     if (e != cudaSuccess) { m->err = cudaGetErrorString(e); return QTM_ECUDA; }
     return QTM_OK;
 }
@@ -815,6 +876,7 @@ qtm_status apply_config(qtm_multi *m, const qtm_multi_config &c)
     const bool replan = c.fuse_width != m->cfg.fuse_width || c.order != m->cfg.order || c.split != m->cfg.split ||
                         m->injected;
     m->cfg = c;
+    m->fwd_valid = false;
     release_graph(m);   // the grid size and the tables are baked into a captured graph
     if (replan) {
         release_device(m);
@@ -866,7 +928,42 @@ qtm_status qtm_multi_run(qtm_multi *m, const void *x, const void *w, const void 
 {
     if (!m || !x || !w || !gE || !E || !gx || !gw) return QTM_EINVAL;
     if (flags & ~QTM_MULTI_GRAPH) return QTM_EINVAL;
+    m->fwd_valid = false;   // the run reuses the state buffers
     return run_impl(m, x, w, gE, E, gx, gw, flags, static_cast<cudaStream_t>(stream));
+}
+
+qtm_status qtm_multi_forward(qtm_multi *m, const void *x, const void *w, void *E, int flags, void *stream)
+{
+    if (!m || !x || !w || !E) return QTM_EINVAL;
+    if (flags & ~QTM_MULTI_GRAPH) return QTM_EINVAL;
+    m->fwd_valid = false;
+    qtm_status st = run_impl(m, x, w, nullptr, E, nullptr, nullptr, flags, static_cast<cudaStream_t>(stream),
+                             MODE_FWD, 1);
+    if (st != QTM_OK) return st;
+    m->fwd_valid = true;
+    m->fwd_x = x;
+    m->fwd_w = w;
+    return QTM_OK;
+}
+
+qtm_status qtm_multi_adjoint(qtm_multi *m, const void *x, const void *w, const void *gE, void *gx, void *gw,
+                             int flags, void *stream)
+{
+    if (!m || !x || !w || !gE || !gx || !gw) return QTM_EINVAL;
+    if (flags & ~(QTM_MULTI_GRAPH | QTM_MULTI_RECOMPUTE)) return QTM_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (flags & QTM_MULTI_RECOMPUTE) {
+        m->fwd_valid = false;   // the recompute overwrites the state buffers
+        return run_impl(m, x, w, gE, nullptr, gx, gw, flags & QTM_MULTI_GRAPH, s, MODE_BOTH, 3);
+    }
+    if (!m->fwd_valid || m->fwd_x != x || m->fwd_w != w) {
+        m->err = "qtm_multi_adjoint: no stored forward for these x and w (call qtm_multi_forward, or pass "
+                 "QTM_MULTI_RECOMPUTE)";
+        return QTM_ESTATE;
+    }
+    qtm_status st = run_impl(m, x, w, gE, nullptr, gx, gw, flags, s, MODE_ADJ, 2);
+    m->fwd_valid = false;   // consumed
+    return st;
 }
 
 qtm_status qtm_multi_tune(qtm_multi *m, const void *x, const void *w, const void *gE, void *E, void *gx,
@@ -961,6 +1058,24 @@ qtm_status qtm_debug_multi_tasks(const qtm_multi *m, int32_t *tasks, int capacit
     return QTM_OK;
 }
 
+qtm_status qtm_debug_multi_mode_tasks(const qtm_multi *m, int which, int32_t *tasks, int capacity, int *n_tasks)
+{
+    if (!m || which < 0 || which > 2 || capacity < 0 || (capacity > 0 && !tasks)) return QTM_EINVAL;
+    const std::vector<Task> &v = which == 0 ? m->tasks : which == 1 ? m->tasks_fwd : m->tasks_adj;
+    for (int i = 0; i < capacity && i < (int)v.size(); ++i) {
+        tasks[3 * i] = v[i].item;
+        tasks[3 * i + 1] = v[i].step;
+        tasks[3 * i + 2] = v[i].tile;
+    }
+    if (n_tasks) *n_tasks = (int)v.size();
+    return QTM_OK;
+}
+
+const char *qtm_multi_last_error(const qtm_multi *m)
+{
+    return m ? m->err.c_str() : "";
+}
+
 qtm_status qtm_debug_multi_inject(qtm_multi *m, const int32_t *tasks, int n, long long wait_ns)
 {
     if (!m || n < 1 || !tasks || wait_ns <= 0) return QTM_EINVAL;
@@ -977,6 +1092,7 @@ qtm_status qtm_debug_multi_inject(qtm_multi *m, const int32_t *tasks, int n, lon
     }
     if (m->dev_block) cudaDeviceSynchronize();
     m->tasks = t;
+    m->fwd_valid = false;
     m->wait_ns = (unsigned long long)wait_ns;
     m->injected = true;
     release_graph(m);

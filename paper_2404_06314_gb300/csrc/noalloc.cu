@@ -1,14 +1,16 @@
 // qtm_forward_noalloc: expectation values without any device allocation.
 //
-// Some callers cannot call cudaMalloc: code that runs while a stream is being
-// captured into a CUDA graph (allocation is not a capturable operation and may
-// synchronise the device), programs whose GPU memory belongs to another
-// allocator with a fixed budget, and latency-critical loops where a first-call
-// allocation would stall.  For them this entry point runs the same fused
+// Some callers cannot call cudaMalloc: a host program whose GPU memory is
+// owned by another allocator with a fixed budget (a framework that reserves
+// the device's memory up front, an embedding application that forbids its
+// plugins to allocate), and loops that must not stall on an allocation, which
+// can synchronise the device.  For them this entry point runs the same fused
 // forward kernels as qtm_forward (per-sample FP64 prep, one shared-memory pass,
 // fixed-order reduction) but takes every device-side table and every scratch
 // buffer from one file-scope device array, g_scratch, that the library holds
 // on each GPU it is loaded on until the process exits.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <cstring>
@@ -27,23 +29,60 @@ namespace {
 static __device__ __align__(256) unsigned char g_scratch[QTM_NOALLOC_SCRATCH_BYTES];
 
 std::mutex g_mu;
-void *g_scratch_ptr[256] = {nullptr};   // device address of g_scratch, per device ordinal
+// Device address of g_scratch per device ordinal, and the context it was
+// resolved in: a device reset (cudaDeviceReset, or a primary-context reset by
+// another library) unloads the module, and the array may come back at another
+// address, so a cached address is only used in the context that produced it.
+struct ScratchAddr {
+    void *ptr = nullptr;
+    unsigned long long ctx_id = 0;
+};
+ScratchAddr g_scratch_addr[256];
 
-// Resolve g_scratch's device address for the current device (once per device).
+// Unique id of the current context (0 if the driver entry points are missing).
+unsigned long long current_context_id()
+{
+    static PFN_cuCtxGetCurrent_v4000 get_current = nullptr;
+    static PFN_cuCtxGetId_v12000 get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 4000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(f);
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<PFN_cuCtxGetId_v12000>(f);
+    });
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS)
+        return 0;
+    return id;
+}
+
+// g_scratch's device address on the current device.  Set-up, once per device
+// (and again after that device's context was replaced): cudaGetSymbolAddress
+// with the device current.  The first call on a device also loads the
+// library's device code there.
 cudaError_t scratch_address(void **out)
 {
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 256) return cudaErrorInvalidDevice;
+    const unsigned long long ctx = current_context_id();   // 0 before the device's first use
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_scratch_ptr[dev]) {
+    ScratchAddr &a = g_scratch_addr[dev];
+    if (!a.ptr || ctx == 0 || a.ctx_id != ctx) {
         void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_scratch);
+        e = cudaGetSymbolAddress(&p, g_scratch);   // makes the device's primary context current
         if (e != cudaSuccess) return e;
-        g_scratch_ptr[dev] = p;
+        a.ptr = p;
+        a.ctx_id = current_context_id();
     }
-    *out = g_scratch_ptr[dev];
+    *out = a.ptr;
     return cudaSuccess;
 }
 
@@ -104,6 +143,9 @@ extern "C" qtm_status qtm_forward_noalloc(qtm_plan *plan, int B, const void *x, 
     unsigned char *sb = static_cast<unsigned char *>(base);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
 
+    // The plan's tables (a few KB) are copied from its host vectors on every
+    // call: cudaMemcpyAsync from pageable memory returns once the bytes have
+    // been staged, so the call does not depend on the plan after it returns.
     auto put = [&](size_t off, const void *src, size_t bytes) {
         if (bytes == 0 || e != cudaSuccess) return;
         e = cudaMemcpyAsync(sb + off, src, bytes, cudaMemcpyHostToDevice, s);
@@ -118,7 +160,10 @@ extern "C" qtm_status qtm_forward_noalloc(qtm_plan *plan, int B, const void *x, 
     put(o_ents, P.pass_ents.data(), sizeof(Ent) * P.pass_ents.size());
     put(o_terms, P.terms.data(), sizeof(Term) * P.terms.size());
     put(o_amap, P.amap_terms.data(), sizeof(MaskTerm) * P.amap_terms.size());
-    if (e == cudaSuccess) e = cudaMemsetAsync(sb + o_status, 0, sizeof(unsigned), s);   // starts at zero
+    // The pass takes a status word, but this path loads no tiles (no TMA, rank
+    // 0 below), so it runs no bounded device wait and never sets the word;
+    // it is zeroed only so that the kernel never sees a stale value.
+    if (e == cudaSuccess) e = cudaMemsetAsync(sb + o_status, 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return QTM_ECUDA;
 
     PrepArgs pa{};

@@ -88,6 +88,26 @@ __device__ __forceinline__ unsigned long long global_ns()
     return t;
 }
 
+// Wait, bounded, for this CTA's tile loads (phase 0 of `bar`); every thread
+// calls it.  After kWaitLimitNs the CTA records kStatusTimeout (qtm_sync
+// reports QTM_ETIMEOUT) and waits once more, again at most kWaitLimitNs, for
+// the copies still in flight, so that none is left writing this CTA's shared
+// memory when it exits.  Returns false when the caller must return.
+__device__ __forceinline__ bool wait_tile_loads(uint64_t *bar, unsigned *status)
+{
+    bool ok = false;
+    unsigned long long t0 = global_ns();
+    while (!(ok = mbar_try_wait(bar, 0)))
+        if (global_ns() - t0 > kWaitLimitNs) break;
+    if (!__syncthreads_or(!ok)) return true;
+    if (threadIdx.x == 0) atomicOr(status, kStatusTimeout);
+    t0 = global_ns();
+    while (!mbar_try_wait(bar, 0))
+        if (global_ns() - t0 > kWaitLimitNs) break;
+    __syncthreads();
+    return false;
+}
+
 __device__ __forceinline__ void tma_load(void *dst, const CUtensorMap *tm, const int *c, int rank,
                                          uint64_t *bar)
 {
@@ -976,14 +996,7 @@ __device__ __forceinline__ void pass_body(const PassArgs &a, const CUtensorMap *
     __syncthreads();
     if (FILL && a.phi_src == SRC_ANALYTIC) fill_analytic<R>(j, S);
     if (load_phi || load_lam) {
-        bool ok = false;
-        const unsigned long long t0 = global_ns();
-        while (!(ok = mbar_try_wait(S.bar, 0)))
-            if (global_ns() - t0 > kWaitLimitNs) break;
-        if (__syncthreads_or(!ok)) {
-            if (tid == 0) atomicOr(a.status, kStatusTimeout);
-            return;
-        }
+        if (!wait_tile_loads(S.bar, a.status)) return;
     } else {
         __syncthreads();
     }

@@ -615,14 +615,7 @@ __device__ __forceinline__ void pass_body_x2(const PassArgs &a, const CUtensorMa
     __syncthreads();
     if (a.phi_src == SRC_ANALYTIC) fill_analytic_x2(j, S);
     if (load_phi || load_lam) {
-        bool ok = false;
-        const unsigned long long t0 = global_ns();
-        while (!(ok = mbar_try_wait(S.bar, 0)))
-            if (global_ns() - t0 > kWaitLimitNs) break;
-        if (__syncthreads_or(!ok)) {
-            if (tid == 0) atomicOr(a.status, kStatusTimeout);
-            return;
-        }
+        if (!wait_tile_loads(S.bar, a.status)) return;
     } else {
         __syncthreads();
     }

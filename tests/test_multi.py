@@ -1,5 +1,6 @@
 """Uneven batches (qtm_build_multi / qtm_multi_run): circuits of different
 qubit counts and depths in one persistent launch."""
+import ctypes
 import json
 import os
 
@@ -64,6 +65,61 @@ def test_multi_task_list_host(split, order):
         assert any(k > 0 for _, k, _ in listed)
         if order == 0:   # highest level first: the first task starts the longest chain
             assert listed[0][1] in (-1, 0)
+
+
+@pytest.mark.parametrize("split,order", [(0, 0), (1, 0), (1, 1)])
+def test_multi_split_launch_task_lists_host(split, order):
+    """qtm_multi_forward and qtm_multi_adjoint hand out only their own
+    passes: every item's forward passes (resp. reverse passes) exactly once,
+    and every (pass, tile) task after all tiles of its item's previous pass
+    of the same launch (the done counters restart at zero in each launch)."""
+    cs = W.workload_uneven(count=10, seed=21, n_lo=11, n_hi=16)
+    mp = capi.MultiPlan(cs, batch=2)
+    mp.config = {"ctas_per_sm": 2, "order": order, "fuse_width": 32, "split": split}
+    _, items = mp.debug_tasks()
+    geo = {}
+    for c in cs:
+        info = capi.Plan(c, dtype="c64").info
+        geo[c.name] = (info["fwd_passes"], info["adj_passes"],
+                       1 << max(0, info["n_qubits"] - info["tile_qubits"]))
+    for which in (1, 2):
+        listed = list(map(tuple, mp.debug_mode_tasks(which).tolist()))
+        expect = set()
+        for i, (c, b) in enumerate(items.tolist()):
+            nf, nr, tiles = geo[cs[c].name]
+            kb, ke = (0, nf) if which == 1 else (nf, nf + nr)
+            if split == 0 or tiles == 1:
+                expect.add((i, -1, 0))
+            else:
+                expect |= {(i, k, t) for k in range(kb, ke) for t in range(tiles)}
+        assert len(listed) == len(set(listed)) and set(listed) == expect
+        done = {}
+        for (i, k, t) in listed:
+            if k >= 0:
+                nf, nr, tiles = geo[cs[items[i][0]].name]
+                first = 0 if which == 1 else nf
+                assert done.get((i, k - 1), 0) == (tiles if k > first else 0), (which, i, k, t)
+                done[(i, k)] = done.get((i, k), 0) + 1
+    assert mp.debug_mode_tasks(0).tolist() == mp.debug_tasks()[0].tolist()
+
+
+def test_multi_adjoint_without_forward_is_estate_host():
+    """qtm_multi_adjoint consumes the states of a matching qtm_multi_forward;
+    with none it returns QTM_ESTATE before any CUDA call (so also here, with
+    no GPU), and any pointer is rejected before that check when NULL."""
+    import torch
+    cs = W.workload_uneven(count=4, seed=3)
+    mp = capi.MultiPlan(cs, batch=1)
+    bufs = {k: torch.zeros(max(1, int(mp.offsets(k)[-1]))) for k in range(6)}
+    L = capi._multi_lib()
+    ptr = {k: ctypes.c_void_p(t.data_ptr()) for k, t in bufs.items()}
+    st = L.qtm_multi_adjoint(mp.handle, ptr[capi.QTM_MULTI_X], ptr[capi.QTM_MULTI_W], ptr[capi.QTM_MULTI_GE],
+                             ptr[capi.QTM_MULTI_GX], ptr[capi.QTM_MULTI_GW], capi.QTM_MULTI_GRAPH, None)
+    assert st == capi.QTM_ESTATE
+    assert "qtm_multi_forward" in mp.last_error()
+    p = ptr[0]
+    assert L.qtm_multi_adjoint(mp.handle, p, p, p, None, p, 0, None) == capi.QTM_EINVAL
+    assert L.qtm_multi_forward(mp.handle, p, p, p, 4, None) == capi.QTM_EINVAL   # unknown flag
 
 
 def test_multi_inject_validates_host():
@@ -206,3 +262,41 @@ def test_multi_tune_and_cache(tmp_path):
     assert len(open(cache).readlines()) == 1
     Es, gxs, gws, _ = _run(mp2, cs, xs, ws, gs)
     _check(cs, xs, ws, gs, Es, gxs, gws)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("split,order,graph", [(1, 0, False), (0, 0, False), (1, 1, True)])
+def test_multi_forward_then_adjoint(split, order, graph):
+    """Forward alone (inference), then the adjoint from the stored states:
+    bit-identical to the fused qtm_multi_run (the same passes, only the state
+    round-trips through memory between them), and within 1e-5 of the oracle.
+    The states are consumed (a second adjoint is QTM_ESTATE) and the
+    recompute flag re-evolves them instead."""
+    import torch
+    cs = W.workload_uneven(count=20, seed=77, n_lo=4, n_hi=15)
+    mp = capi.MultiPlan(cs, batch=2)
+    mp.config = {"ctas_per_sm": 2, "order": order, "fuse_width": 32, "split": split}
+    xs, ws, gs = _inputs(cs, 2, 5)
+    Er, gxr, gwr, (x, w, g, E, gx, gw) = _run(mp, cs, xs, ws, gs)
+    B = mp.batch
+    E2, gx2, gw2 = (torch.full_like(t, float("nan")) for t in (E, gx, gw))
+    for _ in range(2 if graph else 1):
+        mp.forward(x, w, E2, graph=graph)
+        mp.adjoint(x, w, g, gx2, gw2, graph=graph)
+    mp.sync()
+    Es = mp.unpack(E2, capi.QTM_MULTI_E, [(B, c.n_obs) for c in cs])
+    gxs = mp.unpack(gx2, capi.QTM_MULTI_GX, [(B, c.n_inputs) for c in cs])
+    gws = mp.unpack(gw2, capi.QTM_MULTI_GW, [(c.n_weights,) for c in cs])
+    for a_list, b_list in ((Er, Es), (gxr, gxs), (gwr, gws)):
+        for a, b in zip(a_list, b_list):
+            assert np.array_equal(a, b)
+    _check(cs, xs, ws, gs, Es, gxs, gws)
+    with pytest.raises(capi.QtmError) as ei:
+        mp.adjoint(x, w, g, gx2, gw2)
+    assert ei.value.status == capi.QTM_ESTATE
+    gx2.fill_(float("nan"))
+    mp.adjoint(x, w, g, gx2, gw2, recompute=True, graph=graph)
+    mp.sync()
+    gxs = mp.unpack(gx2, capi.QTM_MULTI_GX, [(B, c.n_inputs) for c in cs])
+    for a, b in zip(gxr, gxs):
+        assert np.array_equal(a, b)

@@ -61,7 +61,7 @@ def check(c, B, dtype, path="fused", seed=7, tol=None, plan=None):
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
 @pytest.mark.parametrize("path", ["fused", "naive"])
 def test_workload_4q(dtype, path):
-    check(W.workload_4q(), 8, dtype, path, tol=(1e-11 if dtype == "c128" else None))
+    check(W.workload_4q(), 8, dtype, path, tol=(1e-11 if dtype == "c128" and path == "naive" else None))
 
 
 @pytest.mark.parametrize("dtype", ["c64", "c128"])
@@ -102,7 +102,7 @@ def test_random_circuits(n):
     c = P.rand_small_circuit(rng, n, G=4 * n + 10, n_obs=3)
     c.name = f"rand{n}"
     check(c, 3, "c64")
-    check(c, 2, "c128", tol=1e-11)
+    check(c, 2, "c128")
 
 
 def test_no_parameters_and_empty_observable():
@@ -202,7 +202,7 @@ def test_empty_batch():
         qnn(x0, wv, plan).sum().backward()
         plan.sync()
         assert bool(torch.all(wv.grad == 0))
-        check(c, 3, dtype, plan=plan, tol=1e-11 if dtype == "c128" else None)
+        check(c, 3, dtype, plan=plan)
 
 
 # ---- full-size configurations, sampled rows --------------------------------------
@@ -278,7 +278,7 @@ def test_jacobian_matches_oracle(n, dtype):
     J = plan.jacobian(x, w)
     plan.sync()
     Jo = oracle.jacobian(c, inp.x, inp.w, threads=0)
-    assert_close(J.double().cpu().numpy(), Jo, TOL[dtype] if dtype == "c64" else 1e-11, f"J n={n} {dtype}")
+    assert_close(J.double().cpu().numpy(), Jo, TOL[dtype], f"J n={n} {dtype}")
 
 
 def test_jacobian_paper_workload_tab1_shape():
@@ -303,7 +303,7 @@ def test_h_rzz_random_circuits(n):
     c = P.rand_small_circuit(rng, n, G=5 * n + 10, n_obs=3, extra=True)
     c.name = f"hrzz{n}"
     check(c, 3, "c64")
-    check(c, 2, "c128", tol=1e-11)
+    check(c, 2, "c128")
     if n <= 9:
         check(c, 2, "c64", "naive")
 
@@ -322,7 +322,7 @@ def test_h_rzz_jacobian_columns():
     plan.sync()
     Jo = oracle.jacobian(c, inp.x, inp.w, threads=0)
     assert J.shape == (2, 2, c.n_gates)
-    assert_close(J.cpu().numpy(), Jo, 1e-11, "jacobian with H and RZZ")
+    assert_close(J.cpu().numpy(), Jo, TOL["c128"], "jacobian with H and RZZ")
     no_angle = [g for g, gt in enumerate(c.gates) if gt[0] in (W.H, W.CZ, W.CNOT)]
     assert np.all(J.cpu().numpy()[:, :, no_angle] == 0)
 
@@ -335,7 +335,7 @@ def test_pauli_observables_match_oracle(n):
     c = P.rand_small_circuit(rng, n, G=5 * n + 8, n_obs=3, extra=True, pauli=True)
     c.name = f"pauli{n}"
     check(c, 3, "c64")
-    check(c, 2, "c128", tol=1e-11)
+    check(c, 2, "c128")
 
 
 def test_pauli_jacobian_and_compiled():
@@ -346,7 +346,7 @@ def test_pauli_jacobian_and_compiled():
     plan = capi.Plan(c, dtype="c128")
     J = plan.jacobian(torch.tensor(inp.x, device="cuda"), torch.tensor(inp.w, device="cuda"))
     plan.sync()
-    assert_close(J.cpu().numpy(), oracle.jacobian(c, inp.x, inp.w, threads=0), 1e-11, "pauli jacobian")
+    assert_close(J.cpu().numpy(), oracle.jacobian(c, inp.x, inp.w, threads=0), TOL["c128"], "pauli jacobian")
     inp32 = W.make_inputs(c, 3, 6, real_dtype=np.float32)
     plan32 = capi.Plan(c, dtype="c64").compile()
     assert plan32.compiled_passes() > 0

@@ -1,6 +1,8 @@
 """qtm_forward_noalloc, the allocation-free forward (for callers that cannot
-call cudaMalloc, e.g. during CUDA graph capture or under another allocator's
-fixed budget), against qtm_forward through the C ABI, on two calls in a row.
+call cudaMalloc: programs whose GPU memory another allocator owns with a fixed
+budget, loops that must not stall on an allocation), against qtm_forward
+through the C ABI, on two calls in a row; the second call must leave the
+device's free memory unchanged.
 
 This file sorts last so that a run stopping at its first failure has already
 run every other test; it also passes alone in a fresh process."""
@@ -33,9 +35,13 @@ def test_forward_noalloc_matches_forward_twice():
         E_na = torch.full((B, c.n_obs), float("nan"), dtype=torch.float32, device="cuda")
         st = capi.qtm_forward(plan.handle, B, _ptr(x), _ptr(w), _ptr(E_ref), stream)
         assert st == capi.QTM_OK, capi.qtm_last_error(plan.handle)
+        torch.cuda.synchronize()
+        free_before = torch.cuda.mem_get_info()[0]
         st = capi.qtm_forward_noalloc(plan.handle, B, _ptr(x), _ptr(w), _ptr(E_na), stream)
         assert st == capi.QTM_OK, f"call {call}: status {st}"
         torch.cuda.synchronize()
+        if call > 0:   # the first call on the device loads the library's device code (and the array)
+            assert torch.cuda.mem_get_info()[0] == free_before, f"call {call} changed free device memory"
         err = (E_na.double() - E_ref.double()).abs().max().item()
         assert err <= TOL, f"call {call}: max abs diff {err:.3e}"
 

@@ -38,6 +38,10 @@ WORKLOADS = {
                   desc="qnn20_l4: 20 qubits, RX(x) + 4 layers RY(w) RZ(w) + CNOT chain, "
                        "obs Z_0 and Z^(x)20, B=64, fwd + adjoint",
                   path_desc="fused HBM sweeps: TMA tiles of 2^12 amplitudes"),
+    "qnn12_c128": dict(builder="workload_12q", B=1024, dtype="c128",
+                       desc="qnn12_l6 in complex128: 12 qubits, 6 re-uploading layers RX(x) RY(w) RZ(w) + CZ ring, "
+                            "obs sum Z_i Z_{i+1}, B=1024, fwd + adjoint (grad_x, grad_w)",
+                       path_desc="fused: whole state in shared memory, one CTA per sample (general pass kernel, FP64)"),
     "qnn16": dict(builder="workload_16q_train", B=256, dtype="c64",
                   desc="qnn16_l8: 16 qubits, 8 re-uploading layers + CZ ring, obs sum Z_i, B=256",
                   path_desc="fused HBM sweeps: TMA tiles of 2^12 amplitudes"),
@@ -133,17 +137,13 @@ class ClockSampler:
 # kernel kind the bench runs (profiles/ holds the summaries and commands);
 # reported as null for any other kernel kind.
 PROFILED_TRAFFIC = {
-    ("qnn12", "cpx"): (39.806208e6 + 0.005888e6, "profiles/qtm_gen_pass_cpx_qnn12_l6_b1024.md"),
     ("qnn20", "cpx"): ((0.537211e9 + 1.022075e9 + 1.073937e9 + 1.018183e9 + 1.073976e9 + 0.497157e9 +
                         0.537045e9 + 0.507352e9 + 0.537005e9 + 0.003969e9) / 5,
                        "profiles/qtm_gen_pass_cpx_qnn20_l4_b64.md (mean of reverse passes 0-4)"),
-    ("qnn12", "lanes"): (36.324352e6 + 0.030208e6, "profiles/qtm_gen_pass_lanes_qnn12_l6_b1024.md"),
-    ("qnn20", "lanes"): ((1.560116e9 + 2.095630e9 + 1.575998e9) / 3,
-                         "profiles/qtm_gen_pass_lanes_qnn20_l4_b64.md (mean of reverse passes 1-3)"),
 }
 
 
-def roofline(r, peaks, peak_src):
+def roofline(r, peaks, peak_src, alu_peak=None):
     """Roofline of the dominant kernel, the reverse pass (the specialised
     qtm_gen_pass by default; for one-tile-per-sample plans its launch also
     runs the sample's gradient finalize), from its live CUDA-event durations
@@ -160,20 +160,24 @@ def roofline(r, peaks, peak_src):
     flops = info["adj_flops"] * B / passes
     bytes_ = info["adj_state_bytes"] * B / passes
     sms = r["sm_count"]
-    alu_peak = fp32_alu_peak_tflops(peaks.get("sm_max_mhz", 2070.0), sms)
+    alu_src = None
+    if alu_peak is not None:
+        alu_peak, alu_src = alu_peak
+    else:
+        alu_peak = fp32_alu_peak_tflops(peaks.get("sm_max_mhz", 2070.0), sms)
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     alu = flops / t / 1e12
     hbm = bytes_ / t / 1e9
     alu_obj = {"bound": "alu", "achieved": alu, "peak": alu_peak, "unit": "TFLOP/s",
                "frac": alu / alu_peak,
                "sm_count": sms,
-               "peak_source": "derived: %d SMs (queried) x 128 FP32 lanes x 2 flop x %g MHz (sm_max_mhz of "
-                              "MEASURED_PEAKS.json)" % (sms, peaks.get("sm_max_mhz", 2070.0))}
+               "peak_source": alu_src or "derived: %d SMs (queried) x 128 FP32 lanes x 2 flop x %g MHz (sm_max_mhz "
+                                         "of MEASURED_PEAKS.json)" % (sms, peaks.get("sm_max_mhz", 2070.0))}
     hbm_obj = {"bound": "hbm", "achieved": hbm, "peak": hbm_peak, "unit": "GB/s",
                "frac": hbm / hbm_peak, "peak_source": f"{peak_src} hbm_gbs (burst copy)"}
     main, other = (alu_obj, hbm_obj) if alu_obj["frac"] >= hbm_obj["frac"] else (hbm_obj, alu_obj)
     main = dict(main)
-    tr = PROFILED_TRAFFIC.get((r["workload"], r["kernels"]))
+    tr = PROFILED_TRAFFIC.get((r["workload"], r["kernels"])) if r["kernels"] == "cpx" else None
     main.update({"kernel": KERNEL_LABEL[r["kernels"]], "traffic": tr[0] if tr else None,
                  "traffic_source": tr[1] if tr else None,
                  "launch_ms": t * 1e3, "launches_timed": n,
@@ -230,20 +234,15 @@ def accuracy(outputs, ref):
 # GPU measurement
 # ------------------------------------------------------------------------------
 
-KERNEL_LABEL = {"naive": "naive one-gate-per-launch path","paired": "qtm_gen_pass (plan-specialised, two samples per CTA on f32x2 pairs), reverse",
-                "paired-general": "k_pass_x2<reverse> (general, two samples per CTA on f32x2 pairs)",
-                "one-sample": "qtm_gen_pass (plan-specialised, one sample per CTA), reverse",
-                "lanes": "qtm_gen_pass (plan-specialised, one sample per CTA, amplitudes paired in f32x2), reverse",
+KERNEL_LABEL = {"naive": "naive one-gate-per-launch path",
                 "cpx": "qtm_gen_pass (plan-specialised, one sample per CTA, complex amplitudes as f32x2 pairs), reverse",
-                "general": "k_pass<float, reverse> (general pass kernel)"}
+                "general": "k_pass<R, reverse> (general pass kernel)"}
 
 
 def prepare(plan, kernels):
     """Load the plan's specialised pass kernels unless the general kernel is asked for."""
-    if kernels == "paired-general":
-        plan.set_pairing(True)
-    elif kernels not in ("general", "naive"):
-        plan.compile(kind={"paired": "pairs", "one-sample": "one", "lanes": "lanes", "cpx": "cpx"}[kernels])
+    if kernels == "cpx":
+        plan.compile()
         assert plan.compiled_passes() > 0, "no specialised pass kernel loaded"
     return plan
 
@@ -619,6 +618,200 @@ def measure_paper_context(device, steps=50):
     return out
 
 
+def fma_rate_tflops(dtype: str) -> float:
+    """Measured FMA throughput of this GPU (qtm_debug_fma_rate), TFLOP/s."""
+    import ctypes
+
+    from paper_2404_06314_gb300 import capi
+    L = capi.lib()
+    L.qtm_debug_fma_rate.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+    L.qtm_debug_fma_rate.restype = ctypes.c_int
+    v = ctypes.c_double()
+    st = L.qtm_debug_fma_rate(capi.QTM_C128 if dtype == "c128" else capi.QTM_C64, ctypes.byref(v))
+    if st != capi.QTM_OK:
+        raise capi.QtmError(st, "qtm_debug_fma_rate")
+    return v.value / 1e12
+
+
+def measure_c128(steps, warmup, device, peaks, peak_src):
+    """Config 2's complex128 leg: the 12-qubit workload (B = 1024) in complex128
+    on the general pass kernel, forward + adjoint; roofline against the FP64
+    FMA rate measured on this GPU (qtm_debug_fma_rate), and the max abs
+    error against the FP64 oracle on a few rows."""
+    import numpy as np
+
+    import oracle
+    r = measure_gpu("qnn12_c128", steps, warmup, device, kernels="general")
+    fp64 = fma_rate_tflops("c128")
+    tot = sum(r["step_ms"])
+    c, inp = r["c"], r["inp"]
+    rows = [0, 511, r["B"] - 1]
+    E = oracle.forward(c, inp.x[rows], inp.w, threads=os.cpu_count() or 1)
+    _, gx, gw = oracle.adjoint(c, inp.gE[rows], inp.x[rows], inp.w, threads=os.cpu_count() or 1)
+    line = {"value": r["B"] * len(r["step_ms"]) / (tot / 1e3), "unit": "samples/s",
+            "ms_per_step": tot / len(r["step_ms"]), "steps": len(r["step_ms"]), "dtype": "c128 (fp64 complex)",
+            "config": {"workload": WORKLOADS["qnn12_c128"]["desc"], "path": WORKLOADS["qnn12_c128"]["path_desc"]},
+            "roofline": roofline(r, peaks, peak_src,
+                                 alu_peak=(fp64, "measured: FP64 FMA loop on this GPU (qtm_debug_fma_rate)")),
+            "fp64_fma_tflops_measured": fp64, "gpu_launches": r["launches"],
+            "accuracy": accuracy(r["outputs"], {"rows": rows, "E": E, "gx": gx, "gw": gw})}
+    return line
+
+
+def _median_ms(fn, reps, flush):
+    """Median device time of fn() over reps, CUDA events, L2 flushed before each."""
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return statistics.median(ts)
+
+
+def _compile_all(plans):
+    """Specialised kernels for every eligible plan, compiled concurrently
+    (NVRTC releases the GIL); plans it does not cover keep the general kernels."""
+    import concurrent.futures as cf
+
+    from paper_2404_06314_gb300 import capi
+
+    def one(p):
+        try:
+            p.compile()
+            return "cpx"
+        except capi.QtmError:
+            return "general"
+    with cf.ThreadPoolExecutor(max_workers=8) as ex:
+        return list(ex.map(one, plans))
+
+
+def _linear_r2(xs, ys):
+    import numpy as np
+    xs, ys = np.asarray(xs, float), np.asarray(ys, float)
+    A = np.vstack([xs, np.ones_like(xs)]).T
+    coef, *_ = np.linalg.lstsq(A, ys, rcond=None)
+    resid = ys - A @ coef
+    ss = float(((ys - ys.mean()) ** 2).sum())
+    return {"slope": float(coef[0]), "intercept": float(coef[1]), "r2": 1.0 - float((resid ** 2).sum()) / ss if ss else 1.0}
+
+
+def measure_paper_shapes(device, peaks, reps=5, oracle_budget=1.0):
+    """The paper's benchmark shapes (benchmark ansatz of Eq. (concrete_ansatz),
+    B = 48, complex64, default kernels), each point beside the FP64 oracle on
+    the host's cores (a bounded sample of rows, scaled to the batch):
+      tab1: 12 qubits, depth 3 (168 parameters), M = 1..32 observables:
+            forward, and forward + full Jacobian (B, M, |Theta|) (Tab. I);
+      fig1: depth 3, Z_i on all n qubits, n = 4..20: forward, adjoint (VJP),
+            Jacobian (Fig. 1 (a)-(c));
+      fig2: 12 qubits, Z_i on all qubits, depth 1..11: forward, VJP, Jacobian,
+            with the linear fit in depth (Fig. 2, Sec. III: time linear in depth).
+    Times are medians of `reps` CUDA-event timings with the L2 flushed."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_2404_06314_gb300 import capi, workloads as W
+
+    B = 48
+    threads = os.cpu_count() or 1
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=device)
+    sms = sm_count(device)
+    alu_peak = fp32_alu_peak_tflops(peaks.get("sm_max_mhz", 2070.0), sms)
+
+    def prepare(c, seed):
+        inp = W.make_inputs(c, B, seed, real_dtype=np.float32)
+        f32 = dict(dtype=torch.float32, device=device)
+        return inp, tuple(torch.tensor(a, **f32) for a in (inp.x, inp.w, inp.gE))
+
+    def time_point(plan, t, jac=True):
+        x, w, g = t
+        E = plan.forward(x, w)
+        gx, gw = plan.adjoint(g, x, w)
+        fwd = _median_ms(lambda: plan.forward(x, w, out=E), reps, flush)
+        vjp = _median_ms(lambda: (plan.forward(x, w, out=E), plan.adjoint(g, x, w, gx=gx, gw=gw)), reps, flush) - fwd
+        out = {"fwd_ms": fwd, "vjp_ms": vjp}
+        if jac:
+            J = plan.jacobian(x, w)
+            out["jacobian_ms"] = _median_ms(lambda: plan.jacobian(x, w, out=J), reps, flush)
+        info = plan.info
+        out["alu_frac_fwd_vjp"] = (info["fwd_flops"] + info["adj_flops"]) * B / ((fwd + vjp) * 1e-3) / 1e12 / alu_peak
+        return out
+
+    def oracle_ms(c, inp, what):
+        """Oracle time for the whole batch of 48 from a bounded sample of rows."""
+        rows = list(range(min(B, threads)))
+        t = time.perf_counter()
+        if what == "jacobian":
+            oracle.forward(c, inp.x[rows], inp.w, threads=threads)
+            oracle.jacobian(c, inp.x[rows], inp.w, threads=threads)
+        elif what == "forward":
+            oracle.forward(c, inp.x[rows], inp.w, threads=threads)
+        else:
+            oracle.forward(c, inp.x[rows], inp.w, threads=threads)
+            oracle.adjoint(c, inp.gE[rows], inp.x[rows], inp.w, threads=threads)
+        dt = time.perf_counter() - t
+        return 1e3 * dt * B / len(rows)
+
+    out = {}
+    # ---- Tab. I: observables ----
+    Ms = (1, 2, 4, 8, 12, 16, 24, 32)
+    cs = [W.jerbi_ansatz(12, 3, terms=W.tab1_observables(12, M)) for M in Ms]
+    plans = [capi.Plan(c, dtype="c64") for c in cs]
+    kinds = _compile_all(plans)
+    pts = []
+    for M, c, plan, kind in zip(Ms, cs, plans, kinds):
+        inp, t = prepare(c, 1100 + M)
+        r = time_point(plan, t)
+        r.update({"M": M, "kernels": kind, "oracle_fwd_ms": oracle_ms(c, inp, "forward"),
+                  "oracle_jacobian_ms": oracle_ms(c, inp, "jacobian")})
+        pts.append(r)
+        del plan
+    out["tab1"] = {"config": "benchmark ansatz, 12 qubits, depth 3, 168 parameters, B=48, complex64; observables: "
+                             "Z_i, then Z_i Z_{i+1}, then Z_i Z_{i+2} (Tab. I names only their number)",
+                   "oracle_cores": threads, "points": pts,
+                   "paper": "Tab. I: factors over qiskit-machine-learning on a Ryzen 9 5900X (context only)"}
+    # ---- Fig. 1: qubits ----
+    ns = list(range(4, 21))
+    cs = [W.jerbi_ansatz(n, 3) for n in ns]
+    plans = [capi.Plan(c, dtype="c64") for c in cs]
+    kinds = _compile_all(plans)
+    pts = []
+    for n, c, plan, kind in zip(ns, cs, plans, kinds):
+        inp, t = prepare(c, 1200 + n)
+        r = time_point(plan, t)
+        r.update({"n": n, "parameters": c.n_weights, "kernels": kind,
+                  "oracle_fwd_vjp_ms": oracle_ms(c, inp, "vjp") if n <= 20 else None})
+        pts.append(r)
+        del plan
+    out["fig1"] = {"config": "benchmark ansatz, depth 3, Z_i on all qubits, B=48, complex64, n = 4..20",
+                   "oracle_cores": threads, "points": pts}
+    # ---- Fig. 2: depth ----
+    ds = list(range(1, 12))
+    cs = [W.jerbi_ansatz(12, d) for d in ds]
+    plans = [capi.Plan(c, dtype="c64") for c in cs]
+    kinds = _compile_all(plans)
+    pts = []
+    for d, c, plan, kind in zip(ds, cs, plans, kinds):
+        inp, t = prepare(c, 1300 + d)
+        r = time_point(plan, t)
+        r.update({"depth": d, "parameters": c.n_weights, "kernels": kind,
+                  "adj_flops_per_sample": plan.info["adj_flops"], "oracle_fwd_vjp_ms": oracle_ms(c, inp, "vjp")})
+        pts.append(r)
+        del plan
+    out["fig2"] = {"config": "benchmark ansatz, 12 qubits, Z_i on all qubits, B=48, complex64, depth 1..11",
+                   "oracle_cores": threads, "points": pts,
+                   "linear_in_depth": {k: _linear_r2(ds, [p[k] for p in pts])
+                                       for k in ("vjp_ms", "jacobian_ms", "fwd_ms")}}
+    return out
+
+
 def measure_e2e(name, steps, device, seed_offset=0, kernels="cpx"):
     """End to end through the public API: pinned host inputs -> device,
     forward, adjoint, results -> pinned host, every step."""
@@ -733,6 +926,11 @@ def gpu_main(args):
         extra["train16"] = measure_training(device)
         extra["paper_context"] = measure_paper_context(device)
         extra["pauli12"] = measure_pauli(device)
+        extra["qnn12_c128"] = measure_c128(max(3, args.steps // 4), args.warmup, device, peaks, peak_src)
+        if not args.skip_paper_shapes:
+            t0 = time.perf_counter()
+            extra["paper_shapes"] = measure_paper_shapes(device, peaks)
+            extra["paper_shapes"]["seconds"] = time.perf_counter() - t0
     e2e = measure_e2e(args.workload, max(3, args.steps // 4), device, seed_offset=rank, kernels=args.kernels)
     if ws > 1:
         t = torch.tensor([e2e[0]], device=device, dtype=torch.float64)
@@ -834,9 +1032,11 @@ def reference_main(args):
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)",
-            "config": {"workload": c.name, "per_step_sample": S},
+            "config": {"workload": cfg["desc"], "global_batch": cfg["B"] * ws, "per_gpu_batch": cfg["B"],
+                       "path": "FP64 oracle on the host cores (reference arm)"},
             "cpu_baseline": {"value": value, "unit": "samples/s", "cores": threads, "kind": "oracle",
-                             "sample": f"{S} samples of the {c.name} batch per step"},
+                             "sample": f"{S} samples of the {c.name} batch per step (a bounded sample of the "
+                                       f"{cfg['B']}-sample batch; samples/s is per sample either way)"},
             "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -849,13 +1049,14 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="qnn12")
     ap.add_argument("--skip-n20", action="store_true")
-    ap.add_argument("--kernels", choices=["paired", "one-sample", "lanes", "cpx", "paired-general", "general"],
-                    default="cpx",
-                    help="plan-specialised pass kernels (qtm_compile: lanes = one sample per CTA with "
-                         "amplitudes paired in f32x2 registers, cpx = one sample per CTA with each complex "
-                         "amplitude an f32x2 pair, one-sample = scalar, paired = two samples per CTA), or the "
-                         "general pass kernels (paired-general / general)")
+    ap.add_argument("--kernels", choices=["cpx", "general"], default="cpx",
+                    help="plan-specialised pass kernels (qtm_compile: one sample per CTA, each complex "
+                         "amplitude an f32x2 pair) or the general pass kernel")
     ap.add_argument("--skip-extra", action="store_true", help="skip the uneven-batch and training lines")
+    ap.add_argument("--skip-paper-shapes", action="store_true",
+                    help="skip the Tab. I / Fig. 1 / Fig. 2 shape sweeps")
+    ap.add_argument("--paper-shapes-only", action="store_true",
+                    help="run only the Tab. I / Fig. 1 / Fig. 2 shape sweeps and print them as one JSON line")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle CPU work")
     ap.add_argument("--uneven-only", action="store_true",
@@ -866,6 +1067,13 @@ def main():
         args.warmup = 3
     if args.uneven_only:
         uneven_only(args.steps)
+    elif args.paper_shapes_only:
+        import torch
+        torch.cuda.set_device(0)
+        t0 = time.perf_counter()
+        r = measure_paper_shapes(torch.device("cuda", 0), load_peaks()[0])
+        r["seconds"] = time.perf_counter() - t0
+        print(json.dumps({"paper_shapes": r}), flush=True)
     elif args.impl == "reference":
         reference_main(args)
     else:

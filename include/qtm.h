@@ -164,8 +164,7 @@ qtm_status qtm_build(int n_qubits, const qtm_gate *gates, int n_gates,
  * by the basis change V = RY(-pi/2) on X qubits and RX(pi/2) on Y qubits
  * (V sigma V^dagger = Z), summing the groups' outputs in group order
  * (qtm_plan_parts counts them).  Every entry point below applies, except that
- * qtm_forward_noalloc, the two-samples-per-CTA kernels (qtm_set_sample_pairing,
- * QTM_COMPILE_SAMPLE_PAIRS) return QTM_EUNSUPPORTED for plans with X/Y terms.
+ * qtm_forward_noalloc returns QTM_EUNSUPPORTED for plans with X/Y terms.
  * With Z strings only this is qtm_build.
  */
 qtm_status qtm_build_pauli(int n_qubits, const qtm_gate *gates, int n_gates,
@@ -375,38 +374,21 @@ qtm_status qtm_multi_get_config(const qtm_multi *multi, qtm_multi_config *cfg);
 qtm_status qtm_multi_set_config(qtm_multi *multi, const qtm_multi_config *cfg);
 qtm_status qtm_multi_destroy(qtm_multi *multi);
 
-/* qtm_set_sample_pairing: run the plan's passes on the paired general kernel
- * (on = 1: two samples per CTA, one per half of Blackwell's f32x2 register
- * pairs, op tables read at run time) or the one-sample kernel (on = 0, the
- * default).  Same results within rounding.  Needs a fused complex64 plan with
- * tiles of >= 9 qubits and no X/Y observables (QTM_EUNSUPPORTED otherwise:
- * those read the final state in the one-sample layout).  Changing it drops the
- * workspace and any stored forward state (the state layout changes); it waits
- * for the device when a workspace exists.  Specialised kernels loaded by
- * qtm_compile take precedence while they are loaded. */
-qtm_status qtm_set_sample_pairing(qtm_plan *plan, int on);
-int qtm_get_sample_pairing(const qtm_plan *plan);
-
 /* qtm_compile: specialise the plan's pass kernels.  The schedule is fixed
  * once a plan is built, so every register position, table slot, CZ sign
  * pattern, CNOT form and observable sign pattern of each pass is written out
  * as CUDA source, compiled with NVRTC for sm_103a (compiled images are cached
  * on disk under $QTM_JIT_CACHE, default /tmp/qtm_jit_cache) and loaded on the
  * current device; later qtm_forward / qtm_adjoint / qtm_jacobian calls on that
- * device launch them in place of the general pass kernel.  Kinds (flags): 0
- * (default), one sample per CTA with each complex amplitude one of Blackwell's
- * f32x2 register pairs (re, im; paired fma / mul / add);
- * QTM_COMPILE_SCALAR, one sample per CTA with scalar FP32 registers;
- * QTM_COMPILE_SAMPLE_PAIRS, two samples per CTA, one per half of each f32x2
- * register pair; QTM_COMPILE_LANE_PAIRS, one sample per CTA with two
- * amplitudes (one register bit apart) per f32x2 pair.  Applies
- * to complex64 fused plans with tiles of >= 9 qubits (QTM_EUNSUPPORTED
- * otherwise, or when NVRTC is unavailable, or for QTM_COMPILE_SAMPLE_PAIRS on
- * a plan with X/Y observables; the plan keeps the general kernels).  Synchronises the device and drops the workspace and any stored
- * forward state (the state layout changes). */
-#define QTM_COMPILE_SCALAR 1
-#define QTM_COMPILE_SAMPLE_PAIRS 2
-#define QTM_COMPILE_LANE_PAIRS 3
+ * device launch them in place of the general pass kernel.  The kernels run one
+ * sample per CTA with each complex amplitude one of Blackwell's f32x2
+ * register pairs (re, im; paired fma / mul / add); a stretch of phases that
+ * repeats one phase program with shifted run slots (a layered circuit's
+ * layers) is emitted once, as a loop.  flags: 0 (reserved; other values
+ * QTM_EINVAL).  Applies to complex64 fused plans with tiles of >= 9 qubits
+ * (QTM_EUNSUPPORTED otherwise, or when NVRTC is unavailable; the plan keeps
+ * the general kernels).  Synchronises the device and drops the workspace and
+ * any stored forward state. */
 qtm_status qtm_compile(qtm_plan *plan, int flags);
 
 /* Number of specialised pass kernels loaded for the current device (0 before

@@ -38,6 +38,14 @@ const char *qtm_debug_jit_source(const qtm_plan *plan, int which, int index, int
  * log in qtm_last_error on failure. */
 qtm_status qtm_debug_jit_compile(qtm_plan *plan, int flags);
 
+/* Measured FMA throughput of this GPU in the real type of `dtype` (QTM_C64:
+ * FP32, QTM_C128: FP64), flop/s with an FMA counted as 2: a register-only
+ * loop of independent FMA chains over 16 CTAs of 256 threads per SM, best of
+ * three launches timed with CUDA events on the current device.  Synchronises
+ * the device.  A roofline denominator for the pass kernels, which are FMA
+ * bound at 12 qubits; not used by any compute call. */
+qtm_status qtm_debug_fma_rate(int dtype, double *flops_per_s);
+
 /* The uneven batch's task list (host only), in the order the persistent
  * kernel hands tasks out: tasks[3i .. 3i+2] = (item, step, tile); step = -1
  * is a whole item, step >= 0 one pass (forward passes, then reverse passes)

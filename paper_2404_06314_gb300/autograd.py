@@ -68,10 +68,10 @@ class QuantumModule(torch.nn.Module):
     groups: name -> list of weight indices of the circuit (together a partition
     of range(n_weights)); default one group "weights".  init: name -> "uniform"
     (U[0, 2 pi]), "normal" (N(0, 1)), "ones", "zeros" or a tensor.
-    kernels: "general" (the plan's general pass kernels), "paired-general"
-    (two samples per CTA), "lanes" / "cpx" / "one" / "pairs" (plan-specialised kernels,
-    compiled once here; see Plan.compile) or "auto" (the default specialised
-    kernels, complex pairs, when the plan has them, else the general kernels).
+    kernels: "general" (the plan's general pass kernels), "cpx" (the
+    plan-specialised complex-pair kernels, compiled once here; see
+    Plan.compile) or "auto" (the specialised kernels when the plan has them,
+    else the general kernels).
     """
 
     def __init__(self, circuit, groups: Optional[Dict[str, Sequence[int]]] = None,
@@ -83,14 +83,12 @@ class QuantumModule(torch.nn.Module):
         self.plan = capi.Plan(circuit, dtype=dtype, path=path)
         if kernels == "auto":
             try:
-                self.plan.compile("cpx")
+                self.plan.compile()
             except capi.QtmError as e:
                 if e.status != capi.QTM_EUNSUPPORTED:
                     raise
-        elif kernels == "paired-general":
-            self.plan.set_pairing(True)
-        elif kernels in ("lanes", "one", "pairs", "cpx"):
-            self.plan.compile(kernels)
+        elif kernels == "cpx":
+            self.plan.compile()
         elif kernels != "general":
             raise ValueError(f"unknown kernels {kernels!r}")
         P = circuit.n_weights

@@ -22,7 +22,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU_SOURCES = ["capi.cu", "fused.cu", "naive.cu", "noalloc.cu", "multi.cu", "pauli.cu"]
 CPP_SOURCES = ["plan.cpp", "emulate.cpp", "jit.cpp"]
 # device headers embedded as the prelude of run-time generated kernels (NVRTC)
-PRELUDE_HEADERS = ["pod.h", "finalize_math.h", "tile.cuh", "tile_x2.cuh", "tile_lanes.cuh", "tile_cpx.cuh"]
+PRELUDE_HEADERS = ["pod.h", "finalize_math.h", "tile.cuh", "f32x2.cuh", "tile_cpx.cuh"]
 
 
 def _write_prelude() -> str:

@@ -22,11 +22,6 @@ QTM_OK, QTM_EINVAL, QTM_ENOMEM, QTM_ECUDA, QTM_EUNSUPPORTED, QTM_ETIMEOUT, QTM_E
 QTM_C64, QTM_C128 = 0, 1
 QTM_PATH_AUTO, QTM_PATH_FUSED, QTM_PATH_NAIVE = 0, 1, 2
 QTM_ADJ_GW_PER_SAMPLE, QTM_ADJ_RECOMPUTE = 1, 2
-QTM_COMPILE_SCALAR = 1
-QTM_COMPILE_SAMPLE_PAIRS = 2
-QTM_COMPILE_LANE_PAIRS = 3
-_COMPILE_KIND = {"cpx": 0, "one": QTM_COMPILE_SCALAR, "pairs": QTM_COMPILE_SAMPLE_PAIRS,
-                 "lanes": QTM_COMPILE_LANE_PAIRS}
 
 
 class qtm_gate(ctypes.Structure):
@@ -101,10 +96,6 @@ def lib(build_if_missing: bool = True):
         L.qtm_debug_emulate.argtypes = [vp, i, vp, vp, vp, vp, vp, vp]
         L.qtm_compile.argtypes = [vp, i]
         L.qtm_compile.restype = ctypes.c_int
-        L.qtm_set_sample_pairing.argtypes = [vp, i]
-        L.qtm_set_sample_pairing.restype = ctypes.c_int
-        L.qtm_get_sample_pairing.argtypes = [vp]
-        L.qtm_get_sample_pairing.restype = ctypes.c_int
         L.qtm_compiled_passes.argtypes = [vp]
         L.qtm_compiled_passes.restype = ctypes.c_int
         L.qtm_debug_jit_source.argtypes = [vp, i, i, i]
@@ -325,23 +316,11 @@ class Plan:
         self._raise(st, "qtm_adjoint")
         return gx, gw
 
-    def compile(self, kind: str = "cpx"):
-        """Specialise and load this plan's pass kernels (qtm_compile).  kind:
-        "cpx" (default: one sample per CTA, each complex amplitude one f32x2
-        register pair), "lanes" (one sample per CTA, two amplitudes per f32x2
-        pair), "one" (one sample per CTA, scalar registers) or "pairs" (two
-        samples per CTA on f32x2 register pairs)."""
-        self._raise(lib().qtm_compile(self.handle, _COMPILE_KIND[kind]), "qtm_compile")
+    def compile(self):
+        """Specialise and load this plan's pass kernels (qtm_compile): one
+        sample per CTA, each complex amplitude one f32x2 register pair."""
+        self._raise(lib().qtm_compile(self.handle, 0), "qtm_compile")
         return self
-
-    def set_pairing(self, on: bool = True):
-        """Run passes on the paired general kernel (two samples per CTA)."""
-        self._raise(lib().qtm_set_sample_pairing(self.handle, 1 if on else 0), "qtm_set_sample_pairing")
-        return self
-
-    @property
-    def pairing(self) -> bool:
-        return bool(lib().qtm_get_sample_pairing(self.handle))
 
     @property
     def parts(self) -> int:
@@ -351,12 +330,12 @@ class Plan:
     def compiled_passes(self) -> int:
         return int(lib().qtm_compiled_passes(self.handle))
 
-    def jit_source(self, which: int, index: int, kind: str = "cpx") -> str:
-        return lib().qtm_debug_jit_source(self.handle, int(which), int(index), _COMPILE_KIND[kind]).decode()
+    def jit_source(self, which: int, index: int) -> str:
+        return lib().qtm_debug_jit_source(self.handle, int(which), int(index), 0).decode()
 
-    def jit_compile_check(self, kind: str = "cpx"):
+    def jit_compile_check(self):
         """Compile every specialised pass with NVRTC, host only (no load)."""
-        self._raise(lib().qtm_debug_jit_compile(self.handle, _COMPILE_KIND[kind]), "qtm_debug_jit_compile")
+        self._raise(lib().qtm_debug_jit_compile(self.handle, 0), "qtm_debug_jit_compile")
 
     def jacobian(self, x, w, out=None, stream=None):
         """J[b, m, g] = d<O_m>/d theta_g for every gate angle (zero for CZ/CNOT)."""

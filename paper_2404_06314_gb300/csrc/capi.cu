@@ -64,12 +64,14 @@ struct qtm_plan {
     double2 *d_cs = nullptr;           // [B][rots] (cos, sin) of half angles (prep -> grad finalize)
     double *d_ppart = nullptr;         // [B][chunks][X/Y terms] expectation-value partial sums
     void *d_onehot = nullptr;          // [B][M] cotangent e_m (qtm_jacobian)
+    // qtm_jacobian: the forward's final states [B][2^sq] and the inputs of
+    // the pseudo-samples (sample, observable) [B * chunk][n_in]
+    void *d_jkeep = nullptr, *d_jx = nullptr;
+    size_t jkeep_bytes = 0, jx_bytes = 0;
     int32_t *d_gate_of_rot = nullptr;  // rotation id -> gate index
     std::vector<CUtensorMap> tm_fwd, tm_rev_phi, tm_rev_lam;
     std::vector<TmGeom> g_fwd, g_rev;
     std::vector<size_t> smem_fwd, smem_rev;
-    std::vector<size_t> smem_fwd_x2, smem_rev_x2;   // paired-sample kernels (eligible plans)
-    int pairing = 0;                   // general passes run two samples per CTA (k_pass_x2)
     // Pauli-string observables (qtm_build_pauli): one Z-observable plan per
     // group of terms sharing their X/Y qubits, outputs summed in part order
     std::vector<qtm_plan *> parts;
@@ -85,7 +87,6 @@ struct qtm_plan {
     // run-time specialised pass kernels (qtm_compile)
     std::vector<JitKernel> jit_fwd, jit_rev;
     int jit_device = -1;
-    int jit_pairs = 0;                 // loaded kernels take two samples per CTA
     std::string jit_src_cache;
     // profiling: events around each launch of the last forward / adjoint
     bool profiling = false;
@@ -140,9 +141,11 @@ void free_tables(qtm_plan *p)
 void free_workspace(qtm_plan *p)
 {
     void *ptrs[] = {p->d_phi, p->d_lam, p->d_Escratch, p->d_Epart, p->d_Gpart, p->d_abar, p->d_gw_ws,
-                    p->d_mats, p->d_tabs, p->d_onehot, p->d_cs, p->d_ppart};
+                    p->d_mats, p->d_tabs, p->d_onehot, p->d_cs, p->d_ppart, p->d_jkeep, p->d_jx};
     for (void *q : ptrs)
         if (q) cudaFree(q);
+    p->d_jkeep = p->d_jx = nullptr;
+    p->jkeep_bytes = p->jx_bytes = 0;
     p->d_phi = p->d_lam = p->d_Escratch = p->d_mats = p->d_tabs = p->d_onehot = nullptr;
     p->d_cs = nullptr;
     p->d_Epart = p->d_Gpart = p->d_abar = p->d_gw_ws = p->d_ppart = nullptr;
@@ -270,19 +273,7 @@ bool jit_active(const qtm_plan *p)
     return p->jit_device >= 0 && p->jit_device == p->device;
 }
 
-// The state in HBM is laid out for paired-sample kernels.
-bool use_x2(const qtm_plan *p) { return jit_active(p) ? p->jit_pairs != 0 : p->pairing != 0; }
 
-// Every pass can run on the paired / specialised kernels.
-bool pairable(const Plan &P)
-{
-    if (P.path != QTM_PATH_FUSED) return false;
-    if (!P.pterms.empty()) return false;   // X/Y terms read the state in its one-sample layout
-    for (const auto *v : {&P.fwd, &P.rev})
-        for (const auto &pd : *v)
-            if (!jit_eligible(P, pd)) return false;
-    return true;
-}
 
 cudaError_t launch_any(qtm_plan *p, bool rev, size_t i, PassArgs a, const CUtensorMap &t0, const CUtensorMap &t1,
                        cudaStream_t s)
@@ -291,10 +282,6 @@ cudaError_t launch_any(qtm_plan *p, bool rev, size_t i, PassArgs a, const CUtens
     if (jit_active(p) && i < v.size() && v[i].fn) {
         a.smem_bytes = v[i].smem;
         return jit_launch(v[i], a, t0, t1, s);
-    }
-    if (p->pairing) {
-        a.smem_bytes = (int)(rev ? p->smem_rev_x2[i] : p->smem_fwd_x2[i]);
-        return launch_pass_x2(rev, a, t0, t1, s);
     }
     return launch_pass(p->P.dtype, rev, a, t0, t1, s);
 }
@@ -316,12 +303,8 @@ qtm_status ensure_workspace(qtm_plan *p, int B)
         e = dmalloc(reinterpret_cast<void **>(&(ptr)), bytes);                          \
         if (e != cudaSuccess) { free_workspace(p); return fail(p, QTM_ENOMEM, "workspace allocation failed"); } \
     } while (0)
-    // paired-sample kernels: 16-byte elements per sample pair (an odd batch
-    // rounds up to a whole pair)
-    const bool x2 = use_x2(p);
-    const int Bq = x2 ? ((B + 1) & ~1) : B;
-    AL(p->d_phi, csize * NS * Bq);
-    if (p->needs_lam || P.path == QTM_PATH_NAIVE) AL(p->d_lam, csize * NS * Bq);
+    AL(p->d_phi, csize * NS * B);
+    if (p->needs_lam || P.path == QTM_PATH_NAIVE) AL(p->d_lam, csize * NS * B);
     AL(p->d_Escratch, rsize * (size_t)B * P.n_obs);
     AL(p->d_Epart, sizeof(double) * (size_t)B * tiles * P.n_obs);
     AL(p->d_Gpart, sizeof(double) * (size_t)B * runs * tiles * 3);
@@ -336,8 +319,7 @@ qtm_status ensure_workspace(qtm_plan *p, int B)
 #undef AL
     p->cap_B = B;
     if (P.path == QTM_PATH_FUSED) {
-        const int mdtype = x2 ? QTM_C128 : P.dtype;   // a pair element is laid out like a complex128
-        const int mB = x2 ? Bq / 2 : B;
+        const int mdtype = P.dtype, mB = B;
         p->tm_fwd.assign(P.fwd.size(), CUtensorMap{});
         p->g_fwd.assign(P.fwd.size(), TmGeom{});
         p->tm_rev_phi.assign(P.rev.size(), CUtensorMap{});
@@ -462,7 +444,7 @@ bool fuse_sample_steps(const qtm_plan *p)
 {
     const char *e = std::getenv("QTM_FUSE_SAMPLE_STEPS");
     if (e && *e == '0') return false;
-    return p->P.path == QTM_PATH_FUSED && p->P.tiles_per_sample == 1 && !use_x2(p);
+    return p->P.path == QTM_PATH_FUSED && p->P.tiles_per_sample == 1;
 }
 
 void set_prep_fields(qtm_plan *p, PassArgs &a)
@@ -574,6 +556,18 @@ qtm_status ensure_tmp(qtm_plan *p, size_t bytes)
     if (e != cudaSuccess) return fail(p, QTM_ENOMEM, "composite scratch allocation failed");
     p->tmp_bytes = bytes;
     return QTM_OK;
+}
+
+// A device buffer of at least `bytes` (kept across calls; freed with the workspace).
+cudaError_t ensure_buffer(void *&ptr, size_t &cap, size_t bytes)
+{
+    if (ptr && bytes <= cap) return cudaSuccess;
+    if (ptr) cudaFree(ptr);
+    ptr = nullptr;
+    cap = 0;
+    cudaError_t e = dmalloc(&ptr, bytes);
+    if (e == cudaSuccess) cap = bytes ? bytes : 16;
+    return e;
 }
 
 }  // namespace
@@ -722,6 +716,30 @@ qtm_status composite_adjoint(qtm_plan *p, int B, const void *gE, const void *x, 
     return QTM_OK;
 }
 
+// Observables per reverse sweep of qtm_jacobian.  One-tile plans (one CTA
+// per pseudo-sample) take every observable at once, so that B * M CTAs fill
+// the GPU; plans whose state spans several tiles take as many as keep the
+// chunk's phi and lam within three quarters of L2 (at least one).
+// QTM_JAC_CHUNK=<c> (a tuning switch) sets it.
+int jacobian_chunk(const qtm_plan *p, int B)
+{
+    const Plan &P = p->P;
+    const int M = std::max(1, P.n_obs);
+    int c = M;
+    if (const char *e = std::getenv("QTM_JAC_CHUNK")) {
+        const int v = std::atoi(e);
+        if (v >= 1) c = std::min(v, M);
+    } else if (P.tiles_per_sample > 1) {
+        int l2 = 0;
+        cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, p->device);
+        const double per = (double)B * std::ldexp((double)elem_bytes(P.dtype), P.state_qubits) * (p->needs_lam ? 2 : 1);
+        c = std::max(1, std::min(M, (int)(0.75 * (double)l2 / per)));
+    }
+    // the pseudo-batch stays within the batch sizes the kernels index with int
+    while (c > 1 && (long long)B * c > (1LL << 24)) c = (c + 1) / 2;
+    return c;
+}
+
 qtm_status composite_jacobian(qtm_plan *p, int B, const void *x, const void *w, void *jac, void *stream)
 {
     const Plan &P = p->P;
@@ -755,8 +773,14 @@ qtm_status qtm_build(int n_qubits, const qtm_gate *gates, int n_gates, const qtm
     qtm_plan *p = new (std::nothrow) qtm_plan();
     if (!p) return QTM_ENOMEM;
     std::string err;
+    // phase grouping: automatic (default), or QTM_PHASES=greedy / rr (a tuning switch)
+    const char *pm = std::getenv("QTM_PHASES");
+    const int phase_mode = !pm                              ? PHASES_AUTO
+                           : std::strcmp(pm, "rr") == 0     ? PHASES_ROUND_ROBIN
+                           : std::strcmp(pm, "greedy") == 0 ? PHASES_GREEDY
+                                                            : PHASES_AUTO;
     qtm_status st = make_plan(n_qubits, gates, n_gates, terms, n_terms, n_obs, n_weights, n_inputs,
-                              dtype, path, p->P, err);
+                              dtype, path, p->P, err, kMaxRunLen, phase_mode);
     if (st != QTM_OK) { delete p; return st; }
     const Plan &P = p->P;
     if (P.path == QTM_PATH_FUSED) {
@@ -769,14 +793,6 @@ qtm_status qtm_build(int n_qubits, const qtm_gate *gates, int n_gates, const qtm
         };
         for (const auto &pd : P.fwd) p->smem_fwd.push_back(sm(pd, false));
         for (const auto &pd : P.rev) p->smem_rev.push_back(sm(pd, true));
-        if (pairable(P)) {
-            auto sm2 = [&](const PassDesc &pd, bool rev) {
-                return pass_smem_bytes_x2(pd.K, rev, pd.slot_end - pd.slot_begin, (int)P.terms.size(), P.n_obs,
-                                          P.state_qubits, pd.phi_src == SRC_ANALYTIC ? pd.analytic_ents : 0);
-            };
-            for (const auto &pd : P.fwd) p->smem_fwd_x2.push_back(sm2(pd, false));
-            for (const auto &pd : P.rev) p->smem_rev_x2.push_back(sm2(pd, true));
-        }
         for (size_t v : p->smem_fwd)
             if (v > kMaxDynSmem) { delete p; return QTM_EUNSUPPORTED; }
         for (size_t v : p->smem_rev)
@@ -987,6 +1003,21 @@ qtm_status qtm_adjoint(qtm_plan *p, int B, const void *gE, const void *x, const 
     return QTM_OK;
 }
 
+qtm_status qtm_debug_fma_rate(int dtype, double *flops_per_s)
+{
+    if (!flops_per_s || (dtype != QTM_C64 && dtype != QTM_C128)) return QTM_EINVAL;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return QTM_ECUDA;
+    const int blocks = sms * 16;
+    void *out = nullptr;
+    if (cudaMalloc(&out, (size_t)blocks * 256 * elem_bytes(dtype)) != cudaSuccess) return QTM_ENOMEM;
+    const int iters = dtype == QTM_C128 ? 1 << 11 : 1 << 14;
+    cudaError_t e = probe_fma_rate(dtype, out, blocks, iters, nullptr, flops_per_s);
+    cudaFree(out);
+    return e == cudaSuccess ? QTM_OK : QTM_ECUDA;
+}
+
 qtm_status qtm_jacobian(qtm_plan *p, int B, const void *x, const void *w, void *jac, void *stream)
 {
     if (!p) return QTM_EINVAL;
@@ -1002,55 +1033,59 @@ qtm_status qtm_jacobian(qtm_plan *p, int B, const void *x, const void *w, void *
     if (P.path != QTM_PATH_FUSED) return fail(p, QTM_EUNSUPPORTED, "qtm_jacobian runs on the fused path");
     qtm_status st = ensure_device(p);
     if (st != QTM_OK) return st;
-    st = ensure_workspace(p, B);
-    if (st != QTM_OK) return st;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const size_t rsize = elem_bytes(P.dtype) / 2;
+    const size_t csize = elem_bytes(P.dtype), rsize = csize / 2;
+    const size_t row = csize << P.state_qubits;   // one sample's state
+    const int M = P.n_obs;
     const int G = P.n_user_gates;   // Jacobian columns: the gates as given
-    cudaError_t e = cudaMemsetAsync(jac, 0, rsize * (size_t)B * P.n_obs * (G > 0 ? G : 1), s);
+    // One costate per observable (Sec. II-B's (B, M, |Theta|) output), all of
+    // a chunk of observables in one reverse sweep: pseudo-sample b * cc + k
+    // is sample b with cotangent e_(m0 + k), starting from b's final state.
+    // The forward runs once; its states are kept and expanded per chunk.
+    const int c = jacobian_chunk(p, B);
+    st = ensure_workspace(p, B * c);
+    if (st != QTM_OK) return st;
+    if (ensure_buffer(p->d_jkeep, p->jkeep_bytes, row * (size_t)B) != cudaSuccess ||
+        ensure_buffer(p->d_jx, p->jx_bytes, rsize * (size_t)B * c * std::max(1, P.n_inputs)) != cudaSuccess)
+        return fail(p, QTM_ENOMEM, "jacobian buffer allocation failed");
+    cudaError_t e = cudaMemsetAsync(jac, 0, rsize * (size_t)B * M * (G > 0 ? G : 1), s);
     if (e != cudaSuccess) return cuda_fail(p, e, "jacobian clear");
-    bool consumes = false;
-    for (const auto &pd : P.rev) consumes |= pd.store_phi != 0;
     p->fwd_valid = false;
     prof_begin_call(p, 1, s);
-    // one costate per observable (Sec. II-B's (B, M, |Theta|) output): reverse
-    // passes with cotangent e_m, each rotation's angle gradient scattered to J
-    for (int m = 0; m < P.n_obs; ++m) {
-        if (m == 0 || consumes) {
-            st = run_forward_passes(p, B, x, w, s);
-            if (st != QTM_OK) return st;
-        }
-        e = launch_onehot(P.dtype, p->d_onehot, B, P.n_obs, m, s);
-        if (e != cudaSuccess) return cuda_fail(p, e, "one-hot cotangent");
+    st = run_forward_passes(p, B, x, w, s);
+    if (st != QTM_OK) return st;
+    e = cudaMemcpyAsync(p->d_jkeep, p->d_phi, row * (size_t)B, cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(p, e, "jacobian state copy");
+    for (int m0 = 0; m0 < M; m0 += c) {
+        const int cc = std::min(c, M - m0), Bp = B * cc;
+        e = launch_expand_rows(p->d_jkeep, p->d_phi, row, Bp, cc, s);
+        if (e == cudaSuccess && P.n_inputs > 0) e = launch_expand_x(P.dtype, x, p->d_jx, P.n_inputs, Bp, cc, s);
+        if (e == cudaSuccess) e = launch_onehot(P.dtype, p->d_onehot, Bp, M, m0, cc, s);
+        if (e != cudaSuccess) return cuda_fail(p, e, "jacobian pseudo-samples");
+        const void *xp = P.n_inputs > 0 ? p->d_jx : x;
+        st = run_prep(p, Bp, xp, w, s);   // run matrices and tables of the pseudo-samples
+        if (st != QTM_OK) return st;
         if (!P.pterms.empty()) {
             e = launch_pauli_costate(P.dtype, p->d_phi, P.state_qubits, p->d_pterms, (int)P.pterms.size(),
-                                     p->d_onehot, P.n_obs, B, p->d_lam, s);
+                                     p->d_onehot, M, Bp, p->d_lam, s);
             if (e != cudaSuccess) return cuda_fail(p, e, "pauli costate");
         }
         for (size_t i = 0; i < P.rev.size(); ++i) {
-            PassArgs a = pass_args(p, P.rev[i], p->g_rev[i], p->smem_rev[i], B, x, w, p->d_onehot);
+            PassArgs a = pass_args(p, P.rev[i], p->g_rev[i], p->smem_rev[i], Bp, xp, w, p->d_onehot);
+            ProfScope ps(p, 0);
             e = launch_any(p, true, i, a, p->tm_rev_phi[i], p->tm_rev_lam[i], s);
             if (e != cudaSuccess) return cuda_fail(p, e, "reverse pass launch");
         }
-        FinalizeArgs f = finalize_args(p, B, x, w);
+        FinalizeArgs f = finalize_args(p, Bp, xp, w);
         e = launch_grad_finalize(P.dtype, f, s);
-        if (e != cudaSuccess) return cuda_fail(p, e, "gradient finalize");
-        e = launch_jac_scatter(P.dtype, p->d_abar, p->d_gate_of_rot, (int)P.rots.size(), B, P.n_obs, m, G, jac, s);
-        if (e != cudaSuccess) return cuda_fail(p, e, "jacobian scatter");
+        if (e == cudaSuccess)
+            e = launch_jac_scatter(P.dtype, p->d_abar, p->d_gate_of_rot, (int)P.rots.size(), Bp, M, m0, cc, G, jac, s);
+        if (e != cudaSuccess) return cuda_fail(p, e, "gradient finalize / jacobian scatter");
     }
     return QTM_OK;
 }
 
 namespace {
-
-// Generate and compile every pass (host only; NVRTC, no device).
-JitMode jit_mode(int flags)
-{
-    return flags == QTM_COMPILE_SAMPLE_PAIRS ? JIT_PAIRS
-           : flags == QTM_COMPILE_SCALAR     ? JIT_ONE
-           : flags == QTM_COMPILE_LANE_PAIRS ? JIT_LANES
-                                             : JIT_CPX;
-}
 
 bool applies_udagger(const Plan &P, const PassDesc &pd)
 {
@@ -1060,8 +1095,8 @@ bool applies_udagger(const Plan &P, const PassDesc &pd)
     return false;
 }
 
-qtm_status compile_all(qtm_plan *p, JitMode mode, std::vector<std::vector<char>> &fwd_bin,
-                       std::vector<std::vector<char>> &rev_bin)
+// Generate and compile every pass (host only; NVRTC, no device).
+qtm_status compile_all(qtm_plan *p, std::vector<std::vector<char>> &fwd_bin, std::vector<std::vector<char>> &rev_bin)
 {
     const Plan &P = p->P;
     if (P.path != QTM_PATH_FUSED) return fail(p, QTM_EUNSUPPORTED, "specialised kernels exist for fused plans");
@@ -1070,10 +1105,8 @@ qtm_status compile_all(qtm_plan *p, JitMode mode, std::vector<std::vector<char>>
     std::vector<Job> jobs;
     fwd_bin.assign(P.fwd.size(), {});
     rev_bin.assign(P.rev.size(), {});
-    // CTAs per SM the register budget is compiled for: the paired kernels hold
-    // twice the state per thread
-    const bool pairs = mode == JIT_PAIRS;
-    int minb_f = pairs ? 2 : 3, minb_r = pairs ? 1 : 2;
+    // CTAs per SM the register budget is compiled for (forward, reverse)
+    int minb_f = 3, minb_r = 2;
     if (const char *e = std::getenv("QTM_JIT_MINB")) {   // tuning: "<forward>,<reverse>"
         int f = 0, r = 0;
         if (std::sscanf(e, "%d,%d", &f, &r) == 2 && f >= 1 && f <= 8 && r >= 1 && r <= 8) { minb_f = f; minb_r = r; }
@@ -1093,7 +1126,7 @@ qtm_status compile_all(qtm_plan *p, JitMode mode, std::vector<std::vector<char>>
     std::vector<std::thread> th;
     for (size_t k = 0; k < jobs.size(); ++k)
         th.emplace_back([&, k] {
-            ok[k] = jit_compile(jit_source(P, *jobs[k].pd, jobs[k].minb, mode), *jobs[k].out, logs[k]) ? 1 : 0;
+            ok[k] = jit_compile(jit_source(P, *jobs[k].pd, jobs[k].minb), *jobs[k].out, logs[k]) ? 1 : 0;
         });
     for (auto &t : th) t.join();
     for (size_t k = 0; k < jobs.size(); ++k)
@@ -1102,41 +1135,6 @@ qtm_status compile_all(qtm_plan *p, JitMode mode, std::vector<std::vector<char>>
 }
 
 }  // namespace
-
-qtm_status qtm_set_sample_pairing(qtm_plan *p, int on)
-{
-    if (!p) return QTM_EINVAL;
-    if (is_composite(p)) {
-        for (qtm_plan *part : p->parts) {
-            qtm_status st = qtm_set_sample_pairing(part, on);
-            if (st != QTM_OK) return part_fail(p, part, st);
-        }
-        p->pairing = on;
-        return QTM_OK;
-    }
-    if (on != 0 && on != 1) return fail(p, QTM_EINVAL, "on must be 0 or 1");
-    if (on && !p->P.pterms.empty())
-        return fail(p, QTM_EUNSUPPORTED, "X/Y observables need the one-sample state layout");
-    if (on && !pairable(p->P)) return fail(p, QTM_EUNSUPPORTED, "pairing needs a fused complex64 plan with tiles of >= 9 qubits");
-    if (on) {
-        for (size_t v : p->smem_fwd_x2)
-            if (v > kMaxDynSmem) return fail(p, QTM_EUNSUPPORTED, "paired tile exceeds shared memory");
-        for (size_t v : p->smem_rev_x2)
-            if (v > kMaxDynSmem) return fail(p, QTM_EUNSUPPORTED, "paired tile exceeds shared memory");
-    }
-    if (p->pairing == on) return QTM_OK;
-    if (p->d_phi) {   // the state layout changes: no launch may still use the old workspace
-        cudaError_t e = cudaDeviceSynchronize();
-        if (e != cudaSuccess) return cuda_fail(p, e, "synchronize before changing the state layout");
-    }
-    free_workspace(p);
-    p->cap_B = 0;
-    p->fwd_valid = false;
-    p->pairing = on;
-    return QTM_OK;
-}
-
-int qtm_get_sample_pairing(const qtm_plan *p) { return p ? p->pairing : 0; }
 
 qtm_status qtm_compile(qtm_plan *p, int flags)
 {
@@ -1148,18 +1146,12 @@ qtm_status qtm_compile(qtm_plan *p, int flags)
         }
         return QTM_OK;
     }
-    if (flags != 0 && flags != QTM_COMPILE_SCALAR && flags != QTM_COMPILE_SAMPLE_PAIRS &&
-        flags != QTM_COMPILE_LANE_PAIRS)
-        return fail(p, QTM_EINVAL, "unknown flags");
+    if (flags != 0) return fail(p, QTM_EINVAL, "flags must be 0");
     if (!jit_available()) return fail(p, QTM_EUNSUPPORTED, "NVRTC or driver entry points not available");
-    const JitMode mode = jit_mode(flags);
-    const bool pairs = mode == JIT_PAIRS;
-    if (pairs && !p->P.pterms.empty())
-        return fail(p, QTM_EUNSUPPORTED, "X/Y observables need the one-sample state layout");
     qtm_status st = ensure_device(p);
     if (st != QTM_OK) return st;
     std::vector<std::vector<char>> fb, rb;
-    st = compile_all(p, mode, fb, rb);
+    st = compile_all(p, fb, rb);
     if (st != QTM_OK) return st;
     cudaError_t e = cudaDeviceSynchronize();   // no launch of the old kernels or layout is in flight
     if (e != cudaSuccess) return cuda_fail(p, e, "synchronize before loading kernels");
@@ -1182,12 +1174,8 @@ qtm_status qtm_compile(qtm_plan *p, int flags)
         const auto &pds = rev ? P.rev : P.fwd;
         auto &ks = rev ? p->jit_rev : p->jit_fwd;
         const auto &bins = rev ? rb : fb;
-        const auto &gsm = rev ? p->smem_rev : p->smem_fwd;
         for (size_t i = 0; i < pds.size(); ++i) {
-            const int smem = (int)(pairs ? jit_smem_bytes_x2(P, pds[i])
-                                         : mode == JIT_LANES ? jit_smem_bytes_lanes(P, pds[i])
-                                         : mode == JIT_CPX   ? jit_smem_bytes_cpx(P, pds[i])
-                                                             : gsm[i]);
+            const int smem = (int)jit_smem_bytes_cpx(P, pds[i]);
             if ((size_t)smem > kMaxDynSmem) {
                 unload_all();
                 return fail(p, QTM_EUNSUPPORTED, "specialised kernel needs more shared memory than a CTA has");
@@ -1196,10 +1184,8 @@ qtm_status qtm_compile(qtm_plan *p, int flags)
                 unload_all();
                 return fail(p, QTM_ECUDA, err);
             }
-            ks[i].pairs = pairs ? 1 : 0;
         }
     }
-    p->jit_pairs = pairs ? 1 : 0;
     p->jit_device = p->device;
     return QTM_OK;
 }
@@ -1230,12 +1216,8 @@ const char *qtm_debug_jit_source(const qtm_plan *p, int which, int index, int fl
     const auto &v = which ? P.rev : P.fwd;
     if (index < 0 || index >= (int)v.size()) return "";
     qtm_plan *m = const_cast<qtm_plan *>(p);
-    const JitMode mode = jit_mode(flags);
-    const bool pairs = mode == JIT_PAIRS;
-    m->jit_src_cache = jit_eligible(P, v[index])
-                           ? jit_source(P, v[index],
-                                        pairs ? (which ? 1 : 2) : (which && applies_udagger(P, v[index]) ? 2 : 3),
-                                        mode)
+    m->jit_src_cache = flags == 0 && jit_eligible(P, v[index])
+                           ? jit_source(P, v[index], which && applies_udagger(P, v[index]) ? 2 : 3)
                            : std::string();
     return m->jit_src_cache.c_str();
 }
@@ -1243,8 +1225,9 @@ const char *qtm_debug_jit_source(const qtm_plan *p, int which, int index, int fl
 qtm_status qtm_debug_jit_compile(qtm_plan *p, int flags)
 {
     if (!p) return QTM_EINVAL;
+    if (flags != 0) return fail(p, QTM_EINVAL, "flags must be 0");
     std::vector<std::vector<char>> fb, rb;
-    return compile_all(p, jit_mode(flags), fb, rb);
+    return compile_all(p, fb, rb);
 }
 
 qtm_status qtm_sync(qtm_plan *p, void *stream)

@@ -44,11 +44,6 @@ cudaError_t launch_prep(int dtype, const PrepArgs &a, cudaStream_t s);
 size_t pass_smem_bytes(int K, int dtype, bool reverse, int nslots, int n_terms, int M,
                        int state_qubits, int n_prefix_ents);
 
-// Paired-sample pass kernel (two samples per CTA, complex64, K >= 9): grid
-// ceil(B / 2) * tiles; state laid out as 16-byte pair elements.
-cudaError_t launch_pass_x2(bool reverse, const PassArgs &a, const CUtensorMap &tm_phi, const CUtensorMap &tm_lam,
-                           cudaStream_t s);
-size_t pass_smem_bytes_x2(int K, bool reverse, int nslots, int n_terms, int M, int sq, int n_ents);
 cudaError_t launch_pass(int dtype, bool reverse, const PassArgs &a, const CUtensorMap &tm_phi,
                         const CUtensorMap &tm_lam, cudaStream_t s);
 cudaError_t launch_expval_finalize(int dtype, const FinalizeArgs &f, cudaStream_t s);
@@ -60,7 +55,13 @@ cudaError_t launch_gw_reduce(int dtype, const double *gw_ws, int B, int P, void 
 cudaError_t launch_accumulate(int dtype, const void *src, void *dst, size_t n, cudaStream_t s);
 cudaError_t launch_accumulate_cols(int dtype, const void *src, int Gs, void *dst, int Gd, size_t rows, cudaStream_t s);
 
-cudaError_t launch_onehot(int dtype, void *gE, int B, int M, int m, cudaStream_t s);
+// Jacobian pseudo-samples (b' = b * cc + k stands for sample b, observable
+// m0 + k): one-hot cotangents, the scatter of per-rotation gradients into
+// J [B][M][G], and the expansion of per-sample rows (states, inputs).
+cudaError_t launch_onehot(int dtype, void *gE, int Bp, int M, int m0, int cc, cudaStream_t s);
+cudaError_t probe_fma_rate(int dtype, void *out, int blocks, int iters, cudaStream_t s, double *flops_per_s);
+cudaError_t launch_expand_rows(const void *src, void *dst, size_t row_bytes, int Bp, int cc, cudaStream_t s);
+cudaError_t launch_expand_x(int dtype, const void *x, void *xp, int n_in, int Bp, int cc, cudaStream_t s);
 
 // Pauli strings with X/Y factors on the final state phi [B][2^sq] (pauli.cu):
 // E[b][m] += their expectation values (Ppart: [B][pauli_chunks(sq)][T] FP64
@@ -70,8 +71,8 @@ cudaError_t launch_pauli_expval(int dtype, const void *phi, int sq, const PauliT
                                 double *Ppart, void *E, cudaStream_t s);
 cudaError_t launch_pauli_costate(int dtype, const void *phi, int sq, const PauliTerm *terms, int T, const void *gE,
                                  int M, int B, void *lam, cudaStream_t s);
-cudaError_t launch_jac_scatter(int dtype, const double *abar, const int32_t *gate_of_rot, int n_rots, int B,
-                               int M, int m, int G, void *J, cudaStream_t s);
+cudaError_t launch_jac_scatter(int dtype, const double *abar, const int32_t *gate_of_rot, int n_rots, int Bp,
+                               int M, int m0, int cc, int G, void *J, cudaStream_t s);
 
 // naive one-gate-per-kernel path
 struct NaiveArgs {

@@ -16,7 +16,6 @@
 #include "device.h"
 #include "tile.cuh"
 #include "tile_cpx.cuh"
-#include "tile_x2.cuh"
 
 namespace qtm {
 
@@ -42,17 +41,6 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 1 : (REV ? 2 : 3)) k_pas
 {
     pass_body<R, REV>(a, &tm_phi, &tm_lam, [](const TileJob &j, const TileSmem<R> &S, bool lam_valid) {
         run_phases_any<R, REV>(j, S, lam_valid);
-    });
-}
-
-// Two samples per CTA on f32x2 register pairs (tile_x2.cuh); complex64, K >= 9.
-template <bool REV>
-__global__ void __launch_bounds__(256, REV ? 1 : 2) k_pass_x2(const __grid_constant__ PassArgs a,
-                                                             const __grid_constant__ CUtensorMap tm_phi,
-                                                             const __grid_constant__ CUtensorMap tm_lam)
-{
-    pass_body_x2<REV>(a, &tm_phi, &tm_lam, [](const TileJobX2 &j, const TileSmemX2 &S, bool lam_valid) {
-        run_phases_x2<REV>(j, S, lam_valid);
     });
 }
 
@@ -121,45 +109,111 @@ __global__ void k_gw_reduce(const double *gw_ws, int B, int P, R *gw)
     if (threadIdx.x == 0) gw[j] = (R)red[0];
 }
 
-// cotangent e_m: gE[b][k] = (k == m)
+// Jacobian pseudo-samples: row b' = b * cc + k of a chunk stands for sample
+// b and observable m0 + k.  Cotangent e_(m0 + k): gE[b'][j] = (j == m0 + b' % cc).
 template <typename R>
-__global__ void k_onehot(R *gE, int B, int M, int m)
+__global__ void k_onehot(R *gE, int Bp, int M, int m0, int cc)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < B * M) gE[i] = (i % M) == m ? (R)1 : (R)0;
+    if (i < Bp * M) gE[i] = (i % M) == m0 + (i / M) % cc ? (R)1 : (R)0;
 }
 
-// J[b][m][gate_of_rot[r]] = abar[b][r]  (gates that are not rotations stay 0)
+// J[b][m0 + k][gate_of_rot[r]] = abar[b * cc + k][r]  (gates that are not
+// rotations stay 0)
 template <typename R>
-__global__ void k_jac_scatter(const double *abar, const int32_t *gate_of_rot, int n_rots, int B, int M,
-                              int m, int G, R *J)
+__global__ void k_jac_scatter(const double *abar, const int32_t *gate_of_rot, int n_rots, int Bp, int M,
+                              int m0, int cc, int G, R *J)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= B * n_rots) return;
-    const int b = i / n_rots, r = i % n_rots;
+    if (i >= Bp * n_rots) return;
+    const int bp = i / n_rots, r = i % n_rots;
+    const int b = bp / cc, m = m0 + bp % cc;
     const int g = gate_of_rot[r];   // -1: a constant rotation from a lowered H (no column)
-    if (g >= 0) J[((size_t)b * M + m) * G + g] = (R)abar[(size_t)b * n_rots + r];
+    if (g >= 0) J[((size_t)b * M + m) * G + g] = (R)abar[(size_t)bp * n_rots + r];
+}
+
+// dst[b'][i] = src[b' / cc][i] over rows of `row` 16-byte words (a state
+// row, 2^sq complex amplitudes, is a whole number of them for sq >= 4 (c64)).
+__global__ void k_expand_rows16(const uint4 *src, uint4 *dst, size_t row, int Bp, int cc)
+{
+    const size_t n = row * (size_t)Bp;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t bp = i / row, k = i % row;
+        dst[i] = src[(bp / cc) * row + k];
+    }
+}
+
+// x'[b'][j] = x[b' / cc][j]
+template <typename R>
+__global__ void k_expand_x(const R *x, R *xp, int n_in, int Bp, int cc)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= Bp * n_in) return;
+    xp[i] = x[(size_t)(i / n_in / cc) * n_in + i % n_in];
 }
 
 }  // namespace
 
-cudaError_t launch_onehot(int dtype, void *gE, int B, int M, int m, cudaStream_t s)
+cudaError_t launch_onehot(int dtype, void *gE, int Bp, int M, int m0, int cc, cudaStream_t s)
 {
-    const int n = B * M, blk = 256, grd = (n + blk - 1) / blk;
-    if (dtype == QTM_C128) k_onehot<double><<<grd, blk, 0, s>>>(static_cast<double *>(gE), B, M, m);
-    else k_onehot<float><<<grd, blk, 0, s>>>(static_cast<float *>(gE), B, M, m);
+    const int n = Bp * M, blk = 256, grd = (n + blk - 1) / blk;
+    if (n <= 0) return cudaSuccess;
+    if (dtype == QTM_C128) k_onehot<double><<<grd, blk, 0, s>>>(static_cast<double *>(gE), Bp, M, m0, cc);
+    else k_onehot<float><<<grd, blk, 0, s>>>(static_cast<float *>(gE), Bp, M, m0, cc);
     return cudaGetLastError();
 }
 
-cudaError_t launch_jac_scatter(int dtype, const double *abar, const int32_t *gate_of_rot, int n_rots, int B,
-                               int M, int m, int G, void *J, cudaStream_t s)
+cudaError_t launch_jac_scatter(int dtype, const double *abar, const int32_t *gate_of_rot, int n_rots, int Bp,
+                               int M, int m0, int cc, int G, void *J, cudaStream_t s)
 {
-    if (n_rots <= 0) return cudaSuccess;
-    const int n = B * n_rots, blk = 256, grd = (n + blk - 1) / blk;
+    if (n_rots <= 0 || Bp <= 0) return cudaSuccess;
+    const int n = Bp * n_rots, blk = 256, grd = (n + blk - 1) / blk;
     if (dtype == QTM_C128)
-        k_jac_scatter<double><<<grd, blk, 0, s>>>(abar, gate_of_rot, n_rots, B, M, m, G, static_cast<double *>(J));
+        k_jac_scatter<double><<<grd, blk, 0, s>>>(abar, gate_of_rot, n_rots, Bp, M, m0, cc, G,
+                                                   static_cast<double *>(J));
     else
-        k_jac_scatter<float><<<grd, blk, 0, s>>>(abar, gate_of_rot, n_rots, B, M, m, G, static_cast<float *>(J));
+        k_jac_scatter<float><<<grd, blk, 0, s>>>(abar, gate_of_rot, n_rots, Bp, M, m0, cc, G,
+                                                  static_cast<float *>(J));
+    return cudaGetLastError();
+}
+
+// Register-only FMA loop for a throughput probe: 8 independent chains per
+// thread, `iters` rounds; one store per thread keeps the chains live.
+template <typename R>
+__global__ void k_fma_probe(R *out, int iters, R a, R b)
+{
+    R v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = (R)(threadIdx.x + k);
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) v[k] = v[k] * a + b;
+    }
+    R t = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) t += v[k];
+    out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = t;
+}
+
+cudaError_t launch_expand_rows(const void *src, void *dst, size_t row_bytes, int Bp, int cc, cudaStream_t s)
+{
+    if (Bp <= 0 || row_bytes == 0) return cudaSuccess;
+    if (row_bytes % 16) return cudaErrorInvalidValue;
+    const size_t row = row_bytes / 16, n = row * (size_t)Bp;
+    const int blk = 256;
+    const int grd = (int)std::min<size_t>((n + blk - 1) / blk, 152 * 16);
+    k_expand_rows16<<<grd, blk, 0, s>>>(static_cast<const uint4 *>(src), static_cast<uint4 *>(dst), row, Bp, cc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_expand_x(int dtype, const void *x, void *xp, int n_in, int Bp, int cc, cudaStream_t s)
+{
+    const int n = Bp * n_in, blk = 256, grd = (n + blk - 1) / blk;
+    if (n <= 0) return cudaSuccess;
+    if (dtype == QTM_C128)
+        k_expand_x<double><<<grd, blk, 0, s>>>(static_cast<const double *>(x), static_cast<double *>(xp), n_in, Bp, cc);
+    else
+        k_expand_x<float><<<grd, blk, 0, s>>>(static_cast<const float *>(x), static_cast<float *>(xp), n_in, Bp, cc);
     return cudaGetLastError();
 }
 
@@ -173,24 +227,6 @@ size_t pass_smem_bytes(int K, int dtype, bool reverse, int nslots, int n_terms, 
     Layout L = make_layout(K, csize, reverse, nslots, n_terms, M, state_qubits, n_prefix_ents,
                            nwarps, rsize);
     return (size_t)L.total + 1024;
-}
-
-size_t pass_smem_bytes_x2(int K, bool reverse, int nslots, int n_terms, int M, int sq, int n_ents)
-{
-    const LayoutX2 L = make_layout_x2(K, reverse, nslots, n_terms, M, sq, n_ents, (1 << (K - 4)) >> 5, (int)sizeof(Ent));
-    return (size_t)L.total + 1024;
-}
-
-cudaError_t launch_pass_x2(bool reverse, const PassArgs &a, const CUtensorMap &tm_phi, const CUtensorMap &tm_lam,
-                           cudaStream_t s)
-{
-    const dim3 grid((unsigned)((a.B + 1) / 2) * (unsigned)a.tiles), block(1u << (a.K - 4));
-    const size_t smem = (size_t)a.smem_bytes;
-    auto fn = reverse ? k_pass_x2<true> : k_pass_x2<false>;
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    fn<<<grid, block, smem, s>>>(a, tm_phi, tm_lam);
-    return cudaGetLastError();
 }
 
 cudaError_t launch_pass(int dtype, bool reverse, const PassArgs &a, const CUtensorMap &tm_phi,
@@ -271,6 +307,37 @@ cudaError_t launch_gw_reduce(int dtype, const double *gw_ws, int B, int P, void 
     if (dtype == QTM_C128) k_gw_reduce<double><<<P, 256, 0, s>>>(gw_ws, B, P, static_cast<double *>(gw));
     else k_gw_reduce<float><<<P, 256, 0, s>>>(gw_ws, B, P, static_cast<float *>(gw));
     return cudaGetLastError();
+}
+
+}  // namespace qtm
+
+namespace qtm {
+
+// FMA throughput (flop/s, an FMA counted as 2) of a register-only loop in the
+// plan real type of `dtype`, timed with CUDA events on `s`; `out` holds one
+// element per thread of the grid (blocks x 256).
+cudaError_t probe_fma_rate(int dtype, void *out, int blocks, int iters, cudaStream_t s, double *flops_per_s)
+{
+    cudaEvent_t e0, e1;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e != cudaSuccess) return e;
+    e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) { cudaEventDestroy(e0); return e; }
+    float best = 1e30f;
+    for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
+        cudaEventRecord(e0, s);
+        if (dtype == QTM_C128) k_fma_probe<double><<<blocks, 256, 0, s>>>(static_cast<double *>(out), iters, 0.999999, 1e-7);
+        else k_fma_probe<float><<<blocks, 256, 0, s>>>(static_cast<float *>(out), iters, 0.999999f, 1e-7f);
+        cudaEventRecord(e1, s);
+        e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0 && ms > 0.f) best = std::min(best, ms);   // the first launch is a warm-up
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e == cudaSuccess) *flops_per_s = 2.0 * 8.0 * (double)iters * blocks * 256.0 / (best * 1e-3);
+    return e;
 }
 
 }  // namespace qtm

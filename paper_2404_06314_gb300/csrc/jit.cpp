@@ -65,93 +65,14 @@ uint32_t local_mask(const PassDesc &pd, uint64_t zm)
     return (uint32_t)(zm & ((1ull << pd.l) - 1ull)) | (uint32_t)(((zm >> pd.h) & ((1ull << pd.m) - 1ull)) << pd.l);
 }
 
-// balanced sum of named f2 values: add2 tree
-std::string sum_tree(const std::vector<std::string> &v, size_t b, size_t e)
-{
-    if (e - b == 1) return v[b];
-    const size_t mid = b + (e - b) / 2;
-    return "add2(" + sum_tree(v, b, mid) + ", " + sum_tree(v, mid, e) + ")";
-}
-
-std::string signed_sum(const std::vector<std::string> &pos, const std::vector<std::string> &neg)
-{
-    if (pos.empty() && neg.empty()) return "0ull";
-    if (neg.empty()) return sum_tree(pos, 0, pos.size());
-    if (pos.empty()) return "(" + sum_tree(neg, 0, neg.size()) + " ^ kSign2)";
-    return "sub2(" + sum_tree(pos, 0, pos.size()) + ", " + sum_tree(neg, 0, neg.size()) + ")";
-}
-
 bool has_reg_bit(int x, int lo) { return x < kFixed && x >= lo && x < lo + kRegBits; }
 
-constexpr int kLaneSlotPairsHost = 18;   // f32x2 pairs per run slot in the lane-pair table
-
-// byte offset of the lane-pair table from the tile program's aligned shared base
-size_t lane_table_offset(const Plan &P, const PassDesc &pd)
+// byte offset of the complex-pair matrix table from the tile program's
+// aligned shared base (it follows the tile program's shared memory)
+size_t cpx_table_offset(const Plan &P, const PassDesc &pd)
 {
     return pass_smem_bytes(pd.K, P.dtype, pd.reverse != 0, pd.slot_end - pd.slot_begin, (int)P.terms.size(), P.n_obs,
                            P.state_qubits, pd.phi_src == SRC_ANALYTIC ? pd.analytic_ents : 0) - 1024;
-}
-
-// <O_m> partials with the register sign pattern of every term a constant.
-void gen_expval_x2(std::ostringstream &o, const Plan &P, const PassDesc &pd, int lo)
-{
-    o << "        {\n            f2 pr[kRegs];\n#pragma unroll\n            for (int jj = 0; jj < kRegs; ++jj) "
-         "pr[jj] = fma2(p[jj].r, p[jj].r, mul2(p[jj].i, p[jj].i));\n";
-    std::vector<int> seen(16, 0);
-    for (const Term &t : P.terms) {
-        const int rm = (int)((local_mask(pd, t.zmask) >> lo) & 15u);
-        if (seen[rm]) continue;
-        seen[rm] = 1;
-        std::vector<std::string> pos, neg;
-        for (int jj = 0; jj < kRegs; ++jj)
-            (__builtin_popcount(jj & rm) & 1 ? neg : pos).push_back("pr[" + std::to_string(jj) + "]");
-        o << "            const f2 s" << rm << " = " << signed_sum(pos, neg) << ";\n";
-    }
-    for (int m = 0; m < P.n_obs; ++m) {
-        bool any = false;
-        for (size_t t = 0; t < P.terms.size(); ++t) {
-            if (P.terms[t].obs != m) continue;
-            if (!any) o << "            { f2 e = 0ull;\n";
-            any = true;
-            const uint32_t lm = local_mask(pd, P.terms[t].zmask);
-            const int rm = (int)((lm >> lo) & 15u);
-            o << "              e = fma2(S.tcoef[" << t << "] ^ ((__popc(xt & 0x" << std::hex << lm << std::dec
-              << "u) & 1u) ? kSign2 : 0ull), s" << rm << ", e);\n";
-        }
-        if (any)
-            o << "              e = warp_sum2(e); if (lane == 0) S.redE[warp * " << P.n_obs << " + " << m
-              << "] = e; }\n";
-    }
-    o << "        }\n";
-}
-
-// lam = (sum_m gE_m O_m) phi with constant register sign patterns.
-void gen_costate_x2(std::ostringstream &o, const Plan &P, const PassDesc &pd, int lo)
-{
-    o << "        {\n";
-    std::vector<std::vector<size_t>> by_rm(16);
-    for (size_t t = 0; t < P.terms.size(); ++t)
-        by_rm[(local_mask(pd, P.terms[t].zmask) >> lo) & 15u].push_back(t);
-    std::vector<int> rms;
-    for (int rm = 0; rm < 16; ++rm) {
-        if (by_rm[rm].empty()) continue;
-        rms.push_back(rm);
-        std::vector<std::string> parts;
-        for (size_t t : by_rm[rm]) {
-            std::ostringstream e;
-            e << "(S.tcoef[" << t << "] ^ ((__popc(xt & 0x" << std::hex << local_mask(pd, P.terms[t].zmask)
-              << std::dec << "u) & 1u) ? kSign2 : 0ull))";
-            parts.push_back(e.str());
-        }
-        o << "            const f2 c" << rm << " = " << sum_tree(parts, 0, parts.size()) << ";\n";
-    }
-    for (int jj = 0; jj < kRegs; ++jj) {
-        std::vector<std::string> pos, neg;
-        for (int rm : rms) (__builtin_popcount(jj & rm) & 1 ? neg : pos).push_back("c" + std::to_string(rm));
-        o << "            { const f2 d = " << signed_sum(pos, neg) << "; q[" << jj << "].r = mul2(d, p[" << jj
-          << "].r); q[" << jj << "].i = mul2(d, p[" << jj << "].i); }\n";
-    }
-    o << "        }\n";
 }
 
 // The DIAG sign mask of the thread's 16 registers as an expression (constant
@@ -187,232 +108,6 @@ std::string diag_mask(const Plan &P, const DevOp &op, int lo)
 }
 
 
-// ---- lane-paired one-sample kernels (tile_lanes.cuh) ---------------------------------
-
-// shared accesses of the lane kernels outside register group 0: 64-bit
-// (default; measured 2 % faster at 20 qubits) or scalar 32-bit
-// (QTM_JIT_LANES_VEC64=0, a tuning switch)
-const char *lanes_v64()
-{
-    const char *v = std::getenv("QTM_JIT_LANES_VEC64");
-    return (v && *v == '0') ? "false" : "true";
-}
-
-// run-matrix table reads of the lane kernels: "true" = reads the compiler
-// may not merge across the two applications of a reverse op (default), else
-// plain loads (QTM_JIT_TABLE_VOLATILE=0, a tuning switch)
-std::string lanes_table_volatile()
-{
-    const char *v = std::getenv("QTM_JIT_TABLE_VOLATILE");
-    return (v && *v == '0') ? "false" : "true";
-}
-
-int lane_jj_host(int S, int k, int h) { return ((k >> S) << (S + 1)) | (h << S) | (k & ((1 << S) - 1)); }
-
-// lane bit of a phase: the register bit with the least gate work on it (bit 0
-// for a group at tile bit 0, where 16-byte shared accesses hold one lane pair)
-int choose_lane_bit(const Plan &P, const DevPhase &phs)
-{
-    int cost[4] = {0, 0, 0, 0};
-    const int lo = phs.lo;
-    if (lo == 0) return 0;
-    for (int k = phs.op_begin; k < phs.op_end; ++k) {
-        const DevOp &op = P.ops[k];
-        if ((op.type == OP_U2 || op.type == OP_GRAD) && has_reg_bit(op.a, lo))
-            cost[op.a - lo] += op.type == OP_GRAD ? 3 : 1;
-    }
-    int best = 0;
-    for (int r = 1; r < 4; ++r)
-        if (cost[r] < cost[best]) best = r;
-    return best;
-}
-
-void gen_expval_lanes(std::ostringstream &o, const Plan &P, const PassDesc &pd, int lo, int S)
-{
-    o << "        {\n            f2 pr[kLanePairs];\n#pragma unroll\n            for (int k = 0; k < kLanePairs; ++k) "
-         "pr[k] = fma2(p[k].r, p[k].r, mul2(p[k].i, p[k].i));\n";
-    std::vector<int> seen(16, 0);
-    for (const Term &t : P.terms) {
-        const int rm = (int)((local_mask(pd, t.zmask) >> lo) & 15u);
-        if (seen[rm]) continue;
-        seen[rm] = 1;
-        std::vector<std::string> pos, neg;
-        for (int k = 0; k < 8; ++k)
-            (__builtin_popcount(lane_jj_host(S, k, 0) & rm) & 1 ? neg : pos).push_back("pr[" + std::to_string(k) + "]");
-        o << "            const f2 a" << rm << " = " << signed_sum(pos, neg) << ";\n";
-        o << "            const float s" << rm << " = lane0(a" << rm << ")" << (((rm >> S) & 1) ? " - " : " + ")
-          << "lane1(a" << rm << ");\n";
-    }
-    for (int m = 0; m < P.n_obs; ++m) {
-        bool any = false;
-        for (size_t t = 0; t < P.terms.size(); ++t) {
-            if (P.terms[t].obs != m) continue;
-            if (!any) o << "            { float e = 0.f;\n";
-            any = true;
-            const uint32_t lm = local_mask(pd, P.terms[t].zmask);
-            const int rm = (int)((lm >> lo) & 15u);
-            o << "              e = fmaf((__popc(xt & 0x" << std::hex << lm << std::dec << "u) & 1u) ? -S.tcoef[" << t
-              << "] : S.tcoef[" << t << "], s" << rm << ", e);\n";
-        }
-        if (any)
-            o << "              e = warp_sum(e, 32, 0xffffffffu); if (lane == 0) S.redE[warp * " << P.n_obs << " + "
-              << m << "] = e; }\n";
-    }
-    o << "        }\n";
-}
-
-// acc: q holds the costate's X/Y part (loaded from memory); add the Z part.
-void gen_costate_lanes(std::ostringstream &o, const Plan &P, const PassDesc &pd, int lo, int S, bool acc)
-{
-    o << "        {\n";
-    std::vector<std::vector<size_t>> by_rm(16);
-    for (size_t t = 0; t < P.terms.size(); ++t) by_rm[(local_mask(pd, P.terms[t].zmask) >> lo) & 15u].push_back(t);
-    std::vector<int> rms;
-    for (int rm = 0; rm < 16; ++rm) {
-        if (by_rm[rm].empty()) continue;
-        rms.push_back(rm);
-        o << "            const float c" << rm << " = 0.f";
-        for (size_t t : by_rm[rm])
-            o << " + ((__popc(xt & 0x" << std::hex << local_mask(pd, P.terms[t].zmask) << std::dec
-              << "u) & 1u) ? -S.tcoef[" << t << "] : S.tcoef[" << t << "])";
-        o << ";\n";
-    }
-    auto dexpr = [&](int jj) {
-        std::string e = "0.f";
-        for (int rm : rms) e += std::string(__builtin_popcount(jj & rm) & 1 ? " - c" : " + c") + std::to_string(rm);
-        return e;
-    };
-    for (int k = 0; k < 8; ++k)
-        o << "            { const f2 d = pack2(" << dexpr(lane_jj_host(S, k, 0)) << ", " << dexpr(lane_jj_host(S, k, 1))
-          << (acc ? "); q[" + std::to_string(k) + "].r = fma2(d, p[" + std::to_string(k) + "].r, q[" +
-                        std::to_string(k) + "].r); q[" + std::to_string(k) + "].i = fma2(d, p[" + std::to_string(k) +
-                        "].i, q[" + std::to_string(k) + "].i); }\n"
-                  : "); q[" + std::to_string(k) + "].r = mul2(d, p[" + std::to_string(k) + "].r); q[" +
-                        std::to_string(k) + "].i = mul2(d, p[" + std::to_string(k) + "].i); }\n");
-    o << "        }\n";
-}
-
-
-// One op of a lane-paired phase (register group lo, lane bit sl); `slot` is
-// the C expression of its run slot.
-void lanes_op(std::ostringstream &o, const Plan &P, const PassDesc &pd, int k, int lo, int sl, const std::string &slot)
-{
-    const bool rev = pd.reverse != 0;
-    const int nslots = pd.slot_end - pd.slot_begin;
-    const DevOp &op = P.ops[k];
-    const bool reg_a = has_reg_bit(op.a, lo);
-    const bool reg_b = has_reg_bit(op.b, lo);
-    if (((op.type == OP_U2 || op.type == OP_GRAD) && !reg_a) || (op.type == OP_CNOT && !reg_b) ||
-        ((op.type == OP_U2 || op.type == OP_GRAD) && (op.slot < 0 || op.slot >= nslots)) ||
-        (op.type == OP_DIAG && (op.a < 0 || op.a + op.b > (int)P.diag_pairs.size()))) {
-        o << "#error \"op " << k << " has an operand outside its phase\"\n";
-        return;
-    }
-    const int rb = op.a - lo;
-    const std::string tab = "LT + " + std::to_string(kLaneSlotPairsHost) + " * " + slot;
-    const std::string vt = lanes_table_volatile();
-    const std::string apply =
-        rb == sl ? "u2_lanes_s<" + vt + ">(" : "u2_lanes<SB, " + std::to_string(rb) + ", " + vt + ">(";
-    switch (op.type) {
-    case OP_U2:
-        o << "        " << apply << "p, " << tab << ");\n";
-        break;
-    case OP_GRAD:
-        o << "        { float vx, vy, vz; "
-          << (rb == sl ? std::string("grad_lanes_s(") : "grad_lanes<SB, " + std::to_string(rb) + ">(")
-          << "p, q, vx, vy, vz);"
-          << " const float v = warp_sum3(vx, vy, vz, lane);"
-          << " if ((lane & 7) == 0 && lane < 24) S.redG[warp * " << 3 * nslots << " + 3 * " << slot
-          << " + (lane >> 3)] = v;";
-        if (!(op.flags & OPF_SKIP_APPLY)) o << " " << apply << "p, " << tab << "); " << apply << "q, " << tab << ");";
-        o << " }\n";
-        break;
-    case OP_DIAG:
-        o << "        { " << diag_mask(P, op, lo) << " flip_lanes<SB, " << (rev ? "true" : "false") << ">(p, q, m); }\n";
-        break;
-    case OP_CNOT: {
-        const int rt = op.b - lo;
-        if (has_reg_bit(op.a, lo)) {
-            o << "        cnot_lanes_static<SB, " << (op.a - lo) << ", " << rt << ">(p);";
-            if (rev) o << " cnot_lanes_static<SB, " << (op.a - lo) << ", " << rt << ">(q);";
-            o << "\n";
-        } else {
-            o << "        { const int c = (int)(" << operand_bit(op.a) << " & 1u); cnot_lanes<SB, " << rt << ">(p, c);";
-            if (rev) o << " cnot_lanes<SB, " << rt << ">(q, c);";
-            o << " }\n";
-        }
-        break;
-    }
-    case OP_EXPVAL: gen_expval_lanes(o, P, pd, lo, sl); break;
-    case OP_COSTATE: gen_costate_lanes(o, P, pd, lo, sl, (op.flags & OPF_ACCUMULATE) != 0); break;
-    default: break;
-    }
-}
-
-// Lane-paired pass as threaded code: every distinct routine (phase entry with
-// its register group and lane bit, one op with its register bits, phase exit)
-// is emitted once; a program of (routine, slot) pairs in constant memory
-// drives a dispatch loop.  The routines of a pass are far smaller than the
-// straight-line program, so they stay in the SM's instruction caches.
-std::string lanes_threaded_body(const Plan &P, const PassDesc &pd, int &n_routines, int &n_prog)
-{
-    const bool rev = pd.reverse != 0;
-    std::vector<std::string> routines;
-    std::vector<int> prog;
-    auto emit = [&](const std::string &body, int slot) {
-        size_t r = 0;
-        while (r < routines.size() && routines[r] != body) ++r;
-        if (r == routines.size()) routines.push_back(body);
-        prog.push_back((int)r);
-        prog.push_back(slot);
-    };
-    bool lam_valid = rev && pd.lam_src == SRC_LOAD;
-    for (int ph = pd.phase_begin; ph < pd.phase_end; ++ph) {
-        const DevPhase &phs = P.phases[ph];
-        const int lo = phs.lo, sl = choose_lane_bit(P, phs);
-        const std::string head = "        constexpr int LO = " + std::to_string(lo) + "; constexpr int SB = " +
-                                 std::to_string(sl) + "; (void)LO; (void)SB;\n";
-        {
-            std::ostringstream b;
-            b << head << "        xt = ((uint32_t)tid & ((1u << LO) - 1u)) | (((uint32_t)tid >> LO) << (LO + 4));\n";
-            b << "        regs_load_lanes<LO, SB, " << (lam_valid ? "true" : "false") << ", " << lanes_v64()
-              << ">(p, q, S, xt);\n";
-            emit(b.str(), 0);
-        }
-        for (int k = phs.op_begin; k < phs.op_end; ++k) {
-            std::ostringstream b;
-            b << head;
-            lanes_op(b, P, pd, k, lo, sl, "sl");
-            emit(b.str(), (P.ops[k].type == OP_U2 || P.ops[k].type == OP_GRAD) ? P.ops[k].slot : 0);
-        }
-        {
-            std::ostringstream b;
-            b << head << "        regs_store_lanes<LO, SB, " << (rev ? "true" : "false") << ", " << lanes_v64()
-              << ">(p, q, S, xt);\n        __syncthreads();\n";
-            emit(b.str(), 0);
-        }
-        if (rev) lam_valid = true;
-    }
-    n_routines = (int)routines.size();
-    n_prog = (int)prog.size() / 2;
-    std::ostringstream o;
-    o << "    uint32_t xt = 0;\n";
-    o << "#pragma unroll 1\n    for (int pc = 0; pc < " << n_prog << "; ++pc) {\n";
-    o << "        const int r = kProgram[2 * pc], sl = kProgram[2 * pc + 1];\n        (void)sl;\n";
-    o << "        switch (r) {\n";
-    for (size_t r = 0; r < routines.size(); ++r) {
-        o << "        " << (r + 1 < routines.size() ? "case " + std::to_string(r) + ":" : "default:") << " {\n";
-        o << routines[r] << "        } break;\n";
-    }
-    o << "        }\n    }\n";
-    std::ostringstream t;
-    t << "__constant__ int kProgram[" << (prog.empty() ? 2 : prog.size()) << "] = {";
-    for (size_t i = 0; i < prog.size(); ++i) t << (i ? ", " : "") << prog[i];
-    if (prog.empty()) t << "0, 0";
-    t << "};\n";
-    return t.str() + "\x01" + o.str();
-}
-
 // Phases emitted straight-line (default; measured 5 % faster at 12 and 20
 // qubits) or as a loop over a phase table with one copy of each distinct phase
 // program (QTM_JIT_PHASE_LOOP=1, a tuning switch).
@@ -420,6 +115,46 @@ bool straight_phases(size_t, size_t)
 {
     const char *v = std::getenv("QTM_JIT_PHASE_LOOP");
     return !(v && *v == '1');
+}
+
+// Repeated phase programs emitted once as a loop (default) or every phase
+// straight-line (QTM_JIT_REPEAT_LOOPS=0, a tuning switch).
+bool repeat_loops()
+{
+    const char *v = std::getenv("QTM_JIT_REPEAT_LOOPS");
+    return !(v && *v == '0');
+}
+
+// The longest periodic stretch of a pass's phase table (pairs of program
+// index, first run slot): phases [start, start + period * reps) where phase
+// start + r * period + i runs the program of phase start + i with its slots
+// shifted by r * stride.  A layered circuit scheduled with one run per qubit
+// per phase (PHASES_ROUND_ROBIN) repeats a few phase programs layer after
+// layer; emitted as a loop they are fetched once per CTA instead of once per
+// layer.  reps < 2: no such stretch.
+struct Repeat {
+    int start = 0, period = 0, reps = 0, stride = 0;
+};
+
+Repeat find_repeat(const std::vector<int> &table, int nph)
+{
+    Repeat best;
+    for (int p = 1; p <= 8 && 2 * p <= nph; ++p)
+        for (int st = 0; st + 2 * p <= nph; ++st) {
+            const int stride = table[2 * (st + p) + 1] - table[2 * st + 1];
+            int r = 1;
+            while (st + (r + 1) * p <= nph) {
+                bool ok = true;
+                for (int i = 0; i < p && ok; ++i) {
+                    const int a = st + i, b = st + r * p + i;
+                    ok = table[2 * b] == table[2 * a] && table[2 * b + 1] - table[2 * a + 1] == r * stride;
+                }
+                if (!ok) break;
+                ++r;
+            }
+            if (r >= 2 && p * r > best.period * best.reps) best = {st, p, r, stride};
+        }
+    return best;
 }
 
 // Phase transitions inside one warp.  A thread of a phase with register
@@ -447,13 +182,6 @@ bool warp_local_barriers()
 {
     const char *v = std::getenv("QTM_JIT_WARP_BARRIERS");
     return !(v && *v == '0');
-}
-
-// threaded lane kernels (QTM_JIT_THREADED=1, a tuning switch)
-bool lanes_threaded()
-{
-    const char *v = std::getenv("QTM_JIT_THREADED");
-    return v && *v == '1';
 }
 
 // Body of one phase with its run slots written relative to the phase's first
@@ -674,122 +402,31 @@ void cpx_op(std::ostringstream &o, const Plan &P, const PassDesc &pd, int k, int
     }
 }
 
-std::string phase_body(const Plan &P, const PassDesc &pd, const DevPhase &phs, bool lam_valid, JitMode mode, int sb,
+std::string phase_body(const Plan &P, const PassDesc &pd, const DevPhase &phs, bool lam_valid, int sb,
                        bool fill = false)
 {
     const bool rev = pd.reverse != 0;
-    const bool pairs = mode == JIT_PAIRS;
-    const int nslots = pd.slot_end - pd.slot_begin;
     const int lo = phs.lo;
     std::ostringstream o;
     auto slot = [&](int s) { return "(sb + " + std::to_string(s - sb) + ")"; };
     o << "        constexpr int LO = " << lo << ";\n";
     o << "        const uint32_t xt = ((uint32_t)tid & ((1u << LO) - 1u)) | (((uint32_t)tid >> LO) << (LO + 4));\n";
-    if (mode == JIT_CPX) {
-        if (fill) {   // phi from the closed form, lam (if any) from shared memory
-            if (lam_valid) o << "        regs_load_cpx_lam<LO>(q, S, xt);\n";
-            gen_fill_cpx(o, P, pd, lo);
-        } else {
-            o << "        regs_load_cpx<LO, " << (lam_valid ? "true" : "false") << ">(p, q, S, xt);\n";
-        }
-        for (int k = phs.op_begin; k < phs.op_end; ++k) cpx_op(o, P, pd, k, lo, slot(P.ops[k].slot));
-        o << "        regs_store_cpx<LO, " << (rev ? "true" : "false") << ">(p, q, S, xt);\n";
-        return o.str();
+    if (fill) {   // phi from the closed form, lam (if any) from shared memory
+        if (lam_valid) o << "        regs_load_cpx_lam<LO>(q, S, xt);\n";
+        gen_fill_cpx(o, P, pd, lo);
+    } else {
+        o << "        regs_load_cpx<LO, " << (lam_valid ? "true" : "false") << ">(p, q, S, xt);\n";
     }
-    if (mode == JIT_LANES) {
-        const int sl = choose_lane_bit(P, phs);
-        o << "        constexpr int SB = " << sl << ";\n";
-        o << "        regs_load_lanes<LO, SB, " << (lam_valid ? "true" : "false") << ", " << lanes_v64() << ">(p, q, S, xt);\n";
-        for (int k = phs.op_begin; k < phs.op_end; ++k) lanes_op(o, P, pd, k, lo, sl, slot(P.ops[k].slot));
-        o << "        regs_store_lanes<LO, SB, " << (rev ? "true" : "false") << ", " << lanes_v64() << ">(p, q, S, xt);\n";
-        return o.str();
-    }
-    if (pairs) o << "        regs_load_x2<LO, " << (lam_valid ? "true" : "false") << ">(p, q, S, xt);\n";
-    else o << "        regs_load<R, LO, " << (lam_valid ? "true" : "false") << ">(p, q, S, xt);\n";
-    for (int k = phs.op_begin; k < phs.op_end; ++k) {
-        const DevOp &op = P.ops[k];
-        // register operands must lie in this phase's 4-bit group; a schedule
-        // that breaks this fails to compile instead of running
-        const bool reg_a = has_reg_bit(op.a, lo);
-        const bool reg_b = has_reg_bit(op.b, lo);
-        if (((op.type == OP_U2 || op.type == OP_GRAD) && !reg_a) || (op.type == OP_CNOT && !reg_b) ||
-            ((op.type == OP_U2 || op.type == OP_GRAD) && (op.slot < 0 || op.slot >= nslots)) ||
-            (op.type == OP_DIAG && (op.a < 0 || op.a + op.b > (int)P.diag_pairs.size()))) {
-            o << "#error \"op " << k << " has an operand outside its phase\"\n";
-            continue;
-        }
-        const int rb = op.a - lo;
-        switch (op.type) {
-        case OP_U2:
-            if (pairs) o << "        u2x2<" << rb << ">(p, S.mats + 12 * " << slot(op.slot) << ");\n";
-            else o << "        u2<" << rb << ">(p, S.mats + 4 * " << slot(op.slot) << ");\n";
-            break;
-        case OP_GRAD:
-            if (pairs) {
-                o << "        { f2 vx, vy, vz; grad_x2<" << rb << ">(p, q, vx, vy, vz); grad_store_x2(S, " << nslots
-                  << ", " << slot(op.slot) << ", warp, lane, vx, vy, vz);";
-                if (!(op.flags & OPF_SKIP_APPLY))
-                    o << " u2x2<" << rb << ">(p, S.mats + 12 * " << slot(op.slot) << "); u2x2<" << rb
-                      << ">(q, S.mats + 12 * " << slot(op.slot) << ");";
-                o << " }\n";
-            } else {
-                o << "        { R vx = 0, vy = 0, vz = 0; grad_acc<" << rb << ">(p, q, vx, vy, vz);"
-                  << " const R v = warp_sum3(vx, vy, vz, lane);"
-                  << " if ((lane & 7) == 0 && lane < 24) S.redG[warp * " << 3 * nslots << " + 3 * " << slot(op.slot)
-                  << " + (lane >> 3)] = v;";
-                if (!(op.flags & OPF_SKIP_APPLY))
-                    o << " u2<" << rb << ">(p, S.mats + 4 * " << slot(op.slot) << "); u2<" << rb << ">(q, S.mats + 4 * "
-                      << slot(op.slot) << ");";
-                o << " }\n";
-            }
-            break;
-        case OP_DIAG:
-            o << "        { " << diag_mask(P, op, lo) << (pairs ? " flip_x2<" : " flip_mask<R, ")
-              << (rev ? "true" : "false") << ">(p, q, m); }\n";
-            break;
-        case OP_CNOT: {
-            const int rt = op.b - lo;
-            if (has_reg_bit(op.a, lo)) {
-                const char *f = pairs ? "cnot_static_x2<" : "cnot_static<";
-                o << "        " << f << (op.a - lo) << ", " << rt << ">(p);";
-                if (rev) o << " " << f << (op.a - lo) << ", " << rt << ">(q);";
-                o << "\n";
-            } else if (pairs) {
-                o << "        { const int c = (int)(" << operand_bit(op.a) << " & 1u); cnot_x2<" << rt << ">(p, c);";
-                if (rev) o << " cnot_x2<" << rt << ">(q, c);";
-                o << " }\n";
-            } else {
-                o << "        { const int c = (int)(" << operand_bit(op.a) << " & 1u); cnot_regs<" << rt
-                  << ">(p, -1, c);";
-                if (rev) o << " cnot_regs<" << rt << ">(q, -1, c);";
-                o << " }\n";
-            }
-            break;
-        }
-        case OP_EXPVAL:
-            if (pairs) gen_expval_x2(o, P, pd, lo);
-            else o << "        op_expval<R>(p, S, j, xt, LO, warp, lane, 32, 0xffffffffu);\n";
-            break;
-        case OP_COSTATE:
-            if (pairs) gen_costate_x2(o, P, pd, lo);
-            else o << "        op_costate<R>(p, q, S, j, xt, LO, " << ((op.flags & OPF_ACCUMULATE) ? "true" : "false")
-                   << ");\n";
-            break;
-        default:
-            break;
-        }
-    }
-    if (pairs) o << "        regs_store_x2<LO, " << (rev ? "true" : "false") << ">(p, q, S, xt);\n";
-    else o << "        regs_store<R, LO, " << (rev ? "true" : "false") << ">(p, q, S, xt);\n";
+    for (int k = phs.op_begin; k < phs.op_end; ++k) cpx_op(o, P, pd, k, lo, slot(P.ops[k].slot));
+    o << "        regs_store_cpx<LO, " << (rev ? "true" : "false") << ">(p, q, S, xt);\n";
     return o.str();
 }
 
 }  // namespace
 
-std::string jit_source(const Plan &P, const PassDesc &pd, int min_blocks, JitMode mode)
+std::string jit_source(const Plan &P, const PassDesc &pd, int min_blocks)
 {
     const bool rev = pd.reverse != 0;
-    const bool pairs = mode == JIT_PAIRS;
     // distinct phase bodies (templates) and, per phase, (template, first slot)
     std::vector<std::string> tpl;
     std::vector<int> table;
@@ -801,8 +438,8 @@ std::string jit_source(const Plan &P, const PassDesc &pd, int min_blocks, JitMod
             if ((P.ops[k].type == OP_U2 || P.ops[k].type == OP_GRAD) && (sb < 0 || P.ops[k].slot < sb))
                 sb = P.ops[k].slot;
         if (sb < 0) sb = 0;
-        const bool fill = mode == JIT_CPX && cpx_fill(pd) && ph == pd.phase_begin;
-        const std::string body = phase_body(P, pd, phs, lam_valid, mode, sb, fill);
+        const bool fill = cpx_fill(pd) && ph == pd.phase_begin;
+        const std::string body = phase_body(P, pd, phs, lam_valid, sb, fill);
         size_t t = 0;
         while (t < tpl.size() && tpl[t] != body) ++t;
         if (t == tpl.size()) tpl.push_back(body);
@@ -819,62 +456,53 @@ std::string jit_source(const Plan &P, const PassDesc &pd, int min_blocks, JitMod
     if (table.empty()) o << "0, 0";
     o << "};\n";
     const int nslots = pd.slot_end - pd.slot_begin;
-    if (mode == JIT_LANES && lanes_threaded()) {
-        int nr = 0, np = 0;
-        const std::string tb = lanes_threaded_body(P, pd, nr, np);
-        const size_t cut = tb.find('\x01');
-        o << "// threaded: " << nr << " routines, " << np << " program steps\n" << tb.substr(0, cut);
-        o << "template <typename R>\n__device__ __forceinline__ void gen_phases(const TileJob &j, const TileSmem<R> &S, "
-             "bool)\n{\n    A2 p[kLanePairs];\n    A2 q[kLanePairs];\n"
-          << "    f2 *LT = reinterpret_cast<f2 *>(reinterpret_cast<unsigned char *>(S.phi) + " << lane_table_offset(P, pd)
-          << ");\n    stage_lane_table(S.mats, LT, " << nslots << ");\n    __syncthreads();\n";
-        o << "    const int tid = threadIdx.x;\n    const int warp = tid >> 5, lane = tid & 31;\n";
-        o << "    const uint32_t base = j.base;\n    (void)base; (void)lane; (void)warp; (void)j;\n";
-        o << tb.substr(cut + 1);
-        o << "}\n}  // namespace\n}  // namespace qtm\n\n";
-        o << "extern \"C\" __global__ void __launch_bounds__(256, " << min_blocks << ") qtm_gen_pass("
-          << "const __grid_constant__ qtm::PassArgs a, const __grid_constant__ CUtensorMap tm_phi, "
-          << "const __grid_constant__ CUtensorMap tm_lam)\n{\n";
-        o << "    qtm::pass_body<float, " << (rev ? "true" : "false") << ">(a, &tm_phi, &tm_lam, "
-          << "[](const qtm::TileJob &j, const qtm::TileSmem<float> &S, bool lv) { qtm::gen_phases<float>(j, S, lv); "
-             "});\n}\n";
-        return o.str();
-    }
-    if (pairs)
-        o << "__device__ __forceinline__ void gen_phases(const TileJobX2 &j, const TileSmemX2 &S)\n{\n"
-          << "    using R = float;\n    A2 p[kRegs];\n    A2 q[kRegs];\n";
-    else if (mode == JIT_CPX)
-        o << "template <typename R>\n__device__ __forceinline__ void gen_phases(const TileJob &j, const TileSmem<R> &S, "
-             "bool)\n{\n    f2 p[kRegs];\n    f2 q[kRegs];\n"
-          << "    // complex-pair matrix table after the tile program's shared memory\n"
-          << "    f2 *CT = reinterpret_cast<f2 *>(reinterpret_cast<unsigned char *>(S.phi) + " << lane_table_offset(P, pd)
-          << ");\n    stage_cpx_table(S.mats, CT, " << nslots << ");\n"
-          << (cpx_fill(pd) ? "    f2 *TT = CT + " + std::to_string(kCpxSlotPairsHost * std::max(1, nslots)) +
-                                 ";   // product-state tables, broadcast form\n    stage_cpx_tabs(S.tabs, TT, " +
-                                 std::to_string(16 * ((P.state_qubits + 3) >> 2)) + ");\n"
-                           : std::string())
-          << "    __syncthreads();\n";
-    else if (mode == JIT_LANES)
-        o << "template <typename R>\n__device__ __forceinline__ void gen_phases(const TileJob &j, const TileSmem<R> &S, "
-             "bool)\n{\n    A2 p[kLanePairs];\n    A2 q[kLanePairs];\n"
-          << "    // lane-pair matrix table after the tile program's shared memory\n"
-          << "    f2 *LT = reinterpret_cast<f2 *>(reinterpret_cast<unsigned char *>(S.phi) + " << lane_table_offset(P, pd)
-          << ");\n    stage_lane_table(S.mats, LT, " << nslots << ");\n    __syncthreads();\n";
-    else
-        o << "template <typename R>\n__device__ __forceinline__ void gen_phases(const TileJob &j, const TileSmem<R> &S, "
-             "bool)\n{\n    Cx<R> p[kRegs];\n    Cx<R> q[kRegs];\n";
+    o << "template <typename R>\n__device__ __forceinline__ void gen_phases(const TileJob &j, const TileSmem<R> &S, "
+         "bool)\n{\n    f2 p[kRegs];\n    f2 q[kRegs];\n"
+      << "    // complex-pair matrix table after the tile program's shared memory\n"
+      << "    f2 *CT = reinterpret_cast<f2 *>(reinterpret_cast<unsigned char *>(S.phi) + " << cpx_table_offset(P, pd)
+      << ");\n    stage_cpx_table(S.mats, CT, " << nslots << ");\n"
+      << (cpx_fill(pd) ? "    f2 *TT = CT + " + std::to_string(kCpxSlotPairsHost * std::max(1, nslots)) +
+                             ";   // product-state tables, broadcast form\n    stage_cpx_tabs(S.tabs, TT, " +
+                             std::to_string(16 * ((P.state_qubits + 3) >> 2)) + ");\n"
+                       : std::string())
+      << "    __syncthreads();\n";
     o << "    const int tid = threadIdx.x;\n    const int warp = tid >> 5, lane = tid & 31;\n";
     o << "    const uint32_t base = j.base;\n    (void)base; (void)lane; (void)warp; (void)j;\n";
     if (straight_phases(tpl.size(), (size_t)nph)) {
-        // every phase its own block, in order (slots as constants through sb);
+        // every phase its own block, in order (slots as constants through sb),
+        // except a periodic stretch, which becomes a loop over its first
+        // period with the slots shifted by the stride each time round;
         // complex-pair kernels end a phase with a warp barrier where the next
         // phase's warps hold the same amplitudes (see warp_local_transition)
+        auto lo_of = [&](int ph) { return P.phases[pd.phase_begin + ph].lo; };
+        auto local = [&](int a, int b) {
+            return b < nph && warp_local_barriers() && warp_local_transition(pd.K, lo_of(a), lo_of(b));
+        };
+        auto barrier = [&](bool warp_only) {
+            return warp_only ? "        __syncwarp();\n" : "        __syncthreads();\n";
+        };
+        const Repeat rp = repeat_loops() ? find_repeat(table, nph) : Repeat{};
+        const int loop_end = rp.reps >= 2 ? rp.start + rp.period * rp.reps : 0;
         for (int ph = 0; ph < nph; ++ph) {
-            const bool local = mode == JIT_CPX && ph + 1 < nph && warp_local_barriers() &&
-                               warp_local_transition(pd.K, P.phases[pd.phase_begin + ph].lo,
-                                                     P.phases[pd.phase_begin + ph + 1].lo);
+            if (rp.reps >= 2 && ph == rp.start) {
+                o << "    // phases " << rp.start << " .. " << loop_end - 1 << ": " << rp.reps << " x the next "
+                  << rp.period << " phase programs, slots + " << rp.stride << " each time\n";
+                o << "#pragma unroll 1\n    for (int it = 0; it < " << rp.reps << "; ++it) {\n";
+                for (int i = 0; i < rp.period; ++i) {
+                    const int a = rp.start + i;
+                    // the last program of the period hands over to the period's first
+                    // (next time round) or to the phase after the loop
+                    const bool wl = i + 1 < rp.period ? local(a, a + 1)
+                                                      : local(a, rp.start) && loop_end < nph && local(a, loop_end);
+                    o << "    {\n        const int sb = " << table[2 * a + 1] << " + it * " << rp.stride
+                      << ";\n        (void)sb;\n" << tpl[table[2 * a]] << barrier(wl) << "    }\n";
+                }
+                o << "    }\n";
+                ph = loop_end - 1;
+                continue;
+            }
             o << "    {\n        const int sb = " << table[2 * ph + 1] << ";\n        (void)sb;\n"
-              << tpl[table[2 * ph]] << (local ? "        __syncwarp();\n    }\n" : "        __syncthreads();\n    }\n");
+              << tpl[table[2 * ph]] << barrier(local(ph, ph + 1)) << "    }\n";
         }
     } else {
         o << "#pragma unroll 1\n    for (int ph = 0; ph < " << nph << "; ++ph) {\n";
@@ -890,36 +518,19 @@ std::string jit_source(const Plan &P, const PassDesc &pd, int min_blocks, JitMod
     o << "extern \"C\" __global__ void __launch_bounds__(256, " << min_blocks << ") qtm_gen_pass("
       << "const __grid_constant__ qtm::PassArgs a, const __grid_constant__ CUtensorMap tm_phi, "
       << "const __grid_constant__ CUtensorMap tm_lam)\n{\n";
-    if (pairs)
-        o << "    qtm::pass_body_x2<" << (rev ? "true" : "false") << ">(a, &tm_phi, &tm_lam, "
-          << "[](const qtm::TileJobX2 &j, const qtm::TileSmemX2 &S, bool) { qtm::gen_phases(j, S); });\n}\n";
-    else
-        o << "    qtm::pass_body<float, " << (rev ? "true" : "false")
-          << (mode == JIT_CPX && cpx_fill(pd) ? ", false" : "") << ">(a, &tm_phi, &tm_lam, "
-          << "[](const qtm::TileJob &j, const qtm::TileSmem<float> &S, bool lv) { qtm::gen_phases<float>(j, S, lv); "
-             "});\n}\n";
+    o << "    qtm::pass_body<float, " << (rev ? "true" : "false") << (cpx_fill(pd) ? ", false" : "")
+      << ">(a, &tm_phi, &tm_lam, "
+      << "[](const qtm::TileJob &j, const qtm::TileSmem<float> &S, bool lv) { qtm::gen_phases<float>(j, S, lv); "
+         "});\n}\n";
     return o.str();
-}
-
-size_t jit_smem_bytes_lanes(const Plan &P, const PassDesc &pd)
-{
-    return lane_table_offset(P, pd) + 1024 + (size_t)8 * kLaneSlotPairsHost * std::max(1, pd.slot_end - pd.slot_begin);
 }
 
 size_t jit_smem_bytes_cpx(const Plan &P, const PassDesc &pd)
 {
-    return lane_table_offset(P, pd) + 1024 + (size_t)8 * kCpxSlotPairsHost * std::max(1, pd.slot_end - pd.slot_begin) +
+    return cpx_table_offset(P, pd) + 1024 + (size_t)8 * kCpxSlotPairsHost * std::max(1, pd.slot_end - pd.slot_begin) +
            (cpx_fill(pd) ? (size_t)256 * ((P.state_qubits + 3) >> 2) : 0);
 }
 
-size_t jit_smem_bytes_x2(const Plan &P, const PassDesc &pd)
-{
-    const int nwarps = (1 << (pd.K - 4)) >> 5;
-    const LayoutX2 L = make_layout_x2(pd.K, pd.reverse != 0, pd.slot_end - pd.slot_begin, (int)P.terms.size(),
-                                      P.n_obs, P.state_qubits, pd.phi_src == SRC_ANALYTIC ? pd.analytic_ents : 0,
-                                      nwarps, (int)sizeof(Ent));
-    return (size_t)L.total + 1024;
-}
 
 // ---- NVRTC and the driver API ---------------------------------------------------
 
@@ -1095,8 +706,7 @@ cudaError_t jit_launch(const JitKernel &k, const PassArgs &a, const CUtensorMap 
     PassArgs args = a;
     CUtensorMap t0 = tm_phi, t1 = tm_lam;
     void *params[] = {&args, &t0, &t1};
-    const unsigned units = k.pairs ? (unsigned)(a.B + 1) / 2u : (unsigned)a.B;
-    const unsigned grid = units * (unsigned)a.tiles, block = 1u << (a.K - 4);
+    const unsigned grid = (unsigned)a.B * (unsigned)a.tiles, block = 1u << (a.K - 4);
     CUresult r = drv().launch(static_cast<CUfunction>(k.fn), grid, 1, 1, block, 1, 1, (unsigned)a.smem_bytes,
                               reinterpret_cast<CUstream>(s), params, nullptr);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorLaunchFailure;

@@ -17,7 +17,10 @@
 //      control of a CNOT may lie outside S (they are constant per tile).
 //   4. Phases.  Inside a pass each thread keeps 16 amplitudes in registers
 //      (4 tile bits); a phase is a greedy maximal set of ready gates local to
-//      one 4-bit register group.
+//      one 4-bit register group.  Two rules pick the group: the group whose
+//      set holds the most gates (PHASES_GREEDY), or the groups in turn with
+//      at most one run per qubit in a phase (PHASES_ROUND_ROBIN), which gives
+//      a layered circuit the same few phase programs layer after layer.
 // The reverse (adjoint) schedule runs the same greedy on the reversed gate
 // DAG, then on the folded prefix, whose state is again analytic.
 #include "plan.h"
@@ -100,12 +103,14 @@ double node_weight(const Node &nd)
 
 // Closure of ready nodes executable under (S, lo) among the nodes with
 // member[i] true and done[i] false.  Returns them in execution order.
+// one_run_per_qubit: a qubit's second run waits for the next phase.
 std::vector<int> closure(const std::vector<Node> &nodes, const std::vector<Run> &runs,
                          const std::vector<char> &member, const std::vector<char> &done,
-                         const TileSet &S, int lo, double *weight)
+                         const TileSet &S, int lo, double *weight, bool one_run_per_qubit = false)
 {
     const int N = (int)nodes.size();
     std::vector<char> d(done);
+    std::vector<char> ran(one_run_per_qubit ? kMaxQubits : 0, 0);
     std::vector<int> order;
     double w = 0.0;
     // simple fixed-point sweep in index order (nodes are topologically sorted)
@@ -119,6 +124,11 @@ std::vector<int> closure(const std::vector<Node> &nodes, const std::vector<Run> 
                 if (!d[p]) { ready = false; break; }
             if (!ready) continue;
             if (!executable(nodes[i], runs, S, lo)) continue;
+            if (one_run_per_qubit && nodes[i].type == 0) {
+                const int q = runs[nodes[i].run].q;
+                if (ran[q]) continue;
+                ran[q] = 1;
+            }
             d[i] = 1;
             order.push_back(i);
             w += node_weight(nodes[i]);
@@ -165,20 +175,31 @@ struct Builder {
         };
 
         const int ngroups = (K + kRegBits - 1) / kRegBits;
+        const bool rr = P.phase_mode == PHASES_ROUND_ROBIN;
         int remaining = (int)pass_nodes.size();
-        int last_lo = -1;
+        int last_lo = -1, last_g = -1;
         while (remaining > 0) {
-            int best_lo = -1;
+            int best_lo = -1, best_g = -1;
             double best_w = -1.0;
             std::vector<int> best;
-            for (int g = 0; g < ngroups; ++g) {
-                int lo = std::min(g * kRegBits, K - kRegBits);
-                double w;
-                std::vector<int> c = closure(nodes, P.runs, member, done, S, lo, &w);
-                // prefer staying in the current group on ties (no smem round trip saved,
-                // but keeps phases fewer)
-                if (w > best_w + 1e-9 || (std::fabs(w - best_w) <= 1e-9 && lo == last_lo)) {
-                    best_w = w; best_lo = lo; best = std::move(c);
+            if (rr) {
+                // the groups in turn, skipping a group with nothing ready
+                for (int k = 1; k <= ngroups && best.empty(); ++k) {
+                    const int g = (last_g + k) % ngroups;
+                    const int lo = std::min(g * kRegBits, K - kRegBits);
+                    std::vector<int> c = closure(nodes, P.runs, member, done, S, lo, nullptr, true);
+                    if (!c.empty()) { best_g = g; best_lo = lo; best = std::move(c); }
+                }
+            } else {
+                for (int g = 0; g < ngroups; ++g) {
+                    int lo = std::min(g * kRegBits, K - kRegBits);
+                    double w;
+                    std::vector<int> c = closure(nodes, P.runs, member, done, S, lo, &w);
+                    // prefer staying in the current group on ties (no smem round trip saved,
+                    // but keeps phases fewer)
+                    if (w > best_w + 1e-9 || (std::fabs(w - best_w) <= 1e-9 && lo == last_lo)) {
+                        best_w = w; best_lo = lo; best_g = g; best = std::move(c);
+                    }
                 }
             }
             if (best.empty()) break;   // cannot happen for a valid DAG
@@ -213,6 +234,7 @@ struct Builder {
             ph.op_end = (int)P.ops.size();
             P.phases.push_back(ph);
             last_lo = best_lo;
+            last_g = best_g;
         }
         if (P.phases.size() == (size_t)pd.phase_begin) {   // empty pass: one empty phase
             DevPhase ph{};
@@ -334,9 +356,11 @@ bool closed_form(const std::vector<Ent> &ents, int e, int n, std::vector<MaskTer
 
 }  // namespace
 
-qtm_status make_plan(int n, const qtm_gate *gates, int n_gates, const qtm_zterm *terms,
-                     int n_terms, int n_obs, int n_weights, int n_inputs, int dtype, int path,
-                     Plan &P, std::string &err, int max_run)
+namespace {
+
+qtm_status make_plan_mode(int n, const qtm_gate *gates, int n_gates, const qtm_zterm *terms,
+                          int n_terms, int n_obs, int n_weights, int n_inputs, int dtype, int path,
+                          Plan &P, std::string &err, int max_run, int phase_mode)
 {
     if (max_run < 1) max_run = 1;
     if (max_run > kMaxRunLen) max_run = kMaxRunLen;
@@ -388,6 +412,7 @@ qtm_status make_plan(int n, const qtm_gate *gates, int n_gates, const qtm_zterm 
     }
 
     P = Plan();
+    P.phase_mode = phase_mode == PHASES_ROUND_ROBIN ? PHASES_ROUND_ROBIN : PHASES_GREEDY;
     P.n = n; P.dtype = dtype; P.n_obs = n_obs; P.n_weights = n_weights; P.n_inputs = n_inputs;
     P.path = (path == QTM_PATH_NAIVE) ? QTM_PATH_NAIVE : QTM_PATH_FUSED;
     P.n_user_gates = n_gates;
@@ -722,6 +747,8 @@ qtm_status make_plan(int n, const qtm_gate *gates, int n_gates, const qtm_zterm 
     return QTM_OK;
 }
 
+}  // namespace
+
 void attach_pauli_terms(Plan &P, const std::vector<PauliTerm> &terms)
 {
     P.pterms = terms;
@@ -731,6 +758,91 @@ void attach_pauli_terms(Plan &P, const std::vector<PauliTerm> &terms)
     pd.lam_src = SRC_LOAD;
     for (int o = P.phases[pd.phase_begin].op_begin; o < P.phases[pd.phase_begin].op_end; ++o)
         if (P.ops[o].type == OP_COSTATE) P.ops[o].flags |= OPF_ACCUMULATE;
+}
+
+namespace {
+
+// Ops of a pass's phase as a comparable key: register group, then per op its
+// type, operands, flags, run slot relative to the phase's first slot and,
+// for DIAG ops, the CZ pairs.
+std::vector<int64_t> phase_key(const Plan &P, const DevPhase &ph)
+{
+    int sb = -1;
+    for (int o = ph.op_begin; o < ph.op_end; ++o)
+        if (P.ops[o].slot >= 0 && (sb < 0 || P.ops[o].slot < sb)) sb = P.ops[o].slot;
+    std::vector<int64_t> k{ph.lo};
+    for (int o = ph.op_begin; o < ph.op_end; ++o) {
+        const DevOp &op = P.ops[o];
+        if (op.type == OP_DIAG) {   // a and b locate the pairs in the shared list: key the pairs
+            k.insert(k.end(), {op.type, op.b, op.flags});
+            for (int d = op.a; d < op.a + op.b; ++d) k.insert(k.end(), {P.diag_pairs[d].a, P.diag_pairs[d].b});
+        } else {
+            k.insert(k.end(), {op.type, op.a, op.b, op.flags, op.slot >= 0 ? op.slot - sb : -1});
+        }
+    }
+    return k;
+}
+
+}  // namespace
+
+double periodic_fraction(const Plan &P)
+{
+    double in_loops = 0.0, total = 0.0;
+    for (const auto *v : {&P.fwd, &P.rev})
+        for (const PassDesc &pd : *v) {
+            const int nph = pd.phase_end - pd.phase_begin;
+            std::vector<std::vector<int64_t>> key(nph);
+            std::vector<int> sb(nph, 0), ops(nph, 0);
+            for (int i = 0; i < nph; ++i) {
+                const DevPhase &ph = P.phases[pd.phase_begin + i];
+                key[i] = phase_key(P, ph);
+                ops[i] = ph.op_end - ph.op_begin;
+                int m = -1;
+                for (int o = ph.op_begin; o < ph.op_end; ++o)
+                    if (P.ops[o].slot >= 0 && (m < 0 || P.ops[o].slot < m)) m = P.ops[o].slot;
+                sb[i] = m < 0 ? 0 : m;
+                total += ops[i];
+            }
+            // the longest stretch [st, st + p * r) of phases repeating with a fixed slot stride
+            int best = 0, best_st = 0;
+            for (int p = 1; p <= 8 && 2 * p <= nph; ++p)
+                for (int st = 0; st + 2 * p <= nph; ++st) {
+                    const int stride = sb[st + p] - sb[st];
+                    int r = 1;
+                    while (st + (r + 1) * p <= nph) {
+                        bool ok = true;
+                        for (int i = 0; i < p && ok; ++i) {
+                            const int a = st + i, b = st + r * p + i;
+                            ok = key[b] == key[a] && sb[b] - sb[a] == r * stride;
+                        }
+                        if (!ok) break;
+                        ++r;
+                    }
+                    if (r >= 2 && p * r > best) { best = p * r; best_st = st; }
+                }
+            for (int i = best_st; i < best_st + best; ++i) in_loops += ops[i];
+        }
+    return total > 0.0 ? in_loops / total : 0.0;
+}
+
+qtm_status make_plan(int n, const qtm_gate *gates, int n_gates, const qtm_zterm *terms,
+                     int n_terms, int n_obs, int n_weights, int n_inputs, int dtype, int path,
+                     Plan &P, std::string &err, int max_run, int phase_mode)
+{
+    if (phase_mode != PHASES_AUTO)
+        return make_plan_mode(n, gates, n_gates, terms, n_terms, n_obs, n_weights, n_inputs, dtype, path, P, err,
+                              max_run, phase_mode);
+    // round robin where it makes most of the work periodic, else greedy; the
+    // interpreter kernels (complex128 plans) run a few percent slower on the
+    // extra phases, so those keep greedy
+    if (dtype == QTM_C128)
+        return make_plan_mode(n, gates, n_gates, terms, n_terms, n_obs, n_weights, n_inputs, dtype, path, P, err,
+                              max_run, PHASES_GREEDY);
+    qtm_status st = make_plan_mode(n, gates, n_gates, terms, n_terms, n_obs, n_weights, n_inputs, dtype, path, P,
+                                   err, max_run, PHASES_ROUND_ROBIN);
+    if (st != QTM_OK || P.path != QTM_PATH_FUSED || periodic_fraction(P) >= 0.5) return st;
+    return make_plan_mode(n, gates, n_gates, terms, n_terms, n_obs, n_weights, n_inputs, dtype, path, P, err,
+                          max_run, PHASES_GREEDY);
 }
 
 void plan_costs(const Plan &p, double &fwd_bytes, double &adj_bytes, double &fwd_flops,

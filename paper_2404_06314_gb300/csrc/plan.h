@@ -11,9 +11,16 @@
 
 namespace qtm {
 
+// How a pass's ops are grouped into register phases (see plan.cpp);
+// PHASES_AUTO plans round robin and keeps it when at least half of the ops
+// lie in periodic stretches of phases (periodic_fraction), else greedy;
+// complex128 plans (interpreter kernels only) always get greedy.
+enum { PHASES_GREEDY = 0, PHASES_ROUND_ROBIN = 1, PHASES_AUTO = 2 };
+
 struct Plan {
     // circuit
     int n = 0, dtype = QTM_C64, path = QTM_PATH_FUSED;
+    int phase_mode = PHASES_GREEDY;
     int n_obs = 0, n_weights = 0, n_inputs = 0;
     std::vector<qtm_gate> gates;        // lowered to RX/RY/RZ/CZ/CNOT (H and RZZ expanded)
     int n_user_gates = 0;               // gates as given to qtm_build (Jacobian columns)
@@ -53,10 +60,17 @@ struct Plan {
 };
 
 // Build the plan (host only).  Returns QTM_OK or an error with `err` set.
-// max_run: most rotations fused into one run (the fusion width).
+// max_run: most rotations fused into one run (the fusion width);
+// phase_mode: PHASES_GREEDY, PHASES_ROUND_ROBIN or PHASES_AUTO.
 qtm_status make_plan(int n, const qtm_gate *gates, int n_gates, const qtm_zterm *terms,
                      int n_terms, int n_obs, int n_weights, int n_inputs, int dtype, int path,
-                     Plan &out, std::string &err, int max_run = kMaxRunLen);
+                     Plan &out, std::string &err, int max_run = kMaxRunLen,
+                     int phase_mode = PHASES_GREEDY);
+
+// Fraction of a plan's phase ops that lie in periodic stretches of its
+// passes' phases (the same phase program repeated with shifted run slots),
+// which the specialised kernels emit as loops.
+double periodic_fraction(const Plan &P);
 
 // Give a fused plan observables with X/Y factors: the last forward pass keeps
 // the final state in memory, where the X/Y terms' expectation values and

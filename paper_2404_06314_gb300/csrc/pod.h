@@ -138,38 +138,6 @@ struct PauliTerm {
 #define QTM_POD_HD inline
 #endif
 
-// Shared-memory layout of a paired-sample pass CTA (two samples per CTA, one
-// per half of an f32x2 register pair; offsets from a 1024-byte aligned base).
-// Elements of phi / lam are 16 bytes (re_b0, re_b1, im_b0, im_b1); a run
-// matrix entry or a product-state table entry is three pairs (re, im, -im).
-struct LayoutX2 {
-    int phi, lam, mats, tabs, tcoef, tmask, tobs, ents, redE, redG, bar, total;
-};
-
-QTM_POD_HD int align_up_x2(int v, int a) { return (v + a - 1) / a * a; }
-
-QTM_POD_HD LayoutX2 make_layout_x2(int K, bool rev, int nslots, int n_terms, int M, int sq, int n_ents,
-                                   int nwarps, int ent_bytes)
-{
-    LayoutX2 L{};
-    const int tile = 16 << K;
-    int o = 0;
-    L.phi = o; o += tile;
-    L.lam = align_up_x2(o, 1024); o = L.lam + (rev ? tile : 0);
-    o = align_up_x2(o, 16);
-    L.mats = o; o = align_up_x2(o + 4 * 24 * (nslots > 0 ? nslots : 1), 16);
-    L.tabs = o; o = align_up_x2(o + 16 * 24 * ((sq + 3) / 4), 16);
-    L.tcoef = o; o = align_up_x2(o + 8 * (n_terms > 0 ? n_terms : 1), 16);
-    L.tmask = o; o = align_up_x2(o + 4 * (n_terms > 0 ? n_terms : 1), 16);
-    L.tobs = o; o = align_up_x2(o + 4 * (n_terms > 0 ? n_terms : 1), 16);
-    L.ents = o; o = align_up_x2(o + ent_bytes * (n_ents > 0 ? n_ents : 1), 16);
-    L.redE = o; o = align_up_x2(o + 8 * nwarps * (M > 0 ? M : 1), 16);
-    L.redG = o; o = align_up_x2(o + 8 * nwarps * 3 * (nslots > 0 ? nslots : 1), 16);
-    L.bar = o; o += 16;
-    L.total = o;
-    return L;
-}
-
 // status word bits recorded by kernels
 constexpr unsigned kStatusTimeout = 1u;
 

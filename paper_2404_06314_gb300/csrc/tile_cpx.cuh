@@ -6,13 +6,13 @@
 // complex product is two f32x2 instructions on the pair and its lane swap:
 //     u x = (u.re, u.re) * (x.re, x.im) + (-u.im, u.im) * (x.im, x.re),
 // and Blackwell's f32x2 FMA takes the swapped operand without a register move.
-// Every register bit is then alike (no lane bit as in tile_lanes.cuh): a gate
-// on register bit RB pairs whole registers, a CNOT permutes them, a CZ sign
-// flips both lanes of a register.  The sample, the shared-memory layout and
-// the tile program (tile.cuh) are those of the one-sample kernel.
+// Every register bit is alike: a gate on register bit RB pairs whole
+// registers, a CNOT permutes them, a CZ sign flips both lanes of a register.
+// The sample, the shared-memory layout and the tile program (tile.cuh) are
+// those of the one-sample kernel.
 #pragma once
 
-#include "tile_lanes.cuh"
+#include "f32x2.cuh"
 
 namespace qtm {
 

@@ -114,6 +114,25 @@ def z_sum(n: int) -> Tuple[List[Term], int]:
     return [(1 << i, 1.0, 0) for i in range(n)], 1
 
 
+def tab1_observables(n: int, M: int) -> Tuple[List[Term], int]:
+    """M single-term Z-string observables for the observable sweep of Tab. I
+    (12 qubits, M = 1 .. 32), which names only their number.  Reading used
+    here: Z_0 .. Z_{n-1} first, then the ring pairs Z_i Z_{i+1 mod n}, then
+    Z_i Z_{i+2 mod n}, ... (each string once), observable k taking the k-th
+    string of that list."""
+    strings = [1 << i for i in range(n)]
+    d = 1
+    while len(strings) < M and d < n:
+        for i in range(n):
+            z = (1 << i) | (1 << ((i + d) % n))
+            if z not in strings:
+                strings.append(z)
+        d += 1
+    if M > len(strings):
+        raise ValueError(f"at most {len(strings)} observables at n = {n}")
+    return [(strings[k], 1.0, k) for k in range(M)], M
+
+
 def layered_ansatz(n: int, layers: int, n_inputs: int, entangler: str,
                    encode: str = "every", rotations: Sequence[str] = ("Y", "Z"),
                    terms=None, name: str = "layered") -> Circuit:

@@ -28,4 +28,5 @@ def test_reference_arm_prints_the_contract_line():
     e2e = d["e2e"]
     assert e2e["value"] == d["value"] and e2e["unit"] == d["unit"]
     assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
-    assert d["config"]["workload"] == "qnn12_l6"
+    assert d["config"]["workload"] == bench.WORKLOADS["qnn12"]["desc"]
+    assert d["config"]["per_gpu_batch"] == bench.WORKLOADS["qnn12"]["B"]

@@ -247,19 +247,14 @@ def test_pauli_direct_and_grouped_schedules_agree(n):
     assert np.max(np.abs(a[0] - Eo)) < 1e-11
 
 
-def test_pauli_plans_refuse_paired_layouts_and_noalloc():
-    """Plans with X/Y strings read the final state in its one-sample layout:
-    the two-samples-per-CTA kernels and the allocation-free forward refuse
-    them before touching a device."""
+def test_pauli_plans_refuse_noalloc():
+    """Plans with X/Y strings evaluate those strings on the final state in
+    memory: the allocation-free forward refuses them before touching a device."""
     import ctypes
     rng = np.random.default_rng(3290)
     c = P.rand_small_circuit(rng, 10, G=46, n_obs=2, extra=True, pauli=True)
     plan = capi.Plan(c, dtype="c64")
     assert plan.parts == 1
-    with pytest.raises(capi.QtmError) as ei:
-        plan.set_pairing(True)
-    assert ei.value.status == capi.QTM_EUNSUPPORTED
-    assert "one-sample" in capi.qtm_last_error(plan.handle)
     fake = ctypes.c_void_p(256)   # never dereferenced
     assert capi.qtm_forward_noalloc(plan.handle, 2, fake, fake, fake, None) == capi.QTM_EUNSUPPORTED
 
@@ -322,3 +317,41 @@ def test_prefix_entanglers_undone_out_of_order():
     c2 = P.rand_small_circuit(rng, 16, G=90, n_obs=3, extra=True)
     c2.name = "hrzz16"
     _emulate_vs_oracle(c2, 2, 7)
+
+
+def test_work_linear_in_depth_host():
+    """Fig. 2 / Sec. III: the cost of a gradient grows linearly with the
+    circuit depth.  The plan's adjoint arithmetic per sample for the
+    benchmark ansatz at 12 qubits, depth 1..11, fits a line with R^2 >= 0.98."""
+    ds = np.arange(1, 12)
+    fl = [capi.Plan(W.jerbi_ansatz(12, int(d)), dtype="c64").info["adj_flops"] for d in ds]
+    A = np.vstack([ds, np.ones_like(ds)]).T
+    coef, *_ = np.linalg.lstsq(A, fl, rcond=None)
+    resid = np.asarray(fl) - A @ coef
+    r2 = 1.0 - (resid ** 2).sum() / ((np.asarray(fl) - np.mean(fl)) ** 2).sum()
+    assert coef[0] > 0 and r2 >= 0.98, (coef, r2)
+
+
+def _phases(c):
+    return sum(line.count("{lo") for line in capi.Plan(c, dtype="c64").describe().splitlines())
+
+
+def test_automatic_phase_mode_host(monkeypatch):
+    """Layered circuits that repeat one layer get the round-robin phases
+    (one run per qubit per phase, a periodic phase program the specialised
+    kernels emit as a loop); circuits where that gives no periodic stretch
+    keep the greedy phases.  The choice never changes results (the schedule
+    emulator agrees with the oracle either way)."""
+    c12, c20 = W.workload_12q(), W.workload_20q()
+    counts = {}
+    for mode in ("greedy", "rr", None):
+        if mode is None:
+            monkeypatch.delenv("QTM_PHASES", raising=False)
+        else:
+            monkeypatch.setenv("QTM_PHASES", mode)
+        counts[mode] = (_phases(c12), _phases(c20))
+    assert counts[None][0] == counts["rr"][0] != counts["greedy"][0]
+    assert counts[None][1] == counts["greedy"][1] != counts["rr"][1]
+    for mode in ("greedy", "rr"):
+        monkeypatch.setenv("QTM_PHASES", mode)
+        _emulate_vs_oracle(W.workload_12q(), 3, 5)

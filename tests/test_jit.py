@@ -1,20 +1,17 @@
-"""Run-time specialised pass kernels (qtm_compile).
-
-Four kinds of specialised kernel: lane-paired (default; one sample per CTA,
-the thread's amplitudes paired in f32x2 registers), complex-paired (one
-sample per CTA, each complex amplitude one f32x2 pair), scalar one-sample,
-and sample-paired (two samples per CTA, one per half of an f32x2 register
-pair).
+"""Run-time specialised pass kernels (qtm_compile): one sample per CTA, each
+complex amplitude one f32x2 register pair.
 
 Host part (no GPU): the source written for every pass of the benchmark
-workloads and of random circuits compiles with NVRTC for sm_103a in both
-kinds, and complex128 / naive / small-tile plans are not specialised.
+workloads and of random circuits compiles with NVRTC for sm_103a, periodic
+phase programs are emitted as loops, and complex128 / naive / small-tile
+plans are not specialised.
 
 GPU part: a compiled plan gives the oracle's E, grad_x and per-sample grad_w
 within the complex64 bound (1e-5), the specialised kernels are the ones that
-ran (qtm_compiled_passes), and results agree with the general pass kernel's
-(odd batches included: the paired kernel's last CTA holds one sample).
+ran (qtm_compiled_passes), and results agree with the general pass kernel's.
 """
+import re
+
 import numpy as np
 import pytest
 
@@ -23,9 +20,9 @@ import oracle_pins as P
 from paper_2404_06314_gb300 import capi, workloads as W
 
 
-def _nvrtc_or_skip(plan, kind="pairs"):
+def _nvrtc_or_skip(plan):
     try:
-        plan.jit_compile_check(kind=kind)
+        plan.jit_compile_check()
     except capi.QtmError as e:
         if e.status == capi.QTM_EUNSUPPORTED:
             pytest.skip("NVRTC not available")
@@ -39,37 +36,43 @@ def _rand(n, seed):
     return c
 
 
-def _nvrtc_kind_or_skip(plan, kind):
-    try:
-        plan.jit_compile_check(kind=kind)
-    except capi.QtmError as e:
-        if e.status == capi.QTM_EUNSUPPORTED:
-            pytest.skip("NVRTC not available")
-        raise
-
-
-@pytest.mark.parametrize("kind", ["pairs", "one", "lanes", "cpx"])
-def test_generated_source_compiles_benchmarks(kind):
+def test_generated_source_compiles_benchmarks():
     for c in [W.workload_12q(), W.workload_20q(), W.workload_16q_train()]:
         plan = capi.Plan(c, dtype="c64")
         info = plan.info
         for which, count in ((0, info["fwd_passes"]), (1, info["adj_passes"])):
             for i in range(count):
-                src = plan.jit_source(which, i, kind=kind)
+                src = plan.jit_source(which, i)
                 assert "qtm_gen_pass" in src and "gen_phases" in src, (c.name, which, i)
-                assert ("pass_body_x2" in src) == (kind == "pairs")
-                assert ("regs_load_lanes" in src) == (kind == "lanes")
-                assert ("regs_load_cpx" in src) == (kind == "cpx")
+                assert "regs_load_cpx" in src
                 assert "#error" not in src
-        _nvrtc_kind_or_skip(plan, kind)
+        _nvrtc_or_skip(plan)
 
 
 @pytest.mark.parametrize("n", [9, 13])
 def test_generated_source_compiles_random(n):
-    plan = capi.Plan(_rand(n, 500 + n), dtype="c64")
-    _nvrtc_or_skip(plan, "pairs")
-    _nvrtc_kind_or_skip(plan, "lanes")
-    _nvrtc_kind_or_skip(plan, "cpx")
+    _nvrtc_or_skip(capi.Plan(_rand(n, 500 + n), dtype="c64"))
+
+
+def test_periodic_phases_become_loops():
+    """The 12-qubit workload (6 identical layers) is scheduled with one run
+    per qubit per phase; its forward and reverse passes repeat one
+    three-phase program layer after layer, which the generator emits once as
+    a loop over the layers (the straight-line program did not fit the
+    instruction caches).  Loops cover most phases, and the loop body is
+    what a straight-line program would have written for one period."""
+    plan = capi.Plan(W.workload_12q(), dtype="c64")
+    for which in (0, 1):
+        src = plan.jit_source(which, 0)
+        m = re.search(r"// (\d+) phases, (\d+) distinct phase programs", src)
+        nph, distinct = int(m.group(1)), int(m.group(2))
+        loop = re.search(r"// phases (\d+) \.\. (\d+): (\d+) x the next (\d+) phase programs, slots \+ (\d+)", src)
+        assert loop, which
+        first, last, reps, period, stride = map(int, loop.groups())
+        assert period == 3 and stride == 12 and reps >= 4
+        assert last - first + 1 == reps * period and reps * period >= nph // 2
+        assert distinct < nph
+        assert src.count("for (int it = 0;") == 1
 
 
 def test_analytic_phi_in_registers_exactly_with_a_closed_form():
@@ -90,7 +93,7 @@ def test_analytic_phi_in_registers_exactly_with_a_closed_form():
                 m = re.search(r"phi=(\d+) lam=\d+ ents=(\d+)( closed=(-?\d+))?", lines[i])
                 analytic, ents = m.group(1) == "2", int(m.group(2))
                 closed = m.group(4) is not None and int(m.group(4)) >= 0
-                src = plan.jit_source(which, i, kind="cpx")
+                src = plan.jit_source(which, i)
                 in_regs = "straight into the registers" in src
                 assert in_regs == (analytic and (closed or ents == 0)), (name, which, i)
                 if analytic:
@@ -117,7 +120,9 @@ def test_warp_barriers_only_where_warps_keep_their_amplitudes(builder):
     """The complex-pair kernels end a phase with __syncwarp instead of
     __syncthreads only where every warp loads back exactly the amplitudes it
     stored (checked here by enumerating the thread layout), and end the last
-    phase of a pass with a CTA barrier."""
+    phase of a pass with a CTA barrier.  A loop body's last phase hands over
+    to the body's first phase and, after the last time round, to the phase
+    after the loop: both transitions are checked."""
     import re
     c = getattr(W, builder)()
     plan = capi.Plan(c, dtype="c64")
@@ -126,15 +131,26 @@ def test_warp_barriers_only_where_warps_keep_their_amplitudes(builder):
     local = total = 0
     for which, n in ((0, info["fwd_passes"]), (1, info["adj_passes"])):
         for i in range(n):
-            src = plan.jit_source(which, i, "cpx")
+            src = plan.jit_source(which, i)
             los = [int(v) for v in re.findall(r"constexpr int LO = (\d+);", src)]
             ends = re.findall(r"__(syncwarp|syncthreads)\(\);\n    \}", src)
             assert len(los) == len(ends) and los, (builder, which, i)
-            assert ends[-1] == "syncthreads"
-            for k in range(len(los) - 1):
-                same = _warp_sets(K, los[k]) == _warp_sets(K, los[k + 1])
-                assert (ends[k] == "syncwarp") == same, (builder, which, i, k, los[k], los[k + 1])
-                local += ends[k] == "syncwarp"
+            blocks = list(zip(los, ends))
+            loop = re.search(r"// phases (\d+) \.\. \d+: (\d+) x the next (\d+) phase programs", src)
+            if loop:
+                st, reps, per = map(int, loop.groups())
+                seq = blocks[:st] + blocks[st:st + per] * reps + blocks[st + per:]
+                body_last = {st + per * r + per - 1 for r in range(reps)}
+            else:
+                seq, body_last = blocks, set()
+            assert seq[-1][1] == "syncthreads"
+            for k in range(len(seq) - 1):
+                same = _warp_sets(K, seq[k][0]) == _warp_sets(K, seq[k + 1][0])
+                if seq[k][1] == "syncwarp":
+                    assert same, (builder, which, i, k)   # a warp barrier is always safe
+                elif k not in body_last:
+                    assert not same, (builder, which, i, k)   # and used wherever it is safe
+                local += seq[k][1] == "syncwarp"
                 total += 1
     assert 0 < local < total
 
@@ -169,14 +185,21 @@ def _circuit(name):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("kind", ["pairs", "one", "lanes", "cpx"])
+@pytest.mark.parametrize("phases", ["greedy", "rr", None])
 @pytest.mark.parametrize("name,B", CASES)
-def test_compiled_plan_matches_oracle(name, B, kind):
+def test_compiled_plan_matches_oracle(name, B, phases, monkeypatch):
+    """Both phase groupings (greedy; round robin, whose periodic stretches
+    run as loops) and the automatic choice, against the oracle and against
+    the general kernel on the same schedule."""
+    if phases is None:
+        monkeypatch.delenv("QTM_PHASES", raising=False)
+    else:
+        monkeypatch.setenv("QTM_PHASES", phases)
     c = _circuit(name)
     inp = W.make_inputs(c, B, 21, real_dtype=np.float32)
     general = _run(capi.Plan(c, dtype="c64"), c, inp)
     plan = capi.Plan(c, dtype="c64")
-    plan.compile(kind=kind)
+    plan.compile()
     info = plan.info
     assert plan.compiled_passes() == info["fwd_passes"] + info["adj_passes"]
     got = _run(plan, c, inp)
@@ -184,9 +207,9 @@ def test_compiled_plan_matches_oracle(name, B, kind):
     _, gxo, gwo = oracle.adjoint(c, inp.gE, inp.x, inp.w, threads=0)
     for what, g, r, h in zip(("E", "gx", "gw"), got, (Eo, gxo, gwo), general):
         err = float(np.max(np.abs(g - r))) if r.size else 0.0
-        assert err <= 1e-5, f"{name} B={B} kind={kind} {what}: {err:.3e}"
+        assert err <= 1e-5, f"{name} B={B} phases={phases} {what}: {err:.3e}"
         d = float(np.max(np.abs(g - h))) if h.size else 0.0
-        assert d <= 2e-6, f"{name} B={B} kind={kind} compiled vs general {what}: {d:.3e}"
+        assert d <= 2e-6, f"{name} B={B} phases={phases} compiled vs general {what}: {d:.3e}"
 
 
 @pytest.mark.gpu
@@ -236,65 +259,17 @@ def test_compile_after_forward_and_recompute():
     assert np.max(np.abs(E1 - E0)) <= 2e-6
 
 
-# ---- paired general kernel (qtm_set_sample_pairing) -----------------------------------
-
-def test_pairing_eligibility_host():
-    assert capi.Plan(W.workload_12q(), dtype="c64").set_pairing(True).pairing
-    for c, dt in [(W.workload_12q(), "c128"), (W.workload_4q(), "c64")]:
-        with pytest.raises(capi.QtmError) as ei:
-            capi.Plan(c, dtype=dt).set_pairing(True)
-        assert ei.value.status == capi.QTM_EUNSUPPORTED
-    p = capi.Plan(W.workload_20q(), dtype="c64").set_pairing(True).set_pairing(False)
-    assert not p.pairing
-
-
 @pytest.mark.gpu
-@pytest.mark.parametrize("name,B", CASES)
-def test_paired_general_matches_oracle(name, B):
-    c = _circuit(name)
-    inp = W.make_inputs(c, B, 23, real_dtype=np.float32)
-    general = _run(capi.Plan(c, dtype="c64"), c, inp)
-    plan = capi.Plan(c, dtype="c64").set_pairing(True)
-    got = _run(plan, c, inp)
-    assert plan.compiled_passes() == 0
-    Eo = oracle.forward(c, inp.x, inp.w, threads=0)
-    _, gxo, gwo = oracle.adjoint(c, inp.gE, inp.x, inp.w, threads=0)
-    for what, g, r, h in zip(("E", "gx", "gw"), got, (Eo, gxo, gwo), general):
-        err = float(np.max(np.abs(g - r))) if r.size else 0.0
-        assert err <= 1e-5, f"{name} B={B} paired general {what}: {err:.3e}"
-        d = float(np.max(np.abs(g - h))) if h.size else 0.0
-        assert d <= 2e-6, f"{name} B={B} paired vs one-sample {what}: {d:.3e}"
-
-
-@pytest.mark.gpu
-def test_paired_general_jacobian_and_toggle():
-    import torch
-    c = W.workload_16q_train()
-    plan = capi.Plan(c, dtype="c64").set_pairing(True)
-    inp = W.make_inputs(c, 3, 4, real_dtype=np.float32)
-    x = torch.tensor(inp.x, dtype=torch.float32, device="cuda")
-    w = torch.tensor(inp.w, dtype=torch.float32, device="cuda")
-    J = plan.jacobian(x, w).double().cpu().numpy()
-    Jo = oracle.jacobian(c, inp.x, inp.w, threads=0)
-    assert np.max(np.abs(J - Jo)) <= 1e-5
-    E1 = plan.forward(x, w).double().cpu().numpy()
-    plan.set_pairing(False)
-    E0 = plan.forward(x, w).double().cpu().numpy()
-    assert np.max(np.abs(E1 - E0)) <= 2e-6
-
-
-@pytest.mark.gpu
-@pytest.mark.parametrize("kind", ["lanes", "cpx", "one", "pairs"])
 @pytest.mark.parametrize("n", [9, 12, 14])
-def test_compiled_plan_with_h_and_rzz(n, kind):
+def test_compiled_plan_with_h_and_rzz(n):
     rng = np.random.default_rng(950 + n)
     c = P.rand_small_circuit(rng, n, G=5 * n + 10, n_obs=3, extra=True)
     inp = W.make_inputs(c, 3, 17, real_dtype=np.float32)
     plan = capi.Plan(c, dtype="c64")
-    plan.compile(kind=kind)
+    plan.compile()
     got = _run(plan, c, inp)
     Eo = oracle.forward(c, inp.x, inp.w, threads=0)
     _, gxo, gwo = oracle.adjoint(c, inp.gE, inp.x, inp.w, threads=0)
     for what, g, r in zip(("E", "gx", "gw"), got, (Eo, gxo, gwo)):
         err = float(np.max(np.abs(g - r))) if r.size else 0.0
-        assert err <= 1e-5, f"n={n} kind={kind} {what}: {err:.3e}"
+        assert err <= 1e-5, f"n={n} {what}: {err:.3e}"

@@ -137,6 +137,7 @@ class ClockSampler:
 # kernel kind the bench runs (profiles/ holds the summaries and commands);
 # reported as null for any other kernel kind.
 PROFILED_TRAFFIC = {
+    ("qnn12", "cpx"): (39.686144e6 + 0.019712e6, "profiles/qtm_gen_pass_cpx_qnn12_l6_b1024.md"),
     ("qnn20", "cpx"): ((0.537211e9 + 1.022075e9 + 1.073937e9 + 1.018183e9 + 1.073976e9 + 0.497157e9 +
                         0.537045e9 + 0.507352e9 + 0.537005e9 + 0.003969e9) / 5,
                        "profiles/qtm_gen_pass_cpx_qnn20_l4_b64.md (mean of reverse passes 0-4)"),
@@ -247,7 +248,10 @@ def prepare(plan, kernels):
     return plan
 
 
-def measure_gpu(name, steps, warmup, device, seed_offset=0, profile=True, kernels="cpx"):
+TUNE_CACHE = os.path.join(tempfile.gettempdir(), "qtm_tune_cache.jsonl")
+
+
+def measure_gpu(name, steps, warmup, device, seed_offset=0, profile=True, kernels="cpx", tune=False):
     import numpy as np
     import torch
 
@@ -267,6 +271,11 @@ def measure_gpu(name, steps, warmup, device, seed_offset=0, profile=True, kernel
     gx = torch.empty((B, c.n_inputs), dtype=rd, device=device)
     gw = torch.empty((c.n_weights,), dtype=rd, device=device)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=device)
+    tuned = None
+    if tune:   # schedule chosen by qtm_tune for this batch (before the timed region)
+        t0 = time.perf_counter()
+        tuned = {"schedule": plan.tune(x, w, gE, cache_path=TUNE_CACHE), "seconds": time.perf_counter() - t0,
+                 "cache": "qtm_tune JSON-lines cache in the temp directory"}
 
     def step():
         plan.forward(x, w, out=E)
@@ -318,7 +327,7 @@ def measure_gpu(name, steps, warmup, device, seed_offset=0, profile=True, kernel
     plan.sync()
     outputs = (E.double().cpu().numpy(), gx_o.double().cpu().numpy(), gw_ps.double().cpu().numpy())
     return dict(c=c, B=B, plan=plan, inp=inp, step_ms=step_ms, info=info, kernels=kernels, workload=name,
-                sm_count=sm_count(device),
+                sm_count=sm_count(device), tuned=tuned,
                 outputs=outputs,
                 pass_fwd_ms=pass_fwd_ms, pass_rev_ms=pass_rev_ms, n_fwd_pass=n_fwd_pass,
                 n_rev_pass=n_rev_pass, launches=launches)
@@ -730,6 +739,14 @@ def measure_paper_shapes(device, peaks, reps=5, oracle_budget=1.0):
         f32 = dict(dtype=torch.float32, device=device)
         return inp, tuple(torch.tensor(a, **f32) for a in (inp.x, inp.w, inp.gE))
 
+    def settle():
+        """Keep the GPU busy for ~0.3 s so that the clocks are up before a sweep."""
+        a = torch.empty(64 << 20, dtype=torch.float32, device=device)
+        t_end = time.perf_counter() + 0.3
+        while time.perf_counter() < t_end:
+            a.mul_(1.0)
+            torch.cuda.synchronize()
+
     def time_point(plan, t, jac=True):
         x, w, g = t
         E = plan.forward(x, w)
@@ -766,9 +783,17 @@ def measure_paper_shapes(device, peaks, reps=5, oracle_budget=1.0):
     plans = [capi.Plan(c, dtype="c64") for c in cs]
     kinds = _compile_all(plans)
     pts = []
+    settle()
     for M, c, plan, kind in zip(Ms, cs, plans, kinds):
         inp, t = prepare(c, 1100 + M)
         r = time_point(plan, t)
+        # the same Jacobian with one observable per reverse sweep (QTM_JAC_CHUNK=1)
+        os.environ["QTM_JAC_CHUNK"] = "1"
+        try:
+            J = plan.jacobian(t[0], t[1])
+            r["jacobian_ms_one_observable_per_sweep"] = _median_ms(lambda: plan.jacobian(t[0], t[1], out=J), reps, flush)
+        finally:
+            del os.environ["QTM_JAC_CHUNK"]
         r.update({"M": M, "kernels": kind, "oracle_fwd_ms": oracle_ms(c, inp, "forward"),
                   "oracle_jacobian_ms": oracle_ms(c, inp, "jacobian")})
         pts.append(r)
@@ -783,6 +808,7 @@ def measure_paper_shapes(device, peaks, reps=5, oracle_budget=1.0):
     plans = [capi.Plan(c, dtype="c64") for c in cs]
     kinds = _compile_all(plans)
     pts = []
+    settle()
     for n, c, plan, kind in zip(ns, cs, plans, kinds):
         inp, t = prepare(c, 1200 + n)
         r = time_point(plan, t)
@@ -798,6 +824,7 @@ def measure_paper_shapes(device, peaks, reps=5, oracle_budget=1.0):
     plans = [capi.Plan(c, dtype="c64") for c in cs]
     kinds = _compile_all(plans)
     pts = []
+    settle()
     for d, c, plan, kind in zip(ds, cs, plans, kinds):
         inp, t = prepare(c, 1300 + d)
         r = time_point(plan, t)
@@ -812,7 +839,7 @@ def measure_paper_shapes(device, peaks, reps=5, oracle_budget=1.0):
     return out
 
 
-def measure_e2e(name, steps, device, seed_offset=0, kernels="cpx"):
+def measure_e2e(name, steps, device, seed_offset=0, kernels="cpx", tune=False):
     """End to end through the public API: pinned host inputs -> device,
     forward, adjoint, results -> pinned host, every step."""
     import numpy as np
@@ -827,6 +854,9 @@ def measure_e2e(name, steps, device, seed_offset=0, kernels="cpx"):
     rd = plan.real_dtype()
     inp = W.make_inputs(c, B, W.WORKLOAD_SEEDS[c.name] + seed_offset,
                         real_dtype=np.float32 if rd == torch.float32 else np.float64)
+    if tune:   # the schedule the timed line chose (a cache hit)
+        plan.tune(torch.tensor(inp.x, dtype=rd, device=device), torch.tensor(inp.w, dtype=rd, device=device),
+                  torch.tensor(inp.gE, dtype=rd, device=device), cache_path=TUNE_CACHE)
     hx = torch.tensor(inp.x, dtype=rd).pin_memory()
     hw = torch.tensor(inp.w, dtype=rd).pin_memory()
     hg = torch.tensor(inp.gE, dtype=rd).pin_memory()
@@ -886,7 +916,9 @@ def gpu_main(args):
         dist.barrier()
     torch.cuda.synchronize()
     sampler.mark("t0")
-    r12 = measure_gpu(args.workload, args.steps, args.warmup, device, seed_offset=rank, kernels=args.kernels)
+    tune = args.kernels == "cpx" and not args.no_tune
+    r12 = measure_gpu(args.workload, args.steps, args.warmup, device, seed_offset=rank, kernels=args.kernels,
+                      tune=tune)
     torch.cuda.synchronize()
     sampler.mark("t1")
     total_ms = sum(r12["step_ms"])
@@ -899,7 +931,7 @@ def gpu_main(args):
     n20 = None
     if args.workload == "qnn12" and not args.skip_n20:
         r20 = measure_gpu("qnn20", max(3, args.steps // 4), args.warmup, device, seed_offset=rank,
-                          kernels=args.kernels)
+                          kernels=args.kernels, tune=tune)
         tot20 = sum(r20["step_ms"])
         if ws > 1:
             t = torch.tensor([tot20], device=device, dtype=torch.float64)
@@ -931,7 +963,8 @@ def gpu_main(args):
             t0 = time.perf_counter()
             extra["paper_shapes"] = measure_paper_shapes(device, peaks)
             extra["paper_shapes"]["seconds"] = time.perf_counter() - t0
-    e2e = measure_e2e(args.workload, max(3, args.steps // 4), device, seed_offset=rank, kernels=args.kernels)
+    e2e = measure_e2e(args.workload, max(3, args.steps // 4), device, seed_offset=rank, kernels=args.kernels,
+                      tune=tune)
     if ws > 1:
         t = torch.tensor([e2e[0]], device=device, dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MIN)
@@ -960,6 +993,7 @@ def gpu_main(args):
                 "d2h_bytes_per_step": e2e[2]},
         "plan": {k: info[k] for k in ("fwd_passes", "adj_passes", "fwd_flops", "adj_flops",
                                        "fwd_state_bytes", "adj_state_bytes")},
+        "schedule": r12["tuned"] or {"schedule": r12["plan"].schedule, "tuned": False},
     }
     if n20 is not None:
         r20, tot20 = n20
@@ -974,6 +1008,7 @@ def gpu_main(args):
             "plan": {k: i20[k] for k in ("fwd_passes", "adj_passes", "fwd_flops", "adj_flops",
                                           "fwd_state_bytes", "adj_state_bytes")},
             "gpu_launches": r20["launches"],
+            "schedule": r20["tuned"] or {"schedule": r20["plan"].schedule, "tuned": False},
         }
     line.update(extra)
     if not args.no_cpu_baseline:
@@ -1053,6 +1088,7 @@ def main():
                     help="plan-specialised pass kernels (qtm_compile: one sample per CTA, each complex "
                          "amplitude an f32x2 pair) or the general pass kernel")
     ap.add_argument("--skip-extra", action="store_true", help="skip the uneven-batch and training lines")
+    ap.add_argument("--no-tune", action="store_true", help="time the default schedules (no qtm_tune)")
     ap.add_argument("--skip-paper-shapes", action="store_true",
                     help="skip the Tab. I / Fig. 1 / Fig. 2 shape sweeps")
     ap.add_argument("--paper-shapes-only", action="store_true",

@@ -391,6 +391,51 @@ qtm_status qtm_multi_destroy(qtm_multi *multi);
  * any stored forward state. */
 qtm_status qtm_compile(qtm_plan *plan, int flags);
 
+/* The schedule of a plan: the planner's and the kernels' choices, which do
+ * not change the results beyond rounding (Sec. II-A's computation either way);
+ * the knobs of qtm_tune. */
+typedef struct {
+    int32_t phase_mode;   /* register phases: 0 greedy (the most ready gates per phase), 1 round
+                           * robin (the register groups in turn, one run per qubit per phase),
+                           * 2 automatic (qtm_set_schedule only: round robin where most of the
+                           * work then repeats phase after phase, else greedy) */
+    int32_t tile_qubits;  /* qubits per shared-memory tile of a state that spans several tiles
+                           * (9 .. 12 complex64, 9 .. 11 complex128; 0 = the largest); a state
+                           * that fits one tile is always one tile (qtm_get_schedule reports its
+                           * width, and qtm_set_schedule ignores the field for it) */
+    int32_t low_min;      /* narrowest low block of a tile (4 .. tile_qubits): rows of 2^low_min
+                           * contiguous amplitudes in memory */
+    int32_t kernels;      /* 0 the general pass kernel, 1 the specialised kernels (qtm_compile) */
+    int32_t minb_fwd;     /* CTAs per SM the specialised forward / reverse kernels' registers are */
+    int32_t minb_rev;     /*   budgeted for (1 .. 4) */
+} qtm_schedule;
+
+/* Current schedule of a fused plan (host only). */
+qtm_status qtm_get_schedule(const qtm_plan *plan, qtm_schedule *sched);
+
+/* Re-plan a fused plan with `sched` and load its kernels (NVRTC compile for
+ * kernels = 1).  Where the specialised kernels do not apply (complex128, a
+ * tile below 9 qubits, no NVRTC) it returns QTM_EUNSUPPORTED and the plan
+ * keeps its old schedule, on the general kernel.  Synchronises the device
+ * and drops the workspace and any stored forward state.  Composite (grouped
+ * Pauli) and naive-path plans: QTM_EUNSUPPORTED. */
+qtm_status qtm_set_schedule(qtm_plan *plan, const qtm_schedule *sched);
+
+/* qtm_tune: choose the schedule of a fused plan for batches of B samples by
+ * timing forward + adjoint (CUDA events on `stream`, median of 5 after 2
+ * warm-up steps) over candidate schedules, one knob at a time from the
+ * current one (phase grouping; tile width and low-block width of multi-tile
+ * states; specialised or general kernels and the specialised kernels'
+ * register budgets), keeping a change only when it is at least 1 % faster;
+ * the fastest is applied.  x [B][n_inputs], w, grad_expvals [B][n_obs]: device
+ * inputs of the plan's real type (read only); the outputs go to scratch the
+ * call allocates and frees.  cache_path (or NULL): a JSON-lines file of
+ * earlier choices keyed by the circuit, observables, dtype, B and the device
+ * name; a hit applies the stored schedule without timing, a miss appends the
+ * choice.  Synchronises the device. */
+qtm_status qtm_tune(qtm_plan *plan, int B, const void *x, const void *w, const void *grad_expvals, void *stream,
+                    const char *cache_path);
+
 /* Number of specialised pass kernels loaded for the current device (0 before
  * qtm_compile, or on another device). */
 int qtm_compiled_passes(const qtm_plan *plan);

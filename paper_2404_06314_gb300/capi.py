@@ -40,6 +40,14 @@ class qtm_pauli_term(ctypes.Structure):
                 ("obs", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
+class qtm_schedule(ctypes.Structure):
+    _fields_ = [("phase_mode", ctypes.c_int32), ("tile_qubits", ctypes.c_int32), ("low_min", ctypes.c_int32),
+                ("kernels", ctypes.c_int32), ("minb_fwd", ctypes.c_int32), ("minb_rev", ctypes.c_int32)]
+
+
+SCHEDULE_FIELDS = [f for f, _ in qtm_schedule._fields_]
+
+
 class qtm_plan_info(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int32) for k in (
         "n_qubits", "dtype", "path", "tile_qubits", "fwd_passes", "adj_passes", "fwd_launches",
@@ -96,6 +104,12 @@ def lib(build_if_missing: bool = True):
         L.qtm_debug_emulate.argtypes = [vp, i, vp, vp, vp, vp, vp, vp]
         L.qtm_compile.argtypes = [vp, i]
         L.qtm_compile.restype = ctypes.c_int
+        L.qtm_get_schedule.argtypes = [vp, P(qtm_schedule)]
+        L.qtm_get_schedule.restype = ctypes.c_int
+        L.qtm_set_schedule.argtypes = [vp, P(qtm_schedule)]
+        L.qtm_set_schedule.restype = ctypes.c_int
+        L.qtm_tune.argtypes = [vp, i, vp, vp, vp, vp, ctypes.c_char_p]
+        L.qtm_tune.restype = ctypes.c_int
         L.qtm_compiled_passes.argtypes = [vp]
         L.qtm_compiled_passes.restype = ctypes.c_int
         L.qtm_debug_jit_source.argtypes = [vp, i, i, i]
@@ -326,6 +340,32 @@ class Plan:
     def parts(self) -> int:
         """Measurement groups (1 unless the observables have X/Y terms)."""
         return int(lib().qtm_plan_parts(self.handle))
+
+    @property
+    def schedule(self) -> dict:
+        """The plan's schedule (qtm_get_schedule): phase_mode (0 greedy, 1 round
+        robin), tile_qubits, low_min, kernels (0 general, 1 specialised),
+        minb_fwd, minb_rev."""
+        sc = qtm_schedule()
+        self._raise(lib().qtm_get_schedule(self.handle, ctypes.byref(sc)), "qtm_get_schedule")
+        return {f: getattr(sc, f) for f in SCHEDULE_FIELDS}
+
+    @schedule.setter
+    def schedule(self, d: dict):
+        cur = self.schedule
+        cur.update(d)
+        sc = qtm_schedule(*[int(cur[f]) for f in SCHEDULE_FIELDS])
+        self._raise(lib().qtm_set_schedule(self.handle, ctypes.byref(sc)), "qtm_set_schedule")
+
+    def tune(self, x, w, gE, cache_path=None, stream=None) -> dict:
+        """qtm_tune for batches shaped like x; returns the chosen schedule."""
+        c = self.circuit
+        B = x.shape[0]
+        st = lib().qtm_tune(self.handle, B, self._check(x, (B, c.n_inputs), "x"), self._check(w, (c.n_weights,), "w"),
+                            self._check(gE, (B, c.n_obs), "grad_expvals"), self._stream(stream),
+                            cache_path.encode() if cache_path else None)
+        self._raise(st, "qtm_tune")
+        return self.schedule
 
     def compiled_passes(self) -> int:
         return int(lib().qtm_compiled_passes(self.handle))

@@ -41,6 +41,13 @@ struct TmGeom {
 struct qtm_plan {
     Plan P;
     std::string err;
+    // the circuit as given, kept for re-planning (qtm_set_schedule, qtm_tune)
+    std::vector<qtm_gate> src_gates;
+    std::vector<qtm_zterm> src_terms;
+    std::vector<PauliTerm> src_pterms;   // strings with X/Y factors of a one-evolution plan
+    int src_n = 0, src_n_obs = 0, src_n_weights = 0, src_n_inputs = 0, src_path = QTM_PATH_AUTO;
+    PlanOptions opt;
+    int minb_f = 3, minb_r = 2;          // CTAs per SM the specialised kernels are compiled for
     int device = -1;
     // device tables
     DevOp *d_ops = nullptr;
@@ -558,6 +565,108 @@ qtm_status ensure_tmp(qtm_plan *p, size_t bytes)
     return QTM_OK;
 }
 
+// (Re)build p->P from the circuit as given with p->opt: the schedule, the
+// costate buffer it needs and every pass's shared memory.  Host only; p->P
+// is replaced only on success.
+qtm_status plan_from_source(qtm_plan *p, int dtype)
+{
+    Plan P;
+    std::string err;
+    qtm_status st = make_plan(p->src_n, p->src_gates.data(), (int)p->src_gates.size(), p->src_terms.data(),
+                              (int)p->src_terms.size(), p->src_n_obs, p->src_n_weights, p->src_n_inputs, dtype,
+                              p->src_path, P, err, p->opt);
+    if (st != QTM_OK) { p->err = err; return st; }
+    if (!p->src_pterms.empty()) attach_pauli_terms(P, p->src_pterms);
+    bool needs_lam = !p->src_pterms.empty();
+    std::vector<size_t> sf, sr;
+    if (P.path == QTM_PATH_FUSED) {
+        for (const auto &pd : P.rev)
+            if (pd.lam_src == SRC_LOAD || pd.store_lam) needs_lam = true;
+        auto sm = [&](const PassDesc &pd, bool rev) {
+            return pass_smem_bytes(pd.K, P.dtype, rev, pd.slot_end - pd.slot_begin, (int)P.terms.size(),
+                                   P.n_obs, P.state_qubits,
+                                   pd.phi_src == SRC_ANALYTIC ? pd.analytic_ents : 0);
+        };
+        for (const auto &pd : P.fwd) sf.push_back(sm(pd, false));
+        for (const auto &pd : P.rev) sr.push_back(sm(pd, true));
+        for (size_t v : sf)
+            if (v > kMaxDynSmem) { p->err = "a pass needs more shared memory than a CTA has"; return QTM_EUNSUPPORTED; }
+        for (size_t v : sr)
+            if (v > kMaxDynSmem) { p->err = "a pass needs more shared memory than a CTA has"; return QTM_EUNSUPPORTED; }
+    }
+    p->P = std::move(P);
+    p->needs_lam = needs_lam;
+    p->smem_fwd = std::move(sf);
+    p->smem_rev = std::move(sr);
+    return QTM_OK;
+}
+
+// Key of a tuned schedule: the circuit as given, the observables, dtype,
+// batch size and device name (FNV-1a).
+std::string tune_signature(const qtm_plan *p, int B)
+{
+    unsigned long long h = 1469598103934665603ull;
+    auto mix = [&](unsigned long long v) {
+        for (int k = 0; k < 8; ++k) { h ^= (v >> (8 * k)) & 0xffull; h *= 1099511628211ull; }
+    };
+    mix((unsigned long long)p->src_n); mix((unsigned long long)p->P.dtype); mix((unsigned long long)B);
+    mix((unsigned long long)p->src_n_obs);
+    for (const auto &g : p->src_gates) {
+        mix((unsigned long long)(uint32_t)g.kind); mix((unsigned long long)(uint32_t)g.q0);
+        mix((unsigned long long)(uint32_t)g.q1); mix((unsigned long long)(uint32_t)g.w_idx);
+        mix((unsigned long long)(uint32_t)g.x_idx);
+    }
+    for (const auto &t : p->src_terms) { mix(t.zmask); mix((unsigned long long)(uint32_t)t.obs); }
+    for (const auto &t : p->src_pterms) { mix(t.xmask); mix(t.zmask); mix((unsigned long long)(uint32_t)t.obs); }
+    std::string name = "unknown";
+    int dev = 0;
+    cudaDeviceProp prop;
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaGetDeviceProperties(&prop, dev) == cudaSuccess) name = prop.name;
+    for (char &ch : name) if (ch == '"' || ch == '\\') ch = '_';
+    char buf[32];
+    std::snprintf(buf, sizeof(buf), "%016llx", h);
+    return std::string(buf) + "@" + name;
+}
+
+bool tune_cache_lookup(const char *path, const std::string &sig, qtm_schedule &out)
+{
+    if (!path) return false;
+    FILE *f = std::fopen(path, "r");
+    if (!f) return false;
+    const std::string key = "\"signature\": \"" + sig + "\"";
+    char line[1024];
+    bool found = false;
+    while (std::fgets(line, sizeof(line), f)) {
+        const std::string l(line);
+        if (l.find(key) == std::string::npos) continue;
+        auto num = [&](const char *field) -> int {
+            const std::string k = std::string("\"") + field + "\": ";
+            const size_t at = l.find(k);
+            return at == std::string::npos ? -1 : std::atoi(l.c_str() + at + k.size());
+        };
+        qtm_schedule c{num("phase_mode"), num("tile_qubits"), num("low_min"), num("kernels"), num("minb_fwd"),
+                       num("minb_rev")};
+        if (c.phase_mode < 0 || c.tile_qubits < 0 || c.low_min < 0 || c.kernels < 0 || c.minb_fwd < 1 || c.minb_rev < 1)
+            continue;
+        out = c;
+        found = true;   // the last matching line wins
+    }
+    std::fclose(f);
+    return found;
+}
+
+void tune_cache_store(const char *path, const std::string &sig, const qtm_schedule &c, double ms)
+{
+    if (!path) return;
+    FILE *f = std::fopen(path, "a");
+    if (!f) return;
+    std::fprintf(f,
+                 "{\"signature\": \"%s\", \"phase_mode\": %d, \"tile_qubits\": %d, \"low_min\": %d, \"kernels\": %d, "
+                 "\"minb_fwd\": %d, \"minb_rev\": %d, \"ms\": %.6f}\n",
+                 sig.c_str(), c.phase_mode, c.tile_qubits, c.low_min, c.kernels, c.minb_fwd, c.minb_rev, ms);
+    std::fclose(f);
+}
+
 // A device buffer of at least `bytes` (kept across calls; freed with the workspace).
 cudaError_t ensure_buffer(void *&ptr, size_t &cap, size_t bytes)
 {
@@ -630,8 +739,9 @@ qtm_status qtm_build_pauli(int n_qubits, const qtm_gate *gates, int n_gates, con
         qtm_status st = qtm_build(n_qubits, gates, n_gates, zs.data(), (int)zs.size(), n_obs, n_weights, n_inputs,
                                   dtype, path, &p);
         if (st != QTM_OK) return st;
-        attach_pauli_terms(p->P, ps);
-        p->needs_lam = true;
+        p->src_pterms = ps;
+        st = plan_from_source(p, dtype);   // the same schedule, with the X/Y strings attached
+        if (st != QTM_OK) { qtm_destroy(p); return st; }
         *out = p;
         return QTM_OK;
     }
@@ -770,34 +880,22 @@ qtm_status qtm_build(int n_qubits, const qtm_gate *gates, int n_gates, const qtm
 {
     if (!out) return QTM_EINVAL;
     *out = nullptr;
+    if (n_gates < 0 || (n_gates > 0 && !gates) || n_terms < 0 || (n_terms > 0 && !terms)) return QTM_EINVAL;
     qtm_plan *p = new (std::nothrow) qtm_plan();
     if (!p) return QTM_ENOMEM;
-    std::string err;
+    p->src_gates.assign(gates, gates + n_gates);
+    p->src_terms.assign(terms, terms + n_terms);
+    p->src_n = n_qubits; p->src_n_obs = n_obs; p->src_n_weights = n_weights; p->src_n_inputs = n_inputs;
+    p->src_path = path;
+    p->P.dtype = dtype;
     // phase grouping: automatic (default), or QTM_PHASES=greedy / rr (a tuning switch)
     const char *pm = std::getenv("QTM_PHASES");
-    const int phase_mode = !pm                              ? PHASES_AUTO
-                           : std::strcmp(pm, "rr") == 0     ? PHASES_ROUND_ROBIN
-                           : std::strcmp(pm, "greedy") == 0 ? PHASES_GREEDY
-                                                            : PHASES_AUTO;
-    qtm_status st = make_plan(n_qubits, gates, n_gates, terms, n_terms, n_obs, n_weights, n_inputs,
-                              dtype, path, p->P, err, kMaxRunLen, phase_mode);
+    p->opt.phase_mode = !pm                              ? PHASES_AUTO
+                        : std::strcmp(pm, "rr") == 0     ? PHASES_ROUND_ROBIN
+                        : std::strcmp(pm, "greedy") == 0 ? PHASES_GREEDY
+                                                         : PHASES_AUTO;
+    qtm_status st = plan_from_source(p, dtype);
     if (st != QTM_OK) { delete p; return st; }
-    const Plan &P = p->P;
-    if (P.path == QTM_PATH_FUSED) {
-        for (const auto &pd : P.rev)
-            if (pd.lam_src == SRC_LOAD || pd.store_lam) p->needs_lam = true;
-        auto sm = [&](const PassDesc &pd, bool rev) {
-            return pass_smem_bytes(pd.K, P.dtype, rev, pd.slot_end - pd.slot_begin, (int)P.terms.size(),
-                                   P.n_obs, P.state_qubits,
-                                   pd.phi_src == SRC_ANALYTIC ? pd.analytic_ents : 0);
-        };
-        for (const auto &pd : P.fwd) p->smem_fwd.push_back(sm(pd, false));
-        for (const auto &pd : P.rev) p->smem_rev.push_back(sm(pd, true));
-        for (size_t v : p->smem_fwd)
-            if (v > kMaxDynSmem) { delete p; return QTM_EUNSUPPORTED; }
-        for (size_t v : p->smem_rev)
-            if (v > kMaxDynSmem) { delete p; return QTM_EUNSUPPORTED; }
-    }
     *out = p;
     return QTM_OK;
 }
@@ -1106,7 +1204,7 @@ qtm_status compile_all(qtm_plan *p, std::vector<std::vector<char>> &fwd_bin, std
     fwd_bin.assign(P.fwd.size(), {});
     rev_bin.assign(P.rev.size(), {});
     // CTAs per SM the register budget is compiled for (forward, reverse)
-    int minb_f = 3, minb_r = 2;
+    int minb_f = p->minb_f, minb_r = p->minb_r;
     if (const char *e = std::getenv("QTM_JIT_MINB")) {   // tuning: "<forward>,<reverse>"
         int f = 0, r = 0;
         if (std::sscanf(e, "%d,%d", &f, &r) == 2 && f >= 1 && f <= 8 && r >= 1 && r <= 8) { minb_f = f; minb_r = r; }
@@ -1188,6 +1286,182 @@ qtm_status qtm_compile(qtm_plan *p, int flags)
     }
     p->jit_device = p->device;
     return QTM_OK;
+}
+
+qtm_status qtm_get_schedule(const qtm_plan *p, qtm_schedule *sched)
+{
+    if (!p || !sched) return QTM_EINVAL;
+    if (is_composite(p) || p->P.path != QTM_PATH_FUSED) return QTM_EUNSUPPORTED;
+    sched->phase_mode = p->P.phase_mode;
+    sched->tile_qubits = p->P.K;
+    sched->low_min = p->P.low_min;
+    sched->kernels = jit_active(p) ? 1 : 0;
+    sched->minb_fwd = p->minb_f;
+    sched->minb_rev = p->minb_r;
+    return QTM_OK;
+}
+
+qtm_status qtm_set_schedule(qtm_plan *p, const qtm_schedule *sched)
+{
+    if (!p || !sched) return QTM_EINVAL;
+    if (is_composite(p) || p->P.path != QTM_PATH_FUSED)
+        return fail(p, QTM_EUNSUPPORTED, "schedules apply to single fused plans");
+    const qtm_schedule &q = *sched;
+    const int kmax = p->P.dtype == QTM_C128 ? kMaxTileQubits128 : kMaxTileQubits;
+    if (q.phase_mode < 0 || q.phase_mode > 2 || q.kernels < 0 || q.kernels > 1 || q.minb_fwd < 1 || q.minb_fwd > 4 ||
+        q.minb_rev < 1 || q.minb_rev > 4 || (q.tile_qubits != 0 && (q.tile_qubits < kRegBits || q.tile_qubits > kMaxTileQubits)) ||
+        q.low_min < kRegBits || q.low_min > kMaxTileQubits)
+        return fail(p, QTM_EINVAL, "schedule field out of range");
+    PlanOptions opt = p->opt;
+    opt.phase_mode = q.phase_mode == 1 ? PHASES_ROUND_ROBIN : q.phase_mode == 2 ? PHASES_AUTO : PHASES_GREEDY;
+    // a one-tile state reports its own width; only multi-tile states take the field
+    const bool multi = p->P.state_qubits > kMaxTileQubits;
+    if (multi && q.tile_qubits != 0 && q.tile_qubits < 9)
+        return fail(p, QTM_EINVAL, "tiles of a multi-tile state have 9 .. 12 qubits");
+    opt.tile_qubits = multi ? std::min(q.tile_qubits ? q.tile_qubits : kmax, kmax) : 0;
+    opt.low_min = q.low_min;
+    if (q.kernels == 1 && p->P.dtype != QTM_C64)
+        return fail(p, QTM_EUNSUPPORTED, "specialised kernels exist for complex64 plans");
+    // nothing of the old schedule may still run: tables, workspace and kernels go
+    if (p->d_status) {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (p->device >= 0) cudaSetDevice(p->device);
+        cudaError_t e = cudaDeviceSynchronize();
+        if (cur >= 0) cudaSetDevice(cur);
+        if (e != cudaSuccess) return cuda_fail(p, e, "synchronize before re-planning");
+    }
+    const Plan old_P = p->P;
+    const PlanOptions old_opt = p->opt;
+    const int old_f = p->minb_f, old_r = p->minb_r;
+    p->opt = opt;
+    qtm_status st = plan_from_source(p, p->P.dtype);
+    if (st != QTM_OK) { p->opt = old_opt; return st; }
+    for (auto *v : {&p->jit_fwd, &p->jit_rev})
+        for (auto &k : *v) jit_unload(k);
+    p->jit_fwd.clear();
+    p->jit_rev.clear();
+    p->jit_device = -1;
+    free_workspace(p);
+    free_tables(p);
+    p->device = -1;
+    p->fwd_valid = false;
+    p->minb_f = q.minb_fwd;
+    p->minb_r = q.minb_rev;
+    if (q.kernels == 1) {
+        st = qtm_compile(p, 0);
+        if (st != QTM_OK) {   // back to the old schedule on the general kernel
+            const std::string why = p->err;
+            p->P = old_P;
+            p->opt = old_opt;
+            p->minb_f = old_f;
+            p->minb_r = old_r;
+            plan_from_source(p, p->P.dtype);
+            free_workspace(p);
+            free_tables(p);
+            p->device = -1;
+            p->err = why;
+            return st;
+        }
+    }
+    return QTM_OK;
+}
+
+qtm_status qtm_tune(qtm_plan *p, int B, const void *x, const void *w, const void *gE, void *stream,
+                    const char *cache_path)
+{
+    if (!p) return QTM_EINVAL;
+    if (is_composite(p) || p->P.path != QTM_PATH_FUSED)
+        return fail(p, QTM_EUNSUPPORTED, "schedules apply to single fused plans");
+    const Plan &P0 = p->P;
+    if (B < 1 || (P0.n_inputs > 0 && !x) || (P0.n_weights > 0 && !w) || !gE) return fail(p, QTM_EINVAL, "bad arguments");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const std::string sig = tune_signature(p, B);
+    qtm_schedule best{};
+    qtm_status st = qtm_get_schedule(p, &best);
+    if (st != QTM_OK) return st;
+    if (tune_cache_lookup(cache_path, sig, best)) return qtm_set_schedule(p, &best);
+    const size_t rsize = elem_bytes(P0.dtype) / 2;
+    void *E = nullptr, *gx = nullptr, *gw = nullptr;
+    if (cudaMalloc(&E, rsize * (size_t)B * std::max(1, P0.n_obs)) != cudaSuccess ||
+        cudaMalloc(&gx, rsize * (size_t)B * std::max(1, P0.n_inputs)) != cudaSuccess ||
+        cudaMalloc(&gw, rsize * std::max(1, P0.n_weights)) != cudaSuccess) {
+        cudaFree(E); cudaFree(gx); cudaFree(gw);
+        return fail(p, QTM_ENOMEM, "tuning scratch allocation failed");
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    // median time (ms) of forward + adjoint under schedule c; < 0 if c does not apply
+    auto time_of = [&](const qtm_schedule &c) -> double {
+        if (qtm_set_schedule(p, &c) != QTM_OK) return -1.0;
+        std::vector<float> t;
+        for (int rep = 0; rep < 7; ++rep) {
+            cudaEventRecord(e0, s);
+            if (qtm_forward(p, B, x, w, E, s) != QTM_OK ||
+                qtm_adjoint(p, B, gE, x, w, P0.n_inputs > 0 ? gx : nullptr, P0.n_weights > 0 ? gw : nullptr, 0, s) !=
+                    QTM_OK)
+                return -1.0;
+            cudaEventRecord(e1, s);
+            if (cudaEventSynchronize(e1) != cudaSuccess) return -1.0;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep >= 2) t.push_back(ms);   // two warm-up steps
+        }
+        std::sort(t.begin(), t.end());
+        return t[t.size() / 2];
+    };
+    if (P0.dtype == QTM_C64 && best.kernels == 0) {   // start from the specialised kernels where they apply
+        qtm_schedule c = best;
+        c.kernels = 1;
+        if (qtm_set_schedule(p, &c) == QTM_OK) best = c;
+    }
+    double best_ms = time_of(best);
+    if (best_ms < 0) {
+        cudaFree(E); cudaFree(gx); cudaFree(gw);
+        cudaEventDestroy(e0); cudaEventDestroy(e1);
+        return fail(p, QTM_ECUDA, "timing the current schedule failed: " + p->err);
+    }
+    const bool multi = p->P.state_qubits > kMaxTileQubits;
+    const int kmax = p->P.dtype == QTM_C128 ? kMaxTileQubits128 : kMaxTileQubits;
+    // one knob at a time, each alternative against the best so far
+    std::vector<std::vector<qtm_schedule>> rounds;
+    auto with = [&](auto set) {
+        std::vector<qtm_schedule> v;
+        set(v);
+        rounds.push_back(v);
+    };
+    with([&](std::vector<qtm_schedule> &v) { for (int m : {0, 1}) { qtm_schedule c{}; c.phase_mode = m; v.push_back(c); } });
+    if (multi) {
+        with([&](std::vector<qtm_schedule> &v) { for (int k = kmax; k >= std::max(9, kmax - 2); --k) { qtm_schedule c{}; c.tile_qubits = k; v.push_back(c); } });
+        with([&](std::vector<qtm_schedule> &v) { for (int l : {4, 6, 8}) { qtm_schedule c{}; c.low_min = l; v.push_back(c); } });
+    }
+    if (p->P.dtype == QTM_C64) {
+        with([&](std::vector<qtm_schedule> &v) {
+            for (auto fr : {std::pair<int, int>{3, 2}, {2, 2}, {4, 2}, {3, 1}}) {
+                qtm_schedule c{}; c.minb_fwd = fr.first; c.minb_rev = fr.second; v.push_back(c);
+            }
+        });
+        with([&](std::vector<qtm_schedule> &v) { for (int k : {0, 1}) { qtm_schedule c{}; c.kernels = k; v.push_back(c); } });
+    }
+    for (size_t r = 0; r < rounds.size(); ++r)
+        for (const qtm_schedule &alt : rounds[r]) {
+            qtm_schedule c = best;
+            if (r == 0) c.phase_mode = alt.phase_mode;
+            else if (multi && r == 1) c.tile_qubits = alt.tile_qubits;
+            else if (multi && r == 2) c.low_min = alt.low_min;
+            else if (alt.minb_fwd) { c.minb_fwd = alt.minb_fwd; c.minb_rev = alt.minb_rev; }
+            else c.kernels = alt.kernels;
+            if (std::memcmp(&c, &best, sizeof(c)) == 0) continue;
+            if (c.kernels == 0 && (c.minb_fwd != best.minb_fwd || c.minb_rev != best.minb_rev)) continue;
+            const double ms = time_of(c);
+            if (ms > 0 && ms < 0.99 * best_ms) { best = c; best_ms = ms; }
+        }
+    cudaFree(E); cudaFree(gx); cudaFree(gw);
+    cudaEventDestroy(e0); cudaEventDestroy(e1);
+    st = qtm_set_schedule(p, &best);
+    if (st == QTM_OK) tune_cache_store(cache_path, sig, best, best_ms);
+    return st;
 }
 
 int qtm_compiled_passes(const qtm_plan *p)

@@ -527,9 +527,11 @@ qtm_status plan_all(qtm_multi *m)
     for (int c = 0; c < nc; ++c) {
         const qtm_circuit &d = m->desc[c];
         std::string err;
+        PlanOptions opt;
+        opt.max_run = m->cfg.fuse_width;   // greedy phases: the persistent kernel interprets its op records
         qtm_status st = make_plan(d.n_qubits, m->gates[c].data(), (int)m->gates[c].size(), m->terms[c].data(),
                                   (int)m->terms[c].size(), d.n_obs, d.n_weights, d.n_inputs, m->dtype,
-                                  QTM_PATH_FUSED, m->plans[c], err, m->cfg.fuse_width);
+                                  QTM_PATH_FUSED, m->plans[c], err, opt);
         if (st != QTM_OK) {
             std::ostringstream s;
             s << "circuit " << c << ": " << err;

@@ -272,7 +272,7 @@ struct Builder {
         }
         // candidate tile sets
         std::vector<TileSet> cands;
-        for (int l = kRegBits; l <= K; ++l) {
+        for (int l = std::max(kRegBits, P.low_min); l <= K; ++l) {
             int m = K - l;
             if (m == 0) { cands.push_back({l, l, 0}); continue; }
             for (int h = l; h + m <= n; ++h) cands.push_back({l, h, m});
@@ -360,10 +360,9 @@ namespace {
 
 qtm_status make_plan_mode(int n, const qtm_gate *gates, int n_gates, const qtm_zterm *terms,
                           int n_terms, int n_obs, int n_weights, int n_inputs, int dtype, int path,
-                          Plan &P, std::string &err, int max_run, int phase_mode)
+                          Plan &P, std::string &err, const PlanOptions &opt, int phase_mode)
 {
-    if (max_run < 1) max_run = 1;
-    if (max_run > kMaxRunLen) max_run = kMaxRunLen;
+    const int max_run = std::min(std::max(opt.max_run, 1), kMaxRunLen);
     auto bad = [&](const std::string &m) { err = m; return QTM_EINVAL; };
     if (n < 1 || n > kMaxQubits) return bad("n_qubits out of range 1..30");
     if (n_gates < 0 || (n_gates > 0 && !gates)) return bad("bad gate array");
@@ -413,6 +412,7 @@ qtm_status make_plan_mode(int n, const qtm_gate *gates, int n_gates, const qtm_z
 
     P = Plan();
     P.phase_mode = phase_mode == PHASES_ROUND_ROBIN ? PHASES_ROUND_ROBIN : PHASES_GREEDY;
+    P.low_min = std::min(std::max(opt.low_min, kRegBits), kMaxTileQubits);
     P.n = n; P.dtype = dtype; P.n_obs = n_obs; P.n_weights = n_weights; P.n_inputs = n_inputs;
     P.path = (path == QTM_PATH_NAIVE) ? QTM_PATH_NAIVE : QTM_PATH_FUSED;
     P.n_user_gates = n_gates;
@@ -564,7 +564,11 @@ qtm_status make_plan_mode(int n, const qtm_gate *gates, int n_gates, const qtm_z
     const int Kmax = dtype == QTM_C128 ? kMaxTileQubits128 : kMaxTileQubits;
     const int smem_limit = kMaxTileQubits;   // whole-state tile for either dtype
     P.state_qubits = std::max(n, kRegBits);
-    P.K = (P.state_qubits <= smem_limit) ? P.state_qubits : Kmax;
+    // a state that spans several tiles: tiles of Kmax qubits unless the
+    // options ask for a narrower one (at least 9: full warps of 16 registers)
+    const int Kmulti = (opt.tile_qubits >= 9 && opt.tile_qubits <= Kmax) ? opt.tile_qubits : Kmax;
+    P.K = (P.state_qubits <= smem_limit) ? P.state_qubits : Kmulti;
+    if (P.low_min > P.K) P.low_min = P.K;
     P.tiles_per_sample = 1 << (P.state_qubits - P.K);
 
     P.pass_ents = P.prefix_ents;   // [0, |prefix_ents|): the forward's analytic state
@@ -827,22 +831,22 @@ double periodic_fraction(const Plan &P)
 
 qtm_status make_plan(int n, const qtm_gate *gates, int n_gates, const qtm_zterm *terms,
                      int n_terms, int n_obs, int n_weights, int n_inputs, int dtype, int path,
-                     Plan &P, std::string &err, int max_run, int phase_mode)
+                     Plan &P, std::string &err, const PlanOptions &opt)
 {
-    if (phase_mode != PHASES_AUTO)
+    if (opt.phase_mode != PHASES_AUTO)
         return make_plan_mode(n, gates, n_gates, terms, n_terms, n_obs, n_weights, n_inputs, dtype, path, P, err,
-                              max_run, phase_mode);
+                              opt, opt.phase_mode);
     // round robin where it makes most of the work periodic, else greedy; the
     // interpreter kernels (complex128 plans) run a few percent slower on the
     // extra phases, so those keep greedy
     if (dtype == QTM_C128)
         return make_plan_mode(n, gates, n_gates, terms, n_terms, n_obs, n_weights, n_inputs, dtype, path, P, err,
-                              max_run, PHASES_GREEDY);
+                              opt, PHASES_GREEDY);
     qtm_status st = make_plan_mode(n, gates, n_gates, terms, n_terms, n_obs, n_weights, n_inputs, dtype, path, P,
-                                   err, max_run, PHASES_ROUND_ROBIN);
+                                   err, opt, PHASES_ROUND_ROBIN);
     if (st != QTM_OK || P.path != QTM_PATH_FUSED || periodic_fraction(P) >= 0.5) return st;
     return make_plan_mode(n, gates, n_gates, terms, n_terms, n_obs, n_weights, n_inputs, dtype, path, P, err,
-                          max_run, PHASES_GREEDY);
+                          opt, PHASES_GREEDY);
 }
 
 void plan_costs(const Plan &p, double &fwd_bytes, double &adj_bytes, double &fwd_flops,

@@ -17,10 +17,19 @@ namespace qtm {
 // complex128 plans (interpreter kernels only) always get greedy.
 enum { PHASES_GREEDY = 0, PHASES_ROUND_ROBIN = 1, PHASES_AUTO = 2 };
 
+// Schedule choices of the planner (the autotuner's knobs).
+struct PlanOptions {
+    int max_run = kMaxRunLen;          // most rotations fused into one run (fusion width)
+    int phase_mode = PHASES_GREEDY;    // PHASES_GREEDY, PHASES_ROUND_ROBIN or PHASES_AUTO
+    int tile_qubits = 0;               // K of plans whose state spans several tiles (0: the largest)
+    int low_min = kRegBits;            // narrowest low block l of a tile (contiguous 2^l-amplitude rows)
+};
+
 struct Plan {
     // circuit
     int n = 0, dtype = QTM_C64, path = QTM_PATH_FUSED;
-    int phase_mode = PHASES_GREEDY;
+    int phase_mode = PHASES_GREEDY;    // resolved (never PHASES_AUTO)
+    int low_min = kRegBits;
     int n_obs = 0, n_weights = 0, n_inputs = 0;
     std::vector<qtm_gate> gates;        // lowered to RX/RY/RZ/CZ/CNOT (H and RZZ expanded)
     int n_user_gates = 0;               // gates as given to qtm_build (Jacobian columns)
@@ -60,12 +69,9 @@ struct Plan {
 };
 
 // Build the plan (host only).  Returns QTM_OK or an error with `err` set.
-// max_run: most rotations fused into one run (the fusion width);
-// phase_mode: PHASES_GREEDY, PHASES_ROUND_ROBIN or PHASES_AUTO.
 qtm_status make_plan(int n, const qtm_gate *gates, int n_gates, const qtm_zterm *terms,
                      int n_terms, int n_obs, int n_weights, int n_inputs, int dtype, int path,
-                     Plan &out, std::string &err, int max_run = kMaxRunLen,
-                     int phase_mode = PHASES_GREEDY);
+                     Plan &out, std::string &err, const PlanOptions &opt = PlanOptions());
 
 // Fraction of a plan's phase ops that lie in periodic stretches of its
 // passes' phases (the same phase program repeated with shifted run slots),

@@ -355,3 +355,41 @@ def test_automatic_phase_mode_host(monkeypatch):
     for mode in ("greedy", "rr"):
         monkeypatch.setenv("QTM_PHASES", mode)
         _emulate_vs_oracle(W.workload_12q(), 3, 5)
+
+
+def test_schedule_get_set_replans_host():
+    """qtm_set_schedule re-plans from the circuit as given (host only with
+    the general kernel): the phase grouping, the tile width and the low-block
+    width of a multi-tile plan take effect, every schedule's FP64 emulation
+    matches the oracle, and bad fields are rejected without changing it."""
+    c = W.workload_16q_train()
+    plan = capi.Plan(c, dtype="c64")
+    s0 = plan.schedule
+    assert s0["tile_qubits"] == 12 and s0["kernels"] == 0 and s0["low_min"] == 4
+    inp = W.make_inputs(c, 2, 31)
+    Eo = oracle.forward(c, inp.x, inp.w, threads=0)
+    _, gxo, gwo = oracle.adjoint(c, inp.gE, inp.x, inp.w, threads=0)
+    seen = set()
+    for sched in ({"phase_mode": 1}, {"tile_qubits": 10}, {"tile_qubits": 11, "low_min": 6}, {"phase_mode": 0}):
+        plan.schedule = dict(s0, **sched)
+        got = plan.schedule
+        for k, v in sched.items():
+            assert got[k] == v, (sched, got)
+        info = plan.info
+        assert info["tile_qubits"] == got["tile_qubits"]
+        seen.add((info["fwd_passes"], info["adj_passes"], got["tile_qubits"]))
+        E, gx, gw = capi.qtm_debug_emulate(plan.handle, inp.x, inp.w, inp.gE, circuit=c)
+        for a, b in ((E, Eo), (gx, gxo), (gw, gwo)):
+            assert np.max(np.abs(a - b)) < 1e-11, sched
+    assert len(seen) >= 3   # the tile widths give different schedules
+    before = plan.schedule
+    for bad in ({"phase_mode": 3}, {"tile_qubits": 8}, {"low_min": 3}, {"minb_fwd": 0}, {"kernels": 2}):
+        with pytest.raises(capi.QtmError) as ei:
+            plan.schedule = dict(before, **bad)
+        assert ei.value.status == capi.QTM_EINVAL
+    assert plan.schedule == before
+    small = capi.Plan(W.workload_4q(), dtype="c128")
+    assert small.schedule["tile_qubits"] == 4
+    with pytest.raises(capi.QtmError) as ei:
+        small.schedule = {"kernels": 1}
+    assert ei.value.status == capi.QTM_EUNSUPPORTED

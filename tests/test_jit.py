@@ -273,3 +273,32 @@ def test_compiled_plan_with_h_and_rzz(n):
     for what, g, r in zip(("E", "gx", "gw"), got, (Eo, gxo, gwo)):
         err = float(np.max(np.abs(g - r))) if r.size else 0.0
         assert err <= 1e-5, f"n={n} {what}: {err:.3e}"
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("builder,B", [("workload_12q", 256), ("workload_16q_train", 8)])
+def test_tune_single_plan_and_cache(builder, B, tmp_path):
+    """qtm_tune times candidate schedules (phase grouping, tile widths of a
+    multi-tile state, register budgets, kernel kind), applies the fastest and
+    records it; a second plan of the same circuit and batch applies the
+    cached choice without timing (no new cache line); the tuned plan matches
+    the oracle."""
+    import json
+    import torch
+    c = getattr(W, builder)()
+    inp = W.make_inputs(c, B, 41, real_dtype=np.float32)
+    f32 = dict(dtype=torch.float32, device="cuda")
+    x, w, g = (torch.tensor(a, **f32) for a in (inp.x, inp.w, inp.gE))
+    cache = str(tmp_path / "tune.jsonl")
+    plan = capi.Plan(c, dtype="c64")
+    sched = plan.tune(x, w, g, cache_path=cache)
+    lines = [json.loads(l) for l in open(cache)]
+    assert len(lines) == 1 and all(lines[0][k] == sched[k] for k in capi.SCHEDULE_FIELDS)
+    plan2 = capi.Plan(c, dtype="c64")
+    assert plan2.tune(x, w, g, cache_path=cache) == sched
+    assert len(open(cache).readlines()) == 1
+    got = _run(plan2, c, inp)
+    Eo = oracle.forward(c, inp.x[:4], inp.w, threads=0)
+    _, gxo, gwo = oracle.adjoint(c, inp.gE[:4], inp.x[:4], inp.w, threads=0)
+    for what, a, r in zip(("E", "gx", "gw"), got, (Eo, gxo, gwo)):
+        assert np.max(np.abs(a[:4] - r)) <= 1e-5, (builder, what)

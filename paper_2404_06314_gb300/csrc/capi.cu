@@ -826,11 +826,15 @@ qtm_status composite_adjoint(qtm_plan *p, int B, const void *gE, const void *x, 
     return QTM_OK;
 }
 
-// Observables per reverse sweep of qtm_jacobian.  One-tile plans (one CTA
-// per pseudo-sample) take every observable at once, so that B * M CTAs fill
-// the GPU; plans whose state spans several tiles take as many as keep the
-// chunk's phi and lam within three quarters of L2 (at least one).
+// Observables per reverse sweep of qtm_jacobian: all of them, so that a
+// single reverse launch covers every (sample, observable), unless the
+// pseudo-samples' states (phi and lam) would pass kJacobianStateBudget; then
+// as many as fit (at least one).  The passes are ALU-bound even with the
+// states in HBM: at 16 qubits, B = 96 and 16 observables one chunk of 16
+// took 5.99 ms against 6.32 (chunks of 4) and 7.94 ms (one per sweep).
 // QTM_JAC_CHUNK=<c> (a tuning switch) sets it.
+constexpr double kJacobianStateBudget = 8.0 * (1ull << 30);
+
 int jacobian_chunk(const qtm_plan *p, int B)
 {
     const Plan &P = p->P;
@@ -839,11 +843,9 @@ int jacobian_chunk(const qtm_plan *p, int B)
     if (const char *e = std::getenv("QTM_JAC_CHUNK")) {
         const int v = std::atoi(e);
         if (v >= 1) c = std::min(v, M);
-    } else if (P.tiles_per_sample > 1) {
-        int l2 = 0;
-        cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, p->device);
+    } else {
         const double per = (double)B * std::ldexp((double)elem_bytes(P.dtype), P.state_qubits) * (p->needs_lam ? 2 : 1);
-        c = std::max(1, std::min(M, (int)(0.75 * (double)l2 / per)));
+        c = std::max(1, std::min(M, (int)(kJacobianStateBudget / per)));
     }
     // the pseudo-batch stays within the batch sizes the kernels index with int
     while (c > 1 && (long long)B * c > (1LL << 24)) c = (c + 1) / 2;

@@ -232,8 +232,11 @@ size_t pass_smem_bytes(int K, int dtype, bool reverse, int nslots, int n_terms, 
 cudaError_t launch_pass(int dtype, bool reverse, const PassArgs &a, const CUtensorMap &tm_phi,
                         const CUtensorMap &tm_lam, cudaStream_t s)
 {
+    // a tile below 9 qubits has fewer than 32 threads' worth of registers; the
+    // CTA still takes a full warp, whose other lanes share the staging, the
+    // per-sample prep and the finalize but skip the phases (pass_body)
     const int T = 1 << (a.K - 4);
-    const dim3 grid((unsigned)a.B * (unsigned)a.tiles), block((unsigned)T);
+    const dim3 grid((unsigned)a.B * (unsigned)a.tiles), block((unsigned)(T < 32 ? 32 : T));
     const size_t smem = (size_t)a.smem_bytes;
     cudaError_t e;
 #define QTM_LAUNCH(R, REV)                                                                     \

@@ -957,7 +957,7 @@ __device__ __forceinline__ void pass_body(const PassArgs &a, const CUtensorMap *
     }
 
     TileJob j;
-    j.T = blockDim.x;
+    j.T = 1 << (a.K - 4);   // threads holding the tile's amplitudes (the CTA may have more)
     j.K = a.K; j.l = a.l; j.h = a.h; j.m = a.m; j.sq = a.state_qubits;
     j.base = (gap << a.l) | (rest << (a.h + a.m));
     j.ops = a.ops; j.diag = a.diag; j.phases = a.phases;

@@ -413,3 +413,19 @@ def test_jacobian_chunks_of_observables(n, dtype, compiled, chunk, monkeypatch):
     E = plan.forward(x, w)
     plan.sync()
     assert_close(E.double().cpu().numpy(), oracle.forward(c, inp.x, inp.w, threads=0), TOL[dtype], "E after J")
+
+
+def test_fma_rate_probe():
+    """qtm_debug_fma_rate (the bench's FP64 roofline denominator) measures a
+    plausible FMA throughput: FP32 within (10, 200) TFLOP/s on a GPU whose
+    derived peak is about 80, FP64 positive and below FP32."""
+    import ctypes
+    L = capi.lib()
+    L.qtm_debug_fma_rate.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+    L.qtm_debug_fma_rate.restype = ctypes.c_int
+    r32, r64 = ctypes.c_double(), ctypes.c_double()
+    assert L.qtm_debug_fma_rate(capi.QTM_C64, ctypes.byref(r32)) == capi.QTM_OK
+    assert L.qtm_debug_fma_rate(capi.QTM_C128, ctypes.byref(r64)) == capi.QTM_OK
+    assert 10e12 < r32.value < 200e12, r32.value
+    assert 0 < r64.value < r32.value, (r64.value, r32.value)
+    assert L.qtm_debug_fma_rate(7, ctypes.byref(r64)) == capi.QTM_EINVAL

@@ -964,6 +964,7 @@ void drop_stored_forward(qtm_plan *p)
 
 qtm_status qtm_forward(qtm_plan *p, int B, const void *x, const void *w, void *expvals, void *stream)
 {
+    NvtxRange nvtx_range("qtm_forward");
     if (!p) return QTM_EINVAL;
     qtm_status bs = check_batch(p, B);
     if (bs != QTM_OK) return bs;
@@ -1013,6 +1014,7 @@ qtm_status qtm_forward(qtm_plan *p, int B, const void *x, const void *w, void *e
 qtm_status qtm_adjoint(qtm_plan *p, int B, const void *gE, const void *x, const void *w, void *gx,
                        void *gw, int flags, void *stream)
 {
+    NvtxRange nvtx_range("qtm_adjoint");
     if (!p) return QTM_EINVAL;
     qtm_status bs = check_batch(p, B);
     if (bs != QTM_OK) return bs;
@@ -1120,6 +1122,7 @@ qtm_status qtm_debug_fma_rate(int dtype, double *flops_per_s)
 
 qtm_status qtm_jacobian(qtm_plan *p, int B, const void *x, const void *w, void *jac, void *stream)
 {
+    NvtxRange nvtx_range("qtm_jacobian");
     if (!p) return QTM_EINVAL;
     qtm_status bs = check_batch(p, B);
     if (bs != QTM_OK) return bs;
@@ -1238,6 +1241,7 @@ qtm_status compile_all(qtm_plan *p, std::vector<std::vector<char>> &fwd_bin, std
 
 qtm_status qtm_compile(qtm_plan *p, int flags)
 {
+    NvtxRange nvtx_range("qtm_compile");
     if (!p) return QTM_EINVAL;
     if (is_composite(p)) {
         for (qtm_plan *part : p->parts) {
@@ -1305,6 +1309,7 @@ qtm_status qtm_get_schedule(const qtm_plan *p, qtm_schedule *sched)
 
 qtm_status qtm_set_schedule(qtm_plan *p, const qtm_schedule *sched)
 {
+    NvtxRange nvtx_range("qtm_set_schedule");
     if (!p || !sched) return QTM_EINVAL;
     if (is_composite(p) || p->P.path != QTM_PATH_FUSED)
         return fail(p, QTM_EUNSUPPORTED, "schedules apply to single fused plans");
@@ -1372,6 +1377,7 @@ qtm_status qtm_set_schedule(qtm_plan *p, const qtm_schedule *sched)
 qtm_status qtm_tune(qtm_plan *p, int B, const void *x, const void *w, const void *gE, void *stream,
                     const char *cache_path)
 {
+    NvtxRange nvtx_range("qtm_tune");
     if (!p) return QTM_EINVAL;
     if (is_composite(p) || p->P.path != QTM_PATH_FUSED)
         return fail(p, QTM_EUNSUPPORTED, "schedules apply to single fused plans");

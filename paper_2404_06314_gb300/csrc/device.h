@@ -3,10 +3,22 @@
 
 #include <cuda.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "plan.h"
 
 namespace qtm {
+
+// An NVTX range around one C-ABI call (named by the entry point), so that
+// profilers that read NVTX (ncu --nvtx, nsys) attribute kernels to calls;
+// without such a tool attached the calls do nothing measurable.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+
 
 struct FinalizeArgs {
     int B, M, tiles, n_runs, n_rots, P, n_in;

@@ -928,6 +928,7 @@ qtm_status qtm_multi_offsets(const qtm_multi *m, int which, int64_t *offsets)
 qtm_status qtm_multi_run(qtm_multi *m, const void *x, const void *w, const void *gE, void *E, void *gx,
                          void *gw, int flags, void *stream)
 {
+    NvtxRange nvtx_range("qtm_multi_run");
     if (!m || !x || !w || !gE || !E || !gx || !gw) return QTM_EINVAL;
     if (flags & ~QTM_MULTI_GRAPH) return QTM_EINVAL;
     m->fwd_valid = false;   // the run reuses the state buffers
@@ -936,6 +937,7 @@ qtm_status qtm_multi_run(qtm_multi *m, const void *x, const void *w, const void 
 
 qtm_status qtm_multi_forward(qtm_multi *m, const void *x, const void *w, void *E, int flags, void *stream)
 {
+    NvtxRange nvtx_range("qtm_multi_forward");
     if (!m || !x || !w || !E) return QTM_EINVAL;
     if (flags & ~QTM_MULTI_GRAPH) return QTM_EINVAL;
     m->fwd_valid = false;
@@ -951,6 +953,7 @@ qtm_status qtm_multi_forward(qtm_multi *m, const void *x, const void *w, void *E
 qtm_status qtm_multi_adjoint(qtm_multi *m, const void *x, const void *w, const void *gE, void *gx, void *gw,
                              int flags, void *stream)
 {
+    NvtxRange nvtx_range("qtm_multi_adjoint");
     if (!m || !x || !w || !gE || !gx || !gw) return QTM_EINVAL;
     if (flags & ~(QTM_MULTI_GRAPH | QTM_MULTI_RECOMPUTE)) return QTM_EINVAL;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -971,6 +974,7 @@ qtm_status qtm_multi_adjoint(qtm_multi *m, const void *x, const void *w, const v
 qtm_status qtm_multi_tune(qtm_multi *m, const void *x, const void *w, const void *gE, void *E, void *gx,
                           void *gw, void *stream, const char *cache_path)
 {
+    NvtxRange nvtx_range("qtm_multi_tune");
     if (!m || !x || !w || !gE || !E || !gx || !gw) return QTM_EINVAL;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const std::string sig = signature(m);

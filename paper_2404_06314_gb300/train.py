@@ -22,8 +22,12 @@ def setup_qnn16(B: int = 256, seed: int = W.WORKLOAD_SEEDS["qnn16_l8_train"], de
     return c, inp, y, mod, x, t
 
 
-def train(mod: QuantumModule, x: torch.Tensor, t: torch.Tensor, steps: int, lr: float = 1e-2):
-    opt = torch.optim.Adam(mod.parameters(), lr=lr)
+def train(mod: QuantumModule, x: torch.Tensor, t: torch.Tensor, steps: int, lr: float = 1e-2,
+          opt: torch.optim.Optimizer = None):
+    """`steps` Adam steps (a new optimizer unless `opt` continues one, e.g.
+    after load_checkpoint); returns the losses as one device tensor."""
+    if opt is None:
+        opt = torch.optim.Adam(mod.parameters(), lr=lr)
     losses = []
     for _ in range(steps):
         opt.zero_grad(set_to_none=True)
@@ -33,3 +37,19 @@ def train(mod: QuantumModule, x: torch.Tensor, t: torch.Tensor, steps: int, lr: 
         opt.step()
         losses.append(loss.detach())
     return torch.stack(losses)
+
+
+def save_checkpoint(path: str, mod: torch.nn.Module, opt: torch.optim.Optimizer, step: int) -> None:
+    """Everything a resumed run needs: the module's parameters, the
+    optimizer's state (Adam moments and step counts) and the step reached.
+    The plan itself is rebuilt from the circuit (it holds no trained state)."""
+    torch.save({"module": mod.state_dict(), "optimizer": opt.state_dict(), "step": int(step)}, path)
+
+
+def load_checkpoint(path: str, mod: torch.nn.Module, opt: torch.optim.Optimizer) -> int:
+    """Restore what save_checkpoint wrote into a module and optimizer built
+    the same way; returns the step reached."""
+    ck = torch.load(path, map_location=next(mod.parameters()).device, weights_only=True)
+    mod.load_state_dict(ck["module"])
+    opt.load_state_dict(ck["optimizer"])
+    return int(ck["step"])

@@ -111,3 +111,28 @@ def test_hybrid_module_chain_rule():
     _, gx, gw = oracle.adjoint(c, gE, h, w, threads=0)
     assert np.max(np.abs(pre.weight.grad.cpu().numpy() - gx.T @ x.cpu().numpy())) < 1e-11
     assert np.max(np.abs(q.weights.grad.cpu().numpy() - gw.sum(0))) < 1e-11
+
+
+def test_training_checkpoint_resume_matches_uninterrupted(tmp_path):
+    """Checkpoint/resume of the 16-qubit training loop: 3 Adam steps, a
+    checkpoint (parameters, Adam state, step), a fresh module and optimizer
+    restored from it, 3 more steps; the losses equal those of 6 uninterrupted
+    steps bit for bit (the kernels' reductions have a fixed order)."""
+    import torch
+    from paper_2404_06314_gb300 import train as T
+    c, inp, y, mod, x, t = T.setup_qnn16(B=32)
+    opt = torch.optim.Adam(mod.parameters(), lr=1e-2)
+    straight = T.train(mod, x, t, steps=6, opt=opt).cpu().numpy()
+    _, _, _, mod_a, _, _ = T.setup_qnn16(B=32)
+    opt_a = torch.optim.Adam(mod_a.parameters(), lr=1e-2)
+    first = T.train(mod_a, x, t, steps=3, opt=opt_a).cpu().numpy()
+    path = str(tmp_path / "ck.pt")
+    T.save_checkpoint(path, mod_a, opt_a, 3)
+    _, _, _, mod_b, _, _ = T.setup_qnn16(B=32)
+    with torch.no_grad():
+        for prm in mod_b.parameters():
+            prm.add_(1.0)   # a different starting point, overwritten by the checkpoint
+    opt_b = torch.optim.Adam(mod_b.parameters(), lr=1e-2)
+    assert T.load_checkpoint(path, mod_b, opt_b) == 3
+    second = T.train(mod_b, x, t, steps=3, opt=opt_b).cpu().numpy()
+    assert np.array_equal(np.concatenate([first, second]), straight)

@@ -1,8 +1,8 @@
 """qtm_forward_noalloc, the allocation-free forward (for callers that cannot
 call cudaMalloc: programs whose GPU memory another allocator owns with a fixed
 budget, loops that must not stall on an allocation), against qtm_forward
-through the C ABI, on two calls in a row; the second call must leave the
-device's free memory unchanged.
+(and the FP64 oracle on a few rows) through the C ABI, on two calls in a row;
+the second call must leave the device's free memory unchanged.
 
 This file sorts last so that a run stopping at its first failure has already
 run every other test; it also passes alone in a fresh process."""
@@ -11,6 +11,7 @@ import ctypes
 import numpy as np
 import pytest
 
+import oracle
 from paper_2404_06314_gb300 import capi, workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -44,6 +45,9 @@ def test_forward_noalloc_matches_forward_twice():
             assert torch.cuda.mem_get_info()[0] == free_before, f"call {call} changed free device memory"
         err = (E_na.double() - E_ref.double()).abs().max().item()
         assert err <= TOL, f"call {call}: max abs diff {err:.3e}"
+        rows = [0, B // 2, B - 1]   # and directly against the FP64 oracle on a few rows
+        Eo = oracle.forward(c, inp.x[rows], inp.w, threads=0)
+        assert np.abs(E_na.double().cpu().numpy()[rows] - Eo).max() <= TOL, f"call {call}: vs oracle"
 
 
 def test_forward_noalloc_rejects_oversized_batch_and_unsupported_plans():

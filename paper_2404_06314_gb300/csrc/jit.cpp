@@ -351,8 +351,13 @@ void gen_fill_cpx(std::ostringstream &o, const Plan &P, const PassDesc &pd, int 
 }
 
 // One op of a complex-pair phase (register group lo); `slot` is the C
-// expression of its run slot.
-void cpx_op(std::ostringstream &o, const Plan &P, const PassDesc &pd, int k, int lo, const std::string &slot)
+// expression of its run slot.  deferred (reverse phases): GRAD ops keep their
+// reduced sums in registers vr[i] and the phase stores them at its end (slot
+// expressions collected here), so no shared store waits on a reduction
+// between one run's gradient and the next run's table loads (12 qubits:
+// reverse pass 287 -> 280 us).
+void cpx_op(std::ostringstream &o, const Plan &P, const PassDesc &pd, int k, int lo, const std::string &slot,
+            std::vector<std::string> *deferred = nullptr)
 {
     const bool rev = pd.reverse != 0;
     const int nslots = pd.slot_end - pd.slot_begin;
@@ -372,10 +377,15 @@ void cpx_op(std::ostringstream &o, const Plan &P, const PassDesc &pd, int k, int
         o << "        u2_cpx<" << rb << ">(p, " << tab << ");\n";
         break;
     case OP_GRAD:
-        o << "        { float vx, vy, vz; grad_cpx<" << rb << ">(p, q, vx, vy, vz);"
-          << " const float v = warp_sum3(vx, vy, vz, lane);"
-          << " if ((lane & 7) == 0 && lane < 24) S.redG[warp * " << 3 * nslots << " + 3 * " << slot
-          << " + (lane >> 3)] = v;";
+        o << "        { float vx, vy, vz; grad_cpx<" << rb << ">(p, q, vx, vy, vz);";
+        if (deferred) {
+            o << " vr[" << deferred->size() << "] = warp_sum3(vx, vy, vz, lane);";
+            deferred->push_back(slot);
+        } else {
+            o << " const float v = warp_sum3(vx, vy, vz, lane);"
+              << " if ((lane & 7) == 0 && lane < 24) S.redG[warp * " << 3 * nslots << " + 3 * " << slot
+              << " + (lane >> 3)] = v;";
+        }
         if (!(op.flags & OPF_SKIP_APPLY))
             o << " u2_cpx<" << rb << ">(p, " << tab << "); u2_cpx<" << rb << ">(q, " << tab << ");";
         o << " }\n";
@@ -417,7 +427,20 @@ std::string phase_body(const Plan &P, const PassDesc &pd, const DevPhase &phs, b
     } else {
         o << "        regs_load_cpx<LO, " << (lam_valid ? "true" : "false") << ">(p, q, S, xt);\n";
     }
-    for (int k = phs.op_begin; k < phs.op_end; ++k) cpx_op(o, P, pd, k, lo, slot(P.ops[k].slot));
+    std::vector<std::string> deferred;
+    const bool defer = rev;
+    int ngrad = 0;
+    for (int k = phs.op_begin; k < phs.op_end; ++k) ngrad += P.ops[k].type == OP_GRAD;
+    if (defer && ngrad) o << "        float vr[" << ngrad << "];\n";
+    for (int k = phs.op_begin; k < phs.op_end; ++k)
+        cpx_op(o, P, pd, k, lo, slot(P.ops[k].slot), defer && ngrad ? &deferred : nullptr);
+    if (!deferred.empty()) {
+        const int nslots = pd.slot_end - pd.slot_begin;
+        o << "        if ((lane & 7) == 0 && lane < 24) {";
+        for (size_t i = 0; i < deferred.size(); ++i)
+            o << " S.redG[warp * " << 3 * nslots << " + 3 * " << deferred[i] << " + (lane >> 3)] = vr[" << i << "];";
+        o << " }\n";
+    }
     o << "        regs_store_cpx<LO, " << (rev ? "true" : "false") << ">(p, q, S, xt);\n";
     return o.str();
 }

@@ -828,6 +828,32 @@ __device__ __forceinline__ void run_phases(const TileJob &j, const TileSmem<R> &
     }
 }
 
+// Sum of the per-warp partials p[0], p[stride], ... (nwarps of them) in
+// FP64 precision.  Complex64 plans add them in FP32 with Knuth's TwoSum,
+// carrying each addition's rounding error, and convert once: the same result
+// as FP64 additions up to the FP32 rounding of the carried error, with three
+// FP64 operations instead of 2 x nwarps (the FP64 pipe runs at 1/64 of the
+// FP32 rate on this GPU).
+template <typename R>
+__device__ __forceinline__ double sum_warps(const R *p, int stride, int nwarps)
+{
+    if constexpr (sizeof(R) == 8) {
+        double s = 0.0;
+        for (int w = 0; w < nwarps; ++w) s += (double)p[w * stride];
+        return s;
+    } else {
+        float s = 0.f, e = 0.f;
+        for (int w = 0; w < nwarps; ++w) {
+            const float x = p[w * stride];
+            const float t = s + x;
+            const float z = t - s;
+            e += (s - (t - z)) + (x - z);
+            s = t;
+        }
+        return (double)s + (double)e;
+    }
+}
+
 // Per-tile partial sums: <O_m> partials (forward) or v per run (reverse).
 // Epart_row: [M] for this (sample, tile); Gpart_b: this sample's [n_runs][tiles][3].
 template <typename R, bool REV>
@@ -839,18 +865,15 @@ __device__ __forceinline__ void write_partials(const TileJob &j, const TileSmem<
     if (!REV) {
         if (!has_expval) return;
         for (int i = tid; i < j.M; i += T) {
-            double s = 0.0;
-            for (int w = 0; w < nwarps; ++w) s += (double)S.redE[w * j.M + i];
+            const double s = sum_warps<R>(S.redE + i, j.M, nwarps);
             Epart_row[i] = s;
             if (E_row) E_row[i] = (R)s;   // one tile per sample: the tile's sum is the value
         }
     } else {
         const int nv = 3 * j.nslots;
         for (int i = tid; i < nv; i += T) {
-            double s = 0.0;
-            for (int w = 0; w < nwarps; ++w) s += (double)S.redG[w * nv + i];
             const int run = j.slot_runs[i / 3];
-            Gpart_b[((size_t)run * tiles + tile) * 3 + (i % 3)] = s;
+            Gpart_b[((size_t)run * tiles + tile) * 3 + (i % 3)] = sum_warps<R>(S.redG + i, nv, nwarps);
         }
     }
 }

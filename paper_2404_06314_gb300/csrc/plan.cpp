@@ -57,17 +57,39 @@ inline void touched(const Node &nd, const std::vector<Run> &runs, int &a, int &b
     else { a = nd.ent.a; b = nd.ent.b; }
 }
 
+// Dependencies in circuit order.  CZ gates are diagonal and commute with one
+// another, so a CZ waits only for the last run or CNOT on each of its qubits,
+// and a run or CNOT waits for every CZ on its qubits since then; a CZ ring
+// therefore does not chain around the qubits, and a register group can apply
+// its part of a ring as soon as its neighbours' runs are done.
 void build_deps(std::vector<Node> &nodes, const std::vector<Run> &runs, int n)
 {
-    std::vector<int> last(n, -1);
+    std::vector<int> last(n, -1);                  // last run / CNOT on the qubit
+    std::vector<std::vector<int>> diag(n);         // CZs on the qubit since then
+    auto add = [](std::vector<int> &v, int x) {
+        if (x >= 0 && std::find(v.begin(), v.end(), x) == v.end()) v.push_back(x);
+    };
     for (int i = 0; i < (int)nodes.size(); ++i) {
         int a, b;
         touched(nodes[i], runs, a, b);
-        nodes[i].preds.clear();
-        if (last[a] >= 0) nodes[i].preds.push_back(last[a]);
-        if (b >= 0 && last[b] >= 0 && last[b] != last[a]) nodes[i].preds.push_back(last[b]);
-        last[a] = i;
-        if (b >= 0) last[b] = i;
+        std::vector<int> &pr = nodes[i].preds;
+        pr.clear();
+        const bool cz = nodes[i].type == 1 && nodes[i].ent.kind == QTM_CZ;
+        for (int q : {a, b}) {
+            if (q < 0) continue;
+            add(pr, last[q]);
+            if (!cz)
+                for (int d : diag[q]) add(pr, d);
+        }
+        for (int q : {a, b}) {
+            if (q < 0) continue;
+            if (cz) {
+                diag[q].push_back(i);
+            } else {
+                last[q] = i;
+                diag[q].clear();
+            }
+        }
     }
 }
 

@@ -244,9 +244,12 @@ qtm_status qtm_jacobian(qtm_plan *plan, int B, const void *x, const void *w, voi
 qtm_status qtm_forward_noalloc(qtm_plan *plan, int B, const void *x, const void *w,
                                void *expvals, void *stream);
 
-/* Per-launch timing (profiling aid).  enable != 0: every later qtm_forward /
+/* Per-launch timing (profiling aid).  enable = 1: every later qtm_forward /
  * qtm_adjoint records a pair of CUDA events around each of its kernel
- * launches, on the call's stream.  enable == 0 stops recording. */
+ * launches, on the call's stream; enable = 2: only around the pass kernels
+ * of qtm_adjoint (each event between two kernels delays the second by a
+ * microsecond or two, so timing the dominant kernel alone perturbs the rest
+ * least); enable = 0 stops recording.  Other values: QTM_EINVAL. */
 qtm_status qtm_set_profiling(qtm_plan *plan, int enable);
 
 /* After the stream has been synchronised: the device durations (ms) of the

@@ -116,6 +116,10 @@ def lib(build_if_missing: bool = True):
         L.qtm_debug_jit_source.restype = ctypes.c_char_p
         L.qtm_debug_jit_compile.argtypes = [vp, i]
         L.qtm_debug_jit_compile.restype = ctypes.c_int
+        L.qtm_set_profiling.argtypes = [vp, i]
+        L.qtm_set_profiling.restype = ctypes.c_int
+        L.qtm_get_launch_times.argtypes = [vp, i, P(ctypes.c_float), P(ctypes.c_int), i, P(ctypes.c_int)]
+        L.qtm_get_launch_times.restype = ctypes.c_int
         _LIB = L
     return _LIB
 

@@ -76,6 +76,8 @@ struct qtm_plan {
     void *d_jkeep = nullptr, *d_jx = nullptr;
     size_t jkeep_bytes = 0, jx_bytes = 0;
     int32_t *d_gate_of_rot = nullptr;  // rotation id -> gate index
+    int32_t *d_rot_rep = nullptr;      // first rotation with the same angle definition (fused prep)
+    double2 *d_cs_shared = nullptr;    // [rots] FP64 (cos, sin) of half angles without an input (one call's)
     std::vector<CUtensorMap> tm_fwd, tm_rev_phi, tm_rev_lam;
     std::vector<TmGeom> g_fwd, g_rev;
     std::vector<size_t> smem_fwd, smem_rev;
@@ -96,7 +98,7 @@ struct qtm_plan {
     int jit_device = -1;
     std::string jit_src_cache;
     // profiling: events around each launch of the last forward / adjoint
-    bool profiling = false;
+    int profiling = 0;                 // 0 off, 1 every launch, 2 the adjoint's pass kernels only
     struct Rec { cudaEvent_t a, b; int kind; };
     std::vector<Rec> recs[2];
     // one event pool per kind of call, so that an adjoint's records do not
@@ -135,10 +137,11 @@ void free_tables(qtm_plan *p)
 {
     void *ptrs[] = {p->d_gate_of_rot, p->d_ops, p->d_diag, p->d_amap, p->d_phases, p->d_slot_runs, p->d_runs, p->d_rots,
                     p->d_prefix_run_of_q, p->d_prefix_ents, p->d_terms, p->d_pterms, p->d_w_ptr,
-                    p->d_w_rots, p->d_x_ptr, p->d_x_rots, p->d_status};
+                    p->d_w_rots, p->d_x_ptr, p->d_x_rots, p->d_status, p->d_rot_rep, p->d_cs_shared};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     p->d_gate_of_rot = nullptr;
+    p->d_rot_rep = nullptr; p->d_cs_shared = nullptr;
     p->d_ops = nullptr; p->d_diag = nullptr; p->d_amap = nullptr; p->d_phases = nullptr; p->d_slot_runs = nullptr; p->d_runs = nullptr;
     p->d_rots = nullptr; p->d_prefix_run_of_q = nullptr; p->d_prefix_ents = nullptr;
     p->d_terms = nullptr; p->d_pterms = nullptr; p->d_w_ptr = p->d_w_rots = p->d_x_ptr = p->d_x_rots = nullptr;
@@ -268,6 +271,16 @@ qtm_status ensure_device(qtm_plan *p)
         std::vector<int32_t> gor(P.rots.size());
         for (size_t r = 0; r < P.rots.size(); ++r) gor[r] = P.rots[r].gate;
         UP(p->d_gate_of_rot, gor);
+        // rotations with the same angle definition share one sine and cosine
+        std::vector<int32_t> rep(P.rots.size());
+        for (size_t i = 0; i < P.rots.size(); ++i) {
+            const Rot &a = P.rots[i];
+            size_t k = 0;
+            while (k < i && !(P.rots[k].coef == a.coef && P.rots[k].w_idx == a.w_idx && P.rots[k].x_idx == a.x_idx)) ++k;
+            rep[i] = (int32_t)k;
+        }
+        UP(p->d_rot_rep, rep);
+        UP(p->d_cs_shared, std::vector<double2>(P.rots.size()));
     }
 #undef UP
     p->device = dev;
@@ -382,6 +395,7 @@ struct ProfScope {
     ProfScope(qtm_plan *p_, int kind) : p(p_)
     {
         if (!p->profiling) return;
+        if (p->profiling == 2 && (p->cur_which != 1 || kind != 0)) return;   // reverse passes only
         r.a = prof_event(p);
         r.b = prof_event(p);
         r.kind = kind;
@@ -454,6 +468,27 @@ bool fuse_sample_steps(const qtm_plan *p)
     return p->P.path == QTM_PATH_FUSED && p->P.tiles_per_sample == 1;
 }
 
+// Fused prep with shared sines and cosines (prep_sample_shared): the first
+// forward pass of a one-tile plan starts from the analytic state, so its idle
+// tile holds the per-sample pairs.  QTM_PREP_SHARED=0 (a tuning switch)
+// computes every rotation's pair per sample.
+bool prep_shared(const qtm_plan *p)
+{
+    const Plan &P = p->P;
+    const char *e = std::getenv("QTM_PREP_SHARED");
+    return fuse_sample_steps(p) && !P.fwd.empty() && !(e && *e == '0') && P.fwd[0].phi_src == SRC_ANALYTIC &&
+           P.rots.size() * sizeof(double2) <= ((size_t)elem_bytes(P.dtype) << P.fwd[0].K);
+}
+
+// ... which launches one per-call kernel when some rotation has no input.
+bool prep_shared_launches(const qtm_plan *p)
+{
+    if (!prep_shared(p)) return false;
+    for (const Rot &r : p->P.rots)
+        if (r.x_idx < 0) return true;
+    return false;
+}
+
 void set_prep_fields(qtm_plan *p, PassArgs &a)
 {
     const Plan &P = p->P;
@@ -475,11 +510,21 @@ qtm_status run_forward_passes(qtm_plan *p, int B, const void *x, const void *w, 
         qtm_status st = run_prep(p, B, x, w, s);
         if (st != QTM_OK) return st;
     }
+    const bool shared = prep_shared(p);
+    if (shared) {
+        if (prep_shared_launches(p)) {
+            ProfScope ps(p, 1);
+            cudaError_t e = launch_prep_shared(P.dtype, p->d_rots, p->d_rot_rep, (int)P.rots.size(), w,
+                                               p->d_cs_shared, s);
+            if (e != cudaSuccess) return cuda_fail(p, e, "shared prep launch");
+        }
+    }
     for (size_t i = 0; i < P.fwd.size(); ++i) {
         PassArgs a = pass_args(p, P.fwd[i], p->g_fwd[i], p->smem_fwd[i], B, x, w, nullptr);
         if (fused && i == 0) {
             set_prep_fields(p, a);
             a.prep_fused = 1;
+            if (shared) { a.rot_rep = p->d_rot_rep; a.cs_shared = p->d_cs_shared; }
         }
         if (fused) a.E_out = expvals;
         ProfScope ps(p, 0);
@@ -921,7 +966,7 @@ qtm_status qtm_get_plan_info(const qtm_plan *p, qtm_plan_info *info)
         // strings add two launches forward and one to the adjoint.
         const bool one_tile = P.tiles_per_sample == 1 && !P.fwd.empty();
         const int xy = P.pterms.empty() ? 0 : 1;
-        info->fwd_launches = (int)P.fwd.size() + (one_tile ? 0 : 2) + 2 * xy;
+        info->fwd_launches = (int)P.fwd.size() + (one_tile ? 0 : 2) + 2 * xy + (prep_shared_launches(p) ? 1 : 0);
         info->adj_launches = (int)P.rev.size() + (one_tile ? 0 : 1) + xy;
     } else {
         int nrot = 0;
@@ -1539,7 +1584,8 @@ qtm_status qtm_sync(qtm_plan *p, void *stream)
 qtm_status qtm_set_profiling(qtm_plan *p, int enable)
 {
     if (!p) return QTM_EINVAL;
-    p->profiling = enable != 0;
+    if (enable < 0 || enable > 2) return QTM_EINVAL;
+    p->profiling = enable;
     return QTM_OK;
 }
 

@@ -60,6 +60,10 @@ cudaError_t launch_pass(int dtype, bool reverse, const PassArgs &a, const CUtens
                         const CUtensorMap &tm_lam, cudaStream_t s);
 cudaError_t launch_expval_finalize(int dtype, const FinalizeArgs &f, cudaStream_t s);
 cudaError_t launch_grad_finalize(int dtype, const FinalizeArgs &f, cudaStream_t s);
+// FP64 (cos, sin) of the half angles of the rotations without an input,
+// at cs_shared[i] for each i with rep[i] == i.
+cudaError_t launch_prep_shared(int dtype, const Rot *rots, const int32_t *rep, int n_rots, const void *w,
+                               double2 *cs_shared, cudaStream_t s);
 cudaError_t launch_gw_reduce(int dtype, const double *gw_ws, int B, int P, void *gw,
                              cudaStream_t s);
 

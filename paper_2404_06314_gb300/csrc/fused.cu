@@ -34,6 +34,23 @@ __global__ void k_prep(const PrepArgs a)
                    a.cs ? a.cs + (size_t)b * a.n_rots : nullptr);
 }
 
+// FP64 (cos, sin) of the half angles of the rotations without an input (the
+// same for every sample of a call), one thread per distinct angle.
+template <typename R>
+__global__ void k_prep_shared(const Rot *rots, const int32_t *rep, int n_rots, const R *w, double2 *cs_shared)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_rots || rep[i] != i) return;
+    const Rot ro = rots[i];
+    if (ro.x_idx >= 0) return;
+    double t = ro.coef;
+    if (ro.w_idx >= 0) t *= (double)w[ro.w_idx];
+    double s, c;
+    sincos(0.5 * t, &s, &c);
+    cs_shared[i] = double2{c, s};
+}
+
+
 template <typename R, bool REV>
 __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 1 : (REV ? 2 : 3)) k_pass(const __grid_constant__ PassArgs a,
                                               const __grid_constant__ CUtensorMap tm_phi,
@@ -72,8 +89,6 @@ __global__ void k_grad_finalize(const FinalizeArgs f)
                             f.cs ? f.cs + (size_t)b * f.n_rots : nullptr);
 }
 
-// grad_w[j] = sum_b gw_ws[b][j]: one CTA per weight, each thread a fixed
-// strided subset of samples, then a fixed-shape tree: deterministic.
 // dst[i] += src[i] (composite plans: sum of the parts' outputs, part order)
 template <typename R>
 __global__ void k_accumulate(const R *src, R *dst, size_t n)
@@ -93,20 +108,24 @@ __global__ void k_accumulate_cols(const R *src, int Gs, R *dst, int Gd, size_t r
     }
 }
 
+// grad_w[j] = sum_b gw_ws[b][j]: one CTA per weight; each thread sums a fixed
+// strided subset of the samples, each warp a fixed shuffle butterfly, and the
+// first thread the warps' sums in warp order: the same order on every run.
 template <typename R>
 __global__ void k_gw_reduce(const double *gw_ws, int B, int P, R *gw)
 {
-    __shared__ double red[256];
-    const int j = blockIdx.x;
+    __shared__ double red[32];
+    const int j = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     double s = 0.0;
     for (int b = threadIdx.x; b < B; b += blockDim.x) s += gw_ws[(size_t)b * P + j];
-    red[threadIdx.x] = s;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) red[warp] = s;
     __syncthreads();
-    for (int w = blockDim.x >> 1; w > 0; w >>= 1) {
-        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
-        __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        gw[j] = (R)t;
     }
-    if (threadIdx.x == 0) gw[j] = (R)red[0];
 }
 
 // Jacobian pseudo-samples: row b' = b * cc + k of a chunk stands for sample
@@ -259,6 +278,18 @@ cudaError_t launch_prep(int dtype, const PrepArgs &a, cudaStream_t s)
 {
     if (dtype == QTM_C128) k_prep<double><<<a.B, 128, 0, s>>>(a);
     else k_prep<float><<<a.B, 128, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prep_shared(int dtype, const Rot *rots, const int32_t *rep, int n_rots, const void *w,
+                               double2 *cs_shared, cudaStream_t s)
+{
+    if (n_rots <= 0) return cudaSuccess;
+    const int blk = 64, grd = (n_rots + blk - 1) / blk;   // a few warps on as many SMs
+    if (dtype == QTM_C128)
+        k_prep_shared<double><<<grd, blk, 0, s>>>(rots, rep, n_rots, static_cast<const double *>(w), cs_shared);
+    else
+        k_prep_shared<float><<<grd, blk, 0, s>>>(rots, rep, n_rots, static_cast<const float *>(w), cs_shared);
     return cudaGetLastError();
 }
 

@@ -198,6 +198,12 @@ struct PassArgs {
     // the expectation values [B][M] (plan real type) here, so no separate
     // finalize runs; null otherwise.
     void *E_out;
+    // Fused prep of complex64 plans (may be null): rot_rep[i] is the first
+    // rotation with rotation i's coefficient, weight and input (the same angle
+    // for every sample), and cs_shared[rot_rep[i]] the FP64 (cos, sin) of the
+    // half angle of a rotation without an input, computed once per call.
+    const int32_t *rot_rep;
+    const void *cs_shared;
 };
 
 }  // namespace qtm

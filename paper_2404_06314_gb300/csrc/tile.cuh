@@ -344,6 +344,24 @@ __host__ __device__ inline Layout make_layout(int K, int csize, bool rev, int ns
 // and R U costs two complex products: a <- alpha a - conj(beta) b,
 // b <- beta a + conj(alpha) b.  cs (may be null): each rotation's
 // (cos(t/2), sin(t/2)), indexed like rots.
+// (a, b) <- R (a, b) for R = R_kind(t), c = cos(t/2), s = sin(t/2).
+__device__ __forceinline__ void su2_rotate(int kind, double c, double s, double2 &a, double2 &b)
+{
+    double2 na, nb;
+    if (kind == QTM_RX) {          // a' = c a - i s b, b' = -i s a + c b
+        na = {c * a.x + s * b.y, c * a.y - s * b.x};
+        nb = {s * a.y + c * b.x, c * b.y - s * a.x};
+    } else if (kind == QTM_RY) {   // a' = c a - s b, b' = s a + c b
+        na = {c * a.x - s * b.x, c * a.y - s * b.y};
+        nb = {s * a.x + c * b.x, s * a.y + c * b.y};
+    } else {                       // a' = (c - i s) a, b' = (c + i s) b
+        na = {c * a.x + s * a.y, c * a.y - s * a.x};
+        nb = {c * b.x - s * b.y, c * b.y + s * b.x};
+    }
+    a = na;
+    b = nb;
+}
+
 template <typename R>
 __device__ void run_matrix_f64(const Run rr, const Rot *rots, const R *xb, const R *w, double2 *U, double2 *cs)
 {
@@ -356,23 +374,10 @@ __device__ void run_matrix_f64(const Run rr, const Rot *rots, const R *xb, const
         double s, c;
         sincos(0.5 * t, &s, &c);
         if (cs) cs[i] = double2{c, s};
-        double2 na, nb;
-        if (ro.kind == QTM_RX) {          // a' = c a - i s b, b' = -i s a + c b
-            na = {c * a.x + s * b.y, c * a.y - s * b.x};
-            nb = {s * a.y + c * b.x, c * b.y - s * a.x};
-        } else if (ro.kind == QTM_RY) {   // a' = c a - s b, b' = s a + c b
-            na = {c * a.x - s * b.x, c * a.y - s * b.y};
-            nb = {s * a.x + c * b.x, s * a.y + c * b.y};
-        } else {                          // a' = (c - i s) a, b' = (c + i s) b
-            na = {c * a.x + s * a.y, c * a.y - s * a.x};
-            nb = {c * b.x - s * b.y, c * b.y + s * b.x};
-        }
-        a = na;
-        b = nb;
+        su2_rotate(ro.kind, c, s, a, b);
     }
     U[0] = a; U[1] = double2{-b.x, b.y}; U[2] = b; U[3] = double2{a.x, -a.y};
 }
-
 
 // One CTA: every run's fused matrix for one sample (FP64, rounded once), and
 // the product-state tables T_j[v] = prod_{k<4} u_{4j+k}[bit k of v], u_q = U_prefix(q)|0>.
@@ -386,6 +391,62 @@ __device__ __forceinline__ void prep_sample(const Run *runs, const Rot *rots, co
         double2 U[4];
         const Run rr = runs[r];
         run_matrix_f64<R>(rr, rots, xb, w, U, cs_b);
+        for (int k = 0; k < 4; ++k) mats[4 * r + k] = {(R)U[k].x, (R)U[k].y};
+        if (rr.prefix) { ufac[2 * rr.q] = U[0]; ufac[2 * rr.q + 1] = U[2]; }
+    }
+    for (int q = threadIdx.x; q < sq; q += blockDim.x)
+        if (q >= n || prefix_run_of_q[q] < 0) { ufac[2 * q] = {1, 0}; ufac[2 * q + 1] = {0, 0}; }
+    __syncthreads();
+    const int ntab = (sq + 3) >> 2;
+    for (int i = threadIdx.x; i < ntab * 16; i += blockDim.x) {
+        const int j = i >> 4, v = i & 15;
+        double2 p{1, 0};
+        for (int k = 0; k < 4; ++k) {
+            const int q = 4 * j + k;
+            if (q < sq) {
+                const double2 u = ufac[2 * q + ((v >> k) & 1)];
+                p = double2{p.x * u.x - p.y * u.y, p.x * u.y + p.y * u.x};
+            }
+        }
+        tabs[i] = {(R)p.x, (R)p.y};
+    }
+}
+
+// prep_sample with the angles shared: sines and cosines of the rotations
+// without an input come from cs_shared (computed once per call), those of the
+// others once per distinct angle (rep[i] == i) into scratch (shared memory,
+// n_rots pairs); then every run's product as in run_matrix_f64.  Same
+// outputs as prep_sample, with FP64 sines and cosines per sample only for
+// distinct input-dependent angles (the FP64 pipe runs at 1/64 of the FP32
+// rate on this GPU).
+template <typename R>
+__device__ __forceinline__ void prep_sample_shared(const Run *runs, const Rot *rots, const int32_t *rep,
+                                                   const double2 *cs_shared, const int32_t *prefix_run_of_q,
+                                                   int n_runs, int n_rots, int n, int sq, const R *xb, const R *w,
+                                                   Cx<R> *mats, Cx<R> *tabs, double2 *ufac, double2 *cs_b,
+                                                   double2 *scratch)
+{
+    for (int i = threadIdx.x; i < n_rots; i += blockDim.x) {
+        const Rot ro = rots[i];
+        if (ro.x_idx < 0 || rep[i] != i) continue;
+        double t = ro.coef;   // the factor order of run_matrix_f64 (the same pair, bit for bit)
+        if (ro.w_idx >= 0) t *= (double)w[ro.w_idx];
+        t *= (double)xb[ro.x_idx];
+        double s, c;
+        sincos(0.5 * t, &s, &c);
+        scratch[i] = double2{c, s};
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < n_runs; r += blockDim.x) {
+        const Run rr = runs[r];
+        double2 a{1, 0}, b{0, 0};
+        for (int i = rr.rot_begin; i < rr.rot_end; ++i) {
+            const Rot ro = rots[i];
+            const double2 cs = ro.x_idx < 0 ? cs_shared[rep[i]] : scratch[rep[i]];
+            if (cs_b) cs_b[i] = cs;
+            su2_rotate(ro.kind, cs.x, cs.y, a, b);
+        }
+        const double2 U[4] = {a, double2{-b.x, b.y}, b, double2{a.x, -a.y}};
         for (int k = 0; k < 4; ++k) mats[4 * r + k] = {(R)U[k].x, (R)U[k].y};
         if (rr.prefix) { ufac[2 * rr.q] = U[0]; ufac[2 * rr.q + 1] = U[2]; }
     }
@@ -967,8 +1028,18 @@ __device__ __forceinline__ void pass_body(const PassArgs &a, const CUtensorMap *
     const uint32_t rest = tile >> gapbits;
 
     if constexpr (!REV) {
-        if (a.prep_fused) {   // this CTA's sample: run matrices and tables before anything reads them
-            __shared__ double2 ufac[2 * 32];
+        __shared__ double2 ufac[2 * 32];
+        if (a.prep_fused && a.rot_rep) {   // as below, sines and cosines shared; scratch: the idle tile
+            prep_sample_shared<R>(a.runs, a.rots, a.rot_rep, static_cast<const double2 *>(a.cs_shared), a.prq,
+                                  a.n_runs, a.n_rots, a.n, a.state_qubits,
+                                  static_cast<const R *>(a.x) + (size_t)b * a.n_in, static_cast<const R *>(a.w),
+                                  static_cast<Cx<R> *>(const_cast<void *>(a.mats)) + (size_t)b * a.n_runs * 4,
+                                  static_cast<Cx<R> *>(const_cast<void *>(a.tabs)) +
+                                      (size_t)b * ((a.state_qubits + 3) >> 2) * 16,
+                                  ufac, a.cs ? static_cast<double2 *>(a.cs) + (size_t)b * a.n_rots : nullptr,
+                                  reinterpret_cast<double2 *>(smem));
+            __syncthreads();
+        } else if (a.prep_fused) {   // this CTA's sample: run matrices and tables before anything reads them
             prep_sample<R>(a.runs, a.rots, a.prq, a.n_runs, a.n, a.state_qubits,
                            static_cast<const R *>(a.x) + (size_t)b * a.n_in, static_cast<const R *>(a.w),
                            static_cast<Cx<R> *>(const_cast<void *>(a.mats)) + (size_t)b * a.n_runs * 4,

@@ -261,10 +261,12 @@ def test_pauli_plans_refuse_noalloc():
 
 def test_plan_info_launch_counts_and_xy_costs():
     """Launch counts as the calls launch them (one-tile plans fuse the prep,
-    the expectation values and the gradient finalize into their passes) and
-    the cost model's share of strings with X/Y factors."""
+    the expectation values and the gradient finalize into their passes; the
+    forward adds one per-call kernel for the sines and cosines of the
+    rotations without an input) and the cost model's share of strings with
+    X/Y factors."""
     i12 = capi.Plan(W.workload_12q()).info
-    assert (i12["fwd_launches"], i12["adj_launches"]) == (i12["fwd_passes"], i12["adj_passes"])
+    assert (i12["fwd_launches"], i12["adj_launches"]) == (i12["fwd_passes"] + 1, i12["adj_passes"])
     i20 = capi.Plan(W.workload_20q()).info
     assert (i20["fwd_launches"], i20["adj_launches"]) == (i20["fwd_passes"] + 2, i20["adj_passes"] + 1)
     base = W.workload_12q()

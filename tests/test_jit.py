@@ -10,6 +10,7 @@ GPU part: a compiled plan gives the oracle's E, grad_x and per-sample grad_w
 within the complex64 bound (1e-5), the specialised kernels are the ones that
 ran (qtm_compiled_passes), and results agree with the general pass kernel's.
 """
+import ctypes
 import re
 
 import numpy as np
@@ -231,6 +232,58 @@ def test_compiled_plan_jacobian_and_full_batch():
     J = plan.jacobian(x, w).double().cpu().numpy()
     Jo = oracle.jacobian(c, inp.x[:2], inp.w, threads=0)
     assert np.max(np.abs(J - Jo)) <= 1e-5
+
+
+def _launches(plan, which):
+    L = capi.lib()
+    ms = (ctypes.c_float * 64)()
+    kinds = (ctypes.c_int * 64)()
+    cnt = ctypes.c_int()
+    assert L.qtm_get_launch_times(plan.handle, which, ms, kinds, 64, ctypes.byref(cnt)) == capi.QTM_OK
+    return [(ms[i], kinds[i]) for i in range(min(cnt.value, 64))]
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("builder", ["workload_12q", "workload_20q"])
+def test_profiled_launches_match_plan_info_and_shared_prep(builder, monkeypatch):
+    """Profiling mode 1 brackets every launch: the counts are the plan's
+    (batch-summed grad_w: one more in the adjoint); mode 2 only the adjoint's
+    pass kernels.  The per-call sines and cosines of rotations without an
+    input give the same results, bit for bit, as per-sample ones
+    (QTM_PREP_SHARED=0)."""
+    import torch
+    c = getattr(W, builder)()
+    B = 64 if builder == "workload_12q" else 2
+    inp = W.make_inputs(c, B, 5, real_dtype=np.float32)
+    outs = []
+    for shared in ("1", "0"):
+        monkeypatch.setenv("QTM_PREP_SHARED", shared)
+        plan = capi.Plan(c, dtype="c64").compile()
+        info = plan.info
+        x = torch.tensor(inp.x, dtype=torch.float32, device="cuda")
+        w = torch.tensor(inp.w, dtype=torch.float32, device="cuda")
+        gE = torch.tensor(inp.gE, dtype=torch.float32, device="cuda")
+        L = capi.lib()
+        for mode in (1, 2):
+            assert L.qtm_set_profiling(plan.handle, mode) == capi.QTM_OK
+            E = plan.forward(x, w)
+            gx, gw = plan.adjoint(gE, x, w)
+            torch.cuda.synchronize()
+            f, a = _launches(plan, 0), _launches(plan, 1)
+            if mode == 1:
+                if shared == "1":
+                    assert len(f) == info["fwd_launches"], (f, info)
+                    assert len(a) == info["adj_launches"] + 1, (a, info)
+            else:
+                assert len(f) == 0
+                assert len(a) == info["adj_passes"] and all(k == 0 and t > 0 for t, k in a), a
+        assert L.qtm_set_profiling(plan.handle, 3) == capi.QTM_EINVAL
+        assert L.qtm_set_profiling(plan.handle, 0) == capi.QTM_OK
+        outs.append([t.cpu().numpy() for t in (E, gx, gw)])
+    for u, v in zip(*outs):
+        assert np.array_equal(u, v)
+    Eo = oracle.forward(c, inp.x, inp.w, threads=0)
+    assert np.max(np.abs(outs[0][0] - Eo)) <= 1e-5
 
 
 @pytest.mark.gpu

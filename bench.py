@@ -137,7 +137,7 @@ class ClockSampler:
 # kernel kind the bench runs (profiles/ holds the summaries and commands);
 # reported as null for any other kernel kind.
 PROFILED_TRAFFIC = {
-    ("qnn12", "cpx"): (39.686144e6 + 0.019712e6, "profiles/qtm_gen_pass_cpx_qnn12_l6_b1024.md"),
+    ("qnn12", "cpx"): (39.644160e6 + 0.0, "profiles/qtm_gen_pass_cpx_qnn12_l6_b1024.md"),
     ("qnn20", "cpx"): ((0.537211e9 + 1.022075e9 + 1.073937e9 + 1.018183e9 + 1.073976e9 + 0.497157e9 +
                         0.537045e9 + 0.507352e9 + 0.537005e9 + 0.003969e9) / 5,
                        "profiles/qtm_gen_pass_cpx_qnn20_l4_b64.md (mean of reverse passes 0-4)"),

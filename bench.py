@@ -138,8 +138,8 @@ class ClockSampler:
 # reported as null for any other kernel kind.
 PROFILED_TRAFFIC = {
     ("qnn12", "cpx"): (39.644160e6 + 0.0, "profiles/qtm_gen_pass_cpx_qnn12_l6_b1024.md"),
-    ("qnn20", "cpx"): ((0.537211e9 + 1.022075e9 + 1.073937e9 + 1.018183e9 + 1.073976e9 + 0.497157e9 +
-                        0.537045e9 + 0.507352e9 + 0.537005e9 + 0.003969e9) / 5,
+    ("qnn20", "cpx"): ((0.537222e9 + 1.019826e9 + 1.073918e9 + 1.019058e9 + 1.074121e9 + 0.497195e9 +
+                        0.537016e9 + 0.519352e9 + 0.537040e9 + 0.003919e9) / 5,
                        "profiles/qtm_gen_pass_cpx_qnn20_l4_b64.md (mean of reverse passes 0-4)"),
 }
 

@@ -866,29 +866,41 @@ def measure_e2e(name, steps, device, seed_offset=0, kernels="cpx", tune=False):
     if tune:   # the schedule the timed line chose (a cache hit)
         plan.tune(torch.tensor(inp.x, dtype=rd, device=device), torch.tensor(inp.w, dtype=rd, device=device),
                   torch.tensor(inp.gE, dtype=rd, device=device), cache_path=TUNE_CACHE)
-    hx = torch.tensor(inp.x, dtype=rd).pin_memory()
-    hw = torch.tensor(inp.w, dtype=rd).pin_memory()
-    hg = torch.tensor(inp.gE, dtype=rd).pin_memory()
-    hE = torch.empty((B, c.n_obs), dtype=rd).pin_memory()
-    hgx = torch.empty((B, c.n_inputs), dtype=rd).pin_memory()
-    hgw = torch.empty((c.n_weights,), dtype=rd).pin_memory()
-    x = torch.empty_like(hx, device=device)
-    w = torch.empty_like(hw, device=device)
-    g = torch.empty_like(hg, device=device)
-    E = torch.empty_like(hE, device=device)
-    gx = torch.empty_like(hgx, device=device)
-    gw = torch.empty_like(hgw, device=device)
+    # inputs (x, w, cotangents) and outputs (E, grad_x, grad_w) each packed in
+    # one pinned host buffer and one device buffer (segments 256-byte
+    # aligned): one host-to-device and one device-to-host copy per step
+    def packed(shapes):
+        offs, o = [], 0
+        for sh in shapes:
+            offs.append(o)
+            o += -(-int(np.prod(sh)) // 64) * 64
+        return offs, o
+
+    in_shapes = [(B, c.n_inputs), (c.n_weights,), (B, c.n_obs)]
+    out_shapes = [(B, c.n_obs), (B, c.n_inputs), (c.n_weights,)]
+    in_offs, in_n = packed(in_shapes)
+    out_offs, out_n = packed(out_shapes)
+    h_in = torch.zeros(in_n, dtype=rd).pin_memory()
+    h_out = torch.zeros(out_n, dtype=rd).pin_memory()
+    d_in = torch.empty(in_n, dtype=rd, device=device)
+    d_out = torch.empty(out_n, dtype=rd, device=device)
+
+    def views(buf, offs, shapes):
+        return [buf[o:o + int(np.prod(sh))].view(sh) for o, sh in zip(offs, shapes)]
+
+    for v, a in zip(views(h_in, in_offs, in_shapes), (inp.x, inp.w, inp.gE)):
+        v.copy_(torch.as_tensor(a, dtype=rd))
+    hx, hw, hg = views(h_in, in_offs, in_shapes)
+    x, w, g = views(d_in, in_offs, in_shapes)
+    hE, hgx, hgw = views(h_out, out_offs, out_shapes)
+    E, gx, gw = views(d_out, out_offs, out_shapes)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=device)
 
     def step():
-        x.copy_(hx, non_blocking=True)
-        w.copy_(hw, non_blocking=True)
-        g.copy_(hg, non_blocking=True)
+        d_in.copy_(h_in, non_blocking=True)
         plan.forward(x, w, out=E)
         plan.adjoint(g, x, w, gx=gx, gw=gw)
-        hE.copy_(E, non_blocking=True)
-        hgx.copy_(gx, non_blocking=True)
-        hgw.copy_(gw, non_blocking=True)
+        h_out.copy_(d_out, non_blocking=True)
 
     for _ in range(3):
         step()
@@ -903,8 +915,8 @@ def measure_e2e(name, steps, device, seed_offset=0, kernels="cpx", tune=False):
         torch.cuda.synchronize()
         tot += e0.elapsed_time(e1)
     es = x.element_size()
-    h2d = (hx.numel() + hw.numel() + hg.numel()) * es
-    d2h = (hE.numel() + hgx.numel() + hgw.numel()) * es
+    h2d = h_in.numel() * es
+    d2h = h_out.numel() * es
     return B * steps / (tot / 1e3), h2d, d2h
 
 

@@ -296,14 +296,14 @@ bool jit_active(const qtm_plan *p)
 
 
 cudaError_t launch_any(qtm_plan *p, bool rev, size_t i, PassArgs a, const CUtensorMap &t0, const CUtensorMap &t1,
-                       cudaStream_t s)
+                       cudaStream_t s, bool pdl = false)
 {
     const auto &v = rev ? p->jit_rev : p->jit_fwd;
     if (jit_active(p) && i < v.size() && v[i].fn) {
         a.smem_bytes = v[i].smem;
-        return jit_launch(v[i], a, t0, t1, s);
+        return jit_launch(v[i], a, t0, t1, s, pdl);
     }
-    return launch_pass(p->P.dtype, rev, a, t0, t1, s);
+    return launch_pass(p->P.dtype, rev, a, t0, t1, s, pdl);
 }
 
 qtm_status ensure_workspace(qtm_plan *p, int B)
@@ -511,8 +511,9 @@ qtm_status run_forward_passes(qtm_plan *p, int B, const void *x, const void *w, 
         if (st != QTM_OK) return st;
     }
     const bool shared = prep_shared(p);
+    const bool after_shared = shared && prep_shared_launches(p);   // the first pass follows k_prep_shared
     if (shared) {
-        if (prep_shared_launches(p)) {
+        if (after_shared) {
             ProfScope ps(p, 1);
             cudaError_t e = launch_prep_shared(P.dtype, p->d_rots, p->d_rot_rep, (int)P.rots.size(), w,
                                                p->d_cs_shared, s);
@@ -528,7 +529,8 @@ qtm_status run_forward_passes(qtm_plan *p, int B, const void *x, const void *w, 
         }
         if (fused) a.E_out = expvals;
         ProfScope ps(p, 0);
-        cudaError_t e = launch_any(p, false, i, a, p->tm_fwd[i], p->tm_fwd[i], s);
+        // the first pass may overlap k_prep_shared (it waits before reading its pairs)
+        cudaError_t e = launch_any(p, false, i, a, p->tm_fwd[i], p->tm_fwd[i], s, i == 0 && after_shared);
         if (e != cudaSuccess) return cuda_fail(p, e, "forward pass launch");
     }
     return QTM_OK;

@@ -57,7 +57,7 @@ size_t pass_smem_bytes(int K, int dtype, bool reverse, int nslots, int n_terms, 
                        int state_qubits, int n_prefix_ents);
 
 cudaError_t launch_pass(int dtype, bool reverse, const PassArgs &a, const CUtensorMap &tm_phi,
-                        const CUtensorMap &tm_lam, cudaStream_t s);
+                        const CUtensorMap &tm_lam, cudaStream_t s, bool pdl = false);
 cudaError_t launch_expval_finalize(int dtype, const FinalizeArgs &f, cudaStream_t s);
 cudaError_t launch_grad_finalize(int dtype, const FinalizeArgs &f, cudaStream_t s);
 // FP64 (cos, sin) of the half angles of the rotations without an input,

@@ -39,6 +39,9 @@ __global__ void k_prep(const PrepArgs a)
 template <typename R>
 __global__ void k_prep_shared(const Rot *rots, const int32_t *rep, int n_rots, const R *w, double2 *cs_shared)
 {
+    // the forward pass after this kernel may start now; it waits for these
+    // pairs before reading them
+    asm volatile("griddepcontrol.launch_dependents;");
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_rots || rep[i] != i) return;
     const Rot ro = rots[i];
@@ -114,6 +117,7 @@ __global__ void k_accumulate_cols(const R *src, int Gs, R *dst, int Gd, size_t r
 template <typename R>
 __global__ void k_gw_reduce(const double *gw_ws, int B, int P, R *gw)
 {
+    asm volatile("griddepcontrol.wait;" ::: "memory");   // the per-sample sums of the kernel before
     __shared__ double red[32];
     const int j = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     double s = 0.0;
@@ -248,8 +252,32 @@ size_t pass_smem_bytes(int K, int dtype, bool reverse, int nslots, int n_terms, 
     return (size_t)L.total + 1024;
 }
 
+// Launch, as a programmatic dependent launch when pdl is set (the kernel
+// may start while the stream's previous kernel runs and waits with
+// griddepcontrol.wait before reading what that kernel writes).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_maybe_pdl(void (*fn)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, bool pdl,
+                             Args... args)
+{
+    if (!pdl) {
+        fn<<<grid, block, smem, s>>>(args...);
+        return cudaGetLastError();
+    }
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, fn, args...);
+}
+
 cudaError_t launch_pass(int dtype, bool reverse, const PassArgs &a, const CUtensorMap &tm_phi,
-                        const CUtensorMap &tm_lam, cudaStream_t s)
+                        const CUtensorMap &tm_lam, cudaStream_t s, bool pdl)
 {
     // a tile below 9 qubits has fewer than 32 threads' worth of registers; the
     // CTA still takes a full warp, whose other lanes share the staging, the
@@ -263,7 +291,8 @@ cudaError_t launch_pass(int dtype, bool reverse, const PassArgs &a, const CUtens
         auto fn = k_pass<R, REV>;                                                              \
         e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);  \
         if (e != cudaSuccess) return e;                                                        \
-        fn<<<grid, block, smem, s>>>(a, tm_phi, tm_lam);                                       \
+        e = launch_maybe_pdl(fn, grid, block, smem, s, pdl, a, tm_phi, tm_lam);                \
+        if (e != cudaSuccess) return e;                                                        \
     } while (0)
     if (dtype == QTM_C128) {
         if (reverse) QTM_LAUNCH(double, true); else QTM_LAUNCH(double, false);
@@ -338,9 +367,12 @@ cudaError_t launch_accumulate_cols(int dtype, const void *src, int Gs, void *dst
 cudaError_t launch_gw_reduce(int dtype, const double *gw_ws, int B, int P, void *gw, cudaStream_t s)
 {
     if (P <= 0) return cudaSuccess;
-    if (dtype == QTM_C128) k_gw_reduce<double><<<P, 256, 0, s>>>(gw_ws, B, P, static_cast<double *>(gw));
-    else k_gw_reduce<float><<<P, 256, 0, s>>>(gw_ws, B, P, static_cast<float *>(gw));
-    return cudaGetLastError();
+    // launched while the kernel that writes gw_ws (always one of this
+    // library's) finishes; it waits for it before reading
+    if (dtype == QTM_C128)
+        return launch_maybe_pdl(k_gw_reduce<double>, dim3(P), dim3(256), 0, s, true, gw_ws, B, P,
+                                static_cast<double *>(gw));
+    return launch_maybe_pdl(k_gw_reduce<float>, dim3(P), dim3(256), 0, s, true, gw_ws, B, P, static_cast<float *>(gw));
 }
 
 }  // namespace qtm

@@ -599,6 +599,7 @@ struct Drv {
     PFN_cuModuleUnload_v2000 unload = nullptr;
     PFN_cuFuncSetAttribute_v9000 set_attr = nullptr;
     PFN_cuLaunchKernel_v4000 launch = nullptr;
+    PFN_cuLaunchKernelEx_v11060 launch_ex = nullptr;   // optional: programmatic dependent launches
 };
 
 const Drv &drv()
@@ -616,6 +617,7 @@ const Drv &drv()
                get("cuModuleUnload", reinterpret_cast<void **>(&d.unload)) &&
                get("cuFuncSetAttribute", reinterpret_cast<void **>(&d.set_attr)) &&
                get("cuLaunchKernel", reinterpret_cast<void **>(&d.launch));
+        if (!get("cuLaunchKernelEx", reinterpret_cast<void **>(&d.launch_ex))) d.launch_ex = nullptr;
     });
     return d;
 }
@@ -724,14 +726,29 @@ void jit_unload(JitKernel &k)
 }
 
 cudaError_t jit_launch(const JitKernel &k, const PassArgs &a, const CUtensorMap &tm_phi, const CUtensorMap &tm_lam,
-                       cudaStream_t s)
+                       cudaStream_t s, bool pdl)
 {
     PassArgs args = a;
     CUtensorMap t0 = tm_phi, t1 = tm_lam;
     void *params[] = {&args, &t0, &t1};
     const unsigned grid = (unsigned)a.B * (unsigned)a.tiles, block = 1u << (a.K - 4);
-    CUresult r = drv().launch(static_cast<CUfunction>(k.fn), grid, 1, 1, block, 1, 1, (unsigned)a.smem_bytes,
-                              reinterpret_cast<CUstream>(s), params, nullptr);
+    CUresult r;
+    if (pdl && drv().launch_ex) {
+        CUlaunchAttribute at[1];
+        at[0].id = CU_LAUNCH_ATTRIBUTE_PROGRAMMATIC_STREAM_SERIALIZATION;
+        at[0].value.programmaticStreamSerializationAllowed = 1;
+        CUlaunchConfig cfg{};
+        cfg.gridDimX = grid; cfg.gridDimY = 1; cfg.gridDimZ = 1;
+        cfg.blockDimX = block; cfg.blockDimY = 1; cfg.blockDimZ = 1;
+        cfg.sharedMemBytes = (unsigned)a.smem_bytes;
+        cfg.hStream = reinterpret_cast<CUstream>(s);
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        r = drv().launch_ex(&cfg, static_cast<CUfunction>(k.fn), params, nullptr);
+    } else {
+        r = drv().launch(static_cast<CUfunction>(k.fn), grid, 1, 1, block, 1, 1, (unsigned)a.smem_bytes,
+                         reinterpret_cast<CUstream>(s), params, nullptr);
+    }
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorLaunchFailure;
 }
 

@@ -29,7 +29,10 @@ size_t jit_smem_bytes_cpx(const Plan &P, const PassDesc &pd);
 bool jit_compile(const std::string &body, std::vector<char> &cubin, std::string &log);
 bool jit_load(const std::vector<char> &cubin, int smem, JitKernel &k, std::string &err);
 void jit_unload(JitKernel &k);
+// pdl: a programmatic dependent launch (the kernel may start while the
+// stream's previous kernel runs; it waits with griddepcontrol.wait before
+// reading what that kernel writes).
 cudaError_t jit_launch(const JitKernel &k, const PassArgs &a, const CUtensorMap &tm_phi, const CUtensorMap &tm_lam,
-                       cudaStream_t s);
+                       cudaStream_t s, bool pdl = false);
 
 }  // namespace qtm

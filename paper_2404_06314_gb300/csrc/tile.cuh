@@ -437,6 +437,9 @@ __device__ __forceinline__ void prep_sample_shared(const Run *runs, const Rot *r
         scratch[i] = double2{c, s};
     }
     __syncthreads();
+    // cs_shared comes from the kernel launched just before this one, which
+    // this one may overlap (programmatic dependent launch): wait for it here
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     for (int r = threadIdx.x; r < n_runs; r += blockDim.x) {
         const Run rr = runs[r];
         double2 a{1, 0}, b{0, 0};
@@ -1027,6 +1030,12 @@ __device__ __forceinline__ void pass_body(const PassArgs &a, const CUtensorMap *
     const uint32_t gap = tile & ((1u << gapbits) - 1u);
     const uint32_t rest = tile >> gapbits;
 
+    if constexpr (REV) {
+        // a kernel launched after this one as a programmatic dependent launch
+        // (the batch grad_w reduction) may start once every CTA is running;
+        // it waits for this grid before reading its results
+        asm volatile("griddepcontrol.launch_dependents;");
+    }
     if constexpr (!REV) {
         __shared__ double2 ufac[2 * 32];
         if (a.prep_fused && a.rot_rep) {   // as below, sines and cosines shared; scratch: the idle tile

@@ -1088,8 +1088,10 @@ def reference_main(args):
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)",
+            # the GPU arm's workload keys; how this arm computes it is in "path"
             "config": {"workload": cfg["desc"], "global_batch": cfg["B"] * ws, "per_gpu_batch": cfg["B"],
-                       "path": "FP64 oracle on the host cores (reference arm)"},
+                       "parallelism": f"batch shards x{ws}"},
+            "path": "FP64 oracle on the host cores (reference arm)",
             "cpu_baseline": {"value": value, "unit": "samples/s", "cores": threads, "kind": "oracle",
                              "sample": f"{S} samples of the {c.name} batch per step (a bounded sample of the "
                                        f"{cfg['B']}-sample batch; samples/s is per sample either way)"},

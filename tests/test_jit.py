@@ -287,6 +287,52 @@ def test_profiled_launches_match_plan_info_and_shared_prep(builder, monkeypatch)
 
 
 @pytest.mark.gpu
+@pytest.mark.parametrize("builder,B", [("workload_12q", 96), ("workload_20q", 2)])
+def test_forward_adjoint_in_a_cuda_graph(builder, B):
+    """qtm_forward + qtm_adjoint captured once into a CUDA graph (after a
+    warm-up call that sizes the workspace) and replayed with new inputs copied
+    into the captured buffers: the replays give the eager calls' results (the
+    programmatic dependent launches inside a call become graph dependencies)."""
+    import torch
+    c = getattr(W, builder)()
+    plan = capi.Plan(c, dtype="c64").compile()
+    dev = torch.device("cuda")
+    x = torch.empty((B, c.n_inputs), dtype=torch.float32, device=dev)
+    w = torch.empty((c.n_weights,), dtype=torch.float32, device=dev)
+    gE = torch.empty((B, c.n_obs), dtype=torch.float32, device=dev)
+    E = torch.empty((B, c.n_obs), dtype=torch.float32, device=dev)
+    gx = torch.empty((B, c.n_inputs), dtype=torch.float32, device=dev)
+    gw = torch.empty((c.n_weights,), dtype=torch.float32, device=dev)
+
+    def load(seed):
+        inp = W.make_inputs(c, B, seed, real_dtype=np.float32)
+        x.copy_(torch.tensor(inp.x)); w.copy_(torch.tensor(inp.w)); gE.copy_(torch.tensor(inp.gE))
+
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        load(40)
+        plan.forward(x, w, out=E, stream=s)
+        plan.adjoint(gE, x, w, gx=gx, gw=gw, stream=s)
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        plan.forward(x, w, out=E, stream=s)
+        plan.adjoint(gE, x, w, gx=gx, gw=gw, stream=s)
+    for seed in (41, 42):
+        load(seed)
+        g.replay()
+        torch.cuda.synchronize()
+        got = [t.clone() for t in (E, gx, gw)]
+        plan.forward(x, w, out=E)
+        plan.adjoint(gE, x, w, gx=gx, gw=gw)
+        torch.cuda.synchronize()
+        for a, b in zip(got, (E, gx, gw)):
+            assert torch.equal(a, b), (builder, seed)
+
+
+@pytest.mark.gpu
 def test_compile_after_forward_and_recompute():
     """qtm_compile drops the stored state (its layout changes): an adjoint
     right after it asks for a new forward; recompute works; the general

@@ -115,7 +115,9 @@ typedef struct {
     int32_t tile_qubits;     /* K: qubits per shared-memory tile */
     int32_t fwd_passes;      /* kernel passes over the state in qtm_forward */
     int32_t adj_passes;      /* passes in qtm_adjoint (without recompute) */
-    int32_t fwd_launches;    /* kernel launches per qtm_forward (one-sample kernels) */
+    int32_t fwd_launches;    /* kernel launches per qtm_forward (one-sample kernels; with plans of
+                              * one tile per sample, one per-call kernel for the sines and
+                              * cosines of rotations without an input) */
     int32_t adj_launches;    /* kernel launches per qtm_adjoint (per-sample grad_w; one more
                               * for the batch-summed grad_w) */
     int32_t n_runs;          /* fused single-qubit rotation runs */

@@ -412,8 +412,22 @@ void cpx_op(std::ostringstream &o, const Plan &P, const PassDesc &pd, int k, int
     }
 }
 
+// A phase leaves phi and lam as they are when its only ops are gradients
+// without the undo (a run's last reverse op) and expectation values; it then
+// need not store them back (unless it computed phi in registers itself).
+bool phase_keeps_state(const Plan &P, const DevPhase &phs)
+{
+    for (int k = phs.op_begin; k < phs.op_end; ++k) {
+        const DevOp &op = P.ops[k];
+        if (op.type == OP_EXPVAL) continue;
+        if (op.type == OP_GRAD && (op.flags & OPF_SKIP_APPLY)) continue;
+        return false;
+    }
+    return true;
+}
+
 std::string phase_body(const Plan &P, const PassDesc &pd, const DevPhase &phs, bool lam_valid, int sb,
-                       bool fill = false)
+                       bool fill = false, bool store = true)
 {
     const bool rev = pd.reverse != 0;
     const int lo = phs.lo;
@@ -441,7 +455,7 @@ std::string phase_body(const Plan &P, const PassDesc &pd, const DevPhase &phs, b
             o << " S.redG[warp * " << 3 * nslots << " + 3 * " << deferred[i] << " + (lane >> 3)] = vr[" << i << "];";
         o << " }\n";
     }
-    o << "        regs_store_cpx<LO, " << (rev ? "true" : "false") << ">(p, q, S, xt);\n";
+    if (store) o << "        regs_store_cpx<LO, " << (rev ? "true" : "false") << ">(p, q, S, xt);\n";
     return o.str();
 }
 
@@ -453,6 +467,7 @@ std::string jit_source(const Plan &P, const PassDesc &pd, int min_blocks)
     // distinct phase bodies (templates) and, per phase, (template, first slot)
     std::vector<std::string> tpl;
     std::vector<int> table;
+    std::vector<int> stores;   // per phase: it writes phi / lam back to shared memory
     bool lam_valid = rev && pd.lam_src == SRC_LOAD;
     for (int ph = pd.phase_begin; ph < pd.phase_end; ++ph) {
         const DevPhase &phs = P.phases[ph];
@@ -462,7 +477,9 @@ std::string jit_source(const Plan &P, const PassDesc &pd, int min_blocks)
                 sb = P.ops[k].slot;
         if (sb < 0) sb = 0;
         const bool fill = cpx_fill(pd) && ph == pd.phase_begin;
-        const std::string body = phase_body(P, pd, phs, lam_valid, sb, fill);
+        const bool store = fill || !phase_keeps_state(P, phs);
+        stores.push_back(store ? 1 : 0);
+        const std::string body = phase_body(P, pd, phs, lam_valid, sb, fill, store);
         size_t t = 0;
         while (t < tpl.size() && tpl[t] != body) ++t;
         if (t == tpl.size()) tpl.push_back(body);
@@ -504,6 +521,30 @@ std::string jit_source(const Plan &P, const PassDesc &pd, int min_blocks)
         auto barrier = [&](bool warp_only) {
             return warp_only ? "        __syncwarp();\n" : "        __syncthreads();\n";
         };
+        // The shared tile changes only in phases that store: two neighbouring
+        // phases that both leave it alone need no barrier between them, if
+        // every store so far has been published by a CTA barrier (a warp
+        // barrier after a store only publishes it within the warp, and the
+        // next phase may read another warp's part).  Once a barrier has been
+        // left out, warps may be phases apart, so the next barrier is a CTA
+        // barrier (a warp barrier before a storing phase would let a warp
+        // overwrite what a lagging warp still reads).  The last phase always
+        // ends with one: the partial sums are read next.
+        bool published = true;   // every store so far seen by every warp
+        bool drift = false;      // a barrier left out since the last CTA barrier
+        auto after = [&](int a, int b, bool warp_only) -> std::string {
+            if (b < nph && !stores[a] && !stores[b] && published) {
+                drift = true;
+                return "";
+            }
+            if (drift || !warp_only) {
+                drift = false;
+                published = true;
+                return barrier(false);
+            }
+            if (stores[a]) published = false;
+            return barrier(true);
+        };
         const Repeat rp = repeat_loops() ? find_repeat(table, nph) : Repeat{};
         const int loop_end = rp.reps >= 2 ? rp.start + rp.period * rp.reps : 0;
         for (int ph = 0; ph < nph; ++ph) {
@@ -519,13 +560,17 @@ std::string jit_source(const Plan &P, const PassDesc &pd, int min_blocks)
                                                       : local(a, rp.start) && loop_end < nph && local(a, loop_end);
                     o << "    {\n        const int sb = " << table[2 * a + 1] << " + it * " << rp.stride
                       << ";\n        (void)sb;\n" << tpl[table[2 * a]] << barrier(wl) << "    }\n";
+                    if (i + 1 == rp.period) {   // the loop's last barrier hands over to the phase after it
+                        published = !wl;   // only a CTA barrier publishes the loop's stores
+                        drift = false;
+                    }
                 }
                 o << "    }\n";
                 ph = loop_end - 1;
                 continue;
             }
             o << "    {\n        const int sb = " << table[2 * ph + 1] << ";\n        (void)sb;\n"
-              << tpl[table[2 * ph]] << barrier(local(ph, ph + 1)) << "    }\n";
+              << tpl[table[2 * ph]] << after(ph, ph + 1, local(ph, ph + 1)) << "    }\n";
         }
     } else {
         o << "#pragma unroll 1\n    for (int ph = 0; ph < " << nph << "; ++ph) {\n";

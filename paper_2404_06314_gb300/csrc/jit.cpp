@@ -412,20 +412,6 @@ void cpx_op(std::ostringstream &o, const Plan &P, const PassDesc &pd, int k, int
     }
 }
 
-// A phase leaves phi and lam as they are when its only ops are gradients
-// without the undo (a run's last reverse op) and expectation values; it then
-// need not store them back (unless it computed phi in registers itself).
-bool phase_keeps_state(const Plan &P, const DevPhase &phs)
-{
-    for (int k = phs.op_begin; k < phs.op_end; ++k) {
-        const DevOp &op = P.ops[k];
-        if (op.type == OP_EXPVAL) continue;
-        if (op.type == OP_GRAD && (op.flags & OPF_SKIP_APPLY)) continue;
-        return false;
-    }
-    return true;
-}
-
 std::string phase_body(const Plan &P, const PassDesc &pd, const DevPhase &phs, bool lam_valid, int sb,
                        bool fill = false, bool store = true)
 {
@@ -477,7 +463,9 @@ std::string jit_source(const Plan &P, const PassDesc &pd, int min_blocks)
                 sb = P.ops[k].slot;
         if (sb < 0) sb = 0;
         const bool fill = cpx_fill(pd) && ph == pd.phase_begin;
-        const bool store = fill || !phase_keeps_state(P, phs);
+        // a phase that leaves phi and lam as they are (the planner's flag) need
+        // not store them back, unless it computed phi in registers itself
+        const bool store = fill || !(phs.flags & PHF_KEEPS_STATE);
         stores.push_back(store ? 1 : 0);
         const std::string body = phase_body(P, pd, phs, lam_valid, sb, fill, store);
         size_t t = 0;

@@ -770,6 +770,14 @@ qtm_status make_plan_mode(int n, const qtm_gate *gates, int n_gates, const qtm_z
             P.max_slots = std::max(P.max_slots, pd.slot_end - pd.slot_begin);
             P.max_phases = std::max(P.max_phases, pd.phase_end - pd.phase_begin);
         }
+    for (DevPhase &ph : P.phases) {
+        bool keeps = true;
+        for (int o = ph.op_begin; o < ph.op_end && keeps; ++o) {
+            const DevOp &op = P.ops[o];
+            keeps = op.type == OP_EXPVAL || (op.type == OP_GRAD && (op.flags & OPF_SKIP_APPLY));
+        }
+        ph.flags = keeps ? PHF_KEEPS_STATE : 0;
+    }
     return QTM_OK;
 }
 

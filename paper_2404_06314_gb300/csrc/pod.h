@@ -76,8 +76,12 @@ struct DevPhase {
     int32_t lo;        // register group: tile-local bits [lo, lo + 4)
     int32_t op_begin;  // into the plan's op array
     int32_t op_end;
-    int32_t pad;
+    int32_t flags;     // PHF_*
 };
+// The phase's ops leave phi and lam as they are (gradients of runs' last
+// reverse ops, whose undo is skipped, and expectation values): it need not
+// store them back to shared memory.
+constexpr int32_t PHF_KEEPS_STATE = 1;
 
 enum Src : int32_t { SRC_NONE = 0, SRC_LOAD = 1, SRC_ANALYTIC = 2, SRC_COSTATE = 3 };
 

@@ -18,19 +18,26 @@ namespace qtm {
 
 namespace {
 
-constexpr int kCpxSlotPairs = 8;   // per run slot, for e = u00, u01, u10, u11: (e.re, e.re), (-e.im, e.im)
+// Every run matrix is special unitary, U = [[a, -conj(b)], [b, conj(a)]]
+// (a product of rotations; U^dagger has the same form with a -> conj(a),
+// b -> -b), so its four entries in broadcast form, (e.re, e.re) and
+// (-e.im, e.im), hold six distinct pairs: A_r = (a.re, a.re),
+// A_n = (-a.im, a.im), B_r = (b.re, b.re), B_n = (-b.im, b.im) and the
+// negations -B_r, -A_n.  A slot keeps those six (of eight places).
+constexpr int kCpxSlotPairs = 8;
 
 // Complex-pair table of every run slot from the staged matrices (U or U^dagger).
 __device__ __forceinline__ void stage_cpx_table(const Cx<float> *mats, f2 *tab, int nslots)
 {
     for (int s = threadIdx.x; s < nslots; s += blockDim.x) {
         f2 *t = tab + kCpxSlotPairs * s;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const Cx<float> e = mats[4 * s + k];
-            t[2 * k] = pack2(e.x, e.x);
-            t[2 * k + 1] = pack2(-e.y, e.y);
-        }
+        const Cx<float> a = mats[4 * s], b = mats[4 * s + 2];
+        t[0] = pack2(a.x, a.x);     // A_r
+        t[1] = pack2(-a.y, a.y);    // A_n
+        t[2] = pack2(b.x, b.x);     // B_r
+        t[3] = pack2(-b.y, b.y);    // B_n
+        t[4] = pack2(-b.x, -b.x);   // -B_r
+        t[5] = pack2(a.y, -a.y);    // -A_n
     }
 }
 
@@ -135,22 +142,29 @@ __device__ __forceinline__ f2 cmul_tab(uint32_t addr, f2 amp)
     return fma2(er, amp, mul2(en, swap2(amp)));
 }
 
-// a <- U a on register bit RB: per register pair (x0, x1),
-// y0 = u00 x0 + u01 x1, y1 = u10 x0 + u11 x1.
+// The special-unitary product on one register pair (x0, x1):
+// y0 = a x0 - conj(b) x1 = A_r x0 + A_n s0 - B_r x1 + B_n s1,
+// y1 = b x0 + conj(a) x1 = B_r x0 + B_n s0 + A_r x1 - A_n s1 (s = lane swap).
 template <int RB>
-__device__ __forceinline__ void u2_cpx(f2 (&a)[kRegs], const f2 *t)
+__device__ __forceinline__ void su2_apply(f2 (&a)[kRegs], f2 A_r, f2 A_n, f2 B_r, f2 B_n, f2 NB_r, f2 NA_n)
 {
-    f2 A_r, A_n, B_r, B_n, C_r, C_n, D_r, D_n;
-    lds_table2<true>(t, A_r, A_n); lds_table2<true>(t + 2, B_r, B_n);
-    lds_table2<true>(t + 4, C_r, C_n); lds_table2<true>(t + 6, D_r, D_n);
 #pragma unroll
     for (int j = 0; j < kRegs; ++j) {
         if (j & (1 << RB)) continue;
         const f2 x0 = a[j], x1 = a[j | (1 << RB)];
         const f2 s0 = swap2(x0), s1 = swap2(x1);
-        a[j] = fma2(A_r, x0, fma2(A_n, s0, fma2(B_r, x1, mul2(B_n, s1))));
-        a[j | (1 << RB)] = fma2(C_r, x0, fma2(C_n, s0, fma2(D_r, x1, mul2(D_n, s1))));
+        a[j] = fma2(A_r, x0, fma2(A_n, s0, fma2(NB_r, x1, mul2(B_n, s1))));
+        a[j | (1 << RB)] = fma2(B_r, x0, fma2(B_n, s0, fma2(A_r, x1, mul2(NA_n, s1))));
     }
+}
+
+// a <- U a on register bit RB with U's six pairs from the slot table t.
+template <int RB>
+__device__ __forceinline__ void u2_cpx(f2 (&a)[kRegs], const f2 *t)
+{
+    f2 A_r, A_n, B_r, B_n, NB_r, NA_n;
+    lds_table2<true>(t, A_r, A_n); lds_table2<true>(t + 2, B_r, B_n); lds_table2<true>(t + 4, NB_r, NA_n);
+    su2_apply<RB>(a, A_r, A_n, B_r, B_n, NB_r, NA_n);
 }
 
 // (vx, vy, vz) on register bit RB, the same sums as grad_acc in tile.cuh:
@@ -228,18 +242,9 @@ __device__ __forceinline__ void flip_cpx(f2 (&p)[kRegs], f2 (&q)[kRegs], uint32_
 template <int RB>
 __device__ __forceinline__ void u2_cpx_m(f2 (&a)[kRegs], const Cx<float> *m)
 {
-    const Cx<float> u00 = m[0], u01 = m[1], u10 = m[2], u11 = m[3];
-    const f2 A_r = pack2(u00.x, u00.x), A_n = pack2(-u00.y, u00.y), B_r = pack2(u01.x, u01.x),
-             B_n = pack2(-u01.y, u01.y), C_r = pack2(u10.x, u10.x), C_n = pack2(-u10.y, u10.y),
-             D_r = pack2(u11.x, u11.x), D_n = pack2(-u11.y, u11.y);
-#pragma unroll
-    for (int j = 0; j < kRegs; ++j) {
-        if (j & (1 << RB)) continue;
-        const f2 x0 = a[j], x1 = a[j | (1 << RB)];
-        const f2 s0 = swap2(x0), s1 = swap2(x1);
-        a[j] = fma2(A_r, x0, fma2(A_n, s0, fma2(B_r, x1, mul2(B_n, s1))));
-        a[j | (1 << RB)] = fma2(C_r, x0, fma2(C_n, s0, fma2(D_r, x1, mul2(D_n, s1))));
-    }
+    const Cx<float> u00 = m[0], u10 = m[2];   // special unitary: u01 = -conj(u10), u11 = conj(u00)
+    su2_apply<RB>(a, pack2(u00.x, u00.x), pack2(-u00.y, u00.y), pack2(u10.x, u10.x), pack2(-u10.y, u10.y),
+                  pack2(-u10.x, -u10.x), pack2(u00.y, -u00.y));
 }
 
 __device__ __forceinline__ void u2_cpx_dispatch(int rb, f2 (&a)[kRegs], const Cx<float> *m)

@@ -169,30 +169,33 @@ __device__ __forceinline__ void u2_cpx(f2 (&a)[kRegs], const f2 *t)
 
 // (vx, vy, vz) on register bit RB, the same sums as grad_acc in tile.cuh:
 // with b = lam and a = phi, Im(conj(b) a) = lane0 - lane1 of b * swap(a) and
-// Re(conj(b) a) = lane0 + lane1 of b * a.
+// Re(conj(b) a) = lane0 + lane1 of b * a.  Z's second term enters with a
+// plus sign as swap(b1) * a1 (whose lane0 - lane1 is minus that of
+// b1 * swap(a1)), and X's two terms add, so Z and X each take one
+// accumulator: four instead of six.
 template <int RB>
 __device__ __forceinline__ void grad_cpx(const f2 (&a)[kRegs], const f2 (&b)[kRegs], float &vx, float &vy, float &vz)
 {
-    f2 zp, zn, xp, xq, yp, yn;
+    f2 zs, xs, yp, yn;
 #pragma unroll
     for (int j = 0, first = 1; j < kRegs; ++j) {
         if (j & (1 << RB)) continue;
         const f2 a0 = a[j], a1 = a[j | (1 << RB)], b0 = b[j], b1 = b[j | (1 << RB)];
         const f2 s0 = swap2(a0), s1 = swap2(a1);
         if (first) {   // the first pair starts the accumulators (no zero fill)
-            zp = mul2(b0, s0); zn = mul2(b1, s1);
-            xp = mul2(b0, s1); xq = mul2(b1, s0);
+            zs = fma2(swap2(b1), a1, mul2(b0, s0));
+            xs = fma2(b1, s0, mul2(b0, s1));
             yp = mul2(b1, a0); yn = mul2(b0, a1);
             first = 0;
         } else {
-            zp = fma2(b0, s0, zp); zn = fma2(b1, s1, zn);
-            xp = fma2(b0, s1, xp); xq = fma2(b1, s0, xq);
+            zs = fma2(b0, s0, zs); zs = fma2(swap2(b1), a1, zs);
+            xs = fma2(b0, s1, xs); xs = fma2(b1, s0, xs);
             yp = fma2(b1, a0, yp); yn = fma2(b0, a1, yn);
         }
     }
-    const f2 Z = sub2(zp, zn), X = add2(xp, xq), Y = sub2(yp, yn);
-    vz = lane0(Z) - lane1(Z);
-    vx = lane0(X) - lane1(X);
+    const f2 Y = sub2(yp, yn);
+    vz = lane0(zs) - lane1(zs);
+    vx = lane0(xs) - lane1(xs);
     vy = lane0(Y) + lane1(Y);
 }
 

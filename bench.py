@@ -137,9 +137,9 @@ class ClockSampler:
 # kernel kind the bench runs (profiles/ holds the summaries and commands);
 # reported as null for any other kernel kind.
 PROFILED_TRAFFIC = {
-    ("qnn12", "cpx"): (39.641088e6 + 0.000256e6, "profiles/qtm_gen_pass_cpx_qnn12_l6_b1024.md"),
-    ("qnn20", "cpx"): ((0.537222e9 + 1.019826e9 + 1.073918e9 + 1.019058e9 + 1.074121e9 + 0.497195e9 +
-                        0.537016e9 + 0.519352e9 + 0.537040e9 + 0.003919e9) / 5,
+    ("qnn12", "cpx"): (39.638016e6 + 0.000256e6, "profiles/qtm_gen_pass_cpx_qnn12_l6_b1024.md"),
+    ("qnn20", "cpx"): ((0.537235e9 + 1.019508e9 + 1.073914e9 + 1.018413e9 + 1.073914e9 + 0.496884e9 +
+                        0.536996e9 + 0.494335e9 + 0.537071e9 + 0.004366e9) / 5,
                        "profiles/qtm_gen_pass_cpx_qnn20_l4_b64.md (mean of reverse passes 0-4)"),
 }
 

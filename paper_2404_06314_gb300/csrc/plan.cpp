@@ -740,6 +740,85 @@ qtm_status make_plan_mode(int n, const qtm_gate *gates, int n_gates, const qtm_z
             P.amap_terms.insert(P.amap_terms.end(), t.begin(), t.end());
         }
 
+    // ---- place the CZ gates of each pass so that they merge into few DIAG ops --
+    // A CZ may sit anywhere between the nearest ops of its pass, before and
+    // after it, that do not commute with it: a run or gradient on one of its
+    // qubits, a CNOT whose target is one of them, an expectation value or the
+    // costate.  The fewest positions that cover every CZ's range are chosen
+    // greedily (latest range start first, each new position at that start, so
+    // no CZ moves later than the merge needs) and the CZs of one position
+    // become consecutive ops.  In a reverse pass that stores nothing, a CZ
+    // whose range reaches the pass's end is left out: it would multiply phi
+    // and lam by the same signs, which no later op of the pass tells apart
+    // (each commutes with it, and <D lam|sigma_c|D phi> = <lam|sigma_c|phi>
+    // for a qubit c outside it).
+    {
+        std::vector<std::vector<DevOp>> placed(P.phases.size());
+        std::vector<char> in_pass(P.phases.size(), 0);
+        auto commutes = [](const DevOp &op, int a, int b) {
+            switch (op.type) {
+            case OP_CZ: return true;
+            case OP_U2: case OP_GRAD: return op.a != a && op.a != b;
+            case OP_CNOT: return op.b != a && op.b != b;
+            default: return false;
+            }
+        };
+        struct Range { int s, e, i; };   // gaps s..e (gap g lies before position g); the CZ's position i
+        for (auto *v : {&P.fwd, &P.rev})
+            for (const PassDesc &pd : *v) {
+                std::vector<int> seq, phase_of;   // the pass's ops, phase after phase
+                for (int ph = pd.phase_begin; ph < pd.phase_end; ++ph) {
+                    in_pass[ph] = 1;
+                    for (int o = P.phases[ph].op_begin; o < P.phases[ph].op_end; ++o) {
+                        seq.push_back(o);
+                        phase_of.push_back(ph);
+                    }
+                }
+                const int len = (int)seq.size();
+                std::vector<Range> rs;
+                for (int i = 0; i < len; ++i) {
+                    const DevOp &cz = P.ops[seq[i]];
+                    if (cz.type != OP_CZ) continue;
+                    int s = i, e = i + 1;
+                    while (s > 0 && commutes(P.ops[seq[s - 1]], cz.a, cz.b)) --s;
+                    while (e < len && commutes(P.ops[seq[e]], cz.a, cz.b)) ++e;
+                    rs.push_back({s, e, i});
+                }
+                const bool drop_tail = pd.reverse && !pd.store_phi && !pd.store_lam;
+                std::vector<int> gap_of(len, -1);   // per CZ position its gap, -1 left out
+                std::sort(rs.begin(), rs.end(), [](const Range &x, const Range &y) {
+                    return x.s != y.s ? x.s > y.s : x.i < y.i;
+                });
+                int point = -1;
+                for (const Range &r : rs) {
+                    if (drop_tail && r.e == len) continue;
+                    if (point < 0 || r.e < point) point = r.s;
+                    gap_of[r.i] = point;
+                }
+                auto emit_gap = [&](int g, int ph) {
+                    for (int i = 0; i < len; ++i)
+                        if (gap_of[i] == g) placed[ph].push_back(P.ops[seq[i]]);
+                };
+                for (int i = 0; i < len; ++i) {
+                    // a gap between two phases goes to the end of the earlier one
+                    emit_gap(i, (i > 0 && phase_of[i - 1] != phase_of[i]) ? phase_of[i - 1] : phase_of[i]);
+                    if (P.ops[seq[i]].type != OP_CZ) placed[phase_of[i]].push_back(P.ops[seq[i]]);
+                }
+                if (len > 0) emit_gap(len, phase_of[len - 1]);
+            }
+        std::vector<DevOp> ops;
+        ops.reserve(P.ops.size());
+        for (size_t ph = 0; ph < P.phases.size(); ++ph) {
+            DevPhase &d = P.phases[ph];
+            const int nb = (int)ops.size();
+            if (in_pass[ph]) ops.insert(ops.end(), placed[ph].begin(), placed[ph].end());
+            else ops.insert(ops.end(), P.ops.begin() + d.op_begin, P.ops.begin() + d.op_end);
+            d.op_begin = nb;
+            d.op_end = (int)ops.size();
+        }
+        P.ops.swap(ops);
+    }
+
     // ---- merge runs of consecutive CZ ops inside a phase into one DIAG op -----
     {
         std::vector<DevOp> ops;

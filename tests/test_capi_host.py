@@ -321,6 +321,35 @@ def test_prefix_entanglers_undone_out_of_order():
     _emulate_vs_oracle(c2, 2, 7)
 
 
+def test_cz_gates_merge_into_one_diagonal_op_per_ring():
+    """A CZ may move anywhere the ops around it commute with it; the planner
+    gathers the CZs into as few diagonal ops as that allows.  12-qubit
+    workload (6 layers, CZ ring after each, the first ring folded into the
+    analytic state): one diagonal op of all 12 pairs per ring, 5 in the
+    forward and 6 in the reverse, none in the gradient-only closing phases.
+    CZs ahead of every rotation on their qubits are left out of the last
+    reverse pass (they multiply phi and lam by the same signs and no later
+    op tells them apart); the schedule still gives the oracle's values."""
+    desc = capi.Plan(W.workload_12q(), dtype="c64").describe().splitlines()
+    fwd = " ".join(l for l in desc if l.startswith("fwd["))
+    rev = " ".join(l for l in desc if l.startswith("rev["))
+    assert fwd.count("D[") == 5 and rev.count("D[") == 6
+    for m in re.finditer(r"D\[([^\]]*)\]", fwd + rev):
+        assert len(m.group(1).split()) == 12
+    closing = re.findall(r"\{lo\d+: (?:G\d+s ?)+\}", rev)
+    assert len(closing) == 3
+
+    base = W.layered_ansatz(6, 2, 6, "cz_ring", encode="every", terms=W.zz_chain(6), name="lead")
+    c = W.Circuit(n=6, gates=[(W.CZ, 0, 1, -1, -1, 1.0), (W.CZ, 2, 3, -1, -1, 1.0)] + base.gates,
+                  terms=base.terms, n_obs=base.n_obs, n_weights=base.n_weights, n_inputs=base.n_inputs,
+                  name="lead_cz")
+    rev = " ".join(l for l in capi.Plan(c, dtype="c64").describe().splitlines() if l.startswith("rev["))
+    pairs = [p for m in re.finditer(r"D\[([^\]]*)\]", rev) for p in m.group(1).split()]
+    assert pairs.count("0,1") == 2 and pairs.count("2,3") == 2   # the two rings' copies only
+    _emulate_vs_oracle(c, 2, 11)
+    _emulate_vs_oracle(base, 2, 11)
+
+
 def test_work_linear_in_depth_host():
     """Fig. 2 / Sec. III: the cost of a gradient grows linearly with the
     circuit depth.  The plan's adjoint arithmetic per sample for the

@@ -75,12 +75,14 @@ size_t cpx_table_offset(const Plan &P, const PassDesc &pd)
                            P.state_qubits, pd.phi_src == SRC_ANALYTIC ? pd.analytic_ents : 0) - 1024;
 }
 
-// The DIAG sign mask of the thread's 16 registers as an expression (constant
-// part folded).
-std::string diag_mask(const Plan &P, const DevOp &op, int lo)
+// The DIAG op as sign flips of single registers: a register's sign is its
+// constant part (CZ pairs of two register bits) XOR the thread's sign words,
+// one per register bit paired with thread bits and one for the pairs of two
+// thread bits, each computed once per op.
+std::string diag_flip_cpx(const Plan &P, const DevOp &op, int lo, bool rev)
 {
     uint32_t C = 0;
-    std::vector<std::vector<int>> per_reg(4);
+    std::vector<std::vector<int>> per_reg(kRegBits);
     std::vector<std::pair<int, int>> other;
     for (int k = op.a; k < op.a + op.b; ++k) {
         const DiagPair dp = P.diag_pairs[k];
@@ -91,22 +93,33 @@ std::string diag_mask(const Plan &P, const DevOp &op, int lo)
         else other.push_back({dp.a, dp.b});
     }
     std::ostringstream o;
-    o << "uint32_t m = 0x" << std::hex << C << std::dec << "u;";
-    for (int r = 0; r < 4; ++r) {
+    o << "{";
+    for (int r = 0; r < kRegBits; ++r) {
         if (per_reg[r].empty()) continue;
-        o << " m ^= (0u - ((";
+        o << " const uint32_t t" << r << " = (0u - ((";
         for (size_t i = 0; i < per_reg[r].size(); ++i) o << (i ? " ^ " : "") << operand_bit(per_reg[r][i]);
-        o << ") & 1u)) & " << kRegMask[r] << ";";
+        o << ") & 1u)) & 0x80000000u;";
     }
     if (!other.empty()) {
-        o << " m ^= (0u - ((";
+        o << " const uint32_t to = (0u - ((";
         for (size_t i = 0; i < other.size(); ++i)
             o << (i ? " ^ " : "") << "(" << operand_bit(other[i].first) << " & " << operand_bit(other[i].second) << ")";
-        o << ") & 1u)) & 0xFFFFu;";
+        o << ") & 1u)) & 0x80000000u;";
     }
+    for (int j = 0; j < (1 << kRegBits); ++j) {
+        std::string s;
+        for (int r = 0; r < kRegBits; ++r)
+            if (((j >> r) & 1) && !per_reg[r].empty()) s += (s.empty() ? "t" : " ^ t") + std::to_string(r);
+        if (!other.empty()) s += s.empty() ? "to" : " ^ to";
+        const bool c = (C >> j) & 1u;
+        if (s.empty() && !c) continue;
+        if (s.empty()) s = "0x80000000u";
+        else if (c) s += " ^ 0x80000000u";
+        o << " flip_reg<" << (rev ? "true" : "false") << ", " << j << ">(p, q, " << s << ");";
+    }
+    o << " }";
     return o.str();
 }
-
 
 // Phases emitted straight-line (default; measured 5 % faster at 12 and 20
 // qubits) or as a loop over a phase table with one copy of each distinct phase
@@ -391,7 +404,7 @@ void cpx_op(std::ostringstream &o, const Plan &P, const PassDesc &pd, int k, int
         o << " }\n";
         break;
     case OP_DIAG:
-        o << "        { " << diag_mask(P, op, lo) << " flip_cpx<" << (rev ? "true" : "false") << ">(p, q, m); }\n";
+        o << "        " << diag_flip_cpx(P, op, lo, rev) << "\n";
         break;
     case OP_CNOT: {
         const int rt = op.b - lo;

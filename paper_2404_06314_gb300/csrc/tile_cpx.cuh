@@ -238,6 +238,15 @@ __device__ __forceinline__ void flip_cpx(f2 (&p)[kRegs], f2 (&q)[kRegs], uint32_
     }
 }
 
+// Negate register J (phi, and lam in reverse) by the sign word s (0 or 0x80000000).
+template <bool REV, int J>
+__device__ __forceinline__ void flip_reg(f2 (&p)[kRegs], f2 (&q)[kRegs], uint32_t s)
+{
+    const f2 v = ((f2)s << 32) | s;
+    p[J] ^= v;
+    if (REV) q[J] ^= v;
+}
+
 // ---- the phase interpreter on complex pairs (complex64 general kernels) ----
 
 // a <- U a on register bit RB with U read as four complex entries (the

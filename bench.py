@@ -137,7 +137,7 @@ class ClockSampler:
 # kernel kind the bench runs (profiles/ holds the summaries and commands);
 # reported as null for any other kernel kind.
 PROFILED_TRAFFIC = {
-    ("qnn12", "cpx"): (39.638016e6 + 0.000256e6, "profiles/qtm_gen_pass_cpx_qnn12_l6_b1024.md"),
+    ("qnn12", "cpx"): (39.654400e6 + 0.0, "profiles/qtm_gen_pass_cpx_qnn12_l6_b1024.md"),
     ("qnn20", "cpx"): ((0.537235e9 + 1.019508e9 + 1.073914e9 + 1.018413e9 + 1.073914e9 + 0.496884e9 +
                         0.536996e9 + 0.494335e9 + 0.537071e9 + 0.004366e9) / 5,
                        "profiles/qtm_gen_pass_cpx_qnn20_l4_b64.md (mean of reverse passes 0-4)"),

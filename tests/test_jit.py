@@ -190,12 +190,21 @@ def _run(plan, c, inp):
 
 
 CASES = [("qnn12", 37), ("qnn12", 1), ("qnn20", 2), ("qnn20", 3), ("qnn16", 3), ("rand9", 3), ("rand11", 4),
-         ("rand13", 3), ("rand14", 2), ("rand16", 5)]
+         ("rand13", 3), ("rand14", 2), ("rand16", 5), ("leadcz10", 5)]
+
+
+def _lead_cz10():
+    """CZ rings merged into one diagonal op each, and leading CZs on qubits
+    no rotation has touched yet, which the last reverse pass leaves out."""
+    base = W.layered_ansatz(10, 3, 10, "cz_ring", encode="every", terms=W.zz_chain(10), name="lead")
+    gates = [(W.CZ, 0, 1, -1, -1, 1.0), (W.CZ, 2, 3, -1, -1, 1.0), (W.CZ, 7, 9, -1, -1, 1.0)] + base.gates
+    return W.Circuit(n=10, gates=gates, terms=base.terms, n_obs=base.n_obs, n_weights=base.n_weights,
+                     n_inputs=base.n_inputs, name="leadcz10")
 
 
 def _circuit(name):
-    return {"qnn12": W.workload_12q, "qnn20": W.workload_20q, "qnn16": W.workload_16q_train}.get(
-        name, lambda: _rand(int(name[4:]), 600 + int(name[4:])))()
+    return {"qnn12": W.workload_12q, "qnn20": W.workload_20q, "qnn16": W.workload_16q_train,
+            "leadcz10": _lead_cz10}.get(name, lambda: _rand(int(name[4:]), 600 + int(name[4:])))()
 
 
 @pytest.mark.gpu

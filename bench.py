@@ -144,7 +144,7 @@ PROFILED_TRAFFIC = {
 }
 
 
-def roofline(r, peaks, peak_src, alu_peak=None):
+def roofline(r, peaks, peak_src, alu_peak=None, ceiling=None):
     """Roofline of the dominant kernel, the reverse pass (the specialised
     qtm_gen_pass by default; for one-tile-per-sample plans its launch also
     runs the sample's gradient finalize), from its live CUDA-event durations
@@ -184,7 +184,29 @@ def roofline(r, peaks, peak_src, alu_peak=None):
                  "launch_ms": t * 1e3, "launches_timed": n,
                  "work_per_launch": {"flop": flops, "state_bytes": bytes_},
                  "other": {k: other[k] for k in ("bound", "achieved", "peak", "unit", "frac")}})
+    if ceiling is not None and main["bound"] == "alu" and r["kernels"] == "cpx":
+        main["measured_ceiling"] = {
+            "value": ceiling, "unit": "TFLOP/s", "frac": alu / ceiling,
+            "source": "qtm_debug_gate_rate: the complex-pair kernels' gradient sums and gates in a "
+                      "register-only loop at two CTAs per SM on this GPU (context; frac above is of the "
+                      "derived peak)"}
     return main
+
+
+def gate_rate_tflops() -> float:
+    """Measured throughput of the complex-pair kernels' reverse arithmetic on
+    this GPU (qtm_debug_gate_rate), TFLOP/s."""
+    import ctypes
+
+    from paper_2404_06314_gb300 import capi
+    L = capi.lib()
+    L.qtm_debug_gate_rate.argtypes = [ctypes.POINTER(ctypes.c_double)]
+    L.qtm_debug_gate_rate.restype = ctypes.c_int
+    v = ctypes.c_double()
+    st = L.qtm_debug_gate_rate(ctypes.byref(v))
+    if st != capi.QTM_OK:
+        raise capi.QtmError(st, "qtm_debug_gate_rate")
+    return v.value / 1e12
 
 
 def dist_env():
@@ -997,6 +1019,7 @@ def gpu_main(args):
     K = args.steps
     B = r12["B"]
     value = B * K * ws / (total_ms / 1e3)
+    ceiling = gate_rate_tflops() if args.kernels == "cpx" else None   # after every timed region
     info = r12["info"]
     cfgd = WORKLOADS[args.workload]
     line = {
@@ -1007,7 +1030,7 @@ def gpu_main(args):
         "config": {"workload": cfgd["desc"], "global_batch": B * ws, "per_gpu_batch": B,
                    "path": cfgd["path_desc"], "l2": "flushed between steps (256 MiB write)",
                    "parallelism": f"batch shards x{ws}", "pass_kernels": args.kernels},
-        "roofline": roofline(r12, peaks, peak_src),
+        "roofline": roofline(r12, peaks, peak_src, ceiling=ceiling),
         "gpu_launches": r12["launches"],
         "clocks": clocks,
         "e2e": {"value": e2e[0], "unit": "samples/s", "h2d_bytes_per_step": e2e[1],
@@ -1025,7 +1048,7 @@ def gpu_main(args):
             "ms_per_step": tot20 / K20, "steps": K20,
             "config": {"workload": WORKLOADS["qnn20"]["desc"], "per_gpu_batch": r20["B"],
                        "path": WORKLOADS["qnn20"]["path_desc"]},
-            "roofline": roofline(r20, peaks, peak_src),
+            "roofline": roofline(r20, peaks, peak_src, ceiling=ceiling),
             "plan": {k: i20[k] for k in ("fwd_passes", "adj_passes", "fwd_flops", "adj_flops",
                                           "fwd_state_bytes", "adj_state_bytes")},
             "gpu_launches": r20["launches"],

@@ -46,6 +46,17 @@ qtm_status qtm_debug_jit_compile(qtm_plan *plan, int flags);
  * bound at 12 qubits; not used by any compute call. */
 qtm_status qtm_debug_fma_rate(int dtype, double *flops_per_s);
 
+/* Measured throughput of the complex-pair kernels' own reverse arithmetic on
+ * this GPU, flop/s counted as the plans count it (a gradient op with its two
+ * gates: 40 flop per amplitude): a register-only loop over the kernels'
+ * gradient sums and gates (f32x2 FMAs), 256 threads with the register budget
+ * of two CTAs per SM, four waves, best of three launches timed with CUDA
+ * events on the current device.  It shows how much of the derived FP32 peak
+ * this arithmetic can reach at all (the f32x2 FMAs' operands, not the FMA
+ * units, limit it); a context figure for the 12-qubit reverse pass's
+ * roofline, not used by any compute call.  Synchronises the device. */
+qtm_status qtm_debug_gate_rate(double *flops_per_s);
+
 /* The uneven batch's task list (host only), in the order the persistent
  * kernel hands tasks out: tasks[3i .. 3i+2] = (item, step, tile); step = -1
  * is a whole item, step >= 0 one pass (forward passes, then reverse passes)

@@ -1167,6 +1167,27 @@ qtm_status qtm_debug_fma_rate(int dtype, double *flops_per_s)
     return e == cudaSuccess ? QTM_OK : QTM_ECUDA;
 }
 
+qtm_status qtm_debug_gate_rate(double *flops_per_s)
+{
+    if (!flops_per_s) return QTM_EINVAL;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return QTM_ECUDA;
+    const int blocks = sms * 2 * 4;   // four waves of two CTAs per SM
+    // an SU(2) matrix a = 0.6 + 0.48i, b = 0.64 (|a|^2 + |b|^2 = 1) in the
+    // broadcast form of the complex-pair tables, then 16 amplitude pairs
+    float tab[44] = {0.6f, 0.6f, -0.48f, 0.48f, 0.64f, 0.64f, -0.f, 0.f, -0.64f, -0.64f, 0.48f, -0.48f};
+    for (int j = 0; j < 16; ++j) { tab[12 + 2 * j] = 0.25f; tab[13 + 2 * j] = 0.125f * (float)((j & 3) - 1); }
+    float *out = nullptr, *dtab = nullptr;
+    if (cudaMalloc(&out, (size_t)blocks * 256 * sizeof(float)) != cudaSuccess) return QTM_ENOMEM;
+    if (cudaMalloc(&dtab, sizeof(tab)) != cudaSuccess) { cudaFree(out); return QTM_ENOMEM; }
+    cudaError_t e = cudaMemcpy(dtab, tab, sizeof(tab), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = probe_gate_rate(out, dtab, blocks, 1 << 11, nullptr, flops_per_s);
+    cudaFree(dtab);
+    cudaFree(out);
+    return e == cudaSuccess ? QTM_OK : QTM_ECUDA;
+}
+
 qtm_status qtm_jacobian(qtm_plan *p, int B, const void *x, const void *w, void *jac, void *stream)
 {
     NvtxRange nvtx_range("qtm_jacobian");

@@ -76,6 +76,7 @@ cudaError_t launch_accumulate_cols(int dtype, const void *src, int Gs, void *dst
 // J [B][M][G], and the expansion of per-sample rows (states, inputs).
 cudaError_t launch_onehot(int dtype, void *gE, int Bp, int M, int m0, int cc, cudaStream_t s);
 cudaError_t probe_fma_rate(int dtype, void *out, int blocks, int iters, cudaStream_t s, double *flops_per_s);
+cudaError_t probe_gate_rate(float *out, const float *tab, int blocks, int iters, cudaStream_t s, double *flops_per_s);
 cudaError_t launch_expand_rows(const void *src, void *dst, size_t row_bytes, int Bp, int cc, cudaStream_t s);
 cudaError_t launch_expand_x(int dtype, const void *x, void *xp, int n_in, int Bp, int cc, cudaStream_t s);
 

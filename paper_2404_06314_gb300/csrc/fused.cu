@@ -218,6 +218,40 @@ __global__ void k_fma_probe(R *out, int iters, R a, R b)
     out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = t;
 }
 
+// The complex-pair kernels' reverse arithmetic on registers only: per round
+// and register bit, a run's gradient sums (grad_cpx) and its gate on phi and
+// lam (su2_apply), 256 threads with the register budget of two CTAs per SM,
+// as the 12-qubit reverse pass runs.  `tab` holds six f32x2 table pairs
+// (an SU(2) matrix in broadcast form) and 16 amplitude pairs; one store per
+// thread keeps everything live.
+__global__ void __launch_bounds__(256, 2) k_gate_probe(float *out, int iters, const float *tab)
+{
+    f2 p[kRegs], q[kRegs], t[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) t[k] = pack2(tab[2 * k], tab[2 * k + 1]);
+    const float d = 1e-3f * (float)(threadIdx.x & 31);
+#pragma unroll
+    for (int j = 0; j < kRegs; ++j) {
+        p[j] = pack2(tab[12 + 2 * j] + d, tab[13 + 2 * j]);
+        q[j] = pack2(tab[13 + 2 * j], tab[12 + 2 * j] - d);
+    }
+    float acc = 0.f;
+    for (int it = 0; it < iters; ++it) {
+        float vx, vy, vz;
+        grad_cpx<3>(p, q, vx, vy, vz); acc += vx + vy + vz;
+        su2_apply<3>(p, t[0], t[1], t[2], t[3], t[4], t[5]); su2_apply<3>(q, t[0], t[1], t[2], t[3], t[4], t[5]);
+        grad_cpx<2>(p, q, vx, vy, vz); acc += vx + vy + vz;
+        su2_apply<2>(p, t[0], t[1], t[2], t[3], t[4], t[5]); su2_apply<2>(q, t[0], t[1], t[2], t[3], t[4], t[5]);
+        grad_cpx<1>(p, q, vx, vy, vz); acc += vx + vy + vz;
+        su2_apply<1>(p, t[0], t[1], t[2], t[3], t[4], t[5]); su2_apply<1>(q, t[0], t[1], t[2], t[3], t[4], t[5]);
+        grad_cpx<0>(p, q, vx, vy, vz); acc += vx + vy + vz;
+        su2_apply<0>(p, t[0], t[1], t[2], t[3], t[4], t[5]); su2_apply<0>(q, t[0], t[1], t[2], t[3], t[4], t[5]);
+    }
+#pragma unroll
+    for (int j = 0; j < kRegs; ++j) acc += lane0(p[j]) + lane1(q[j]);
+    out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = acc;
+}
+
 cudaError_t launch_expand_rows(const void *src, void *dst, size_t row_bytes, int Bp, int cc, cudaStream_t s)
 {
     if (Bp <= 0 || row_bytes == 0) return cudaSuccess;
@@ -403,6 +437,35 @@ cudaError_t probe_fma_rate(int dtype, void *out, int blocks, int iters, cudaStre
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (e == cudaSuccess) *flops_per_s = 2.0 * 8.0 * (double)iters * blocks * 256.0 / (best * 1e-3);
+    return e;
+}
+
+
+// Throughput of k_gate_probe (flop/s counted as the plans count a gradient
+// op with its two gates: 40 flop per amplitude) over `blocks` CTAs; `out`
+// holds one float per thread, `tab` the 44 floats the kernel reads.
+cudaError_t probe_gate_rate(float *out, const float *tab, int blocks, int iters, cudaStream_t s, double *flops_per_s)
+{
+    cudaEvent_t e0, e1;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e != cudaSuccess) return e;
+    e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) { cudaEventDestroy(e0); return e; }
+    float best = 1e30f;
+    for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
+        cudaEventRecord(e0, s);
+        k_gate_probe<<<blocks, 256, 0, s>>>(out, iters, tab);
+        cudaEventRecord(e1, s);
+        e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaGetLastError();
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0 && ms > 0.f) best = std::min(best, ms);   // the first launch is a warm-up
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    // per round and thread: 4 gradient ops of 16 amplitudes at 40 flop each
+    if (e == cudaSuccess) *flops_per_s = 4.0 * 16.0 * 40.0 * (double)iters * blocks * 256.0 / (best * 1e-3);
     return e;
 }
 

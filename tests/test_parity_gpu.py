@@ -429,3 +429,20 @@ def test_fma_rate_probe():
     assert 10e12 < r32.value < 200e12, r32.value
     assert 0 < r64.value < r32.value, (r64.value, r32.value)
     assert L.qtm_debug_fma_rate(7, ctypes.byref(r64)) == capi.QTM_EINVAL
+
+
+def test_gate_rate_probe():
+    """qtm_debug_gate_rate (the measured ceiling the bench reports beside the
+    reverse pass's roofline) gives a throughput between a fifth of the
+    derived FP32 peak and that peak, and rejects a null result pointer."""
+    import ctypes
+    import torch
+    L = capi.lib()
+    L.qtm_debug_gate_rate.argtypes = [ctypes.POINTER(ctypes.c_double)]
+    L.qtm_debug_gate_rate.restype = ctypes.c_int
+    r = ctypes.c_double()
+    assert L.qtm_debug_gate_rate(ctypes.byref(r)) == capi.QTM_OK
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    peak = sms * 128 * 2 * 2.1e9   # derived FP32 peak at the highest clock this GPU reaches, with margin
+    assert 0.2 * peak < r.value < peak, (r.value, peak)
+    assert L.qtm_debug_gate_rate(None) == capi.QTM_EINVAL
